@@ -1,0 +1,984 @@
+// fsp_oracle.cpp -- TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow CPU restatement of the WENO-interpolation-based, upwind-biased,
+// free-stream-preserving (WENOIU) schemes of Q. Li and D. Sun, "WENO interpolation-based
+// and upwind-biased schemes with free-stream preservation" (arXiv:1810.11103).
+// It is the oracle that the CUDA library is checked against.  Only the test suite,
+// the smoke check and the CPU-baseline leg of the benchmark may load it; the product
+// path never does.  It shares no code, header or table with the CUDA library.
+//
+// Everything is written as loops over lines, nodes and interfaces in the order the
+// paper states the method: no tiling, fusion or reordering.  Build: g++ -O2
+// -ffp-contract=off (no fused multiply-add), so every product is rounded on its own.
+//
+// The core is templated on the scalar type:
+//   double       the oracle proper (FP64)
+//   long double  higher precision; shows the free-stream residual is round-off
+//   Dual         forward-mode tangent (value + one directional derivative)
+//   Counted      counts floating-point operations (+ - * / sqrt, one each)
+//
+// Conventions (identical in meaning, not in code, to the CUDA library):
+//   * nodes (i, j), i fastest; unit computational spacing (d xi = d eta = 1);
+//   * state Q = (rho, rho u, rho v, E), 4 planes [4][nj][ni];
+//   * metrics: 5 planes (xi_x^, xi_y^, eta_x^, eta_y^, J^-1) on a grid extended by
+//     G = 4 ghost layers on every side: plane p, node (i, j) at
+//     M[p*(nj+8)*(ni+8) + (j+4)*(ni+8) + (i+4)];
+//   * boundary faces 0..3 = i-min, i-max, j-min, j-max; codes PERIODIC=0,
+//     TRANSMISSIVE=1, DIRICHLET=2, SLIPWALL=3, FARFIELD=4.
+//
+// Readings of points the paper leaves open are marked "Reading:" where they are used.
+// Parity status: every routine is pinned by the tests in tests/test_oracle_*.py
+// (Table 3 and Table 4 of the paper, free-stream preservation, closed forms,
+// symmetry, conservation, tangent vs finite differences); none is "parity unpinned".
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+namespace orc {
+
+// ----------------------------------------------------------------------------------
+// Scalar types
+// ----------------------------------------------------------------------------------
+struct Dual {
+  double v, d;
+  Dual() : v(0), d(0) {}
+  Dual(double a) : v(a), d(0) {}
+  Dual(double a, double b) : v(a), d(b) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+inline Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
+inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
+inline bool operator<=(Dual a, Dual b) { return a.v <= b.v; }
+inline bool operator>=(Dual a, Dual b) { return a.v >= b.v; }
+inline Dual sqrt(Dual a) {
+  double s = std::sqrt(a.v);
+  return Dual(s, s > 0 ? a.d / (2.0 * s) : 0.0);
+}
+inline Dual fabs(Dual a) { return a.v >= 0 ? a : -a; }
+inline double val(Dual a) { return a.v; }
+
+static long long g_flops = 0;
+struct Counted {
+  double v;
+  Counted() : v(0) {}
+  Counted(double a) : v(a) {}
+};
+inline Counted operator+(Counted a, Counted b) { ++g_flops; return Counted(a.v + b.v); }
+inline Counted operator-(Counted a, Counted b) { ++g_flops; return Counted(a.v - b.v); }
+inline Counted operator-(Counted a) { return Counted(-a.v); }
+inline Counted operator*(Counted a, Counted b) { ++g_flops; return Counted(a.v * b.v); }
+inline Counted operator/(Counted a, Counted b) { ++g_flops; return Counted(a.v / b.v); }
+inline Counted& operator+=(Counted& a, Counted b) { a = a + b; return a; }
+inline Counted& operator-=(Counted& a, Counted b) { a = a - b; return a; }
+inline Counted& operator*=(Counted& a, Counted b) { a = a * b; return a; }
+inline bool operator<(Counted a, Counted b) { return a.v < b.v; }
+inline bool operator>(Counted a, Counted b) { return a.v > b.v; }
+inline bool operator<=(Counted a, Counted b) { return a.v <= b.v; }
+inline bool operator>=(Counted a, Counted b) { return a.v >= b.v; }
+inline Counted sqrt(Counted a) { ++g_flops; return Counted(std::sqrt(a.v)); }
+inline Counted fabs(Counted a) { return Counted(std::fabs(a.v)); }
+inline double val(Counted a) { return a.v; }
+
+inline double val(double a) { return a; }
+inline double val(long double a) { return (double)a; }
+using std::sqrt;
+using std::fabs;
+
+template <class T> inline T cst(long double c) { return T((double)c); }
+template <> inline long double cst<long double>(long double c) { return c; }
+
+// ----------------------------------------------------------------------------------
+// Scheme tables (Section 3).  All four variants, with the printed coefficients.
+// ----------------------------------------------------------------------------------
+enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, BC_FARFIELD = 4 };
+static const int G = 4;  // ghost layers of the stored metrics
+
+struct SchemeTab {
+  int r;                  // points of each WENO candidate stencil (Table 1)
+  long double hmid[2];    // h+ coefficient of f+_{j+1/2+m}, m = 0, -1
+  long double hnode[5];   // h+ coefficient of f+_{j+k}, k = -2..2
+  long double cnode[3];   // delta^{c,(1)}: a_k multiplying (f_{j+k} - f_{j-k}), k = 1..3
+  long double cmid[2];    // delta^{c,(1)}: b_m multiplying (f~_{j+m} - f~_{j-m}), m = 1/2, 3/2
+};
+
+static const SchemeTab TAB[4] = {
+  // WENOIU3-1MP: h+ of Eq. (3.4); delta^{c,(1)} of Eq. (3.7).
+  {2, {1.0L, 0.0L}, {0.0L, -1.0L / 24, 2.0L / 24, -1.0L / 24, 0.0L},
+   {2.0L / 48, -1.0L / 48, 0.0L}, {1.0L, 0.0L}},
+  // WENOIU3-2MP: h+ of Eq. (3.8), f_{j+1/2} + (-f_{j-1/2} + 2 f_j - f_{j+1/2})/6;
+  // delta^{c,(1)} of Eq. (3.9).
+  {2, {1.0L - 1.0L / 6, -1.0L / 6}, {0.0L, 0.0L, 2.0L / 6, 0.0L, 0.0L},
+   {2.0L / 12, 0.0L, 0.0L}, {11.0L / 12, -1.0L / 12}},
+  // WENOIU5-1MP: h+ of Eq. (3.16); delta^{c,(1)} of Eq. (3.19).
+  {3, {1.0L, 0.0L}, {19.0L / 1920, -29.0L / 480, 77.0L / 960, -3.0L / 160, -7.0L / 640},
+   {17.0L / 256, -13.0L / 320, 19.0L / 3840}, {1.0L, 0.0L}},
+  // WENOIU5-2MP: h+ of Eq. (3.20), f_{j+1/2} + [(-4 f_{j+1} + f_j + f_{j-1}) + (6 f_{j+1/2}
+  // - 4 f_{j-1/2})]/30; delta^{c,(1)} of Eq. (3.21).
+  {3, {1.0L + 6.0L / 30, -4.0L / 30}, {0.0L, 1.0L / 30, 1.0L / 30, -4.0L / 30, 0.0L},
+   {-4.0L / 60, 1.0L / 60, 0.0L}, {19.0L / 15, -1.0L / 15}},
+};
+
+// ----------------------------------------------------------------------------------
+// Run parameters
+// ----------------------------------------------------------------------------------
+template <class T>
+struct Par {
+  int scheme = S51;
+  int interp = 0;      // midpoint interpolation of nodal metric/coordinate values:
+                       // 0 = central Lagrange matched to the order (4 points for the
+                       //     third-order schemes, 6 points for the fifth-order ones),
+                       // 1 = two-point average.
+  int ppm = 1;         // 1: piecewise-polynomial mapping of the weights, Eq. (3.15)/(3.23)
+  int linw = 0;        // 1: linear weights omega_k = C_k (no mapping)
+  int bc[4] = {0, 0, 0, 0};
+  T gamma = T(1.4), alpha = cst<T>(1.1L), eps = cst<T>(1e-40L);
+  T bcq[4][4];
+  int ni = 0, nj = 0;
+};
+
+template <class T>
+static void unpack(const int* ip, const double* dp, int ni, int nj, Par<T>& P) {
+  P.scheme = ip[0]; P.interp = ip[1]; P.ppm = ip[2]; P.linw = ip[3];
+  for (int f = 0; f < 4; ++f) P.bc[f] = ip[4 + f];
+  P.gamma = T(dp[0]); P.alpha = T(dp[1]); P.eps = T(dp[2]);
+  for (int f = 0; f < 4; ++f)
+    for (int v = 0; v < 4; ++v) P.bcq[f][v] = T(dp[3 + 4 * f + v]);
+  P.ni = ni; P.nj = nj;
+}
+
+static inline int floordiv(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+
+// ----------------------------------------------------------------------------------
+// Midpoint interpolation I of nodal values along one grid direction (Section 2.4).
+// Reading: the paper asks for a "directionally consistent" linear interpolation and
+// names none.  Default: the central Lagrange interpolant whose order matches the
+// scheme; option: the two-point average.  phi(k) returns the nodal value at offset k
+// from node j; the result approximates the value at j + 1/2.
+// ----------------------------------------------------------------------------------
+template <class T, class F>
+static T interp_mid(int scheme, int interp, F phi) {
+  if (interp == 1) return (phi(0) + phi(1)) * cst<T>(0.5L);
+  if (scheme == S31 || scheme == S32)   // 4-point Lagrange
+    return (cst<T>(-1) * phi(-1) + cst<T>(9) * phi(0) + cst<T>(9) * phi(1) - phi(2)) / cst<T>(16);
+  // 6-point Lagrange
+  return (cst<T>(3) * phi(-2) - cst<T>(25) * phi(-1) + cst<T>(150) * phi(0) + cst<T>(150) * phi(1)
+          - cst<T>(25) * phi(2) + cst<T>(3) * phi(3)) / cst<T>(256);
+}
+
+// ----------------------------------------------------------------------------------
+// Coordinates with ghost nodes.
+// Reading (boundaries are not treated in the paper): a periodic direction wraps and
+// adds the period vector per wrap; any other direction extends the grid by odd
+// reflection about the boundary node, x_{-k} = 2 x_0 - x_k.
+// ----------------------------------------------------------------------------------
+template <class T>
+struct Coords {
+  int ni, nj, bc[4];
+  T per[2][2];          // per[0] = (dx, dy) added per wrap in i, per[1] likewise in j
+  const T* x; const T* y;
+  void at(int i, int j, T& X, T& Y) const {
+    if (j < 0 || j >= nj) {
+      if (bc[2] == BC_PERIODIC) {
+        int q = floordiv(j, nj);
+        at(i, j - q * nj, X, Y);
+        X = X + T(double(q)) * per[1][0]; Y = Y + T(double(q)) * per[1][1];
+        return;
+      }
+      int jb = (j < 0) ? 0 : nj - 1;
+      T X0, Y0, X1, Y1;
+      at(i, jb, X0, Y0); at(i, 2 * jb - j, X1, Y1);
+      X = cst<T>(2) * X0 - X1; Y = cst<T>(2) * Y0 - Y1;
+      return;
+    }
+    if (i < 0 || i >= ni) {
+      if (bc[0] == BC_PERIODIC) {
+        int q = floordiv(i, ni);
+        at(i - q * ni, j, X, Y);
+        X = X + T(double(q)) * per[0][0]; Y = Y + T(double(q)) * per[0][1];
+        return;
+      }
+      int ib = (i < 0) ? 0 : ni - 1;
+      T X0, Y0, X1, Y1;
+      at(ib, j, X0, Y0); at(2 * ib - i, j, X1, Y1);
+      X = cst<T>(2) * X0 - X1; Y = cst<T>(2) * Y0 - Y1;
+      return;
+    }
+    X = x[(size_t)j * ni + i]; Y = y[(size_t)j * ni + i];
+  }
+};
+
+// Central operator delta^{c,(1)} of the scheme (Eq. 2.7 and Eqs. 3.7/3.9/3.19/3.21),
+// applied along direction dir at node (i, j) to the coordinate component comp
+// (0 = x, 1 = y).  Midpoint values f~ come from the interpolation I above.
+template <class T>
+static T central_D(const Par<T>& P, const Coords<T>& C, int dir, int comp, int i, int j) {
+  const SchemeTab& S = TAB[P.scheme];
+  auto node = [&](int k) {
+    T X, Y;
+    if (dir == 0) C.at(i + k, j, X, Y); else C.at(i, j + k, X, Y);
+    return comp == 0 ? X : Y;
+  };
+  // midpoint value at node offset k + 1/2
+  auto mid = [&](int k) {
+    return interp_mid<T>(P.scheme, P.interp, [&](int l) { return node(k + l); });
+  };
+  T d = T(0);
+  for (int k = 1; k <= 3; ++k)
+    if (S.cnode[k - 1] != 0.0L) d = d + cst<T>(S.cnode[k - 1]) * (node(k) - node(-k));
+  // b_{1/2} (f~_{j+1/2} - f~_{j-1/2}) + b_{3/2} (f~_{j+3/2} - f~_{j-3/2})
+  d = d + cst<T>(S.cmid[0]) * (mid(0) - mid(-1));
+  if (S.cmid[1] != 0.0L) d = d + cst<T>(S.cmid[1]) * (mid(1) - mid(-2));
+  return d;
+}
+
+// Conservative metrics in two dimensions (Eq. 2.3 with z = zeta) and the Jacobian
+// (Eq. 2.5, whose 2-D form reduces to x_xi y_eta - x_eta y_xi), on the grid extended by
+// G ghost layers.  Every derivative uses the scheme's central operator (Section 2.3).
+template <class T>
+static void metrics(const Par<T>& P, const Coords<T>& C, T* M) {
+  const int ni = P.ni, nj = P.nj, W = ni + 2 * G, H = nj + 2 * G;
+  const size_t plane = (size_t)W * H;
+  for (int j = -G; j < nj + G; ++j)
+    for (int i = -G; i < ni + G; ++i) {
+      T x_xi = central_D(P, C, 0, 0, i, j), y_xi = central_D(P, C, 0, 1, i, j);
+      T x_eta = central_D(P, C, 1, 0, i, j), y_eta = central_D(P, C, 1, 1, i, j);
+      size_t o = (size_t)(j + G) * W + (i + G);
+      M[0 * plane + o] = y_eta;        // xi_x^  =  y_eta
+      M[1 * plane + o] = -x_eta;       // xi_y^  = -x_eta
+      M[2 * plane + o] = -y_xi;        // eta_x^ = -y_xi
+      M[3 * plane + o] = x_xi;         // eta_y^ =  x_xi
+      M[4 * plane + o] = x_xi * y_eta - x_eta * y_xi;  // J^-1
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// Euler flux, primitives, eigenvectors (Section 2.1, Section 3.4)
+// ----------------------------------------------------------------------------------
+template <class T>
+static T pressure(const T* q, T gamma) {
+  T u = q[1] / q[0], v = q[2] / q[0];
+  return (gamma - cst<T>(1)) * (q[3] - cst<T>(0.5L) * q[0] * (u * u + v * v));
+}
+
+// Metric-weighted flux E^ = mx E + my F (Eq. 2.2, 2-D).
+template <class T>
+static void flux(const T* q, T mx, T my, T gamma, T* f) {
+  T rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  T p = (gamma - cst<T>(1)) * (q[3] - cst<T>(0.5L) * rho * (u * u + v * v));
+  T U = mx * u + my * v;
+  f[0] = rho * U;
+  f[1] = rho * u * U + mx * p;
+  f[2] = rho * v * U + my * p;
+  f[3] = (q[3] + p) * U;
+}
+
+// |U^| + c |k^| at a node (the spectral radius inside the MAX of Section 2.3).
+template <class T>
+static T spectral(const T* q, T mx, T my, T gamma) {
+  T rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  T p = (gamma - cst<T>(1)) * (q[3] - cst<T>(0.5L) * rho * (u * u + v * v));
+  T c = sqrt(gamma * p / rho);
+  return fabs(mx * u + my * v) + c * sqrt(mx * mx + my * my);
+}
+
+// Left/right eigenvectors of the Jacobian of the flux in direction n (unit vector),
+// evaluated at state q (Section 3.4).  Reading: the standard normalisation of the 2-D
+// Euler eigenvectors; R columns are the acoustic, entropy, shear and acoustic waves.
+template <class T>
+static void eigvec(const T* q, T nx, T ny, T gamma, T L[4][4], T R[4][4]) {
+  T rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  T q2 = u * u + v * v;
+  T p = (gamma - cst<T>(1)) * (q[3] - cst<T>(0.5L) * rho * q2);
+  T c = sqrt(gamma * p / rho);
+  T H = (q[3] + p) / rho;
+  T Un = u * nx + v * ny, Ut = v * nx - u * ny;
+  T b1 = (gamma - cst<T>(1)) / (c * c), b2 = cst<T>(0.5L) * b1 * q2;
+  const T h = cst<T>(0.5L);
+  // right eigenvectors as columns
+  R[0][0] = T(1);           R[0][1] = T(1);              R[0][2] = T(0);  R[0][3] = T(1);
+  R[1][0] = u - c * nx;     R[1][1] = u;                 R[1][2] = -ny;   R[1][3] = u + c * nx;
+  R[2][0] = v - c * ny;     R[2][1] = v;                 R[2][2] = nx;    R[2][3] = v + c * ny;
+  R[3][0] = H - c * Un;     R[3][1] = h * q2;            R[3][2] = Ut;    R[3][3] = H + c * Un;
+  // left eigenvectors as rows
+  L[0][0] = h * (b2 + Un / c); L[0][1] = h * (-b1 * u - nx / c); L[0][2] = h * (-b1 * v - ny / c); L[0][3] = h * b1;
+  L[1][0] = T(1) - b2;         L[1][1] = b1 * u;                L[1][2] = b1 * v;                L[1][3] = -b1;
+  L[2][0] = -Ut;               L[2][1] = -ny;                   L[2][2] = nx;                    L[2][3] = T(0);
+  L[3][0] = h * (b2 - Un / c); L[3][1] = h * (-b1 * u + nx / c); L[3][2] = h * (-b1 * v + ny / c); L[3][3] = h * b1;
+}
+
+// ----------------------------------------------------------------------------------
+// WENO interpolation to the midpoint x_{j+1/2} (Eqs. 3.10-3.13, Table 1), smoothness
+// indicators of Eq. (3.22), mapping of Eq. (3.15) (r = 2) or Eq. (3.23) (r = 3).
+// u[0..4] = u_{j-2} .. u_{j+2}.
+// Reading (Section 5.1): the third-order (r = 2) interpolation takes IS_0 and IS_1 of
+// Eq. (3.22), i.e. the three-point stencils {j-2, j-1, j} and {j-1, j, j+1}, instead of
+// Eq. (3.14).  The indicators are written in the equivalent sum-of-squares form
+// (13/12 (second difference)^2 + 1/4 (first difference)^2), algebraically identical to the
+// printed quadratic forms.
+// ----------------------------------------------------------------------------------
+// With the consecutive differences da = b - a, db = c - b of a three-point stencil
+// (a, b, c): second difference a - 2b + c = db - da; the first-difference terms are
+// a - 4b + 3c = 3 db - da (IS_0), a - c = -(da + db) (IS_1), 3a - 4b + c = db - 3 da (IS_2).
+// Written on differences, every indicator is exactly zero on constant data.
+template <class T>
+static T is0(T a, T b, T c) {
+  T da = b - a, db = c - b;
+  T d2 = db - da, d1 = cst<T>(3) * db - da;
+  return cst<T>(13.0L / 12) * d2 * d2 + cst<T>(0.25L) * d1 * d1;
+}
+template <class T>
+static T is1(T a, T b, T c) {
+  T da = b - a, db = c - b;
+  T d2 = db - da, d1 = da + db;
+  return cst<T>(13.0L / 12) * d2 * d2 + cst<T>(0.25L) * d1 * d1;
+}
+template <class T>
+static T is2(T a, T b, T c) {
+  T da = b - a, db = c - b;
+  T d2 = db - da, d1 = db - cst<T>(3) * da;
+  return cst<T>(13.0L / 12) * d2 * d2 + cst<T>(0.25L) * d1 * d1;
+}
+
+// Piecewise-polynomial mapping g(omega) about C (Eq. 3.15 for order 2, Eq. 3.23 for 3).
+template <class T>
+static T ppm_map(int order, T w, T C) {
+  if (order == 2) {
+    if (w <= C) { T s = w / C - cst<T>(1); return C * (cst<T>(1) - s * s); }
+    T d = w - C; return C - d * d / (C - cst<T>(1));
+  }
+  if (w <= C) { T s = w / C - cst<T>(1); return C * (cst<T>(1) + s * s * s); }
+  T d = w - C, e = C - cst<T>(1);
+  return C + d * d * d / (e * e);
+}
+
+struct WenoOpt { int ppm, linw; };
+
+template <class T>
+static T weno_mid(int r, const T* u, const WenoOpt& o, T eps) {
+  // Table 1 coefficients b^r_{k,l} and C^r_k
+  static const long double b2[2][2] = {{-0.5L, 1.5L}, {0.5L, 0.5L}};
+  static const long double c2[2] = {0.25L, 0.75L};
+  static const long double b3[3][3] = {{3.0L / 8, -10.0L / 8, 15.0L / 8},
+                                       {-1.0L / 8, 6.0L / 8, 3.0L / 8},
+                                       {3.0L / 8, 6.0L / 8, -1.0L / 8}};
+  static const long double c3[3] = {1.0L / 16, 10.0L / 16, 5.0L / 16};
+  // u_{j+m} = u[m + 2]
+  T p[3], IS[3], Ck[3];
+  if (r == 3) {
+    for (int k = 0; k < 3; ++k) {
+      // p_k = sum_l b_{k,l} u_{j-r+k+l+1} (Eq. 3.11)
+      p[k] = T(0);
+      for (int l = 0; l < 3; ++l) p[k] = p[k] + cst<T>(b3[k][l]) * u[(k + l - 2) + 2];
+      Ck[k] = cst<T>(c3[k]);
+    }
+    IS[0] = is0(u[0], u[1], u[2]);
+    IS[1] = is1(u[1], u[2], u[3]);
+    IS[2] = is2(u[2], u[3], u[4]);
+  } else {
+    for (int k = 0; k < 2; ++k) {
+      p[k] = T(0);
+      for (int l = 0; l < 2; ++l) p[k] = p[k] + cst<T>(b2[k][l]) * u[(k + l - 1) + 2];
+      Ck[k] = cst<T>(c2[k]);
+    }
+    IS[0] = is0(u[0], u[1], u[2]);
+    IS[1] = is1(u[1], u[2], u[3]);
+  }
+  T w[3];
+  if (o.linw) {
+    for (int k = 0; k < r; ++k) w[k] = Ck[k];
+  } else {
+    // alpha_k = C_k / (eps + IS_k)^2, omega_k = alpha_k / sum alpha (Eqs. 3.12-3.13)
+    T a[3], s = T(0);
+    for (int k = 0; k < r; ++k) { T d = eps + IS[k]; a[k] = Ck[k] / (d * d); s = s + a[k]; }
+    for (int k = 0; k < r; ++k) w[k] = a[k] / s;
+    if (o.ppm) {
+      // map each omega_k with its own C_k, then normalise the mapped values
+      T g[3], sg = T(0);
+      for (int k = 0; k < r; ++k) { g[k] = ppm_map(r, w[k], Ck[k]); sg = sg + g[k]; }
+      for (int k = 0; k < r; ++k) w[k] = g[k] / sg;
+    }
+  }
+  T out = T(0);
+  for (int k = 0; k < r; ++k) out = out + w[k] * p[k];   // Eq. (3.10)
+  return out;
+}
+
+// ----------------------------------------------------------------------------------
+// Semi-discrete right-hand side (Sections 2.3, 3, 3.4)
+// ----------------------------------------------------------------------------------
+template <class T>
+struct Field {
+  const Par<T>& P;
+  const T* M;   // haloed metrics
+  const T* Q;   // [4][nj][ni]
+  size_t mplane() const { return (size_t)(P.ni + 2 * G) * (P.nj + 2 * G); }
+  T met(int p, int i, int j) const {
+    return M[p * mplane() + (size_t)(j + G) * (P.ni + 2 * G) + (i + G)];
+  }
+  T q(int v, int i, int j) const { return Q[(size_t)v * P.ni * P.nj + (size_t)j * P.ni + i]; }
+
+  // State at position s of line L in direction dir, with ghost values by the boundary
+  // rule of the face.  Reading (the paper does not treat boundaries): periodic wraps;
+  // transmissive copies the boundary node; Dirichlet gives the prescribed state; slip
+  // wall mirrors node s about the boundary node and reverses the velocity component
+  // along the boundary node's grid-direction normal; far field takes the prescribed
+  // state where the prescribed velocity enters through the face, else is transmissive.
+  void state(int dir, int L, int s, T* out) const {
+    const int n = dir == 0 ? P.ni : P.nj;
+    auto rd = [&](int ss, T* o) {
+      for (int v = 0; v < 4; ++v) o[v] = dir == 0 ? q(v, ss, L) : q(v, L, ss);
+    };
+    if (s >= 0 && s < n) { rd(s, out); return; }
+    const int face = 2 * dir + (s < 0 ? 0 : 1);
+    const int b = s < 0 ? 0 : n - 1;
+    switch (P.bc[face]) {
+      case BC_PERIODIC: { int ss = s - floordiv(s, n) * n; rd(ss, out); return; }
+      case BC_TRANSMISSIVE: rd(b, out); return;
+      case BC_DIRICHLET: for (int v = 0; v < 4; ++v) out[v] = P.bcq[face][v]; return;
+      case BC_SLIPWALL: {
+        int sm = 2 * b - s;
+        rd(sm, out);
+        T mx = dir == 0 ? met(0, b, L) : met(2, L, b);
+        T my = dir == 0 ? met(1, b, L) : met(3, L, b);
+        T mn = sqrt(mx * mx + my * my), nx = mx / mn, ny = my / mn;
+        T un = out[1] * nx + out[2] * ny;
+        out[1] = out[1] - cst<T>(2) * un * nx;
+        out[2] = out[2] - cst<T>(2) * un * ny;
+        return;
+      }
+      case BC_FARFIELD: {
+        T mx = dir == 0 ? met(0, b, L) : met(2, L, b);
+        T my = dir == 0 ? met(1, b, L) : met(3, L, b);
+        T sgn = s < 0 ? T(-1) : T(1);
+        T vn = sgn * (P.bcq[face][1] * mx + P.bcq[face][2] * my);   // outward momentum flux
+        if (vn < T(0)) { for (int v = 0; v < 4; ++v) out[v] = P.bcq[face][v]; }
+        else rd(b, out);
+        return;
+      }
+    }
+    rd(b, out);
+  }
+  void nodemet(int dir, int L, int s, T& mx, T& my) const {
+    if (dir == 0) { mx = met(0, s, L); my = met(1, s, L); }
+    else { mx = met(2, L, s); my = met(3, L, s); }
+  }
+};
+
+// A^ of the Lax-Friedrichs-type splitting (Section 2.3): alpha times the maximum of
+// |U^| + c |k^| over the interior nodes of the grid line.  Reading: the printed
+// MAX(U^ + c|k^|) is taken with |U^| (a wave speed), and the maximum runs over the
+// line's interior nodes; ties keep the lowest index (matters only for derivatives).
+template <class T>
+static T line_lambda(const Field<T>& F, int dir, int L) {
+  const int n = dir == 0 ? F.P.ni : F.P.nj;
+  T best = T(0);
+  for (int s = 0; s < n; ++s) {
+    T q[4], mx, my;
+    F.state(dir, L, s, q);
+    F.nodemet(dir, L, s, mx, my);
+    T sp = spectral(q, mx, my, F.P.gamma);
+    if (s == 0 || sp > best) best = sp;
+  }
+  return F.P.alpha * best;
+}
+
+// One direction: accumulates (H_{s+1/2} - H_{s-1/2}) into R for every node of every line.
+template <class T>
+static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
+  const Par<T>& P = F.P;
+  const SchemeTab& S = TAB[P.scheme];
+  const int n = dir == 0 ? P.ni : P.nj, nl = dir == 0 ? P.nj : P.ni;
+  const int NB = n + 8;           // nodes s = -4 .. n+3, stored at s + 4
+  const int NI = n + 3;           // interfaces p + 1/2, p = -2 .. n, stored at p + 2
+  const WenoOpt wo{P.ppm, P.linw};
+  std::vector<T> q(4 * NB), mxs(NB), mys(NB), fp(4 * NB), fm(4 * NB);
+  std::vector<T> fpm(4 * NI), fmm(4 * NI), Hh(4 * NI);
+  for (int L = 0; L < nl; ++L) {
+    const T A = line_lambda(F, dir, L);
+    // node states, metrics and split fluxes f+- = (E^ +- A^ Q)/2
+    for (int s = -4; s < n + 4; ++s) {
+      T qs[4], f[4];
+      F.state(dir, L, s, qs);
+      F.nodemet(dir, L, s, mxs[s + 4], mys[s + 4]);
+      flux(qs, mxs[s + 4], mys[s + 4], P.gamma, f);
+      for (int v = 0; v < 4; ++v) {
+        q[4 * (s + 4) + v] = qs[v];
+        fp[4 * (s + 4) + v] = cst<T>(0.5L) * (f[v] + A * qs[v]);
+        fm[4 * (s + 4) + v] = cst<T>(0.5L) * (f[v] - A * qs[v]);
+      }
+    }
+    // interfaces: characteristic WENO interpolation from each side, then split fluxes
+    for (int p = -2; p <= n; ++p) {
+      const int c0 = p + 4;                    // node p
+      // characteristic direction from the averaged metrics (Section 3.4)
+      T mbx = cst<T>(0.5L) * (mxs[c0] + mxs[c0 + 1]);
+      T mby = cst<T>(0.5L) * (mys[c0] + mys[c0 + 1]);
+      T mb = sqrt(mbx * mbx + mby * mby);
+      T nx = mbx / mb, ny = mby / mb;
+      T Qs[2][4];
+      for (int side = 0; side < 2; ++side) {
+        // side 0 ("+"): eigenvectors at Q_p, stencil p-2..p+2;
+        // side 1 ("-"): eigenvectors at Q_{p+1}, mirrored stencil p+3..p-1.
+        const int ce = side == 0 ? c0 : c0 + 1;
+        T Lm[4][4], Rm[4][4];
+        eigvec(&q[4 * ce], nx, ny, P.gamma, Lm, Rm);
+        T Wmid[4];
+        for (int k = 0; k < 4; ++k) {
+          T u[5];
+          for (int m = -2; m <= 2; ++m) {
+            const int node = side == 0 ? c0 + m : c0 + 1 - m;
+            T w = T(0);
+            for (int v = 0; v < 4; ++v) w = w + Lm[k][v] * q[4 * node + v];
+            u[m + 2] = w;
+          }
+          Wmid[k] = weno_mid(S.r, u, wo, P.eps);
+        }
+        for (int v = 0; v < 4; ++v) {
+          T acc = T(0);
+          for (int k = 0; k < 4; ++k) acc = acc + Rm[v][k] * Wmid[k];
+          Qs[side][v] = acc;
+        }
+      }
+      // midpoint metrics by the same interpolation I as the metric evaluation
+      T mmx = interp_mid<T>(P.scheme, P.interp, [&](int l) { return mxs[c0 + l]; });
+      T mmy = interp_mid<T>(P.scheme, P.interp, [&](int l) { return mys[c0 + l]; });
+      T fpl[4], fmi[4];
+      flux(Qs[0], mmx, mmy, P.gamma, fpl);
+      flux(Qs[1], mmx, mmy, P.gamma, fmi);
+      for (int v = 0; v < 4; ++v) {
+        fpm[4 * (p + 2) + v] = cst<T>(0.5L) * (fpl[v] + A * Qs[0][v]);
+        fmm[4 * (p + 2) + v] = cst<T>(0.5L) * (fmi[v] - A * Qs[1][v]);
+      }
+    }
+    // h = h+ + h-; h- mirrors h+ about x_{p+1/2}: f_{p+k} -> f_{p+1-k},
+    // f_{p+1/2+m} -> f_{p+1/2-m}
+    for (int p = -1; p <= n - 1; ++p) {
+      for (int v = 0; v < 4; ++v) {
+        T hp = T(0), hm = T(0);
+        for (int m = 0; m >= -1; --m) {
+          if (S.hmid[-m] == 0.0L) continue;
+          hp = hp + cst<T>(S.hmid[-m]) * fpm[4 * (p + m + 2) + v];
+          hm = hm + cst<T>(S.hmid[-m]) * fmm[4 * (p - m + 2) + v];
+        }
+        for (int k = -2; k <= 2; ++k) {
+          if (S.hnode[k + 2] == 0.0L) continue;
+          hp = hp + cst<T>(S.hnode[k + 2]) * fp[4 * (p + k + 4) + v];
+          hm = hm + cst<T>(S.hnode[k + 2]) * fm[4 * (p + 1 - k + 4) + v];
+        }
+        Hh[4 * (p + 2) + v] = hp + hm;
+      }
+    }
+    // difference (Eq. 3.2 with unit spacing)
+    for (int s = 0; s < n; ++s) {
+      const int i = dir == 0 ? s : L, j = dir == 0 ? L : s;
+      for (int v = 0; v < 4; ++v) {
+        size_t o = (size_t)v * P.ni * P.nj + (size_t)j * P.ni + i;
+        R[o] = R[o] + (Hh[4 * (s + 2) + v] - Hh[4 * (s + 1) + v]);
+      }
+    }
+  }
+}
+
+// dQ/dt = -(dE^/dxi + dF^/deta) / J^-1 (Eq. 2.2 on a stationary grid).
+template <class T>
+static void rhs(const Par<T>& P, const T* M, const T* Q, T* dQ) {
+  Field<T> F{P, M, Q};
+  const size_t N = (size_t)P.ni * P.nj;
+  std::vector<T> R(4 * N, T(0));
+  sweep(F, 0, R);
+  sweep(F, 1, R);
+  for (int j = 0; j < P.nj; ++j)
+    for (int i = 0; i < P.ni; ++i) {
+      T Jinv = F.met(4, i, j);
+      for (int v = 0; v < 4; ++v) {
+        size_t o = (size_t)v * N + (size_t)j * P.ni + i;
+        dQ[o] = -R[o] / Jinv;
+      }
+    }
+}
+
+// Third-order TVD Runge-Kutta (Section 6), Shu-Osher form.
+template <class T>
+static void rk3(const Par<T>& P, const T* M, T* Q, T dt) {
+  const size_t N = 4 * (size_t)P.ni * P.nj;
+  std::vector<T> R(N), Q1(N), Q2(N);
+  rhs(P, M, Q, R.data());
+  for (size_t k = 0; k < N; ++k) Q1[k] = Q[k] + dt * R[k];
+  rhs(P, M, Q1.data(), R.data());
+  for (size_t k = 0; k < N; ++k) Q2[k] = cst<T>(0.75L) * Q[k] + cst<T>(0.25L) * (Q1[k] + dt * R[k]);
+  rhs(P, M, Q2.data(), R.data());
+  for (size_t k = 0; k < N; ++k)
+    Q[k] = cst<T>(1.0L / 3) * Q[k] + cst<T>(2.0L / 3) * (Q2[k] + dt * R[k]);
+}
+
+// Reading (the paper uses fixed steps): dt = CFL / max over interior nodes of
+// [(|U^_xi| + c |grad xi^|) + (|U^_eta| + c |grad eta^|)] / J^-1.
+template <class T>
+static T cfl_dt(const Par<T>& P, const T* M, const T* Q, T cfl) {
+  Field<T> F{P, M, Q};
+  T best = T(0);
+  for (int j = 0; j < P.nj; ++j)
+    for (int i = 0; i < P.ni; ++i) {
+      T q[4];
+      for (int v = 0; v < 4; ++v) q[v] = F.q(v, i, j);
+      T s = (spectral(q, F.met(0, i, j), F.met(1, i, j), P.gamma) +
+             spectral(q, F.met(2, i, j), F.met(3, i, j), P.gamma)) / F.met(4, i, j);
+      if (s > best) best = s;
+    }
+  return cfl / best;
+}
+
+// ----------------------------------------------------------------------------------
+// Scalar linear advection u_t + u_x = 0 (Section 5.1, Table 3): periodic [-1, 1),
+// N nodes, upwind split f+ = u, f- = 0 (reading), classical RK4 with
+// dt = 2 / ceil(2 / dx^{5/4}), final time t.
+// ----------------------------------------------------------------------------------
+static void advect_rhs(int scheme, int N, double dx, const std::vector<double>& u,
+                       std::vector<double>& du) {
+  const SchemeTab& S = TAB[scheme];
+  const WenoOpt wo{1, 0};
+  auto U = [&](int k) { return u[(size_t)(((k % N) + N) % N)]; };
+  std::vector<double> fmid(N), h(N);
+  for (int p = 0; p < N; ++p) {              // f+_{p+1/2}
+    double st[5];
+    for (int m = -2; m <= 2; ++m) st[m + 2] = U(p + m);
+    fmid[p] = weno_mid<double>(S.r, st, wo, 1e-40);
+  }
+  for (int p = 0; p < N; ++p) {              // h_{p+1/2}
+    double hp = 0.0;
+    for (int m = 0; m >= -1; --m)
+      if (S.hmid[-m] != 0.0L) hp += (double)S.hmid[-m] * fmid[(size_t)(((p + m) % N + N) % N)];
+    for (int k = -2; k <= 2; ++k)
+      if (S.hnode[k + 2] != 0.0L) hp += (double)S.hnode[k + 2] * U(p + k);
+    h[p] = hp;
+  }
+  for (int p = 0; p < N; ++p) du[p] = -(h[p] - h[(p + N - 1) % N]) / dx;
+}
+
+static void advect1d(int scheme, int N, double tfinal, double* out) {
+  const double PI = 3.14159265358979323846;
+  const double dx = 2.0 / N;
+  auto u0 = [&](double x) { return std::sin(PI * x - std::sin(PI * x) / PI); };
+  std::vector<double> u(N), k1(N), k2(N), k3(N), k4(N), tmp(N);
+  for (int i = 0; i < N; ++i) u[i] = u0(-1.0 + dx * i);
+  const int nsteps = (int)std::ceil(tfinal / std::pow(dx, 1.25));
+  const double dt = tfinal / nsteps;
+  for (int st = 0; st < nsteps; ++st) {
+    advect_rhs(scheme, N, dx, u, k1);
+    for (int i = 0; i < N; ++i) tmp[i] = u[i] + 0.5 * dt * k1[i];
+    advect_rhs(scheme, N, dx, tmp, k2);
+    for (int i = 0; i < N; ++i) tmp[i] = u[i] + 0.5 * dt * k2[i];
+    advect_rhs(scheme, N, dx, tmp, k3);
+    for (int i = 0; i < N; ++i) tmp[i] = u[i] + dt * k3[i];
+    advect_rhs(scheme, N, dx, tmp, k4);
+    for (int i = 0; i < N; ++i) u[i] += dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  }
+  double s2 = 0.0, smax = 0.0;
+  for (int i = 0; i < N; ++i) {
+    // exact solution: the initial profile translated by t (period 2)
+    double xe = -1.0 + dx * i - tfinal;
+    xe = xe - 2.0 * std::floor((xe + 1.0) / 2.0);
+    double e = std::fabs(u[i] - u0(xe));
+    s2 += e * e; smax = std::max(smax, e);
+  }
+  out[0] = std::sqrt(s2 / N);   // L2 = root mean square
+  out[1] = smax;
+  out[2] = (double)nsteps;
+}
+
+// ----------------------------------------------------------------------------------
+// Exact solution of the 1-D Riemann problem for an ideal gas (used to check Sod):
+// pressure in the star region by Newton iteration on the sum of the two wave
+// functions (shock: Rankine-Hugoniot, rarefaction: isentropic), then sampling of x/t.
+// ----------------------------------------------------------------------------------
+static void riemann_exact(double g, const double* WL, const double* WR, double x0, double t,
+                          int n, const double* x, double* out) {
+  const double rl = WL[0], ul = WL[1], pl = WL[2], rr = WR[0], ur = WR[1], pr = WR[2];
+  const double cl = std::sqrt(g * pl / rl), cr = std::sqrt(g * pr / rr);
+  auto fk = [&](double p, double rk, double pk, double ck, double& df) {
+    if (p > pk) {  // shock
+      double A = 2.0 / ((g + 1.0) * rk), B = (g - 1.0) / (g + 1.0) * pk;
+      double s = std::sqrt(A / (p + B));
+      df = s * (1.0 - 0.5 * (p - pk) / (p + B));
+      return (p - pk) * s;
+    }
+    double e = (g - 1.0) / (2.0 * g);   // rarefaction
+    double f = 2.0 * ck / (g - 1.0) * (std::pow(p / pk, e) - 1.0);
+    df = 1.0 / (rk * ck) * std::pow(p / pk, -(g + 1.0) / (2.0 * g));
+    return f;
+  };
+  double p = 0.5 * (pl + pr);
+  for (int it = 0; it < 100; ++it) {
+    double dl, dr;
+    double f = fk(p, rl, pl, cl, dl) + fk(p, rr, pr, cr, dr) + (ur - ul);
+    double pn = p - f / (dl + dr);
+    if (pn < 1e-12) pn = 1e-12;
+    if (std::fabs(pn - p) < 1e-15 * (pn + p)) { p = pn; break; }
+    p = pn;
+  }
+  double dl, dr;
+  const double fl = fk(p, rl, pl, cl, dl), fr = fk(p, rr, pr, cr, dr);
+  const double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+  for (int k = 0; k < n; ++k) {
+    const double S = (x[k] - x0) / t;
+    double r, u, pp;
+    if (S <= us) {   // left of the contact
+      if (p > pl) {
+        double SL = ul - cl * std::sqrt((g + 1.0) / (2.0 * g) * p / pl + (g - 1.0) / (2.0 * g));
+        if (S <= SL) { r = rl; u = ul; pp = pl; }
+        else { r = rl * ((p / pl + (g - 1.0) / (g + 1.0)) / ((g - 1.0) / (g + 1.0) * p / pl + 1.0)); u = us; pp = p; }
+      } else {
+        double SHL = ul - cl, cs = cl * std::pow(p / pl, (g - 1.0) / (2.0 * g)), STL = us - cs;
+        if (S <= SHL) { r = rl; u = ul; pp = pl; }
+        else if (S > STL) { r = rl * std::pow(p / pl, 1.0 / g); u = us; pp = p; }
+        else {
+          u = 2.0 / (g + 1.0) * (cl + (g - 1.0) / 2.0 * ul + S);
+          double c = 2.0 / (g + 1.0) * (cl + (g - 1.0) / 2.0 * (ul - S));
+          r = rl * std::pow(c / cl, 2.0 / (g - 1.0)); pp = pl * std::pow(c / cl, 2.0 * g / (g - 1.0));
+        }
+      }
+    } else {
+      if (p > pr) {
+        double SR = ur + cr * std::sqrt((g + 1.0) / (2.0 * g) * p / pr + (g - 1.0) / (2.0 * g));
+        if (S >= SR) { r = rr; u = ur; pp = pr; }
+        else { r = rr * ((p / pr + (g - 1.0) / (g + 1.0)) / ((g - 1.0) / (g + 1.0) * p / pr + 1.0)); u = us; pp = p; }
+      } else {
+        double SHR = ur + cr, cs = cr * std::pow(p / pr, (g - 1.0) / (2.0 * g)), STR = us + cs;
+        if (S >= SHR) { r = rr; u = ur; pp = pr; }
+        else if (S < STR) { r = rr * std::pow(p / pr, 1.0 / g); u = us; pp = p; }
+        else {
+          u = 2.0 / (g + 1.0) * (-cr + (g - 1.0) / 2.0 * ur + S);
+          double c = 2.0 / (g + 1.0) * (cr - (g - 1.0) / 2.0 * (ur - S));
+          r = rr * std::pow(c / cr, 2.0 / (g - 1.0)); pp = pr * std::pow(c / cr, 2.0 * g / (g - 1.0));
+        }
+      }
+    }
+    out[3 * k + 0] = r; out[3 * k + 1] = u; out[3 * k + 2] = pp;
+  }
+}
+
+template <class T>
+static Coords<T> make_coords(const Par<T>& P, const double* period, const T* x, const T* y) {
+  Coords<T> C;
+  C.ni = P.ni; C.nj = P.nj;
+  for (int f = 0; f < 4; ++f) C.bc[f] = P.bc[f];
+  C.per[0][0] = T(period[0]); C.per[0][1] = T(period[1]);
+  C.per[1][0] = T(period[2]); C.per[1][1] = T(period[3]);
+  C.x = x; C.y = y;
+  return C;
+}
+
+static int check(const int* ip, int ni, int nj) {
+  if (ni < 1 || nj < 1) return 1;
+  if (ip[0] < 0 || ip[0] > 3) return 2;
+  if ((ip[4] == BC_PERIODIC) != (ip[5] == BC_PERIODIC)) return 3;
+  if ((ip[6] == BC_PERIODIC) != (ip[7] == BC_PERIODIC)) return 3;
+  if (ip[4] != BC_PERIODIC && ni < 9) return 4;
+  if (ip[6] != BC_PERIODIC && nj < 9) return 4;
+  return 0;
+}
+
+template <class T>
+static std::vector<T> conv(const double* a, size_t n) {
+  std::vector<T> r(n);
+  for (size_t k = 0; k < n; ++k) r[k] = T(a[k]);
+  return r;
+}
+
+}  // namespace orc
+
+// Free-stream residual computed in the wider type T (metrics and right-hand side both
+// in T) for the uniform conservative state q0: returns max |dQ/dt| over all nodes.
+namespace orc {
+template <class T>
+static double fsp_residual(const int* ip, const double* dp, int ni, int nj, const double* period,
+                           const double* x, const double* y, const double* q0) {
+  Par<T> P; unpack(ip, dp, ni, nj, P);
+  const size_t N = (size_t)ni * nj;
+  std::vector<T> X = conv<T>(x, N), Y = conv<T>(y, N);
+  Coords<T> C = make_coords(P, period, X.data(), Y.data());
+  std::vector<T> M((size_t)5 * (ni + 2 * G) * (nj + 2 * G)), Q(4 * N), R(4 * N);
+  metrics(P, C, M.data());
+  for (int v = 0; v < 4; ++v)
+    for (size_t k = 0; k < N; ++k) Q[v * N + k] = T(q0[v]);
+  rhs(P, M.data(), Q.data(), R.data());
+  double worst = 0.0;
+  for (size_t k = 0; k < 4 * N; ++k) worst = std::max(worst, std::fabs(val(R[k])));
+  return worst;
+}
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+// ip = {scheme, interp, ppm, linear_weights, bc[0..3]}
+// dp = {gamma, lf_alpha, eps, bc_state[4][4] (conservative, per face)}
+// period = {dx_i, dy_i, dx_j, dy_j}
+
+size_t orc_metrics_len(int ni, int nj) { return (size_t)5 * (ni + 2 * G) * (nj + 2 * G); }
+
+int orc_metrics(const int* ip, int ni, int nj, const double* period, const double* x,
+                const double* y, double* M) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<double> P; double dp[19] = {1.4, 1.1, 1e-40};
+  unpack(ip, dp, ni, nj, P);
+  Coords<double> C = make_coords(P, period, x, y);
+  metrics(P, C, M);
+  return 0;
+}
+
+// Tangent of the metrics along (dx, dy).
+int orc_metrics_jvp(const int* ip, int ni, int nj, const double* period, const double* x,
+                    const double* y, const double* dx, const double* dy, double* M, double* dM) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<Dual> P; double dp[19] = {1.4, 1.1, 1e-40};
+  unpack(ip, dp, ni, nj, P);
+  const size_t N = (size_t)ni * nj;
+  std::vector<Dual> X(N), Y(N);
+  for (size_t k = 0; k < N; ++k) { X[k] = Dual(x[k], dx[k]); Y[k] = Dual(y[k], dy[k]); }
+  Coords<Dual> C = make_coords(P, period, X.data(), Y.data());
+  std::vector<Dual> Md(orc_metrics_len(ni, nj));
+  metrics(P, C, Md.data());
+  for (size_t k = 0; k < Md.size(); ++k) { M[k] = Md[k].v; dM[k] = Md[k].d; }
+  return 0;
+}
+
+int orc_lambda(const int* ip, const double* dp, int ni, int nj, const double* M, const double* Q,
+               double* lam_xi, double* lam_eta) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<double> P; unpack(ip, dp, ni, nj, P);
+  Field<double> F{P, M, Q};
+  for (int j = 0; j < nj; ++j) lam_xi[j] = line_lambda(F, 0, j);
+  for (int i = 0; i < ni; ++i) lam_eta[i] = line_lambda(F, 1, i);
+  return 0;
+}
+
+int orc_rhs(const int* ip, const double* dp, int ni, int nj, const double* M, const double* Q,
+            double* dQ) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<double> P; unpack(ip, dp, ni, nj, P);
+  rhs(P, M, Q, dQ);
+  return 0;
+}
+
+// Tangent of the right-hand side along (dM, dQ) (either may be null = zero).
+int orc_rhs_jvp(const int* ip, const double* dp, int ni, int nj, const double* M, const double* dM,
+                const double* Q, const double* dQ, double* R, double* dR) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<Dual> P; unpack(ip, dp, ni, nj, P);
+  const size_t NM = orc_metrics_len(ni, nj), NQ = 4 * (size_t)ni * nj;
+  std::vector<Dual> Md(NM), Qd(NQ), Rd(NQ);
+  for (size_t k = 0; k < NM; ++k) Md[k] = Dual(M[k], dM ? dM[k] : 0.0);
+  for (size_t k = 0; k < NQ; ++k) Qd[k] = Dual(Q[k], dQ ? dQ[k] : 0.0);
+  rhs(P, Md.data(), Qd.data(), Rd.data());
+  for (size_t k = 0; k < NQ; ++k) { R[k] = Rd[k].v; dR[k] = Rd[k].d; }
+  return 0;
+}
+
+int orc_rk3(const int* ip, const double* dp, int ni, int nj, const double* M, double* Q, double dt,
+            int nsteps) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<double> P; unpack(ip, dp, ni, nj, P);
+  for (int s = 0; s < nsteps; ++s) rk3(P, M, Q, dt);
+  return 0;
+}
+
+// Tangent of nsteps RK3 steps along (dM, dQ); Q and dQ are advanced in place.
+int orc_rk3_jvp(const int* ip, const double* dp, int ni, int nj, const double* M, const double* dM,
+                double* Q, double* dQ, double dt, int nsteps) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<Dual> P; unpack(ip, dp, ni, nj, P);
+  const size_t NM = orc_metrics_len(ni, nj), NQ = 4 * (size_t)ni * nj;
+  std::vector<Dual> Md(NM), Qd(NQ);
+  for (size_t k = 0; k < NM; ++k) Md[k] = Dual(M[k], dM ? dM[k] : 0.0);
+  for (size_t k = 0; k < NQ; ++k) Qd[k] = Dual(Q[k], dQ[k]);
+  for (int s = 0; s < nsteps; ++s) rk3(P, Md.data(), Qd.data(), Dual(dt));
+  for (size_t k = 0; k < NQ; ++k) { Q[k] = Qd[k].v; dQ[k] = Qd[k].d; }
+  return 0;
+}
+
+double orc_cfl_dt(const int* ip, const double* dp, int ni, int nj, const double* M, const double* Q,
+                  double cfl) {
+  if (check(ip, ni, nj)) return -1.0;
+  Par<double> P; unpack(ip, dp, ni, nj, P);
+  return cfl_dt(P, M, Q, cfl);
+}
+
+// Floating-point operations of one right-hand side (each + - * / sqrt counts one).
+long long orc_count_flops(const int* ip, const double* dp, int ni, int nj, const double* M,
+                          const double* Q) {
+  if (check(ip, ni, nj)) return -1;
+  Par<Counted> P; unpack(ip, dp, ni, nj, P);
+  const size_t NM = orc_metrics_len(ni, nj), NQ = 4 * (size_t)ni * nj;
+  std::vector<Counted> Mc = conv<Counted>(M, NM), Qc = conv<Counted>(Q, NQ), Rc(NQ);
+  g_flops = 0;
+  rhs(P, Mc.data(), Qc.data(), Rc.data());
+  return g_flops;
+}
+
+double orc_fsp_residual(const int* ip, const double* dp, int ni, int nj, const double* period,
+                        const double* x, const double* y, const double* q0, int wide) {
+  if (check(ip, ni, nj)) return -1.0;
+  return wide ? fsp_residual<long double>(ip, dp, ni, nj, period, x, y, q0)
+              : fsp_residual<double>(ip, dp, ni, nj, period, x, y, q0);
+}
+
+int orc_long_double_digits(void) { return (int)__LDBL_MANT_DIG__; }
+
+double orc_weno(int r, int ppm, int linw, double eps, const double* u5) {
+  WenoOpt o{ppm, linw};
+  return weno_mid<double>(r, u5, o, eps);
+}
+
+double orc_ppm(int order, double w, double C) { return ppm_map<double>(order, w, C); }
+
+void orc_smoothness(const double* u5, double* is3) {
+  is3[0] = is0<double>(u5[0], u5[1], u5[2]);
+  is3[1] = is1<double>(u5[1], u5[2], u5[3]);
+  is3[2] = is2<double>(u5[2], u5[3], u5[4]);
+}
+
+void orc_eig(double gamma, const double* q, double nx, double ny, double* L, double* R) {
+  double Lm[4][4], Rm[4][4];
+  eigvec<double>(q, nx, ny, gamma, Lm, Rm);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) { L[4 * a + b] = Lm[a][b]; R[4 * a + b] = Rm[a][b]; }
+}
+
+void orc_scheme_table(int scheme, double* out /* r, hmid[2], hnode[5], cnode[3], cmid[2] */) {
+  const SchemeTab& S = TAB[scheme];
+  out[0] = S.r;
+  for (int k = 0; k < 2; ++k) out[1 + k] = (double)S.hmid[k];
+  for (int k = 0; k < 5; ++k) out[3 + k] = (double)S.hnode[k];
+  for (int k = 0; k < 3; ++k) out[8 + k] = (double)S.cnode[k];
+  for (int k = 0; k < 2; ++k) out[11 + k] = (double)S.cmid[k];
+}
+
+int orc_advect1d(int scheme, int N, double tfinal, double* out) {
+  if (scheme < 0 || scheme > 3 || N < 5) return 1;
+  advect1d(scheme, N, tfinal, out);
+  return 0;
+}
+
+int orc_riemann_exact(double gamma, const double* WL, const double* WR, double x0, double t, int n,
+                      const double* x, double* out) {
+  riemann_exact(gamma, WL, WR, x0, t, n, x, out);
+  return 0;
+}
+
+}  // extern "C"

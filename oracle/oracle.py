@@ -1,0 +1,255 @@
+"""ctypes front end of the CPU oracle (test infrastructure only).
+
+Builds ``_build/libfsp_oracle.so`` from ``fsp_oracle.cpp`` with g++ (``-O2
+-ffp-contract=off``, no OpenMP: the oracle runs on one core) and exposes numpy-level
+functions.  The configuration is a plain dict with the keys
+
+    scheme          0..3 = WENOIU3-1MP, WENOIU3-2MP, WENOIU5-1MP, WENOIU5-2MP
+    interp          0 = order-matched Lagrange midpoint interpolation, 1 = 2-point average
+    ppm             1 = piecewise-polynomial mapping of the weights (Eqs. 3.15/3.23)
+    linear_weights  1 = omega_k = C_k (linear interpolation)
+    bc              4 face codes (i-min, i-max, j-min, j-max): 0 periodic, 1 transmissive,
+                    2 Dirichlet, 3 slip wall, 4 far field
+    bc_state        4 x 4 conservative states used by Dirichlet / far-field faces
+    gamma, lf_alpha, eps
+    period          ((dx, dy) per wrap in i, (dx, dy) per wrap in j)
+
+Arrays: coordinates ``x, y`` are (nj, ni); the state ``Q`` is (4, nj, ni); metrics are
+(5, nj+8, ni+8) planes (xi_x^, xi_y^, eta_x^, eta_y^, J^-1) with 4 ghost layers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+__all__ = [
+    "build", "lib", "metrics", "metrics_jvp", "line_lambda", "rhs", "rhs_jvp", "rk3", "rk3_jvp",
+    "cfl_dt", "count_flops", "fsp_residual", "weno", "ppm", "smoothness", "eig",
+    "scheme_table", "advect1d", "riemann_exact", "long_double_digits", "G",
+]
+
+G = 4
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fsp_oracle.cpp")
+_OUT = os.path.join(_HERE, "_build", "libfsp_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (g++, -O2 -ffp-contract=off)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".tmp{os.getpid()}"
+        cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            sig = {
+                "orc_metrics": (ctypes.c_int, [_I, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]),
+                "orc_metrics_jvp": (ctypes.c_int, [_I, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D]),
+                "orc_lambda": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]),
+                "orc_rhs": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
+                "orc_rhs_jvp": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D]),
+                "orc_rk3": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_int]),
+                "orc_rk3_jvp": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D,
+                                               ctypes.c_double, ctypes.c_int]),
+                "orc_cfl_dt": (ctypes.c_double, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double]),
+                "orc_count_flops": (ctypes.c_longlong, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D]),
+                "orc_fsp_residual": (ctypes.c_double, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D,
+                                                       ctypes.c_int]),
+                "orc_weno": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]),
+                "orc_ppm": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+                "orc_smoothness": (None, [_D, _D]),
+                "orc_eig": (None, [ctypes.c_double, _D, ctypes.c_double, ctypes.c_double, _D, _D]),
+                "orc_scheme_table": (None, [ctypes.c_int, _D]),
+                "orc_advect1d": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]),
+                "orc_riemann_exact": (ctypes.c_int, [ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_int, _D, _D]),
+                "orc_long_double_digits": (ctypes.c_int, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _params(cfg):
+    ip = np.array([cfg.get("scheme", 2), cfg.get("interp", 0), cfg.get("ppm", 1),
+                   cfg.get("linear_weights", 0)] + list(cfg.get("bc", (0, 0, 0, 0))), dtype=np.int32)
+    st = np.zeros((4, 4)) if cfg.get("bc_state") is None else np.asarray(cfg["bc_state"], dtype=np.float64)
+    dp = np.concatenate([[cfg.get("gamma", 1.4), cfg.get("lf_alpha", 1.1), cfg.get("eps", 1e-40)],
+                         st.reshape(16)]).astype(np.float64)
+    per = np.asarray(cfg.get("period", ((0.0, 0.0), (0.0, 0.0))), dtype=np.float64).reshape(4)
+    return ip, dp, per
+
+
+def _ck(rc, name):
+    if rc != 0:
+        raise ValueError(f"oracle {name}: invalid arguments (code {rc})")
+
+
+def metrics(cfg, x, y):
+    x, y = _f64(x), _f64(y)
+    nj, ni = x.shape
+    ip, _, per = _params(cfg)
+    M = np.empty((5, nj + 2 * G, ni + 2 * G))
+    _ck(lib().orc_metrics(ip.ctypes.data_as(_I), ni, nj, _dp(per), _dp(x), _dp(y), _dp(M)), "metrics")
+    return M
+
+
+def metrics_jvp(cfg, x, y, dx, dy):
+    x, y, dx, dy = _f64(x), _f64(y), _f64(dx), _f64(dy)
+    nj, ni = x.shape
+    ip, _, per = _params(cfg)
+    M = np.empty((5, nj + 2 * G, ni + 2 * G))
+    dM = np.empty_like(M)
+    _ck(lib().orc_metrics_jvp(ip.ctypes.data_as(_I), ni, nj, _dp(per), _dp(x), _dp(y), _dp(dx), _dp(dy),
+                              _dp(M), _dp(dM)), "metrics_jvp")
+    return M, dM
+
+
+def line_lambda(cfg, M, Q):
+    M, Q = _f64(M), _f64(Q)
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    lx, le = np.empty(nj), np.empty(ni)
+    _ck(lib().orc_lambda(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q), _dp(lx), _dp(le)), "lambda")
+    return lx, le
+
+
+def rhs(cfg, M, Q):
+    M, Q = _f64(M), _f64(Q)
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    R = np.empty_like(Q)
+    _ck(lib().orc_rhs(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q), _dp(R)), "rhs")
+    return R
+
+
+def rhs_jvp(cfg, M, Q, dM=None, dQ=None):
+    M, Q = _f64(M), _f64(Q)
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    dM = np.zeros_like(M) if dM is None else _f64(dM)
+    dQ = np.zeros_like(Q) if dQ is None else _f64(dQ)
+    R, dR = np.empty_like(Q), np.empty_like(Q)
+    _ck(lib().orc_rhs_jvp(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(dM), _dp(Q), _dp(dQ),
+                          _dp(R), _dp(dR)), "rhs_jvp")
+    return R, dR
+
+
+def rk3(cfg, M, Q, dt, nsteps=1):
+    M = _f64(M)
+    Q = np.array(Q, dtype=np.float64, copy=True, order="C")
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    _ck(lib().orc_rk3(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q), float(dt), int(nsteps)), "rk3")
+    return Q
+
+
+def rk3_jvp(cfg, M, Q, dQ, dt, nsteps=1, dM=None):
+    M = _f64(M)
+    Q = np.array(Q, dtype=np.float64, copy=True, order="C")
+    dQ = np.array(dQ, dtype=np.float64, copy=True, order="C")
+    dM = np.zeros_like(M) if dM is None else _f64(dM)
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    _ck(lib().orc_rk3_jvp(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(dM), _dp(Q), _dp(dQ),
+                          float(dt), int(nsteps)), "rk3_jvp")
+    return Q, dQ
+
+
+def cfl_dt(cfg, M, Q, cfl):
+    M, Q = _f64(M), _f64(Q)
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    return lib().orc_cfl_dt(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q), float(cfl))
+
+
+def count_flops(cfg, M, Q):
+    M, Q = _f64(M), _f64(Q)
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    return int(lib().orc_count_flops(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q)))
+
+
+def fsp_residual(cfg, x, y, q0, wide=False):
+    x, y = _f64(x), _f64(y)
+    nj, ni = x.shape
+    ip, dp, per = _params(cfg)
+    q0 = _f64(q0)
+    return lib().orc_fsp_residual(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(per), _dp(x), _dp(y),
+                                  _dp(q0), int(bool(wide)))
+
+
+def weno(r, u5, ppm=1, linw=0, eps=1e-40):
+    u5 = _f64(u5)
+    return lib().orc_weno(int(r), int(ppm), int(linw), float(eps), _dp(u5))
+
+
+def ppm(order, w, C):
+    return lib().orc_ppm(int(order), float(w), float(C))
+
+
+def smoothness(u5):
+    u5 = _f64(u5)
+    out = np.empty(3)
+    lib().orc_smoothness(_dp(u5), _dp(out))
+    return out
+
+
+def eig(gamma, q, nx, ny):
+    q = _f64(q)
+    L, R = np.empty((4, 4)), np.empty((4, 4))
+    lib().orc_eig(float(gamma), _dp(q), float(nx), float(ny), _dp(L), _dp(R))
+    return L, R
+
+
+def scheme_table(scheme):
+    out = np.empty(13)
+    lib().orc_scheme_table(int(scheme), _dp(out))
+    return {"r": int(out[0]), "hmid": out[1:3], "hnode": out[3:8], "cnode": out[8:11], "cmid": out[11:13]}
+
+
+def advect1d(scheme, N, tfinal=2.0):
+    out = np.empty(3)
+    _ck(lib().orc_advect1d(int(scheme), int(N), float(tfinal), _dp(out)), "advect1d")
+    return out[0], out[1], int(out[2])
+
+
+def riemann_exact(gamma, left, right, x0, t, x):
+    x = _f64(x)
+    L, R = _f64(left), _f64(right)
+    out = np.empty((x.size, 3))
+    lib().orc_riemann_exact(float(gamma), _dp(L), _dp(R), float(x0), float(t), x.size, _dp(x), _dp(out))
+    return out
+
+
+def long_double_digits():
+    return int(lib().orc_long_double_digits())

@@ -1,0 +1,195 @@
+"""Seeded synthetic inputs: grids and initial states shaped like the paper's test cases.
+
+This module holds no arithmetic of the method (no metrics, fluxes, interpolation or
+time stepping).  It only draws random numbers and writes coordinates and initial states,
+so both the CPU oracle and the CUDA path can be fed the same inputs.
+
+Random numbers: splitmix64 of ``seed ^ (block << 32) ^ (4 * node + draw)`` mapped to a
+double in [0, 1) by ``(z >> 11) * 2**-53``.  ``node`` is the flat index j * ni + i,
+``draw`` is 0 (x offset), 1 (y offset) or 2 (the coin, bit 0 of the draw).
+
+Randomised grids follow Section 6.1 (1): every node moves along one coordinate only,
+chosen by a fair coin, by h * 2A (r - 1/2).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GAMMA = 1.4
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 finaliser applied element-wise to uint64 keys (wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def _keys(seed: int, block: int, n: int, draw: int) -> np.ndarray:
+    node = np.arange(n, dtype=np.uint64)
+    base = np.uint64(seed) ^ (np.uint64(block) << np.uint64(32))
+    return base ^ (np.uint64(4) * node + np.uint64(draw))
+
+
+def uniform(seed: int, block: int, n: int, draw: int) -> np.ndarray:
+    """n uniform doubles in [0, 1) for nodes 0..n-1."""
+    z = splitmix64(_keys(seed, block, n, draw))
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def coin(seed: int, block: int, n: int) -> np.ndarray:
+    """n fair bits (0/1) for nodes 0..n-1."""
+    z = splitmix64(_keys(seed, block, n, 2))
+    return (z & np.uint64(1)).astype(np.float64)
+
+
+def randomize(x: np.ndarray, y: np.ndarray, hx: float, hy: float, amp: np.ndarray, seed: int,
+              block: int = 0):
+    """Perturb a grid as in Section 6.1 (1): one coordinate per node, chosen by a coin."""
+    nj, ni = x.shape
+    n = ni * nj
+    r1 = uniform(seed, block, n, 0).reshape(nj, ni)
+    r2 = uniform(seed, block, n, 1).reshape(nj, ni)
+    b = coin(seed, block, n).reshape(nj, ni)
+    xr = x + hx * 2.0 * amp * (r1 - 0.5) * b
+    yr = y + hy * 2.0 * amp * (r2 - 0.5) * (1.0 - b)
+    return xr, yr
+
+
+def periodic_square(n: int, length: float, amp: float, seed: int, origin=(0.0, 0.0), nj: int | None = None):
+    """n x nj unique nodes of a periodic box [origin, origin + length)^2, every node
+    randomised with amplitude ``amp`` (fraction of the spacing).  Returns x, y, period."""
+    nj = n if nj is None else nj
+    hx, hy = length / n, length / nj
+    i = np.arange(n, dtype=np.float64)
+    j = np.arange(nj, dtype=np.float64)
+    x = np.broadcast_to(origin[0] + hx * i[None, :], (nj, n)).copy()
+    y = np.broadcast_to(origin[1] + hy * j[:, None], (nj, n)).copy()
+    if amp > 0:
+        x, y = randomize(x, y, hx, hy, np.full((nj, n), amp), seed)
+    period = ((length, 0.0), (0.0, length))
+    return x, y, period
+
+
+def paper_random_grid(imax: int, jmax: int, length: float, amp: float, seed: int, margin: int = 4):
+    """The grid of Section 6.1 (1): [-L/2, L/2]^2 with imax x jmax nodes, nodes of the
+    interior window (1-based i = 5..imax-4 and j = 5..jmax-4 for margin 4) randomised."""
+    h = length / (imax - 1)
+    i = np.arange(imax, dtype=np.float64)
+    j = np.arange(jmax, dtype=np.float64)
+    x = np.broadcast_to(-length / 2 + h * i[None, :], (jmax, imax)).copy()
+    y = np.broadcast_to(-length / 2 + h * j[:, None], (jmax, imax)).copy()
+    A = np.zeros((jmax, imax))
+    A[margin:jmax - margin, margin:imax - margin] = amp
+    x, y = randomize(x, y, h, h, A, seed)
+    return x, y
+
+
+def curved_periodic(n: int, length: float, warp: float = 0.1, origin=(0.0, 0.0)):
+    """A smooth curved periodic grid: x = xi + warp L/(2 pi) sin(2 pi xi/L) sin(2 pi eta/L),
+    y likewise (both perturbations periodic).  Returns x, y, period."""
+    h = length / n
+    s = origin[0] + h * np.arange(n, dtype=np.float64)
+    t = origin[1] + h * np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(s, t)
+    k = 2.0 * math.pi / length
+    a = warp / k
+    x = X + a * np.sin(k * (X - origin[0])) * np.sin(k * (Y - origin[1]))
+    y = Y + a * np.sin(k * (X - origin[0])) * np.sin(k * (Y - origin[1]))
+    return x, y, ((length, 0.0), (0.0, length))
+
+
+# ----------------------------------------------------------------------------------------
+# Initial states (conservative variables Q = (rho, rho u, rho v, E), E = p/(g-1) + rho|u|^2/2)
+# ----------------------------------------------------------------------------------------
+def conservative(rho, u, v, p, gamma: float = GAMMA) -> np.ndarray:
+    rho, u, v, p = np.broadcast_arrays(*(np.asarray(a, dtype=np.float64) for a in (rho, u, v, p)))
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def uniform_state(shape, rho=1.0, u=1.0, v=1.0, p=1.0, gamma: float = GAMMA) -> np.ndarray:
+    nj, ni = shape
+    return conservative(np.full((nj, ni), rho), np.full((nj, ni), u), np.full((nj, ni), v),
+                        np.full((nj, ni), p), gamma)
+
+
+def isentropic_vortex(x, y, center, strength=5.0, free=(1.0, 1.0, 1.0, 1.0), period=None,
+                      alpha=0.5, rc=1.0, gamma: float = GAMMA) -> np.ndarray:
+    """Isentropic vortex of Section 6.3 (1) on a free stream (rho, u, v, p); the paper's
+    epsilon is strength / (2 pi).  With ``period`` = (Lx, Ly) the nearest periodic image
+    of the centre is used."""
+    rho0, u0, v0, p0 = free
+    dx = x - center[0]
+    dy = y - center[1]
+    if period is not None:
+        dx = dx - period[0] * np.round(dx / period[0])
+        dy = dy - period[1] * np.round(dy / period[1])
+    r2 = (dx * dx + dy * dy) / (rc * rc)
+    eps = strength / (2.0 * math.pi)
+    e = np.exp(alpha * (1.0 - r2))
+    # (du, dv) = eps r e^{alpha(1 - r^2)} (sin theta, -cos theta) = eps e (dy, -dx)
+    du = eps * e * dy / rc
+    dv = -eps * e * dx / rc
+    T0 = p0 / rho0
+    dT = -(gamma - 1.0) * eps * eps / (4.0 * alpha * gamma) * e * e
+    T = T0 + dT
+    S0 = p0 / rho0 ** gamma
+    rho = (T / S0) ** (1.0 / (gamma - 1.0))     # isentropic: T = p/rho = S0 rho^(g-1)
+    p = rho * T
+    return conservative(rho, u0 + du, v0 + dv, p, gamma)
+
+
+def sod_1d(n: int = 200, gamma: float = GAMMA):
+    """Sod tube on [0, 1] with n cell-centred nodes, interface at 0.5: left (1, 0, 1),
+    right (0.125, 0, 0.1).  Returns x (1, n), y (1, n), Q (4, 1, n), period."""
+    xs = (np.arange(n, dtype=np.float64) + 0.5) / n
+    left = xs < 0.5
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    Q = conservative(rho[None, :], np.zeros((1, n)), np.zeros((1, n)), p[None, :], gamma)
+    x = xs[None, :].copy()
+    y = np.zeros((1, n))
+    period = ((0.0, 0.0), (0.0, 1.0 / n))
+    return x, y, Q, period
+
+
+def riemann_quadrants(x, y, gamma: float = GAMMA) -> np.ndarray:
+    """Four-quadrant state on [0, 1]^2 split at 0.5, quadrants in the paper's order
+    (upper right, upper left, lower left, lower right)."""
+    states = {
+        "ur": (1.5, 0.0, 0.0, 1.5),
+        "ul": (0.5323, 1.206, 0.0, 0.3),
+        "ll": (0.138, 1.206, 1.206, 0.029),
+        "lr": (0.5323, 0.0, 1.206, 0.3),
+    }
+    right = x >= 0.5
+    up = y >= 0.5
+    out = np.zeros((4,) + x.shape)
+    for key, mask in (("ur", right & up), ("ul", ~right & up), ("ll", ~right & ~up), ("lr", right & ~up)):
+        q = conservative(*(np.full(x.shape, c) for c in states[key]), gamma=gamma)
+        out[:, mask] = q[:, mask]
+    return out
+
+
+def riemann_grid(n: int, amp: float, seed: int, lo: float = 0.25, hi: float = 0.75):
+    """[0, 1]^2 with n x n nodes, nodes inside the central square [lo, hi]^2 randomised."""
+    h = 1.0 / (n - 1)
+    s = h * np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(s, s)
+    A = np.where((X > lo) & (X < hi) & (Y > lo) & (Y < hi), amp, 0.0)
+    return randomize(X, Y, h, h, A, seed)
+
+
+def random_state(shape, seed: int, rho=(0.8, 1.2), vel=(-0.3, 0.3), p=(0.8, 1.2),
+                 gamma: float = GAMMA, block: int = 7) -> np.ndarray:
+    """A smooth-free random state (every node independent) for algebraic tests."""
+    nj, ni = shape
+    n = ni * nj
+    r = [uniform(seed, block + k, n, 0).reshape(nj, ni) for k in range(4)]
+    return conservative(rho[0] + (rho[1] - rho[0]) * r[0], vel[0] + (vel[1] - vel[0]) * r[1],
+                        vel[0] + (vel[1] - vel[0]) * r[2], p[0] + (p[1] - p[0]) * r[3], gamma)
