@@ -1,0 +1,188 @@
+/*
+ * fsp.h -- C ABI of libfsp, the GB300 (sm_103a) implementation of the WENO
+ * interpolation-based, upwind-biased, free-stream-preserving (WENOIU) schemes of
+ * Q. Li and D. Sun, arXiv:1810.11103, for the 2-D compressible Euler equations on
+ * structured curvilinear grids.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  Nodes (i, j), 0 <= i < ni, 0 <= j < nj, i fastest; unit computational
+ *   spacing.  Coordinates x, y: device arrays of nj * ni doubles, node (i, j) at
+ *   [j * ni + i].
+ * State.  Conservative Q = (rho, rho u, rho v, E), E = p/(gamma-1) + rho |u|^2 / 2
+ *   (Eq. 2.1 in two dimensions): 4 planes, plane v at Q + v * nj * ld, node (i, j) at
+ *   [j * ld + i]; ld >= ni.  Element type double (FSP_FP64) or float (FSP_FP32).
+ *   The same layout holds for dQ/dt, Q_bar and every other state-shaped array.
+ * Metrics.  5 planes of doubles (xi_x^, xi_y^, eta_x^, eta_y^, J^-1) on the grid
+ *   extended by FSP_G ghost layers on each side: plane p, node (i, j) with
+ *   -FSP_G <= i < ni + FSP_G, -FSP_G <= j < nj + FSP_G, at
+ *   [p * (nj + 2 FSP_G) * (ni + 2 FSP_G) + (j + FSP_G) * (ni + 2 FSP_G) + (i + FSP_G)].
+ *   fsp_metrics_elems() gives the count.
+ * Boundaries.  Faces 0..3 = i-min, i-max, j-min, j-max.  Ghost states are formed
+ *   inside the kernels (no ghost storage for Q): periodic wraps; transmissive copies
+ *   the boundary node; Dirichlet uses bc_state[face]; slip wall mirrors about the
+ *   boundary node and reverses the velocity along the boundary node's grid normal;
+ *   far field takes bc_state[face] where its velocity enters through the face and is
+ *   transmissive elsewhere.  Ghost coordinates: periodic wrap plus the period vector,
+ *   otherwise odd reflection x_{-k} = 2 x_0 - x_k.  Periodic faces come in pairs; a
+ *   non-periodic direction needs at least 9 nodes.
+ * Memory.  All array arguments are device pointers owned by the caller.  The library
+ *   allocates nothing; calls needing scratch take a caller-provided workspace `ws` of
+ *   at least fsp_workspace_size() bytes (256-byte aligned).
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every call only enqueues work on it and returns; results are ready after the
+ *   caller synchronises the stream.
+ * Errors.  Every entry point returns an fsp_status and never aborts.  Arguments are
+ *   checked on the host before anything is enqueued (FSP_ERR_INVALID_ARG; host or
+ *   unregistered pointers are rejected); launch failures return FSP_ERR_CUDA.
+ *   Asynchronous device faults surface at the caller's next synchronisation.
+ * Threads.  No global mutable state except where stated; distinct calls may run on
+ *   distinct streams concurrently if their output and workspace buffers differ.
+ */
+#ifndef FSP_H
+#define FSP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSP_G 4 /* ghost layers of the stored metrics */
+
+typedef enum {
+  FSP_OK = 0,
+  FSP_ERR_INVALID_ARG = 1,
+  FSP_ERR_UNSUPPORTED = 2,
+  FSP_ERR_CUDA = 3,
+  FSP_ERR_NONFINITE = 4,
+  FSP_ERR_TIMEOUT = 5,
+  FSP_ERR_NOMEM = 6
+} fsp_status;
+
+/* Schemes of Section 3: third- and fifth-order, one or two midpoints. */
+enum { FSP_WENOIU3_1MP = 0, FSP_WENOIU3_2MP = 1, FSP_WENOIU5_1MP = 2, FSP_WENOIU5_2MP = 3 };
+/* Arithmetic of the right-hand side.  Metrics are FP64 in every mode. */
+enum { FSP_FP64 = 0, FSP_FP32 = 1 };
+enum { FSP_BC_PERIODIC = 0, FSP_BC_TRANSMISSIVE = 1, FSP_BC_DIRICHLET = 2, FSP_BC_SLIPWALL = 3,
+       FSP_BC_FARFIELD = 4 };
+
+typedef struct {
+  int scheme;          /* FSP_WENOIU*                                                   */
+  int precision;       /* FSP_FP64 or FSP_FP32                                          */
+  int interp;          /* midpoint interpolation of nodal metrics and coordinates:
+                          0 = central Lagrange, 4 points (third order) or 6 points
+                          (fifth order); 1 = two-point average (Section 2.4)           */
+  int ppm;             /* 1 = piecewise-polynomial mapping of the weights (Eqs. 3.15,
+                          3.23); 0 = plain weights (Eqs. 3.12-3.13)                    */
+  int linear_weights;  /* 1 = omega_k = C_k (linear interpolation, no mapping)          */
+  int bc[4];           /* FSP_BC_* per face                                            */
+  double gamma;        /* ratio of specific heats (1.4)                                */
+  double lf_alpha;     /* alpha of the Lax-Friedrichs-type splitting, 1.1-1.2 (Sec. 2.3) */
+  double eps;          /* epsilon of Eq. (3.13): 1e-40 with the mapping, else 1e-6     */
+  double bc_state[4][4]; /* conservative state per face (Dirichlet, far field)         */
+} fsp_config;
+
+typedef struct {
+  int ni, nj;          /* nodes per direction                                          */
+  long long ld;        /* row stride of Q-shaped arrays, elements (>= ni)              */
+  double period[2][2]; /* (dx, dy) added to the coordinates per wrap in i, then in j    */
+} fsp_block;
+
+/* Human-readable text of a status code (static storage). */
+const char* fsp_status_string(fsp_status s);
+
+/* Number of doubles of a metrics array for this block: 5 (nj + 8)(ni + 8). */
+size_t fsp_metrics_elems(const fsp_block* blk);
+
+/* Bytes of workspace needed by fsp_rhs, fsp_rk3_step, fsp_cfl_dt and the VJPs. */
+fsp_status fsp_workspace_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes);
+
+/*
+ * fsp_metrics -- conservative grid metrics (Eq. 2.3 in 2-D: xi_x^ = y_eta,
+ * xi_y^ = -x_eta, eta_x^ = -y_xi, eta_y^ = x_xi) and Jacobian (Eq. 2.5, whose 2-D form is
+ * J^-1 = x_xi y_eta - x_eta y_xi).  Every derivative uses the scheme's central operator
+ * delta^{c,(1)} (Eq. 2.7; Eqs. 3.7, 3.9, 3.19, 3.21) along its direction, with midpoint
+ * values from the interpolation chosen by cfg->interp (Section 2.4).  Computed on the
+ * node range extended by FSP_G ghost layers.  x, y: nj*ni doubles; metrics: output,
+ * fsp_metrics_elems() doubles.  FP64 regardless of cfg->precision.
+ */
+fsp_status fsp_metrics(const fsp_config* cfg, const fsp_block* blk, const double* x,
+                       const double* y, double* metrics, void* stream);
+
+/*
+ * fsp_line_lambda -- the per-line maxima behind A^ of the Lax-Friedrichs-type splitting
+ * (Section 2.3): for each grid line the maximum over its interior nodes of
+ * |U^| + c |k^|, with U^ = k_x^ u + k_y^ v and k^ the line's own metric pair; the
+ * splitting uses A^ = lf_alpha * maximum.  lam_xi: nj doubles (one per row, direction
+ * xi); lam_eta: ni doubles (one per column).  Output buffers are overwritten.
+ */
+fsp_status fsp_line_lambda(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                           const void* Q, double* lam_xi, double* lam_eta, void* stream);
+
+/*
+ * fsp_rhs -- the semi-discrete right-hand side dQ/dt = -(dE^/dxi + dF^/deta) / J^-1 of
+ * Eq. (2.2) on a stationary grid.  Per direction: the split fluxes f+- = (E^ +- A^ Q)/2
+ * at the nodes (Section 2.3); at every midpoint the state interpolated from each side by
+ * characteristic WENO (Eqs. 3.10-3.13 with Table 1, indicators of Eq. 3.22, mapping
+ * 3.15/3.23, projection of Section 3.4), split with the interpolated midpoint metrics;
+ * the upwind-biased combination h = h+ + h- of Eq. (3.4), (3.8), (3.16) or (3.20); and
+ * the difference of Eq. (3.2).  Q: input state; dQdt: output (same layout, may not alias
+ * Q); ws: workspace.
+ */
+fsp_status fsp_rhs(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                   const void* Q, void* dQdt, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * fsp_flux_difference -- one direction of the right-hand side: at every node the
+ * difference H_{s+1/2} - H_{s-1/2} (Eq. 3.2, unit spacing) along direction dir (0 = xi
+ * along i, 1 = eta along j), with h = h+ + h- built exactly as in fsp_rhs and
+ * A^ = lf_alpha * lam[line].  lam: the per-line maxima of fsp_line_lambda for that
+ * direction (nj values for xi, ni for eta).  mode 0: D <- the difference; mode 1:
+ * D <- -(acc + difference) / J^-1, which is dQ/dt when acc holds the other direction's
+ * difference.  acc (mode 1 only) and D have the state layout; D may not alias Q or acc.
+ * fsp_rhs is fsp_line_lambda + this call for xi (mode 0) + this call for eta (mode 1).
+ */
+fsp_status fsp_flux_difference(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                               const void* Q, const double* lam, int dir, int mode, const void* acc,
+                               void* D, void* stream);
+
+/*
+ * fsp_rk3_step -- one step of the third-order TVD Runge-Kutta scheme (Section 6),
+ * Shu-Osher form Q1 = Q + dt R(Q); Q2 = 3/4 Q + 1/4 (Q1 + dt R(Q1));
+ * Q <- 1/3 Q + 2/3 (Q2 + dt R(Q2)), with R = fsp_rhs.  Q is updated in place.
+ */
+fsp_status fsp_rk3_step(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                        void* Q, double dt, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * fsp_cfl_dt -- the time step cfl / max over interior nodes of
+ * [(|U^_xi| + c |grad xi^|) + (|U^_eta| + c |grad eta^|)] / J^-1, written to the device
+ * double *dt_out.  (The paper uses fixed steps; this is the stated reading of a CFL.)
+ */
+fsp_status fsp_cfl_dt(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                      const void* Q, double cfl, double* dt_out, void* ws, size_t ws_bytes,
+                      void* stream);
+
+/*
+ * fsp_norms -- per variable v: out[2v] = sqrt(mean over interior nodes of e^2),
+ * out[2v+1] = max |e|, with e = A - B (B may be NULL: e = A).  out: 8 device doubles.
+ * precision selects the element type of A and B.  Used for error norms and the
+ * free-stream residual.
+ */
+fsp_status fsp_norms(const fsp_block* blk, int precision, const void* A, const void* B,
+                     double* out, void* stream);
+
+/*
+ * fsp_fma_peak -- throughput probe of the FP64 (precision FSP_FP64) or FP32 FMA pipe:
+ * launches `blocks` x 256 threads, each running `iters` x 8 independent FMA chains, and
+ * writes the chains' sum to sink[blocks * 256].  The floating-point operations done are
+ * 2 * 8 * iters * blocks * 256.  Used to measure the ALU roof; no counterpart in the paper.
+ */
+fsp_status fsp_fma_peak(int precision, int blocks, int iters, void* sink, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSP_H */

@@ -1,0 +1,42 @@
+"""Writes paper_1810_11103_gb300/algorithmic_flops.json: floating-point operations of one
+right-hand side per node, counted by running the oracle with an operation-counting scalar
+(each + - * / sqrt counts one; a fused multiply-add is two).  Used as the algorithmic
+work of the roofline.  Run: python -m oracle.count_flops
+"""
+import json
+import os
+
+import numpy as np
+
+from . import oracle as O
+from paper_1810_11103_gb300 import inputs as I
+
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "paper_1810_11103_gb300", "algorithmic_flops.json")
+
+
+def main():
+    x, y, per = I.periodic_square(256, 10.0, 0.2, seed=1810)
+    q = I.isentropic_vortex(x, y, (5.0, 5.0), strength=5.0, free=(1.0, 1.0, 1.0, 1.0), period=(10.0, 10.0))
+    n = x.size
+    res = {"workload": "periodic vortex 256x256, randomised grid A=0.2, seed 1810",
+           "how": "oracle with an operation-counting scalar; + - * / sqrt = 1 flop each",
+           "schemes": {}}
+    names = ["WENOIU3-1MP", "WENOIU3-2MP", "WENOIU5-1MP", "WENOIU5-2MP"]
+    for s in range(4):
+        cfg = dict(scheme=s, period=per)
+        M = O.metrics(cfg, x, y)
+        lx, sx, le, se, fin = O.count_flops_parts(cfg, M, q)
+        res["schemes"][names[s]] = {
+            "rhs_per_node": (lx + sx + le + se + fin) / n,
+            "lambda_per_node": (lx + le) / n,
+            "sweep_xi_per_node": sx / n,
+            "sweep_eta_per_node": (se + fin) / n,
+        }
+    with open(OUT, "w") as f:
+        json.dump(res, f, indent=1)
+    print(OUT)
+
+
+if __name__ == "__main__":
+    main()

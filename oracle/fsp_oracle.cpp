@@ -931,6 +931,34 @@ long long orc_count_flops(const int* ip, const double* dp, int ni, int nj, const
   return g_flops;
 }
 
+// Floating-point operations by part of one right-hand side:
+// out = {line maxima xi, xi sweep without its line maxima, line maxima eta,
+//        eta sweep without its line maxima, final division by J^-1}.
+int orc_count_flops_parts(const int* ip, const double* dp, int ni, int nj, const double* M,
+                          const double* Q, long long* out) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<Counted> P; unpack(ip, dp, ni, nj, P);
+  const size_t NM = orc_metrics_len(ni, nj), NQ = 4 * (size_t)ni * nj;
+  std::vector<Counted> Mc = conv<Counted>(M, NM), Qc = conv<Counted>(Q, NQ), R(NQ, Counted(0.0));
+  Field<Counted> F{P, Mc.data(), Qc.data()};
+  for (int dir = 0; dir < 2; ++dir) {
+    const int nl = dir == 0 ? nj : ni;
+    g_flops = 0;
+    for (int L = 0; L < nl; ++L) line_lambda(F, dir, L);
+    const long long lam = g_flops;
+    g_flops = 0;
+    sweep(F, dir, R);
+    out[2 * dir] = lam;
+    out[2 * dir + 1] = g_flops - lam;
+  }
+  std::vector<Counted> dQ(NQ);
+  g_flops = 0;
+  rhs(P, Mc.data(), Qc.data(), dQ.data());
+  long long total = g_flops;
+  out[4] = total - out[0] - out[1] - out[2] - out[3];
+  return 0;
+}
+
 double orc_fsp_residual(const int* ip, const double* dp, int ni, int nj, const double* period,
                         const double* x, const double* y, const double* q0, int wide) {
   if (check(ip, ni, nj)) return -1.0;

@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "build", "lib", "metrics", "metrics_jvp", "line_lambda", "rhs", "rhs_jvp", "rk3", "rk3_jvp",
-    "cfl_dt", "count_flops", "fsp_residual", "weno", "ppm", "smoothness", "eig",
+    "cfl_dt", "count_flops", "count_flops_parts", "fsp_residual", "weno", "ppm", "smoothness", "eig",
     "scheme_table", "advect1d", "riemann_exact", "long_double_digits", "G",
 ]
 
@@ -71,6 +71,8 @@ def lib():
                                                ctypes.c_double, ctypes.c_int]),
                 "orc_cfl_dt": (ctypes.c_double, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double]),
                 "orc_count_flops": (ctypes.c_longlong, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D]),
+                "orc_count_flops_parts": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D,
+                                                         ctypes.POINTER(ctypes.c_longlong)]),
                 "orc_fsp_residual": (ctypes.c_double, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D,
                                                        ctypes.c_int]),
                 "orc_weno": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]),
@@ -197,6 +199,16 @@ def count_flops(cfg, M, Q):
     _, nj, ni = Q.shape
     ip, dp, _ = _params(cfg)
     return int(lib().orc_count_flops(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q)))
+
+
+def count_flops_parts(cfg, M, Q):
+    """Flops of one right-hand side by part: (lambda_xi, sweep_xi, lambda_eta, sweep_eta, final)."""
+    M, Q = _f64(M), _f64(Q)
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    out = (ctypes.c_longlong * 5)()
+    _ck(lib().orc_count_flops_parts(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q), out), "count")
+    return tuple(int(v) for v in out)
 
 
 def fsp_residual(cfg, x, y, q0, wide=False):

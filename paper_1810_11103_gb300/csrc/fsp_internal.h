@@ -1,0 +1,39 @@
+// fsp_internal.h -- declarations shared by the translation units of libfsp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/fsp.h"
+#include "fsp_device.cuh"
+
+namespace fsp {
+
+// Launchers (enqueue only; return the launch status).
+cudaError_t launch_metrics(const fsp_config& cfg, const fsp_block& blk, const double* x,
+                           const double* y, double* M, cudaStream_t st);
+
+// Per-line spectral maxima (without the factor alpha) into lam_xi[nj], lam_eta[ni];
+// cfl_max (nullable) receives the largest per-node CFL rate.  Buffers must be zeroed.
+cudaError_t launch_lambda(const Params& P, int precision, const void* Q, double* lam_xi,
+                          double* lam_eta, double* cfl_max, cudaStream_t st);
+
+// One right-hand-side evaluation in two passes.  mode 0: out = dQ/dt.  mode 1: RK stage
+// out = ca * Qn + cb * (Q + dt * dQ/dt).  Racc: 4 * nj * ld scratch of the state type.
+cudaError_t launch_rhs(int scheme, int precision, const Params& P, const void* Q,
+                       const double* lam_xi, const double* lam_eta, void* Racc, void* out,
+                       int mode, const void* Qn, double ca, double cb, double dt, cudaStream_t st);
+
+// One direction only: mode 0 writes the difference to out; mode 1 writes
+// -(acc + difference) / J^-1.
+cudaError_t launch_flux_difference(int scheme, int precision, const Params& P, const void* Q,
+                                   const double* lam, int dir, int mode, const void* acc, void* out,
+                                   cudaStream_t st);
+
+cudaError_t launch_cfl_finish(const double* cfl_max, double cfl, double* dt_out, cudaStream_t st);
+
+cudaError_t launch_norms(const fsp_block& blk, int precision, const void* A, const void* B,
+                         double* out, cudaStream_t st);
+
+cudaError_t launch_fma_peak(int precision, int blocks, int iters, void* sink, cudaStream_t st);
+
+}  // namespace fsp

@@ -1,0 +1,31 @@
+// probe.cu -- FMA throughput probe used as the ALU roof of the roofline: eight
+// independent multiply-add chains per thread keep the FP64 (or FP32) pipe saturated.
+#include "fsp_internal.h"
+
+namespace fsp {
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(int iters, T* sink) {
+  T x[8];
+  const T a = T(0.9999999), b = T(1e-7);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = T(threadIdx.x + k) * T(1e-3);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fma_peak(int precision, int blocks, int iters, void* sink, cudaStream_t st) {
+  if (precision == FSP_FP64)
+    fma_peak_kernel<double><<<blocks, 256, 0, st>>>(iters, static_cast<double*>(sink));
+  else
+    fma_peak_kernel<float><<<blocks, 256, 0, st>>>(iters, static_cast<float*>(sink));
+  return cudaGetLastError();
+}
+
+}  // namespace fsp

@@ -1,0 +1,250 @@
+"""Thin Python binding of libfsp (include/fsp.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; torch supplies device memory
+and streams.  The library must be built (``python -m paper_1810_11103_gb300.build``);
+there is no fallback: a missing library or a failed call raises.
+
+Shapes: coordinates ``x, y`` (nj, ni) float64; state ``Q`` (4, nj, ni) float64 or
+float32 with unit stride along i (row stride = ld); metrics (5, nj+8, ni+8) float64.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+from typing import Optional, Sequence
+
+import torch
+
+G = 4
+FP64, FP32 = 0, 1
+WENOIU3_1MP, WENOIU3_2MP, WENOIU5_1MP, WENOIU5_2MP = 0, 1, 2, 3
+BC_PERIODIC, BC_TRANSMISSIVE, BC_DIRICHLET, BC_SLIPWALL, BC_FARFIELD = 0, 1, 2, 3, 4
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfsp.so")
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "CUDA error",
+           4: "non-finite value", 5: "device wait timed out", 6: "out of memory"}
+
+
+class FspError(RuntimeError):
+    def __init__(self, name, code):
+        super().__init__(f"{name}: {_STATUS.get(code, 'unknown')} (status {code})")
+        self.code = code
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int), ("precision", ctypes.c_int), ("interp", ctypes.c_int),
+                ("ppm", ctypes.c_int), ("linear_weights", ctypes.c_int), ("bc", ctypes.c_int * 4),
+                ("gamma", ctypes.c_double), ("lf_alpha", ctypes.c_double), ("eps", ctypes.c_double),
+                ("bc_state", (ctypes.c_double * 4) * 4)]
+
+
+class _Block(ctypes.Structure):
+    _fields_ = [("ni", ctypes.c_int), ("nj", ctypes.c_int), ("ld", ctypes.c_longlong),
+                ("period", (ctypes.c_double * 2) * 2)]
+
+
+@dataclasses.dataclass
+class Config:
+    """Mirror of fsp_config."""
+    scheme: int = WENOIU5_1MP
+    precision: int = FP64
+    interp: int = 0
+    ppm: int = 1
+    linear_weights: int = 0
+    bc: Sequence[int] = (0, 0, 0, 0)
+    gamma: float = 1.4
+    lf_alpha: float = 1.1
+    eps: float = 1e-40
+    bc_state: Optional[Sequence[Sequence[float]]] = None
+    period: Sequence[Sequence[float]] = ((0.0, 0.0), (0.0, 0.0))
+
+    @classmethod
+    def from_dict(cls, d):
+        keys = {f.name for f in dataclasses.fields(cls)}
+        return cls(**{k: v for k, v in d.items() if k in keys})
+
+    def _c(self):
+        c = _Config()
+        c.scheme, c.precision, c.interp = int(self.scheme), int(self.precision), int(self.interp)
+        c.ppm, c.linear_weights = int(self.ppm), int(self.linear_weights)
+        for f in range(4):
+            c.bc[f] = int(self.bc[f])
+        c.gamma, c.lf_alpha, c.eps = float(self.gamma), float(self.lf_alpha), float(self.eps)
+        st = self.bc_state if self.bc_state is not None else [[0.0] * 4] * 4
+        for f in range(4):
+            for v in range(4):
+                c.bc_state[f][v] = float(st[f][v])
+        return c
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Load libfsp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libfsp.so not built ({LIB_PATH}); run "
+                                   "`python -m paper_1810_11103_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            C, B = ctypes.POINTER(_Config), ctypes.POINTER(_Block)
+            sig = {
+                "fsp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+                "fsp_metrics_elems": (ctypes.c_size_t, [B]),
+                "fsp_workspace_size": (ctypes.c_int, [C, B, ctypes.POINTER(ctypes.c_size_t)]),
+                "fsp_metrics": (ctypes.c_int, [C, B, _P, _P, _P, _P]),
+                "fsp_line_lambda": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P]),
+                "fsp_rhs": (ctypes.c_int, [C, B, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+                "fsp_flux_difference": (ctypes.c_int, [C, B, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+                "fsp_rk3_step": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, ctypes.c_size_t, _P]),
+                "fsp_cfl_dt": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, ctypes.c_size_t, _P]),
+                "fsp_norms": (ctypes.c_int, [B, ctypes.c_int, _P, _P, _P, _P]),
+                "fsp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype, f.argtypes = res, args
+            _lib = L
+    return _lib
+
+
+def _check(name, code):
+    if code != 0:
+        raise FspError(name, code)
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype(cfg: Config):
+    return torch.float64 if cfg.precision == FP64 else torch.float32
+
+
+def block_of(cfg: Config, Q: torch.Tensor) -> _Block:
+    """fsp_block of a (4, nj, ni) state tensor (unit stride along i)."""
+    if Q.dim() != 3 or Q.shape[0] != 4:
+        raise ValueError("state must have shape (4, nj, ni)")
+    if Q.stride(2) != 1 or Q.stride(0) != Q.shape[1] * Q.stride(1):
+        raise ValueError("state planes must be dense with unit stride along i")
+    b = _Block()
+    b.nj, b.ni, b.ld = int(Q.shape[1]), int(Q.shape[2]), int(Q.stride(1))
+    for a in range(2):
+        for k in range(2):
+            b.period[a][k] = float(cfg.period[a][k])
+    return b
+
+
+def _block_shape(cfg: Config, ni: int, nj: int, ld: Optional[int] = None) -> _Block:
+    b = _Block()
+    b.ni, b.nj, b.ld = int(ni), int(nj), int(ni if ld is None else ld)
+    for a in range(2):
+        for k in range(2):
+            b.period[a][k] = float(cfg.period[a][k])
+    return b
+
+
+def workspace_size(cfg: Config, ni: int, nj: int, ld: Optional[int] = None) -> int:
+    n = ctypes.c_size_t()
+    _check("fsp_workspace_size", lib().fsp_workspace_size(ctypes.byref(cfg._c()),
+                                                           ctypes.byref(_block_shape(cfg, ni, nj, ld)),
+                                                           ctypes.byref(n)))
+    return int(n.value)
+
+
+def workspace(cfg: Config, Q: torch.Tensor) -> torch.Tensor:
+    b = block_of(cfg, Q)
+    return torch.empty(workspace_size(cfg, b.ni, b.nj, b.ld), dtype=torch.uint8, device=Q.device)
+
+
+def metrics(cfg: Config, x: torch.Tensor, y: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    nj, ni = x.shape
+    x = x.contiguous()
+    y = y.contiguous()
+    if out is None:
+        out = torch.empty((5, nj + 2 * G, ni + 2 * G), dtype=torch.float64, device=x.device)
+    _check("fsp_metrics", lib().fsp_metrics(ctypes.byref(cfg._c()), ctypes.byref(_block_shape(cfg, ni, nj)),
+                                            _ptr(x), _ptr(y), _ptr(out), _stream(stream)))
+    return out
+
+
+def line_lambda(cfg: Config, M: torch.Tensor, Q: torch.Tensor, stream=None):
+    b = block_of(cfg, Q)
+    lx = torch.empty(b.nj, dtype=torch.float64, device=Q.device)
+    le = torch.empty(b.ni, dtype=torch.float64, device=Q.device)
+    _check("fsp_line_lambda", lib().fsp_line_lambda(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M),
+                                                    _ptr(Q), _ptr(lx), _ptr(le), _stream(stream)))
+    return lx, le
+
+
+def rhs(cfg: Config, M: torch.Tensor, Q: torch.Tensor, out=None, ws=None, stream=None) -> torch.Tensor:
+    b = block_of(cfg, Q)
+    if out is None:
+        out = torch.empty_like(Q)
+    if ws is None:
+        ws = workspace(cfg, Q)
+    _check("fsp_rhs", lib().fsp_rhs(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M), _ptr(Q), _ptr(out),
+                                    _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def flux_difference(cfg: Config, M: torch.Tensor, Q: torch.Tensor, lam: torch.Tensor, dir: int,
+                    mode: int = 0, acc=None, out=None, stream=None) -> torch.Tensor:
+    """One direction of the right-hand side (see fsp_flux_difference)."""
+    b = block_of(cfg, Q)
+    if out is None:
+        out = torch.empty_like(Q)
+    _check("fsp_flux_difference", lib().fsp_flux_difference(
+        ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M), _ptr(Q), _ptr(lam), int(dir), int(mode), _ptr(acc),
+        _ptr(out), _stream(stream)))
+    return out
+
+
+def rk3_step(cfg: Config, M: torch.Tensor, Q: torch.Tensor, dt: float, ws=None, stream=None) -> torch.Tensor:
+    """One TVD-RK3 step, in place on Q."""
+    b = block_of(cfg, Q)
+    if ws is None:
+        ws = workspace(cfg, Q)
+    _check("fsp_rk3_step", lib().fsp_rk3_step(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M), _ptr(Q),
+                                              float(dt), _ptr(ws), ws.numel(), _stream(stream)))
+    return Q
+
+
+def cfl_dt(cfg: Config, M: torch.Tensor, Q: torch.Tensor, cfl: float, out=None, ws=None, stream=None):
+    b = block_of(cfg, Q)
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=Q.device)
+    if ws is None:
+        ws = workspace(cfg, Q)
+    _check("fsp_cfl_dt", lib().fsp_cfl_dt(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M), _ptr(Q),
+                                          float(cfl), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def norms(A: torch.Tensor, B: Optional[torch.Tensor] = None, out=None, stream=None) -> torch.Tensor:
+    """(rms, max) of A - B per variable: tensor of 8 doubles (rms_0, max_0, ...)."""
+    prec = FP64 if A.dtype == torch.float64 else FP32
+    cfg = Config(precision=prec)
+    b = block_of(cfg, A)
+    if out is None:
+        out = torch.empty(8, dtype=torch.float64, device=A.device)
+    _check("fsp_norms", lib().fsp_norms(ctypes.byref(b), prec, _ptr(A), _ptr(B), _ptr(out), _stream(stream)))
+    return out
+
+
+def fma_peak(precision: int, blocks: int, iters: int, sink: torch.Tensor, stream=None):
+    _check("fsp_fma_peak", lib().fsp_fma_peak(int(precision), int(blocks), int(iters), _ptr(sink),
+                                              _stream(stream)))
