@@ -1,6 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element on
 the same seeded inputs.  FP64 bar: relative max-norm max|gpu - oracle| / max|oracle|
-<= 1e-12 for right-hand sides and RK3 states; for metrics the same bar per plane.  The
+<= 1e-12 for right-hand sides and RK3 states; for metrics the same bar, the four metric
+planes against their common maximum and J^-1 against its own.  The
 metrics are differences of O(1) coordinates that come out O(h), so their rounding is
 O(eps / h) relative: about 4e-13 at h = 1/1023 with both sides correctly rounded."""
 import math
@@ -71,8 +72,9 @@ def _check_case(F, cfgd, x, y, q, tol=TOL_RHS):
     M_o = O.metrics(cfgd, x, y)
     M_g = F.metrics(cfg, _dev(x), _dev(y))
     Mh = _host(M_g)
-    for p in range(5):
-        assert _rel(Mh[p], M_o[p]) < TOL_MET, p
+    # the four metric planes are coordinate derivatives of one scale; J^-1 has its own
+    assert np.abs(Mh[:4] - M_o[:4]).max() < TOL_MET * np.abs(M_o[:4]).max()
+    assert _rel(Mh[4], M_o[4]) < TOL_MET
     R_o = O.rhs(cfgd, M_o, q)
     R_g = F.rhs(cfg, _dev(M_o), _dev(q))
     err = _rel(_host(R_g), R_o)
