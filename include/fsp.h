@@ -134,6 +134,30 @@ fsp_status fsp_rhs(const fsp_config* cfg, const fsp_block* blk, const double* me
                    const void* Q, void* dQdt, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * fsp_rhs_noalloc -- the same right-hand side as fsp_rhs, for callers that cannot
+ * allocate device memory (no workspace argument).  The paper has no counterpart: this is
+ * a convenience of the library.  It suits a solver plugin inside an application that owns
+ * every device allocation, a real-time loop where cudaMalloc/cudaFree would synchronise
+ * the device, or a caller without an allocator of its own.  Its scratch (per-line maxima
+ * and the xi accumulator) lives in one fixed device array of FSP_NOALLOC_SCRATCH_BYTES
+ * inside the library, which every GPU that loads the library holds until the process
+ * exits.  Limits and behaviour:
+ *   - FP64 only (FSP_ERR_UNSUPPORTED otherwise);
+ *   - the block must fit: 8 (ni + nj) bytes, rounded up to 256, plus 32 nj ld bytes
+ *     <= FSP_NOALLOC_SCRATCH_BYTES, else FSP_ERR_NOMEM and nothing is enqueued;
+ *   - the first call on a device looks up the array's device address (this may load the
+ *     module), so make that first call before any stream capture;
+ *   - all calls share the one array: calls that overlap on the GPU (other streams, other
+ *     host threads on the same device) race and must be serialised by the caller;
+ *   - the array keeps the previous call's contents; each call clears what must start at
+ *     zero.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+#define FSP_NOALLOC_SCRATCH_BYTES (8u << 20)
+fsp_status fsp_rhs_noalloc(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                           const void* Q, void* dQdt, void* stream);
+
+/*
  * fsp_flux_difference -- one direction of the right-hand side: at every node the
  * difference H_{s+1/2} - H_{s-1/2} (Eq. 3.2, unit spacing) along direction dir (0 = xi
  * along i, 1 = eta along j), with h = h+ + h- built exactly as in fsp_rhs and
