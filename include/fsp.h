@@ -11,7 +11,8 @@
  *   [j * ni + i].
  * State.  Conservative Q = (rho, rho u, rho v, E), E = p/(gamma-1) + rho |u|^2 / 2
  *   (Eq. 2.1 in two dimensions): 4 planes, plane v at Q + v * nj * ld, node (i, j) at
- *   [j * ld + i]; ld >= ni.  Element type double (FSP_FP64) or float (FSP_FP32).
+ *   [j * ld + i]; ld >= ni.  Element type double (FSP_FP64) or float (FSP_FP32,
+ *   FSP_FP32_MIXED).
  *   The same layout holds for dQ/dt, Q_bar and every other state-shaped array.
  * Metrics.  5 planes of doubles (xi_x^, xi_y^, eta_x^, eta_y^, J^-1) on the grid
  *   extended by FSP_G ghost layers on each side: plane p, node (i, j) with
@@ -62,8 +63,14 @@ typedef enum {
 
 /* Schemes of Section 3: third- and fifth-order, one or two midpoints. */
 enum { FSP_WENOIU3_1MP = 0, FSP_WENOIU3_2MP = 1, FSP_WENOIU5_1MP = 2, FSP_WENOIU5_2MP = 3 };
-/* Arithmetic of the right-hand side.  Metrics are FP64 in every mode. */
-enum { FSP_FP64 = 0, FSP_FP32 = 1 };
+/* Arithmetic of the right-hand side.  Metrics are FP64 in every mode.
+ * FSP_FP64        everything in double.
+ * FSP_FP32        state, WENO and fluxes in float (metrics rounded to float on load); the
+ *                 free-stream residual is at FP32 round-off.
+ * FSP_FP32_MIXED  state, characteristic projection and WENO in float; metric products,
+ *                 fluxes, the h combination and the difference in double, so the
+ *                 free-stream residual stays at FP64 round-off.  State arrays are float. */
+enum { FSP_FP64 = 0, FSP_FP32 = 1, FSP_FP32_MIXED = 2 };
 enum { FSP_BC_PERIODIC = 0, FSP_BC_TRANSMISSIVE = 1, FSP_BC_DIRICHLET = 2, FSP_BC_SLIPWALL = 3,
        FSP_BC_FARFIELD = 4 };
 
@@ -165,6 +172,8 @@ fsp_status fsp_rhs_noalloc(const fsp_config* cfg, const fsp_block* blk, const do
  * direction (nj values for xi, ni for eta).  mode 0: D <- the difference; mode 1:
  * D <- -(acc + difference) / J^-1, which is dQ/dt when acc holds the other direction's
  * difference.  acc (mode 1 only) and D have the state layout; D may not alias Q or acc.
+ * Element types: the difference and acc are double (FSP_FP64, FSP_FP32_MIXED) or float
+ * (FSP_FP32); dQ/dt (mode 1) has the state's type.
  * fsp_rhs is fsp_line_lambda + this call for xi (mode 0) + this call for eta (mode 1).
  */
 fsp_status fsp_flux_difference(const fsp_config* cfg, const fsp_block* blk, const double* metrics,

@@ -13,6 +13,8 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
 size_t elem_size(int prec) { return prec == FSP_FP64 ? sizeof(double) : sizeof(float); }
+// element size of the xi accumulator: the flux arithmetic's type
+size_t acc_size(int prec) { return prec == FSP_FP32 ? sizeof(float) : sizeof(double); }
 
 // Workspace: [lam_xi nj | lam_eta ni | cfl 1] doubles, then the xi accumulator and two
 // RK stage buffers, each 4 * nj * ld elements of the state type.
@@ -23,9 +25,10 @@ struct WsLayout {
 WsLayout ws_layout(const fsp_config& c, const fsp_block& b) {
   WsLayout L;
   const size_t state = 4 * (size_t)b.nj * (size_t)b.ld * elem_size(c.precision);
+  const size_t acc = 4 * (size_t)b.nj * (size_t)b.ld * acc_size(c.precision);
   L.lam = 0;
   L.racc = align_up(((size_t)b.ni + b.nj + 1) * sizeof(double));
-  L.q1 = L.racc + align_up(state);
+  L.q1 = L.racc + align_up(acc);
   L.q2 = L.q1 + align_up(state);
   L.total = L.q2 + align_up(state);
   return L;
@@ -44,7 +47,7 @@ bool device_pointer(const void* p) {
 fsp_status check_cfg(const fsp_config* c, const fsp_block* b) {
   if (!c || !b) return FSP_ERR_INVALID_ARG;
   if (c->scheme < 0 || c->scheme > 3) return FSP_ERR_INVALID_ARG;
-  if (c->precision != FSP_FP64 && c->precision != FSP_FP32) return FSP_ERR_INVALID_ARG;
+  if (c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED) return FSP_ERR_INVALID_ARG;
   if (c->interp < 0 || c->interp > 1) return FSP_ERR_INVALID_ARG;
   for (int f = 0; f < 4; ++f)
     if (c->bc[f] < FSP_BC_PERIODIC || c->bc[f] > FSP_BC_FARFIELD) return FSP_ERR_INVALID_ARG;
@@ -214,7 +217,7 @@ fsp_status fsp_cfl_dt(const fsp_config* cfg, const fsp_block* blk, const double*
 fsp_status fsp_norms(const fsp_block* blk, int precision, const void* A, const void* B,
                      double* out, void* stream) {
   if (!blk || blk->ni < 1 || blk->nj < 1 || blk->ld < blk->ni) return FSP_ERR_INVALID_ARG;
-  if (precision != FSP_FP64 && precision != FSP_FP32) return FSP_ERR_INVALID_ARG;
+  if (precision < FSP_FP64 || precision > FSP_FP32_MIXED) return FSP_ERR_INVALID_ARG;
   if (!device_pointer(A) || !device_pointer(out) || (B && !device_pointer(B))) return FSP_ERR_INVALID_ARG;
   return cuda_status(launch_norms(*blk, precision, A, B, out, (cudaStream_t)stream));
 }

@@ -16,6 +16,8 @@ enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, 
 // --------------------------------------------------------------------------------------
 // Scheme coefficients (Section 3)
 // --------------------------------------------------------------------------------------
+// Scheme<S>: r = points per WENO candidate, nmp = midpoints in h+, m0/m1 = h+ coefficients
+// of f+_{j+1/2} and f+_{j-1/2}, n(k) = h+ coefficient of f+_{j+k-2} (k = 0..4).
 template <int S> struct Scheme;
 // WENOIU3-1MP, Eq. (3.4): h+ = f_{j+1/2} + (-f_{j-1} + 2 f_j - f_{j+1}) / 24
 template <> struct Scheme<S31> {
@@ -48,8 +50,6 @@ template <> struct Scheme<S52> {
     return k == 1 || k == 2 ? 1.0 / 30 : k == 3 ? -4.0 / 30 : 0.0;
   }
 };
-
-// n(k): h+ coefficient of f+_{j+k-2}, k = 0..4 (node offsets -2..2).
 
 // Central operator delta^{c,(1)} of each scheme (Eq. 2.7), used for the metrics:
 //   D f_j = sum_k a_k (f_{j+k} - f_{j-k}) + b_{1/2}(f~_{j+1/2} - f~_{j-1/2})
@@ -165,37 +165,68 @@ __device__ __forceinline__ Real spectral_radius(const Real q[4], Real mx, Real m
 }
 
 // --------------------------------------------------------------------------------------
-// Characteristic projection (Section 3.4): left eigenvector rows at a state q along the
-// unit direction (nx, ny); R is applied in factored form in recon().
+// Small arithmetic helpers by precision
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// quotient: IEEE division in FP64; the fast approximate quotient in FP32
+__device__ __forceinline__ double quot(double a, double b) { return a / b; }
+__device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
+// x <= 0 from the sign and magnitude bits (integer compare, no floating-point pipe)
+__device__ __forceinline__ bool nonpos(double x) { return __double_as_longlong(x) <= 0LL; }
+__device__ __forceinline__ bool nonpos(float x) { return __float_as_int(x) <= 0; }
+
+// Primitive quantities of a node used by the characteristic projection (Section 3.4).
+template <typename Real>
+struct Prim {
+  Real u, v, c, cinv, H, b1, h2;  // b1 = (gamma-1)/c^2, h2 = |u|^2/2
+};
+
+template <typename Real>
+__device__ __forceinline__ Prim<Real> prim_of(const Real q[4], Real gamma) {
+  Prim<Real> w;
+  const Real rinv = Real(1) / q[0];
+  w.u = q[1] * rinv;
+  w.v = q[2] * rinv;
+  w.h2 = Real(0.5) * (w.u * w.u + w.v * w.v);
+  const Real gm1 = gamma - Real(1);
+  const Real p = gm1 * (q[3] - q[0] * w.h2);
+  const Real c2 = gamma * p * rinv;
+  w.cinv = rsq(c2);
+  w.c = c2 * w.cinv;
+  w.H = (q[3] + p) * rinv;
+  w.b1 = gm1 * w.cinv * w.cinv;
+  return w;
+}
+
+// --------------------------------------------------------------------------------------
+// Characteristic projection (Section 3.4): left eigenvector rows of the flux Jacobian at
+// a node along the unit direction (nx, ny); R is applied in factored form in recon().
 // --------------------------------------------------------------------------------------
 template <typename Real>
 struct Eig {
   Real L[4][4];
-  Real u, v, c, H, Un, Ut, nx, ny, h2;  // h2 = |u|^2 / 2
+  Real u, v, c, H, Un, Ut, nx, ny, h2;
 
-  __device__ __forceinline__ void build(const Real q[4], Real nx_, Real ny_, Real gamma) {
+  __device__ __forceinline__ void build(const Prim<Real>& w, Real nx_, Real ny_) {
     nx = nx_; ny = ny_;
-    const Real rinv = Real(1) / q[0];
-    u = q[1] * rinv; v = q[2] * rinv;
-    h2 = Real(0.5) * (u * u + v * v);
-    const Real gm1 = gamma - Real(1);
-    const Real p = gm1 * (q[3] - q[0] * h2);
-    const Real c2 = gamma * p * rinv;
-    c = sqrt(c2);
-    const Real cinv = Real(1) / c;
-    H = (q[3] + p) * rinv;
+    u = w.u; v = w.v; c = w.c; H = w.H; h2 = w.h2;
     Un = u * nx + v * ny;
     Ut = v * nx - u * ny;
-    const Real b1 = gm1 * cinv * cinv;
-    const Real b2 = b1 * h2;
+    const Real b1 = w.b1, b2 = b1 * h2;
     const Real hb1 = Real(0.5) * b1, hb2 = Real(0.5) * b2;
-    const Real hUc = Real(0.5) * Un * cinv, hnxc = Real(0.5) * nx * cinv, hnyc = Real(0.5) * ny * cinv;
+    const Real hc = Real(0.5) * w.cinv;
+    const Real hUc = Un * hc, hnxc = nx * hc, hnyc = ny * hc;
     L[0][0] = hb2 + hUc; L[0][1] = -hb1 * u - hnxc; L[0][2] = -hb1 * v - hnyc; L[0][3] = hb1;
     L[1][0] = Real(1) - b2; L[1][1] = b1 * u; L[1][2] = b1 * v; L[1][3] = -b1;
     L[2][0] = -Ut; L[2][1] = -ny; L[2][2] = nx; L[2][3] = Real(0);
     L[3][0] = hb2 - hUc; L[3][1] = -hb1 * u + hnxc; L[3][2] = -hb1 * v + hnyc; L[3][3] = hb1;
   }
-  // Q = R W with R's columns (1, u - c nx, v - c ny, H - c Un), (1, u, v, |u|^2/2),
+  __device__ __forceinline__ Real project(int k, Real d0, Real d1, Real d2, Real d3) const {
+    if (k == 2) return L[2][0] * d0 + L[2][1] * d1 + L[2][2] * d2;
+    return L[k][0] * d0 + L[k][1] * d1 + L[k][2] * d2 + L[k][3] * d3;
+  }
+  // dq = R W with R's columns (1, u - c nx, v - c ny, H - c Un), (1, u, v, |u|^2/2),
   // (0, -ny, nx, Ut), (1, u + c nx, v + c ny, H + c Un)
   __device__ __forceinline__ void recon(const Real W[4], Real q[4]) const {
     const Real s = W[0] + W[3], d = W[3] - W[0];
@@ -208,67 +239,115 @@ struct Eig {
 };
 
 // --------------------------------------------------------------------------------------
-// WENO interpolation to x_{j+1/2} (Eqs. 3.10-3.13, Table 1) with the indicators of
-// Eq. (3.22) (written on consecutive differences; for r = 2 the three-point IS_0, IS_1 of
-// Section 5.1) and the mapping of Eq. (3.15) (r = 2) or (3.23) (r = 3).
-// u[0..4] = u_{j-2} .. u_{j+2}.  The weights are formed with one reciprocal:
-// omega_k = C_k prod_{l != k} b_l^2 / sum_m C_m prod_{l != m} b_l^2, b = eps + IS;
-// the mapped weights g_k are normalised in the final quotient sum g p / sum g.
+// WENO interpolation to x_{j+1/2} (Eqs. 3.10-3.13, Table 1), indicators of Eq. (3.22) on
+// consecutive differences (for r = 2 the three-point IS_0, IS_1 of Section 5.1), mapping
+// of Eq. (3.15) (r = 2) or (3.23) (r = 3).  Written on values relative to the stencil
+// centre, u[m+2] = w_{j+m} - w_j (u[2] is not read): the candidates' coefficients sum to
+// one and the indicators use differences only, so the interpolant of w is w_j plus the
+// returned value, and uniform data give exactly 0.
+// Weights.  FP64: omega_k = C_k prod_{l!=k} b_l^2 / sum_m C_m prod_{l!=m} b_l^2,
+// b = eps + IS (one reciprocal; b >= eps keeps every product in range).  FP32:
+// omega_k proportional to C_k (b_min / b_k)^2, whose terms stay in [0, C_k].
+// The mapped weights g_k are normalised in the final quotient sum g p / sum g.
 // --------------------------------------------------------------------------------------
-template <int R>
-__device__ __forceinline__ double weno_mid(const double* u, double eps, int ppm, int linw) {
+template <typename T>
+__device__ __forceinline__ T is_b(T e, T f, T eps) {
+  return eps + T(13.0 / 12) * e * e + T(0.25) * f * f;
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void raw_weights(const T* b, const T* C, T* w) {
+  if constexpr (sizeof(T) == 8) {
+    T s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] = b[k] * b[k];
+    T t[K];
+    if constexpr (K == 3) {
+      t[0] = C[0] * (s[1] * s[2]);
+      t[1] = C[1] * (s[0] * s[2]);
+      t[2] = C[2] * (s[0] * s[1]);
+    } else {
+      t[0] = C[0] * s[1];
+      t[1] = C[1] * s[0];
+    }
+    T sum = t[0];
+#pragma unroll
+    for (int k = 1; k < K; ++k) sum += t[k];
+    const T inv = T(1) / sum;
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = t[k] * inv;
+  } else {
+    T bmin = b[0];
+#pragma unroll
+    for (int k = 1; k < K; ++k) bmin = fminf(bmin, b[k]);
+    T t[K], sum = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const T r = quot(bmin, b[k]);
+      t[k] = C[k] * r * r;
+      sum += t[k];
+    }
+    const T inv = quot(T(1), sum);
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = t[k] * inv;
+  }
+}
+
+template <int R, typename T>
+__device__ __forceinline__ T weno_delta(const T* u, T eps, int ppm, int linw) {
   if constexpr (R == 3) {
-    const double p0 = 0.375 * u[0] - 1.25 * u[1] + 1.875 * u[2];
-    const double p1 = -0.125 * u[1] + 0.75 * u[2] + 0.375 * u[3];
-    const double p2 = 0.375 * u[2] + 0.75 * u[3] - 0.125 * u[4];
-    constexpr double C0 = 1.0 / 16, C1 = 10.0 / 16, C2 = 5.0 / 16;
-    if (linw) return C0 * p0 + C1 * p1 + C2 * p2;
-    const double d1 = u[1] - u[0], d2 = u[2] - u[1], d3 = u[3] - u[2], d4 = u[4] - u[3];
-    const double e0 = d2 - d1, e1 = d3 - d2, e2 = d4 - d3;
-    const double f0 = 3.0 * d2 - d1, f1 = d2 + d3, f2 = d4 - 3.0 * d3;
-    const double b0 = eps + (13.0 / 12) * e0 * e0 + 0.25 * f0 * f0;
-    const double b1 = eps + (13.0 / 12) * e1 * e1 + 0.25 * f1 * f1;
-    const double b2 = eps + (13.0 / 12) * e2 * e2 + 0.25 * f2 * f2;
-    const double s0 = b0 * b0, s1 = b1 * b1, s2 = b2 * b2;
-    const double t0 = C0 * s1 * s2, t1 = C1 * s0 * s2, t2 = C2 * s0 * s1;
-    const double inv = 1.0 / (t0 + t1 + t2);
-    double w0 = t0 * inv, w1 = t1 * inv, w2 = t2 * inv;
+    // candidates of Table 1 relative to w_j
+    const T p0 = T(0.375) * u[0] - T(1.25) * u[1];
+    const T p1 = T(-0.125) * u[1] + T(0.375) * u[3];
+    const T p2 = T(0.75) * u[3] - T(0.125) * u[4];
+    const T C[3] = {T(1.0 / 16), T(10.0 / 16), T(5.0 / 16)};
+    if (linw) return C[0] * p0 + C[1] * p1 + C[2] * p2;
+    const T d1 = u[1] - u[0], d2 = -u[1], d3 = u[3], d4 = u[4] - u[3];
+    const T b[3] = {is_b(d2 - d1, T(3) * d2 - d1, eps), is_b(d3 - d2, d2 + d3, eps),
+                    is_b(d4 - d3, d4 - T(3) * d3, eps)};
+    T w[3];
+    raw_weights<T, 3>(b, C, w);
     if (ppm) {
       // g = C + (w - C)^3 / C^2 (w <= C), C + (w - C)^3 / (C - 1)^2 (w > C)   [Eq. 3.23]
-      const double q0 = w0 - C0, q1 = w1 - C1, q2 = w2 - C2;
-      const double k0 = q0 <= 0.0 ? 1.0 / (C0 * C0) : 1.0 / ((C0 - 1) * (C0 - 1));
-      const double k1 = q1 <= 0.0 ? 1.0 / (C1 * C1) : 1.0 / ((C1 - 1) * (C1 - 1));
-      const double k2 = q2 <= 0.0 ? 1.0 / (C2 * C2) : 1.0 / ((C2 - 1) * (C2 - 1));
-      w0 = C0 + q0 * q0 * q0 * k0;
-      w1 = C1 + q1 * q1 * q1 * k1;
-      w2 = C2 + q2 * q2 * q2 * k2;
-      return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+      const T K0[3] = {T(256.0), T(256.0 / 100), T(256.0 / 25)};          // 1 / C^2
+      const T K1[3] = {T(256.0 / 225), T(256.0 / 36), T(256.0 / 121)};   // 1 / (C - 1)^2
+      T num = T(0), den = T(0);
+      const T p[3] = {p0, p1, p2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const T q = w[k] - C[k];
+        const T g = C[k] + q * q * q * (nonpos(q) ? K0[k] : K1[k]);
+        num += g * p[k];
+        den += g;
+      }
+      return quot(num, den);
     }
-    return w0 * p0 + w1 * p1 + w2 * p2;
+    return w[0] * p0 + w[1] * p1 + w[2] * p2;
   } else {
-    const double p0 = -0.5 * u[1] + 1.5 * u[2];
-    const double p1 = 0.5 * u[2] + 0.5 * u[3];
-    constexpr double C0 = 0.25, C1 = 0.75;
-    if (linw) return C0 * p0 + C1 * p1;
-    const double d1 = u[1] - u[0], d2 = u[2] - u[1], d3 = u[3] - u[2];
-    const double e0 = d2 - d1, e1 = d3 - d2;
-    const double f0 = 3.0 * d2 - d1, f1 = d2 + d3;
-    const double b0 = eps + (13.0 / 12) * e0 * e0 + 0.25 * f0 * f0;
-    const double b1 = eps + (13.0 / 12) * e1 * e1 + 0.25 * f1 * f1;
-    const double s0 = b0 * b0, s1 = b1 * b1;
-    const double t0 = C0 * s1, t1 = C1 * s0;
-    const double inv = 1.0 / (t0 + t1);
-    double w0 = t0 * inv, w1 = t1 * inv;
+    const T p0 = T(-0.5) * u[1];
+    const T p1 = T(0.5) * u[3];
+    const T C[2] = {T(0.25), T(0.75)};
+    if (linw) return C[0] * p0 + C[1] * p1;
+    const T d1 = u[1] - u[0], d2 = -u[1], d3 = u[3];
+    const T b[2] = {is_b(d2 - d1, T(3) * d2 - d1, eps), is_b(d3 - d2, d2 + d3, eps)};
+    T w[2];
+    raw_weights<T, 2>(b, C, w);
     if (ppm) {
       // g = C - (w - C)^2 / C (w <= C), C - (w - C)^2 / (C - 1) (w > C)   [Eq. 3.15]
-      const double q0 = w0 - C0, q1 = w1 - C1;
-      const double k0 = q0 <= 0.0 ? 1.0 / C0 : 1.0 / (C0 - 1);
-      const double k1 = q1 <= 0.0 ? 1.0 / C1 : 1.0 / (C1 - 1);
-      w0 = C0 - q0 * q0 * k0;
-      w1 = C1 - q1 * q1 * k1;
-      return (w0 * p0 + w1 * p1) / (w0 + w1);
+      const T K0[2] = {T(4.0), T(4.0 / 3)};        // 1 / C
+      const T K1[2] = {T(-4.0 / 3), T(-4.0)};      // 1 / (C - 1)
+      const T p[2] = {p0, p1};
+      T num = T(0), den = T(0);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const T q = w[k] - C[k];
+        const T g = C[k] - q * q * (nonpos(q) ? K0[k] : K1[k]);
+        num += g * p[k];
+        den += g;
+      }
+      return quot(num, den);
     }
-    return w0 * p0 + w1 * p1;
+    return w[0] * p0 + w[1] * p1;
   }
 }
 

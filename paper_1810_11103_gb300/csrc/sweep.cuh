@@ -1,0 +1,335 @@
+// sweep.cuh -- one direction of the WENOIU right-hand side (Li & Sun, arXiv:1810.11103,
+// Sections 2.3, 3 and 3.4) as a tiled CUDA kernel, templated on the arithmetic:
+//   Real  state, primitives, characteristic projection and WENO interpolation
+//   Acc   metric products, fluxes, the h combination and the difference
+// (double/double for FP64, float/float for FP32, float/double for FP32 with FP64 fluxes).
+//
+// A CTA owns NL grid lines x T output nodes of one direction.  Phase 1 stages every node of
+// the tile plus four ghosts a side in shared memory: the state (ghosts by the boundary
+// rule), the direction's metrics, the node flux E^ and the primitives the characteristic
+// projection needs.  Phase 2 gives each thread one interface p + 1/2: the eigenvectors at
+// Q_p and Q_{p+1} along the averaged metric direction, WENO interpolation of the
+// characteristic differences from both sides, the states Q+- at the midpoint, and the split
+// midpoint fluxes with the interpolated midpoint metrics.  The h = h+ + h- combination and
+// the difference H_{s+1/2} - H_{s-1/2} follow from shared memory; the epilogue writes the
+// difference, dQ/dt, or a TVD-RK3 stage.
+#pragma once
+
+#include <type_traits>
+
+#include "fsp_device.cuh"
+
+namespace fsp {
+
+enum { MODE_ACC = 0, MODE_RHS = 1, MODE_STAGE = 2 };
+
+template <int S, int DIR, typename Real, typename Acc>
+struct TileShape {
+  static constexpr int NL = DIR == 0 ? 2 : 8;        // grid lines per CTA
+  static constexpr int W = DIR == 0 ? 128 : 32;      // interface slots per line
+  static constexpr int NMP = Scheme<S>::nmp;
+  static constexpr int T = W - NMP - 1;              // output nodes per line
+  static constexpr int NP = T + 8;                   // staged nodes per line
+  static constexpr int PLO = -NMP;                   // first interface p (of p + 1/2)
+  static constexpr int THREADS = 256;
+  static constexpr int NN = NL * NP, NW = NL * W;
+  static constexpr bool SPLIT_MET = !std::is_same<Real, Acc>::value;
+  static constexpr size_t smem_bytes() {
+    return sizeof(Real) * ((size_t)(4 + 7) * NN + (SPLIT_MET ? 2 * NN : 0)) +
+           sizeof(Acc) * ((size_t)(4 + 2) * NN + (size_t)4 * NW + (NMP == 2 ? (size_t)8 * NW : 0));
+  }
+};
+
+template <int S, int DIR, int MODE, typename Real, typename Acc>
+__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 3)
+sweep_kernel(Params P, const Real* __restrict__ Q, const double* __restrict__ lam,
+             const Acc* __restrict__ Dacc, Acc* __restrict__ Dout, Real* qout, const Real* Qn,
+             double ca, double cb, double dt) {
+  using Sh = TileShape<S, DIR, Real, Acc>;
+  using Sc = Scheme<S>;
+  constexpr int NL = Sh::NL, W = Sh::W, T = Sh::T, NP = Sh::NP, PLO = Sh::PLO;
+  constexpr int NN = Sh::NN, NW = Sh::NW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Acc* sE = reinterpret_cast<Acc*>(smem_raw);            // [4][NN] node E^
+  Acc* sMa = sE + 4 * NN;                                // [2][NN] metrics (flux arithmetic)
+  Acc* sH = sMa + 2 * NN;                                // [4][NW] h at interfaces
+  Acc* sF = sH + 4 * NW;                                 // [8][NW] f+-_mid (two midpoints)
+  Real* sQ = reinterpret_cast<Real*>(sF + (Sh::NMP == 2 ? 8 * NW : 0));  // [4][NN]
+  Real* sP = sQ + 4 * NN;                                // [7][NN] primitives
+  Real* sMr = Sh::SPLIT_MET ? sP + 7 * NN : nullptr;     // [2][NN] metrics in Real
+
+  const int n = DIR == 0 ? P.ni : P.nj;
+  const int nlines = DIR == 0 ? P.nj : P.ni;
+  const int line0 = blockIdx.y * NL;
+  const int base = blockIdx.x * T;
+  const Real gamma = Real(P.gamma);
+  const Real eps = sizeof(Real) == 8 ? Real(P.eps) : Real(fmax(P.eps, 1e-30));
+  const long long plane = (long long)P.nj * P.ld;
+
+  auto SI = [](int l, int s) { return DIR == 0 ? l * NP + s : s * NL + l; };
+  auto WI = [](int l, int p) { return DIR == 0 ? l * W + p : p * NL + l; };
+  auto metR = [&](int c, int o) -> Real {
+    if constexpr (Sh::SPLIT_MET) return sMr[c * NN + o];
+    else return sMa[c * NN + o];
+  };
+
+  // ---- phase 1: nodes ----
+  for (int k = threadIdx.x; k < NN; k += Sh::THREADS) {
+    const int l = DIR == 0 ? k / NP : k % NL;
+    const int s = DIR == 0 ? k % NP : k / NL;
+    const int line = line0 + l;
+    if (line >= nlines) continue;
+    const int g = min(base + s - 4, n + 3);  // positions past n+3 are never used
+    Real q[4];
+    load_state(P, Q, DIR, line, g, q);
+    double mx, my;
+    if (DIR == 0) { mx = met_at(P, 0, g, line); my = met_at(P, 1, g, line); }
+    else          { mx = met_at(P, 2, line, g); my = met_at(P, 3, line, g); }
+    const Prim<Real> w = prim_of(q, gamma);
+    // E^ = mx E + my F with the metric products in Acc
+    const Real p = (gamma - Real(1)) * (q[3] - q[0] * w.h2);
+    const Acc U = Acc(mx) * Acc(w.u) + Acc(my) * Acc(w.v);
+    const int o = SI(l, s);
+    sE[0 * NN + o] = Acc(q[0]) * U;
+    sE[1 * NN + o] = Acc(q[1]) * U + Acc(mx) * Acc(p);
+    sE[2 * NN + o] = Acc(q[2]) * U + Acc(my) * Acc(p);
+    sE[3 * NN + o] = Acc(q[3] + p) * U;
+    sMa[o] = Acc(mx);
+    sMa[NN + o] = Acc(my);
+    if constexpr (Sh::SPLIT_MET) { sMr[o] = Real(mx); sMr[NN + o] = Real(my); }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sQ[v * NN + o] = q[v];
+    sP[0 * NN + o] = w.u; sP[1 * NN + o] = w.v; sP[2 * NN + o] = w.c; sP[3 * NN + o] = w.cinv;
+    sP[4 * NN + o] = w.H; sP[5 * NN + o] = w.b1; sP[6 * NN + o] = w.h2;
+  }
+  __syncthreads();
+
+  // ---- phase 2: interfaces p + 1/2 ----
+  for (int k = threadIdx.x; k < NW; k += Sh::THREADS) {
+    const int l = DIR == 0 ? k / W : k % NL;
+    const int pi = DIR == 0 ? k % W : k / NL;
+    const int line = line0 + l;
+    const int p = PLO + pi;
+    if (line >= nlines || base + p > n) continue;
+    const Acc A = Acc(P.alpha * lam[line]);
+    const int c0 = p + 4;  // staged position of node p
+    const int o0 = SI(l, c0), o1 = SI(l, c0 + 1);
+
+    // characteristic direction: unit vector of the averaged metrics (Section 3.4)
+    const Real mbx = Real(0.5) * (metR(0, o0) + metR(0, o1));
+    const Real mby = Real(0.5) * (metR(1, o0) + metR(1, o1));
+    const Real rn = rsq(mbx * mbx + mby * mby);
+    const Real nx = mbx * rn, ny = mby * rn;
+
+    Real Qs[2][4];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      // "+" side: eigenvectors at Q_p, stencil p-2..p+2; "-" side: at Q_{p+1}, mirrored
+      const int oc = side == 0 ? o0 : o1;
+      Prim<Real> w;
+      w.u = sP[0 * NN + oc]; w.v = sP[1 * NN + oc]; w.c = sP[2 * NN + oc]; w.cinv = sP[3 * NN + oc];
+      w.H = sP[4 * NN + oc]; w.b1 = sP[5 * NN + oc]; w.h2 = sP[6 * NN + oc];
+      Eig<Real> E;
+      E.build(w, nx, ny);
+      const Real qc0 = sQ[oc], qc1 = sQ[NN + oc], qc2 = sQ[2 * NN + oc], qc3 = sQ[3 * NN + oc];
+      // state differences to the centre at the stencil offsets -2, -1, +1, +2
+      Real dq[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int m = a < 2 ? a - 2 : a - 1;
+        if (Sc::r == 2 && m == 2) { dq[a][0] = dq[a][1] = dq[a][2] = dq[a][3] = Real(0); continue; }
+        const int o = SI(l, side == 0 ? c0 + m : c0 + 1 - m);
+        dq[a][0] = sQ[o] - qc0;
+        dq[a][1] = sQ[NN + o] - qc1;
+        dq[a][2] = sQ[2 * NN + o] - qc2;
+        dq[a][3] = sQ[3 * NN + o] - qc3;
+      }
+      Real Wm[4];
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+        Real u[5];
+        u[0] = E.project(kc, dq[0][0], dq[0][1], dq[0][2], dq[0][3]);
+        u[1] = E.project(kc, dq[1][0], dq[1][1], dq[1][2], dq[1][3]);
+        u[2] = Real(0);
+        u[3] = E.project(kc, dq[2][0], dq[2][1], dq[2][2], dq[2][3]);
+        u[4] = Sc::r == 3 ? E.project(kc, dq[3][0], dq[3][1], dq[3][2], dq[3][3]) : Real(0);
+        Wm[kc] = weno_delta<Sc::r, Real>(u, eps, P.ppm, P.linw);
+      }
+      Real dQm[4];
+      E.recon(Wm, dQm);
+      Qs[side][0] = qc0 + dQm[0];
+      Qs[side][1] = qc1 + dQm[1];
+      Qs[side][2] = qc2 + dQm[2];
+      Qs[side][3] = qc3 + dQm[3];
+    }
+
+    // midpoint metrics by the same interpolation as the metric evaluation (Section 2.4)
+    Acc vx[6], vy[6];
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk) {
+      const int o = SI(l, c0 - 2 + kk);
+      vx[kk] = sMa[o];
+      vy[kk] = sMa[NN + o];
+    }
+    const Acc mmx = mid_interp(P.interp, Sc::r == 3, vx);
+    const Acc mmy = mid_interp(P.interp, Sc::r == 3, vy);
+    // split midpoint fluxes f+ = (E^(Q+) + A^ Q+)/2, f- = (E^(Q-) - A^ Q-)/2
+    Acc fs[2][4];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const Real* q = Qs[side];
+      const Real rinv = Real(1) / q[0];
+      const Real u = q[1] * rinv, v = q[2] * rinv;
+      const Real pr = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
+      const Acc U = mmx * Acc(u) + mmy * Acc(v);
+      const Acc sg = side == 0 ? A : -A;
+      fs[side][0] = Acc(0.5) * (Acc(q[0]) * U + sg * Acc(q[0]));
+      fs[side][1] = Acc(0.5) * (Acc(q[1]) * U + mmx * Acc(pr) + sg * Acc(q[1]));
+      fs[side][2] = Acc(0.5) * (Acc(q[2]) * U + mmy * Acc(pr) + sg * Acc(q[2]));
+      fs[side][3] = Acc(0.5) * (Acc(q[3] + pr) * U + sg * Acc(q[3]));
+    }
+    if constexpr (Sc::nmp == 1) {
+      // h = h+ + h-: the midpoint terms plus the node terms of f+- = (E^ +- A^ Q)/2, h- the
+      // mirror of h+ about p + 1/2 (f_{p+k} -> f_{p+1-k})
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        Acc h = Acc(Sc::m0) * (fs[0][v] + fs[1][v]);
+#pragma unroll
+        for (int kk = -2; kk <= 2; ++kk) {
+          if (Sc::n(kk + 2) == 0.0) continue;
+          const int a = SI(l, c0 + kk), b = SI(l, c0 + 1 - kk);
+          h += Acc(Sc::n(kk + 2) * 0.5) *
+               ((sE[v * NN + a] + sE[v * NN + b]) + A * Acc(sQ[v * NN + a] - sQ[v * NN + b]));
+        }
+        sH[v * NW + WI(l, pi)] = h;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        sF[v * NW + WI(l, pi)] = fs[0][v];
+        sF[(4 + v) * NW + WI(l, pi)] = fs[1][v];
+      }
+    }
+  }
+
+  if constexpr (Sc::nmp == 2) {
+    __syncthreads();
+    // h+ uses f+ at p+1/2 and p-1/2; h- uses f- at p+1/2 and p+3/2
+    for (int k = threadIdx.x; k < NW; k += Sh::THREADS) {
+      const int l = DIR == 0 ? k / W : k % NL;
+      const int pi = DIR == 0 ? k % W : k / NL;
+      const int line = line0 + l;
+      const int p = PLO + pi;
+      if (line >= nlines || p < -1 || p > T - 1 || base + p > n - 1) continue;
+      const Acc A = Acc(P.alpha * lam[line]);
+      const int c0 = p + 4;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        Acc h = Acc(Sc::m0) * (sF[v * NW + WI(l, pi)] + sF[(4 + v) * NW + WI(l, pi)]) +
+                Acc(Sc::m1) * (sF[v * NW + WI(l, pi - 1)] + sF[(4 + v) * NW + WI(l, pi + 1)]);
+#pragma unroll
+        for (int kk = -2; kk <= 2; ++kk) {
+          if (Sc::n(kk + 2) == 0.0) continue;
+          const int a = SI(l, c0 + kk), b = SI(l, c0 + 1 - kk);
+          h += Acc(Sc::n(kk + 2) * 0.5) *
+               ((sE[v * NN + a] + sE[v * NN + b]) + A * Acc(sQ[v * NN + a] - sQ[v * NN + b]));
+        }
+        sH[v * NW + WI(l, pi)] = h;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- nodes: difference of h (Eq. 3.2) and the epilogue ----
+  for (int k = threadIdx.x; k < NL * T; k += Sh::THREADS) {
+    const int l = DIR == 0 ? k / T : k % NL;
+    const int s = DIR == 0 ? k % T : k / NL;
+    const int line = line0 + l;
+    const int g = base + s;
+    if (line >= nlines || g >= n) continue;
+    const int pi = s - PLO;  // interface s + 1/2
+    const int i = DIR == 0 ? g : line, j = DIR == 0 ? line : g;
+    const long long o = (long long)j * P.ld + i;
+    Acc R[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) R[v] = sH[v * NW + WI(l, pi)] - sH[v * NW + WI(l, pi - 1)];
+    if constexpr (MODE == MODE_ACC) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Dout[v * plane + o] = R[v];
+    } else {
+      const Acc mJ = Acc(-1.0 / met_at(P, 4, i, j));
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const Acc d = (Dacc[v * plane + o] + R[v]) * mJ;
+        if constexpr (MODE == MODE_RHS) {
+          qout[v * plane + o] = Real(d);
+        } else {
+          const Acc qs = Acc(sQ[v * NN + SI(l, s + 4)]);
+          qout[v * plane + o] = Real(Acc(ca) * Acc(Qn[v * plane + o]) + Acc(cb) * (qs + Acc(dt) * d));
+        }
+      }
+    }
+  }
+}
+
+template <int S, int DIR, int MODE, typename Real, typename Acc>
+cudaError_t launch_sweep(const Params& P, const Real* Q, const double* lam, const Acc* Dacc, Acc* Dout,
+                         Real* qout, const Real* Qn, double ca, double cb, double dt, cudaStream_t st) {
+  using Sh = TileShape<S, DIR, Real, Acc>;
+  const int n = DIR == 0 ? P.ni : P.nj, nlines = DIR == 0 ? P.nj : P.ni;
+  dim3 grid((n + Sh::T - 1) / Sh::T, (nlines + Sh::NL - 1) / Sh::NL);
+  const size_t smem = Sh::smem_bytes();
+  auto kern = sweep_kernel<S, DIR, MODE, Real, Acc>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, Sh::THREADS, smem, st>>>(P, Q, lam, Dacc, Dout, qout, Qn, ca, cb, dt);
+  return cudaGetLastError();
+}
+
+// Both directions for one scheme: xi into the accumulator, eta with the epilogue
+// (mode 0: dQ/dt, mode 1: RK stage).
+template <int S, typename Real, typename Acc>
+cudaError_t rhs_passes(const Params& P, const Real* Q, const double* lam_xi, const double* lam_eta,
+                       Acc* Racc, Real* out, int mode, const Real* Qn, double ca, double cb, double dt,
+                       cudaStream_t st) {
+  cudaError_t e = launch_sweep<S, 0, MODE_ACC, Real, Acc>(P, Q, lam_xi, nullptr, Racc, nullptr, nullptr,
+                                                          0, 0, 0, st);
+  if (e != cudaSuccess) return e;
+  if (mode == 0)
+    return launch_sweep<S, 1, MODE_RHS, Real, Acc>(P, Q, lam_eta, Racc, nullptr, out, nullptr, 0, 0, 0, st);
+  return launch_sweep<S, 1, MODE_STAGE, Real, Acc>(P, Q, lam_eta, Racc, nullptr, out, Qn, ca, cb, dt, st);
+}
+
+// One direction through the public per-direction entry (mode 0: difference into D (Acc);
+// mode 1: dQ/dt = -(acc + difference) / J^-1 into the state type).
+template <int S, typename Real, typename Acc>
+cudaError_t flux_difference_passes(const Params& P, const Real* Q, const double* lam, int dir, int mode,
+                                   const Acc* acc, void* out, cudaStream_t st) {
+  if (dir == 0)
+    return mode == 0
+               ? launch_sweep<S, 0, MODE_ACC, Real, Acc>(P, Q, lam, nullptr, static_cast<Acc*>(out), nullptr,
+                                                         nullptr, 0, 0, 0, st)
+               : launch_sweep<S, 0, MODE_RHS, Real, Acc>(P, Q, lam, acc, nullptr, static_cast<Real*>(out),
+                                                         nullptr, 0, 0, 0, st);
+  return mode == 0
+             ? launch_sweep<S, 1, MODE_ACC, Real, Acc>(P, Q, lam, nullptr, static_cast<Acc*>(out), nullptr,
+                                                       nullptr, 0, 0, 0, st)
+             : launch_sweep<S, 1, MODE_RHS, Real, Acc>(P, Q, lam, acc, nullptr, static_cast<Real*>(out),
+                                                       nullptr, 0, 0, 0, st);
+}
+
+// Precision instantiations: each lives in its own translation unit.
+cudaError_t rhs_fp64(int scheme, const Params& P, const void* Q, const double* lx, const double* le,
+                     void* Racc, void* out, int mode, const void* Qn, double ca, double cb, double dt,
+                     cudaStream_t st);
+cudaError_t rhs_fp32(int scheme, bool mixed, const Params& P, const void* Q, const double* lx,
+                     const double* le, void* Racc, void* out, int mode, const void* Qn, double ca,
+                     double cb, double dt, cudaStream_t st);
+cudaError_t flux_difference_fp64(int scheme, const Params& P, const void* Q, const double* lam, int dir,
+                                 int mode, const void* acc, void* out, cudaStream_t st);
+cudaError_t flux_difference_fp32(int scheme, bool mixed, const Params& P, const void* Q, const double* lam,
+                                 int dir, int mode, const void* acc, void* out, cudaStream_t st);
+
+}  // namespace fsp
