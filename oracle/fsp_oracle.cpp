@@ -104,7 +104,33 @@ template <> inline long double cst<long double>(long double c) { return c; }
 // Scheme tables (Section 3).  All four variants, with the printed coefficients.
 // ----------------------------------------------------------------------------------
 enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, BC_FARFIELD = 4 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, BC_FARFIELD = 4,
+       BC_LINK = 5 };
+
+// A face joined to a face of another block (multi-block grids).  The blocks partition the
+// nodes of one larger structured grid: the ghost at depth k (k = 0 first) beyond face f of
+// block B is the node at depth k inward from face `face` of block `nbr`; along the face
+// the index runs the same way or `rev`ersed; `off` is added to ghost coordinates.
+struct Link { int nbr, face, rev; double off[2]; };
+
+// Index of the node of the neighbour behind face f for a ghost of a block of size ni x nj.
+// (gi, gj) is the ghost (outside the range along face f's direction); returns (ni', nj').
+static inline void link_map(const Link& L, int f, int ni, int nj, int nni, int nnj, int gi, int gj,
+                            int& oi, int& oj) {
+  int k, t;
+  if (f == 0) { k = -1 - gi; t = gj; }
+  else if (f == 1) { k = gi - ni; t = gj; }
+  else if (f == 2) { k = -1 - gj; t = gi; }
+  else { k = gj - nj; t = gi; }
+  const int nt = (L.face < 2) ? nnj : nni;
+  if (L.rev) t = nt - 1 - t;
+  int depth;
+  if (L.face == 0) depth = k;
+  else if (L.face == 1) depth = nni - 1 - k;
+  else if (L.face == 2) depth = k;
+  else depth = nnj - 1 - k;
+  if (L.face < 2) { oi = depth; oj = t; } else { oi = t; oj = depth; }
+}
 static const int G = 4;  // ghost layers of the stored metrics
 
 struct SchemeTab {
@@ -190,8 +216,20 @@ struct Coords {
   int ni, nj, bc[4];
   T per[2][2];          // per[0] = (dx, dy) added per wrap in i, per[1] likewise in j
   const T* x; const T* y;
+  const Link* links = nullptr;       // 4 per block when some face is BC_LINK
+  const Coords<T>* blocks = nullptr; // every block of a multi-block grid
+  int hops = 0;
+  void linked(int f, int i, int j, T& X, T& Y) const {
+    const Link& L = links[f];
+    const Coords<T>& N = blocks[L.nbr];
+    int oi, oj;
+    link_map(L, f, ni, nj, N.ni, N.nj, i, j, oi, oj);
+    N.at(oi, oj, X, Y);
+    X = X + T(L.off[0]); Y = Y + T(L.off[1]);
+  }
   void at(int i, int j, T& X, T& Y) const {
     if (j < 0 || j >= nj) {
+      if (bc[j < 0 ? 2 : 3] == BC_LINK) { linked(j < 0 ? 2 : 3, i, j, X, Y); return; }
       if (bc[2] == BC_PERIODIC) {
         int q = floordiv(j, nj);
         at(i, j - q * nj, X, Y);
@@ -205,6 +243,7 @@ struct Coords {
       return;
     }
     if (i < 0 || i >= ni) {
+      if (bc[i < 0 ? 0 : 1] == BC_LINK) { linked(i < 0 ? 0 : 1, i, j, X, Y); return; }
       if (bc[0] == BC_PERIODIC) {
         int q = floordiv(i, ni);
         at(i - q * ni, j, X, Y);
@@ -425,6 +464,8 @@ struct Field {
   const Par<T>& P;
   const T* M;   // haloed metrics
   const T* Q;   // [4][nj][ni]
+  const Link* links = nullptr;        // 4 per block when some face is BC_LINK
+  const Field<T>* blocks = nullptr;   // every block of a multi-block grid
   size_t mplane() const { return (size_t)(P.ni + 2 * G) * (P.nj + 2 * G); }
   T met(int p, int i, int j) const {
     return M[p * mplane() + (size_t)(j + G) * (P.ni + 2 * G) + (i + G)];
@@ -447,6 +488,15 @@ struct Field {
     const int b = s < 0 ? 0 : n - 1;
     switch (P.bc[face]) {
       case BC_PERIODIC: { int ss = s - floordiv(s, n) * n; rd(ss, out); return; }
+      case BC_LINK: {   // the neighbour block's node behind the face
+        const Link& Lk = links[face];
+        const Field<T>& N = blocks[Lk.nbr];
+        const int gi = dir == 0 ? s : L, gj = dir == 0 ? L : s;
+        int oi, oj;
+        link_map(Lk, face, P.ni, P.nj, N.P.ni, N.P.nj, gi, gj, oi, oj);
+        for (int v = 0; v < 4; ++v) out[v] = N.q(v, oi, oj);
+        return;
+      }
       case BC_TRANSMISSIVE: rd(b, out); return;
       case BC_DIRICHLET: for (int v = 0; v < 4; ++v) out[v] = P.bcq[face][v]; return;
       case BC_SLIPWALL: {
@@ -595,8 +645,8 @@ static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
 
 // dQ/dt = -(dE^/dxi + dF^/deta) / J^-1 (Eq. 2.2 on a stationary grid).
 template <class T>
-static void rhs(const Par<T>& P, const T* M, const T* Q, T* dQ) {
-  Field<T> F{P, M, Q};
+static void rhs_field(const Field<T>& F, T* dQ) {
+  const Par<T>& P = F.P;
   const size_t N = (size_t)P.ni * P.nj;
   std::vector<T> R(4 * N, T(0));
   sweep(F, 0, R);
@@ -609,6 +659,12 @@ static void rhs(const Par<T>& P, const T* M, const T* Q, T* dQ) {
         dQ[o] = -R[o] / Jinv;
       }
     }
+}
+
+template <class T>
+static void rhs(const Par<T>& P, const T* M, const T* Q, T* dQ) {
+  Field<T> F{P, M, Q};
+  rhs_field(F, dQ);
 }
 
 // Third-order TVD Runge-Kutta (Section 6), Shu-Osher form.
@@ -784,6 +840,8 @@ static Coords<T> make_coords(const Par<T>& P, const double* period, const T* x, 
 
 static int check(const int* ip, int ni, int nj) {
   if (ni < 1 || nj < 1) return 1;
+  for (int f = 0; f < 4; ++f)
+    if (ip[4 + f] < 0 || ip[4 + f] > BC_FARFIELD) return 5;   // links need the multi-block entry
   if (ip[0] < 0 || ip[0] > 3) return 2;
   if ((ip[4] == BC_PERIODIC) != (ip[5] == BC_PERIODIC)) return 3;
   if ((ip[6] == BC_PERIODIC) != (ip[7] == BC_PERIODIC)) return 3;
@@ -819,6 +877,33 @@ static double fsp_residual(const int* ip, const double* dp, int ni, int nj, cons
   double worst = 0.0;
   for (size_t k = 0; k < 4 * N; ++k) worst = std::max(worst, std::fabs(val(R[k])));
   return worst;
+}
+}  // namespace orc
+
+namespace orc {
+// ----------------------------------------------------------------------------------
+// Multi-block grids: blocks joined by Link faces (see Link).  Arrays of all blocks are
+// concatenated in block order: coordinates ni*nj per block, metrics 5 (ni+8)(nj+8), state
+// 4 ni nj.  The line maxima of the splitting are taken per block line.
+// ----------------------------------------------------------------------------------
+template <class T>
+static int mb_setup(const int* ip, const double* dp, int nb, const int* dims, const int* bcs, const int* lk,
+                    const double* loff, std::vector<Par<T>>& P, std::vector<Link>& L) {
+  if (nb < 1) return 1;
+  P.resize(nb);
+  L.resize(4 * (size_t)nb);
+  for (int b = 0; b < nb; ++b) {
+    unpack(ip, dp, dims[2 * b], dims[2 * b + 1], P[b]);
+    for (int f = 0; f < 4; ++f) {
+      P[b].bc[f] = bcs[4 * b + f];
+      Link& l = L[4 * b + f];
+      l.nbr = lk[12 * b + 3 * f]; l.face = lk[12 * b + 3 * f + 1]; l.rev = lk[12 * b + 3 * f + 2];
+      l.off[0] = loff ? loff[8 * b + 2 * f] : 0.0; l.off[1] = loff ? loff[8 * b + 2 * f + 1] : 0.0;
+      if (P[b].bc[f] == BC_LINK && (l.nbr < 0 || l.nbr >= nb || l.face < 0 || l.face > 3)) return 6;
+    }
+    if (P[b].ni < 1 || P[b].nj < 1) return 1;
+  }
+  return 0;
 }
 }  // namespace orc
 
@@ -1009,4 +1094,90 @@ int orc_riemann_exact(double gamma, const double* WL, const double* WR, double x
   return 0;
 }
 
+
+// ---- multi-block entry points ----
+// dims: ni, nj per block; bcs: 4 codes per block (BC_LINK = 5 joins a face); lk: per
+// block and face (nbr, face, rev); loff: per block and face the ghost coordinate offset
+// (nullable); periods: per block the periodic vectors (dx_i, dy_i, dx_j, dy_j).
+int orc_mb_metrics(const int* ip, int nb, const int* dims, const int* bcs, const int* lk,
+                   const double* loff, const double* periods, const double* x, const double* y,
+                   double* M) {
+  std::vector<Par<double>> P;
+  std::vector<Link> L;
+  double dp[19] = {1.4, 1.1, 1e-40};
+  if (int e = mb_setup(ip, dp, nb, dims, bcs, lk, loff, P, L)) return e;
+  std::vector<Coords<double>> C(nb);
+  size_t xo = 0;
+  for (int b = 0; b < nb; ++b) {
+    C[b] = make_coords(P[b], periods + 4 * b, x + xo, y + xo);
+    C[b].links = &L[4 * (size_t)b];
+    C[b].blocks = C.data();
+    xo += (size_t)P[b].ni * P[b].nj;
+  }
+  size_t mo = 0;
+  for (int b = 0; b < nb; ++b) {
+    metrics(P[b], C[b], M + mo);
+    mo += orc_metrics_len(P[b].ni, P[b].nj);
+  }
+  return 0;
+}
+
+static void mb_fields(std::vector<Par<double>>& P, std::vector<Link>& L, const double* M, const double* Q,
+                      std::vector<Field<double>>& F) {
+  const int nb = (int)P.size();
+  F.clear();
+  F.reserve(nb);
+  size_t mo = 0, qo = 0;
+  for (int b = 0; b < nb; ++b) {
+    F.push_back(Field<double>{P[b], M + mo, Q + qo});
+    mo += orc_metrics_len(P[b].ni, P[b].nj);
+    qo += 4 * (size_t)P[b].ni * P[b].nj;
+  }
+  for (int b = 0; b < nb; ++b) { F[b].links = &L[4 * (size_t)b]; F[b].blocks = F.data(); }
+}
+
+int orc_mb_rhs(const int* ip, const double* dp, int nb, const int* dims, const int* bcs, const int* lk,
+               const double* M, const double* Q, double* dQ) {
+  std::vector<Par<double>> P;
+  std::vector<Link> L;
+  if (int e = mb_setup(ip, dp, nb, dims, bcs, lk, nullptr, P, L)) return e;
+  std::vector<Field<double>> F;
+  mb_fields(P, L, M, Q, F);
+  size_t qo = 0;
+  for (int b = 0; b < nb; ++b) {
+    rhs_field(F[b], dQ + qo);
+    qo += 4 * (size_t)P[b].ni * P[b].nj;
+  }
+  return 0;
+}
+
+// nsteps TVD-RK3 steps of every block in lockstep (all blocks finish a stage before the
+// next stage reads their ghosts); Q is updated in place.
+int orc_mb_rk3(const int* ip, const double* dp, int nb, const int* dims, const int* bcs, const int* lk,
+               const double* M, double* Q, double dt, int nsteps) {
+  std::vector<Par<double>> P;
+  std::vector<Link> L;
+  if (int e = mb_setup(ip, dp, nb, dims, bcs, lk, nullptr, P, L)) return e;
+  size_t NQ = 0;
+  for (int b = 0; b < nb; ++b) NQ += 4 * (size_t)P[b].ni * P[b].nj;
+  std::vector<double> Q1(NQ), Q2(NQ), R(NQ);
+  std::vector<Field<double>> F;
+  auto all_rhs = [&](const double* Qs) {
+    mb_fields(P, L, M, Qs, F);
+    size_t qo = 0;
+    for (int b = 0; b < nb; ++b) {
+      rhs_field(F[b], R.data() + qo);
+      qo += 4 * (size_t)P[b].ni * P[b].nj;
+    }
+  };
+  for (int st = 0; st < nsteps; ++st) {
+    all_rhs(Q);
+    for (size_t k = 0; k < NQ; ++k) Q1[k] = Q[k] + dt * R[k];
+    all_rhs(Q1.data());
+    for (size_t k = 0; k < NQ; ++k) Q2[k] = 0.75 * Q[k] + 0.25 * (Q1[k] + dt * R[k]);
+    all_rhs(Q2.data());
+    for (size_t k = 0; k < NQ; ++k) Q[k] = (1.0 / 3) * Q[k] + (2.0 / 3) * (Q2[k] + dt * R[k]);
+  }
+  return 0;
+}
 }  // extern "C"

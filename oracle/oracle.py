@@ -30,6 +30,7 @@ __all__ = [
     "build", "lib", "metrics", "metrics_jvp", "line_lambda", "rhs", "rhs_jvp", "rk3", "rk3_jvp",
     "cfl_dt", "count_flops", "count_flops_parts", "fsp_residual", "weno", "ppm", "smoothness", "eig",
     "scheme_table", "advect1d", "riemann_exact", "long_double_digits", "G",
+    "mb_metrics", "mb_rhs", "mb_rk3",
 ]
 
 G = 4
@@ -84,6 +85,10 @@ def lib():
                 "orc_riemann_exact": (ctypes.c_int, [ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_int, _D, _D]),
                 "orc_long_double_digits": (ctypes.c_int, []),
+                "orc_mb_metrics": (ctypes.c_int, [_I, ctypes.c_int, _I, _I, _I, _D, _D, _D, _D, _D]),
+                "orc_mb_rhs": (ctypes.c_int, [_I, _D, ctypes.c_int, _I, _I, _I, _D, _D, _D]),
+                "orc_mb_rk3": (ctypes.c_int, [_I, _D, ctypes.c_int, _I, _I, _I, _D, _D, ctypes.c_double,
+                                              ctypes.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -265,3 +270,76 @@ def riemann_exact(gamma, left, right, x0, t, x):
 
 def long_double_digits():
     return int(lib().orc_long_double_digits())
+
+
+# ---------------------------------------------------------------------------------------
+# Multi-block grids.  `blocks` is a list of dicts with keys x, y (nj, ni), bc (4 codes, 5 =
+# linked face), links (4 entries, each None or (nbr, face, reversed)), offsets (4 entries
+# (dx, dy) or None, added to ghost coordinates across the link), period (as for one block).
+# ---------------------------------------------------------------------------------------
+def _mb_tables(blocks):
+    nb = len(blocks)
+    dims = np.array([[b["x"].shape[1], b["x"].shape[0]] for b in blocks], dtype=np.int32).reshape(-1)
+    bcs = np.array([list(b["bc"]) for b in blocks], dtype=np.int32).reshape(-1)
+    lk = np.full((nb, 4, 3), -1, dtype=np.int32)
+    off = np.zeros((nb, 4, 2))
+    per = np.zeros((nb, 4))
+    for k, b in enumerate(blocks):
+        for f in range(4):
+            l = (b.get("links") or [None] * 4)[f]
+            if l is not None:
+                lk[k, f] = l
+            o = (b.get("offsets") or [None] * 4)[f]
+            if o is not None:
+                off[k, f] = o
+        per[k] = np.asarray(b.get("period", ((0.0, 0.0), (0.0, 0.0))), dtype=np.float64).reshape(4)
+    return nb, dims, bcs, lk.reshape(-1), off.reshape(-1), per.reshape(-1)
+
+
+def mb_metrics(cfg, blocks):
+    nb, dims, bcs, lk, off, per = _mb_tables(blocks)
+    ip, _, _ = _params(cfg)
+    x = np.concatenate([_f64(b["x"]).reshape(-1) for b in blocks])
+    y = np.concatenate([_f64(b["y"]).reshape(-1) for b in blocks])
+    sizes = [5 * (b["x"].shape[0] + 2 * G) * (b["x"].shape[1] + 2 * G) for b in blocks]
+    M = np.empty(sum(sizes))
+    _ck(lib().orc_mb_metrics(ip.ctypes.data_as(_I), nb, dims.ctypes.data_as(_I), bcs.ctypes.data_as(_I),
+                             lk.ctypes.data_as(_I), _dp(off), _dp(per), _dp(x), _dp(y), _dp(M)), "mb_metrics")
+    out, o = [], 0
+    for b, n in zip(blocks, sizes):
+        out.append(M[o:o + n].reshape(5, b["x"].shape[0] + 2 * G, b["x"].shape[1] + 2 * G))
+        o += n
+    return out
+
+
+def _mb_state(blocks, Qs):
+    return np.concatenate([_f64(q).reshape(-1) for q in Qs])
+
+
+def mb_rhs(cfg, blocks, Ms, Qs):
+    nb, dims, bcs, lk, _, _ = _mb_tables(blocks)
+    ip, dp, _ = _params(cfg)
+    M = np.concatenate([_f64(m).reshape(-1) for m in Ms])
+    Q = _mb_state(blocks, Qs)
+    R = np.empty_like(Q)
+    _ck(lib().orc_mb_rhs(ip.ctypes.data_as(_I), _dp(dp), nb, dims.ctypes.data_as(_I), bcs.ctypes.data_as(_I),
+                         lk.ctypes.data_as(_I), _dp(M), _dp(Q), _dp(R)), "mb_rhs")
+    out, o = [], 0
+    for q in Qs:
+        out.append(R[o:o + q.size].reshape(q.shape))
+        o += q.size
+    return out
+
+
+def mb_rk3(cfg, blocks, Ms, Qs, dt, nsteps=1):
+    nb, dims, bcs, lk, _, _ = _mb_tables(blocks)
+    ip, dp, _ = _params(cfg)
+    M = np.concatenate([_f64(m).reshape(-1) for m in Ms])
+    Q = _mb_state(blocks, Qs).copy()
+    _ck(lib().orc_mb_rk3(ip.ctypes.data_as(_I), _dp(dp), nb, dims.ctypes.data_as(_I), bcs.ctypes.data_as(_I),
+                         lk.ctypes.data_as(_I), _dp(M), _dp(Q), float(dt), int(nsteps)), "mb_rk3")
+    out, o = [], 0
+    for q in Qs:
+        out.append(Q[o:o + q.size].reshape(q.shape))
+        o += q.size
+    return out

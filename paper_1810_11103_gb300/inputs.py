@@ -193,3 +193,103 @@ def random_state(shape, seed: int, rho=(0.8, 1.2), vel=(-0.3, 0.3), p=(0.8, 1.2)
     r = [uniform(seed, block + k, n, 0).reshape(nj, ni) for k in range(4)]
     return conservative(rho[0] + (rho[1] - rho[0]) * r[0], vel[0] + (vel[1] - vel[0]) * r[1],
                         vel[0] + (vel[1] - vel[0]) * r[2], p[0] + (p[1] - p[0]) * r[3], gamma)
+
+
+# ----------------------------------------------------------------------------------------
+# Multi-block grids
+# ----------------------------------------------------------------------------------------
+LINK = 5
+
+
+def split_blocks(x, y, q, isplit, jsplit, bc_outer, period=None):
+    """Cut one (nj, ni) grid into blocks at the i indices `isplit` and j indices `jsplit`
+    (interior cut points).  Faces between blocks are linked; the outer faces keep
+    bc_outer (i-min, i-max, j-min, j-max), periodic outer faces becoming links that wrap
+    (with the period vector as the coordinate offset).  Returns (blocks, states)."""
+    nj, ni = x.shape
+    ic = [0] + list(isplit) + [ni]
+    jc = [0] + list(jsplit) + [nj]
+    na, nbk = len(ic) - 1, len(jc) - 1
+    per = period if period is not None else ((0.0, 0.0), (0.0, 0.0))
+    blocks, states = [], []
+    idx = lambda a, b: b * na + a
+    for b in range(nbk):
+        for a in range(na):
+            sl = (slice(jc[b], jc[b + 1]), slice(ic[a], ic[a + 1]))
+            bc, links, offs = [0] * 4, [None] * 4, [None] * 4
+            # i-min / i-max
+            for f, (da, outer) in enumerate(((-1, a == 0), (1, a == na - 1))):
+                if not outer:
+                    bc[f], links[f] = LINK, (idx(a + da, b), 1 - f, 0)
+                elif bc_outer[f] == 0:
+                    bc[f], links[f] = LINK, (idx((a + da) % na, b), 1 - f, 0)
+                    offs[f] = (da * per[0][0], da * per[0][1])
+                else:
+                    bc[f] = bc_outer[f]
+            for f, (db, outer) in ((2, (-1, b == 0)), (3, (1, b == nbk - 1))):
+                if not outer:
+                    bc[f], links[f] = LINK, (idx(a, b + db), 5 - f, 0)
+                elif bc_outer[f] == 0:
+                    bc[f], links[f] = LINK, (idx(a, (b + db) % nbk), 5 - f, 0)
+                    offs[f] = (db * per[1][0], db * per[1][1])
+                else:
+                    bc[f] = bc_outer[f]
+            blocks.append({"x": x[sl].copy(), "y": y[sl].copy(), "bc": bc, "links": links, "offsets": offs,
+                           "period": ((0.0, 0.0), (0.0, 0.0))})
+            states.append(None if q is None else q[(slice(None),) + sl].copy())
+    return blocks, states
+
+
+def cylinder_blocks(seed=1812, cols=8, rows=8, imin=64, imax=512, jmin=64, jmax=384, step=32,
+                    r_in=0.5, r_out=6.0, stretch=1.002, frac_random=0.3, amp=0.2, margin=4,
+                    mach=4.0, gamma: float = GAMMA):
+    """Body-fitted polar blocks around a cylinder of diameter one: `cols` angular columns of
+    I_a nodes and `rows` radial rows of J_b nodes (sizes drawn from the seed, multiples of
+    `step`), so blocks are uneven but shared faces match node for node.  Angle runs
+    clockwise so the grid is right-handed; radius is geometrically stretched from r_in to
+    r_out.  A seeded `frac_random` of the blocks is randomised with amplitude `amp` away
+    from a `margin`-node frame.  Faces: slip wall at r_in, far field at r_out (free stream
+    Mach `mach` along +x), links elsewhere (the angular direction wraps).
+    Returns (blocks, states, free_state)."""
+    rng_i = uniform(seed, 900, cols, 0)
+    rng_j = uniform(seed, 901, rows, 0)
+    I = [imin + step * int(r * ((imax - imin) // step + 1)) for r in rng_i]
+    J = [jmin + step * int(r * ((jmax - jmin) // step + 1)) for r in rng_j]
+    nth, nr = sum(I), sum(J)
+    th = 2.0 * math.pi * np.arange(nth) / nth
+    m = np.arange(nr, dtype=np.float64)
+    rr = r_in + (r_out - r_in) * (stretch ** m - 1.0) / (stretch ** (nr - 1) - 1.0)
+    TH, RR = np.meshgrid(th, rr)
+    x = RR * np.cos(TH)
+    y = -RR * np.sin(TH)
+    free = conservative(1.0, mach, 0.0, 1.0 / gamma, gamma)
+    q = np.broadcast_to(free[:, None, None], (4, nr, nth)).copy()
+    blocks, states = split_blocks(x, y, q, np.cumsum(I)[:-1], np.cumsum(J)[:-1],
+                                  (0, 0, BC_WALL, BC_FAR))
+    pick = uniform(seed, 902, len(blocks), 0) < frac_random
+    for k, b in enumerate(blocks):
+        b["bc_state"] = [list(free)] * 4
+        if pick[k]:
+            nj, ni = b["x"].shape
+            A = np.zeros((nj, ni))
+            A[margin:nj - margin, margin:ni - margin] = amp
+            b["x"], b["y"] = randomize_local(b["x"], b["y"], A, seed, block=1000 + k)
+    return blocks, states, free
+
+
+BC_WALL, BC_FAR = 3, 4
+
+
+def randomize_local(x, y, amp, seed, block=0):
+    """Section 6.1 (1) randomisation on a curved block: each node moves by 2A (r - 1/2)
+    times the local spacing along one grid direction (a coin picks which)."""
+    nj, ni = x.shape
+    n = ni * nj
+    r1 = uniform(seed, block, n, 0).reshape(nj, ni)
+    r2 = uniform(seed, block, n, 1).reshape(nj, ni)
+    b = coin(seed, block, n).reshape(nj, ni)
+    dxi = (np.gradient(x, axis=1), np.gradient(y, axis=1))
+    deta = (np.gradient(x, axis=0), np.gradient(y, axis=0))
+    s1 = 2.0 * amp * (r1 - 0.5) * b
+    s2 = 2.0 * amp * (r2 - 0.5) * (1.0 - b)
+    return x + s1 * dxi[0] + s2 * deta[0], y + s1 * dxi[1] + s2 * deta[1]
