@@ -72,7 +72,7 @@ enum { FSP_WENOIU3_1MP = 0, FSP_WENOIU3_2MP = 1, FSP_WENOIU5_1MP = 2, FSP_WENOIU
  *                 free-stream residual stays at FP64 round-off.  State arrays are float. */
 enum { FSP_FP64 = 0, FSP_FP32 = 1, FSP_FP32_MIXED = 2 };
 enum { FSP_BC_PERIODIC = 0, FSP_BC_TRANSMISSIVE = 1, FSP_BC_DIRICHLET = 2, FSP_BC_SLIPWALL = 3,
-       FSP_BC_FARFIELD = 4 };
+       FSP_BC_FARFIELD = 4, FSP_BC_LINK = 5 /* multi-block only: see fsp_batch_create */ };
 
 typedef struct {
   int scheme;          /* FSP_WENOIU*                                                   */
@@ -213,6 +213,54 @@ fsp_status fsp_norms(const fsp_block* blk, int precision, const void* A, const v
  * 2 * 8 * iters * blocks * 256.  Used to measure the ALU roof; no counterpart in the paper.
  */
 fsp_status fsp_fma_peak(int precision, int blocks, int iters, void* sink, void* stream);
+
+/*
+ * ---- Multi-block grids --------------------------------------------------------------
+ * The paper's motivating case (Section 1): many structured blocks, of uneven sizes,
+ * joined face to face.  The blocks partition the nodes of one larger grid: behind a face
+ * of kind FSP_BC_LINK lie the linked block's own nodes, the ghost at depth k (k = 0 the
+ * first) being the neighbour's node at depth k inward from its linked face, with the
+ * index along the face running the same way or reversed.  Linked faces must match node
+ * for node, and the neighbour must have at least 4 nodes across the face (state ghosts);
+ * ghost coordinates follow links, periodic wraps or odd reflection through up to eight
+ * layers, corners included.  Line maxima of the splitting are taken per block line.
+ * The handle owns its device memory (descriptors, tile tables, per-block line maxima,
+ * xi accumulators and RK stage states) from create to destroy; no other call allocates.
+ * Each pass runs all blocks in one launch over a table of tiles (NL lines x T nodes, as
+ * for one block); ghosts of linked faces are read straight from the neighbour's state,
+ * so no halo copies are made.  Calls on one handle must not overlap.
+ */
+typedef struct {
+  int nbr;            /* linked block (FSP_BC_LINK faces only)                         */
+  int face;           /* its face, 0..3 (i-min, i-max, j-min, j-max)                   */
+  int reversed;       /* 1: the index along the face runs the other way                */
+  double offset[2];   /* added to coordinates across the link (periodic wraps)         */
+} fsp_link;
+
+typedef struct fsp_batch fsp_batch;
+
+/* nblocks blocks (blocks[b].period used by their FSP_BC_PERIODIC faces), 4 face codes per
+ * block in bc, 4 links per block in links (read for FSP_BC_LINK faces).  Shared settings
+ * (scheme, precision, gamma, bc_state, ...) come from cfg.  *out receives the handle. */
+fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block* blocks, const int* bc,
+                            const fsp_link* links, fsp_batch** out);
+/* Host arrays of nblocks device pointers: coordinates (nj*ni doubles), metrics
+ * (fsp_metrics_elems doubles, written by fsp_batch_metrics) and the state of each block
+ * (updated in place by fsp_batch_rk3_step).  Rebinding drops a captured graph. */
+fsp_status fsp_batch_bind(fsp_batch* b, const double* const* x, const double* const* y,
+                          double* const* metrics, void* const* Q);
+/* fsp_metrics for every block, ghost coordinates through the links. */
+fsp_status fsp_batch_metrics(fsp_batch* b, void* stream);
+/* dQ/dt of every block (host array of device pointers, state layout). */
+fsp_status fsp_batch_rhs(fsp_batch* b, void* const* dQdt, void* stream);
+/* One TVD-RK3 step of every block in lockstep; launches the captured graph when one was
+ * captured for this dt. */
+fsp_status fsp_batch_rk3_step(fsp_batch* b, double dt, void* stream);
+/* Runs one step, then records one RK3 step (9 kernels, 3 memsets) as a CUDA graph that
+ * later fsp_batch_rk3_step calls with the same dt launch as a whole.  The eager step
+ * advances the state like any other step. */
+fsp_status fsp_batch_capture_graph(fsp_batch* b, double dt, void* stream);
+fsp_status fsp_batch_destroy(fsp_batch* b);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,467 @@
+// batch.cu -- many structured blocks joined by linked faces, advanced together.
+//
+// A multi-block grid (the paper's motivating case, Section 1) is a set of blocks whose
+// faces are either physical boundaries or links to a face of another block.  The blocks
+// partition the nodes of one larger grid: the ghosts behind a linked face are the
+// neighbour's own nodes, read directly from the neighbour's state by the tile loaders, so
+// the halo exchange is fused into the sweeps and needs no copies and no waits (each launch
+// boundary orders the RK stages).  Each pass is one launch over a tile table that spans
+// every block; the hardware CTA scheduler hands tiles to SMs as slots free up, which
+// balances the uneven blocks.  The whole RK3 step can be captured once as a CUDA graph.
+// Line maxima of the splitting are taken per block line.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fsp_internal.h"
+#include "sweep.cuh"
+
+namespace fsp {
+
+// ---- metrics with linked faces -------------------------------------------------------
+struct CoordBlock {
+  int ni, nj, bc[4], lnb[4], lface[4], lrev[4];
+  double loff[4][2];
+  double per[2][2];
+  const double* x;
+  const double* y;
+};
+
+// Coordinates of node (i, j) of block b, any (i, j) within eight layers of the block:
+// ghost indices are resolved face by face (j first, then i) through links (the
+// neighbour's node plus the link's offset), periodic wraps (plus the period vector) or
+// odd reflection about the boundary node (a weighted pair of nodes).
+__device__ void coord_mb(const CoordBlock* __restrict__ B, int b, int i, int j, double& X, double& Y) {
+  struct Item { double w; int b, i, j; };
+  Item st[16];
+  int n = 1;
+  st[0] = {1.0, b, i, j};
+  X = 0.0;
+  Y = 0.0;
+  for (int guard = 0; n > 0 && guard < 64; ++guard) {
+    const Item it = st[--n];
+    const CoordBlock& C = B[it.b];
+    const bool jout = it.j < 0 || it.j >= C.nj, iout = it.i < 0 || it.i >= C.ni;
+    if (!jout && !iout) {
+      const long long o = (long long)it.j * C.ni + it.i;
+      X += it.w * __ldg(C.x + o);
+      Y += it.w * __ldg(C.y + o);
+      continue;
+    }
+    if (n > 13) break;  // cannot happen for blocks of at least 9 nodes; keeps the stack in bounds
+    const int dirj = jout ? 1 : 0;
+    const int f = jout ? (it.j < 0 ? 2 : 3) : (it.i < 0 ? 0 : 1);
+    const int kind = C.bc[f];
+    if (kind == BC_LINK) {
+      int oi, oj;
+      const CoordBlock& N = B[C.lnb[f]];
+      link_node(f, C.ni, C.nj, C.lface[f], C.lrev[f], N.ni, N.nj, it.i, it.j, oi, oj);
+      X += it.w * C.loff[f][0];
+      Y += it.w * C.loff[f][1];
+      st[n++] = {it.w, C.lnb[f], oi, oj};
+    } else if (kind == BC_PERIODIC) {
+      const int len = dirj ? C.nj : C.ni, a = dirj ? it.j : it.i;
+      const int m = pmod(a, len), q = (a - m) / len;
+      X += it.w * q * C.per[dirj][0];
+      Y += it.w * q * C.per[dirj][1];
+      st[n++] = dirj ? Item{it.w, it.b, it.i, m} : Item{it.w, it.b, m, it.j};
+    } else {
+      const int len = dirj ? C.nj : C.ni, a = dirj ? it.j : it.i;
+      const int bd = a < 0 ? 0 : len - 1;
+      st[n++] = dirj ? Item{2.0 * it.w, it.b, it.i, bd} : Item{2.0 * it.w, it.b, bd, it.j};
+      st[n++] = dirj ? Item{-it.w, it.b, it.i, 2 * bd - a} : Item{-it.w, it.b, 2 * bd - a, it.j};
+    }
+  }
+}
+
+__device__ __forceinline__ double central_diff9(const Central& c, int interp, bool sixth, const double* f) {
+  double d = c.a1 * (f[5] - f[3]) + c.a2 * (f[6] - f[2]) + c.a3 * (f[7] - f[1]);
+  d += c.b12 * (mid_interp(interp, sixth, f + 2) - mid_interp(interp, sixth, f + 1));
+  if (c.b32 != 0.0) d += c.b32 * (mid_interp(interp, sixth, f + 3) - mid_interp(interp, sixth, f + 0));
+  return d;
+}
+
+__global__ void metrics_mb_kernel(const CoordBlock* __restrict__ B, int b, Central cen, int interp, int sixth,
+                                  double* __restrict__ M) {
+  const int ni = B[b].ni, nj = B[b].nj;
+  const int W = ni + 2 * G, H = nj + 2 * G;
+  const long long plane = (long long)W * H;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % W) - G, j = (int)(t / W) - G;
+    double fx[9], fy[9], gx[9], gy[9];
+    for (int k = 0; k < 9; ++k) {
+      coord_mb(B, b, i + k - 4, j, fx[k], fy[k]);
+      coord_mb(B, b, i, j + k - 4, gx[k], gy[k]);
+    }
+    const double x_xi = central_diff9(cen, interp, sixth, fx), y_xi = central_diff9(cen, interp, sixth, fy);
+    const double x_eta = central_diff9(cen, interp, sixth, gx), y_eta = central_diff9(cen, interp, sixth, gy);
+    M[0 * plane + t] = y_eta;
+    M[1 * plane + t] = -x_eta;
+    M[2 * plane + t] = -y_xi;
+    M[3 * plane + t] = x_xi;
+    M[4 * plane + t] = x_xi * y_eta - x_eta * y_xi;
+  }
+}
+
+// ---- line maxima of every block in one launch ------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(256) lambda_batch_kernel(const Params* __restrict__ Ps,
+                                                           const TileRef* __restrict__ tiles,
+                                                           const Real* const* q, double* const* lamx,
+                                                           double* const* lame) {
+  __shared__ double col[8][33];
+  const TileRef t = tiles[blockIdx.x];
+  const Params& P = Ps[t.block];
+  const Real* Q = q[t.block];
+  const int ni = P.ni, nj = P.nj;
+  const int i = t.bx * 32 + threadIdx.x, j = t.by * 8 + threadIdx.y;
+  double sx = 0.0, se = 0.0;
+  if (i < ni && j < nj) {
+    const long long plane = (long long)nj * P.ld, o = (long long)j * P.ld + i;
+    double qq[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qq[v] = (double)Q[v * plane + o];
+    sx = spectral_radius(qq, met_at(P, 0, i, j), met_at(P, 1, i, j), P.gamma);
+    se = spectral_radius(qq, met_at(P, 2, i, j), met_at(P, 3, i, j), P.gamma);
+  }
+  double rx = sx;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) rx = fmax(rx, __shfl_xor_sync(0xffffffffu, rx, off));
+  if (threadIdx.x == 0 && j < nj)
+    atomicMax(reinterpret_cast<unsigned long long*>(lamx[t.block] + j), (unsigned long long)__double_as_longlong(rx));
+  col[threadIdx.y][threadIdx.x] = se;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < ni) {
+    double m = col[0][threadIdx.x];
+#pragma unroll
+    for (int r = 1; r < 8; ++r) m = fmax(m, col[r][threadIdx.x]);
+    atomicMax(reinterpret_cast<unsigned long long*>(lame[t.block] + i), (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+}  // namespace fsp
+
+using namespace fsp;
+
+// ---- the handle ----------------------------------------------------------------------
+struct fsp_batch {
+  fsp_config cfg;
+  int nb = 0;
+  int device = 0;
+  std::vector<fsp_block> blk;
+  std::vector<int> bc;               // 4 per block
+  std::vector<fsp_link> links;       // 4 per block
+  std::vector<Params> params;        // host copy
+  std::vector<CoordBlock> coords;    // host copy
+  std::vector<TileRef> tx, te, tl;   // xi, eta and line-maxima tiles
+  // device memory (one allocation)
+  char* dmem = nullptr;
+  Params* d_params = nullptr;
+  CoordBlock* d_coords = nullptr;
+  TileRef *d_tx = nullptr, *d_te = nullptr, *d_tl = nullptr;
+  double* d_lam = nullptr;
+  size_t lam_count = 0;
+  std::vector<size_t> lam_off, acc_off, st_off;
+  char* d_acc = nullptr;             // xi differences, one per block
+  char* d_q1 = nullptr;              // RK stage states
+  char* d_q2 = nullptr;
+  void** d_tab = nullptr;            // pointer tables, nb entries each (see Tab)
+  bool bound = false;
+  std::vector<double*> M;
+  cudaGraphExec_t gexec = nullptr;
+  double gdt = 0.0;
+};
+
+namespace {
+
+// pointer tables inside d_tab
+enum Tab { T_Q0 = 0, T_Q1, T_Q2, T_ACC, T_LX, T_LE, T_OUT, T_COUNT };
+
+size_t al(size_t b) { return (b + 255) / 256 * 256; }
+
+bool dev_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t state_size(int prec) { return prec == FSP_FP64 ? 8 : 4; }
+size_t acc_elem(int prec) { return prec == FSP_FP32 ? 4 : 8; }
+
+fsp_status check_batch(const fsp_config* c, int nb, const fsp_block* blk, const int* bc, const fsp_link* lk) {
+  if (!c || nb < 1 || !blk || !bc || !lk) return FSP_ERR_INVALID_ARG;
+  if (c->scheme < 0 || c->scheme > 3 || c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED ||
+      c->interp < 0 || c->interp > 1 || !(c->gamma > 1.0) || !(c->lf_alpha > 0.0) || !(c->eps > 0.0))
+    return FSP_ERR_INVALID_ARG;
+  for (int b = 0; b < nb; ++b) {
+    const fsp_block& B = blk[b];
+    if (B.ni < 1 || B.nj < 1 || B.ld < B.ni || B.ni > 8 * 65535 || B.nj > 2 * 65535) return FSP_ERR_INVALID_ARG;
+    for (int f = 0; f < 4; ++f) {
+      const int k = bc[4 * b + f];
+      if (k < FSP_BC_PERIODIC || k > FSP_BC_LINK) return FSP_ERR_INVALID_ARG;
+      const int along = f < 2 ? B.ni : B.nj, across = f < 2 ? B.nj : B.ni;
+      if (k == FSP_BC_LINK) {
+        const fsp_link& L = lk[4 * b + f];
+        if (L.nbr < 0 || L.nbr >= nb || L.face < 0 || L.face > 3) return FSP_ERR_INVALID_ARG;
+        const fsp_block& N = blk[L.nbr];
+        // the faces must match node for node, and the neighbour must hold 4 ghost layers
+        if ((L.face < 2 ? N.nj : N.ni) != across) return FSP_ERR_INVALID_ARG;
+        if ((L.face < 2 ? N.ni : N.nj) < 4) return FSP_ERR_INVALID_ARG;
+      } else if (k != FSP_BC_PERIODIC && along < 9) {
+        return FSP_ERR_INVALID_ARG;
+      }
+    }
+    if ((bc[4 * b] == FSP_BC_PERIODIC) != (bc[4 * b + 1] == FSP_BC_PERIODIC)) return FSP_ERR_INVALID_ARG;
+    if ((bc[4 * b + 2] == FSP_BC_PERIODIC) != (bc[4 * b + 3] == FSP_BC_PERIODIC)) return FSP_ERR_INVALID_ARG;
+  }
+  return FSP_OK;
+}
+
+template <typename T>
+T* carve(char*& cur, size_t count) {
+  T* p = reinterpret_cast<T*>(cur);
+  cur += al(count * sizeof(T));
+  return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block* blocks, const int* bc,
+                            const fsp_link* links, fsp_batch** out) {
+  if (!out) return FSP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (fsp_status s = check_batch(cfg, nblocks, blocks, bc, links)) return s;
+  fsp_batch* h = new (std::nothrow) fsp_batch();
+  if (!h) return FSP_ERR_NOMEM;
+  h->cfg = *cfg;
+  h->nb = nblocks;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return FSP_ERR_CUDA; }
+  h->blk.assign(blocks, blocks + nblocks);
+  h->bc.assign(bc, bc + 4 * nblocks);
+  h->links.assign(links, links + 4 * nblocks);
+  // host descriptors
+  h->params.resize(nblocks);
+  h->coords.resize(nblocks);
+  size_t lam = 0, acc = 0, st = 0;
+  int Tx, NLx, Te, NLe;
+  tile_dims(cfg->scheme, 0, Tx, NLx);
+  tile_dims(cfg->scheme, 1, Te, NLe);
+  for (int b = 0; b < nblocks; ++b) {
+    const fsp_block& B = blocks[b];
+    Params& P = h->params[b];
+    std::memset(&P, 0, sizeof(P));
+    P.ni = B.ni; P.nj = B.nj; P.ld = B.ld;
+    P.interp = cfg->interp; P.ppm = cfg->ppm; P.linw = cfg->linear_weights;
+    P.gamma = cfg->gamma; P.alpha = cfg->lf_alpha; P.eps = cfg->eps;
+    for (int f = 0; f < 4; ++f) {
+      P.bc[f] = bc[4 * b + f];
+      for (int v = 0; v < 4; ++v) P.bcq[f][v] = cfg->bc_state[f][v];
+      const fsp_link& L = links[4 * b + f];
+      if (P.bc[f] == FSP_BC_LINK) {
+        const fsp_block& N = blocks[L.nbr];
+        P.lnb[f] = L.nbr; P.lface[f] = L.face; P.lrev[f] = L.reversed ? 1 : 0;
+        P.lni[f] = N.ni; P.lnj[f] = N.nj; P.lld[f] = N.ld;
+      }
+    }
+    P.mld = (long long)B.ni + 2 * G;
+    P.mplane = P.mld * ((long long)B.nj + 2 * G);
+    CoordBlock& C = h->coords[b];
+    std::memset(&C, 0, sizeof(C));
+    C.ni = B.ni; C.nj = B.nj;
+    for (int f = 0; f < 4; ++f) {
+      C.bc[f] = P.bc[f]; C.lnb[f] = P.lnb[f]; C.lface[f] = P.lface[f]; C.lrev[f] = P.lrev[f];
+      C.loff[f][0] = links[4 * b + f].offset[0]; C.loff[f][1] = links[4 * b + f].offset[1];
+    }
+    for (int a = 0; a < 2; ++a)
+      for (int k = 0; k < 2; ++k) C.per[a][k] = B.period[a][k];
+    h->lam_off.push_back(lam);
+    lam += (size_t)B.ni + B.nj;
+    h->acc_off.push_back(acc);
+    acc += al(4 * (size_t)B.nj * B.ld * acc_elem(cfg->precision));
+    h->st_off.push_back(st);
+    st += al(4 * (size_t)B.nj * B.ld * state_size(cfg->precision));
+    for (int by = 0; by < (B.nj + NLx - 1) / NLx; ++by)
+      for (int bx = 0; bx < (B.ni + Tx - 1) / Tx; ++bx) h->tx.push_back({b, bx, by});
+    for (int by = 0; by < (B.ni + NLe - 1) / NLe; ++by)
+      for (int bx = 0; bx < (B.nj + Te - 1) / Te; ++bx) h->te.push_back({b, bx, by});
+    for (int by = 0; by < (B.nj + 7) / 8; ++by)
+      for (int bx = 0; bx < (B.ni + 31) / 32; ++bx) h->tl.push_back({b, bx, by});
+  }
+  h->lam_count = lam;
+  const size_t bytes = al(sizeof(Params) * nblocks) + al(sizeof(CoordBlock) * nblocks) +
+                       al(sizeof(TileRef) * h->tx.size()) + al(sizeof(TileRef) * h->te.size()) +
+                       al(sizeof(TileRef) * h->tl.size()) + al(sizeof(double) * lam) + acc + 2 * st +
+                       al(sizeof(void*) * T_COUNT * nblocks);
+  if (cudaMalloc(&h->dmem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return FSP_ERR_NOMEM;
+  }
+  char* cur = h->dmem;
+  h->d_params = carve<Params>(cur, nblocks);
+  h->d_coords = carve<CoordBlock>(cur, nblocks);
+  h->d_tx = carve<TileRef>(cur, h->tx.size());
+  h->d_te = carve<TileRef>(cur, h->te.size());
+  h->d_tl = carve<TileRef>(cur, h->tl.size());
+  h->d_lam = carve<double>(cur, lam);
+  h->d_acc = cur; cur += acc;
+  h->d_q1 = cur; cur += st;
+  h->d_q2 = cur; cur += st;
+  h->d_tab = reinterpret_cast<void**>(cur);
+  bool ok = cudaMemcpy(h->d_params, h->params.data(), sizeof(Params) * nblocks, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(h->d_tx, h->tx.data(), sizeof(TileRef) * h->tx.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(h->d_te, h->te.data(), sizeof(TileRef) * h->te.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(h->d_tl, h->tl.data(), sizeof(TileRef) * h->tl.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) { fsp_batch_destroy(h); return FSP_ERR_CUDA; }
+  *out = h;
+  return FSP_OK;
+}
+
+fsp_status fsp_batch_bind(fsp_batch* h, const double* const* x, const double* const* y, double* const* metrics,
+                          void* const* Q) {
+  if (!h || !x || !y || !metrics || !Q) return FSP_ERR_INVALID_ARG;
+  for (int b = 0; b < h->nb; ++b)
+    if (!dev_ptr(x[b]) || !dev_ptr(y[b]) || !dev_ptr(metrics[b]) || !dev_ptr(Q[b])) return FSP_ERR_INVALID_ARG;
+  const int nb = h->nb;
+  std::vector<void*> tab((size_t)T_COUNT * nb, nullptr);
+  h->M.assign(metrics, metrics + nb);
+  for (int b = 0; b < nb; ++b) {
+    h->params[b].met = metrics[b];
+    h->coords[b].x = x[b];
+    h->coords[b].y = y[b];
+    tab[T_Q0 * nb + b] = Q[b];
+    tab[T_Q1 * nb + b] = h->d_q1 + h->st_off[b];
+    tab[T_Q2 * nb + b] = h->d_q2 + h->st_off[b];
+    tab[T_ACC * nb + b] = h->d_acc + h->acc_off[b];
+    tab[T_LX * nb + b] = h->d_lam + h->lam_off[b];
+    tab[T_LE * nb + b] = h->d_lam + h->lam_off[b] + h->blk[b].nj;
+  }
+  if (cudaMemcpy(h->d_params, h->params.data(), sizeof(Params) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->d_coords, h->coords.data(), sizeof(CoordBlock) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->d_tab, tab.data(), sizeof(void*) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return FSP_ERR_CUDA;
+  h->bound = true;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return FSP_OK;
+}
+
+fsp_status fsp_batch_metrics(fsp_batch* h, void* stream) {
+  if (!h || !h->bound) return FSP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Central cen = central_of(h->cfg.scheme);
+  for (int b = 0; b < h->nb; ++b) {
+    const long long n = (long long)(h->blk[b].ni + 2 * G) * (h->blk[b].nj + 2 * G);
+    const long long want = (n + 255) / 256;
+    metrics_mb_kernel<<<(int)(want < 152 * 8 ? want : 152 * 8), 256, 0, st>>>(
+        h->d_coords, b, cen, h->cfg.interp, h->cfg.scheme >= S51 ? 1 : 0, h->M[b]);
+    if (cudaGetLastError() != cudaSuccess) return FSP_ERR_CUDA;
+  }
+  return FSP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// one right-hand side of every block; input table `in`, output table `out`; mode 0:
+// dQ/dt, mode 1: RK stage out = ca Q0 + cb (in + dt dQ/dt)
+fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, double cb, double dt, cudaStream_t st) {
+  const int nb = h->nb;
+  void** T = h->d_tab;
+  if (cudaMemsetAsync(h->d_lam, 0, sizeof(double) * h->lam_count, st) != cudaSuccess) return FSP_ERR_CUDA;
+  dim3 blk(32, 8);
+  if (h->cfg.precision == FSP_FP64)
+    lambda_batch_kernel<double><<<(unsigned)h->tl.size(), blk, 0, st>>>(
+        h->d_params, h->d_tl, reinterpret_cast<const double* const*>(T + in * nb),
+        reinterpret_cast<double* const*>(T + T_LX * nb), reinterpret_cast<double* const*>(T + T_LE * nb));
+  else
+    lambda_batch_kernel<float><<<(unsigned)h->tl.size(), blk, 0, st>>>(
+        h->d_params, h->d_tl, reinterpret_cast<const float* const*>(T + in * nb),
+        reinterpret_cast<double* const*>(T + T_LX * nb), reinterpret_cast<double* const*>(T + T_LE * nb));
+  if (cudaGetLastError() != cudaSuccess) return FSP_ERR_CUDA;
+  const PassTables xi{h->d_params, h->d_tx, T + in * nb, T + T_LX * nb, nullptr, T + T_ACC * nb, nullptr,
+                      nullptr};
+  const PassTables eta{h->d_params, h->d_te, T + in * nb, T + T_LE * nb, T + T_ACC * nb, nullptr, T + out * nb,
+                       T + T_Q0 * nb};
+  const int ntx = (int)h->tx.size(), nte = (int)h->te.size();
+  cudaError_t e = h->cfg.precision == FSP_FP64
+                      ? batch_fp64(h->cfg.scheme, mode, xi, ntx, eta, nte, ca, cb, dt, st)
+                      : batch_fp32(h->cfg.scheme, h->cfg.precision == FSP_FP32_MIXED, mode, xi, ntx, eta, nte, ca,
+                                   cb, dt, st);
+  return e == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
+}
+
+fsp_status batch_rk3(fsp_batch* h, double dt, cudaStream_t st) {
+  if (fsp_status s = batch_stage(h, T_Q0, T_Q1, 1, 0.0, 1.0, dt, st)) return s;
+  if (fsp_status s = batch_stage(h, T_Q1, T_Q2, 1, 0.75, 0.25, dt, st)) return s;
+  return batch_stage(h, T_Q2, T_Q0, 1, 1.0 / 3.0, 2.0 / 3.0, dt, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+fsp_status fsp_batch_rhs(fsp_batch* h, void* const* dQdt, void* stream) {
+  if (!h || !h->bound || !dQdt) return FSP_ERR_INVALID_ARG;
+  for (int b = 0; b < h->nb; ++b)
+    if (!dev_ptr(dQdt[b])) return FSP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the output table is copied from pageable memory: the call returns once it is staged
+  if (cudaMemcpyAsync(h->d_tab + T_OUT * h->nb, dQdt, sizeof(void*) * h->nb, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return FSP_ERR_CUDA;
+  return batch_stage(h, T_Q0, T_OUT, 0, 0.0, 0.0, 0.0, st);
+}
+
+fsp_status fsp_batch_rk3_step(fsp_batch* h, double dt, void* stream) {
+  if (!h || !h->bound) return FSP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->gexec && dt == h->gdt) return cudaGraphLaunch(h->gexec, st) == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
+  return batch_rk3(h, dt, st);
+}
+
+fsp_status fsp_batch_capture_graph(fsp_batch* h, double dt, void* stream) {
+  if (!h || !h->bound) return FSP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  // one eager step on the caller's stream: kernel attributes are set and modules loaded
+  // outside the capture
+  if (fsp_status s = batch_rk3(h, dt, st)) return s;
+  // record on a private stream (the legacy default stream cannot be captured); nothing
+  // runs during the recording, and the graph is later launched on the caller's stream
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return FSP_ERR_CUDA;
+  cudaGraph_t g = nullptr;
+  fsp_status s = FSP_ERR_CUDA;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    s = batch_rk3(h, dt, cs);
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess) s = FSP_ERR_CUDA;
+  }
+  cudaStreamDestroy(cs);
+  if (s == FSP_OK && g && cudaGraphInstantiate(&h->gexec, g, 0) == cudaSuccess) {
+    h->gdt = dt;
+  } else {
+    h->gexec = nullptr;
+    if (s == FSP_OK) s = FSP_ERR_CUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return s;
+}
+
+fsp_status fsp_batch_destroy(fsp_batch* h) {
+  if (!h) return FSP_OK;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->dmem) cudaFree(h->dmem);
+  delete h;
+  return FSP_OK;
+}
+
+}  // extern "C"

@@ -11,7 +11,8 @@ namespace fsp {
 constexpr int G = 4;  // ghost layers of the stored metrics
 
 enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, BC_FARFIELD = 4 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, BC_FARFIELD = 4,
+       BC_LINK = 5 };
 
 // --------------------------------------------------------------------------------------
 // Scheme coefficients (Section 3)
@@ -86,7 +87,24 @@ struct Params {
   const double* met;        // haloed metrics
   long long mld;            // ni + 2G
   long long mplane;         // (ni + 2G) (nj + 2G)
+  // linked faces (multi-block): neighbour block, its face, reversed tangential index,
+  // and the neighbour's extents; the neighbour's state comes from a per-block table
+  int lnb[4], lface[4], lrev[4], lni[4], lnj[4];
+  long long lld[4];
 };
+
+// Node of the neighbour behind linked face f for the ghost (gi, gj) of a block of size
+// ni x nj: the blocks partition one larger grid, so the ghost at depth k beyond face f is
+// the neighbour's node at depth k inward from its face, with the index along the face
+// running the same way or reversed.
+__host__ __device__ __forceinline__ void link_node(int f, int ni, int nj, int nface, int nrev, int nni,
+                                                   int nnj, int gi, int gj, int& oi, int& oj) {
+  const int k = f == 0 ? -1 - gi : f == 1 ? gi - ni : f == 2 ? -1 - gj : gj - nj;
+  int t = f < 2 ? gj : gi;
+  if (nrev) t = (nface < 2 ? nnj : nni) - 1 - t;
+  const int d = (nface == 0 || nface == 2) ? k : (nface == 1 ? nni - 1 - k : nnj - 1 - k);
+  if (nface < 2) { oi = d; oj = t; } else { oi = t; oj = d; }
+}
 
 __device__ __forceinline__ double met_at(const Params& P, int p, int i, int j) {
   return __ldg(P.met + p * P.mplane + (long long)(j + G) * P.mld + (i + G));
@@ -101,7 +119,8 @@ __device__ __forceinline__ int pmod(int a, int n) {
 // dir 1) at position g (any integer; interior when 0 <= g < n).
 template <typename Real>
 __device__ __forceinline__ void load_state(const Params& P, const Real* __restrict__ Q, int dir,
-                                           int line, int g, Real q[4]) {
+                                           int line, int g, Real q[4],
+                                           const Real* const* qtab = nullptr) {
   const int n = dir == 0 ? P.ni : P.nj;
   const long long plane = (long long)P.nj * P.ld;
   auto rd = [&](int gg) {
@@ -114,6 +133,16 @@ __device__ __forceinline__ void load_state(const Params& P, const Real* __restri
   const int b = g < 0 ? 0 : n - 1;
   const int kind = P.bc[face];
   if (kind == BC_PERIODIC) { rd(pmod(g, n)); return; }
+  if (kind == BC_LINK) {
+    int oi, oj;
+    link_node(face, P.ni, P.nj, P.lface[face], P.lrev[face], P.lni[face], P.lnj[face],
+              dir == 0 ? g : line, dir == 0 ? line : g, oi, oj);
+    const Real* N = qtab[P.lnb[face]];
+    const long long nplane = (long long)P.lnj[face] * P.lld[face], o = (long long)oj * P.lld[face] + oi;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) q[v] = N[v * nplane + o];
+    return;
+  }
   if (kind == BC_DIRICHLET) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[v] = Real(P.bcq[face][v]);

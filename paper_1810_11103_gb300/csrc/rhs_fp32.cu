@@ -49,4 +49,10 @@ cudaError_t flux_difference_fp32(int scheme, bool mixed, const Params& P, const 
                : fd_f32<float>(scheme, P, Q, lam, dir, mode, acc, out, st);
 }
 
+cudaError_t batch_fp32(int scheme, bool mixed, int mode, const PassTables& xi, int ntx, const PassTables& eta,
+                       int nte, double ca, double cb, double dt, cudaStream_t st) {
+  return mixed ? batch_dispatch<float, double>(scheme, mode, xi, ntx, eta, nte, ca, cb, dt, st)
+               : batch_dispatch<float, float>(scheme, mode, xi, ntx, eta, nte, ca, cb, dt, st);
+}
+
 }  // namespace fsp

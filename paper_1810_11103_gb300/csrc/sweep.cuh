@@ -40,11 +40,21 @@ struct TileShape {
   }
 };
 
+// Host view of the tile shape: output nodes per line T and lines per CTA NL.
+inline void tile_dims(int scheme, int dir, int& T, int& NL) {
+  const int nmp = (scheme == S32 || scheme == S52) ? 2 : 1;
+  NL = dir == 0 ? 2 : 8;
+  T = (dir == 0 ? 128 : 32) - nmp - 1;
+}
+
+// One tile (bx along the lines, by across them) of one block.  qtab: every block's state
+// for linked faces (null for a lone block).
 template <int S, int DIR, int MODE, typename Real, typename Acc>
-__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 3)
-sweep_kernel(Params P, const Real* __restrict__ Q, const double* __restrict__ lam,
-             const Acc* __restrict__ Dacc, Acc* __restrict__ Dout, Real* qout, const Real* Qn,
-             double ca, double cb, double dt) {
+__device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restrict__ Q,
+                                           const Real* const* qtab, const double* __restrict__ lam,
+                                           const Acc* __restrict__ Dacc, Acc* __restrict__ Dout,
+                                           Real* qout, const Real* Qn, double ca, double cb, double dt,
+                                           int bx, int by) {
   using Sh = TileShape<S, DIR, Real, Acc>;
   using Sc = Scheme<S>;
   constexpr int NL = Sh::NL, W = Sh::W, T = Sh::T, NP = Sh::NP, PLO = Sh::PLO;
@@ -60,8 +70,8 @@ sweep_kernel(Params P, const Real* __restrict__ Q, const double* __restrict__ la
 
   const int n = DIR == 0 ? P.ni : P.nj;
   const int nlines = DIR == 0 ? P.nj : P.ni;
-  const int line0 = blockIdx.y * NL;
-  const int base = blockIdx.x * T;
+  const int line0 = by * NL;
+  const int base = bx * T;
   const Real gamma = Real(P.gamma);
   const Real eps = sizeof(Real) == 8 ? Real(P.eps) : Real(fmax(P.eps, 1e-30));
   const long long plane = (long long)P.nj * P.ld;
@@ -81,7 +91,7 @@ sweep_kernel(Params P, const Real* __restrict__ Q, const double* __restrict__ la
     if (line >= nlines) continue;
     const int g = min(base + s - 4, n + 3);  // positions past n+3 are never used
     Real q[4];
-    load_state(P, Q, DIR, line, g, q);
+    load_state(P, Q, DIR, line, g, q, qtab);
     double mx, my;
     if (DIR == 0) { mx = met_at(P, 0, g, line); my = met_at(P, 1, g, line); }
     else          { mx = met_at(P, 2, line, g); my = met_at(P, 3, line, g); }
@@ -273,6 +283,84 @@ sweep_kernel(Params P, const Real* __restrict__ Q, const double* __restrict__ la
 }
 
 template <int S, int DIR, int MODE, typename Real, typename Acc>
+__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 3)
+sweep_kernel(Params P, const Real* __restrict__ Q, const double* __restrict__ lam,
+             const Acc* __restrict__ Dacc, Acc* __restrict__ Dout, Real* qout, const Real* Qn,
+             double ca, double cb, double dt) {
+  sweep_tile<S, DIR, MODE, Real, Acc>(P, Q, nullptr, lam, Dacc, Dout, qout, Qn, ca, cb, dt, blockIdx.x,
+                                      blockIdx.y);
+}
+
+// ---- many blocks in one launch: CTA b takes tile tiles[b] of block tiles[b].block ----
+struct TileRef { int block, bx, by; };
+
+template <typename Real, typename Acc>
+struct BatchPass {                 // device arrays indexed by block
+  const Params* params;
+  const TileRef* tiles;
+  const Real* const* q;            // state read by this pass (and by neighbours' ghosts)
+  const double* const* lam;        // line maxima of the pass's direction
+  const Acc* const* dacc;          // other direction's difference (modes 1, 2)
+  Acc* const* dout;                // this direction's difference (mode 0)
+  Real* const* qout;               // dQ/dt or the stage state (modes 1, 2)
+  const Real* const* qn;           // Q^n of the RK step (mode 2)
+};
+
+template <int S, int DIR, int MODE, typename Real, typename Acc>
+__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 3)
+sweep_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
+  __shared__ Params sp;
+  const TileRef t = B.tiles[blockIdx.x];
+  if (threadIdx.x == 0) sp = B.params[t.block];
+  __syncthreads();
+  const int b = t.block;
+  sweep_tile<S, DIR, MODE, Real, Acc>(sp, B.q[b], B.q, B.lam[b], MODE == MODE_ACC ? nullptr : B.dacc[b],
+                                      MODE == MODE_ACC ? B.dout[b] : nullptr,
+                                      MODE == MODE_ACC ? nullptr : B.qout[b],
+                                      MODE == MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, t.bx, t.by);
+}
+
+// Untyped pass tables (device arrays of per-block pointers) and their typed view.
+struct PassTables {
+  const void* params;
+  const void* tiles;
+  void* const* q;
+  void* const* lam;
+  void* const* dacc;
+  void* const* dout;
+  void* const* qout;
+  void* const* qn;
+};
+
+template <typename Real, typename Acc>
+BatchPass<Real, Acc> typed_pass(const PassTables& t) {
+  BatchPass<Real, Acc> B;
+  B.params = static_cast<const Params*>(t.params);
+  B.tiles = static_cast<const TileRef*>(t.tiles);
+  B.q = reinterpret_cast<const Real* const*>(t.q);
+  B.lam = reinterpret_cast<const double* const*>(t.lam);
+  B.dacc = reinterpret_cast<const Acc* const*>(t.dacc);
+  B.dout = reinterpret_cast<Acc* const*>(t.dout);
+  B.qout = reinterpret_cast<Real* const*>(t.qout);
+  B.qn = reinterpret_cast<const Real* const*>(t.qn);
+  return B;
+}
+
+template <int S, int DIR, int MODE, typename Real, typename Acc>
+cudaError_t launch_sweep_batch(const BatchPass<Real, Acc>& B, int ntiles, double ca, double cb, double dt,
+                               cudaStream_t st) {
+  using Sh = TileShape<S, DIR, Real, Acc>;
+  auto kern = sweep_batch_kernel<S, DIR, MODE, Real, Acc>;
+  const size_t smem = Sh::smem_bytes();
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (ntiles > 0) kern<<<ntiles, Sh::THREADS, smem, st>>>(B, ca, cb, dt);
+  return cudaGetLastError();
+}
+
+template <int S, int DIR, int MODE, typename Real, typename Acc>
 cudaError_t launch_sweep(const Params& P, const Real* Q, const double* lam, const Acc* Dacc, Acc* Dout,
                          Real* qout, const Real* Qn, double ca, double cb, double dt, cudaStream_t st) {
   using Sh = TileShape<S, DIR, Real, Acc>;
@@ -319,6 +407,33 @@ cudaError_t flux_difference_passes(const Params& P, const Real* Q, const double*
              : launch_sweep<S, 1, MODE_RHS, Real, Acc>(P, Q, lam, acc, nullptr, static_cast<Real*>(out),
                                                        nullptr, 0, 0, 0, st);
 }
+
+// Both directions of every block for one scheme (mode 0: dQ/dt, mode 1: RK stage).
+template <int S, typename Real, typename Acc>
+cudaError_t batch_scheme(int mode, const PassTables& xi, int ntx, const PassTables& eta, int nte, double ca,
+                         double cb, double dt, cudaStream_t st) {
+  const BatchPass<Real, Acc> X = typed_pass<Real, Acc>(xi), E = typed_pass<Real, Acc>(eta);
+  cudaError_t e = launch_sweep_batch<S, 0, MODE_ACC, Real, Acc>(X, ntx, 0, 0, 0, st);
+  if (e != cudaSuccess) return e;
+  if (mode == 0) return launch_sweep_batch<S, 1, MODE_RHS, Real, Acc>(E, nte, 0, 0, 0, st);
+  return launch_sweep_batch<S, 1, MODE_STAGE, Real, Acc>(E, nte, ca, cb, dt, st);
+}
+
+template <typename Real, typename Acc>
+cudaError_t batch_dispatch(int scheme, int mode, const PassTables& xi, int ntx, const PassTables& eta, int nte,
+                           double ca, double cb, double dt, cudaStream_t st) {
+  switch (scheme) {
+    case S31: return batch_scheme<S31, Real, Acc>(mode, xi, ntx, eta, nte, ca, cb, dt, st);
+    case S32: return batch_scheme<S32, Real, Acc>(mode, xi, ntx, eta, nte, ca, cb, dt, st);
+    case S51: return batch_scheme<S51, Real, Acc>(mode, xi, ntx, eta, nte, ca, cb, dt, st);
+    default:  return batch_scheme<S52, Real, Acc>(mode, xi, ntx, eta, nte, ca, cb, dt, st);
+  }
+}
+
+cudaError_t batch_fp64(int scheme, int mode, const PassTables& xi, int ntx, const PassTables& eta, int nte,
+                       double ca, double cb, double dt, cudaStream_t st);
+cudaError_t batch_fp32(int scheme, bool mixed, int mode, const PassTables& xi, int ntx, const PassTables& eta,
+                       int nte, double ca, double cb, double dt, cudaStream_t st);
 
 // Precision instantiations: each lives in its own translation unit.
 cudaError_t rhs_fp64(int scheme, const Params& P, const void* Q, const double* lx, const double* le,

@@ -20,7 +20,8 @@ import torch
 G = 4
 FP64, FP32 = 0, 1
 WENOIU3_1MP, WENOIU3_2MP, WENOIU5_1MP, WENOIU5_2MP = 0, 1, 2, 3
-BC_PERIODIC, BC_TRANSMISSIVE, BC_DIRICHLET, BC_SLIPWALL, BC_FARFIELD = 0, 1, 2, 3, 4
+BC_PERIODIC, BC_TRANSMISSIVE, BC_DIRICHLET, BC_SLIPWALL, BC_FARFIELD, BC_LINK = 0, 1, 2, 3, 4, 5
+FP32_MIXED = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfsp.so")
@@ -45,6 +46,11 @@ class _Config(ctypes.Structure):
 class _Block(ctypes.Structure):
     _fields_ = [("ni", ctypes.c_int), ("nj", ctypes.c_int), ("ld", ctypes.c_longlong),
                 ("period", (ctypes.c_double * 2) * 2)]
+
+
+class _Link(ctypes.Structure):
+    _fields_ = [("nbr", ctypes.c_int), ("face", ctypes.c_int), ("reversed", ctypes.c_int),
+                ("offset", ctypes.c_double * 2)]
 
 
 @dataclasses.dataclass
@@ -108,6 +114,15 @@ def lib():
                 "fsp_cfl_dt": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_norms": (ctypes.c_int, [B, ctypes.c_int, _P, _P, _P, _P]),
                 "fsp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+                "fsp_batch_create": (ctypes.c_int, [C, ctypes.c_int, B, ctypes.POINTER(ctypes.c_int),
+                                                    ctypes.POINTER(_Link), ctypes.POINTER(ctypes.c_void_p)]),
+                "fsp_batch_bind": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                                  ctypes.POINTER(_P)]),
+                "fsp_batch_metrics": (ctypes.c_int, [_P, _P]),
+                "fsp_batch_rhs": (ctypes.c_int, [_P, ctypes.POINTER(_P), _P]),
+                "fsp_batch_rk3_step": (ctypes.c_int, [_P, ctypes.c_double, _P]),
+                "fsp_batch_capture_graph": (ctypes.c_int, [_P, ctypes.c_double, _P]),
+                "fsp_batch_destroy": (ctypes.c_int, [_P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -248,3 +263,76 @@ def norms(A: torch.Tensor, B: Optional[torch.Tensor] = None, out=None, stream=No
 def fma_peak(precision: int, blocks: int, iters: int, sink: torch.Tensor, stream=None):
     _check("fsp_fma_peak", lib().fsp_fma_peak(int(precision), int(blocks), int(iters), _ptr(sink),
                                               _stream(stream)))
+
+
+class Batch:
+    """Many structured blocks joined by linked faces (fsp_batch_*).
+
+    blocks: list of dicts with ``x``, ``y`` (nj, ni) arrays or tensors, ``bc`` (4 codes,
+    BC_LINK for joined faces), ``links`` (4 entries: None or (nbr, face, reversed)),
+    optional ``offsets`` (4 entries: None or (dx, dy)) and ``period``.  states: the
+    initial (4, nj, ni) state of every block (copied to the device in the precision's
+    dtype).  Device memory for coordinates, metrics and states is held here; the library
+    handle holds its own scratch."""
+
+    def __init__(self, cfg: Config, blocks, states, device="cuda"):
+        self.cfg = cfg
+        n = len(blocks)
+        dt = torch.float64 if cfg.precision == FP64 else torch.float32
+        self.x = [torch.as_tensor(b["x"], dtype=torch.float64, device=device).contiguous() for b in blocks]
+        self.y = [torch.as_tensor(b["y"], dtype=torch.float64, device=device).contiguous() for b in blocks]
+        self.Q = [torch.as_tensor(q, dtype=dt, device=device).contiguous() for q in states]
+        self.M = [torch.empty((5, x.shape[0] + 2 * G, x.shape[1] + 2 * G), dtype=torch.float64, device=device)
+                  for x in self.x]
+        blk = (_Block * n)()
+        bc = (ctypes.c_int * (4 * n))()
+        lk = (_Link * (4 * n))()
+        for k, b in enumerate(blocks):
+            nj, ni = self.x[k].shape
+            blk[k].ni, blk[k].nj, blk[k].ld = ni, nj, ni
+            per = b.get("period", ((0.0, 0.0), (0.0, 0.0)))
+            for a in range(2):
+                for c in range(2):
+                    blk[k].period[a][c] = float(per[a][c])
+            for f in range(4):
+                bc[4 * k + f] = int(b["bc"][f])
+                l = (b.get("links") or [None] * 4)[f]
+                if l is not None:
+                    lk[4 * k + f].nbr, lk[4 * k + f].face, lk[4 * k + f].reversed = int(l[0]), int(l[1]), int(l[2])
+                o = (b.get("offsets") or [None] * 4)[f]
+                if o is not None:
+                    lk[4 * k + f].offset[0], lk[4 * k + f].offset[1] = float(o[0]), float(o[1])
+        self._h = ctypes.c_void_p()
+        _check("fsp_batch_create", lib().fsp_batch_create(ctypes.byref(cfg._c()), n, blk, bc, lk,
+                                                          ctypes.byref(self._h)))
+        self.n = n
+        self._ptrs = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+        _check("fsp_batch_bind", lib().fsp_batch_bind(self._h, self._ptrs(self.x), self._ptrs(self.y),
+                                                      self._ptrs(self.M), self._ptrs(self.Q)))
+
+    def metrics(self, stream=None):
+        _check("fsp_batch_metrics", lib().fsp_batch_metrics(self._h, _stream(stream)))
+        return self.M
+
+    def rhs(self, out=None, stream=None):
+        out = [torch.empty_like(q) for q in self.Q] if out is None else out
+        _check("fsp_batch_rhs", lib().fsp_batch_rhs(self._h, self._ptrs(out), _stream(stream)))
+        return out
+
+    def rk3_step(self, dt: float, stream=None):
+        _check("fsp_batch_rk3_step", lib().fsp_batch_rk3_step(self._h, float(dt), _stream(stream)))
+        return self.Q
+
+    def capture_graph(self, dt: float, stream=None):
+        _check("fsp_batch_capture_graph", lib().fsp_batch_capture_graph(self._h, float(dt), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fsp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

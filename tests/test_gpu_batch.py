@@ -1,0 +1,150 @@
+"""Multi-block batch (fsp_batch_*) against the oracle's multi-block path: metrics with the
+ghost layers, right-hand sides and RK3 steps of every block, on cylinder blocks (uneven
+sizes, randomised blocks, slip wall, far field, angular wrap) and on a grid whose second
+block is stored rotated behind reversed links."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1810_11103_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1810_11103_gb300 import build, fsp
+    build.build()
+    return fsp
+
+
+def _small_cylinder():
+    blocks, states, free = I.cylinder_blocks(imin=24, imax=48, jmin=16, jmax=32, step=8, cols=4, rows=3,
+                                             stretch=1.02, frac_random=0.5)
+    return blocks, states, free
+
+
+def _cfgd(free, scheme=2, prec=0):
+    return dict(scheme=scheme, precision=prec, bc_state=np.tile(free, (4, 1)))
+
+
+def _perturbed(states, seed, amp):
+    """Each block's state with its primitive variables perturbed by a relative amp (the
+    pressure stays positive)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in states:
+        rho = q[0] * (1 + amp * rng.standard_normal(q[0].shape))
+        u = q[1] / q[0] + amp * rng.standard_normal(q[0].shape)
+        v = q[2] / q[0] + amp * rng.standard_normal(q[0].shape)
+        p = 0.4 * (q[3] - 0.5 * (q[1] ** 2 + q[2] ** 2) / q[0]) * (1 + amp * rng.standard_normal(q[0].shape))
+        out.append(I.conservative(rho, u, v, p))
+    return out
+
+
+def _maxrel(As, Bs):
+    scale = max(np.abs(b).max() for b in Bs)
+    return max(np.abs(a - b).max() for a, b in zip(As, Bs)) / scale
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+def test_batch_metrics_and_rhs_small_cylinder(F, scheme):
+    blocks, states, free = _small_cylinder()
+    cfgd = _cfgd(free, scheme)
+    Ms = O.mb_metrics(cfgd, blocks)
+    bt = F.Batch(F.Config.from_dict(cfgd), blocks, states)
+    Mg = [m.cpu().numpy() for m in bt.metrics()]
+    for a, b in zip(Mg, Ms):
+        assert np.abs(a[:4] - b[:4]).max() < TOL * np.abs(b[:4]).max()
+        assert np.abs(a[4] - b[4]).max() < TOL * np.abs(b[4]).max()
+    # perturb the free stream so the right-hand side is not trivially zero
+    qs = _perturbed(states, scheme, 0.05)
+    for k, q in enumerate(qs):
+        bt.Q[k].copy_(torch.as_tensor(q))
+        # both sides take the far-field inflow/outflow decision (the sign of the free
+        # stream's normal velocity, zero where it runs tangent to the outer circle) from
+        # the same metrics
+        bt.M[k].copy_(torch.as_tensor(Ms[k]))
+    Rg = [r.cpu().numpy() for r in bt.rhs()]
+    Ro = O.mb_rhs(cfgd, blocks, Ms, qs)
+    assert _maxrel(Rg, Ro) < TOL
+    bt.close()
+
+
+def test_batch_rk3_eager_and_graph(F):
+    blocks, states, free = _small_cylinder()
+    cfgd = _cfgd(free, 3)
+    Ms = O.mb_metrics(cfgd, blocks)
+    dt = 2e-4   # well inside the CFL limit of the smallest wall cells
+    q2 = O.mb_rk3(cfgd, blocks, Ms, states, dt, 2)
+    q4 = O.mb_rk3(cfgd, blocks, Ms, states, dt, 4)
+    bt = F.Batch(F.Config.from_dict(cfgd), blocks, states)
+    for k in range(len(blocks)):
+        bt.M[k].copy_(torch.as_tensor(Ms[k]))
+    bt.rk3_step(dt)
+    bt.rk3_step(dt)
+    torch.cuda.synchronize()
+    assert _maxrel([q.cpu().numpy() for q in bt.Q], q2) < TOL
+    bt.capture_graph(dt)          # one eager step, then the captured step
+    bt.rk3_step(dt)
+    torch.cuda.synchronize()
+    assert _maxrel([q.cpu().numpy() for q in bt.Q], q4) < TOL
+    bt.close()
+
+
+def test_batch_reversed_links(F):
+    x, y, per = I.periodic_square(30, 8.0, 0.2, seed=3, nj=24)
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * x / 8.0) * np.cos(2 * np.pi * y / 8.0)
+    q = I.conservative(rho, 0.6 + 0.1 * np.cos(2 * np.pi * y / 8.0), np.full_like(x, -0.3), rho * 1.1)
+    blocks, qs = I.split_blocks(x, y, q, (14,), (), (0, 0, 1, 1), period=((8.0, 0.0), (0.0, 0.0)))
+    B = dict(blocks[1])
+    B["x"], B["y"] = blocks[1]["x"][::-1, ::-1].copy(), blocks[1]["y"][::-1, ::-1].copy()
+    B["bc"] = [5, 5, 1, 1]
+    B["links"] = [(0, 0, 1), (0, 1, 1), None, None]
+    B["offsets"] = [blocks[1]["offsets"][1], blocks[1]["offsets"][0], None, None]
+    A = dict(blocks[0])
+    A["links"] = [(1, 0, 1), (1, 1, 1), None, None]
+    blocks2 = [A, B]
+    qs2 = [qs[0], qs[1][:, ::-1, ::-1].copy()]
+    cfgd = dict(scheme=3)
+    Ms = O.mb_metrics(cfgd, blocks2)
+    Ro = O.mb_rhs(cfgd, blocks2, Ms, qs2)
+    bt = F.Batch(F.Config.from_dict(cfgd), blocks2, qs2)
+    Mg = [m.cpu().numpy() for m in bt.metrics()]
+    assert max(np.abs(a - b).max() for a, b in zip(Mg, Ms)) < TOL * max(np.abs(b).max() for b in Ms)
+    assert _maxrel([r.cpu().numpy() for r in bt.rhs()], Ro) < TOL
+    bt.close()
+
+
+@pytest.mark.parametrize("prec,bound", [(1, 1e-4), (2, 5e-5)])
+def test_batch_fp32_paths(F, prec, bound):
+    blocks, states, free = _small_cylinder()
+    qs = [q.astype(np.float32).astype(np.float64) for q in _perturbed(states, 7, 0.05)]
+    cfgd = _cfgd(free, 2)
+    Ms = O.mb_metrics(cfgd, blocks)
+    Ro = O.mb_rhs(cfgd, blocks, Ms, qs)
+    bt = F.Batch(F.Config.from_dict(dict(cfgd, precision=prec)), blocks, qs)
+    for k in range(len(blocks)):
+        bt.M[k].copy_(torch.as_tensor(Ms[k]))
+    assert _maxrel([r.double().cpu().numpy() for r in bt.rhs()], Ro) < bound
+    bt.close()
+
+
+def test_batch_full_size_cylinder(F):
+    # the 64-block cylinder workload at full size (about 4 million nodes)
+    blocks, states, free = I.cylinder_blocks()
+    qs = _perturbed(states, 11, 0.02)
+    cfgd = _cfgd(free, 2)
+    bt = F.Batch(F.Config.from_dict(cfgd), blocks, qs)
+    Mg = [m.cpu().numpy() for m in bt.metrics()]
+    Ms = O.mb_metrics(cfgd, blocks)
+    assert max(np.abs(a[:4] - b[:4]).max() / np.abs(b[:4]).max() for a, b in zip(Mg, Ms)) < TOL
+    Ro = O.mb_rhs(cfgd, blocks, Ms, qs)
+    for k in range(len(blocks)):              # identical metrics isolate the right-hand side
+        bt.M[k].copy_(torch.as_tensor(Ms[k]))
+    assert _maxrel([r.cpu().numpy() for r in bt.rhs()], Ro) < TOL
+    bt.close()
