@@ -1,18 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the WENOIU free-stream-preserving Euler right-hand side on GB300.
 
-One step = one TVD-RK3 step (three right-hand sides: per-line spectral radius, xi sweep,
-eta sweep fused with the stage update) over the whole synthetic workload, through the C
-ABI of libfsp.  Metric: Mcell-RHS/s = nodes x right-hand sides / second.
+Workload (default "cylinder64"): supersonic flow (Mach 4) around a cylinder on 64 body-fitted
+blocks of uneven sizes (5.9 M nodes, 30 % of the blocks randomised), WENOIU5-1MP.  One step
+= one TVD-RK3 step of every block (three right-hand sides), launched as one captured CUDA
+graph through fsp_batch_rk3_step.  Metric: Mcell-RHS/s = nodes x right-hand sides / second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                    [--precision fp64|fp32|mixed] [--no-all-precisions]
+                    [--workload cylinder64|vortex256] [--precision fp64|fp32|mixed]
+                    [--no-all-precisions] [--no-cpu-baseline]
 
-The headline `value` is the FP64 path; the FP32 and mixed FP32/FP64 paths of the same
-workload are reported beside it ("fp32", "fp32_mixed"), each with its own roofline.
-
-Under torchrun every rank runs the same workload on its own GPU (independent problems,
-weak scaling, no data-path collective); rank 0 prints one JSON line.
+The headline `value` is the FP64 path.  Beside it: the FP32 and mixed FP32/FP64 paths of the
+same workload ("fp32", "fp32_mixed"), each with its own roofline, and the same FP64 step as a
+loop of per-block fsp_rk3_step calls ("per_block_fp64", links read as transmissive).
+Under torchrun every rank runs the workload on its own GPU (independent problems, weak
+scaling, no data-path collective); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -32,7 +34,10 @@ sys.path.insert(0, ROOT)
 METRIC = "Mcell-RHS/s 2-D Euler WENO5 FP64 vs FP32 batched, % roofline; adjoint/fwd ratio"
 UNIT = "Mcell-RHS/s"
 SCHEME_NAMES = ["WENOIU3-1MP", "WENOIU3-2MP", "WENOIU5-1MP", "WENOIU5-2MP"]
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
+DTYPES = {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64"}
 L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
+LINK = 5
 
 
 def parse():
@@ -41,37 +46,44 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="cylinder64", choices=["cylinder64", "vortex256"])
     ap.add_argument("--scheme", type=int, default=2)
-    ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
     ap.add_argument("--all-precisions", action=argparse.BooleanOptionalAction, default=True,
                     help="also measure the other two precisions and report them beside the headline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=list(PRECISIONS), default=None,
+                    help="profiling run for ncu: build the cylinder batch in this precision, evaluate one "
+                         "right-hand side, then launch the batched xi sweep three times; no timing")
     return ap.parse_args()
 
 
-def workload(n):
-    """The periodic vortex case: n x n nodes on [0, 10)^2, every node randomised by up to
-    +-0.2 h (seed 1810), vortex of strength 5 on the free stream (1, 1, 1, 1)."""
+# ------------------------------------------------------------------------------------------
+# workloads
+# ------------------------------------------------------------------------------------------
+def cylinder_workload():
+    """64 blocks around a cylinder of diameter one (seed 1812): 8 angular columns x 8 radial
+    rows, sizes 64..512 x 64..384, slip wall, far field at Mach 4, 30 % randomised blocks."""
+    from paper_1810_11103_gb300 import inputs as I
+    return I.cylinder_blocks()
+
+
+def vortex_workload(n=256):
     from paper_1810_11103_gb300 import inputs as I
     x, y, per = I.periodic_square(n, 10.0, 0.2, seed=1810)
     q = I.isentropic_vortex(x, y, (5.0, 5.0), strength=5.0, free=(1.0, 1.0, 1.0, 1.0), period=(10.0, 10.0))
     return x, y, per, q
 
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
-DTYPES = {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64"}
-
-
-def config_of(args, per):
-    return dict(scheme=args.scheme, precision=PRECISIONS[getattr(args, "precision", "fp64")], interp=0, ppm=1, linear_weights=0, bc=(0, 0, 0, 0),
-                gamma=1.4, lf_alpha=1.1, eps=1e-40, period=per)
-
-
-def workload_config(args):
-    return {"workload": f"periodic isentropic vortex {args.n}x{args.n}, randomised grid +-0.2h, "
-                        f"{SCHEME_NAMES[args.scheme]}, TVD-RK3",
-            "ni": args.n, "nj": args.n, "scheme": SCHEME_NAMES[args.scheme], "precision": args.precision,
+def workload_config(args, nodes, nblocks):
+    if args.workload == "cylinder64":
+        return {"workload": f"Mach 4 cylinder, {nblocks} linked blocks of uneven sizes (seed 1812), "
+                            f"{SCHEME_NAMES[args.scheme]}, TVD-RK3",
+                "nodes": nodes, "blocks": nblocks, "scheme": SCHEME_NAMES[args.scheme], "precision": args.precision,
+                "step": "one RK3 step of every block = 3 right-hand sides, one captured CUDA graph",
+                "l2": "inputs larger than L2 (state and metrics > 300 MB); no flush"}
+    return {"workload": f"periodic isentropic vortex 256x256, randomised grid +-0.2h, {SCHEME_NAMES[args.scheme]}",
+            "nodes": nodes, "blocks": 1, "scheme": SCHEME_NAMES[args.scheme], "precision": args.precision,
             "step": "one RK3 step = 3 right-hand sides",
             "l2": "flushed between timed steps (256 MiB write outside the events)"}
 
@@ -83,6 +95,27 @@ def source_hash():
         with open(os.path.join(src, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
+
+
+def algorithmic_flops(args):
+    with open(os.path.join(ROOT, "paper_1810_11103_gb300", "algorithmic_flops.json")) as f:
+        d = json.load(f)
+    if args.workload == "cylinder64":
+        return d["cylinder64"]["schemes"][SCHEME_NAMES[args.scheme]]
+    return d["schemes"][SCHEME_NAMES[args.scheme]]
+
+
+def traffic_of(args, prec):
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        entries = json.load(f)
+    for tr in entries if isinstance(entries, list) else [entries]:
+        if (tr.get("source_hash") == source_hash() and tr.get("workload") == args.workload
+                and tr.get("scheme") == args.scheme and tr.get("precision") == prec):
+            return tr.get("bytes_per_launch")
+    return None
 
 
 class ClockSampler:
@@ -103,6 +136,7 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            time.sleep(0.3)   # let the first samples arrive before the timed region
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -138,12 +172,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(args, seconds=12.0):
-    """The oracle, as it stands, on one host core: right-hand sides of the full workload."""
+# ------------------------------------------------------------------------------------------
+# CPU baseline and the reference arm: the oracle, as it stands, on one host core
+# ------------------------------------------------------------------------------------------
+def oracle_sample(args):
+    """(cfg, metrics, state, nodes, description) of the bounded sample the oracle is timed
+    on: for the cylinder, its first block (512 x 384) with linked faces read as transmissive
+    (the same arithmetic per node); for the vortex, the whole 256 x 256 block."""
+    import numpy as np
     import oracle as O
-    x, y, per, q = workload(args.n)
-    cfg = config_of(args, per)
-    M = O.metrics(cfg, x, y)
+    if args.workload == "cylinder64":
+        blocks, states, free = cylinder_workload()
+        b = blocks[0]
+        cfg = dict(scheme=args.scheme, bc=[1 if c == LINK else c for c in b["bc"]],
+                   bc_state=np.tile(free, (4, 1)))
+        M = O.metrics(cfg, b["x"], b["y"])
+        return cfg, M, states[0], b["x"].size, f"block 0 ({b['x'].shape[1]}x{b['x'].shape[0]}) of the cylinder"
+    x, y, per, q = vortex_workload()
+    cfg = dict(scheme=args.scheme, period=per)
+    return cfg, O.metrics(cfg, x, y), q, x.size, "the 256x256 vortex block"
+
+
+def cpu_baseline(args, seconds=12.0):
+    import oracle as O
+    cfg, M, q, nodes, what = oracle_sample(args)
     t0 = time.perf_counter()
     k = 0
     while True:
@@ -152,8 +204,8 @@ def cpu_baseline(args, seconds=12.0):
         t = time.perf_counter() - t0
         if t > seconds:
             break
-    return {"value": x.size * k / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} right-hand sides of the {args.n}x{args.n} workload (oracle, one thread)"}
+    return {"value": nodes * k / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} right-hand sides of {what} (oracle, one thread)"}
 
 
 def run_reference(args, rank):
@@ -161,67 +213,169 @@ def run_reference(args, rank):
         return
     import oracle as O
     O.build()
-    x, y, per, q = workload(args.n)
-    cfg = config_of(args, per)
-    M = O.metrics(cfg, x, y)
+    cfg, M, q, nodes, what = oracle_sample(args)
     for _ in range(args.warmup):
         O.rhs(cfg, M, q)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         O.rhs(cfg, M, q)
     t = time.perf_counter() - t0
-    value = x.size * args.steps / t / 1e6
+    value = nodes * args.steps / t / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(workload_config(args),
-                                                 step="one right-hand side (oracle, one host thread)"),
+            "data": "synthetic",
+            "config": dict(workload_config(args, nodes, 1), step=f"one right-hand side of {what} (oracle, one host thread)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} right-hand sides of the {args.n}x{args.n} workload"},
+                             "sample": f"{args.steps} right-hand sides of {what}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def measure(args, prec, dev, world, rank, torch, fsp, dist):
-    """Time the RK3 step (device-resident and end to end) and the dominant kernel for one
-    precision of the workload; returns a dict."""
-    x, y, per, q = workload(args.n)
-    cfgd = dict(config_of(args, per), precision=PRECISIONS[prec])
-    cfg = fsp.Config.from_dict(cfgd)
-    stream = torch.cuda.current_stream()
-    X, Y = torch.as_tensor(x, device=dev), torch.as_tensor(y, device=dev)
-    M = fsp.metrics(cfg, X, Y)
-    sdt = torch.float64 if prec == "fp64" else torch.float32
-    Q = torch.as_tensor(q, dtype=sdt, device=dev)
-    ws = fsp.workspace(cfg, Q)
-    dt = float(fsp.cfl_dt(cfg, M, Q, 0.5, ws=ws).item())
-    nodes = args.n * args.n
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+# ------------------------------------------------------------------------------------------
+# GPU measurement
+# ------------------------------------------------------------------------------------------
+class Ctx:
+    def __init__(self, torch, fsp, dist, dev, world):
+        self.torch, self.fsp, self.dist, self.dev, self.world = torch, fsp, dist, dev, world
+        self.stream = torch.cuda.current_stream()
+        self.flush = None
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+        self.torch.cuda.synchronize()
 
-    def timed(body, reps):
+    def timed(self, body, reps, flush=False):
+        torch = self.torch
+        if flush and self.flush is None:
+            self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=self.dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-        barrier()
+        self.barrier()
         for a, b in ev:
-            flush.zero_()
-            a.record(stream)
+            if flush:
+                self.flush.zero_()
+            a.record(self.stream)
             body()
-            b.record(stream)
-        barrier()
+            b.record(self.stream)
+        self.barrier()
         return sum(a.elapsed_time(b) for a, b in ev) / 1e3
 
+    def peak(self, prec):
+        fsp, torch = self.fsp, self.torch
+        pipe = 0 if prec == "fp64" else 1
+        blocks, iters = 152 * 8, 4096 if pipe == 0 else 65536
+        sink = torch.empty(blocks * 256, dtype=torch.float64 if pipe == 0 else torch.float32, device=self.dev)
+        fsp.fma_peak(pipe, blocks, iters, sink)
+        t = self.timed(lambda: fsp.fma_peak(pipe, blocks, iters, sink), 3) / 3
+        return 2.0 * 8 * iters * blocks * 256 / t / 1e12, ("FP64" if pipe == 0 else "FP32")
+
+    def max_over_ranks(self, *vals):
+        if self.world == 1:
+            return vals
+        t = self.torch.tensor(vals, dtype=self.torch.float64, device=self.dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return tuple(float(v) for v in t)
+
+
+def measure_cylinder(args, prec, C, per_block=False):
+    import numpy as np
+    torch, fsp = C.torch, C.fsp
+    blocks, states, free = cylinder_workload()
+    cfgd = dict(scheme=args.scheme, precision=PRECISIONS[prec], bc_state=np.tile(free, (4, 1)))
+    cfg = fsp.Config.from_dict(cfgd)
+    bt = fsp.Batch(cfg, blocks, states, device=C.dev)
+    bt.metrics()
+    nodes = sum(b["x"].size for b in blocks)
+    # a stable step: CFL 0.3 on the initial state, from the per-block CFL rate
+    dts = []
+    for k, b in enumerate(blocks):
+        cb = fsp.Config.from_dict(dict(cfgd, bc=[1 if c == LINK else c for c in b["bc"]]))
+        dts.append(float(fsp.cfl_dt(cb, bt.M[k], bt.Q[k], 0.3).item()))
+    dt = min(dts)
+    bt.capture_graph(dt)
+    for _ in range(args.warmup):
+        bt.rk3_step(dt)
+    clocks = ClockSampler(C.dev.index or 0)
+    clocks.start()
+    t_dev = C.timed(lambda: bt.rk3_step(dt), args.steps)
+    clk = clocks.stop()
+    # end to end: every block's state from pinned host memory, the step, the states back
+    sdt = torch.float64 if prec == "fp64" else torch.float32
+    host_in = [torch.as_tensor(q, dtype=sdt).pin_memory() for q in states]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+
+    def e2e():
+        for d, h in zip(bt.Q, host_in):
+            d.copy_(h, non_blocking=True)
+        bt.rk3_step(dt)
+        for h, d in zip(host_out, bt.Q):
+            h.copy_(d, non_blocking=True)
+    e2e()
+    t_e2e = C.timed(e2e, args.steps)
+    state_bytes = sum(q.numel() * q.element_size() for q in bt.Q)
+    # the dominant kernel alone: the xi sweep of every block (one launch)
+    for d, h in zip(bt.Q, host_in):
+        d.copy_(h)
+    bt.rhs()
+    D = [torch.empty(q.shape, dtype=torch.float32 if prec == "fp32" else torch.float64, device=C.dev) for q in bt.Q]
+    bt.flux_difference(0, D)
+    t_k = C.timed(lambda: bt.flux_difference(0, D), 20) / 20
+    peak, pipe = C.peak(prec)
+    t_dev, t_e2e = C.max_over_ranks(t_dev, t_e2e)
+    fl = algorithmic_flops(args)
+    achieved = fl["sweep_xi_per_node"] * nodes / t_k / 1e12
+    rhs_total = nodes * 3 * args.steps * C.world
+    out = {
+        "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps, "nodes": nodes,
+        "nblocks": len(blocks),
+        "e2e": {"value": rhs_total / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "roofline": {"bound": "alu", "kernel": "sweep_batch_kernel xi, all 64 blocks (fsp_batch_flux_difference dir 0)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic_of(args, prec),
+                     "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
+                     "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
+                     "kernel_ms": 1e3 * t_k},
+        "clocks": clk,
+    }
+    if per_block:
+        # the same FP64 step as a loop of single-block calls (links read as transmissive)
+        cbs, wss = [], []
+        for k, b in enumerate(blocks):
+            cb = fsp.Config.from_dict(dict(cfgd, bc=[1 if c == LINK else c for c in b["bc"]]))
+            cbs.append(cb)
+            wss.append(fsp.workspace(cb, bt.Q[k]))
+
+        def loop():
+            for k in range(len(blocks)):
+                fsp.rk3_step(cbs[k], bt.M[k], bt.Q[k], dt, ws=wss[k])
+        loop()
+        reps = max(3, args.steps // 4)
+        t_loop = C.timed(loop, reps)
+        out["per_block_fp64"] = {"value": nodes * 3 * reps / t_loop / 1e6, "unit": UNIT,
+                                 "ms_per_step": 1e3 * t_loop / reps,
+                                 "how": "64 fsp_rk3_step calls per step, one block each, eager launches"}
+    bt.close()
+    return out
+
+
+def measure_vortex(args, prec, C):
+    torch, fsp = C.torch, C.fsp
+    x, y, per, q = vortex_workload()
+    cfg = fsp.Config.from_dict(dict(scheme=args.scheme, precision=PRECISIONS[prec], period=per))
+    M = fsp.metrics(cfg, torch.as_tensor(x, device=C.dev), torch.as_tensor(y, device=C.dev))
+    sdt = torch.float64 if prec == "fp64" else torch.float32
+    Q = torch.as_tensor(q, dtype=sdt, device=C.dev)
+    ws = fsp.workspace(cfg, Q)
+    dt = float(fsp.cfl_dt(cfg, M, Q, 0.5, ws=ws).item())
+    nodes = x.size
     for _ in range(args.warmup):
         fsp.rk3_step(cfg, M, Q, dt, ws=ws)
-    clocks = ClockSampler(dev.index or 0)
+    clocks = ClockSampler(C.dev.index or 0)
     clocks.start()
-    t_dev = timed(lambda: fsp.rk3_step(cfg, M, Q, dt, ws=ws), args.steps)
+    t_dev = C.timed(lambda: fsp.rk3_step(cfg, M, Q, dt, ws=ws), args.steps, flush=True)
     clk = clocks.stop()
-
-    # end to end through the API: pinned host state in, RK3 step, state back to the host
     Qh = torch.as_tensor(q, dtype=sdt).pin_memory()
     Qout = torch.empty_like(Qh).pin_memory()
 
@@ -229,57 +383,56 @@ def measure(args, prec, dev, world, rank, torch, fsp, dist):
         Q.copy_(Qh, non_blocking=True)
         fsp.rk3_step(cfg, M, Q, dt, ws=ws)
         Qout.copy_(Q, non_blocking=True)
-    for _ in range(2):
-        e2e()
-    t_e2e = timed(e2e, args.steps)
-
-    # the dominant kernel alone: the xi sweep (fsp_flux_difference, direction 0)
+    e2e()
+    t_e2e = C.timed(e2e, args.steps, flush=True)
     lx, le = fsp.line_lambda(cfg, M, Q)
-    D = torch.empty(Q.shape, dtype=torch.float32 if prec == "fp32" else torch.float64, device=dev)
-    for _ in range(3):
-        fsp.flux_difference(cfg, M, Q, lx, 0, 0, out=D)
-    t_k = timed(lambda: fsp.flux_difference(cfg, M, Q, lx, 0, 0, out=D), 20) / 20
-
-    # ALU roof: FMA probe of the precision that bounds the kernel
-    pipe = 0 if prec == "fp64" else 1
-    blocks, iters = 152 * 8, 4096 if pipe == 0 else 65536
-    sink = torch.empty(blocks * 256, dtype=torch.float64 if pipe == 0 else torch.float32, device=dev)
-    fsp.fma_peak(pipe, blocks, iters, sink)
-    t_p = timed(lambda: fsp.fma_peak(pipe, blocks, iters, sink), 3) / 3
-    peak = 2.0 * 8 * iters * blocks * 256 / t_p / 1e12
-
-    if world > 1:
-        t = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev, t_e2e = float(t[0]), float(t[1])
-    with open(os.path.join(ROOT, "paper_1810_11103_gb300", "algorithmic_flops.json")) as f:
-        flops = json.load(f)["schemes"][SCHEME_NAMES[args.scheme]]
-    achieved = flops["sweep_xi_per_node"] * nodes / t_k / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tr = json.load(f)
-        if (tr.get("source_hash") == source_hash() and tr.get("n") == args.n and tr.get("scheme") == args.scheme
-                and tr.get("precision", "fp64") == prec):
-            traffic = tr.get("bytes_per_launch")
-    rhs_total = nodes * 3 * args.steps * world
-    state_bytes = Q.numel() * Q.element_size()
+    D = torch.empty(Q.shape, dtype=torch.float32 if prec == "fp32" else torch.float64, device=C.dev)
+    fsp.flux_difference(cfg, M, Q, lx, 0, 0, out=D)
+    t_k = C.timed(lambda: fsp.flux_difference(cfg, M, Q, lx, 0, 0, out=D), 20, flush=True) / 20
+    peak, pipe = C.peak(prec)
+    t_dev, t_e2e = C.max_over_ranks(t_dev, t_e2e)
+    fl = algorithmic_flops(args)
+    achieved = fl["sweep_xi_per_node"] * nodes / t_k / 1e12
+    rhs_total = nodes * 3 * args.steps * C.world
+    sb = Q.numel() * Q.element_size()
     return {
-        "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps,
-        "e2e": {"value": rhs_total / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes},
-        "roofline": {"bound": "alu", "kernel": "sweep_kernel xi (fsp_flux_difference dir 0)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic,
-                     "peak_source": ("FP64" if pipe == 0 else "FP32") + " FMA probe (fsp_fma_peak) in this run",
-                     "flops_per_node": flops["sweep_xi_per_node"], "kernel_ms": 1e3 * t_k},
+        "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps, "nodes": nodes, "nblocks": 1,
+        "e2e": {"value": rhs_total / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": sb, "d2h_bytes_per_step": sb},
+        "roofline": {"bound": "alu", "kernel": "sweep_kernel xi (fsp_flux_difference dir 0)", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_of(args, prec),
+                     "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
+                     "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
+                     "kernel_ms": 1e3 * t_k},
         "clocks": clk,
     }
 
 
+def profile_run(args, prec):
+    """Minimal launch sequence for a profiler: metrics, one right-hand side (line maxima,
+    xi sweep, eta sweep), then three launches of the batched xi sweep alone."""
+    import numpy as np
+    import torch
+    from paper_1810_11103_gb300 import build as B
+    B.build()
+    from paper_1810_11103_gb300 import fsp
+    blocks, states, free = cylinder_workload()
+    cfg = fsp.Config.from_dict(dict(scheme=args.scheme, precision=PRECISIONS[prec], bc_state=np.tile(free, (4, 1))))
+    bt = fsp.Batch(cfg, blocks, states)
+    bt.metrics()
+    bt.rhs()
+    D = [torch.empty(q.shape, dtype=torch.float32 if prec == "fp32" else torch.float64, device="cuda") for q in bt.Q]
+    for _ in range(3):
+        bt.flux_difference(0, D)
+    torch.cuda.synchronize()
+    print(f"profile run done: {prec}, {sum(b['x'].size for b in blocks)} nodes")
+    bt.close()
+
+
 def main():
     args = parse()
+    if args.profile:
+        profile_run(args, args.profile)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -297,21 +450,28 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    C = Ctx(torch, fsp, dist, dev, world)
 
-    head = measure(args, args.precision, dev, world, rank, torch, fsp, dist)
+    def measure(prec, head=False):
+        if args.workload == "cylinder64":
+            return measure_cylinder(args, prec, C, per_block=head and prec == "fp64")
+        return measure_vortex(args, prec, C)
+
+    head = measure(args.precision, head=True)
     others = {}
     if args.all_precisions:
-        for p in ("fp64", "fp32", "mixed"):
+        for p in PRECISIONS:
             if p != args.precision:
-                others[p] = measure(args, p, dev, world, rank, torch, fsp, dist)
+                others[p] = measure(p)
     if rank == 0:
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
-            "data": "synthetic", "config": workload_config(args),
+            "data": "synthetic", "config": workload_config(args, head["nodes"], head["nblocks"]),
             "e2e": head["e2e"],
-            "gpu_launches": 9 * args.steps,   # per RK3 step: 3 x (line maxima, xi sweep, eta sweep)
+            # per RK3 step: 3 x (line maxima, xi sweep, eta sweep) of all blocks
+            "gpu_launches": 9 * args.steps,
             "roofline": head["roofline"],
             "clocks": head["clocks"],
         }
@@ -319,6 +479,8 @@ def main():
             line["fp32_mixed" if p == "mixed" else p] = {
                 "value": r["value"], "unit": UNIT, "dtype": DTYPES[p], "ms_per_step": r["ms_per_step"],
                 "e2e": r["e2e"]["value"], "roofline": r["roofline"], "clocks": r["clocks"]}
+        if "per_block_fp64" in head:
+            line["per_block_fp64"] = head["per_block_fp64"]
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

@@ -253,6 +253,11 @@ fsp_status fsp_batch_bind(fsp_batch* b, const double* const* x, const double* co
 fsp_status fsp_batch_metrics(fsp_batch* b, void* stream);
 /* dQ/dt of every block (host array of device pointers, state layout). */
 fsp_status fsp_batch_rhs(fsp_batch* b, void* const* dQdt, void* stream);
+/* One direction (dir 0 = xi, 1 = eta) of every block, as fsp_flux_difference mode 0: the
+ * difference H_{s+1/2} - H_{s-1/2} into D[b] (host array of device pointers; double for
+ * FSP_FP64 and FSP_FP32_MIXED, float for FSP_FP32), for the bound states, with the line
+ * maxima left by the last fsp_batch_rhs on this handle.  One launch over all blocks. */
+fsp_status fsp_batch_flux_difference(fsp_batch* b, int dir, void* const* D, void* stream);
 /* One TVD-RK3 step of every block in lockstep; launches the captured graph when one was
  * captured for this dt. */
 fsp_status fsp_batch_rk3_step(fsp_batch* b, double dt, void* stream);

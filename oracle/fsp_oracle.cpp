@@ -571,8 +571,11 @@ static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
         fm[4 * (s + 4) + v] = cst<T>(0.5L) * (f[v] - A * qs[v]);
       }
     }
-    // interfaces: characteristic WENO interpolation from each side, then split fluxes
-    for (int p = -2; p <= n; ++p) {
+    // interfaces: characteristic WENO interpolation from each side, then split fluxes;
+    // h at p + 1/2 (p = -1 .. n-1) uses midpoints p + 1/2 only (one-midpoint schemes) or
+    // p - 1/2 .. p + 3/2 (two-midpoint schemes)
+    const int nmp = S.hmid[1] != 0.0L ? 2 : 1;
+    for (int p = -nmp; p <= n - 2 + nmp; ++p) {
       const int c0 = p + 4;                    // node p
       // characteristic direction from the averaged metrics (Section 3.4)
       T mbx = cst<T>(0.5L) * (mxs[c0] + mxs[c0 + 1]);

@@ -118,12 +118,14 @@ __global__ void __launch_bounds__(256) lambda_batch_kernel(const Params* __restr
   const int i = t.bx * 32 + threadIdx.x, j = t.by * 8 + threadIdx.y;
   double sx = 0.0, se = 0.0;
   if (i < ni && j < nj) {
+    // |U^| + c|k^| in the state's arithmetic (the splitting only needs A^ constant per line)
     const long long plane = (long long)nj * P.ld, o = (long long)j * P.ld + i;
-    double qq[4];
+    Real qq[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) qq[v] = (double)Q[v * plane + o];
-    sx = spectral_radius(qq, met_at(P, 0, i, j), met_at(P, 1, i, j), P.gamma);
-    se = spectral_radius(qq, met_at(P, 2, i, j), met_at(P, 3, i, j), P.gamma);
+    for (int v = 0; v < 4; ++v) qq[v] = Q[v * plane + o];
+    const Real g = from_f64<Real>(P.gamma);
+    sx = (double)spectral_radius(qq, from_f64<Real>(met_at(P, 0, i, j)), from_f64<Real>(met_at(P, 1, i, j)), g);
+    se = (double)spectral_radius(qq, from_f64<Real>(met_at(P, 2, i, j)), from_f64<Real>(met_at(P, 3, i, j)), g);
   }
   double rx = sx;
 #pragma unroll
@@ -418,6 +420,24 @@ fsp_status fsp_batch_rhs(fsp_batch* h, void* const* dQdt, void* stream) {
       cudaSuccess)
     return FSP_ERR_CUDA;
   return batch_stage(h, T_Q0, T_OUT, 0, 0.0, 0.0, 0.0, st);
+}
+
+fsp_status fsp_batch_flux_difference(fsp_batch* h, int dir, void* const* D, void* stream) {
+  if (!h || !h->bound || !D || (dir != 0 && dir != 1)) return FSP_ERR_INVALID_ARG;
+  for (int b = 0; b < h->nb; ++b)
+    if (!dev_ptr(D[b])) return FSP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = h->nb;
+  void** T = h->d_tab;
+  if (cudaMemcpyAsync(T + T_OUT * nb, D, sizeof(void*) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return FSP_ERR_CUDA;
+  const PassTables t{h->d_params, dir == 0 ? h->d_tx : h->d_te, T + T_Q0 * nb, T + (dir == 0 ? T_LX : T_LE) * nb,
+                     nullptr, T + T_OUT * nb, nullptr, nullptr};
+  const int nt = (int)(dir == 0 ? h->tx.size() : h->te.size());
+  cudaError_t e = h->cfg.precision == FSP_FP64
+                      ? batch_direction_fp64(h->cfg.scheme, dir, t, nt, st)
+                      : batch_direction_fp32(h->cfg.scheme, h->cfg.precision == FSP_FP32_MIXED, dir, t, nt, st);
+  return e == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
 }
 
 fsp_status fsp_batch_rk3_step(fsp_batch* h, double dt, void* stream) {

@@ -115,6 +115,40 @@ __device__ __forceinline__ int pmod(int a, int n) {
   return r < 0 ? r + n : r;
 }
 
+// --------------------------------------------------------------------------------------
+// Small arithmetic helpers by precision
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// quotient: IEEE division in FP64; the fast approximate quotient in FP32
+__device__ __forceinline__ double quot(double a, double b) { return a / b; }
+__device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
+// reciprocal: IEEE in FP64; the fast approximate reciprocal in FP32
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+
+// A double rounded to the state type.  To float with integer operations only (round to
+// nearest even; zero and subnormals to signed zero, overflow to infinity), so the FP32
+// path issues nothing to the FP64 pipe when it reads FP64 metrics.
+template <typename T> __device__ __forceinline__ T from_f64(double d);
+template <> __device__ __forceinline__ double from_f64<double>(double d) { return d; }
+template <> __device__ __forceinline__ float from_f64<float>(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 of the 52 mantissa bits
+  const unsigned rest = lo & 0x1fffffffu;              // the 29 bits dropped
+  m += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float(sign | (((unsigned)e << 23) + m));   // a mantissa carry bumps the exponent
+}
+
+// x <= 0 from the sign and magnitude bits (integer compare, no floating-point pipe)
+__device__ __forceinline__ bool nonpos(double x) { return __double_as_longlong(x) <= 0LL; }
+__device__ __forceinline__ bool nonpos(float x) { return __float_as_int(x) <= 0; }
+
 // Ghost state along direction dir for the line `line` (row j for dir 0, column i for
 // dir 1) at position g (any integer; interior when 0 <= g < n).
 template <typename Real>
@@ -186,24 +220,12 @@ __device__ __forceinline__ void euler_flux(const Real q[4], Real mx, Real my, Re
 // |U^| + c |k^| (the quantity maximised along a line for A^, Section 2.3)
 template <typename Real>
 __device__ __forceinline__ Real spectral_radius(const Real q[4], Real mx, Real my, Real gamma) {
-  const Real rinv = Real(1) / q[0];
+  const Real rinv = recip(q[0]);
   const Real u = q[1] * rinv, v = q[2] * rinv;
   const Real p = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
   const Real c = sqrt(gamma * p * rinv);
   return fabs(mx * u + my * v) + c * sqrt(mx * mx + my * my);
 }
-
-// --------------------------------------------------------------------------------------
-// Small arithmetic helpers by precision
-// --------------------------------------------------------------------------------------
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-// quotient: IEEE division in FP64; the fast approximate quotient in FP32
-__device__ __forceinline__ double quot(double a, double b) { return a / b; }
-__device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
-// x <= 0 from the sign and magnitude bits (integer compare, no floating-point pipe)
-__device__ __forceinline__ bool nonpos(double x) { return __double_as_longlong(x) <= 0LL; }
-__device__ __forceinline__ bool nonpos(float x) { return __float_as_int(x) <= 0; }
 
 // Primitive quantities of a node used by the characteristic projection (Section 3.4).
 template <typename Real>
@@ -214,7 +236,7 @@ struct Prim {
 template <typename Real>
 __device__ __forceinline__ Prim<Real> prim_of(const Real q[4], Real gamma) {
   Prim<Real> w;
-  const Real rinv = Real(1) / q[0];
+  const Real rinv = recip(q[0]);
   w.u = q[1] * rinv;
   w.v = q[2] * rinv;
   w.h2 = Real(0.5) * (w.u * w.u + w.v * w.v);

@@ -22,6 +22,24 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
+// Per node |U^| + c|k^| of both directions (and the CFL rate) in the state's arithmetic:
+// the splitting needs A^ constant along a line, not any particular precision, so the FP32
+// paths take their line maxima in float.
+template <typename Real>
+__device__ __forceinline__ void node_speeds(const Params& P, const Real* __restrict__ Q, int i, int j,
+                                            double& sx, double& se, double& rate) {
+  const long long plane = (long long)P.nj * P.ld, o = (long long)j * P.ld + i;
+  Real q[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) q[v] = Q[v * plane + o];
+  const Real g = from_f64<Real>(P.gamma);
+  const Real a = spectral_radius(q, from_f64<Real>(met_at(P, 0, i, j)), from_f64<Real>(met_at(P, 1, i, j)), g);
+  const Real b = spectral_radius(q, from_f64<Real>(met_at(P, 2, i, j)), from_f64<Real>(met_at(P, 3, i, j)), g);
+  sx = (double)a;
+  se = (double)b;
+  rate = (double)((a + b) * recip(from_f64<Real>(met_at(P, 4, i, j))));
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(256) lambda_kernel(Params P, const Real* __restrict__ Q,
                                                      double* __restrict__ lam_xi,
@@ -30,18 +48,8 @@ __global__ void __launch_bounds__(256) lambda_kernel(Params P, const Real* __res
   __shared__ double col[8][33];
   __shared__ double cfl_s[8];
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
-  const bool in = i < P.ni && j < P.nj;
   double sx = 0.0, se = 0.0, rate = 0.0;
-  if (in) {
-    const long long plane = (long long)P.nj * P.ld, o = (long long)j * P.ld + i;
-    double q[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) q[v] = (double)Q[v * plane + o];
-    const double g = P.gamma;
-    sx = spectral_radius(q, met_at(P, 0, i, j), met_at(P, 1, i, j), g);
-    se = spectral_radius(q, met_at(P, 2, i, j), met_at(P, 3, i, j), g);
-    rate = (sx + se) / met_at(P, 4, i, j);
-  }
+  if (i < P.ni && j < P.nj) node_speeds(P, Q, i, j, sx, se, rate);
   // row maximum across the warp (one row of 32 nodes)
   double rx = sx, rr = rate;
 #pragma unroll
@@ -100,6 +108,10 @@ cudaError_t flux_difference_fp64(int scheme, const Params& P, const void* Q, con
 cudaError_t batch_fp64(int scheme, int mode, const PassTables& xi, int ntx, const PassTables& eta, int nte,
                        double ca, double cb, double dt, cudaStream_t st) {
   return batch_dispatch<double, double>(scheme, mode, xi, ntx, eta, nte, ca, cb, dt, st);
+}
+
+cudaError_t batch_direction_fp64(int scheme, int dir, const PassTables& t, int ntiles, cudaStream_t st) {
+  return batch_one_direction<double, double>(scheme, dir, t, ntiles, st);
 }
 
 cudaError_t launch_rhs(int scheme, int precision, const Params& P, const void* Q,

@@ -55,4 +55,10 @@ cudaError_t batch_fp32(int scheme, bool mixed, int mode, const PassTables& xi, i
                : batch_dispatch<float, float>(scheme, mode, xi, ntx, eta, nte, ca, cb, dt, st);
 }
 
+cudaError_t batch_direction_fp32(int scheme, bool mixed, int dir, const PassTables& t, int ntiles,
+                                 cudaStream_t st) {
+  return mixed ? batch_one_direction<float, double>(scheme, dir, t, ntiles, st)
+               : batch_one_direction<float, float>(scheme, dir, t, ntiles, st);
+}
+
 }  // namespace fsp

@@ -36,7 +36,7 @@ struct TileShape {
   static constexpr bool SPLIT_MET = !std::is_same<Real, Acc>::value;
   static constexpr size_t smem_bytes() {
     return sizeof(Real) * ((size_t)(4 + 7) * NN + (SPLIT_MET ? 2 * NN : 0)) +
-           sizeof(Acc) * ((size_t)(4 + 2) * NN + (size_t)4 * NW + (NMP == 2 ? (size_t)8 * NW : 0));
+           sizeof(Acc) * ((size_t)(4 + 2) * NN + (size_t)4 * NW + (NMP == 2 ? (size_t)8 * NW : 0) + NL);
   }
 };
 
@@ -64,16 +64,17 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
   Acc* sMa = sE + 4 * NN;                                // [2][NN] metrics (flux arithmetic)
   Acc* sH = sMa + 2 * NN;                                // [4][NW] h at interfaces
   Acc* sF = sH + 4 * NW;                                 // [8][NW] f+-_mid (two midpoints)
-  Real* sQ = reinterpret_cast<Real*>(sF + (Sh::NMP == 2 ? 8 * NW : 0));  // [4][NN]
+  Real* sQ = reinterpret_cast<Real*>(sF + (Sh::NMP == 2 ? 8 * NW : 0) + NL);  // [4][NN] (after A^)
   Real* sP = sQ + 4 * NN;                                // [7][NN] primitives
   Real* sMr = Sh::SPLIT_MET ? sP + 7 * NN : nullptr;     // [2][NN] metrics in Real
+  Acc* sA = reinterpret_cast<Acc*>(smem_raw) + 6 * NN + 4 * NW + (Sh::NMP == 2 ? 8 * NW : 0);  // [NL] A^
 
   const int n = DIR == 0 ? P.ni : P.nj;
   const int nlines = DIR == 0 ? P.nj : P.ni;
   const int line0 = by * NL;
   const int base = bx * T;
   const Real gamma = Real(P.gamma);
-  const Real eps = sizeof(Real) == 8 ? Real(P.eps) : Real(fmax(P.eps, 1e-30));
+  const Real eps = sizeof(Real) == 8 ? from_f64<Real>(P.eps) : from_f64<Real>(P.eps < 1e-30 ? 1e-30 : P.eps);
   const long long plane = (long long)P.nj * P.ld;
 
   auto SI = [](int l, int s) { return DIR == 0 ? l * NP + s : s * NL + l; };
@@ -83,6 +84,11 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     else return sMa[c * NN + o];
   };
 
+  // A^ = alpha x line maximum, once per line (Section 2.3)
+  if (threadIdx.x < NL) {
+    const int line = line0 + threadIdx.x;
+    sA[threadIdx.x] = line < nlines ? Acc(P.alpha * lam[line]) : Acc(0);
+  }
   // ---- phase 1: nodes ----
   for (int k = threadIdx.x; k < NN; k += Sh::THREADS) {
     const int l = DIR == 0 ? k / NP : k % NL;
@@ -98,15 +104,16 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const Prim<Real> w = prim_of(q, gamma);
     // E^ = mx E + my F with the metric products in Acc
     const Real p = (gamma - Real(1)) * (q[3] - q[0] * w.h2);
-    const Acc U = Acc(mx) * Acc(w.u) + Acc(my) * Acc(w.v);
+    const Acc amx = from_f64<Acc>(mx), amy = from_f64<Acc>(my);
+    const Acc U = amx * Acc(w.u) + amy * Acc(w.v);
     const int o = SI(l, s);
     sE[0 * NN + o] = Acc(q[0]) * U;
-    sE[1 * NN + o] = Acc(q[1]) * U + Acc(mx) * Acc(p);
-    sE[2 * NN + o] = Acc(q[2]) * U + Acc(my) * Acc(p);
+    sE[1 * NN + o] = Acc(q[1]) * U + amx * Acc(p);
+    sE[2 * NN + o] = Acc(q[2]) * U + amy * Acc(p);
     sE[3 * NN + o] = Acc(q[3] + p) * U;
-    sMa[o] = Acc(mx);
-    sMa[NN + o] = Acc(my);
-    if constexpr (Sh::SPLIT_MET) { sMr[o] = Real(mx); sMr[NN + o] = Real(my); }
+    sMa[o] = amx;
+    sMa[NN + o] = amy;
+    if constexpr (Sh::SPLIT_MET) { sMr[o] = from_f64<Real>(mx); sMr[NN + o] = from_f64<Real>(my); }
 #pragma unroll
     for (int v = 0; v < 4; ++v) sQ[v * NN + o] = q[v];
     sP[0 * NN + o] = w.u; sP[1 * NN + o] = w.v; sP[2 * NN + o] = w.c; sP[3 * NN + o] = w.cinv;
@@ -121,7 +128,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const int line = line0 + l;
     const int p = PLO + pi;
     if (line >= nlines || base + p > n) continue;
-    const Acc A = Acc(P.alpha * lam[line]);
+    const Acc A = sA[l];
     const int c0 = p + 4;  // staged position of node p
     const int o0 = SI(l, c0), o1 = SI(l, c0 + 1);
 
@@ -188,7 +195,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const Real* q = Qs[side];
-      const Real rinv = Real(1) / q[0];
+      const Real rinv = recip(q[0]);
       const Real u = q[1] * rinv, v = q[2] * rinv;
       const Real pr = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
       const Acc U = mmx * Acc(u) + mmy * Acc(v);
@@ -231,7 +238,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
       const int line = line0 + l;
       const int p = PLO + pi;
       if (line >= nlines || p < -1 || p > T - 1 || base + p > n - 1) continue;
-      const Acc A = Acc(P.alpha * lam[line]);
+      const Acc A = sA[l];
       const int c0 = p + 4;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -267,7 +274,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
 #pragma unroll
       for (int v = 0; v < 4; ++v) Dout[v * plane + o] = R[v];
     } else {
-      const Acc mJ = Acc(-1.0 / met_at(P, 4, i, j));
+      const Acc mJ = -recip(from_f64<Acc>(met_at(P, 4, i, j)));
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const Acc d = (Dacc[v * plane + o] + R[v]) * mJ;
@@ -429,6 +436,25 @@ cudaError_t batch_dispatch(int scheme, int mode, const PassTables& xi, int ntx, 
     default:  return batch_scheme<S52, Real, Acc>(mode, xi, ntx, eta, nte, ca, cb, dt, st);
   }
 }
+
+// One direction of every block into dout (mode 0 tiles), with the current line maxima.
+template <typename Real, typename Acc>
+cudaError_t batch_one_direction(int scheme, int dir, const PassTables& t, int ntiles, cudaStream_t st) {
+  const BatchPass<Real, Acc> B = typed_pass<Real, Acc>(t);
+  switch (scheme * 2 + dir) {
+    case 0: return launch_sweep_batch<S31, 0, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
+    case 1: return launch_sweep_batch<S31, 1, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
+    case 2: return launch_sweep_batch<S32, 0, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
+    case 3: return launch_sweep_batch<S32, 1, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
+    case 4: return launch_sweep_batch<S51, 0, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
+    case 5: return launch_sweep_batch<S51, 1, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
+    case 6: return launch_sweep_batch<S52, 0, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
+    default: return launch_sweep_batch<S52, 1, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
+  }
+}
+cudaError_t batch_direction_fp64(int scheme, int dir, const PassTables& t, int ntiles, cudaStream_t st);
+cudaError_t batch_direction_fp32(int scheme, bool mixed, int dir, const PassTables& t, int ntiles,
+                                 cudaStream_t st);
 
 cudaError_t batch_fp64(int scheme, int mode, const PassTables& xi, int ntx, const PassTables& eta, int nte,
                        double ca, double cb, double dt, cudaStream_t st);

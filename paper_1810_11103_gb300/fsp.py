@@ -121,6 +121,7 @@ def lib():
                 "fsp_batch_metrics": (ctypes.c_int, [_P, _P]),
                 "fsp_batch_rhs": (ctypes.c_int, [_P, ctypes.POINTER(_P), _P]),
                 "fsp_batch_rk3_step": (ctypes.c_int, [_P, ctypes.c_double, _P]),
+                "fsp_batch_flux_difference": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), _P]),
                 "fsp_batch_capture_graph": (ctypes.c_int, [_P, ctypes.c_double, _P]),
                 "fsp_batch_destroy": (ctypes.c_int, [_P]),
             }
@@ -317,6 +318,12 @@ class Batch:
     def rhs(self, out=None, stream=None):
         out = [torch.empty_like(q) for q in self.Q] if out is None else out
         _check("fsp_batch_rhs", lib().fsp_batch_rhs(self._h, self._ptrs(out), _stream(stream)))
+        return out
+
+    def flux_difference(self, dir: int, out, stream=None):
+        """One direction of every block into out[b] (after a rhs() call on this handle)."""
+        _check("fsp_batch_flux_difference", lib().fsp_batch_flux_difference(self._h, int(dir), self._ptrs(out),
+                                                                            _stream(stream)))
         return out
 
     def rk3_step(self, dt: float, stream=None):
