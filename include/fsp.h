@@ -207,6 +207,40 @@ fsp_status fsp_norms(const fsp_block* blk, int precision, const void* A, const v
                      double* out, void* stream);
 
 /*
+ * ---- Discrete adjoint (FP64) --------------------------------------------------------
+ * Vector-Jacobian products of the right-hand side, of one RK3 step and of the metrics, for
+ * gradients of a scalar functional with respect to the state and the grid coordinates.
+ * The paper has no adjoint; these are the exact reverse of the discrete operators above:
+ * every nonlinear step of fsp_rhs (characteristic WENO with the mapped weights, the split
+ * fluxes, the per-line maxima) is differentiated, so free-stream preservation carries into
+ * the sensitivities.  At non-smooth points the derivative of |x| at 0 is +1, the mapping
+ * branch is taken as in the forward pass, and the derivative of a line maximum goes to the
+ * lowest index attaining it.  Adjoint outputs are accumulated (+=) into the caller's
+ * buffers, which the caller zeroes.  The workspace must hold fsp_vjp_workspace_size bytes.
+ */
+fsp_status fsp_vjp_workspace_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes);
+
+/* Q_bar += (d dQdt / dQ)^T dQdt_bar and metrics_bar += (d dQdt / dM)^T dQdt_bar over the
+ * haloed metric array (metrics_bar nullable: the metric part is then discarded).  Ghost
+ * contributions go back to the interior nodes they were formed from (periodic, transmissive,
+ * slip wall with its normal, far field; Dirichlet ghosts carry none). */
+fsp_status fsp_rhs_vjp(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                       const void* Q, const void* dQdt_bar, void* Q_bar, double* metrics_bar,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Reverse of fsp_rk3_step at the step's input state Q_n: on entry Q_bar = dJ/dQ^{n+1}, on
+ * return dJ/dQ^n; metrics_bar (nullable) += the step's metric adjoint.  The two stage states
+ * are recomputed from Q_n. */
+fsp_status fsp_rk3_step_vjp(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                            const void* Q_n, double dt, void* Q_bar, double* metrics_bar, void* ws,
+                            size_t ws_bytes, void* stream);
+
+/* x_bar, y_bar += (d metrics / d(x, y))^T metrics_bar: the reverse of fsp_metrics through
+ * the ghost-coordinate rule (periodic offsets are constants). */
+fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const double* x, const double* y,
+                           const double* metrics_bar, double* x_bar, double* y_bar, void* stream);
+
+/*
  * fsp_fma_peak -- throughput probe of the FP64 (precision FSP_FP64) or FP32 FMA pipe:
  * launches `blocks` x 256 threads, each running `iters` x 8 independent FMA chains, and
  * writes the chains' sum to sink[blocks * 256].  The floating-point operations done are

@@ -22,24 +22,6 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// Per node |U^| + c|k^| of both directions (and the CFL rate) in the state's arithmetic:
-// the splitting needs A^ constant along a line, not any particular precision, so the FP32
-// paths take their line maxima in float.
-template <typename Real>
-__device__ __forceinline__ void node_speeds(const Params& P, const Real* __restrict__ Q, int i, int j,
-                                            double& sx, double& se, double& rate) {
-  const long long plane = (long long)P.nj * P.ld, o = (long long)j * P.ld + i;
-  Real q[4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) q[v] = Q[v * plane + o];
-  const Real g = from_f64<Real>(P.gamma);
-  const Real a = spectral_radius(q, from_f64<Real>(met_at(P, 0, i, j)), from_f64<Real>(met_at(P, 1, i, j)), g);
-  const Real b = spectral_radius(q, from_f64<Real>(met_at(P, 2, i, j)), from_f64<Real>(met_at(P, 3, i, j)), g);
-  sx = (double)a;
-  se = (double)b;
-  rate = (double)((a + b) * recip(from_f64<Real>(met_at(P, 4, i, j))));
-}
-
 template <typename Real>
 __global__ void __launch_bounds__(256) lambda_kernel(Params P, const Real* __restrict__ Q,
                                                      double* __restrict__ lam_xi,

@@ -114,6 +114,10 @@ def lib():
                 "fsp_cfl_dt": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_norms": (ctypes.c_int, [B, ctypes.c_int, _P, _P, _P, _P]),
                 "fsp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+                "fsp_vjp_workspace_size": (ctypes.c_int, [C, B, ctypes.POINTER(ctypes.c_size_t)]),
+                "fsp_rhs_vjp": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+                "fsp_rk3_step_vjp": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P]),
+                "fsp_metrics_vjp": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P, _P]),
                 "fsp_batch_create": (ctypes.c_int, [C, ctypes.c_int, B, ctypes.POINTER(ctypes.c_int),
                                                     ctypes.POINTER(_Link), ctypes.POINTER(ctypes.c_void_p)]),
                 "fsp_batch_bind": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -184,6 +188,50 @@ def workspace_size(cfg: Config, ni: int, nj: int, ld: Optional[int] = None) -> i
 def workspace(cfg: Config, Q: torch.Tensor) -> torch.Tensor:
     b = block_of(cfg, Q)
     return torch.empty(workspace_size(cfg, b.ni, b.nj, b.ld), dtype=torch.uint8, device=Q.device)
+
+
+def vjp_workspace(cfg: Config, Q: torch.Tensor) -> torch.Tensor:
+    b = block_of(cfg, Q)
+    n = ctypes.c_size_t()
+    _check("fsp_vjp_workspace_size", lib().fsp_vjp_workspace_size(ctypes.byref(cfg._c()), ctypes.byref(b),
+                                                                   ctypes.byref(n)))
+    return torch.empty(int(n.value), dtype=torch.uint8, device=Q.device)
+
+
+def rhs_vjp(cfg: Config, M: torch.Tensor, Q: torch.Tensor, gbar: torch.Tensor, Qbar=None, Mbar=None, ws=None,
+            stream=None):
+    """(Qbar, Mbar) += the adjoint of dQ/dt = rhs(M, Q) applied to gbar (FP64)."""
+    b = block_of(cfg, Q)
+    Qbar = torch.zeros_like(Q) if Qbar is None else Qbar
+    Mbar = torch.zeros_like(M) if Mbar is None else Mbar
+    ws = vjp_workspace(cfg, Q) if ws is None else ws
+    _check("fsp_rhs_vjp", lib().fsp_rhs_vjp(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M), _ptr(Q),
+                                            _ptr(gbar.contiguous()), _ptr(Qbar), _ptr(Mbar), _ptr(ws), ws.numel(),
+                                            _stream(stream)))
+    return Qbar, Mbar
+
+
+def rk3_step_vjp(cfg: Config, M: torch.Tensor, Qn: torch.Tensor, dt: float, Qbar: torch.Tensor, Mbar=None,
+                 ws=None, stream=None):
+    """In place: Qbar (dJ/dQ^{n+1} on entry) becomes dJ/dQ^n; Mbar += the metric adjoint."""
+    b = block_of(cfg, Qn)
+    ws = vjp_workspace(cfg, Qn) if ws is None else ws
+    _check("fsp_rk3_step_vjp", lib().fsp_rk3_step_vjp(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M), _ptr(Qn),
+                                                      float(dt), _ptr(Qbar), _ptr(Mbar), _ptr(ws), ws.numel(),
+                                                      _stream(stream)))
+    return Qbar, Mbar
+
+
+def metrics_vjp(cfg: Config, x: torch.Tensor, y: torch.Tensor, Mbar: torch.Tensor, xbar=None, ybar=None,
+                stream=None):
+    """(xbar, ybar) += the adjoint of the metrics applied to Mbar."""
+    nj, ni = x.shape
+    xbar = torch.zeros_like(x) if xbar is None else xbar
+    ybar = torch.zeros_like(y) if ybar is None else ybar
+    _check("fsp_metrics_vjp", lib().fsp_metrics_vjp(ctypes.byref(cfg._c()), ctypes.byref(_block_shape(cfg, ni, nj)),
+                                                    _ptr(x.contiguous()), _ptr(y.contiguous()), _ptr(Mbar.contiguous()),
+                                                    _ptr(xbar), _ptr(ybar), _stream(stream)))
+    return xbar, ybar
 
 
 def metrics(cfg: Config, x: torch.Tensor, y: torch.Tensor, out=None, stream=None) -> torch.Tensor:
