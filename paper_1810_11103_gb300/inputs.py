@@ -293,3 +293,87 @@ def randomize_local(x, y, amp, seed, block=0):
     s1 = 2.0 * amp * (r1 - 0.5) * b
     s2 = 2.0 * amp * (r2 - 0.5) * (1.0 - b)
     return x + s1 * dxi[0] + s2 * deta[0], y + s1 * dxi[1] + s2 * deta[1]
+
+
+# ----------------------------------------------------------------------------------------
+# Shock-vortex interaction (Section 6.3 (4)) on a smooth stretched grid
+# ----------------------------------------------------------------------------------------
+def _sinh_map(n: int, lo: float, hi: float, beta: float):
+    """n nodes on [lo, hi] clustered around 0 by x = c sinh(beta (s - s0)), s uniform in
+    [0, 1]; s0 and c are fixed by x(0) = lo, x(1) = hi (lo < 0 < hi).  The ratio of
+    neighbouring spacings is at most exp(beta / (n - 1))."""
+    a, b = 0.0, 1.0
+    for _ in range(200):                      # bisection on sinh(beta s0) / sinh(beta (1 - s0)) = -lo / hi
+        s0 = 0.5 * (a + b)
+        if math.sinh(beta * s0) * hi < -lo * math.sinh(beta * (1.0 - s0)):
+            a = s0
+        else:
+            b = s0
+    c = hi / math.sinh(beta * (1.0 - s0))
+    s = np.arange(n, dtype=np.float64) / (n - 1)
+    x = c * np.sinh(beta * (s - s0))
+    x[0], x[-1] = lo, hi
+    return s, x, c * beta * np.cosh(beta * (s - s0)) / (n - 1)
+
+
+def shock_vortex_grid(n: int = 512, nj: int | None = None, lo=(-20.0, -15.0), hi=(10.0, 15.0),
+                      beta: float = 3.0, warp: float = 0.1, waves: int = 4):
+    """The domain of Section 6.3 (4), [-20, 10] x [-15, 15], with x(xi) clustered at the
+    shock (x = 0) and y(eta) at y = 0 by a sinh stretching, plus a smooth warp of
+    ``warp`` times the local spacing, sin(2 pi waves s) sin(2 pi waves t) in both
+    coordinates, which vanishes on the four boundaries.  Returns x, y of shape (nj, n)."""
+    nj = n if nj is None else nj
+    s, xs, hx = _sinh_map(n, lo[0], hi[0], beta)
+    t, ys, hy = _sinh_map(nj, lo[1], hi[1], beta)
+    w = np.sin(2.0 * math.pi * waves * s)[None, :] * np.sin(2.0 * math.pi * waves * t)[:, None]
+    x = xs[None, :] + warp * hx[None, :] * w
+    y = ys[:, None] + warp * hy[:, None] * w
+    return x, y
+
+
+def shock_vortex_state(x, y, mach: float = 1.1, strength: float = 0.4, center=(4.0, 0.0),
+                       gamma: float = GAMMA) -> np.ndarray:
+    """Stationary normal shock at x = 0 with an isentropic vortex ahead of it (Section 6.3
+    (4)).  Upstream (x > 0): (rho, u, v, p) = (1, -1, 0, 1/(gamma M^2)); downstream from the
+    Rankine-Hugoniot relations.  Vortex: u_theta = G r e^{(1 - r^2)/2},
+    T = 1 - (gamma - 1)/2 M^2 G^2 e^{1 - r^2}, rho = T^{1/(gamma-1)}, p = rho T/(gamma M^2)
+    (the M^2 factor makes dp/dr = rho u_theta^2 / r hold)."""
+    m2 = mach * mach
+    p1 = 1.0 / (gamma * m2)
+    rho2 = (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (m2 - 1.0))
+    u2 = -1.0 / rho2
+    dx, dy = x - center[0], y - center[1]
+    e = np.exp(1.0 - dx * dx - dy * dy)
+    T = 1.0 - 0.5 * (gamma - 1.0) * m2 * strength * strength * e
+    rho_v = T ** (1.0 / (gamma - 1.0))
+    g = strength * np.sqrt(e)                  # u_theta / r
+    up = x > 0.0
+    rho = np.where(up, rho_v, rho2)
+    u = np.where(up, -1.0 - g * dy, u2)
+    v = np.where(up, g * dx, 0.0)
+    p = np.where(up, rho_v * T * p1, p2)
+    return conservative(rho, u, v, p, gamma)
+
+
+def shock_vortex_bc(mach: float = 1.1, gamma: float = GAMMA):
+    """Boundary kinds and states of the shock-vortex case: transmissive outflow at x = -20
+    (face 0), the upstream state imposed at x = 10 (face 1), transmissive at y = +-15."""
+    up = conservative(1.0, -1.0, 0.0, 1.0 / (gamma * mach * mach), gamma)
+    return (1, 2, 1, 1), np.tile(up, (4, 1))
+
+
+def smooth_field(shape, seed: int, modes: int = 3, block: int = 11) -> np.ndarray:
+    """A smooth random field on an (nj, ni) index grid: a sum of modes x modes products of
+    sines with seeded amplitudes and phases, peak value about 1."""
+    nj, ni = shape
+    r = uniform(seed, block, 4 * modes * modes, 0)
+    s = np.arange(ni, dtype=np.float64) / max(ni - 1, 1)
+    t = np.arange(nj, dtype=np.float64) / max(nj - 1, 1)
+    out = np.zeros((nj, ni))
+    for a in range(modes):
+        for b in range(modes):
+            k = 4 * (a * modes + b)
+            amp, ph1, ph2 = 2.0 * r[k] - 1.0, 2.0 * math.pi * r[k + 1], 2.0 * math.pi * r[k + 2]
+            out += amp * np.sin(math.pi * (a + 1) * s + ph1)[None, :] * np.sin(math.pi * (b + 1) * t + ph2)[:, None]
+    return out / max(np.abs(out).max(), 1e-300)
