@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--all-precisions", action=argparse.BooleanOptionalAction, default=True,
                     help="also measure the other two precisions and report them beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint cost measurement")
     ap.add_argument("--profile", choices=list(PRECISIONS), default=None,
                     help="profiling run for ncu: build the cylinder batch in this precision, evaluate one "
                          "right-hand side, then launch the batched xi sweep three times; no timing")
@@ -407,6 +408,62 @@ def measure_vortex(args, prec, C):
     }
 
 
+def measure_adjoint(args, C, nsteps=200, every=14):
+    """Adjoint cost on the shock-vortex case (512 x 512 stretched grid, Mach 1.1 shock plus
+    vortex, WENOIU5-1MP, FP64): each adjoint entry point against its forward, and the
+    gradient of the pressure functional over a 200-step march at CFL 0.5 with checkpoints
+    every 14 steps (forward with checkpoints + reverse sweep with segment recompute)
+    against the plain 200-step march."""
+    import numpy as np
+    torch, fsp = C.torch, C.fsp
+    from paper_1810_11103_gb300 import autograd as AD
+    from paper_1810_11103_gb300 import inputs as I
+    from paper_1810_11103_gb300 import objectives as OBJ
+    x, y = I.shock_vortex_grid(512)
+    q0 = I.shock_vortex_state(x, y)
+    bc, st = I.shock_vortex_bc()
+    cfg = fsp.Config.from_dict(dict(scheme=args.scheme, bc=bc, bc_state=st, eps=1e-6))
+    gx, gy = torch.as_tensor(x, device=C.dev), torch.as_tensor(y, device=C.dev)
+    Q = torch.as_tensor(q0, device=C.dev)
+    M = fsp.metrics(cfg, gx, gy)
+    ws, vws = fsp.workspace(cfg, Q), fsp.vjp_workspace(cfg, Q)
+    R, Qb, Mb = torch.empty_like(Q), torch.zeros_like(Q), torch.zeros_like(M)
+    g = torch.as_tensor(I.smooth_field(x.shape, 7), device=C.dev).expand(4, -1, -1).contiguous()
+    dts, _ = AD.cfl_schedule(cfg, M, Q, nsteps, 0.5)
+    dt = dts[0]
+    Qs = Q.clone()
+    reps = 20
+    for f in (lambda: fsp.rhs(cfg, M, Q, out=R, ws=ws), lambda: fsp.rhs_vjp(cfg, M, Q, g, Qb, Mb, ws=vws)):
+        f()
+    t_rhs = C.timed(lambda: fsp.rhs(cfg, M, Q, out=R, ws=ws), reps, flush=True) / reps
+    t_rhs_vjp = C.timed(lambda: fsp.rhs_vjp(cfg, M, Q, g, Qb, Mb, ws=vws), reps, flush=True) / reps
+    t_rk3 = C.timed(lambda: fsp.rk3_step(cfg, M, Qs, dt, ws=ws), reps, flush=True) / reps
+    t_rk3_vjp = C.timed(lambda: fsp.rk3_step_vjp(cfg, M, Q, dt, Qb, Mb, ws=vws), reps, flush=True) / reps
+    win = OBJ.window_of(x)
+
+    def march():
+        Qm = Q.clone()
+        for d in dts:
+            fsp.rk3_step(cfg, M, Qm, d, ws=ws)
+
+    def gradient():
+        ax, ay, aq = gx.clone().requires_grad_(True), gy.clone().requires_grad_(True), Q.clone().requires_grad_(True)
+        Ma = AD.metrics(cfg, ax, ay)
+        OBJ.shock_vortex_functional(AD.rk3_march(cfg, Ma, aq, dts, every), ax, ay, Ma, win).backward()
+
+    march()
+    gradient()
+    t_fwd = C.timed(march, 1)
+    t_grad = C.timed(gradient, 1)
+    return {
+        "workload": f"shock_vortex512: 512x512 stretched grid, Mach 1.1 shock + vortex, {SCHEME_NAMES[args.scheme]}, "
+                    f"FP64, {nsteps} RK3 steps at CFL 0.5, checkpoint every {every}",
+        "rhs_ms": 1e3 * t_rhs, "rhs_vjp_ms": 1e3 * t_rhs_vjp, "rhs_vjp_over_rhs": t_rhs_vjp / t_rhs,
+        "rk3_step_ms": 1e3 * t_rk3, "rk3_step_vjp_ms": 1e3 * t_rk3_vjp, "rk3_step_vjp_over_rk3_step": t_rk3_vjp / t_rk3,
+        "march_forward_s": t_fwd, "march_gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd,
+    }
+
+
 def profile_run(args, prec):
     """Minimal launch sequence for a profiler: metrics, one right-hand side (line maxima,
     xi sweep, eta sweep), then three launches of the batched xi sweep alone."""
@@ -463,6 +520,7 @@ def main():
         for p in PRECISIONS:
             if p != args.precision:
                 others[p] = measure(p)
+    adjoint = None if args.no_adjoint else measure_adjoint(args, C)
     if rank == 0:
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
@@ -481,6 +539,8 @@ def main():
                 "e2e": r["e2e"]["value"], "roofline": r["roofline"], "clocks": r["clocks"]}
         if "per_block_fp64" in head:
             line["per_block_fp64"] = head["per_block_fp64"]
+        if not args.no_adjoint:
+            line["adjoint"] = adjoint
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

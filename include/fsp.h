@@ -229,11 +229,27 @@ fsp_status fsp_rhs_vjp(const fsp_config* cfg, const fsp_block* blk, const double
                        void* ws, size_t ws_bytes, void* stream);
 
 /* Reverse of fsp_rk3_step at the step's input state Q_n: on entry Q_bar = dJ/dQ^{n+1}, on
- * return dJ/dQ^n; metrics_bar (nullable) += the step's metric adjoint.  The two stage states
- * are recomputed from Q_n. */
+ * return dJ/dQ^n; metrics_bar (nullable) += the step's metric adjoint.  The stages are
+ * recomputed from Q_n (three right-hand sides, recorded in the workspace). */
 fsp_status fsp_rk3_step_vjp(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
                             const void* Q_n, double dt, void* Q_bar, double* metrics_bar, void* ws,
                             size_t ws_bytes, void* stream);
+
+/* Recorded steps, for reverse sweeps over many steps.  A step tape (fsp_rk3_tape_size
+ * bytes, device memory, 256-byte aligned, owned by the caller) holds the three stage states
+ * Q^n, Q^(1), Q^(2) of one TVD-RK3 step (Section 6, Shu-Osher form), their right-hand sides
+ * and their line maxima.  fsp_rk3_step_record advances Q in place by one step, as
+ * fsp_rk3_step does (stage by stage, so the result may differ from it in the last bits),
+ * and fills the tape; ws holds fsp_workspace_size bytes.  fsp_rk3_step_vjp_tape is the
+ * reverse of that step read from its tape, with the argument meaning of fsp_rk3_step_vjp
+ * and a workspace of fsp_vjp_workspace_size bytes; it runs no forward right-hand side. */
+fsp_status fsp_rk3_tape_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes);
+fsp_status fsp_rk3_step_record(const fsp_config* cfg, const fsp_block* blk, const double* metrics, void* Q,
+                               double dt, void* tape, size_t tape_bytes, void* ws, size_t ws_bytes,
+                               void* stream);
+fsp_status fsp_rk3_step_vjp_tape(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                                 const void* tape, size_t tape_bytes, double dt, void* Q_bar,
+                                 double* metrics_bar, void* ws, size_t ws_bytes, void* stream);
 
 /* x_bar, y_bar += (d metrics / d(x, y))^T metrics_bar: the reverse of fsp_metrics through
  * the ghost-coordinate rule (periodic offsets are constants). */

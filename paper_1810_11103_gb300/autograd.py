@@ -57,22 +57,28 @@ class FspRHS(torch.autograd.Function):
 
 class FspRK3(torch.autograd.Function):
     """Q0 advanced by len(dts) TVD-RK3 steps.  Every ``every``-th state is kept; the
-    backward pass recomputes the states of one segment at a time from its checkpoint and
-    runs the step adjoints over it in reverse, so memory holds about
-    len(dts)/every + every states.  every <= 0 keeps every state."""
+    backward pass replays one segment at a time from its checkpoint, recording each step's
+    stages (fsp_rk3_step_record), and runs the recorded steps' adjoints in reverse
+    (fsp_rk3_step_vjp_tape), so memory holds about len(dts)/every states and every step
+    tapes.  every <= 0 records every step during the forward pass and replays nothing."""
 
     @staticmethod
     def forward(ctx, cfg: fsp.Config, M: torch.Tensor, Q0: torch.Tensor, dts: Sequence[float], every: int):
         _need_fp64(cfg)
         ctx.cfg, ctx.dts = cfg, tuple(float(d) for d in dts)
         n = len(ctx.dts)
-        ctx.every = n if every <= 0 else int(every)
+        ctx.every = max(n, 1) if every <= 0 else int(every)
+        ctx.taped = every <= 0
         M = M.contiguous()
         Q = Q0.detach().clone(memory_format=torch.contiguous_format)
         ws = fsp.workspace(cfg, Q)
         keep = []
         for k, dt in enumerate(ctx.dts):
-            if every <= 0 or k % ctx.every == 0:
+            if ctx.taped:
+                keep.append(fsp.rk3_tape(cfg, Q))
+                fsp.rk3_step_record(cfg, M, Q, dt, keep[-1], ws=ws)
+                continue
+            if k % ctx.every == 0:
                 keep.append(Q.clone())
             fsp.rk3_step(cfg, M, Q, dt, ws=ws)
         ctx.save_for_backward(M, *keep)
@@ -87,19 +93,21 @@ class FspRK3(torch.autograd.Function):
         Mb = torch.zeros_like(M)
         if n == 0:
             return None, Mb, Qb, None, None
-        ws = fsp.workspace(cfg, Qb)
         vws = fsp.vjp_workspace(cfg, Qb)
-        every_state = len(keep) == n
-        seg_len = 1 if every_state else ctx.every
-        for s in range((n - 1) // seg_len, -1, -1):
-            lo, hi = s * seg_len, min(n, (s + 1) * seg_len)
-            states = [keep[s]]
-            for k in range(lo, hi - 1):           # recompute Q_{lo+1} .. Q_{hi-1}
-                Q = states[-1].clone()
-                fsp.rk3_step(cfg, M, Q, dts[k], ws=ws)
-                states.append(Q)
+        if ctx.taped:
+            for k in range(n - 1, -1, -1):
+                fsp.rk3_step_vjp_tape(cfg, M, keep[k], dts[k], Qb, Mb, ws=vws)
+            return None, Mb, Qb, None, None
+        ws = fsp.workspace(cfg, Qb)
+        seg = ctx.every
+        tapes = [fsp.rk3_tape(cfg, Qb) for _ in range(min(seg, n))]
+        for s in range((n - 1) // seg, -1, -1):
+            lo, hi = s * seg, min(n, (s + 1) * seg)
+            Q = keep[s].clone()
+            for k in range(lo, hi):               # replay the segment, recording each step
+                fsp.rk3_step_record(cfg, M, Q, dts[k], tapes[k - lo], ws=ws)
             for k in range(hi - 1, lo - 1, -1):
-                fsp.rk3_step_vjp(cfg, M, states[k - lo], dts[k], Qb, Mb, ws=vws)
+                fsp.rk3_step_vjp_tape(cfg, M, tapes[k - lo], dts[k], Qb, Mb, ws=vws)
         return None, Mb, Qb, None, None
 
 

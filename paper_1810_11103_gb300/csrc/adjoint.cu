@@ -83,6 +83,10 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
   double* sMb = sQb + 4 * NN;                        // [2][NN] metric adjoint
   double* sEb = sMb + 2 * NN;                        // [4][NN] node-flux adjoint
   double* sAb = sEb + 4 * NN;                        // [NL] A^ adjoint
+  double* sTape = sAb + NL;                          // [4][WT][THREADS] WENO tapes
+  Tape tape[4];
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) tape[kc] = Tape{sTape + kc * WT * Sh::THREADS + threadIdx.x, Sh::THREADS};
 
   const int n = DIR == 0 ? P.ni : P.nj;
   const int nlines = DIR == 0 ? P.nj : P.ni;
@@ -162,46 +166,11 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
         Ab += h * (sQ[v * NN + a] - sQ[v * NN + b]);
       }
     }
-    // forward recomputation of the interface
+    // midpoint metrics mm = sum_k c_k m(c0 - 2 + k) and the interface direction
     const int o0 = SI(l, c0), o1 = SI(l, c0 + 1);
     const double mbx = 0.5 * (sM[o0] + sM[o1]), mby = 0.5 * (sM[NN + o0] + sM[NN + o1]);
     const double rn = rsqrt(mbx * mbx + mby * mby);
     const double nx = mbx * rn, ny = mby * rn;
-    double Qs[2][4], dq[2][4][4];
-    Prim<double> wc[2];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int oc = side == 0 ? o0 : o1;
-      Prim<double>& w = wc[side];
-      w.u = sP[0 * NN + oc]; w.v = sP[1 * NN + oc]; w.c = sP[2 * NN + oc]; w.cinv = sP[3 * NN + oc];
-      w.H = sP[4 * NN + oc]; w.b1 = sP[5 * NN + oc]; w.h2 = sP[6 * NN + oc];
-      const double qc[4] = {sQ[oc], sQ[NN + oc], sQ[2 * NN + oc], sQ[3 * NN + oc]};
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int m = a < 2 ? a - 2 : a - 1;
-        if (Sc::r == 2 && m == 2) { dq[side][a][0] = dq[side][a][1] = dq[side][a][2] = dq[side][a][3] = 0.0; continue; }
-        const int o = SI(l, side == 0 ? c0 + m : c0 + 1 - m);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) dq[side][a][v] = sQ[v * NN + o] - qc[v];
-      }
-      Eig<double> E;
-      E.build(w, nx, ny);
-      double Wm[4];
-#pragma unroll
-      for (int kc = 0; kc < 4; ++kc) {
-        double u[5];
-        u[0] = E.project(kc, dq[side][0][0], dq[side][0][1], dq[side][0][2], dq[side][0][3]);
-        u[1] = E.project(kc, dq[side][1][0], dq[side][1][1], dq[side][1][2], dq[side][1][3]);
-        u[2] = 0.0;
-        u[3] = E.project(kc, dq[side][2][0], dq[side][2][1], dq[side][2][2], dq[side][2][3]);
-        u[4] = Sc::r == 3 ? E.project(kc, dq[side][3][0], dq[side][3][1], dq[side][3][2], dq[side][3][3]) : 0.0;
-        Wm[kc] = weno_delta<Sc::r, double>(u, eps, P.ppm, P.linw);
-      }
-      double dQm[4];
-      E.recon(Wm, dQm);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Qs[side][v] = qc[v] + dQm[v];
-    }
     double vx[6], vy[6];
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk) {
@@ -210,45 +179,55 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
       vy[kk] = sM[NN + o];
     }
     const double mmx = mid_interp(P.interp, Sc::r == 3, vx), mmy = mid_interp(P.interp, Sc::r == 3, vy);
-    // split midpoint fluxes, reverse: f = (E^(Qs; mm) + sg A Qs) / 2
-    double Qsb[2][4] = {};
-    double mmxb = 0.0, mmyb = 0.0;
-#pragma unroll
+    double mmxb = 0.0, mmyb = 0.0, nxb = 0.0, nyb = 0.0;
+    // each side: forward once (WENO internals to the tape), then its reverse
+#pragma unroll 1
     for (int side = 0; side < 2; ++side) {
+      const int oc = side == 0 ? o0 : o1;
+      Prim<double> w;
+      w.u = sP[0 * NN + oc]; w.v = sP[1 * NN + oc]; w.c = sP[2 * NN + oc]; w.cinv = sP[3 * NN + oc];
+      w.H = sP[4 * NN + oc]; w.b1 = sP[5 * NN + oc]; w.h2 = sP[6 * NN + oc];
+      const double qc[4] = {sQ[oc], sQ[NN + oc], sQ[2 * NN + oc], sQ[3 * NN + oc]};
+      double dq[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int m = a < 2 ? a - 2 : a - 1;
+        if (Sc::r == 2 && m == 2) { dq[a][0] = dq[a][1] = dq[a][2] = dq[a][3] = 0.0; continue; }
+        const int o = SI(l, side == 0 ? c0 + m : c0 + 1 - m);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) dq[a][v] = sQ[v * NN + o] - qc[v];
+      }
+      Eig<double> E;
+      E.build(w, nx, ny);
+      double Wm[4], dQm[4], Qs[4];
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+        double u[5];
+        u[0] = E.project(kc, dq[0][0], dq[0][1], dq[0][2], dq[0][3]);
+        u[1] = E.project(kc, dq[1][0], dq[1][1], dq[1][2], dq[1][3]);
+        u[2] = 0.0;
+        u[3] = E.project(kc, dq[2][0], dq[2][1], dq[2][2], dq[2][3]);
+        u[4] = Sc::r == 3 ? E.project(kc, dq[3][0], dq[3][1], dq[3][2], dq[3][3]) : 0.0;
+        Wm[kc] = weno_fwd_tape<Sc::r>(u, eps, P.ppm, P.linw, tape[kc]);
+      }
+      E.recon(Wm, dQm);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Qs[v] = qc[v] + dQm[v];
+      // split midpoint flux f = (E^(Qs; mm) + sg A Qs) / 2, reverse
       const double sg = side == 0 ? 1.0 : -1.0;
       const double* fb = side == 0 ? fbp : fbm;
-      double eb[4];
+      double eb[4], Qsb[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         eb[v] = 0.5 * fb[v];
-        Qsb[side][v] += 0.5 * sg * A * fb[v];
-        Ab += 0.5 * sg * fb[v] * Qs[side][v];
+        Qsb[v] = 0.5 * sg * A * fb[v];
+        Ab += 0.5 * sg * fb[v] * Qs[v];
       }
-      flux_bwd(Qs[side], mmx, mmy, gm1, eb, Qsb[side], mmxb, mmyb);
-    }
-    // midpoint metrics: mm = sum_k c_k m(c0 - 2 + k)
-    {
-      double cw[6];
-      if (P.interp == 1) { cw[0] = cw[1] = cw[4] = cw[5] = 0.0; cw[2] = cw[3] = 0.5; }
-      else if (Sc::r == 3) { cw[0] = cw[5] = 3.0 / 256; cw[1] = cw[4] = -25.0 / 256; cw[2] = cw[3] = 150.0 / 256; }
-      else { cw[0] = cw[5] = 0.0; cw[1] = cw[4] = -1.0 / 16; cw[2] = cw[3] = 9.0 / 16; }
-#pragma unroll
-      for (int kk = 0; kk < 6; ++kk) {
-        if (cw[kk] == 0.0) continue;
-        const int o = SI(l, c0 - 2 + kk);
-        atomicAdd(sMb + o, cw[kk] * mmxb);
-        atomicAdd(sMb + NN + o, cw[kk] * mmyb);
-      }
-    }
-    // the two characteristic interpolations, reverse
-    double nxb = 0.0, nyb = 0.0;
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int oc = side == 0 ? o0 : o1;
+      flux_bwd(Qs, mmx, mmy, gm1, eb, Qsb, mmxb, mmyb);
+      // the characteristic interpolation, reverse
       double qcb[4] = {0, 0, 0, 0}, dqb[4][4] = {};
       PrimBar pb{0, 0, 0, 0, 0, 0, 0};
-      side_bwd<Sc::r>(wc[side], nx, ny, dq[side], eps, P.ppm, P.linw, Qsb[side], qcb, dqb, pb, nxb, nyb);
-      const double qc[4] = {sQ[oc], sQ[NN + oc], sQ[2 * NN + oc], sQ[3 * NN + oc]};
+      side_bwd_tape<Sc::r>(E, w, nx, ny, dq, Wm, P.ppm, P.linw, tape, Qsb, qcb, dqb, pb, nxb, nyb);
       prim_bwd(qc, gamma, pb, qcb);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -263,6 +242,20 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
       }
 #pragma unroll
       for (int v = 0; v < 4; ++v) atomicAdd(sQb + v * NN + oc, qcb[v]);
+    }
+    // midpoint metrics, reverse
+    {
+      double cw[6];
+      if (P.interp == 1) { cw[0] = cw[1] = cw[4] = cw[5] = 0.0; cw[2] = cw[3] = 0.5; }
+      else if (Sc::r == 3) { cw[0] = cw[5] = 3.0 / 256; cw[1] = cw[4] = -25.0 / 256; cw[2] = cw[3] = 150.0 / 256; }
+      else { cw[0] = cw[5] = 0.0; cw[1] = cw[4] = -1.0 / 16; cw[2] = cw[3] = 9.0 / 16; }
+#pragma unroll
+      for (int kk = 0; kk < 6; ++kk) {
+        if (cw[kk] == 0.0) continue;
+        const int o = SI(l, c0 - 2 + kk);
+        atomicAdd(sMb + o, cw[kk] * mmxb);
+        atomicAdd(sMb + NN + o, cw[kk] * mmyb);
+      }
     }
     // direction n = mb / |mb|, mb = (m(p) + m(p+1)) / 2
     const double dn = nx * nxb + ny * nyb;
@@ -374,7 +367,7 @@ static cudaError_t launch_vjp_sweep(const Params& P, const double* Q, const doub
   using Sh = TileShape<S, DIR, double, double>;
   const int n = DIR == 0 ? P.ni : P.nj, nlines = DIR == 0 ? P.nj : P.ni;
   dim3 grid((n + Sh::T - 1) / Sh::T, (nlines + Sh::NL - 1) / Sh::NL);
-  const size_t smem = sizeof(double) * (27 * (size_t)Sh::NN + Sh::NL);
+  const size_t smem = sizeof(double) * (27 * (size_t)Sh::NN + Sh::NL + 4 * (size_t)WT * Sh::THREADS);
   auto kern = vjp_sweep_kernel<S, DIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -515,7 +508,26 @@ size_t al(size_t b) { return (b + 255) / 256 * 256; }
 
 // Adjoint workspace, after the forward part of fsp_workspace_size: dQ/dt, a metric-sized
 // scratch, line-maxima adjoints and argmax indices, and four state buffers for the RK3 step.
-struct VjpWs { size_t fwd, dqdt, mbar, abar, arg, t1, t2, t3, gq, total; };
+// One recorded RK3 step: the stage states Q^n, Q^(1), Q^(2), their right-hand sides and
+// their line maxima (xi lines then eta lines).
+struct StepTape { size_t q[3], r[3], lam[3], total; };
+
+StepTape step_tape(const fsp_block& b) {
+  StepTape T;
+  const size_t state = al(4 * (size_t)b.nj * b.ld * sizeof(double));
+  const size_t lam = al(((size_t)b.ni + b.nj) * sizeof(double));
+  size_t o = 0;
+  for (int k = 0; k < 3; ++k) { T.q[k] = o; o += state; }
+  for (int k = 0; k < 3; ++k) { T.r[k] = o; o += state; }
+  for (int k = 0; k < 3; ++k) { T.lam[k] = o; o += lam; }
+  T.total = o;
+  return T;
+}
+
+// Adjoint workspace: the forward workspace, then dQ/dt, a metric adjoint for callers
+// passing none, line-maximum adjoints and argmax indices, two state temporaries and one
+// step tape (fsp_rk3_step_vjp records into it).
+struct VjpWs { size_t fwd, dqdt, mbar, abar, arg, t3, gq, tape, total; };
 
 VjpWs vjp_ws(const fsp_config& c, const fsp_block& b, size_t fwd_bytes) {
   VjpWs L;
@@ -526,11 +538,10 @@ VjpWs vjp_ws(const fsp_config& c, const fsp_block& b, size_t fwd_bytes) {
   L.mbar = L.dqdt + state;
   L.abar = L.mbar + met;
   L.arg = L.abar + al(((size_t)b.ni + b.nj) * sizeof(double));
-  L.t1 = L.arg + al(((size_t)b.ni + b.nj) * sizeof(int));
-  L.t2 = L.t1 + state;
-  L.t3 = L.t2 + state;
+  L.t3 = L.arg + al(((size_t)b.ni + b.nj) * sizeof(int));
   L.gq = L.t3 + state;
-  L.total = L.gq + state;
+  L.tape = L.gq + state;
+  L.total = L.tape + step_tape(b).total;
   (void)c;
   return L;
 }
@@ -563,23 +574,19 @@ extern "C" fsp_status fsp_vjp_workspace_size(const fsp_config* cfg, const fsp_bl
   return FSP_OK;
 }
 
-// gbar -> Qbar (+=), Mbar (+=); ws: the forward workspace followed by the adjoint part
-static fsp_status rhs_vjp_impl(const fsp_config& c, const fsp_block& b, const double* metrics, const double* Q,
-                               const double* gbar, double* Qbar, double* Mbar, char* ws, size_t fwd_bytes,
-                               cudaStream_t st) {
-  const VjpWs L = vjp_ws(c, b, fwd_bytes);
-  double* dqdt = reinterpret_cast<double*>(ws + L.dqdt);
+// The reverse of one right-hand side at Q whose output R = dQ/dt and line maxima lam are
+// given: gbar -> Qbar (+=), Mbar (+=).  Uses the abar and arg parts of the workspace.
+static fsp_status vjp_core(const fsp_config& c, const fsp_block& b, const double* metrics, const double* Q,
+                           const double* R, const double* lam, const double* gbar, double* Qbar, double* Mbar,
+                           char* ws, const VjpWs& L, cudaStream_t st) {
   double* abar = reinterpret_cast<double*>(ws + L.abar);
   int* arg = reinterpret_cast<int*>(ws + L.arg);
-  // forward: line maxima (left at the start of ws) and dQ/dt
-  if (fsp_status s = fsp_rhs(&c, &b, metrics, Q, dqdt, ws, fwd_bytes, st)) return s;
-  const double* lam = reinterpret_cast<const double*>(ws);  // lam_xi[nj], lam_eta[ni]
   const Params P = params_of(c, b, metrics);
   TRY(cudaMemsetAsync(abar, 0, sizeof(double) * (b.ni + b.nj), st));
   TRY(cudaMemsetAsync(arg, 0x7f, sizeof(int) * (b.ni + b.nj), st));
   const long long N = (long long)b.ni * b.nj;
   const int g1 = (int)((N + 255) / 256 < 152 * 8 ? (N + 255) / 256 : 152 * 8);
-  jac_bwd_kernel<<<g1, 256, 0, st>>>(P, gbar, dqdt, Mbar);
+  jac_bwd_kernel<<<g1, 256, 0, st>>>(P, gbar, R, Mbar);
   TRY(cudaGetLastError());
   cudaError_t e;
   switch (c.scheme) {
@@ -594,6 +601,75 @@ static fsp_status rhs_vjp_impl(const fsp_config& c, const fsp_block& b, const do
   TRY(cudaGetLastError());
   // arg_xi is at arg[0..nj), arg_eta at arg[nj..); lambda_bwd reads them by line
   lambda_bwd_kernel<<<(b.ni + b.nj + 255) / 256, 256, 0, st>>>(P, Q, abar, arg, arg + b.nj, Qbar, Mbar);
+  TRY(cudaGetLastError());
+  return FSP_OK;
+}
+
+// gbar -> Qbar (+=), Mbar (+=): the forward right-hand side (for R and the line maxima,
+// left at the start of the forward workspace), then the core
+static fsp_status rhs_vjp_impl(const fsp_config& c, const fsp_block& b, const double* metrics, const double* Q,
+                               const double* gbar, double* Qbar, double* Mbar, char* ws, size_t fwd_bytes,
+                               cudaStream_t st) {
+  const VjpWs L = vjp_ws(c, b, fwd_bytes);
+  double* dqdt = reinterpret_cast<double*>(ws + L.dqdt);
+  if (fsp_status s = fsp_rhs(&c, &b, metrics, Q, dqdt, ws, fwd_bytes, st)) return s;
+  return vjp_core(c, b, metrics, Q, dqdt, reinterpret_cast<const double*>(ws), gbar, Qbar, Mbar, ws, L, st);
+}
+
+static int grid_of(long long n) { return (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8); }
+
+// The stages of one TVD-RK3 step from the tape's Q^n (already in place), each right-hand
+// side and its line maxima kept in the tape; Q^{n+1} written to qout when it is not null.
+static fsp_status record_stages(const fsp_config& c, const fsp_block& b, const double* metrics, char* tape,
+                                double dt, double* qout, char* ws, size_t fwd_bytes, cudaStream_t st) {
+  const StepTape T = step_tape(b);
+  const long long n = 4 * (long long)b.nj * b.ld;
+  const size_t lam_bytes = sizeof(double) * ((size_t)b.ni + b.nj);
+  auto Qk = [&](int k) { return reinterpret_cast<double*>(tape + T.q[k]); };
+  auto Rk = [&](int k) { return reinterpret_cast<double*>(tape + T.r[k]); };
+  for (int k = 0; k < 3; ++k) {
+    if (fsp_status s = fsp_rhs(&c, &b, metrics, Qk(k), Rk(k), ws, fwd_bytes, st)) return s;
+    TRY(cudaMemcpyAsync(tape + T.lam[k], ws, lam_bytes, cudaMemcpyDeviceToDevice, st));
+    if (k == 0) {
+      axpby_kernel<<<grid_of(n), 256, 0, st>>>(n, 1.0, Qk(0), dt, Rk(0), Qk(1));           // Q1 = Qn + dt R0
+    } else if (k == 1) {
+      axpby_kernel<<<grid_of(n), 256, 0, st>>>(n, 1.0, Qk(1), dt, Rk(1), Qk(2));           // Q1 + dt R1
+      axpby_kernel<<<grid_of(n), 256, 0, st>>>(n, 0.75, Qk(0), 0.25, Qk(2), Qk(2));        // Q2
+    } else if (qout) {
+      axpby_kernel<<<grid_of(n), 256, 0, st>>>(n, 1.0, Qk(2), dt, Rk(2), qout);            // Q2 + dt R2
+      axpby_kernel<<<grid_of(n), 256, 0, st>>>(n, 1.0 / 3.0, Qk(0), 2.0 / 3.0, qout, qout);  // Q^{n+1}
+    }
+    TRY(cudaGetLastError());
+  }
+  return FSP_OK;
+}
+
+// The reverse of a recorded step: a (in: dJ/dQ^{n+1}, out: dJ/dQ^n), Mbar +=.
+static fsp_status reverse_stages(const fsp_config& c, const fsp_block& b, const double* metrics,
+                                 const char* tape, double dt, double* a, double* Mbar, char* ws, const VjpWs& L,
+                                 cudaStream_t st) {
+  const StepTape T = step_tape(b);
+  const long long n = 4 * (long long)b.nj * b.ld;
+  const int grid = grid_of(n);
+  auto Qk = [&](int k) { return reinterpret_cast<const double*>(tape + T.q[k]); };
+  auto Rk = [&](int k) { return reinterpret_cast<const double*>(tape + T.r[k]); };
+  auto Lk = [&](int k) { return reinterpret_cast<const double*>(tape + T.lam[k]); };
+  double* t3 = reinterpret_cast<double*>(ws + L.t3);
+  double* gq = reinterpret_cast<double*>(ws + L.gq);
+  // Q^{n+1} = 1/3 Qn + 2/3 (Q2 + dt R(Q2)): Q2bar = 2/3 a + R_Q2^T (2/3 dt a); a -> 1/3 a
+  axpby_kernel<<<grid, 256, 0, st>>>(n, 2.0 / 3.0 * dt, a, 0.0, nullptr, gq);
+  axpby_kernel<<<grid, 256, 0, st>>>(n, 2.0 / 3.0, a, 0.0, nullptr, t3);
+  if (fsp_status s = vjp_core(c, b, metrics, Qk(2), Rk(2), Lk(2), gq, t3, Mbar, ws, L, st)) return s;
+  axpby_kernel<<<grid, 256, 0, st>>>(n, 1.0 / 3.0, a, 0.0, nullptr, a);
+  // Q2 = 3/4 Qn + 1/4 (Q1 + dt R(Q1)): a += 3/4 Q2bar; Q1bar = 1/4 Q2bar + R_Q1^T (dt/4 Q2bar)
+  axpby_kernel<<<grid, 256, 0, st>>>(n, 0.75, t3, 1.0, a, a);
+  axpby_kernel<<<grid, 256, 0, st>>>(n, 0.25 * dt, t3, 0.0, nullptr, gq);
+  axpby_kernel<<<grid, 256, 0, st>>>(n, 0.25, t3, 0.0, nullptr, t3);
+  if (fsp_status s = vjp_core(c, b, metrics, Qk(1), Rk(1), Lk(1), gq, t3, Mbar, ws, L, st)) return s;
+  // Q1 = Qn + dt R(Qn): a += Q1bar + R_Qn^T (dt Q1bar)
+  axpby_kernel<<<grid, 256, 0, st>>>(n, 1.0, t3, 1.0, a, a);
+  axpby_kernel<<<grid, 256, 0, st>>>(n, dt, t3, 0.0, nullptr, gq);
+  if (fsp_status s = vjp_core(c, b, metrics, Qk(0), Rk(0), Lk(0), gq, a, Mbar, ws, L, st)) return s;
   TRY(cudaGetLastError());
   return FSP_OK;
 }
@@ -641,38 +717,54 @@ fsp_status fsp_rk3_step_vjp(const fsp_config* cfg, const fsp_block* blk, const d
     Mb = reinterpret_cast<double*>(w + L.mbar);
     TRY(cudaMemsetAsync(Mb, 0, fsp_metrics_elems(blk) * sizeof(double), st));
   }
-  const long long n = 4 * (long long)blk->nj * blk->ld;
-  const int grid = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
-  const double* Qn = static_cast<const double*>(Q_n);
-  double* a = static_cast<double*>(Q_bar);
-  double* t1 = reinterpret_cast<double*>(w + L.t1);
-  double* t2 = reinterpret_cast<double*>(w + L.t2);
-  double* t3 = reinterpret_cast<double*>(w + L.t3);
-  double* gq = reinterpret_cast<double*>(w + L.gq);
-  // forward stages: Q1 = Qn + dt R(Qn); Q2 = 3/4 Qn + 1/4 (Q1 + dt R(Q1)), kept in t1 / t2
-  if (fsp_status s = fsp_rhs(cfg, blk, metrics, Qn, gq, w, fwd, st)) return s;
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 1.0, Qn, dt, gq, t1);                       // t1 = Q1
-  if (fsp_status s = fsp_rhs(cfg, blk, metrics, t1, gq, w, fwd, st)) return s;
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 1.0, t1, dt, gq, t2);                       // t2 = Q1 + dt R(Q1)
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 0.75, Qn, 0.25, t2, t2);                    // t2 = Q2
-  TRY(cudaGetLastError());
-  // reverse of Q^{n+1} = 1/3 Qn + 2/3 (Q2 + dt R(Q2))
-  // t3 = Q2bar = 2/3 a + R_Q2^T (2/3 dt a); abar_n = 1/3 a (kept in a at the end)
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 2.0 / 3.0 * dt, a, 0.0, nullptr, gq);
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 2.0 / 3.0, a, 0.0, nullptr, t3);
-  if (fsp_status s = rhs_vjp_impl(*cfg, *blk, metrics, t2, gq, t3, Mb, w, fwd, st)) return s;
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 1.0 / 3.0, a, 0.0, nullptr, a);             // a = Qn part
-  // reverse of Q2 = 3/4 Qn + 1/4 (Q1 + dt R(Q1)): Q1bar = 1/4 t3 + R_Q1^T (dt/4 t3)
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 0.75, t3, 1.0, a, a);                       // a += 3/4 Q2bar
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 0.25 * dt, t3, 0.0, nullptr, gq);
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 0.25, t3, 0.0, nullptr, t3);                // t3 = Q1bar (linear part)
-  if (fsp_status s = rhs_vjp_impl(*cfg, *blk, metrics, t1, gq, t3, Mb, w, fwd, st)) return s;
-  // reverse of Q1 = Qn + dt R(Qn): Qn bar += Q1bar + R_Qn^T (dt Q1bar)
-  axpby_kernel<<<grid, 256, 0, st>>>(n, 1.0, t3, 1.0, a, a);
-  axpby_kernel<<<grid, 256, 0, st>>>(n, dt, t3, 0.0, nullptr, gq);
-  if (fsp_status s = rhs_vjp_impl(*cfg, *blk, metrics, Qn, gq, a, Mb, w, fwd, st)) return s;
-  TRY(cudaGetLastError());
+  char* tape = w + L.tape;
+  TRY(cudaMemcpyAsync(tape + step_tape(*blk).q[0], Q_n, 4 * (size_t)blk->nj * blk->ld * sizeof(double),
+                      cudaMemcpyDeviceToDevice, st));
+  if (fsp_status s = record_stages(*cfg, *blk, metrics, tape, dt, nullptr, w, fwd, st)) return s;
+  return reverse_stages(*cfg, *blk, metrics, tape, dt, static_cast<double*>(Q_bar), Mb, w, L, st);
+}
+
+fsp_status fsp_rk3_tape_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes) {
+  size_t fwd = 0;
+  if (fsp_status s = check_vjp(cfg, blk, &fwd)) return s;
+  if (!bytes) return FSP_ERR_INVALID_ARG;
+  *bytes = step_tape(*blk).total;
   return FSP_OK;
+}
+
+fsp_status fsp_rk3_step_record(const fsp_config* cfg, const fsp_block* blk, const double* metrics, void* Q,
+                               double dt, void* tape, size_t tape_bytes, void* ws, size_t ws_bytes, void* stream) {
+  size_t fwd = 0;
+  if (fsp_status s = check_vjp(cfg, blk, &fwd)) return s;
+  if (!dptr(metrics) || !dptr(Q) || !dptr(tape) || !dptr(ws)) return FSP_ERR_INVALID_ARG;
+  if (tape_bytes < step_tape(*blk).total || reinterpret_cast<uintptr_t>(tape) % 256) return FSP_ERR_INVALID_ARG;
+  if (ws_bytes < fwd || reinterpret_cast<uintptr_t>(ws) % 256) return FSP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* t = static_cast<char*>(tape);
+  TRY(cudaMemcpyAsync(t + step_tape(*blk).q[0], Q, 4 * (size_t)blk->nj * blk->ld * sizeof(double),
+                      cudaMemcpyDeviceToDevice, st));
+  return record_stages(*cfg, *blk, metrics, t, dt, static_cast<double*>(Q), static_cast<char*>(ws), fwd, st);
+}
+
+fsp_status fsp_rk3_step_vjp_tape(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
+                                 const void* tape, size_t tape_bytes, double dt, void* Q_bar, double* metrics_bar,
+                                 void* ws, size_t ws_bytes, void* stream) {
+  size_t fwd = 0;
+  if (fsp_status s = check_vjp(cfg, blk, &fwd)) return s;
+  if (!dptr(metrics) || !dptr(tape) || !dptr(Q_bar) || !dptr(ws) || (metrics_bar && !dptr(metrics_bar)))
+    return FSP_ERR_INVALID_ARG;
+  if (tape_bytes < step_tape(*blk).total || reinterpret_cast<uintptr_t>(tape) % 256) return FSP_ERR_INVALID_ARG;
+  const VjpWs L = vjp_ws(*cfg, *blk, fwd);
+  if (ws_bytes < L.total || reinterpret_cast<uintptr_t>(ws) % 256) return FSP_ERR_INVALID_ARG;
+  char* w = static_cast<char*>(ws);
+  cudaStream_t st = (cudaStream_t)stream;
+  double* Mb = metrics_bar;
+  if (!Mb) {
+    Mb = reinterpret_cast<double*>(w + L.mbar);
+    TRY(cudaMemsetAsync(Mb, 0, fsp_metrics_elems(blk) * sizeof(double), st));
+  }
+  return reverse_stages(*cfg, *blk, metrics, static_cast<const char*>(tape), dt, static_cast<double*>(Q_bar), Mb,
+                        w, L, st);
 }
 
 fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const double* x, const double* y,

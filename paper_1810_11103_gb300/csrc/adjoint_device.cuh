@@ -7,118 +7,183 @@
 
 namespace fsp {
 
-// ---- WENO interpolation on centre differences (weno_delta), reverse ------------------
-// u[0], u[1], u[3], u[4]: w_{j-2}-w_j, w_{j-1}-w_j, w_{j+1}-w_j, w_{j+2}-w_j (r = 3;
-// r = 2 uses u[0], u[1], u[3]).  Adds d(out)/du * obar to ub[].
+// ---- WENO with a tape: the forward pass keeps what the reverse pass needs -------------
+// One component's tape, WT slots in shared memory, slot i at p[i * stride]: the stencil
+// differences u (4: offsets -2, -1, +1, +2), b = eps + IS_k (3), the raw weights (3),
+// 1 / sum of the unnormalised weights, 1 / sum of the mapped weights, the interpolant.
+constexpr int WT = 13;
+
+struct Tape {
+  double* p;
+  int stride;
+  __device__ __forceinline__ double& operator[](int i) const { return p[i * stride]; }
+};
+
+// Same arithmetic as weno_delta<R, double>, except that the mapped quotient is formed as
+// num * (1/den) so that the reverse pass reuses the reciprocal.
 template <int R>
-__device__ __forceinline__ void weno_delta_bwd(const double* u, double eps, int ppm, int linw, double obar,
-                                               double* ub) {
+__device__ __forceinline__ double weno_fwd_tape(const double* u, double eps, int ppm, int linw, Tape t) {
+  t[0] = u[0]; t[1] = u[1]; t[2] = u[3]; t[3] = u[4];
+  if constexpr (R == 3) {
+    const double p0 = 0.375 * u[0] - 1.25 * u[1];
+    const double p1 = -0.125 * u[1] + 0.375 * u[3];
+    const double p2 = 0.75 * u[3] - 0.125 * u[4];
+    const double C[3] = {1.0 / 16, 10.0 / 16, 5.0 / 16};
+    if (linw) return C[0] * p0 + C[1] * p1 + C[2] * p2;
+    const double d1 = u[1] - u[0], d2 = -u[1], d3 = u[3], d4 = u[4] - u[3];
+    const double b[3] = {is_b(d2 - d1, 3.0 * d2 - d1, eps), is_b(d3 - d2, d2 + d3, eps),
+                         is_b(d4 - d3, d4 - 3.0 * d3, eps)};
+    const double s[3] = {b[0] * b[0], b[1] * b[1], b[2] * b[2]};
+    const double tt[3] = {C[0] * (s[1] * s[2]), C[1] * (s[0] * s[2]), C[2] * (s[0] * s[1])};
+    const double iS = 1.0 / (tt[0] + tt[1] + tt[2]);
+    const double w[3] = {tt[0] * iS, tt[1] * iS, tt[2] * iS};
+    t[4] = b[0]; t[5] = b[1]; t[6] = b[2]; t[7] = w[0]; t[8] = w[1]; t[9] = w[2]; t[10] = iS;
+    const double p[3] = {p0, p1, p2};
+    double out;
+    if (ppm) {
+      const double K0[3] = {256.0, 256.0 / 100, 256.0 / 25}, K1[3] = {256.0 / 225, 256.0 / 36, 256.0 / 121};
+      double num = 0.0, den = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double q = w[k] - C[k];
+        const double g = C[k] + q * q * q * (nonpos(q) ? K0[k] : K1[k]);
+        num += g * p[k];
+        den += g;
+      }
+      const double rden = 1.0 / den;
+      out = num * rden;
+      t[11] = rden;
+    } else {
+      out = w[0] * p0 + w[1] * p1 + w[2] * p2;
+    }
+    t[12] = out;
+    return out;
+  } else {
+    const double p0 = -0.5 * u[1], p1 = 0.5 * u[3];
+    const double C[2] = {0.25, 0.75};
+    if (linw) return C[0] * p0 + C[1] * p1;
+    const double d1 = u[1] - u[0], d2 = -u[1], d3 = u[3];
+    const double b[2] = {is_b(d2 - d1, 3.0 * d2 - d1, eps), is_b(d3 - d2, d2 + d3, eps)};
+    const double tt[2] = {C[0] * (b[1] * b[1]), C[1] * (b[0] * b[0])};
+    const double iS = 1.0 / (tt[0] + tt[1]);
+    const double w[2] = {tt[0] * iS, tt[1] * iS};
+    t[4] = b[0]; t[5] = b[1]; t[7] = w[0]; t[8] = w[1]; t[10] = iS;
+    const double p[2] = {p0, p1};
+    double out;
+    if (ppm) {
+      const double K0[2] = {4.0, 4.0 / 3}, K1[2] = {-4.0 / 3, -4.0};
+      double num = 0.0, den = 0.0;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const double q = w[k] - C[k];
+        const double g = C[k] - q * q * (nonpos(q) ? K0[k] : K1[k]);
+        num += g * p[k];
+        den += g;
+      }
+      const double rden = 1.0 / den;
+      out = num * rden;
+      t[11] = rden;
+    } else {
+      out = w[0] * p0 + w[1] * p1;
+    }
+    t[12] = out;
+    return out;
+  }
+}
+
+// Reverse of weno_fwd_tape: adds d(out)/du * obar to ub[0], ub[1], ub[3], ub[4] (the
+// layout of weno_delta_bwd), reading the forward values from the tape.
+template <int R>
+__device__ __forceinline__ void weno_bwd_tape(Tape t, int ppm, int linw, double obar, double* ub) {
+  const double u0 = t[0], u1 = t[1], u3 = t[2], u4 = t[3];
   if constexpr (R == 3) {
     const double C[3] = {1.0 / 16, 10.0 / 16, 5.0 / 16};
-    const double p[3] = {0.375 * u[0] - 1.25 * u[1], -0.125 * u[1] + 0.375 * u[3], 0.75 * u[3] - 0.125 * u[4]};
     double pb[3];
-    const double d1 = u[1] - u[0], d2 = -u[1], d3 = u[3], d4 = u[4] - u[3];
-    const double e[3] = {d2 - d1, d3 - d2, d4 - d3};
-    const double f[3] = {3.0 * d2 - d1, d2 + d3, d4 - 3.0 * d3};
     double eb[3] = {0, 0, 0}, fb[3] = {0, 0, 0};
     if (linw) {
+#pragma unroll
       for (int k = 0; k < 3; ++k) pb[k] = obar * C[k];
     } else {
-      double b[3], s[3];
-      for (int k = 0; k < 3; ++k) {
-        b[k] = eps + (13.0 / 12) * e[k] * e[k] + 0.25 * f[k] * f[k];
-        s[k] = b[k] * b[k];
-      }
-      const double t[3] = {C[0] * s[1] * s[2], C[1] * s[0] * s[2], C[2] * s[0] * s[1]};
-      const double S = t[0] + t[1] + t[2];
-      const double iS = 1.0 / S;
-      double w[3] = {t[0] * iS, t[1] * iS, t[2] * iS};
+      const double p[3] = {0.375 * u0 - 1.25 * u1, -0.125 * u1 + 0.375 * u3, 0.75 * u3 - 0.125 * u4};
+      const double b[3] = {t[4], t[5], t[6]};
+      const double w[3] = {t[7], t[8], t[9]};
+      const double iS = t[10];
       double wb[3];
       if (ppm) {
         const double K0[3] = {256.0, 256.0 / 100, 256.0 / 25}, K1[3] = {256.0 / 225, 256.0 / 36, 256.0 / 121};
-        double q[3], K[3], g[3], num = 0, den = 0;
+        const double rden = t[11];
+        const double numb = obar * rden, denb = -obar * t[12] * rden;
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-          q[k] = w[k] - C[k];
-          K[k] = nonpos(q[k]) ? K0[k] : K1[k];
-          g[k] = C[k] + q[k] * q[k] * q[k] * K[k];
-          num += g[k] * p[k];
-          den += g[k];
-        }
-        const double out = num / den;
-        const double numb = obar / den, denb = -obar * out / den;
-        for (int k = 0; k < 3; ++k) {
+          const double q = w[k] - C[k];
+          const double K = nonpos(q) ? K0[k] : K1[k];
+          const double q2K = q * q * K;
+          const double g = C[k] + q2K * q;
           const double gb = numb * p[k] + denb;
-          pb[k] = numb * g[k];
-          wb[k] = gb * 3.0 * q[k] * q[k] * K[k];
+          pb[k] = numb * g;
+          wb[k] = gb * 3.0 * q2K;
         }
       } else {
+#pragma unroll
         for (int k = 0; k < 3; ++k) { wb[k] = obar * p[k]; pb[k] = obar * w[k]; }
       }
       const double dotw = wb[0] * w[0] + wb[1] * w[1] + wb[2] * w[2];
-      double tb[3];
-      for (int k = 0; k < 3; ++k) tb[k] = (wb[k] - dotw) * iS;
-      const double sb[3] = {tb[1] * C[1] * s[2] + tb[2] * C[2] * s[1], tb[0] * C[0] * s[2] + tb[2] * C[2] * s[0],
-                            tb[0] * C[0] * s[1] + tb[1] * C[1] * s[0]};
+      const double tb[3] = {(wb[0] - dotw) * iS * C[0], (wb[1] - dotw) * iS * C[1], (wb[2] - dotw) * iS * C[2]};
+      const double s[3] = {b[0] * b[0], b[1] * b[1], b[2] * b[2]};
+      const double sb[3] = {tb[1] * s[2] + tb[2] * s[1], tb[0] * s[2] + tb[2] * s[0], tb[0] * s[1] + tb[1] * s[0]};
+      const double d1 = u1 - u0, d2 = -u1, d3 = u3, d4 = u4 - u3;
+      const double e[3] = {d2 - d1, d3 - d2, d4 - d3};
+      const double f[3] = {3.0 * d2 - d1, d2 + d3, d4 - 3.0 * d3};
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
         const double bb = sb[k] * 2.0 * b[k];
         eb[k] = bb * (2.0 * 13.0 / 12) * e[k];
         fb[k] = bb * 0.5 * f[k];
       }
     }
-    // e0 = d2 - d1, f0 = 3 d2 - d1, e1 = d3 - d2, f1 = d2 + d3, e2 = d4 - d3, f2 = d4 - 3 d3
     const double d1b = -eb[0] - fb[0];
     const double d2b = eb[0] + 3.0 * fb[0] - eb[1] + fb[1];
     const double d3b = eb[1] + fb[1] - eb[2] - 3.0 * fb[2];
     const double d4b = eb[2] + fb[2];
-    // d1 = u1 - u0, d2 = -u1, d3 = u3, d4 = u4 - u3
     ub[0] += 0.375 * pb[0] - d1b;
     ub[1] += -1.25 * pb[0] - 0.125 * pb[1] + d1b - d2b;
     ub[3] += 0.375 * pb[1] + 0.75 * pb[2] + d3b - d4b;
     ub[4] += -0.125 * pb[2] + d4b;
   } else {
     const double C[2] = {0.25, 0.75};
-    const double p[2] = {-0.5 * u[1], 0.5 * u[3]};
     double pb[2];
-    const double d1 = u[1] - u[0], d2 = -u[1], d3 = u[3];
-    const double e[2] = {d2 - d1, d3 - d2};
-    const double f[2] = {3.0 * d2 - d1, d2 + d3};
     double eb[2] = {0, 0}, fb[2] = {0, 0};
     if (linw) {
-      for (int k = 0; k < 2; ++k) pb[k] = obar * C[k];
+      pb[0] = obar * C[0];
+      pb[1] = obar * C[1];
     } else {
-      double b[2], s[2];
-      for (int k = 0; k < 2; ++k) {
-        b[k] = eps + (13.0 / 12) * e[k] * e[k] + 0.25 * f[k] * f[k];
-        s[k] = b[k] * b[k];
-      }
-      const double t[2] = {C[0] * s[1], C[1] * s[0]};
-      const double S = t[0] + t[1];
-      const double iS = 1.0 / S;
-      const double w[2] = {t[0] * iS, t[1] * iS};
+      const double p[2] = {-0.5 * u1, 0.5 * u3};
+      const double b[2] = {t[4], t[5]};
+      const double w[2] = {t[7], t[8]};
+      const double iS = t[10];
       double wb[2];
       if (ppm) {
         const double K0[2] = {4.0, 4.0 / 3}, K1[2] = {-4.0 / 3, -4.0};
-        double q[2], K[2], g[2], num = 0, den = 0;
+        const double rden = t[11];
+        const double numb = obar * rden, denb = -obar * t[12] * rden;
+#pragma unroll
         for (int k = 0; k < 2; ++k) {
-          q[k] = w[k] - C[k];
-          K[k] = nonpos(q[k]) ? K0[k] : K1[k];
-          g[k] = C[k] - q[k] * q[k] * K[k];
-          num += g[k] * p[k];
-          den += g[k];
-        }
-        const double out = num / den;
-        const double numb = obar / den, denb = -obar * out / den;
-        for (int k = 0; k < 2; ++k) {
+          const double q = w[k] - C[k];
+          const double K = nonpos(q) ? K0[k] : K1[k];
+          const double g = C[k] - q * q * K;
           const double gb = numb * p[k] + denb;
-          pb[k] = numb * g[k];
-          wb[k] = -gb * 2.0 * q[k] * K[k];
+          pb[k] = numb * g;
+          wb[k] = -gb * 2.0 * q * K;
         }
       } else {
         for (int k = 0; k < 2; ++k) { wb[k] = obar * p[k]; pb[k] = obar * w[k]; }
       }
       const double dotw = wb[0] * w[0] + wb[1] * w[1];
-      const double tb[2] = {(wb[0] - dotw) * iS, (wb[1] - dotw) * iS};
-      const double sb[2] = {tb[1] * C[1], tb[0] * C[0]};
+      const double sb[2] = {(wb[1] - dotw) * iS * C[1], (wb[0] - dotw) * iS * C[0]};
+      const double d1 = u1 - u0, d2 = -u1, d3 = u3;
+      const double e[2] = {d2 - d1, d3 - d2};
+      const double f[2] = {3.0 * d2 - d1, d2 + d3};
+#pragma unroll
       for (int k = 0; k < 2; ++k) {
         const double bb = sb[k] * 2.0 * b[k];
         eb[k] = bb * (2.0 * 13.0 / 12) * e[k];
@@ -235,28 +300,17 @@ __device__ __forceinline__ void spectral_bwd(const double q[4], double mx, doubl
   qb[2] += q2b;
 }
 
-// ---- one side of the characteristic WENO interpolation, reverse ----------------------
+// ---- one side of the characteristic WENO interpolation, reverse (taped) ---------------
 // Forward: Q^s = Q_c + R W, W_k = WENO(L_k dQ_m) with L, R at the centre's primitives w
-// and the unit direction (nx, ny).  Given Qsb (adjoint of Q^s), adds the adjoints of the
-// centre state (qcb), of the stencil differences (dqb[a][4], a = offsets -2, -1, +1, +2),
-// of the primitives (pbar) and of the direction (nxb, nyb).
+// and the unit direction (nx, ny); E, W and the WENO tapes (one per characteristic
+// component) come from that forward pass.  Given Qsb (adjoint of Q^s), adds the adjoints
+// of the centre state (qcb), of the stencil differences (dqb[a][4], a = offsets -2, -1,
+// +1, +2), of the primitives (pbar) and of the direction (nxb, nyb).
 template <int R>
-__device__ __forceinline__ void side_bwd(const Prim<double>& w, double nx, double ny, const double dq[4][4],
-                                         double eps, int ppm, int linw, const double* Qsb, double* qcb,
-                                         double dqb[4][4], PrimBar& pbar, double& nxb, double& nyb) {
-  Eig<double> E;
-  E.build(w, nx, ny);
-  // forward characteristic values and interpolants
-  double uu[4][5], W[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    uu[k][0] = E.project(k, dq[0][0], dq[0][1], dq[0][2], dq[0][3]);
-    uu[k][1] = E.project(k, dq[1][0], dq[1][1], dq[1][2], dq[1][3]);
-    uu[k][2] = 0.0;
-    uu[k][3] = E.project(k, dq[2][0], dq[2][1], dq[2][2], dq[2][3]);
-    uu[k][4] = R == 3 ? E.project(k, dq[3][0], dq[3][1], dq[3][2], dq[3][3]) : 0.0;
-    W[k] = weno_delta<R, double>(uu[k], eps, ppm, linw);
-  }
+__device__ __forceinline__ void side_bwd_tape(const Eig<double>& E, const Prim<double>& w, double nx, double ny,
+                                              const double dq[4][4], const double W[4], int ppm, int linw,
+                                              const Tape* tape, const double* Qsb, double* qcb, double dqb[4][4],
+                                              PrimBar& pbar, double& nxb, double& nyb) {
   // Q^s = Q_c + dQ
 #pragma unroll
   for (int v = 0; v < 4; ++v) qcb[v] += Qsb[v];
@@ -286,7 +340,7 @@ __device__ __forceinline__ void side_bwd(const Prim<double>& w, double nx, doubl
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     double ubk[5] = {0, 0, 0, 0, 0};
-    weno_delta_bwd<R>(uu[k], eps, ppm, linw, Wb[k], ubk);
+    weno_bwd_tape<R>(tape[k], ppm, linw, Wb[k], ubk);
     const int mlist[4] = {0, 1, 3, 4};
 #pragma unroll
     for (int aa = 0; aa < 4; ++aa) {

@@ -118,6 +118,11 @@ def lib():
                 "fsp_rhs_vjp": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_rk3_step_vjp": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_metrics_vjp": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P, _P]),
+                "fsp_rk3_tape_size": (ctypes.c_int, [C, B, ctypes.POINTER(ctypes.c_size_t)]),
+                "fsp_rk3_step_record": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, ctypes.c_size_t, _P,
+                                                        ctypes.c_size_t, _P]),
+                "fsp_rk3_step_vjp_tape": (ctypes.c_int, [C, B, _P, _P, ctypes.c_size_t, ctypes.c_double, _P, _P, _P,
+                                                          ctypes.c_size_t, _P]),
                 "fsp_batch_create": (ctypes.c_int, [C, ctypes.c_int, B, ctypes.POINTER(ctypes.c_int),
                                                     ctypes.POINTER(_Link), ctypes.POINTER(ctypes.c_void_p)]),
                 "fsp_batch_bind": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -219,6 +224,36 @@ def rk3_step_vjp(cfg: Config, M: torch.Tensor, Qn: torch.Tensor, dt: float, Qbar
     _check("fsp_rk3_step_vjp", lib().fsp_rk3_step_vjp(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M), _ptr(Qn),
                                                       float(dt), _ptr(Qbar), _ptr(Mbar), _ptr(ws), ws.numel(),
                                                       _stream(stream)))
+    return Qbar, Mbar
+
+
+def rk3_tape(cfg: Config, Q: torch.Tensor) -> torch.Tensor:
+    """An empty step tape for states shaped like Q (device bytes)."""
+    b = block_of(cfg, Q)
+    n = ctypes.c_size_t()
+    _check("fsp_rk3_tape_size", lib().fsp_rk3_tape_size(ctypes.byref(cfg._c()), ctypes.byref(b), ctypes.byref(n)))
+    return torch.empty(int(n.value), dtype=torch.uint8, device=Q.device)
+
+
+def rk3_step_record(cfg: Config, M: torch.Tensor, Q: torch.Tensor, dt: float, tape: torch.Tensor, ws=None,
+                    stream=None) -> torch.Tensor:
+    """One TVD-RK3 step in place on Q, its stages kept in tape."""
+    b = block_of(cfg, Q)
+    ws = workspace(cfg, Q) if ws is None else ws
+    _check("fsp_rk3_step_record", lib().fsp_rk3_step_record(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M), _ptr(Q),
+                                                            float(dt), _ptr(tape), tape.numel(), _ptr(ws), ws.numel(),
+                                                            _stream(stream)))
+    return Q
+
+
+def rk3_step_vjp_tape(cfg: Config, M: torch.Tensor, tape: torch.Tensor, dt: float, Qbar: torch.Tensor, Mbar=None,
+                      ws=None, stream=None):
+    """In place: Qbar (dJ/dQ^{n+1} on entry) becomes dJ/dQ^n for the recorded step."""
+    b = block_of(cfg, Qbar)
+    ws = vjp_workspace(cfg, Qbar) if ws is None else ws
+    _check("fsp_rk3_step_vjp_tape", lib().fsp_rk3_step_vjp_tape(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M),
+                                                                _ptr(tape), tape.numel(), float(dt), _ptr(Qbar),
+                                                                _ptr(Mbar), _ptr(ws), ws.numel(), _stream(stream)))
     return Qbar, Mbar
 
 
