@@ -53,9 +53,10 @@ def parse():
                     help="also measure the other two precisions and report them beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint cost measurement")
-    ap.add_argument("--profile", choices=list(PRECISIONS), default=None,
+    ap.add_argument("--profile", choices=list(PRECISIONS) + ["adjoint"], default=None,
                     help="profiling run for ncu: build the cylinder batch in this precision, evaluate one "
-                         "right-hand side, then launch the batched xi sweep three times; no timing")
+                         "right-hand side, then launch the batched xi sweep three times; 'adjoint': three "
+                         "fsp_rhs_vjp calls on the 512 x 512 shock-vortex case; no timing")
     return ap.parse_args()
 
 
@@ -287,6 +288,8 @@ def measure_cylinder(args, prec, C, per_block=False):
     cfg = fsp.Config.from_dict(cfgd)
     bt = fsp.Batch(cfg, blocks, states, device=C.dev)
     bt.metrics()
+    # tile shapes chosen by timing each variant's pass on this batch (fsp_batch_tune)
+    tiles = {d: dict(zip(("variant", "lines", "outputs_per_line"), t)) for d, t in zip(("xi", "eta"), bt.tune())}
     nodes = sum(b["x"].size for b in blocks)
     # a stable step: CFL 0.3 on the initial state, from the per-block CFL rate
     dts = []
@@ -339,6 +342,7 @@ def measure_cylinder(args, prec, C, per_block=False):
                      "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
                      "kernel_ms": 1e3 * t_k},
         "clocks": clk,
+        "tiles": tiles,
     }
     if per_block:
         # the same FP64 step as a loop of single-block calls (links read as transmissive)
@@ -485,8 +489,32 @@ def profile_run(args, prec):
     bt.close()
 
 
+def profile_adjoint(args):
+    """Minimal launch sequence for a profiler: three right-hand-side adjoints (each a forward
+    right-hand side, then the adjoint kernels) on the 512 x 512 shock-vortex case."""
+    import torch
+    from paper_1810_11103_gb300 import build as B
+    B.build()
+    from paper_1810_11103_gb300 import fsp
+    from paper_1810_11103_gb300 import inputs as I
+    x, y = I.shock_vortex_grid(512)
+    bc, st = I.shock_vortex_bc()
+    cfg = fsp.Config.from_dict(dict(scheme=args.scheme, bc=bc, bc_state=st, eps=1e-6))
+    Q = torch.as_tensor(I.shock_vortex_state(x, y), device="cuda")
+    M = fsp.metrics(cfg, torch.as_tensor(x, device="cuda"), torch.as_tensor(y, device="cuda"))
+    g = torch.as_tensor(I.smooth_field(x.shape, 7), device="cuda").expand(4, -1, -1).contiguous()
+    Qb, Mb, ws = torch.zeros_like(Q), torch.zeros_like(M), fsp.vjp_workspace(cfg, Q)
+    for _ in range(3):
+        fsp.rhs_vjp(cfg, M, Q, g, Qb, Mb, ws=ws)
+    torch.cuda.synchronize()
+    print("profile run done: adjoint, 262144 nodes")
+
+
 def main():
     args = parse()
+    if args.profile == "adjoint":
+        profile_adjoint(args)
+        return
     if args.profile:
         profile_run(args, args.profile)
         return
@@ -533,10 +561,12 @@ def main():
             "roofline": head["roofline"],
             "clocks": head["clocks"],
         }
+        if head.get("tiles"):
+            line["config"]["tiles"] = head["tiles"]
         for p, r in others.items():
             line["fp32_mixed" if p == "mixed" else p] = {
                 "value": r["value"], "unit": UNIT, "dtype": DTYPES[p], "ms_per_step": r["ms_per_step"],
-                "e2e": r["e2e"]["value"], "roofline": r["roofline"], "clocks": r["clocks"]}
+                "e2e": r["e2e"]["value"], "roofline": r["roofline"], "clocks": r["clocks"], "tiles": r.get("tiles")}
         if "per_block_fp64" in head:
             line["per_block_fp64"] = head["per_block_fp64"]
         if not args.no_adjoint:

@@ -276,8 +276,8 @@ fsp_status fsp_fma_peak(int precision, int blocks, int iters, void* sink, void* 
  * layers, corners included.  Line maxima of the splitting are taken per block line.
  * The handle owns its device memory (descriptors, tile tables, per-block line maxima,
  * xi accumulators and RK stage states) from create to destroy; no other call allocates.
- * Each pass runs all blocks in one launch over a table of tiles (NL lines x T nodes, as
- * for one block); ghosts of linked faces are read straight from the neighbour's state,
+ * Each pass runs all blocks in one launch over a table of tiles (NL lines x T nodes, see
+ * fsp_batch_tune); ghosts of linked faces are read straight from the neighbour's state,
  * so no halo copies are made.  Calls on one handle must not overlap.
  */
 typedef struct {
@@ -315,6 +315,26 @@ fsp_status fsp_batch_rk3_step(fsp_batch* b, double dt, void* stream);
  * later fsp_batch_rk3_step calls with the same dt launch as a whole.  The eager step
  * advances the state like any other step. */
 fsp_status fsp_batch_capture_graph(fsp_batch* b, double dt, void* stream);
+
+/* Tile shapes.  Every pass uses 256-thread tiles of NL grid lines; the variant sets NL:
+ *   xi  (dir 0): variant 0, 1, 2 = 2, 1, 4 lines of 128, 256, 64 interfaces;
+ *   eta (dir 1): variant 0, 1, 2 = 8, 4, 16 lines of 32, 64, 16 interfaces.
+ * Results do not depend on the variant (each interface is computed the same way); the
+ * speed does.  fsp_batch_tune picks, for each direction, the fastest variant on this
+ * handle's blocks and bound state: it times five launches of each variant's pass (after two
+ * untimed ones) with CUDA events on `stream` and waits for them.  With table_path non-null
+ * it first looks up a key made of the device name and SM count, the scheme and arithmetic
+ * options and a hash of the block sizes in that text file ("key vx ve ms_xi ms_eta" per
+ * line, '#' comments; the last entry of a key wins).  If it finds the key it applies the
+ * stored choice without timing; otherwise it times and appends the choice.  Changing a
+ * shape synchronises the device and drops a captured graph (capture again after tuning).
+ * Returns FSP_ERR_INVALID_ARG for an unbound handle or an unwritable table (the timed
+ * choice is applied all the same).  fsp_batch_set_tile_shape forces a variant;
+ * fsp_batch_tile_shape reports the current variant, lines per tile and output nodes per
+ * line (any output pointer may be null). */
+fsp_status fsp_batch_tune(fsp_batch* b, const char* table_path, void* stream);
+fsp_status fsp_batch_set_tile_shape(fsp_batch* b, int dir, int variant);
+fsp_status fsp_batch_tile_shape(const fsp_batch* b, int dir, int* variant, int* lines, int* outputs);
 fsp_status fsp_batch_destroy(fsp_batch* b);
 
 #ifdef __cplusplus

@@ -9,8 +9,11 @@
 // every block; the hardware CTA scheduler hands tiles to SMs as slots free up, which
 // balances the uneven blocks.  The whole RK3 step can be captured once as a CUDA graph.
 // Line maxima of the splitting are taken per block line.
+#include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "fsp_internal.h"
@@ -157,6 +160,8 @@ struct fsp_batch {
   std::vector<Params> params;        // host copy
   std::vector<CoordBlock> coords;    // host copy
   std::vector<TileRef> tx, te, tl;   // xi, eta and line-maxima tiles
+  int vx = 0, ve = 0;                // tile shape variants of the xi and eta passes
+  size_t tx_cap = 0, te_cap = 0;     // device table capacity (the largest variant)
   // device memory (one allocation)
   char* dmem = nullptr;
   Params* d_params = nullptr;
@@ -231,6 +236,34 @@ T* carve(char*& cur, size_t count) {
   return p;
 }
 
+// The tiles of one direction in shape variant v, block by block.
+void tiles_for(const fsp_batch* h, int dir, int v, std::vector<TileRef>& out) {
+  int T, NL;
+  tile_dims(h->cfg.scheme, dir, T, NL, v);
+  out.clear();
+  for (int b = 0; b < h->nb; ++b) {
+    const fsp_block& B = h->blk[b];
+    const int n = dir == 0 ? B.ni : B.nj, nl = dir == 0 ? B.nj : B.ni;
+    for (int by = 0; by < (nl + NL - 1) / NL; ++by)
+      for (int bx = 0; bx < (n + T - 1) / T; ++bx) out.push_back({b, bx, by});
+  }
+}
+
+// Switch one direction to shape variant v: the host and device tile tables (the device is
+// synchronised first, since queued launches may read the table) and any captured graph.
+fsp_status set_tiles(fsp_batch* h, int dir, int v) {
+  if (v < 0 || v >= NVARIANT) return FSP_ERR_INVALID_ARG;
+  std::vector<TileRef>& t = dir == 0 ? h->tx : h->te;
+  tiles_for(h, dir, v, t);
+  if (cudaDeviceSynchronize() != cudaSuccess) return FSP_ERR_CUDA;
+  if (cudaMemcpy(dir == 0 ? h->d_tx : h->d_te, t.data(), sizeof(TileRef) * t.size(), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return FSP_ERR_CUDA;
+  (dir == 0 ? h->vx : h->ve) = v;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return FSP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -252,9 +285,6 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   h->params.resize(nblocks);
   h->coords.resize(nblocks);
   size_t lam = 0, acc = 0, st = 0;
-  int Tx, NLx, Te, NLe;
-  tile_dims(cfg->scheme, 0, Tx, NLx);
-  tile_dims(cfg->scheme, 1, Te, NLe);
   for (int b = 0; b < nblocks; ++b) {
     const fsp_block& B = blocks[b];
     Params& P = h->params[b];
@@ -289,16 +319,21 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
     acc += al(4 * (size_t)B.nj * B.ld * acc_elem(cfg->precision));
     h->st_off.push_back(st);
     st += al(4 * (size_t)B.nj * B.ld * state_size(cfg->precision));
-    for (int by = 0; by < (B.nj + NLx - 1) / NLx; ++by)
-      for (int bx = 0; bx < (B.ni + Tx - 1) / Tx; ++bx) h->tx.push_back({b, bx, by});
-    for (int by = 0; by < (B.ni + NLe - 1) / NLe; ++by)
-      for (int bx = 0; bx < (B.nj + Te - 1) / Te; ++bx) h->te.push_back({b, bx, by});
     for (int by = 0; by < (B.nj + 7) / 8; ++by)
       for (int bx = 0; bx < (B.ni + 31) / 32; ++bx) h->tl.push_back({b, bx, by});
   }
   h->lam_count = lam;
+  for (int v = 0; v < NVARIANT; ++v) {
+    std::vector<TileRef> t;
+    tiles_for(h, 0, v, t);
+    h->tx_cap = std::max(h->tx_cap, t.size());
+    tiles_for(h, 1, v, t);
+    h->te_cap = std::max(h->te_cap, t.size());
+  }
+  tiles_for(h, 0, 0, h->tx);
+  tiles_for(h, 1, 0, h->te);
   const size_t bytes = al(sizeof(Params) * nblocks) + al(sizeof(CoordBlock) * nblocks) +
-                       al(sizeof(TileRef) * h->tx.size()) + al(sizeof(TileRef) * h->te.size()) +
+                       al(sizeof(TileRef) * h->tx_cap) + al(sizeof(TileRef) * h->te_cap) +
                        al(sizeof(TileRef) * h->tl.size()) + al(sizeof(double) * lam) + acc + 2 * st +
                        al(sizeof(void*) * T_COUNT * nblocks);
   if (cudaMalloc(&h->dmem, bytes) != cudaSuccess) {
@@ -309,8 +344,8 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   char* cur = h->dmem;
   h->d_params = carve<Params>(cur, nblocks);
   h->d_coords = carve<CoordBlock>(cur, nblocks);
-  h->d_tx = carve<TileRef>(cur, h->tx.size());
-  h->d_te = carve<TileRef>(cur, h->te.size());
+  h->d_tx = carve<TileRef>(cur, h->tx_cap);
+  h->d_te = carve<TileRef>(cur, h->te_cap);
   h->d_tl = carve<TileRef>(cur, h->tl.size());
   h->d_lam = carve<double>(cur, lam);
   h->d_acc = cur; cur += acc;
@@ -374,7 +409,7 @@ namespace {
 
 // one right-hand side of every block; input table `in`, output table `out`; mode 0:
 // dQ/dt, mode 1: RK stage out = ca Q0 + cb (in + dt dQ/dt)
-fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, double cb, double dt, cudaStream_t st) {
+fsp_status batch_lambda(fsp_batch* h, int in, cudaStream_t st) {
   const int nb = h->nb;
   void** T = h->d_tab;
   if (cudaMemsetAsync(h->d_lam, 0, sizeof(double) * h->lam_count, st) != cudaSuccess) return FSP_ERR_CUDA;
@@ -387,16 +422,22 @@ fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, doubl
     lambda_batch_kernel<float><<<(unsigned)h->tl.size(), blk, 0, st>>>(
         h->d_params, h->d_tl, reinterpret_cast<const float* const*>(T + in * nb),
         reinterpret_cast<double* const*>(T + T_LX * nb), reinterpret_cast<double* const*>(T + T_LE * nb));
-  if (cudaGetLastError() != cudaSuccess) return FSP_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
+}
+
+fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, double cb, double dt, cudaStream_t st) {
+  const int nb = h->nb;
+  void** T = h->d_tab;
+  if (fsp_status s = batch_lambda(h, in, st)) return s;
   const PassTables xi{h->d_params, h->d_tx, T + in * nb, T + T_LX * nb, nullptr, T + T_ACC * nb, nullptr,
                       nullptr};
   const PassTables eta{h->d_params, h->d_te, T + in * nb, T + T_LE * nb, T + T_ACC * nb, nullptr, T + out * nb,
                        T + T_Q0 * nb};
   const int ntx = (int)h->tx.size(), nte = (int)h->te.size();
   cudaError_t e = h->cfg.precision == FSP_FP64
-                      ? batch_fp64(h->cfg.scheme, mode, xi, ntx, eta, nte, ca, cb, dt, st)
-                      : batch_fp32(h->cfg.scheme, h->cfg.precision == FSP_FP32_MIXED, mode, xi, ntx, eta, nte, ca,
-                                   cb, dt, st);
+                      ? batch_fp64(h->cfg.scheme, mode, xi, ntx, h->vx, eta, nte, h->ve, ca, cb, dt, st)
+                      : batch_fp32(h->cfg.scheme, h->cfg.precision == FSP_FP32_MIXED, mode, xi, ntx, h->vx, eta,
+                                   nte, h->ve, ca, cb, dt, st);
   return e == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
 }
 
@@ -434,9 +475,10 @@ fsp_status fsp_batch_flux_difference(fsp_batch* h, int dir, void* const* D, void
   const PassTables t{h->d_params, dir == 0 ? h->d_tx : h->d_te, T + T_Q0 * nb, T + (dir == 0 ? T_LX : T_LE) * nb,
                      nullptr, T + T_OUT * nb, nullptr, nullptr};
   const int nt = (int)(dir == 0 ? h->tx.size() : h->te.size());
+  const int v = dir == 0 ? h->vx : h->ve;
   cudaError_t e = h->cfg.precision == FSP_FP64
-                      ? batch_direction_fp64(h->cfg.scheme, dir, t, nt, st)
-                      : batch_direction_fp32(h->cfg.scheme, h->cfg.precision == FSP_FP32_MIXED, dir, t, nt, st);
+                      ? batch_direction_fp64(h->cfg.scheme, dir, t, nt, v, st)
+                      : batch_direction_fp32(h->cfg.scheme, h->cfg.precision == FSP_FP32_MIXED, dir, t, nt, v, st);
   return e == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
 }
 
@@ -474,6 +516,130 @@ fsp_status fsp_batch_capture_graph(fsp_batch* h, double dt, void* stream) {
   if (g) cudaGraphDestroy(g);
   cudaGetLastError();
   return s;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Median duration (ms) of one direction's pass over every block (difference mode, into
+// the xi accumulators, which the next right-hand side overwrites) in the current variant.
+fsp_status time_direction(fsp_batch* h, int dir, cudaStream_t st, float* ms) {
+  const int nb = h->nb;
+  void** T = h->d_tab;
+  const PassTables t{h->d_params, dir == 0 ? h->d_tx : h->d_te, T + T_Q0 * nb, T + (dir == 0 ? T_LX : T_LE) * nb,
+                     nullptr, T + T_ACC * nb, nullptr, nullptr};
+  const int nt = (int)(dir == 0 ? h->tx.size() : h->te.size());
+  const int v = dir == 0 ? h->vx : h->ve;
+  auto run = [&]() {
+    return h->cfg.precision == FSP_FP64
+               ? batch_direction_fp64(h->cfg.scheme, dir, t, nt, v, st)
+               : batch_direction_fp32(h->cfg.scheme, h->cfg.precision == FSP_FP32_MIXED, dir, t, nt, v, st);
+  };
+  constexpr int WARM = 2, REPS = 5;
+  cudaEvent_t ev[REPS + 1];
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return FSP_ERR_CUDA;
+  bool ok = true;
+  for (int k = 0; k < WARM; ++k) ok = ok && run() == cudaSuccess;
+  ok = ok && cudaEventRecord(ev[0], st) == cudaSuccess;
+  for (int k = 0; k < REPS; ++k) ok = ok && run() == cudaSuccess && cudaEventRecord(ev[k + 1], st) == cudaSuccess;
+  ok = ok && cudaEventSynchronize(ev[REPS]) == cudaSuccess;
+  std::vector<float> d(REPS);
+  for (int k = 0; ok && k < REPS; ++k) ok = cudaEventElapsedTime(&d[k], ev[k], ev[k + 1]) == cudaSuccess;
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (!ok) return FSP_ERR_CUDA;
+  std::sort(d.begin(), d.end());
+  *ms = d[REPS / 2];
+  return FSP_OK;
+}
+
+// The table key: device, scheme and arithmetic options, and the block sizes (FNV-1a hash).
+std::string tune_key(const fsp_batch* h) {
+  cudaDeviceProp p;
+  std::string name = "gpu";
+  int sms = 0;
+  if (cudaGetDeviceProperties(&p, h->device) == cudaSuccess) { name = p.name; sms = p.multiProcessorCount; }
+  for (char& c : name)
+    if (c == ' ' || c == '\t') c = '_';
+  unsigned long long x = 1469598103934665603ULL;
+  auto mix = [&](long long v) {
+    for (int k = 0; k < 8; ++k) { x ^= (unsigned long long)((v >> (8 * k)) & 0xff); x *= 1099511628211ULL; }
+  };
+  for (const fsp_block& B : h->blk) { mix(B.ni); mix(B.nj); }
+  char buf[320];
+  std::snprintf(buf, sizeof buf, "%s|sm%d|scheme%d|prec%d|interp%d|ppm%d|linw%d|nb%d|%016llx", name.c_str(), sms,
+                h->cfg.scheme, h->cfg.precision, h->cfg.interp, h->cfg.ppm, h->cfg.linear_weights, h->nb, x);
+  return buf;
+}
+
+bool table_lookup(const char* path, const std::string& key, int* vx, int* ve) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#') continue;
+    char k[512];
+    int a, b;
+    if (std::sscanf(line, "%511s %d %d", k, &a, &b) == 3 && key == k && a >= 0 && a < NVARIANT && b >= 0 &&
+        b < NVARIANT) {
+      *vx = a;
+      *ve = b;
+      found = true;  // the last entry for a key wins
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+}  // namespace
+
+extern "C" {
+
+fsp_status fsp_batch_tune(fsp_batch* h, const char* table_path, void* stream) {
+  if (!h || !h->bound) return FSP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const std::string key = tune_key(h);
+  int best[2] = {-1, -1};
+  if (table_path && table_lookup(table_path, key, &best[0], &best[1])) {
+    if (fsp_status s = set_tiles(h, 0, best[0])) return s;
+    return set_tiles(h, 1, best[1]);
+  }
+  if (fsp_status s = batch_lambda(h, T_Q0, st)) return s;
+  float best_ms[2] = {0, 0};
+  for (int dir = 0; dir < 2; ++dir) {
+    for (int v = 0; v < NVARIANT; ++v) {
+      if (fsp_status s = set_tiles(h, dir, v)) return s;
+      float ms = 0;
+      if (fsp_status s = time_direction(h, dir, st, &ms)) return s;
+      if (best[dir] < 0 || ms < best_ms[dir]) { best[dir] = v; best_ms[dir] = ms; }
+    }
+    if (fsp_status s = set_tiles(h, dir, best[dir])) return s;
+  }
+  if (table_path) {
+    FILE* f = std::fopen(table_path, "a");
+    if (!f) return FSP_ERR_INVALID_ARG;
+    std::fprintf(f, "%s %d %d %.4f %.4f\n", key.c_str(), best[0], best[1], best_ms[0], best_ms[1]);
+    std::fclose(f);
+  }
+  return FSP_OK;
+}
+
+fsp_status fsp_batch_set_tile_shape(fsp_batch* h, int dir, int variant) {
+  if (!h || (dir != 0 && dir != 1)) return FSP_ERR_INVALID_ARG;
+  return set_tiles(h, dir, variant);
+}
+
+fsp_status fsp_batch_tile_shape(const fsp_batch* h, int dir, int* variant, int* lines, int* outputs) {
+  if (!h || (dir != 0 && dir != 1)) return FSP_ERR_INVALID_ARG;
+  const int v = dir == 0 ? h->vx : h->ve;
+  int T, NL;
+  tile_dims(h->cfg.scheme, dir, T, NL, v);
+  if (variant) *variant = v;
+  if (lines) *lines = NL;
+  if (outputs) *outputs = T;
+  return FSP_OK;
 }
 
 fsp_status fsp_batch_destroy(fsp_batch* h) {

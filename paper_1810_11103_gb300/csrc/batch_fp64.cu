@@ -1,0 +1,17 @@
+// batch_fp64.cu -- FP64 instantiations of the batched sweeps (sweep.cuh) in every tile
+// shape variant.
+#include "fsp_internal.h"
+#include "sweep.cuh"
+
+namespace fsp {
+
+cudaError_t batch_fp64(int scheme, int mode, const PassTables& xi, int ntx, int vx, const PassTables& eta, int nte,
+                       int ve, double ca, double cb, double dt, cudaStream_t st) {
+  return batch_dispatch<double, double>(scheme, mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
+}
+
+cudaError_t batch_direction_fp64(int scheme, int dir, const PassTables& t, int ntiles, int v, cudaStream_t st) {
+  return batch_one_direction<double, double>(scheme, dir, t, ntiles, v, st);
+}
+
+}  // namespace fsp

@@ -87,15 +87,6 @@ cudaError_t flux_difference_fp64(int scheme, const Params& P, const void* Q, con
   }
 }
 
-cudaError_t batch_fp64(int scheme, int mode, const PassTables& xi, int ntx, const PassTables& eta, int nte,
-                       double ca, double cb, double dt, cudaStream_t st) {
-  return batch_dispatch<double, double>(scheme, mode, xi, ntx, eta, nte, ca, cb, dt, st);
-}
-
-cudaError_t batch_direction_fp64(int scheme, int dir, const PassTables& t, int ntiles, cudaStream_t st) {
-  return batch_one_direction<double, double>(scheme, dir, t, ntiles, st);
-}
-
 cudaError_t launch_rhs(int scheme, int precision, const Params& P, const void* Q,
                        const double* lam_xi, const double* lam_eta, void* Racc, void* out, int mode,
                        const void* Qn, double ca, double cb, double dt, cudaStream_t st) {

@@ -49,16 +49,4 @@ cudaError_t flux_difference_fp32(int scheme, bool mixed, const Params& P, const 
                : fd_f32<float>(scheme, P, Q, lam, dir, mode, acc, out, st);
 }
 
-cudaError_t batch_fp32(int scheme, bool mixed, int mode, const PassTables& xi, int ntx, const PassTables& eta,
-                       int nte, double ca, double cb, double dt, cudaStream_t st) {
-  return mixed ? batch_dispatch<float, double>(scheme, mode, xi, ntx, eta, nte, ca, cb, dt, st)
-               : batch_dispatch<float, float>(scheme, mode, xi, ntx, eta, nte, ca, cb, dt, st);
-}
-
-cudaError_t batch_direction_fp32(int scheme, bool mixed, int dir, const PassTables& t, int ntiles,
-                                 cudaStream_t st) {
-  return mixed ? batch_one_direction<float, double>(scheme, dir, t, ntiles, st)
-               : batch_one_direction<float, float>(scheme, dir, t, ntiles, st);
-}
-
 }  // namespace fsp

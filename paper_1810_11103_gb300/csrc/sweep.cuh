@@ -6,8 +6,8 @@
 //
 // A CTA owns NL grid lines x T output nodes of one direction.  Phase 1 stages every node of
 // the tile plus four ghosts a side in shared memory: the state (ghosts by the boundary
-// rule), the direction's metrics, the node flux E^ and the primitives the characteristic
-// projection needs.  Phase 2 gives each thread one interface p + 1/2: the eigenvectors at
+// rule), the direction's metrics, the node split fluxes f+- = (E^ +- A^ Q)/2 and the
+// primitives the characteristic projection needs.  Phase 2 gives each thread one interface p + 1/2: the eigenvectors at
 // Q_p and Q_{p+1} along the averaged metric direction, WENO interpolation of the
 // characteristic differences from both sides, the states Q+- at the midpoint, and the split
 // midpoint fluxes with the interpolated midpoint metrics.  The h = h+ + h- combination and
@@ -23,10 +23,19 @@ namespace fsp {
 
 enum { MODE_ACC = 0, MODE_RHS = 1, MODE_STAGE = 2 };
 
-template <int S, int DIR, typename Real, typename Acc>
+// Tile shapes: 256 threads, NL grid lines x W interface slots per CTA.  Variant 0 is the
+// default; fsp_batch_tune may pick another per direction for a batch.
+//   xi:  (NL, W) = (2, 128), (1, 256), (4, 64)
+//   eta: (NL, W) = (8, 32),  (4, 64),  (16, 16)
+constexpr int NVARIANT = 3;
+constexpr int shape_nl(int dir, int v) {
+  return dir == 0 ? (v == 1 ? 1 : v == 2 ? 4 : 2) : (v == 1 ? 4 : v == 2 ? 16 : 8);
+}
+
+template <int S, int DIR, typename Real, typename Acc, int V = 0>
 struct TileShape {
-  static constexpr int NL = DIR == 0 ? 2 : 8;        // grid lines per CTA
-  static constexpr int W = DIR == 0 ? 128 : 32;      // interface slots per line
+  static constexpr int NL = shape_nl(DIR, V);       // grid lines per CTA
+  static constexpr int W = 256 / NL;                 // interface slots per line
   static constexpr int NMP = Scheme<S>::nmp;
   static constexpr int T = W - NMP - 1;              // output nodes per line
   static constexpr int NP = T + 8;                   // staged nodes per line
@@ -36,38 +45,39 @@ struct TileShape {
   static constexpr bool SPLIT_MET = !std::is_same<Real, Acc>::value;
   static constexpr size_t smem_bytes() {
     return sizeof(Real) * ((size_t)(4 + 7) * NN + (SPLIT_MET ? 2 * NN : 0)) +
-           sizeof(Acc) * ((size_t)(4 + 2) * NN + (size_t)4 * NW + (NMP == 2 ? (size_t)8 * NW : 0) + NL);
+           sizeof(Acc) * ((size_t)(8 + 2) * NN + (size_t)4 * NW + (NMP == 2 ? (size_t)8 * NW : 0) + NL);
   }
 };
 
 // Host view of the tile shape: output nodes per line T and lines per CTA NL.
-inline void tile_dims(int scheme, int dir, int& T, int& NL) {
+inline void tile_dims(int scheme, int dir, int& T, int& NL, int variant = 0) {
   const int nmp = (scheme == S32 || scheme == S52) ? 2 : 1;
-  NL = dir == 0 ? 2 : 8;
-  T = (dir == 0 ? 128 : 32) - nmp - 1;
+  NL = shape_nl(dir, variant);
+  T = 256 / NL - nmp - 1;
 }
 
 // One tile (bx along the lines, by across them) of one block.  qtab: every block's state
 // for linked faces (null for a lone block).
-template <int S, int DIR, int MODE, typename Real, typename Acc>
+template <int S, int DIR, int MODE, typename Real, typename Acc, int V = 0>
 __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restrict__ Q,
                                            const Real* const* qtab, const double* __restrict__ lam,
                                            const Acc* __restrict__ Dacc, Acc* __restrict__ Dout,
                                            Real* qout, const Real* Qn, double ca, double cb, double dt,
                                            int bx, int by) {
-  using Sh = TileShape<S, DIR, Real, Acc>;
+  using Sh = TileShape<S, DIR, Real, Acc, V>;
   using Sc = Scheme<S>;
   constexpr int NL = Sh::NL, W = Sh::W, T = Sh::T, NP = Sh::NP, PLO = Sh::PLO;
   constexpr int NN = Sh::NN, NW = Sh::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Acc* sE = reinterpret_cast<Acc*>(smem_raw);            // [4][NN] node E^
-  Acc* sMa = sE + 4 * NN;                                // [2][NN] metrics (flux arithmetic)
+  Acc* sFp = reinterpret_cast<Acc*>(smem_raw);           // [4][NN] node f+ = (E^ + A^ Q)/2
+  Acc* sFm = sFp + 4 * NN;                               // [4][NN] node f- = (E^ - A^ Q)/2
+  Acc* sMa = sFm + 4 * NN;                               // [2][NN] metrics (flux arithmetic)
   Acc* sH = sMa + 2 * NN;                                // [4][NW] h at interfaces
   Acc* sF = sH + 4 * NW;                                 // [8][NW] f+-_mid (two midpoints)
   Real* sQ = reinterpret_cast<Real*>(sF + (Sh::NMP == 2 ? 8 * NW : 0) + NL);  // [4][NN] (after A^)
   Real* sP = sQ + 4 * NN;                                // [7][NN] primitives
   Real* sMr = Sh::SPLIT_MET ? sP + 7 * NN : nullptr;     // [2][NN] metrics in Real
-  Acc* sA = reinterpret_cast<Acc*>(smem_raw) + 6 * NN + 4 * NW + (Sh::NMP == 2 ? 8 * NW : 0);  // [NL] A^
+  Acc* sA = reinterpret_cast<Acc*>(smem_raw) + 10 * NN + 4 * NW + (Sh::NMP == 2 ? 8 * NW : 0);  // [NL] A^
 
   const int n = DIR == 0 ? P.ni : P.nj;
   const int nlines = DIR == 0 ? P.nj : P.ni;
@@ -89,6 +99,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const int line = line0 + threadIdx.x;
     sA[threadIdx.x] = line < nlines ? Acc(P.alpha * lam[line]) : Acc(0);
   }
+  __syncthreads();
   // ---- phase 1: nodes ----
   for (int k = threadIdx.x; k < NN; k += Sh::THREADS) {
     const int l = DIR == 0 ? k / NP : k % NL;
@@ -107,10 +118,15 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const Acc amx = from_f64<Acc>(mx), amy = from_f64<Acc>(my);
     const Acc U = amx * Acc(w.u) + amy * Acc(w.v);
     const int o = SI(l, s);
-    sE[0 * NN + o] = Acc(q[0]) * U;
-    sE[1 * NN + o] = Acc(q[1]) * U + amx * Acc(p);
-    sE[2 * NN + o] = Acc(q[2]) * U + amy * Acc(p);
-    sE[3 * NN + o] = Acc(q[3] + p) * U;
+    // f+- = (E^ +- A^ Q)/2, the node terms of the split
+    const Acc hA = Acc(0.5) * sA[l];
+    const Acc E[4] = {Acc(q[0]) * U, Acc(q[1]) * U + amx * Acc(p), Acc(q[2]) * U + amy * Acc(p), Acc(q[3] + p) * U};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const Acc e = Acc(0.5) * E[v], aq = hA * Acc(q[v]);
+      sFp[v * NN + o] = e + aq;
+      sFm[v * NN + o] = e - aq;
+    }
     sMa[o] = amx;
     sMa[NN + o] = amy;
     if constexpr (Sh::SPLIT_MET) { sMr[o] = from_f64<Real>(mx); sMr[NN + o] = from_f64<Real>(my); }
@@ -206,8 +222,8 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
       fs[side][3] = Acc(0.5) * (Acc(q[3] + pr) * U + sg * Acc(q[3]));
     }
     if constexpr (Sc::nmp == 1) {
-      // h = h+ + h-: the midpoint terms plus the node terms of f+- = (E^ +- A^ Q)/2, h- the
-      // mirror of h+ about p + 1/2 (f_{p+k} -> f_{p+1-k})
+      // h = h+ + h-: the midpoint terms plus the node terms n_k (f+_{p+k} + f-_{p+1-k}),
+      // h- the mirror of h+ about p + 1/2
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         Acc h = Acc(Sc::m0) * (fs[0][v] + fs[1][v]);
@@ -215,8 +231,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
         for (int kk = -2; kk <= 2; ++kk) {
           if (Sc::n(kk + 2) == 0.0) continue;
           const int a = SI(l, c0 + kk), b = SI(l, c0 + 1 - kk);
-          h += Acc(Sc::n(kk + 2) * 0.5) *
-               ((sE[v * NN + a] + sE[v * NN + b]) + A * Acc(sQ[v * NN + a] - sQ[v * NN + b]));
+          h += Acc(Sc::n(kk + 2)) * (sFp[v * NN + a] + sFm[v * NN + b]);
         }
         sH[v * NW + WI(l, pi)] = h;
       }
@@ -238,7 +253,6 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
       const int line = line0 + l;
       const int p = PLO + pi;
       if (line >= nlines || p < -1 || p > T - 1 || base + p > n - 1) continue;
-      const Acc A = sA[l];
       const int c0 = p + 4;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -248,8 +262,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
         for (int kk = -2; kk <= 2; ++kk) {
           if (Sc::n(kk + 2) == 0.0) continue;
           const int a = SI(l, c0 + kk), b = SI(l, c0 + 1 - kk);
-          h += Acc(Sc::n(kk + 2) * 0.5) *
-               ((sE[v * NN + a] + sE[v * NN + b]) + A * Acc(sQ[v * NN + a] - sQ[v * NN + b]));
+          h += Acc(Sc::n(kk + 2)) * (sFp[v * NN + a] + sFm[v * NN + b]);
         }
         sH[v * NW + WI(l, pi)] = h;
       }
@@ -290,7 +303,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
 }
 
 template <int S, int DIR, int MODE, typename Real, typename Acc>
-__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 3)
+__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 4)
 sweep_kernel(Params P, const Real* __restrict__ Q, const double* __restrict__ lam,
              const Acc* __restrict__ Dacc, Acc* __restrict__ Dout, Real* qout, const Real* Qn,
              double ca, double cb, double dt) {
@@ -313,15 +326,15 @@ struct BatchPass {                 // device arrays indexed by block
   const Real* const* qn;           // Q^n of the RK step (mode 2)
 };
 
-template <int S, int DIR, int MODE, typename Real, typename Acc>
-__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 3)
+template <int S, int DIR, int MODE, typename Real, typename Acc, int V>
+__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 4)
 sweep_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
   __shared__ Params sp;
   const TileRef t = B.tiles[blockIdx.x];
   if (threadIdx.x == 0) sp = B.params[t.block];
   __syncthreads();
   const int b = t.block;
-  sweep_tile<S, DIR, MODE, Real, Acc>(sp, B.q[b], B.q, B.lam[b], MODE == MODE_ACC ? nullptr : B.dacc[b],
+  sweep_tile<S, DIR, MODE, Real, Acc, V>(sp, B.q[b], B.q, B.lam[b], MODE == MODE_ACC ? nullptr : B.dacc[b],
                                       MODE == MODE_ACC ? B.dout[b] : nullptr,
                                       MODE == MODE_ACC ? nullptr : B.qout[b],
                                       MODE == MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, t.bx, t.by);
@@ -353,11 +366,11 @@ BatchPass<Real, Acc> typed_pass(const PassTables& t) {
   return B;
 }
 
-template <int S, int DIR, int MODE, typename Real, typename Acc>
-cudaError_t launch_sweep_batch(const BatchPass<Real, Acc>& B, int ntiles, double ca, double cb, double dt,
-                               cudaStream_t st) {
-  using Sh = TileShape<S, DIR, Real, Acc>;
-  auto kern = sweep_batch_kernel<S, DIR, MODE, Real, Acc>;
+template <int S, int DIR, int MODE, typename Real, typename Acc, int V>
+cudaError_t launch_sweep_batch_v(const BatchPass<Real, Acc>& B, int ntiles, double ca, double cb, double dt,
+                                 cudaStream_t st) {
+  using Sh = TileShape<S, DIR, Real, Acc, V>;
+  auto kern = sweep_batch_kernel<S, DIR, MODE, Real, Acc, V>;
   const size_t smem = Sh::smem_bytes();
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -365,6 +378,16 @@ cudaError_t launch_sweep_batch(const BatchPass<Real, Acc>& B, int ntiles, double
   }
   if (ntiles > 0) kern<<<ntiles, Sh::THREADS, smem, st>>>(B, ca, cb, dt);
   return cudaGetLastError();
+}
+
+template <int S, int DIR, int MODE, typename Real, typename Acc>
+cudaError_t launch_sweep_batch(const BatchPass<Real, Acc>& B, int ntiles, int v, double ca, double cb, double dt,
+                               cudaStream_t st) {
+  switch (v) {
+    case 1: return launch_sweep_batch_v<S, DIR, MODE, Real, Acc, 1>(B, ntiles, ca, cb, dt, st);
+    case 2: return launch_sweep_batch_v<S, DIR, MODE, Real, Acc, 2>(B, ntiles, ca, cb, dt, st);
+    default: return launch_sweep_batch_v<S, DIR, MODE, Real, Acc, 0>(B, ntiles, ca, cb, dt, st);
+  }
 }
 
 template <int S, int DIR, int MODE, typename Real, typename Acc>
@@ -415,51 +438,57 @@ cudaError_t flux_difference_passes(const Params& P, const Real* Q, const double*
                                                        nullptr, 0, 0, 0, st);
 }
 
-// Both directions of every block for one scheme (mode 0: dQ/dt, mode 1: RK stage).
+// Both directions of every block for one scheme (mode 0: dQ/dt, mode 1: RK stage), xi tiles
+// of shape variant vx, eta tiles of variant ve.
 template <int S, typename Real, typename Acc>
-cudaError_t batch_scheme(int mode, const PassTables& xi, int ntx, const PassTables& eta, int nte, double ca,
-                         double cb, double dt, cudaStream_t st) {
+cudaError_t batch_scheme(int mode, const PassTables& xi, int ntx, int vx, const PassTables& eta, int nte, int ve,
+                         double ca, double cb, double dt, cudaStream_t st) {
   const BatchPass<Real, Acc> X = typed_pass<Real, Acc>(xi), E = typed_pass<Real, Acc>(eta);
-  cudaError_t e = launch_sweep_batch<S, 0, MODE_ACC, Real, Acc>(X, ntx, 0, 0, 0, st);
+  cudaError_t e = launch_sweep_batch<S, 0, MODE_ACC, Real, Acc>(X, ntx, vx, 0, 0, 0, st);
   if (e != cudaSuccess) return e;
-  if (mode == 0) return launch_sweep_batch<S, 1, MODE_RHS, Real, Acc>(E, nte, 0, 0, 0, st);
-  return launch_sweep_batch<S, 1, MODE_STAGE, Real, Acc>(E, nte, ca, cb, dt, st);
+  if (mode == 0) return launch_sweep_batch<S, 1, MODE_RHS, Real, Acc>(E, nte, ve, 0, 0, 0, st);
+  return launch_sweep_batch<S, 1, MODE_STAGE, Real, Acc>(E, nte, ve, ca, cb, dt, st);
 }
 
 template <typename Real, typename Acc>
-cudaError_t batch_dispatch(int scheme, int mode, const PassTables& xi, int ntx, const PassTables& eta, int nte,
-                           double ca, double cb, double dt, cudaStream_t st) {
+cudaError_t batch_dispatch(int scheme, int mode, const PassTables& xi, int ntx, int vx, const PassTables& eta,
+                           int nte, int ve, double ca, double cb, double dt, cudaStream_t st) {
   switch (scheme) {
-    case S31: return batch_scheme<S31, Real, Acc>(mode, xi, ntx, eta, nte, ca, cb, dt, st);
-    case S32: return batch_scheme<S32, Real, Acc>(mode, xi, ntx, eta, nte, ca, cb, dt, st);
-    case S51: return batch_scheme<S51, Real, Acc>(mode, xi, ntx, eta, nte, ca, cb, dt, st);
-    default:  return batch_scheme<S52, Real, Acc>(mode, xi, ntx, eta, nte, ca, cb, dt, st);
+    case S31: return batch_scheme<S31, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
+    case S32: return batch_scheme<S32, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
+    case S51: return batch_scheme<S51, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
+    default:  return batch_scheme<S52, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
   }
 }
 
-// One direction of every block into dout (mode 0 tiles), with the current line maxima.
+// One direction of every block into dout (mode 0 tiles of variant v), with the current line
+// maxima.
 template <typename Real, typename Acc>
-cudaError_t batch_one_direction(int scheme, int dir, const PassTables& t, int ntiles, cudaStream_t st) {
+cudaError_t batch_one_direction(int scheme, int dir, const PassTables& t, int ntiles, int v, cudaStream_t st) {
   const BatchPass<Real, Acc> B = typed_pass<Real, Acc>(t);
   switch (scheme * 2 + dir) {
-    case 0: return launch_sweep_batch<S31, 0, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
-    case 1: return launch_sweep_batch<S31, 1, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
-    case 2: return launch_sweep_batch<S32, 0, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
-    case 3: return launch_sweep_batch<S32, 1, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
-    case 4: return launch_sweep_batch<S51, 0, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
-    case 5: return launch_sweep_batch<S51, 1, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
-    case 6: return launch_sweep_batch<S52, 0, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
-    default: return launch_sweep_batch<S52, 1, MODE_ACC, Real, Acc>(B, ntiles, 0, 0, 0, st);
+    case 0: return launch_sweep_batch<S31, 0, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    case 1: return launch_sweep_batch<S31, 1, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    case 2: return launch_sweep_batch<S32, 0, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    case 3: return launch_sweep_batch<S32, 1, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    case 4: return launch_sweep_batch<S51, 0, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    case 5: return launch_sweep_batch<S51, 1, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    case 6: return launch_sweep_batch<S52, 0, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    default: return launch_sweep_batch<S52, 1, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
   }
 }
-cudaError_t batch_direction_fp64(int scheme, int dir, const PassTables& t, int ntiles, cudaStream_t st);
-cudaError_t batch_direction_fp32(int scheme, bool mixed, int dir, const PassTables& t, int ntiles,
+// Batch passes (shape variants vx, ve for the xi and eta tiles): FP64 in batch_fp64.cu;
+// FP32 and mixed in batch_fp32.cu and batch_mixed.cu.
+cudaError_t batch_fp64(int scheme, int mode, const PassTables& xi, int ntx, int vx, const PassTables& eta, int nte,
+                       int ve, double ca, double cb, double dt, cudaStream_t st);
+cudaError_t batch_direction_fp64(int scheme, int dir, const PassTables& t, int ntiles, int v, cudaStream_t st);
+cudaError_t batch_fp32(int scheme, bool mixed, int mode, const PassTables& xi, int ntx, int vx,
+                       const PassTables& eta, int nte, int ve, double ca, double cb, double dt, cudaStream_t st);
+cudaError_t batch_direction_fp32(int scheme, bool mixed, int dir, const PassTables& t, int ntiles, int v,
                                  cudaStream_t st);
-
-cudaError_t batch_fp64(int scheme, int mode, const PassTables& xi, int ntx, const PassTables& eta, int nte,
-                       double ca, double cb, double dt, cudaStream_t st);
-cudaError_t batch_fp32(int scheme, bool mixed, int mode, const PassTables& xi, int ntx, const PassTables& eta,
-                       int nte, double ca, double cb, double dt, cudaStream_t st);
+cudaError_t batch_mixed(int scheme, int mode, const PassTables& xi, int ntx, int vx, const PassTables& eta,
+                        int nte, int ve, double ca, double cb, double dt, cudaStream_t st);
+cudaError_t batch_direction_mixed(int scheme, int dir, const PassTables& t, int ntiles, int v, cudaStream_t st);
 
 // Precision instantiations: each lives in its own translation unit.
 cudaError_t rhs_fp64(int scheme, const Params& P, const void* Q, const double* lx, const double* le,

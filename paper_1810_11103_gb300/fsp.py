@@ -132,6 +132,10 @@ def lib():
                 "fsp_batch_rk3_step": (ctypes.c_int, [_P, ctypes.c_double, _P]),
                 "fsp_batch_flux_difference": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), _P]),
                 "fsp_batch_capture_graph": (ctypes.c_int, [_P, ctypes.c_double, _P]),
+                "fsp_batch_tune": (ctypes.c_int, [_P, ctypes.c_char_p, _P]),
+                "fsp_batch_set_tile_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+                "fsp_batch_tile_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
                 "fsp_batch_destroy": (ctypes.c_int, [_P]),
             }
             for name, (res, args) in sig.items():
@@ -415,6 +419,22 @@ class Batch:
 
     def capture_graph(self, dt: float, stream=None):
         _check("fsp_batch_capture_graph", lib().fsp_batch_capture_graph(self._h, float(dt), _stream(stream)))
+
+    def tune(self, table_path: Optional[str] = None, stream=None):
+        """Pick the fastest tile shape of each direction (fsp_batch_tune); returns the
+        (variant, lines, output nodes) of the xi and eta tiles."""
+        path = None if table_path is None else os.fsencode(table_path)
+        _check("fsp_batch_tune", lib().fsp_batch_tune(self._h, path, _stream(stream)))
+        return self.tile_shape(0), self.tile_shape(1)
+
+    def set_tile_shape(self, dir: int, variant: int):
+        _check("fsp_batch_set_tile_shape", lib().fsp_batch_set_tile_shape(self._h, int(dir), int(variant)))
+
+    def tile_shape(self, dir: int):
+        v, nl, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check("fsp_batch_tile_shape", lib().fsp_batch_tile_shape(self._h, int(dir), ctypes.byref(v), ctypes.byref(nl),
+                                                                  ctypes.byref(t)))
+        return v.value, nl.value, t.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -148,3 +148,51 @@ def test_batch_full_size_cylinder(F):
         bt.M[k].copy_(torch.as_tensor(Ms[k]))
     assert _maxrel([r.cpu().numpy() for r in bt.rhs()], Ro) < TOL
     bt.close()
+
+
+@pytest.mark.parametrize("scheme,prec", [(2, 0), (3, 0), (0, 1), (3, 2)])
+def test_batch_tile_shapes_agree(F, scheme, prec):
+    # every tile shape computes each interface the same way: identical FP64 right-hand sides;
+    # in float the instantiations may contract products into FMAs differently (last bits)
+    blocks, states, free = _small_cylinder()
+    cfgd = _cfgd(free, scheme, prec)
+    qs = _perturbed(states, 3, 0.05)
+    bt = F.Batch(F.Config.from_dict(cfgd), blocks, qs)
+    bt.metrics()
+    ref = [r.double().cpu().numpy() for r in bt.rhs()]
+    bound = 0.0 if prec == 0 else 1e-5 * max(np.abs(r).max() for r in ref)
+    shapes = set()
+    for vx in range(3):
+        for ve in range(3):
+            bt.set_tile_shape(0, vx)
+            bt.set_tile_shape(1, ve)
+            shapes.add((bt.tile_shape(0), bt.tile_shape(1)))
+            got = [r.double().cpu().numpy() for r in bt.rhs()]
+            assert max(np.abs(a - b).max() for a, b in zip(got, ref)) <= bound, (vx, ve)
+    assert len(shapes) == 9
+    bt.close()
+
+
+def test_batch_tune_table(F, tmp_path):
+    blocks, states, free = _small_cylinder()
+    bt = F.Batch(F.Config.from_dict(_cfgd(free, 2)), blocks, states)
+    bt.metrics()
+    table = tmp_path / "tiles.txt"
+    first = bt.tune(str(table))
+    lines = [l for l in table.read_text().splitlines() if l and not l.startswith("#")]
+    assert len(lines) == 1
+    key, vx, ve = lines[0].split()[:3]
+    assert (int(vx), int(ve)) == (first[0][0], first[1][0])
+    # a forced shape is replaced by the stored choice, without a new entry
+    bt.set_tile_shape(0, (first[0][0] + 1) % 3)
+    assert bt.tune(str(table)) == first
+    assert len([l for l in table.read_text().splitlines() if l and not l.startswith("#")]) == 1
+    # the tuned batch still steps correctly
+    Ms = O.mb_metrics(_cfgd(free, 2), blocks)
+    for k in range(len(blocks)):
+        bt.M[k].copy_(torch.as_tensor(Ms[k]))
+    q1 = O.mb_rk3(_cfgd(free, 2), blocks, Ms, states, 2e-4, 1)
+    bt.capture_graph(2e-4)
+    torch.cuda.synchronize()
+    assert _maxrel([q.cpu().numpy() for q in bt.Q], q1) < TOL
+    bt.close()
