@@ -118,14 +118,28 @@ __device__ __forceinline__ int pmod(int a, int n) {
 // --------------------------------------------------------------------------------------
 // Small arithmetic helpers by precision
 // --------------------------------------------------------------------------------------
+// FP32 uses the hardware's approximate reciprocal and reciprocal square root (PTX
+// rcp.approx.ftz / rsqrt.approx.ftz, about 1 ulp) directly: every operand here is a
+// positive normal number (densities, sound speeds, metric norms, eps + IS >= 1e-30, sums of
+// weights), and a result flushed to zero is the right limit for a vanishing weight.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-// quotient: IEEE division in FP64; the fast approximate quotient in FP32
+__device__ __forceinline__ float rsq(float x) { return rsqrt_approx(x); }
+// quotient: IEEE division in FP64; a times the approximate reciprocal in FP32
 __device__ __forceinline__ double quot(double a, double b) { return a / b; }
-__device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
-// reciprocal: IEEE in FP64; the fast approximate reciprocal in FP32
+__device__ __forceinline__ float quot(float a, float b) { return a * rcp_approx(b); }
+// reciprocal: IEEE in FP64; the approximate reciprocal in FP32
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
 
 // A double rounded to the state type.  To float with integer operations only (round to
 // nearest even; zero and subnormals to signed zero, overflow to infinity), so the FP32
@@ -417,6 +431,99 @@ __device__ __forceinline__ T weno_delta(const T* u, T eps, int ppm, int linw) {
       return quot(num, den);
     }
     return w[0] * p0 + w[1] * p1;
+  }
+}
+
+// --------------------------------------------------------------------------------------
+// FP32 WENO on two characteristic components at once (Blackwell packed two-lane float
+// arithmetic).  The same operations as weno_delta<R, float>, lane by lane: additions,
+// multiplications and fused multiply-adds are packed; quotients, minima and the mapping's
+// branch are taken per lane.
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 quot2(float2 a, float2 b) {
+  return mul2(a, make_float2(rcp_approx(b.x), rcp_approx(b.y)));
+}
+__device__ __forceinline__ float2 is_b2(float2 e, float2 f, float2 eps) {
+  return fma2(mul2(bc2(13.0f / 12), e), e, fma2(mul2(bc2(0.25f), f), f, eps));
+}
+// raw weights, ratio form C_k (b_min / b_k)^2 normalised (as raw_weights<float, K>)
+template <int K>
+__device__ __forceinline__ void raw_weights2(const float2* b, const float* C, float2* w) {
+  float2 bmin = b[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) bmin = make_float2(fminf(bmin.x, b[k].x), fminf(bmin.y, b[k].y));
+  float2 t[K], sum;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float2 r = quot2(bmin, b[k]);
+    t[k] = mul2(mul2(bc2(C[k]), r), r);
+    sum = k == 0 ? t[0] : add2(sum, t[k]);
+  }
+  const float2 inv = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
+#pragma unroll
+  for (int k = 0; k < K; ++k) w[k] = mul2(t[k], inv);
+}
+
+template <int R>
+__device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int ppm, int linw) {
+  const float2 eps = bc2(eps_);
+  if constexpr (R == 3) {
+    const float2 p[3] = {fma2(bc2(0.375f), u[0], mul2(bc2(-1.25f), u[1])),
+                         fma2(bc2(-0.125f), u[1], mul2(bc2(0.375f), u[3])),
+                         fma2(bc2(0.75f), u[3], mul2(bc2(-0.125f), u[4]))};
+    const float C[3] = {1.0f / 16, 10.0f / 16, 5.0f / 16};
+    if (linw) return fma2(bc2(C[0]), p[0], fma2(bc2(C[1]), p[1], mul2(bc2(C[2]), p[2])));
+    const float2 m1 = bc2(-1.0f);
+    const float2 d1 = fma2(u[0], m1, u[1]), d2 = mul2(u[1], m1), d3 = u[3], d4 = fma2(u[3], m1, u[4]);
+    const float2 b[3] = {is_b2(fma2(d1, m1, d2), fma2(bc2(3.0f), d2, mul2(d1, m1)), eps),
+                         is_b2(fma2(d2, m1, d3), add2(d2, d3), eps),
+                         is_b2(fma2(d3, m1, d4), fma2(bc2(-3.0f), d3, d4), eps)};
+    float2 w[3];
+    raw_weights2<3>(b, C, w);
+    if (ppm) {
+      // g = C + (w - C)^3 / C^2 (w <= C), C + (w - C)^3 / (C - 1)^2 (w > C)   [Eq. 3.23]
+      const float K0[3] = {256.0f, 256.0f / 100, 256.0f / 25}, K1[3] = {256.0f / 225, 256.0f / 36, 256.0f / 121};
+      float2 num, den;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float2 q = add2(w[k], bc2(-C[k]));
+        const float2 K = make_float2(nonpos(q.x) ? K0[k] : K1[k], nonpos(q.y) ? K0[k] : K1[k]);
+        const float2 g = fma2(mul2(mul2(q, q), q), K, bc2(C[k]));
+        num = k == 0 ? mul2(g, p[0]) : fma2(g, p[k], num);
+        den = k == 0 ? g : add2(den, g);
+      }
+      return quot2(num, den);
+    }
+    return fma2(w[0], p[0], fma2(w[1], p[1], mul2(w[2], p[2])));
+  } else {
+    const float2 p[2] = {mul2(bc2(-0.5f), u[1]), mul2(bc2(0.5f), u[3])};
+    const float C[2] = {0.25f, 0.75f};
+    if (linw) return fma2(bc2(C[0]), p[0], mul2(bc2(C[1]), p[1]));
+    const float2 m1 = bc2(-1.0f);
+    const float2 d1 = fma2(u[0], m1, u[1]), d2 = mul2(u[1], m1), d3 = u[3];
+    const float2 b[2] = {is_b2(fma2(d1, m1, d2), fma2(bc2(3.0f), d2, mul2(d1, m1)), eps),
+                         is_b2(fma2(d2, m1, d3), add2(d2, d3), eps)};
+    float2 w[2];
+    raw_weights2<2>(b, C, w);
+    if (ppm) {
+      // g = C - (w - C)^2 / C (w <= C), C - (w - C)^2 / (C - 1) (w > C)   [Eq. 3.15]
+      const float K0[2] = {4.0f, 4.0f / 3}, K1[2] = {-4.0f / 3, -4.0f};
+      float2 num, den;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float2 q = add2(w[k], bc2(-C[k]));
+        const float2 K = make_float2(nonpos(q.x) ? -K0[k] : -K1[k], nonpos(q.y) ? -K0[k] : -K1[k]);
+        const float2 g = fma2(mul2(q, q), K, bc2(C[k]));
+        num = k == 0 ? mul2(g, p[0]) : fma2(g, p[k], num);
+        den = k == 0 ? g : add2(den, g);
+      }
+      return quot2(num, den);
+    }
+    return fma2(w[0], p[0], mul2(w[1], p[1]));
   }
 }
 

@@ -178,15 +178,33 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
         dq[a][3] = sQ[3 * NN + o] - qc3;
       }
       Real Wm[4];
+      if constexpr (std::is_same<Real, float>::value) {
+        // components (0, 1) and (2, 3) in the two lanes of packed float arithmetic
 #pragma unroll
-      for (int kc = 0; kc < 4; ++kc) {
-        Real u[5];
-        u[0] = E.project(kc, dq[0][0], dq[0][1], dq[0][2], dq[0][3]);
-        u[1] = E.project(kc, dq[1][0], dq[1][1], dq[1][2], dq[1][3]);
-        u[2] = Real(0);
-        u[3] = E.project(kc, dq[2][0], dq[2][1], dq[2][2], dq[2][3]);
-        u[4] = Sc::r == 3 ? E.project(kc, dq[3][0], dq[3][1], dq[3][2], dq[3][3]) : Real(0);
-        Wm[kc] = weno_delta<Sc::r, Real>(u, eps, P.ppm, P.linw);
+        for (int kp = 0; kp < 2; ++kp) {
+          float2 u[5];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            if (Sc::r == 2 && a == 3) { u[4] = make_float2(0.f, 0.f); continue; }
+            u[a < 2 ? a : a + 1] = make_float2(E.project(2 * kp, dq[a][0], dq[a][1], dq[a][2], dq[a][3]),
+                                               E.project(2 * kp + 1, dq[a][0], dq[a][1], dq[a][2], dq[a][3]));
+          }
+          u[2] = make_float2(0.f, 0.f);
+          const float2 W2 = weno_delta_x2<Sc::r>(u, eps, P.ppm, P.linw);
+          Wm[2 * kp] = W2.x;
+          Wm[2 * kp + 1] = W2.y;
+        }
+      } else {
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc) {
+          Real u[5];
+          u[0] = E.project(kc, dq[0][0], dq[0][1], dq[0][2], dq[0][3]);
+          u[1] = E.project(kc, dq[1][0], dq[1][1], dq[1][2], dq[1][3]);
+          u[2] = Real(0);
+          u[3] = E.project(kc, dq[2][0], dq[2][1], dq[2][2], dq[2][3]);
+          u[4] = Sc::r == 3 ? E.project(kc, dq[3][0], dq[3][1], dq[3][2], dq[3][3]) : Real(0);
+          Wm[kc] = weno_delta<Sc::r, Real>(u, eps, P.ppm, P.linw);
+        }
       }
       Real dQm[4];
       E.recon(Wm, dQm);
