@@ -53,6 +53,9 @@ def parse():
                     help="also measure the other two precisions and report them beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint cost measurement")
+    ap.add_argument("--profile-tiles", default="2,1",
+                    help="profiling run: tile shape variants 'vx,ve' of the xi and eta passes (the tuner's "
+                         "choice on this workload), set without timing")
     ap.add_argument("--profile", choices=list(PRECISIONS) + ["adjoint"], default=None,
                     help="profiling run for ncu: build the cylinder batch in this precision, evaluate one "
                          "right-hand side, then launch the batched xi sweep three times; 'adjoint': three "
@@ -450,21 +453,27 @@ def measure_adjoint(args, C, nsteps=200, every=14):
         for d in dts:
             fsp.rk3_step(cfg, M, Qm, d, ws=ws)
 
-    def gradient():
+    def gradient(ev=every):
         ax, ay, aq = gx.clone().requires_grad_(True), gy.clone().requires_grad_(True), Q.clone().requires_grad_(True)
         Ma = AD.metrics(cfg, ax, ay)
-        OBJ.shock_vortex_functional(AD.rk3_march(cfg, Ma, aq, dts, every), ax, ay, Ma, win).backward()
+        OBJ.shock_vortex_functional(AD.rk3_march(cfg, Ma, aq, dts, ev), ax, ay, Ma, win).backward()
 
     march()
     gradient()
     t_fwd = C.timed(march, 1)
     t_grad = C.timed(gradient, 1)
+    # every step recorded during the forward pass (no replay): 6 states per step on the device
+    gradient(0)
+    t_grad_tape = C.timed(lambda: gradient(0), 1)
+    tape_gb = nsteps * fsp.rk3_tape(cfg, Q).numel() / 1e9
     return {
         "workload": f"shock_vortex512: 512x512 stretched grid, Mach 1.1 shock + vortex, {SCHEME_NAMES[args.scheme]}, "
                     f"FP64, {nsteps} RK3 steps at CFL 0.5, checkpoint every {every}",
         "rhs_ms": 1e3 * t_rhs, "rhs_vjp_ms": 1e3 * t_rhs_vjp, "rhs_vjp_over_rhs": t_rhs_vjp / t_rhs,
         "rk3_step_ms": 1e3 * t_rk3, "rk3_step_vjp_ms": 1e3 * t_rk3_vjp, "rk3_step_vjp_over_rk3_step": t_rk3_vjp / t_rk3,
         "march_forward_s": t_fwd, "march_gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd,
+        "full_tape": {"march_gradient_s": t_grad_tape, "gradient_over_forward": t_grad_tape / t_fwd,
+                      "tape_gb": tape_gb, "how": "every step recorded in the forward pass, no replay"},
     }
 
 
@@ -480,6 +489,8 @@ def profile_run(args, prec):
     cfg = fsp.Config.from_dict(dict(scheme=args.scheme, precision=PRECISIONS[prec], bc_state=np.tile(free, (4, 1))))
     bt = fsp.Batch(cfg, blocks, states)
     bt.metrics()
+    for d, v in enumerate(args.profile_tiles.split(",")):
+        bt.set_tile_shape(d, int(v))
     bt.rhs()
     D = [torch.empty(q.shape, dtype=torch.float32 if prec == "fp32" else torch.float64, device="cuda") for q in bt.Q]
     for _ in range(3):

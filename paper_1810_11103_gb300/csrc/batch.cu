@@ -113,13 +113,14 @@ __global__ void __launch_bounds__(256) lambda_batch_kernel(const Params* __restr
                                                            const TileRef* __restrict__ tiles,
                                                            const Real* const* q, double* const* lamx,
                                                            double* const* lame) {
-  __shared__ double col[8][33];
+  // maxima in the state's arithmetic, one conversion per line at the atomic
+  __shared__ Real col[8][33];
   const TileRef t = tiles[blockIdx.x];
   const Params& P = Ps[t.block];
   const Real* Q = q[t.block];
   const int ni = P.ni, nj = P.nj;
   const int i = t.bx * 32 + threadIdx.x, j = t.by * 8 + threadIdx.y;
-  double sx = 0.0, se = 0.0;
+  Real sx = Real(0), se = Real(0);
   if (i < ni && j < nj) {
     // |U^| + c|k^| in the state's arithmetic (the splitting only needs A^ constant per line)
     const long long plane = (long long)nj * P.ld, o = (long long)j * P.ld + i;
@@ -127,21 +128,23 @@ __global__ void __launch_bounds__(256) lambda_batch_kernel(const Params* __restr
 #pragma unroll
     for (int v = 0; v < 4; ++v) qq[v] = Q[v * plane + o];
     const Real g = from_f64<Real>(P.gamma);
-    sx = (double)spectral_radius(qq, from_f64<Real>(met_at(P, 0, i, j)), from_f64<Real>(met_at(P, 1, i, j)), g);
-    se = (double)spectral_radius(qq, from_f64<Real>(met_at(P, 2, i, j)), from_f64<Real>(met_at(P, 3, i, j)), g);
+    sx = spectral_radius(qq, from_f64<Real>(met_at(P, 0, i, j)), from_f64<Real>(met_at(P, 1, i, j)), g);
+    se = spectral_radius(qq, from_f64<Real>(met_at(P, 2, i, j)), from_f64<Real>(met_at(P, 3, i, j)), g);
   }
-  double rx = sx;
+  Real rx = sx;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) rx = fmax(rx, __shfl_xor_sync(0xffffffffu, rx, off));
+  for (int off = 16; off > 0; off >>= 1) rx = max(rx, __shfl_xor_sync(0xffffffffu, rx, off));
   if (threadIdx.x == 0 && j < nj)
-    atomicMax(reinterpret_cast<unsigned long long*>(lamx[t.block] + j), (unsigned long long)__double_as_longlong(rx));
+    atomicMax(reinterpret_cast<unsigned long long*>(lamx[t.block] + j),
+              (unsigned long long)__double_as_longlong((double)rx));
   col[threadIdx.y][threadIdx.x] = se;
   __syncthreads();
   if (threadIdx.y == 0 && i < ni) {
-    double m = col[0][threadIdx.x];
+    Real m = col[0][threadIdx.x];
 #pragma unroll
-    for (int r = 1; r < 8; ++r) m = fmax(m, col[r][threadIdx.x]);
-    atomicMax(reinterpret_cast<unsigned long long*>(lame[t.block] + i), (unsigned long long)__double_as_longlong(m));
+    for (int r = 1; r < 8; ++r) m = max(m, col[r][threadIdx.x]);
+    atomicMax(reinterpret_cast<unsigned long long*>(lame[t.block] + i),
+              (unsigned long long)__double_as_longlong((double)m));
   }
 }
 

@@ -269,17 +269,15 @@ __device__ __forceinline__ Prim<Real> prim_of(const Real q[4], Real gamma) {
 // paths take their line maxima in float.
 template <typename Real>
 __device__ __forceinline__ void node_speeds(const Params& P, const Real* __restrict__ Q, int i, int j,
-                                            double& sx, double& se, double& rate) {
+                                            Real& sx, Real& se, Real& rate) {
   const long long plane = (long long)P.nj * P.ld, o = (long long)j * P.ld + i;
   Real q[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) q[v] = Q[v * plane + o];
   const Real g = from_f64<Real>(P.gamma);
-  const Real a = spectral_radius(q, from_f64<Real>(met_at(P, 0, i, j)), from_f64<Real>(met_at(P, 1, i, j)), g);
-  const Real b = spectral_radius(q, from_f64<Real>(met_at(P, 2, i, j)), from_f64<Real>(met_at(P, 3, i, j)), g);
-  sx = (double)a;
-  se = (double)b;
-  rate = (double)((a + b) * recip(from_f64<Real>(met_at(P, 4, i, j))));
+  sx = spectral_radius(q, from_f64<Real>(met_at(P, 0, i, j)), from_f64<Real>(met_at(P, 1, i, j)), g);
+  se = spectral_radius(q, from_f64<Real>(met_at(P, 2, i, j)), from_f64<Real>(met_at(P, 3, i, j)), g);
+  rate = (sx + se) * recip(from_f64<Real>(met_at(P, 4, i, j)));
 }
 
 // --------------------------------------------------------------------------------------

@@ -27,33 +27,35 @@ __global__ void __launch_bounds__(256) lambda_kernel(Params P, const Real* __res
                                                      double* __restrict__ lam_xi,
                                                      double* __restrict__ lam_eta,
                                                      double* __restrict__ cfl_max) {
-  __shared__ double col[8][33];
-  __shared__ double cfl_s[8];
+  // maxima in the state's arithmetic (non-negative values order the same in float and
+  // double); one conversion per line at the atomic
+  __shared__ Real col[8][33];
+  __shared__ Real cfl_s[8];
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
-  double sx = 0.0, se = 0.0, rate = 0.0;
+  Real sx = Real(0), se = Real(0), rate = Real(0);
   if (i < P.ni && j < P.nj) node_speeds(P, Q, i, j, sx, se, rate);
   // row maximum across the warp (one row of 32 nodes)
-  double rx = sx, rr = rate;
+  Real rx = sx, rr = rate;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    rx = fmax(rx, __shfl_xor_sync(0xffffffffu, rx, off));
-    rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, off));
+    rx = max(rx, __shfl_xor_sync(0xffffffffu, rx, off));
+    rr = max(rr, __shfl_xor_sync(0xffffffffu, rr, off));
   }
-  if (threadIdx.x == 0 && j < P.nj) atomic_max_pos(lam_xi + j, rx);
+  if (threadIdx.x == 0 && j < P.nj) atomic_max_pos(lam_xi + j, (double)rx);
   col[threadIdx.y][threadIdx.x] = se;
   if (threadIdx.x == 0) cfl_s[threadIdx.y] = rr;
   __syncthreads();
   if (threadIdx.y == 0 && i < P.ni) {
-    double m = col[0][threadIdx.x];
+    Real m = col[0][threadIdx.x];
 #pragma unroll
-    for (int r = 1; r < 8; ++r) m = fmax(m, col[r][threadIdx.x]);
-    atomic_max_pos(lam_eta + i, m);
+    for (int r = 1; r < 8; ++r) m = max(m, col[r][threadIdx.x]);
+    atomic_max_pos(lam_eta + i, (double)m);
   }
   if (cfl_max && threadIdx.x == 0 && threadIdx.y == 0) {
-    double m = cfl_s[0];
+    Real m = cfl_s[0];
 #pragma unroll
-    for (int r = 1; r < 8; ++r) m = fmax(m, cfl_s[r]);
-    atomic_max_pos(cfl_max, m);
+    for (int r = 1; r < 8; ++r) m = max(m, cfl_s[r]);
+    atomic_max_pos(cfl_max, (double)m);
   }
 }
 

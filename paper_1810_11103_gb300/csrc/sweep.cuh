@@ -43,9 +43,17 @@ struct TileShape {
   static constexpr int THREADS = 256;
   static constexpr int NN = NL * NP, NW = NL * W;
   static constexpr bool SPLIT_MET = !std::is_same<Real, Acc>::value;
-  static constexpr size_t smem_bytes() {
+  static constexpr int NO = NL * T;                  // output nodes
+  static constexpr size_t base_bytes() {
     return sizeof(Real) * ((size_t)(4 + 7) * NN + (SPLIT_MET ? 2 * NN : 0)) +
            sizeof(Acc) * ((size_t)(8 + 2) * NN + (size_t)4 * NW + (NMP == 2 ? (size_t)8 * NW : 0) + NL);
+  }
+  // epilogue operands prefetched per output node: the other direction's difference (modes
+  // 1, 2), Q^n (mode 2), J^-1 (modes 1, 2); 16-byte aligned after the base regions
+  static constexpr size_t ep_off() { return (base_bytes() + 15) / 16 * 16; }
+  static constexpr size_t smem_bytes(int mode) {
+    return mode == 0 ? base_bytes()
+                     : ep_off() + (size_t)NO * (8 + 4 * sizeof(Acc) + (mode == 2 ? 4 * sizeof(Real) : 0));
   }
 };
 
@@ -55,6 +63,15 @@ inline void tile_dims(int scheme, int dir, int& T, int& NL, int variant = 0) {
   NL = shape_nl(dir, variant);
   T = 256 / NL - nmp - 1;
 }
+
+// Asynchronous global-to-shared copies (cp.async, 4 or 8 bytes) of the epilogue operands.
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // One tile (bx along the lines, by across them) of one block.  qtab: every block's state
 // for linked faces (null for a lone block).
@@ -100,6 +117,30 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     sA[threadIdx.x] = line < nlines ? Acc(P.alpha * lam[line]) : Acc(0);
   }
   __syncthreads();
+  // prefetch of the epilogue's global operands, issued now and consumed in the last phase
+  // by the same thread (the node mapping of that phase)
+  double* sJ = reinterpret_cast<double*>(smem_raw + Sh::ep_off());
+  Acc* sDa = reinterpret_cast<Acc*>(sJ + Sh::NO);
+  Real* sQn = reinterpret_cast<Real*>(sDa + 4 * Sh::NO);
+  if constexpr (MODE != MODE_ACC) {
+    for (int k = threadIdx.x; k < Sh::NO; k += Sh::THREADS) {
+      const int l = DIR == 0 ? k / T : k % NL;
+      const int s = DIR == 0 ? k % T : k / NL;
+      const int line = line0 + l;
+      const int g = base + s;
+      if (line >= nlines || g >= n) continue;
+      const int i = DIR == 0 ? g : line, j = DIR == 0 ? line : g;
+      const long long o = (long long)j * P.ld + i;
+      cp_async<8>(sJ + k, P.met + 4 * P.mplane + (long long)(j + G) * P.mld + (i + G));
+#pragma unroll
+      for (int v = 0; v < 4; ++v) cp_async<sizeof(Acc)>(sDa + v * Sh::NO + k, Dacc + v * plane + o);
+      if constexpr (MODE == MODE_STAGE) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cp_async<sizeof(Real)>(sQn + v * Sh::NO + k, Qn + v * plane + o);
+      }
+    }
+    cp_async_commit();
+  }
   // ---- phase 1: nodes ----
   for (int k = threadIdx.x; k < NN; k += Sh::THREADS) {
     const int l = DIR == 0 ? k / NP : k % NL;
@@ -305,15 +346,16 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
 #pragma unroll
       for (int v = 0; v < 4; ++v) Dout[v * plane + o] = R[v];
     } else {
-      const Acc mJ = -recip(from_f64<Acc>(met_at(P, 4, i, j)));
+      cp_async_wait_all();
+      const Acc mJ = -recip(from_f64<Acc>(sJ[k]));
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const Acc d = (Dacc[v * plane + o] + R[v]) * mJ;
+        const Acc d = (sDa[v * Sh::NO + k] + R[v]) * mJ;
         if constexpr (MODE == MODE_RHS) {
           qout[v * plane + o] = Real(d);
         } else {
           const Acc qs = Acc(sQ[v * NN + SI(l, s + 4)]);
-          qout[v * plane + o] = Real(Acc(ca) * Acc(Qn[v * plane + o]) + Acc(cb) * (qs + Acc(dt) * d));
+          qout[v * plane + o] = Real(Acc(ca) * Acc(sQn[v * Sh::NO + k]) + Acc(cb) * (qs + Acc(dt) * d));
         }
       }
     }
@@ -389,7 +431,7 @@ cudaError_t launch_sweep_batch_v(const BatchPass<Real, Acc>& B, int ntiles, doub
                                  cudaStream_t st) {
   using Sh = TileShape<S, DIR, Real, Acc, V>;
   auto kern = sweep_batch_kernel<S, DIR, MODE, Real, Acc, V>;
-  const size_t smem = Sh::smem_bytes();
+  const size_t smem = Sh::smem_bytes(MODE);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -414,7 +456,7 @@ cudaError_t launch_sweep(const Params& P, const Real* Q, const double* lam, cons
   using Sh = TileShape<S, DIR, Real, Acc>;
   const int n = DIR == 0 ? P.ni : P.nj, nlines = DIR == 0 ? P.nj : P.ni;
   dim3 grid((n + Sh::T - 1) / Sh::T, (nlines + Sh::NL - 1) / Sh::NL);
-  const size_t smem = Sh::smem_bytes();
+  const size_t smem = Sh::smem_bytes(MODE);
   auto kern = sweep_kernel<S, DIR, MODE, Real, Acc>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
