@@ -217,6 +217,8 @@ fsp_status fsp_norms(const fsp_block* blk, int precision, const void* A, const v
  * branch is taken as in the forward pass, and the derivative of a line maximum goes to the
  * lowest index attaining it.  Adjoint outputs are accumulated (+=) into the caller's
  * buffers, which the caller zeroes.  The workspace must hold fsp_vjp_workspace_size bytes.
+ * Every adjoint entry point, the size queries included, returns FSP_ERR_UNSUPPORTED for a
+ * precision other than FSP_FP64.
  */
 fsp_status fsp_vjp_workspace_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes);
 

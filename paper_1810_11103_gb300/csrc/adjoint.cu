@@ -569,6 +569,7 @@ Params params_of(const fsp_config& c, const fsp_block& b, const double* metrics)
 extern "C" fsp_status fsp_vjp_workspace_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes) {
   size_t fwd = 0;
   if (fsp_status s = fsp_workspace_size(cfg, blk, &fwd)) return s;
+  if (cfg->precision != FSP_FP64) return FSP_ERR_UNSUPPORTED;
   if (!bytes) return FSP_ERR_INVALID_ARG;
   *bytes = vjp_ws(*cfg, *blk, fwd).total;
   return FSP_OK;

@@ -52,3 +52,60 @@ def test_host_only_calls(so):
         fsp.workspace_size(fsp.Config(bc=(0, 1, 0, 0)), 16, 16)   # unpaired periodic face
     with pytest.raises(fsp.FspError):
         fsp.workspace_size(fsp.Config(bc=(1, 1, 1, 1)), 8, 16)    # too few nodes to reflect
+
+
+def _ws_code(fsp, cfg, ni, nj, ld=None):
+    b = fsp._block_shape(cfg, ni, nj, ld)
+    n = ctypes.c_size_t()
+    return fsp.lib().fsp_workspace_size(ctypes.byref(cfg._c()), ctypes.byref(b), ctypes.byref(n))
+
+
+def test_argument_validation_on_the_host(so):
+    # every case is refused before anything touches the device (no GPU needed)
+    from paper_1810_11103_gb300 import fsp
+    per = fsp.Config(scheme=2, bc=(0, 0, 0, 0))
+    wall = fsp.Config(scheme=2, bc=(3, 3, 1, 1))
+    assert _ws_code(fsp, per, 1, 1) == 0                   # a single periodic node is a valid block
+    assert _ws_code(fsp, per, 0, 16) == 1                  # empty
+    assert _ws_code(fsp, per, 16, 0) == 1
+    assert _ws_code(fsp, per, 16, 16, ld=15) == 1          # row stride below the row length
+    assert _ws_code(fsp, wall, 9, 9) == 0                  # smallest non-periodic extent
+    assert _ws_code(fsp, wall, 8, 9) == 1
+    assert _ws_code(fsp, wall, 9, 8) == 1
+    assert _ws_code(fsp, fsp.Config(scheme=2, bc=(0, 1, 0, 0)), 16, 16) == 1   # unpaired periodic face
+    assert _ws_code(fsp, per, 8 * 65535, 9) == 0           # the longest lines the sweep grids allow
+    assert _ws_code(fsp, per, 8 * 65535 + 1, 9) == 1
+    assert _ws_code(fsp, per, 9, 2 * 65535) == 0
+    assert _ws_code(fsp, per, 9, 2 * 65535 + 1) == 1
+    for bad in (dict(gamma=1.0), dict(lf_alpha=0.0), dict(eps=0.0), dict(interp=2), dict(precision=3),
+                dict(bc=(6, 6, 0, 0))):
+        assert _ws_code(fsp, fsp.Config(**dict(dict(scheme=2, bc=(0, 0, 0, 0)), **bad)), 16, 16) == 1, bad
+    # the adjoint is FP64 only
+    b = fsp._block_shape(per, 16, 16)
+    n = ctypes.c_size_t()
+    c32 = fsp.Config(scheme=2, bc=(0, 0, 0, 0), precision=1)
+    assert fsp.lib().fsp_vjp_workspace_size(ctypes.byref(c32._c()), ctypes.byref(b), ctypes.byref(n)) == 2
+    assert fsp.lib().fsp_rk3_tape_size(ctypes.byref(c32._c()), ctypes.byref(b), ctypes.byref(n)) == 2
+    # null and host pointers are refused
+    assert fsp.lib().fsp_rhs(ctypes.byref(per._c()), ctypes.byref(b), None, None, None, None, 0, None) == 1
+    host = (ctypes.c_double * 4096)()
+    hp = ctypes.cast(host, ctypes.c_void_p)
+    assert fsp.lib().fsp_rhs(ctypes.byref(per._c()), ctypes.byref(b), hp, hp, hp, hp, 1 << 20, None) == 1
+
+
+def test_batch_argument_validation_on_the_host(so):
+    from paper_1810_11103_gb300 import fsp
+    L = fsp.lib()
+    cfg = fsp.Config(scheme=2)
+    h = ctypes.c_void_p()
+    blk = (fsp._Block * 2)(fsp._block_shape(cfg, 16, 16), fsp._block_shape(cfg, 16, 16))
+    links = (fsp._Link * 8)()
+    ok_bc = (ctypes.c_int * 8)(1, 1, 1, 1, 1, 1, 1, 1)
+    assert L.fsp_batch_create(ctypes.byref(cfg._c()), 0, blk, ok_bc, links, ctypes.byref(h)) == 1   # no blocks
+    bad = (ctypes.c_int * 8)(5, 1, 1, 1, 1, 1, 1, 1)       # a link to a block that does not exist
+    links[0].nbr = 7
+    assert L.fsp_batch_create(ctypes.byref(cfg._c()), 2, blk, bad, links, ctypes.byref(h)) == 1
+    links[0].nbr, links[0].face = 1, 1                      # a link whose faces do not match in length
+    blk[1] = fsp._block_shape(cfg, 16, 12)
+    assert L.fsp_batch_create(ctypes.byref(cfg._c()), 2, blk, bad, links, ctypes.byref(h)) == 1
+    assert not h.value

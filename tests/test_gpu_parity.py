@@ -210,3 +210,16 @@ def test_full_size_riemann_1024_parity(F):
     x, y = I.riemann_grid(1024, 0.3, 1811)
     q = I.riemann_quadrants(x, y)
     _check_case(F, _cfg(scheme=2, bc=(1, 1, 1, 1)), x, y, q)
+
+
+@pytest.mark.parametrize("shape", [(9, 2 * 65535), (8 * 65535, 9)])
+def test_rhs_parity_longest_lines(F, shape):
+    # the largest line counts the sweep grids allow (65535 CTAs across the lines of the xi
+    # sweep, 2 rows each, and of the eta sweep, 8 columns each), transmissive faces
+    ni, nj = shape
+    h = 1.0 / 64
+    x = np.broadcast_to(h * np.arange(ni, dtype=np.float64)[None, :], (nj, ni)).copy()
+    y = np.broadcast_to(0.7 * h * np.arange(nj, dtype=np.float64)[:, None], (nj, ni)).copy()
+    x, y = I.randomize(x, y, h, 0.7 * h, np.full((nj, ni), 0.2), seed=12)
+    q = I.random_state((nj, ni), seed=13)
+    _check_case(F, _cfg(scheme=2, bc=(1, 1, 1, 1)), x, y, q)
