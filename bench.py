@@ -93,10 +93,15 @@ def workload_config(args, nodes, nblocks):
             "l2": "flushed between timed steps (256 MiB write outside the events)"}
 
 
+# the sources the batched sweep kernels (the roofline kernels) are built from
+SWEEP_SOURCES = ("sweep.cuh", "fsp_device.cuh", "fsp_internal.h", "batch.cu", "batch_fp64.cu", "batch_fp32.cu",
+                 "batch_mixed.cu")
+
+
 def source_hash():
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_1810_11103_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
+    for f in SWEEP_SOURCES:
         with open(os.path.join(src, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
