@@ -72,9 +72,16 @@ def _check_case(F, cfgd, x, y, q, tol=TOL_RHS):
     M_o = O.metrics(cfgd, x, y)
     M_g = F.metrics(cfg, _dev(x), _dev(y))
     Mh = _host(M_g)
-    # the four metric planes are coordinate derivatives of one scale; J^-1 has its own
-    assert np.abs(Mh[:4] - M_o[:4]).max() < TOL_MET * np.abs(M_o[:4]).max()
-    assert _rel(Mh[4], M_o[4]) < TOL_MET
+    # the four metric planes are coordinate derivatives of one scale; J^-1 has its own.
+    # Every intermediate of a metric is a combination of coordinates, so each side rounds at
+    # a few ulps of the largest coordinate X (the coefficients' absolute sum is about 3):
+    # an absolute floor of 32 eps X on the planes, and through the two products of J^-1
+    # 4 x that floor x the largest metric.  It matters only for lines far from the origin.
+    X = max(np.abs(x).max(), np.abs(y).max())
+    floor = 32 * np.finfo(np.float64).eps * X
+    m4 = np.abs(M_o[:4]).max()
+    assert np.abs(Mh[:4] - M_o[:4]).max() < TOL_MET * m4 + floor
+    assert np.abs(Mh[4] - M_o[4]).max() < TOL_MET * np.abs(M_o[4]).max() + 4 * floor * m4
     R_o = O.rhs(cfgd, M_o, q)
     R_g = F.rhs(cfg, _dev(M_o), _dev(q))
     err = _rel(_host(R_g), R_o)
