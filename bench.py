@@ -8,11 +8,13 @@ graph through fsp_batch_rk3_step.  Metric: Mcell-RHS/s = nodes x right-hand side
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
                     [--workload cylinder64|vortex256] [--precision fp64|fp32|mixed]
-                    [--no-all-precisions] [--no-cpu-baseline]
+                    [--no-all-precisions] [--no-cpu-baseline] [--accuracy none|quick|full]
 
 The headline `value` is the FP64 path.  Beside it: the FP32 and mixed FP32/FP64 paths of the
 same workload ("fp32", "fp32_mixed"), each with its own roofline, and the same FP64 step as a
 loop of per-block fsp_rk3_step calls ("per_block_fp64", links read as transmissive).
+Beside them ("accuracy"): final-time density errors of each precision on the 256 x 256 vortex
+(and with --accuracy full the 1024 x 1024 Riemann problem) and the free-stream residual.
 Under torchrun every rank runs the workload on its own GPU (independent problems, weak
 scaling, no data-path collective); rank 0 prints one JSON line.
 """
@@ -53,6 +55,9 @@ def parse():
                     help="also measure the other two precisions and report them beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint cost measurement")
+    ap.add_argument("--accuracy", choices=["none", "quick", "full"], default="quick",
+                    help="final-time errors per precision: quick = the 256 x 256 vortex over one period and "
+                         "the free-stream residual; full adds the 1024 x 1024 Riemann problem to t = 0.3")
     ap.add_argument("--profile-tiles", default="2,1",
                     help="profiling run: tile shape variants 'vx,ve' of the xi and eta passes (the tuner's "
                          "choice on this workload), set without timing")
@@ -482,6 +487,94 @@ def measure_adjoint(args, C, nsteps=200, every=14):
     }
 
 
+def _march(fsp, cfg, M, Q, dts, ws):
+    for d in dts:
+        fsp.rk3_step(cfg, M, Q, d, ws=ws)
+    return Q
+
+
+def _cfl_schedule(fsp, cfg, M, Q, tfinal, ws, cfl=0.5):
+    """The time steps of an FP64 march at the CFL number to tfinal (last step clipped),
+    marching Q in place: dt from fsp_cfl_dt before every step."""
+    dts, t = [], 0.0
+    while t < tfinal - 1e-14:
+        d = min(float(fsp.cfl_dt(cfg, M, Q, cfl, ws=ws).item()), tfinal - t)
+        fsp.rk3_step(cfg, M, Q, d, ws=ws)
+        dts.append(d)
+        t += d
+    return dts
+
+
+def _rho_err(a, b):
+    e = (a[0] - b[0]).double()
+    return {"L2": float(e.pow(2).mean().sqrt()), "Linf": float(e.abs().max())}
+
+
+def measure_accuracy(args, C, full=False):
+    """Final-time errors of each precision on the paper-shaped synthetic cases.
+    vortex256: the 256 x 256 randomised periodic vortex over one period (t = 10, where the
+    exact solution is the initial state), every scheme, CFL 0.5 (the FP64 march's steps
+    replayed by the float paths): density L2 (root mean square) and Linf against the exact
+    solution, and of each float path against the FP64 path.  free_stream: uniform flow
+    (1, 1, 1, 1) on the same grid, max |dQ/dt| of one right-hand side and L2 of v - v0 after
+    100 steps.  riemann1024 (full only): the four-quadrant problem on the partially randomised
+    1024 x 1024 grid to t = 0.3, WENOIU5-1MP, float paths against FP64."""
+    import numpy as np
+    torch, fsp = C.torch, C.fsp
+    from paper_1810_11103_gb300 import inputs as I
+    dev = C.dev
+    x, y, per, q = vortex_workload()
+    gx, gy = torch.as_tensor(x, device=dev), torch.as_tensor(y, device=dev)
+    out = {"vortex256": {}, "free_stream": {}}
+    for scheme in range(4):
+        res = {}
+        cfg = {p: fsp.Config.from_dict(dict(scheme=scheme, precision=v, period=per)) for p, v in PRECISIONS.items()}
+        M = fsp.metrics(cfg["fp64"], gx, gy)
+        Q0 = torch.as_tensor(q, device=dev)
+        Q64 = Q0.clone()
+        dts = _cfl_schedule(fsp, cfg["fp64"], M, Q64, 10.0, fsp.workspace(cfg["fp64"], Q64))
+        res["steps"] = len(dts)
+        res["fp64"] = {"vs_exact": _rho_err(Q64, Q0)}
+        for p in ("fp32", "mixed"):
+            Qs = Q0.float().contiguous()
+            _march(fsp, cfg[p], M, Qs, dts, fsp.workspace(cfg[p], Qs))
+            res[p] = {"vs_exact": _rho_err(Qs, Q0), "vs_fp64": _rho_err(Qs, Q64)}
+        out["vortex256"][SCHEME_NAMES[scheme]] = res
+        # free stream on the same grid
+        fs = {}
+        qu = I.uniform_state(x.shape, 1.0, 1.0, 1.0, 1.0)
+        for p, c in cfg.items():
+            sdt = torch.float64 if p == "fp64" else torch.float32
+            Qu = torch.as_tensor(qu, dtype=sdt, device=dev)
+            ws = fsp.workspace(c, Qu)
+            r = float(fsp.rhs(c, M, Qu, ws=ws).abs().max())
+            d = float(fsp.cfl_dt(cfg["fp64"], M, Qu.double(), 0.5).item())
+            _march(fsp, c, M, Qu, [d] * 100, ws)
+            v = (Qu[2].double() / Qu[0].double() - 1.0)
+            fs[p] = {"rhs_max": r, "v_L2_after_100_steps": float(v.pow(2).mean().sqrt())}
+        out["free_stream"][SCHEME_NAMES[scheme]] = fs
+    out["vortex256"]["how"] = ("t = 10 (one period), CFL 0.5 steps of the FP64 march replayed by the float paths; "
+                               "density errors, L2 = root mean square over nodes")
+    if full:
+        xr, yr = I.riemann_grid(1024, 0.3, 1811)
+        qr = I.riemann_quadrants(xr, yr)
+        cfg = {p: fsp.Config.from_dict(dict(scheme=args.scheme, precision=v, bc=(1, 1, 1, 1)))
+               for p, v in PRECISIONS.items()}
+        M = fsp.metrics(cfg["fp64"], torch.as_tensor(xr, device=dev), torch.as_tensor(yr, device=dev))
+        Q0 = torch.as_tensor(qr, device=dev)
+        Q64 = Q0.clone()
+        dts = _cfl_schedule(fsp, cfg["fp64"], M, Q64, 0.3, fsp.workspace(cfg["fp64"], Q64))
+        rr = {"steps": len(dts), "scheme": SCHEME_NAMES[args.scheme]}
+        for p in ("fp32", "mixed"):
+            Qs = Q0.float().contiguous()
+            _march(fsp, cfg[p], M, Qs, dts, fsp.workspace(cfg[p], Qs))
+            e = _rho_err(Qs, Q64)
+            e["Linf_rel"] = e["Linf"] / float(Q64[0].abs().max())
+            rr[p] = {"vs_fp64": e}
+        out["riemann1024"] = rr
+    return out
+
+
 def profile_run(args, prec):
     """Minimal launch sequence for a profiler: metrics, one right-hand side (line maxima,
     xi sweep, eta sweep), then three launches of the batched xi sweep alone."""
@@ -565,6 +658,7 @@ def main():
             if p != args.precision:
                 others[p] = measure(p)
     adjoint = None if args.no_adjoint else measure_adjoint(args, C)
+    accuracy = None if args.accuracy == "none" else measure_accuracy(args, C, full=args.accuracy == "full")
     if rank == 0:
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
@@ -587,6 +681,8 @@ def main():
             line["per_block_fp64"] = head["per_block_fp64"]
         if not args.no_adjoint:
             line["adjoint"] = adjoint
+        if accuracy is not None:
+            line["accuracy"] = accuracy
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

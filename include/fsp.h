@@ -318,9 +318,13 @@ fsp_status fsp_batch_rk3_step(fsp_batch* b, double dt, void* stream);
  * advances the state like any other step. */
 fsp_status fsp_batch_capture_graph(fsp_batch* b, double dt, void* stream);
 
-/* Tile shapes.  Every pass uses 256-thread tiles of NL grid lines; the variant sets NL:
+/* Tile shapes.  Variants 0-2 of a pass use 256-thread tiles of NL grid lines:
  *   xi  (dir 0): variant 0, 1, 2 = 2, 1, 4 lines of 128, 256, 64 interfaces;
  *   eta (dir 1): variant 0, 1, 2 = 8, 4, 16 lines of 32, 64, 16 interfaces.
+ * xi variant 3 marches: each warp walks one row segment (rows longer than 512 nodes are cut
+ * into equal segments) 32 nodes at a time, keeping the stencil nodes in a shared-memory
+ * ring, with four rows per 128-thread CTA; fsp_batch_tile_shape reports 4 lines and 512
+ * output nodes for it.  The eta pass has variants 0-2 only.
  * Results do not depend on the variant (each interface is computed the same way); the
  * speed does.  fsp_batch_tune picks, for each direction, the fastest variant on this
  * handle's blocks and bound state: it times five launches of each variant's pass (after two

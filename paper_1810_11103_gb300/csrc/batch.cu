@@ -247,6 +247,7 @@ void tiles_for(const fsp_batch* h, int dir, int v, std::vector<TileRef>& out) {
   for (int b = 0; b < h->nb; ++b) {
     const fsp_block& B = h->blk[b];
     const int n = dir == 0 ? B.ni : B.nj, nl = dir == 0 ? B.nj : B.ni;
+    if (dir == 0 && v == MARCH) T = march_seg_len(n);   // rows split into equal segments
     for (int by = 0; by < (nl + NL - 1) / NL; ++by)
       for (int bx = 0; bx < (n + T - 1) / T; ++bx) out.push_back({b, bx, by});
   }
@@ -255,7 +256,7 @@ void tiles_for(const fsp_batch* h, int dir, int v, std::vector<TileRef>& out) {
 // Switch one direction to shape variant v: the host and device tile tables (the device is
 // synchronised first, since queued launches may read the table) and any captured graph.
 fsp_status set_tiles(fsp_batch* h, int dir, int v) {
-  if (v < 0 || v >= NVARIANT) return FSP_ERR_INVALID_ARG;
+  if (v < 0 || v >= nvariant(dir)) return FSP_ERR_INVALID_ARG;
   std::vector<TileRef>& t = dir == 0 ? h->tx : h->te;
   tiles_for(h, dir, v, t);
   if (cudaDeviceSynchronize() != cudaSuccess) return FSP_ERR_CUDA;
@@ -330,6 +331,7 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
     std::vector<TileRef> t;
     tiles_for(h, 0, v, t);
     h->tx_cap = std::max(h->tx_cap, t.size());
+    if (v >= nvariant(1)) continue;
     tiles_for(h, 1, v, t);
     h->te_cap = std::max(h->te_cap, t.size());
   }
@@ -585,8 +587,8 @@ bool table_lookup(const char* path, const std::string& key, int* vx, int* ve) {
     if (line[0] == '#') continue;
     char k[512];
     int a, b;
-    if (std::sscanf(line, "%511s %d %d", k, &a, &b) == 3 && key == k && a >= 0 && a < NVARIANT && b >= 0 &&
-        b < NVARIANT) {
+    if (std::sscanf(line, "%511s %d %d", k, &a, &b) == 3 && key == k && a >= 0 && a < nvariant(0) && b >= 0 &&
+        b < nvariant(1)) {
       *vx = a;
       *ve = b;
       found = true;  // the last entry for a key wins
@@ -612,7 +614,7 @@ fsp_status fsp_batch_tune(fsp_batch* h, const char* table_path, void* stream) {
   if (fsp_status s = batch_lambda(h, T_Q0, st)) return s;
   float best_ms[2] = {0, 0};
   for (int dir = 0; dir < 2; ++dir) {
-    for (int v = 0; v < NVARIANT; ++v) {
+    for (int v = 0; v < nvariant(dir); ++v) {
       if (fsp_status s = set_tiles(h, dir, v)) return s;
       float ms = 0;
       if (fsp_status s = time_direction(h, dir, st, &ms)) return s;

@@ -25,12 +25,98 @@ enum { MODE_ACC = 0, MODE_RHS = 1, MODE_STAGE = 2 };
 
 // Tile shapes: 256 threads, NL grid lines x W interface slots per CTA.  Variant 0 is the
 // default; fsp_batch_tune may pick another per direction for a batch.
-//   xi:  (NL, W) = (2, 128), (1, 256), (4, 64)
+//   xi:  (NL, W) = (2, 128), (1, 256), (4, 64); variant 3: marching warps (below)
 //   eta: (NL, W) = (8, 32),  (4, 64),  (16, 16)
-constexpr int NVARIANT = 3;
+constexpr int NVARIANT = 4;                         // variants of the xi pass
+constexpr int MARCH = 3;                            // the marching xi variant
+constexpr int nvariant(int dir) { return dir == 0 ? 4 : 3; }
 constexpr int shape_nl(int dir, int v) {
   return dir == 0 ? (v == 1 ? 1 : v == 2 ? 4 : 2) : (v == 1 ? 4 : v == 2 ? 16 : 8);
 }
+
+// Shared-memory vectors of 16 bytes.  A 4-value quantity of node o is one float4 (FP32) or
+// two double2 held in two arrays of n entries (FP64), so a warp reading consecutive nodes
+// issues conflict-free 128-bit loads.
+template <typename T>
+__device__ __forceinline__ void st4(T* b, int n, int o, T a0, T a1, T a2, T a3) {
+  if constexpr (sizeof(T) == 4) {
+    reinterpret_cast<float4*>(b)[o] = make_float4(a0, a1, a2, a3);
+  } else {
+    reinterpret_cast<double2*>(b)[o] = make_double2(a0, a1);
+    reinterpret_cast<double2*>(b + 2 * n)[o] = make_double2(a2, a3);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void ld4(const T* b, int n, int o, T v[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 t = reinterpret_cast<const float4*>(b)[o];
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const double2 s = reinterpret_cast<const double2*>(b)[o], t = reinterpret_cast<const double2*>(b + 2 * n)[o];
+    v[0] = s.x; v[1] = s.y; v[2] = t.x; v[3] = t.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st2(T* b, int o, T a0, T a1) {
+  if constexpr (sizeof(T) == 4) reinterpret_cast<float2*>(b)[o] = make_float2(a0, a1);
+  else reinterpret_cast<double2*>(b)[o] = make_double2(a0, a1);
+}
+template <typename T>
+__device__ __forceinline__ void ld2(const T* b, int o, T& x, T& y) {
+  if constexpr (sizeof(T) == 4) { const float2 t = reinterpret_cast<const float2*>(b)[o]; x = t.x; y = t.y; }
+  else { const double2 t = reinterpret_cast<const double2*>(b)[o]; x = t.x; y = t.y; }
+}
+
+// Staged node data of n nodes (tile positions or ring slots), 16-byte vectors:
+//   fp, fm  split node fluxes f+- = (E^ +- A^ Q)/2 (Acc, 4 values)
+//   ma      direction metrics in Acc (2 values)
+//   q       state (Real, 4 values)
+//   p0, p1  primitives (u, v, c, 1/c) and (H, b1, |u|^2/2, 0) of the projection
+//   mr      direction metrics rounded to Real (only when Real differs from Acc)
+template <typename Real, typename Acc>
+struct Staged {
+  static constexpr bool SPLIT = !std::is_same<Real, Acc>::value;
+  Acc *fp, *fm, *ma;
+  Real *q, *p0, *p1, *mr;
+  int n;
+  // arrays of padded length (a multiple of 4 nodes keeps every array 16-byte aligned)
+  static constexpr int padded(int nn) { return (nn + 3) / 4 * 4; }
+  static constexpr size_t bytes(int nn) {
+    return sizeof(Acc) * (size_t)padded(nn) * 10 + sizeof(Real) * (size_t)padded(nn) * (12 + (SPLIT ? 2 : 0));
+  }
+  __device__ __forceinline__ void carve(unsigned char* base, int nn0) {
+    const int nn = padded(nn0);
+    n = nn;
+    fp = reinterpret_cast<Acc*>(base);
+    fm = fp + 4 * nn;
+    ma = fm + 4 * nn;
+    q = reinterpret_cast<Real*>(ma + 2 * nn);
+    p0 = q + 4 * nn;
+    p1 = p0 + 4 * nn;
+    mr = SPLIT ? p1 + 4 * nn : nullptr;
+  }
+  __device__ __forceinline__ void store(int o, const Real qq[4], const Prim<Real>& w, Acc amx, Acc amy,
+                                        const Acc f[4], const Acc g[4], double mx, double my) const {
+    st4(fp, n, o, f[0], f[1], f[2], f[3]);
+    st4(fm, n, o, g[0], g[1], g[2], g[3]);
+    st2(ma, o, amx, amy);
+    if constexpr (SPLIT) st2(mr, o, from_f64<Real>(mx), from_f64<Real>(my));
+    st4(q, n, o, qq[0], qq[1], qq[2], qq[3]);
+    st4(p0, n, o, w.u, w.v, w.c, w.cinv);
+    st4(p1, n, o, w.H, w.b1, w.h2, Real(0));
+  }
+  __device__ __forceinline__ void met_real(int o, Real& x, Real& y) const {
+    if constexpr (SPLIT) ld2(mr, o, x, y);
+    else ld2(ma, o, x, y);
+  }
+  __device__ __forceinline__ void prim(int o, Prim<Real>& w) const {
+    Real a[4], b[4];
+    ld4(p0, n, o, a);
+    ld4(p1, n, o, b);
+    w.u = a[0]; w.v = a[1]; w.c = a[2]; w.cinv = a[3];
+    w.H = b[0]; w.b1 = b[1]; w.h2 = b[2];
+  }
+};
 
 template <int S, int DIR, typename Real, typename Acc, int V = 0>
 struct TileShape {
@@ -42,29 +128,54 @@ struct TileShape {
   static constexpr int PLO = -NMP;                   // first interface p (of p + 1/2)
   static constexpr int THREADS = 256;
   static constexpr int NN = NL * NP, NW = NL * W;
-  static constexpr bool SPLIT_MET = !std::is_same<Real, Acc>::value;
   static constexpr int NO = NL * T;                  // output nodes
-  static constexpr size_t base_bytes() {
-    return sizeof(Real) * ((size_t)(4 + 7) * NN + (SPLIT_MET ? 2 * NN : 0)) +
-           sizeof(Acc) * ((size_t)(8 + 2) * NN + (size_t)4 * NW + (NMP == 2 ? (size_t)8 * NW : 0) + NL);
-  }
+  // shared memory: staged nodes, then h (4 Acc per interface), the two-midpoint fluxes
+  // f+- (8 Acc per interface, two-midpoint schemes), A^ per line
+  static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(NN); }
+  static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * (size_t)NW; }
+  static constexpr size_t o_a() { return o_f() + (NMP == 2 ? sizeof(Acc) * 8 * (size_t)NW : 0); }
+  static constexpr size_t base_bytes() { return (o_a() + sizeof(Acc) * NL + 15) / 16 * 16; }
   // epilogue operands prefetched per output node: the other direction's difference (modes
   // 1, 2), Q^n (mode 2), J^-1 (modes 1, 2); 16-byte aligned after the base regions
-  static constexpr size_t ep_off() { return (base_bytes() + 15) / 16 * 16; }
+  static constexpr size_t ep_off() { return base_bytes(); }
   static constexpr size_t smem_bytes(int mode) {
     return mode == 0 ? base_bytes()
                      : ep_off() + (size_t)NO * (8 + 4 * sizeof(Acc) + (mode == 2 ? 4 * sizeof(Real) : 0));
   }
 };
 
-// Host view of the tile shape: output nodes per line T and lines per CTA NL.
+// Marching xi pass: each warp owns one grid row segment of at most MARCH_SEG nodes and
+// walks along it 32 nodes at a time; four warps (four rows of one block) per CTA.
+constexpr int MARCH_WARPS = 4;
+constexpr int MARCH_SEG = 512;
+constexpr int RING = 64;                             // node ring slots per warp
+__host__ __device__ constexpr int march_seg_len(int n) {
+  const int nseg = (n + MARCH_SEG - 1) / MARCH_SEG;
+  const int per = (n + nseg - 1) / nseg;
+  return (per + 31) / 32 * 32;
+}
+template <int S, typename Real, typename Acc>
+struct MarchShape {
+  static constexpr int NMP = Scheme<S>::nmp;
+  // per warp: the node ring, h per ring slot (4 Acc), f+- at the midpoints (two-midpoint
+  // schemes, 8 Acc per slot), and the raw node prefetch (state, two metrics) of 32 lanes
+  static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(RING); }
+  static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * RING; }
+  static constexpr size_t o_raw() { return o_f() + (NMP == 2 ? sizeof(Acc) * 8 * RING : 0); }
+  static constexpr size_t warp_bytes() { return o_raw() + 32 * (4 * sizeof(Real) + 16); }
+  static constexpr size_t smem_bytes() { return MARCH_WARPS * warp_bytes(); }
+};
+
+// Host view of the tile shape: output nodes per line T and lines per CTA NL (for the
+// marching variant: rows per CTA, and the longest segment a warp walks).
 inline void tile_dims(int scheme, int dir, int& T, int& NL, int variant = 0) {
   const int nmp = (scheme == S32 || scheme == S52) ? 2 : 1;
+  if (dir == 0 && variant == MARCH) { NL = MARCH_WARPS; T = MARCH_SEG; return; }
   NL = shape_nl(dir, variant);
   T = 256 / NL - nmp - 1;
 }
 
-// Asynchronous global-to-shared copies (cp.async, 4 or 8 bytes) of the epilogue operands.
+// Asynchronous global-to-shared copies (cp.async, 4 or 8 bytes).
 template <int B>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -72,6 +183,149 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// --------------------------------------------------------------------------------------
+// Per-node and per-interface arithmetic, shared by the tile and the marching kernels (the
+// same operations in the same order, so every layout gives the same results)
+// --------------------------------------------------------------------------------------
+// A node (Section 2.3): primitives of the projection and the split fluxes
+// f+- = (E^ +- A^ Q)/2, E^ = mx E + my F with the metric products in Acc.
+template <typename Real, typename Acc>
+__device__ __forceinline__ void node_split(const Real q[4], double mx, double my, Real gamma, Acc hA,
+                                           Prim<Real>& w, Acc& amx, Acc& amy, Acc fp[4], Acc fm[4]) {
+  w = prim_of(q, gamma);
+  const Real p = (gamma - Real(1)) * (q[3] - q[0] * w.h2);
+  amx = from_f64<Acc>(mx);
+  amy = from_f64<Acc>(my);
+  const Acc U = amx * Acc(w.u) + amy * Acc(w.v);
+  const Acc E[4] = {Acc(q[0]) * U, Acc(q[1]) * U + amx * Acc(p), Acc(q[2]) * U + amy * Acc(p), Acc(q[3] + p) * U};
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const Acc e = Acc(0.5) * E[v], aq = hA * Acc(q[v]);
+    fp[v] = e + aq;
+    fm[v] = e - aq;
+  }
+}
+
+// The interface p + 1/2 between staged nodes at(0) (node p) and at(1) (node p + 1); at(m)
+// gives the staged index of node p + m, m = -2..3.  Characteristic direction from the
+// averaged metrics (Section 3.4), eigenvectors at Q_p ("+" side, stencil p-2..p+2) and at
+// Q_{p+1} ("-" side, the mirror), WENO interpolation of the characteristic differences, the
+// states Q+- at the midpoint, and the split midpoint fluxes fs[0] = f+, fs[1] = f- with the
+// midpoint metrics interpolated as in the metric evaluation (Section 2.4).
+template <int S, typename Real, typename Acc, typename At>
+__device__ __forceinline__ void interface_fluxes(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
+                                                 int ppm, int linw, int interp, Acc A, Acc fs[2][4]) {
+  using Sc = Scheme<S>;
+  const int o0 = at(0), o1 = at(1);
+  Real m0x, m0y, m1x, m1y;
+  st.met_real(o0, m0x, m0y);
+  st.met_real(o1, m1x, m1y);
+  const Real mbx = Real(0.5) * (m0x + m1x);
+  const Real mby = Real(0.5) * (m0y + m1y);
+  const Real rn = rsq(mbx * mbx + mby * mby);
+  const Real nx = mbx * rn, ny = mby * rn;
+
+  Real Qs[2][4];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int oc = side == 0 ? o0 : o1;
+    Prim<Real> w;
+    st.prim(oc, w);
+    Eig<Real> E;
+    E.build(w, nx, ny);
+    Real qc[4];
+    ld4(st.q, st.n, oc, qc);
+    // state differences to the centre at the stencil offsets -2, -1, +1, +2
+    Real dq[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int m = a < 2 ? a - 2 : a - 1;
+      if (Sc::r == 2 && m == 2) { dq[a][0] = dq[a][1] = dq[a][2] = dq[a][3] = Real(0); continue; }
+      Real t[4];
+      ld4(st.q, st.n, at(side == 0 ? m : 1 - m), t);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dq[a][v] = t[v] - qc[v];
+    }
+    Real Wm[4];
+    if constexpr (std::is_same<Real, float>::value) {
+      // components (0, 1) and (2, 3) in the two lanes of packed float arithmetic
+#pragma unroll
+      for (int kp = 0; kp < 2; ++kp) {
+        float2 u[5];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (Sc::r == 2 && a == 3) { u[4] = make_float2(0.f, 0.f); continue; }
+          u[a < 2 ? a : a + 1] = make_float2(E.project(2 * kp, dq[a][0], dq[a][1], dq[a][2], dq[a][3]),
+                                             E.project(2 * kp + 1, dq[a][0], dq[a][1], dq[a][2], dq[a][3]));
+        }
+        u[2] = make_float2(0.f, 0.f);
+        const float2 W2 = weno_delta_x2<Sc::r>(u, eps, ppm, linw);
+        Wm[2 * kp] = W2.x;
+        Wm[2 * kp + 1] = W2.y;
+      }
+    } else {
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+        Real u[5];
+        u[0] = E.project(kc, dq[0][0], dq[0][1], dq[0][2], dq[0][3]);
+        u[1] = E.project(kc, dq[1][0], dq[1][1], dq[1][2], dq[1][3]);
+        u[2] = Real(0);
+        u[3] = E.project(kc, dq[2][0], dq[2][1], dq[2][2], dq[2][3]);
+        u[4] = Sc::r == 3 ? E.project(kc, dq[3][0], dq[3][1], dq[3][2], dq[3][3]) : Real(0);
+        Wm[kc] = weno_delta<Sc::r, Real>(u, eps, ppm, linw);
+      }
+    }
+    Real dQm[4];
+    E.recon(Wm, dQm);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Qs[side][v] = qc[v] + dQm[v];
+  }
+
+  Acc vx[6], vy[6];
+#pragma unroll
+  for (int kk = 0; kk < 6; ++kk) ld2(st.ma, at(kk - 2), vx[kk], vy[kk]);
+  const Acc mmx = mid_interp(interp, Sc::r == 3, vx);
+  const Acc mmy = mid_interp(interp, Sc::r == 3, vy);
+  // split midpoint fluxes f+ = (E^(Q+) + A^ Q+)/2, f- = (E^(Q-) - A^ Q-)/2
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const Real* q = Qs[side];
+    const Real rinv = recip(q[0]);
+    const Real u = q[1] * rinv, v = q[2] * rinv;
+    const Real pr = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
+    const Acc U = mmx * Acc(u) + mmy * Acc(v);
+    const Acc sg = side == 0 ? A : -A;
+    fs[side][0] = Acc(0.5) * (Acc(q[0]) * U + sg * Acc(q[0]));
+    fs[side][1] = Acc(0.5) * (Acc(q[1]) * U + mmx * Acc(pr) + sg * Acc(q[1]));
+    fs[side][2] = Acc(0.5) * (Acc(q[2]) * U + mmy * Acc(pr) + sg * Acc(q[2]));
+    fs[side][3] = Acc(0.5) * (Acc(q[3] + pr) * U + sg * Acc(q[3]));
+  }
+}
+
+// h = h+ + h- at p + 1/2 (Eqs. 3.4, 3.8, 3.16, 3.20; h- the mirror of h+): the midpoint
+// terms m0 (f+_{p+1/2} + f-_{p+1/2}) + m1 (f+_{p-1/2} + f-_{p+3/2}) given as mid0 = f+ + f- at
+// p + 1/2 and mid1 = f+_{p-1/2} + f-_{p+3/2} (two-midpoint schemes), plus the node terms
+// n_k (f+_{p+k} + f-_{p+1-k}) from the staged node fluxes.
+template <int S, typename Real, typename Acc, typename At>
+__device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At& at, const Acc mid0[4],
+                                          const Acc mid1[4], Acc h[4]) {
+  using Sc = Scheme<S>;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    if constexpr (Sc::nmp == 1) h[v] = Acc(Sc::m0) * mid0[v];
+    else h[v] = Acc(Sc::m0) * mid0[v] + Acc(Sc::m1) * mid1[v];
+  }
+#pragma unroll
+  for (int kk = -2; kk <= 2; ++kk) {
+    if (Sc::n(kk + 2) == 0.0) continue;
+    Acc a[4], b[4];
+    ld4(st.fp, st.n, at(kk), a);
+    ld4(st.fm, st.n, at(1 - kk), b);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) h[v] += Acc(Sc::n(kk + 2)) * (a[v] + b[v]);
+  }
+}
 
 // One tile (bx along the lines, by across them) of one block.  qtab: every block's state
 // for linked faces (null for a lone block).
@@ -86,15 +340,11 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
   constexpr int NL = Sh::NL, W = Sh::W, T = Sh::T, NP = Sh::NP, PLO = Sh::PLO;
   constexpr int NN = Sh::NN, NW = Sh::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Acc* sFp = reinterpret_cast<Acc*>(smem_raw);           // [4][NN] node f+ = (E^ + A^ Q)/2
-  Acc* sFm = sFp + 4 * NN;                               // [4][NN] node f- = (E^ - A^ Q)/2
-  Acc* sMa = sFm + 4 * NN;                               // [2][NN] metrics (flux arithmetic)
-  Acc* sH = sMa + 2 * NN;                                // [4][NW] h at interfaces
-  Acc* sF = sH + 4 * NW;                                 // [8][NW] f+-_mid (two midpoints)
-  Real* sQ = reinterpret_cast<Real*>(sF + (Sh::NMP == 2 ? 8 * NW : 0) + NL);  // [4][NN] (after A^)
-  Real* sP = sQ + 4 * NN;                                // [7][NN] primitives
-  Real* sMr = Sh::SPLIT_MET ? sP + 7 * NN : nullptr;     // [2][NN] metrics in Real
-  Acc* sA = reinterpret_cast<Acc*>(smem_raw) + 10 * NN + 4 * NW + (Sh::NMP == 2 ? 8 * NW : 0);  // [NL] A^
+  Staged<Real, Acc> st;
+  st.carve(smem_raw, NN);
+  Acc* sH = reinterpret_cast<Acc*>(smem_raw + Sh::o_h());   // h at interfaces (4 values)
+  Acc* sF = reinterpret_cast<Acc*>(smem_raw + Sh::o_f());   // f+ and f- at midpoints (two-midpoint)
+  Acc* sA = reinterpret_cast<Acc*>(smem_raw + Sh::o_a());   // A^ per line
 
   const int n = DIR == 0 ? P.ni : P.nj;
   const int nlines = DIR == 0 ? P.nj : P.ni;
@@ -106,17 +356,12 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
 
   auto SI = [](int l, int s) { return DIR == 0 ? l * NP + s : s * NL + l; };
   auto WI = [](int l, int p) { return DIR == 0 ? l * W + p : p * NL + l; };
-  auto metR = [&](int c, int o) -> Real {
-    if constexpr (Sh::SPLIT_MET) return sMr[c * NN + o];
-    else return sMa[c * NN + o];
-  };
 
   // A^ = alpha x line maximum, once per line (Section 2.3)
   if (threadIdx.x < NL) {
     const int line = line0 + threadIdx.x;
     sA[threadIdx.x] = line < nlines ? Acc(P.alpha * lam[line]) : Acc(0);
   }
-  __syncthreads();
   // prefetch of the epilogue's global operands, issued now and consumed in the last phase
   // by the same thread (the node mapping of that phase)
   double* sJ = reinterpret_cast<double*>(smem_raw + Sh::ep_off());
@@ -141,40 +386,35 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     }
     cp_async_commit();
   }
-  // ---- phase 1: nodes ----
-  for (int k = threadIdx.x; k < NN; k += Sh::THREADS) {
+  // ---- phase 1: nodes.  The global loads of both rounds are issued before any arithmetic,
+  // so the second (partial) round does not wait for a second memory latency.
+  constexpr int NR = (NN + Sh::THREADS - 1) / Sh::THREADS;
+  Real qv[NR][4];
+  double mxv[NR], myv[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int k = threadIdx.x + r * Sh::THREADS;
     const int l = DIR == 0 ? k / NP : k % NL;
     const int s = DIR == 0 ? k % NP : k / NL;
     const int line = line0 + l;
-    if (line >= nlines) continue;
+    if (k >= NN || line >= nlines) continue;
     const int g = min(base + s - 4, n + 3);  // positions past n+3 are never used
-    Real q[4];
-    load_state(P, Q, DIR, line, g, q, qtab);
-    double mx, my;
-    if (DIR == 0) { mx = met_at(P, 0, g, line); my = met_at(P, 1, g, line); }
-    else          { mx = met_at(P, 2, line, g); my = met_at(P, 3, line, g); }
-    const Prim<Real> w = prim_of(q, gamma);
-    // E^ = mx E + my F with the metric products in Acc
-    const Real p = (gamma - Real(1)) * (q[3] - q[0] * w.h2);
-    const Acc amx = from_f64<Acc>(mx), amy = from_f64<Acc>(my);
-    const Acc U = amx * Acc(w.u) + amy * Acc(w.v);
-    const int o = SI(l, s);
-    // f+- = (E^ +- A^ Q)/2, the node terms of the split
-    const Acc hA = Acc(0.5) * sA[l];
-    const Acc E[4] = {Acc(q[0]) * U, Acc(q[1]) * U + amx * Acc(p), Acc(q[2]) * U + amy * Acc(p), Acc(q[3] + p) * U};
+    load_state(P, Q, DIR, line, g, qv[r], qtab);
+    if (DIR == 0) { mxv[r] = met_at(P, 0, g, line); myv[r] = met_at(P, 1, g, line); }
+    else          { mxv[r] = met_at(P, 2, line, g); myv[r] = met_at(P, 3, line, g); }
+  }
+  __syncthreads();  // A^ in shared memory
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const Acc e = Acc(0.5) * E[v], aq = hA * Acc(q[v]);
-      sFp[v * NN + o] = e + aq;
-      sFm[v * NN + o] = e - aq;
-    }
-    sMa[o] = amx;
-    sMa[NN + o] = amy;
-    if constexpr (Sh::SPLIT_MET) { sMr[o] = from_f64<Real>(mx); sMr[NN + o] = from_f64<Real>(my); }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) sQ[v * NN + o] = q[v];
-    sP[0 * NN + o] = w.u; sP[1 * NN + o] = w.v; sP[2 * NN + o] = w.c; sP[3 * NN + o] = w.cinv;
-    sP[4 * NN + o] = w.H; sP[5 * NN + o] = w.b1; sP[6 * NN + o] = w.h2;
+  for (int r = 0; r < NR; ++r) {
+    const int k = threadIdx.x + r * Sh::THREADS;
+    const int l = DIR == 0 ? k / NP : k % NL;
+    const int s = DIR == 0 ? k % NP : k / NL;
+    const int line = line0 + l;
+    if (k >= NN || line >= nlines) continue;
+    Prim<Real> w;
+    Acc amx, amy, fp[4], fm[4];
+    node_split<Real, Acc>(qv[r], mxv[r], myv[r], gamma, Acc(0.5) * sA[l], w, amx, amy, fp, fm);
+    st.store(SI(l, s), qv[r], w, amx, amy, fp, fm, mxv[r], myv[r]);
   }
   __syncthreads();
 
@@ -185,121 +425,19 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const int line = line0 + l;
     const int p = PLO + pi;
     if (line >= nlines || base + p > n) continue;
-    const Acc A = sA[l];
     const int c0 = p + 4;  // staged position of node p
-    const int o0 = SI(l, c0), o1 = SI(l, c0 + 1);
-
-    // characteristic direction: unit vector of the averaged metrics (Section 3.4)
-    const Real mbx = Real(0.5) * (metR(0, o0) + metR(0, o1));
-    const Real mby = Real(0.5) * (metR(1, o0) + metR(1, o1));
-    const Real rn = rsq(mbx * mbx + mby * mby);
-    const Real nx = mbx * rn, ny = mby * rn;
-
-    Real Qs[2][4];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      // "+" side: eigenvectors at Q_p, stencil p-2..p+2; "-" side: at Q_{p+1}, mirrored
-      const int oc = side == 0 ? o0 : o1;
-      Prim<Real> w;
-      w.u = sP[0 * NN + oc]; w.v = sP[1 * NN + oc]; w.c = sP[2 * NN + oc]; w.cinv = sP[3 * NN + oc];
-      w.H = sP[4 * NN + oc]; w.b1 = sP[5 * NN + oc]; w.h2 = sP[6 * NN + oc];
-      Eig<Real> E;
-      E.build(w, nx, ny);
-      const Real qc0 = sQ[oc], qc1 = sQ[NN + oc], qc2 = sQ[2 * NN + oc], qc3 = sQ[3 * NN + oc];
-      // state differences to the centre at the stencil offsets -2, -1, +1, +2
-      Real dq[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int m = a < 2 ? a - 2 : a - 1;
-        if (Sc::r == 2 && m == 2) { dq[a][0] = dq[a][1] = dq[a][2] = dq[a][3] = Real(0); continue; }
-        const int o = SI(l, side == 0 ? c0 + m : c0 + 1 - m);
-        dq[a][0] = sQ[o] - qc0;
-        dq[a][1] = sQ[NN + o] - qc1;
-        dq[a][2] = sQ[2 * NN + o] - qc2;
-        dq[a][3] = sQ[3 * NN + o] - qc3;
-      }
-      Real Wm[4];
-      if constexpr (std::is_same<Real, float>::value) {
-        // components (0, 1) and (2, 3) in the two lanes of packed float arithmetic
-#pragma unroll
-        for (int kp = 0; kp < 2; ++kp) {
-          float2 u[5];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            if (Sc::r == 2 && a == 3) { u[4] = make_float2(0.f, 0.f); continue; }
-            u[a < 2 ? a : a + 1] = make_float2(E.project(2 * kp, dq[a][0], dq[a][1], dq[a][2], dq[a][3]),
-                                               E.project(2 * kp + 1, dq[a][0], dq[a][1], dq[a][2], dq[a][3]));
-          }
-          u[2] = make_float2(0.f, 0.f);
-          const float2 W2 = weno_delta_x2<Sc::r>(u, eps, P.ppm, P.linw);
-          Wm[2 * kp] = W2.x;
-          Wm[2 * kp + 1] = W2.y;
-        }
-      } else {
-#pragma unroll
-        for (int kc = 0; kc < 4; ++kc) {
-          Real u[5];
-          u[0] = E.project(kc, dq[0][0], dq[0][1], dq[0][2], dq[0][3]);
-          u[1] = E.project(kc, dq[1][0], dq[1][1], dq[1][2], dq[1][3]);
-          u[2] = Real(0);
-          u[3] = E.project(kc, dq[2][0], dq[2][1], dq[2][2], dq[2][3]);
-          u[4] = Sc::r == 3 ? E.project(kc, dq[3][0], dq[3][1], dq[3][2], dq[3][3]) : Real(0);
-          Wm[kc] = weno_delta<Sc::r, Real>(u, eps, P.ppm, P.linw);
-        }
-      }
-      Real dQm[4];
-      E.recon(Wm, dQm);
-      Qs[side][0] = qc0 + dQm[0];
-      Qs[side][1] = qc1 + dQm[1];
-      Qs[side][2] = qc2 + dQm[2];
-      Qs[side][3] = qc3 + dQm[3];
-    }
-
-    // midpoint metrics by the same interpolation as the metric evaluation (Section 2.4)
-    Acc vx[6], vy[6];
-#pragma unroll
-    for (int kk = 0; kk < 6; ++kk) {
-      const int o = SI(l, c0 - 2 + kk);
-      vx[kk] = sMa[o];
-      vy[kk] = sMa[NN + o];
-    }
-    const Acc mmx = mid_interp(P.interp, Sc::r == 3, vx);
-    const Acc mmy = mid_interp(P.interp, Sc::r == 3, vy);
-    // split midpoint fluxes f+ = (E^(Q+) + A^ Q+)/2, f- = (E^(Q-) - A^ Q-)/2
+    auto at = [&](int m) { return SI(l, c0 + m); };
     Acc fs[2][4];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const Real* q = Qs[side];
-      const Real rinv = recip(q[0]);
-      const Real u = q[1] * rinv, v = q[2] * rinv;
-      const Real pr = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
-      const Acc U = mmx * Acc(u) + mmy * Acc(v);
-      const Acc sg = side == 0 ? A : -A;
-      fs[side][0] = Acc(0.5) * (Acc(q[0]) * U + sg * Acc(q[0]));
-      fs[side][1] = Acc(0.5) * (Acc(q[1]) * U + mmx * Acc(pr) + sg * Acc(q[1]));
-      fs[side][2] = Acc(0.5) * (Acc(q[2]) * U + mmy * Acc(pr) + sg * Acc(q[2]));
-      fs[side][3] = Acc(0.5) * (Acc(q[3] + pr) * U + sg * Acc(q[3]));
-    }
+    interface_fluxes<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, sA[l], fs);
     if constexpr (Sc::nmp == 1) {
-      // h = h+ + h-: the midpoint terms plus the node terms n_k (f+_{p+k} + f-_{p+1-k}),
-      // h- the mirror of h+ about p + 1/2
+      Acc mid0[4], h[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        Acc h = Acc(Sc::m0) * (fs[0][v] + fs[1][v]);
-#pragma unroll
-        for (int kk = -2; kk <= 2; ++kk) {
-          if (Sc::n(kk + 2) == 0.0) continue;
-          const int a = SI(l, c0 + kk), b = SI(l, c0 + 1 - kk);
-          h += Acc(Sc::n(kk + 2)) * (sFp[v * NN + a] + sFm[v * NN + b]);
-        }
-        sH[v * NW + WI(l, pi)] = h;
-      }
+      for (int v = 0; v < 4; ++v) mid0[v] = fs[0][v] + fs[1][v];
+      h_combine<S, Real, Acc>(st, at, mid0, mid0, h);
+      st4(sH, NW, WI(l, pi), h[0], h[1], h[2], h[3]);
     } else {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        sF[v * NW + WI(l, pi)] = fs[0][v];
-        sF[(4 + v) * NW + WI(l, pi)] = fs[1][v];
-      }
+      st4(sF, NW, WI(l, pi), fs[0][0], fs[0][1], fs[0][2], fs[0][3]);
+      st4(sF + 4 * NW, NW, WI(l, pi), fs[1][0], fs[1][1], fs[1][2], fs[1][3]);
     }
   }
 
@@ -313,18 +451,16 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
       const int p = PLO + pi;
       if (line >= nlines || p < -1 || p > T - 1 || base + p > n - 1) continue;
       const int c0 = p + 4;
+      auto at = [&](int m) { return SI(l, c0 + m); };
+      Acc a[4], b[4], c[4], d[4], mid0[4], mid1[4], h[4];
+      ld4(sF, NW, WI(l, pi), a);
+      ld4(sF + 4 * NW, NW, WI(l, pi), b);
+      ld4(sF, NW, WI(l, pi - 1), c);
+      ld4(sF + 4 * NW, NW, WI(l, pi + 1), d);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        Acc h = Acc(Sc::m0) * (sF[v * NW + WI(l, pi)] + sF[(4 + v) * NW + WI(l, pi)]) +
-                Acc(Sc::m1) * (sF[v * NW + WI(l, pi - 1)] + sF[(4 + v) * NW + WI(l, pi + 1)]);
-#pragma unroll
-        for (int kk = -2; kk <= 2; ++kk) {
-          if (Sc::n(kk + 2) == 0.0) continue;
-          const int a = SI(l, c0 + kk), b = SI(l, c0 + 1 - kk);
-          h += Acc(Sc::n(kk + 2)) * (sFp[v * NN + a] + sFm[v * NN + b]);
-        }
-        sH[v * NW + WI(l, pi)] = h;
-      }
+      for (int v = 0; v < 4; ++v) { mid0[v] = a[v] + b[v]; mid1[v] = c[v] + d[v]; }
+      h_combine<S, Real, Acc>(st, at, mid0, mid1, h);
+      st4(sH, NW, WI(l, pi), h[0], h[1], h[2], h[3]);
     }
   }
   __syncthreads();
@@ -339,14 +475,18 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const int pi = s - PLO;  // interface s + 1/2
     const int i = DIR == 0 ? g : line, j = DIR == 0 ? line : g;
     const long long o = (long long)j * P.ld + i;
-    Acc R[4];
+    Acc hp[4], hm[4], R[4];
+    ld4(sH, NW, WI(l, pi), hp);
+    ld4(sH, NW, WI(l, pi - 1), hm);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) R[v] = sH[v * NW + WI(l, pi)] - sH[v * NW + WI(l, pi - 1)];
+    for (int v = 0; v < 4; ++v) R[v] = hp[v] - hm[v];
     if constexpr (MODE == MODE_ACC) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) Dout[v * plane + o] = R[v];
     } else {
       cp_async_wait_all();
+      Real qs[4];
+      if constexpr (MODE == MODE_STAGE) ld4(st.q, st.n, SI(l, s + 4), qs);
       const Acc mJ = -recip(from_f64<Acc>(sJ[k]));
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -354,12 +494,159 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
         if constexpr (MODE == MODE_RHS) {
           qout[v * plane + o] = Real(d);
         } else {
-          const Acc qs = Acc(sQ[v * NN + SI(l, s + 4)]);
-          qout[v * plane + o] = Real(Acc(ca) * Acc(sQn[v * Sh::NO + k]) + Acc(cb) * (qs + Acc(dt) * d));
+          qout[v * plane + o] = Real(Acc(ca) * Acc(sQn[v * Sh::NO + k]) + Acc(cb) * (Acc(qs[v]) + Acc(dt) * d));
         }
       }
     }
   }
+}
+
+// --------------------------------------------------------------------------------------
+// Marching xi pass.  A warp walks one row segment [s0, s1) of a block 32 nodes at a time.
+// Every step t (lane L):
+//   nodes       m = s0 + K + 32 t + L  into ring slot m mod 64 (state and metrics staged by
+//               cp.async during the previous step when the node is interior)
+//   interfaces  q = s0 - NMP + 32 t + L: midpoint fluxes (and for one-midpoint schemes h)
+//   h           (two-midpoint schemes) at q - 1, from the midpoint ring
+//   outputs     node s = the interface just completed, H_s - H_{s-1} from the h ring
+// with K = 3 (one midpoint) or 2 (two midpoints), so that every stencil node of a step's
+// interfaces is in the ring; a start-up pass stages the six nodes before s0 + K.  The ring
+// holds the 38 nodes a step reads; the warp synchronises between the phases only.
+// --------------------------------------------------------------------------------------
+template <int S, int MODE, typename Real, typename Acc>
+__device__ __forceinline__ void march_row(const Params& P, const Real* __restrict__ Q, const Real* const* qtab,
+                                          double lamv, const Acc* __restrict__ Dacc, Acc* __restrict__ Dout,
+                                          Real* qout, const Real* Qn, double ca, double cb, double dt, int row,
+                                          int s0, int s1, unsigned char* wsm) {
+  using Ms = MarchShape<S, Real, Acc>;
+  constexpr int NMP = Scheme<S>::nmp;
+  constexpr int K = NMP == 1 ? 3 : 2;
+  const int L = threadIdx.x & 31;
+  Staged<Real, Acc> st;
+  st.carve(wsm, RING);
+  Acc* rH = reinterpret_cast<Acc*>(wsm + Ms::o_h());
+  Acc* rF = reinterpret_cast<Acc*>(wsm + Ms::o_f());
+  Real* rawq = reinterpret_cast<Real*>(wsm + Ms::o_raw());           // [4][32]
+  double* rawm = reinterpret_cast<double*>(rawq + 4 * 32);           // [2][32]
+  const int n = P.ni;
+  const Real gamma = Real(P.gamma);
+  const Real eps = sizeof(Real) == 8 ? from_f64<Real>(P.eps) : from_f64<Real>(P.eps < 1e-30 ? 1e-30 : P.eps);
+  const long long plane = (long long)P.nj * P.ld;
+  const Acc A = Acc(P.alpha * lamv);
+  const Acc hA = Acc(0.5) * A;
+  const Real* Qrow = Q + (long long)row * P.ld;
+  const double* M0 = P.met + (long long)(row + G) * P.mld + G;   // xi_x^ of node (i, row) at M0[i]
+  const double* M1 = M0 + P.mplane;                                // xi_y^
+
+  // the node stage of one position: interior nodes from the cp.async staging (if staged),
+  // else through the boundary rule; positions past n + 3 are never read
+  auto stage_node = [&](int m, bool staged) {
+    if (m > s1 + 3 || m > n + 3) return;
+    Real q[4];
+    double mx, my;
+    if (staged) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) q[v] = rawq[v * 32 + L];
+      mx = rawm[L];
+      my = rawm[32 + L];
+    } else {
+      load_state(P, Q, 0, row, m, q, qtab);
+      mx = met_at(P, 0, m, row);
+      my = met_at(P, 1, m, row);
+    }
+    Prim<Real> w;
+    Acc amx, amy, fp[4], fm[4];
+    node_split<Real, Acc>(q, mx, my, gamma, hA, w, amx, amy, fp, fm);
+    st.store(m & (RING - 1), q, w, amx, amy, fp, fm, mx, my);
+  };
+  // cp.async of node m's state and metrics into this lane's staging slot (interior only)
+  auto prefetch = [&](int m) -> bool {
+    if (m < 0 || m >= n || m > s1 + 3) return false;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) cp_async<sizeof(Real)>(rawq + v * 32 + L, Qrow + v * plane + m);
+    cp_async<8>(rawm + L, M0 + m);
+    cp_async<8>(rawm + 32 + L, M1 + m);
+    return true;
+  };
+
+  // start-up: the six nodes s0 + K - 6 .. s0 + K - 1, and the first step's nodes in flight
+  if (L < 6) stage_node(s0 + K - 6 + L, false);
+  bool staged = prefetch(s0 + K + L);
+  cp_async_commit();
+  const int steps = (s1 - s0 + 2 * NMP - 1 + 31) / 32;   // until the output s1 - 1
+  for (int t = 0; t < steps; ++t) {
+    const int m = s0 + K + 32 * t + L;
+    cp_async_wait_all();
+    stage_node(m, staged);
+    __syncwarp();
+    staged = prefetch(m + 32);       // the next step's node, in flight during this step
+    cp_async_commit();
+    // interfaces
+    const int q = s0 - NMP + 32 * t + L;
+    if (q <= s1 + NMP - 2) {   // interfaces s0 - NMP .. s1 + NMP - 2
+      auto at = [&](int mm) { return (q + mm) & (RING - 1); };
+      Acc fs[2][4];
+      interface_fluxes<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, fs);
+      if constexpr (NMP == 1) {
+        Acc mid0[4], h[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) mid0[v] = fs[0][v] + fs[1][v];
+        h_combine<S, Real, Acc>(st, at, mid0, mid0, h);
+        st4(rH, RING, q & (RING - 1), h[0], h[1], h[2], h[3]);
+      } else {
+        st4(rF, RING, q & (RING - 1), fs[0][0], fs[0][1], fs[0][2], fs[0][3]);
+        st4(rF + 4 * RING, RING, q & (RING - 1), fs[1][0], fs[1][1], fs[1][2], fs[1][3]);
+      }
+    }
+    __syncwarp();
+    int s = q;
+    if constexpr (NMP == 2) {
+      // h at p = q - 1 from the midpoint fluxes at p - 1/2, p + 1/2, p + 3/2
+      const int p = q - 1;
+      if (p >= s0 - 1 && p <= s1 - 1) {
+        auto at = [&](int mm) { return (p + mm) & (RING - 1); };
+        Acc a[4], b[4], c[4], d[4], mid0[4], mid1[4], h[4];
+        ld4(rF, RING, p & (RING - 1), a);
+        ld4(rF + 4 * RING, RING, p & (RING - 1), b);
+        ld4(rF, RING, (p - 1) & (RING - 1), c);
+        ld4(rF + 4 * RING, RING, (p + 1) & (RING - 1), d);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { mid0[v] = a[v] + b[v]; mid1[v] = c[v] + d[v]; }
+        h_combine<S, Real, Acc>(st, at, mid0, mid1, h);
+        st4(rH, RING, p & (RING - 1), h[0], h[1], h[2], h[3]);
+      }
+      __syncwarp();
+      s = p;
+    }
+    // outputs: node s, H_{s+1/2} - H_{s-1/2}
+    if (s >= s0 && s < s1) {
+      Acc hp[4], hm[4], R[4];
+      ld4(rH, RING, s & (RING - 1), hp);
+      ld4(rH, RING, (s - 1) & (RING - 1), hm);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) R[v] = hp[v] - hm[v];
+      const long long o = (long long)row * P.ld + s;
+      if constexpr (MODE == MODE_ACC) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Dout[v * plane + o] = R[v];
+      } else {
+        const Acc mJ = -recip(from_f64<Acc>(__ldg(P.met + 4 * P.mplane + (long long)(row + G) * P.mld + s + G)));
+        Real qs[4];
+        if constexpr (MODE == MODE_STAGE) ld4(st.q, st.n, s & (RING - 1), qs);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const Acc d = (Dacc[v * plane + o] + R[v]) * mJ;
+          if constexpr (MODE == MODE_RHS) {
+            qout[v * plane + o] = Real(d);
+          } else {
+            qout[v * plane + o] = Real(Acc(ca) * Acc(Qn[v * plane + o]) + Acc(cb) * (Acc(qs[v]) + Acc(dt) * d));
+          }
+        }
+      }
+    }
+    __syncwarp();   // the next step overwrites ring slots read above
+  }
+  cp_async_wait_all();
 }
 
 template <int S, int DIR, int MODE, typename Real, typename Acc>
@@ -398,6 +685,30 @@ sweep_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
                                       MODE == MODE_ACC ? B.dout[b] : nullptr,
                                       MODE == MODE_ACC ? nullptr : B.qout[b],
                                       MODE == MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, t.bx, t.by);
+}
+
+// Marching xi pass of many blocks: CTA b takes rows 4 by .. 4 by + 3 (one per warp) of
+// block tiles[b].block, segment tiles[b].bx of each row.
+template <int S, int MODE, typename Real, typename Acc>
+__global__ void __launch_bounds__(32 * MARCH_WARPS, sizeof(Real) == 8 ? 3 : 7)
+march_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
+  using Ms = MarchShape<S, Real, Acc>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Params sp;
+  const TileRef t = B.tiles[blockIdx.x];
+  if (threadIdx.x == 0) sp = B.params[t.block];
+  __syncthreads();
+  const int b = t.block;
+  const int warp = threadIdx.x >> 5;
+  const int row = t.by * MARCH_WARPS + warp;
+  if (row >= sp.nj) return;   // whole warps only; no block-wide barrier follows
+  const int seg = march_seg_len(sp.ni);
+  const int s0 = t.bx * seg, s1 = min(sp.ni, s0 + seg);
+  if (s0 >= s1) return;
+  march_row<S, MODE, Real, Acc>(sp, B.q[b], B.q, B.lam[b][row], MODE == MODE_ACC ? nullptr : B.dacc[b],
+                                MODE == MODE_ACC ? B.dout[b] : nullptr, MODE == MODE_ACC ? nullptr : B.qout[b],
+                                MODE == MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, row, s0, s1,
+                                smem_raw + warp * Ms::warp_bytes());
 }
 
 // Untyped pass tables (device arrays of per-block pointers) and their typed view.
@@ -440,9 +751,25 @@ cudaError_t launch_sweep_batch_v(const BatchPass<Real, Acc>& B, int ntiles, doub
   return cudaGetLastError();
 }
 
+template <int S, int MODE, typename Real, typename Acc>
+cudaError_t launch_march_batch(const BatchPass<Real, Acc>& B, int ntiles, double ca, double cb, double dt,
+                               cudaStream_t st) {
+  auto kern = march_batch_kernel<S, MODE, Real, Acc>;
+  const size_t smem = MarchShape<S, Real, Acc>::smem_bytes();
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (ntiles > 0) kern<<<ntiles, 32 * MARCH_WARPS, smem, st>>>(B, ca, cb, dt);
+  return cudaGetLastError();
+}
+
 template <int S, int DIR, int MODE, typename Real, typename Acc>
 cudaError_t launch_sweep_batch(const BatchPass<Real, Acc>& B, int ntiles, int v, double ca, double cb, double dt,
                                cudaStream_t st) {
+  if constexpr (DIR == 0) {
+    if (v == MARCH) return launch_march_batch<S, MODE, Real, Acc>(B, ntiles, ca, cb, dt, st);
+  }
   switch (v) {
     case 1: return launch_sweep_batch_v<S, DIR, MODE, Real, Acc, 1>(B, ntiles, ca, cb, dt, st);
     case 2: return launch_sweep_batch_v<S, DIR, MODE, Real, Acc, 2>(B, ntiles, ca, cb, dt, st);

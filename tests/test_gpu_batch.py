@@ -146,14 +146,19 @@ def test_batch_full_size_cylinder(F):
     Ro = O.mb_rhs(cfgd, blocks, Ms, qs)
     for k in range(len(blocks)):              # identical metrics isolate the right-hand side
         bt.M[k].copy_(torch.as_tensor(Ms[k]))
+    ref = [r.cpu().numpy() for r in bt.rhs()]
+    assert _maxrel(ref, Ro) < TOL
+    bt.set_tile_shape(0, 3)                   # marching xi pass
     assert _maxrel([r.cpu().numpy() for r in bt.rhs()], Ro) < TOL
     bt.close()
 
 
 @pytest.mark.parametrize("scheme,prec", [(2, 0), (3, 0), (0, 1), (3, 2)])
 def test_batch_tile_shapes_agree(F, scheme, prec):
-    # every tile shape computes each interface the same way: identical FP64 right-hand sides;
-    # in float the instantiations may contract products into FMAs differently (last bits)
+    # every tile shape computes each interface the same way: identical FP64 right-hand sides
+    # among the tile variants; the marching kernel (xi variant 3) inlines the same arithmetic
+    # into another kernel, whose products the compiler may contract into FMAs differently
+    # (last bits), as may the float instantiations
     blocks, states, free = _small_cylinder()
     cfgd = _cfgd(free, scheme, prec)
     qs = _perturbed(states, 3, 0.05)
@@ -162,14 +167,37 @@ def test_batch_tile_shapes_agree(F, scheme, prec):
     ref = [r.double().cpu().numpy() for r in bt.rhs()]
     bound = 0.0 if prec == 0 else 1e-5 * max(np.abs(r).max() for r in ref)
     shapes = set()
-    for vx in range(3):
+    for vx in range(4):          # xi variant 3: marching warps
         for ve in range(3):
             bt.set_tile_shape(0, vx)
             bt.set_tile_shape(1, ve)
             shapes.add((bt.tile_shape(0), bt.tile_shape(1)))
             got = [r.double().cpu().numpy() for r in bt.rhs()]
-            assert max(np.abs(a - b).max() for a, b in zip(got, ref)) <= bound, (vx, ve)
-    assert len(shapes) == 9
+            b = bound if vx < 3 or prec != 0 else 1e-13 * max(np.abs(r).max() for r in ref)
+            assert max(np.abs(a - b_).max() for a, b_ in zip(got, ref)) <= b, (vx, ve)
+    assert len(shapes) == 12
+    with pytest.raises(F.FspError):
+        bt.set_tile_shape(1, 3)  # the eta pass has no marching variant
+    bt.close()
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+def test_batch_marching_segments(F, scheme):
+    # rows longer than one marching segment (1100 nodes: three segments of 384, 384, 332),
+    # periodic in both directions, against the oracle and against the tile variant
+    x, y, per = I.periodic_square(1100, 10.0, 0.2, seed=5, nj=6)
+    q = I.random_state(x.shape, seed=9)
+    cfgd = dict(scheme=scheme, period=per)
+    M = O.metrics(cfgd, x, y)
+    Ro = O.rhs(cfgd, M, q)
+    bt = F.Batch(F.Config.from_dict(cfgd), [dict(x=x, y=y, bc=(0, 0, 0, 0), period=per)], [q])
+    bt.M[0].copy_(torch.as_tensor(M))
+    bt.set_tile_shape(0, 3)
+    got = bt.rhs()[0].cpu().numpy()
+    assert np.abs(got - Ro).max() / np.abs(Ro).max() < TOL
+    bt.set_tile_shape(0, 0)
+    ref = bt.rhs()[0].cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
     bt.close()
 
 
