@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--profile-tiles", default="2,1",
                     help="profiling run: tile shape variants 'vx,ve' of the xi and eta passes (the tuner's "
                          "choice on this workload), set without timing")
+    ap.add_argument("--profile-dir", type=int, default=0, choices=[0, 1],
+                    help="profiling run: the direction whose batched sweep is launched three times")
     ap.add_argument("--profile", choices=list(PRECISIONS) + ["adjoint"], default=None,
                     help="profiling run for ncu: build the cylinder batch in this precision, evaluate one "
                          "right-hand side, then launch the batched xi sweep three times; 'adjoint': three "
@@ -343,17 +345,22 @@ def measure_cylinder(args, prec, C, per_block=False):
     fl = algorithmic_flops(args)
     achieved = fl["sweep_xi_per_node"] * nodes / t_k / 1e12
     rhs_total = nodes * 3 * args.steps * C.world
+    kname = ("march_batch_kernel xi (marching warps)" if tiles["xi"]["variant"] == 3 else "sweep_batch_kernel xi") \
+        + ", all 64 blocks (fsp_batch_flux_difference dir 0)"
+    roof = {"bound": "alu", "kernel": kname,
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic_of(args, prec),
+            "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
+            "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
+            "kernel_ms": 1e3 * t_k}
+    if prec == "mixed":
+        roof = mixed_roofline(args, C, roof, fl["sweep_xi_per_node"], nodes, t_k)
     out = {
         "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps, "nodes": nodes,
         "nblocks": len(blocks),
         "e2e": {"value": rhs_total / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},
-        "roofline": {"bound": "alu", "kernel": "sweep_batch_kernel xi, all 64 blocks (fsp_batch_flux_difference dir 0)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic_of(args, prec),
-                     "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
-                     "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
-                     "kernel_ms": 1e3 * t_k},
+        "roofline": roof,
         "clocks": clk,
         "tiles": tiles,
     }
@@ -375,6 +382,37 @@ def measure_cylinder(args, prec, C, per_block=False):
                                  "ms_per_step": 1e3 * t_loop / reps,
                                  "how": "64 fsp_rk3_step calls per step, one block each, eager launches"}
     bt.close()
+    return out
+
+
+# FP64 operations per node of one direction in the mixed path (FP32 state, projection, WENO,
+# Cartesian fluxes and dissipative part; double metric products, central combination and
+# difference), counted from its formulas with a fused multiply-add as two: node products
+# mx E + my F (4 x 3), midpoint metric interpolation (2 x 9 six-point, 2 x 5 four-point),
+# midpoint products (one mean flux, 4 x 3; two-midpoint schemes both sides, 4 x 6), central
+# combination of node pairs and midpoint terms, double + float parts and the difference (4 + 4).
+MIXED_FP64_FLOPS = {0: 70, 1: 86, 2: 90, 3: 106}
+
+
+def mixed_roofline(args, C, roof, flops_node, nodes, t_k):
+    """Roofline of the mixed path: t_roof = max(FP32 flops / FP32 peak, FP64 flops / FP64
+    peak); the FP64 part bounds it.  The FP32 part is the rest of the algorithmic count."""
+    f64 = MIXED_FP64_FLOPS[args.scheme]
+    f32 = flops_node - f64
+    p64, _ = C.peak("fp64")
+    p32 = roof["peak"]
+    t32, t64 = f32 * nodes / (p32 * 1e12), f64 * nodes / (p64 * 1e12)
+    part32 = {"flops_per_node": f32, "achieved": f32 * nodes / t_k / 1e12, "peak": p32,
+              "frac": f32 * nodes / t_k / 1e12 / p32}
+    part64 = {"flops_per_node": f64, "achieved": f64 * nodes / t_k / 1e12, "peak": p64,
+              "frac": f64 * nodes / t_k / 1e12 / p64}
+    head, other = (part64, part32) if t64 >= t32 else (part32, part64)
+    out = dict(roof)
+    out.update({"bound": "alu", "achieved": head["achieved"], "peak": head["peak"], "frac": head["frac"],
+                "flops_per_node": head["flops_per_node"],
+                "part": "FP64 part" if head is part64 else "FP32 part",
+                "peak_source": ("FP64" if head is part64 else "FP32") + " FMA probe (fsp_fma_peak) in this run",
+                "other_part": other, "t_roof_ms": 1e3 * max(t32, t64)})
     return out
 
 
@@ -577,7 +615,7 @@ def measure_accuracy(args, C, full=False):
 
 def profile_run(args, prec):
     """Minimal launch sequence for a profiler: metrics, one right-hand side (line maxima,
-    xi sweep, eta sweep), then three launches of the batched xi sweep alone."""
+    xi sweep, eta sweep), then three launches of one direction's batched sweep alone."""
     import numpy as np
     import torch
     from paper_1810_11103_gb300 import build as B
@@ -592,7 +630,7 @@ def profile_run(args, prec):
     bt.rhs()
     D = [torch.empty(q.shape, dtype=torch.float32 if prec == "fp32" else torch.float64, device="cuda") for q in bt.Q]
     for _ in range(3):
-        bt.flux_difference(0, D)
+        bt.flux_difference(args.profile_dir, D)
     torch.cuda.synchronize()
     print(f"profile run done: {prec}, {sum(b['x'].size for b in blocks)} nodes")
     bt.close()

@@ -248,6 +248,7 @@ void tiles_for(const fsp_batch* h, int dir, int v, std::vector<TileRef>& out) {
     const fsp_block& B = h->blk[b];
     const int n = dir == 0 ? B.ni : B.nj, nl = dir == 0 ? B.nj : B.ni;
     if (dir == 0 && v == MARCH) T = march_seg_len(n);   // rows split into equal segments
+    if (dir == 1 && v == MARCH) { T = march_eta_seg((h->cfg.scheme == S32 || h->cfg.scheme == S52) ? 2 : 1); NL = 32; }
     for (int by = 0; by < (nl + NL - 1) / NL; ++by)
       for (int bx = 0; bx < (n + T - 1) / T; ++bx) out.push_back({b, bx, by});
   }
@@ -331,7 +332,6 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
     std::vector<TileRef> t;
     tiles_for(h, 0, v, t);
     h->tx_cap = std::max(h->tx_cap, t.size());
-    if (v >= nvariant(1)) continue;
     tiles_for(h, 1, v, t);
     h->te_cap = std::max(h->te_cap, t.size());
   }

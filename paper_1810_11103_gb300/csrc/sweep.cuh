@@ -26,10 +26,10 @@ enum { MODE_ACC = 0, MODE_RHS = 1, MODE_STAGE = 2 };
 // Tile shapes: 256 threads, NL grid lines x W interface slots per CTA.  Variant 0 is the
 // default; fsp_batch_tune may pick another per direction for a batch.
 //   xi:  (NL, W) = (2, 128), (1, 256), (4, 64); variant 3: marching warps (below)
-//   eta: (NL, W) = (8, 32),  (4, 64),  (16, 16)
-constexpr int NVARIANT = 4;                         // variants of the xi pass
-constexpr int MARCH = 3;                            // the marching xi variant
-constexpr int nvariant(int dir) { return dir == 0 ? 4 : 3; }
+//   eta: (NL, W) = (8, 32),  (4, 64),  (16, 16); variant 3: marching CTAs (below)
+constexpr int NVARIANT = 4;                         // variants of each pass
+constexpr int MARCH = 3;                            // the marching variant (xi and eta)
+constexpr int nvariant(int) { return NVARIANT; }
 constexpr int shape_nl(int dir, int v) {
   return dir == 0 ? (v == 1 ? 1 : v == 2 ? 4 : 2) : (v == 1 ? 4 : v == 2 ? 16 : 8);
 }
@@ -68,7 +68,8 @@ __device__ __forceinline__ void ld2(const T* b, int o, T& x, T& y) {
 }
 
 // Staged node data of n nodes (tile positions or ring slots), 16-byte vectors:
-//   fp, fm  split node fluxes f+- = (E^ +- A^ Q)/2 (Acc, 4 values)
+//   fp, fm  split node fluxes f+- = (E^ +- A^ Q)/2 (Acc, 4 values); in mixed precision fp
+//           holds the metric-weighted flux E^ and there is no fm
 //   ma      direction metrics in Acc (2 values)
 //   q       state (Real, 4 values)
 //   p0, p1  primitives (u, v, c, 1/c) and (H, b1, |u|^2/2, 0) of the projection
@@ -82,14 +83,15 @@ struct Staged {
   // arrays of padded length (a multiple of 4 nodes keeps every array 16-byte aligned)
   static constexpr int padded(int nn) { return (nn + 3) / 4 * 4; }
   static constexpr size_t bytes(int nn) {
-    return sizeof(Acc) * (size_t)padded(nn) * 10 + sizeof(Real) * (size_t)padded(nn) * (12 + (SPLIT ? 2 : 0));
+    return sizeof(Acc) * (size_t)padded(nn) * (SPLIT ? 6 : 10) +
+           sizeof(Real) * (size_t)padded(nn) * (12 + (SPLIT ? 2 : 0));
   }
   __device__ __forceinline__ void carve(unsigned char* base, int nn0) {
     const int nn = padded(nn0);
     n = nn;
     fp = reinterpret_cast<Acc*>(base);
-    fm = fp + 4 * nn;
-    ma = fm + 4 * nn;
+    fm = SPLIT ? nullptr : fp + 4 * nn;
+    ma = fp + (SPLIT ? 4 : 8) * nn;
     q = reinterpret_cast<Real*>(ma + 2 * nn);
     p0 = q + 4 * nn;
     p1 = p0 + 4 * nn;
@@ -98,7 +100,7 @@ struct Staged {
   __device__ __forceinline__ void store(int o, const Real qq[4], const Prim<Real>& w, Acc amx, Acc amy,
                                         const Acc f[4], const Acc g[4], double mx, double my) const {
     st4(fp, n, o, f[0], f[1], f[2], f[3]);
-    st4(fm, n, o, g[0], g[1], g[2], g[3]);
+    if constexpr (!SPLIT) st4(fm, n, o, g[0], g[1], g[2], g[3]);
     st2(ma, o, amx, amy);
     if constexpr (SPLIT) st2(mr, o, from_f64<Real>(mx), from_f64<Real>(my));
     st4(q, n, o, qq[0], qq[1], qq[2], qq[3]);
@@ -118,6 +120,45 @@ struct Staged {
   }
 };
 
+// What the h combination needs from one interface (midpoint p + 1/2).  Same precision: f[0],
+// f[1] = the split midpoint fluxes f+, f-.  Mixed: f[s] = E^(Q_s) = mm_x E(Q_s) + mm_y F(Q_s)
+// (double products of float Cartesian fluxes) and q[s] = Q_s, s = +, -; for one-midpoint
+// schemes only their combinations are kept: f[0] = (E^(Q+) + E^(Q-))/2, q[0] = Q+ - Q-.
+template <typename Real, typename Acc>
+struct Mid {
+  Acc f[2][4];
+  Real q[2][4];
+};
+
+// Midpoint records of two-midpoint schemes in shared memory: per interface and side the 4
+// Acc values of Mid::f and, in mixed precision, the 4 Real values of Mid::q; nw interfaces.
+template <typename Real, typename Acc>
+struct MidStore {
+  Acc* f;      // [2 sides][4][nw] (16-byte vectors)
+  Real* q;     // [2 sides][4][nw] (mixed precision only)
+  int nw;
+  static constexpr size_t bytes(int nw) {
+    return (sizeof(Acc) + (Staged<Real, Acc>::SPLIT ? sizeof(Real) : 0)) * 8 * (size_t)nw;
+  }
+  __device__ __forceinline__ void carve(unsigned char* base, int n) {
+    nw = n;
+    f = reinterpret_cast<Acc*>(base);
+    q = Staged<Real, Acc>::SPLIT ? reinterpret_cast<Real*>(f + 8 * n) : nullptr;
+  }
+  __device__ __forceinline__ void put(int o, const Mid<Real, Acc>& m) const {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      st4(f + 4 * nw * s, nw, o, m.f[s][0], m.f[s][1], m.f[s][2], m.f[s][3]);
+      if constexpr (Staged<Real, Acc>::SPLIT) st4(q + 4 * nw * s, nw, o, m.q[s][0], m.q[s][1], m.q[s][2], m.q[s][3]);
+    }
+  }
+  // side s of interface o into m (the other side is left alone)
+  __device__ __forceinline__ void get(int o, int s, Mid<Real, Acc>& m) const {
+    ld4(f + 4 * nw * s, nw, o, m.f[s]);
+    if constexpr (Staged<Real, Acc>::SPLIT) ld4(q + 4 * nw * s, nw, o, m.q[s]);
+  }
+};
+
 template <int S, int DIR, typename Real, typename Acc, int V = 0>
 struct TileShape {
   static constexpr int NL = shape_nl(DIR, V);       // grid lines per CTA
@@ -133,7 +174,7 @@ struct TileShape {
   // f+- (8 Acc per interface, two-midpoint schemes), A^ per line
   static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(NN); }
   static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * (size_t)NW; }
-  static constexpr size_t o_a() { return o_f() + (NMP == 2 ? sizeof(Acc) * 8 * (size_t)NW : 0); }
+  static constexpr size_t o_a() { return o_f() + (NMP == 2 ? MidStore<Real, Acc>::bytes(NW) : 0); }
   static constexpr size_t base_bytes() { return (o_a() + sizeof(Acc) * NL + 15) / 16 * 16; }
   // epilogue operands prefetched per output node: the other direction's difference (modes
   // 1, 2), Q^n (mode 2), J^-1 (modes 1, 2); 16-byte aligned after the base regions
@@ -161,7 +202,7 @@ struct MarchShape {
   // schemes, 8 Acc per slot), and the raw node prefetch (state, two metrics) of 32 lanes
   static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(RING); }
   static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * RING; }
-  static constexpr size_t o_raw() { return o_f() + (NMP == 2 ? sizeof(Acc) * 8 * RING : 0); }
+  static constexpr size_t o_raw() { return o_f() + (NMP == 2 ? MidStore<Real, Acc>::bytes(RING) : 0); }
   static constexpr size_t warp_bytes() { return o_raw() + 32 * (4 * sizeof(Real) + 16); }
   static constexpr size_t smem_bytes() { return MARCH_WARPS * warp_bytes(); }
 };
@@ -171,6 +212,7 @@ struct MarchShape {
 inline void tile_dims(int scheme, int dir, int& T, int& NL, int variant = 0) {
   const int nmp = (scheme == S32 || scheme == S52) ? 2 : 1;
   if (dir == 0 && variant == MARCH) { NL = MARCH_WARPS; T = MARCH_SEG; return; }
+  if (dir == 1 && variant == MARCH) { NL = 32; T = 8 * 8 - (2 * nmp - 1); return; }   // EW = 8
   NL = shape_nl(dir, variant);
   T = 256 / NL - nmp - 1;
 }
@@ -188,8 +230,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Per-node and per-interface arithmetic, shared by the tile and the marching kernels (the
 // same operations in the same order, so every layout gives the same results)
 // --------------------------------------------------------------------------------------
-// A node (Section 2.3): primitives of the projection and the split fluxes
-// f+- = (E^ +- A^ Q)/2, E^ = mx E + my F with the metric products in Acc.
+// A node (Section 2.3).  Same precision throughout (Real = Acc): primitives of the projection
+// and the split fluxes f+- = (E^ +- A^ Q)/2, E^ = mx E + my F, stored in fp and fm.  Mixed
+// precision (float state, double Acc): only the metric-weighted flux E^ = mx E + my F, with the
+// Cartesian fluxes E, F in float and the two metric products in double, stored in fp; the
+// dissipative part A^ Q of the split is taken at the interfaces from the staged state.
 template <typename Real, typename Acc>
 __device__ __forceinline__ void node_split(const Real q[4], double mx, double my, Real gamma, Acc hA,
                                            Prim<Real>& w, Acc& amx, Acc& amy, Acc fp[4], Acc fm[4]) {
@@ -197,13 +242,21 @@ __device__ __forceinline__ void node_split(const Real q[4], double mx, double my
   const Real p = (gamma - Real(1)) * (q[3] - q[0] * w.h2);
   amx = from_f64<Acc>(mx);
   amy = from_f64<Acc>(my);
-  const Acc U = amx * Acc(w.u) + amy * Acc(w.v);
-  const Acc E[4] = {Acc(q[0]) * U, Acc(q[1]) * U + amx * Acc(p), Acc(q[2]) * U + amy * Acc(p), Acc(q[3] + p) * U};
+  if constexpr (Staged<Real, Acc>::SPLIT) {
+    const Real ex[4] = {q[1], q[1] * w.u + p, q[2] * w.u, (q[3] + p) * w.u};
+    const Real ey[4] = {q[2], q[1] * w.v, q[2] * w.v + p, (q[3] + p) * w.v};
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const Acc e = Acc(0.5) * E[v], aq = hA * Acc(q[v]);
-    fp[v] = e + aq;
-    fm[v] = e - aq;
+    for (int v = 0; v < 4; ++v) fp[v] = amx * Acc(ex[v]) + amy * Acc(ey[v]);
+  } else {
+    const Acc U = amx * Acc(w.u) + amy * Acc(w.v);
+    const Acc E[4] = {Acc(q[0]) * U, Acc(q[1]) * U + amx * Acc(p), Acc(q[2]) * U + amy * Acc(p),
+                      Acc(q[3] + p) * U};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const Acc e = Acc(0.5) * E[v], aq = hA * Acc(q[v]);
+      fp[v] = e + aq;
+      fm[v] = e - aq;
+    }
   }
 }
 
@@ -211,11 +264,11 @@ __device__ __forceinline__ void node_split(const Real q[4], double mx, double my
 // gives the staged index of node p + m, m = -2..3.  Characteristic direction from the
 // averaged metrics (Section 3.4), eigenvectors at Q_p ("+" side, stencil p-2..p+2) and at
 // Q_{p+1} ("-" side, the mirror), WENO interpolation of the characteristic differences, the
-// states Q+- at the midpoint, and the split midpoint fluxes fs[0] = f+, fs[1] = f- with the
-// midpoint metrics interpolated as in the metric evaluation (Section 2.4).
+// states Q+- at the midpoint, and the midpoint fluxes with the midpoint metrics interpolated
+// as in the metric evaluation (Section 2.4).
 template <int S, typename Real, typename Acc, typename At>
-__device__ __forceinline__ void interface_fluxes(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
-                                                 int ppm, int linw, int interp, Acc A, Acc fs[2][4]) {
+__device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
+                                              int ppm, int linw, int interp, Acc A, Mid<Real, Acc>& mo) {
   using Sc = Scheme<S>;
   const int o0 = at(0), o1 = at(1);
   Real m0x, m0y, m1x, m1y;
@@ -287,45 +340,120 @@ __device__ __forceinline__ void interface_fluxes(const Staged<Real, Acc>& st, co
   for (int kk = 0; kk < 6; ++kk) ld2(st.ma, at(kk - 2), vx[kk], vy[kk]);
   const Acc mmx = mid_interp(interp, Sc::r == 3, vx);
   const Acc mmy = mid_interp(interp, Sc::r == 3, vy);
-  // split midpoint fluxes f+ = (E^(Q+) + A^ Q+)/2, f- = (E^(Q-) - A^ Q-)/2
+  if constexpr (Staged<Real, Acc>::SPLIT) {
+    // Cartesian fluxes of Q+ and Q- in float
+    Real ex[2][4], ey[2][4];
 #pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const Real* q = Qs[side];
-    const Real rinv = recip(q[0]);
-    const Real u = q[1] * rinv, v = q[2] * rinv;
-    const Real pr = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
-    const Acc U = mmx * Acc(u) + mmy * Acc(v);
-    const Acc sg = side == 0 ? A : -A;
-    fs[side][0] = Acc(0.5) * (Acc(q[0]) * U + sg * Acc(q[0]));
-    fs[side][1] = Acc(0.5) * (Acc(q[1]) * U + mmx * Acc(pr) + sg * Acc(q[1]));
-    fs[side][2] = Acc(0.5) * (Acc(q[2]) * U + mmy * Acc(pr) + sg * Acc(q[2]));
-    fs[side][3] = Acc(0.5) * (Acc(q[3] + pr) * U + sg * Acc(q[3]));
+    for (int side = 0; side < 2; ++side) {
+      const Real* q = Qs[side];
+      const Real rinv = recip(q[0]);
+      const Real u = q[1] * rinv, v = q[2] * rinv;
+      const Real pr = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
+      ex[side][0] = q[1]; ex[side][1] = q[1] * u + pr; ex[side][2] = q[2] * u; ex[side][3] = (q[3] + pr) * u;
+      ey[side][0] = q[2]; ey[side][1] = q[1] * v; ey[side][2] = q[2] * v + pr; ey[side][3] = (q[3] + pr) * v;
+    }
+    if constexpr (Sc::nmp == 1) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        mo.f[0][v] = mmx * Acc(Real(0.5) * (ex[0][v] + ex[1][v])) + mmy * Acc(Real(0.5) * (ey[0][v] + ey[1][v]));
+        mo.q[0][v] = Qs[0][v] - Qs[1][v];
+      }
+    } else {
+#pragma unroll
+      for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          mo.f[side][v] = mmx * Acc(ex[side][v]) + mmy * Acc(ey[side][v]);
+          mo.q[side][v] = Qs[side][v];
+        }
+    }
+  } else {
+    // split midpoint fluxes f+ = (E^(Q+) + A^ Q+)/2, f- = (E^(Q-) - A^ Q-)/2
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const Real* q = Qs[side];
+      const Real rinv = recip(q[0]);
+      const Real u = q[1] * rinv, v = q[2] * rinv;
+      const Real pr = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
+      const Acc U = mmx * Acc(u) + mmy * Acc(v);
+      const Acc sg = side == 0 ? A : -A;
+      mo.f[side][0] = Acc(0.5) * (Acc(q[0]) * U + sg * Acc(q[0]));
+      mo.f[side][1] = Acc(0.5) * (Acc(q[1]) * U + mmx * Acc(pr) + sg * Acc(q[1]));
+      mo.f[side][2] = Acc(0.5) * (Acc(q[2]) * U + mmy * Acc(pr) + sg * Acc(q[2]));
+      mo.f[side][3] = Acc(0.5) * (Acc(q[3] + pr) * U + sg * Acc(q[3]));
+    }
   }
 }
 
-// h = h+ + h- at p + 1/2 (Eqs. 3.4, 3.8, 3.16, 3.20; h- the mirror of h+): the midpoint
-// terms m0 (f+_{p+1/2} + f-_{p+1/2}) + m1 (f+_{p-1/2} + f-_{p+3/2}) given as mid0 = f+ + f- at
-// p + 1/2 and mid1 = f+_{p-1/2} + f-_{p+3/2} (two-midpoint schemes), plus the node terms
-// n_k (f+_{p+k} + f-_{p+1-k}) from the staged node fluxes.
+// h+ coefficient n_k of the node flux f+_{p+k}, k = -2..2 (0 outside)
+template <int S>
+__host__ __device__ constexpr double hnode(int k) { return k < -2 || k > 2 ? 0.0 : Scheme<S>::n(k + 2); }
+
+// h = h+ + h- at p + 1/2 (Eqs. 3.4, 3.8, 3.16, 3.20; h- the mirror of h+), the midpoint
+// terms m0 (f+_{p+1/2} + f-_{p+1/2}) + m1 (f+_{p-1/2} + f-_{p+3/2}) plus the node terms
+// n_k (f+_{p+k} + f-_{p+1-k}).  `c` is the interface p + 1/2; for two-midpoint schemes
+// `lo` holds the plus side at p - 1/2 and `hi` the minus side at p + 3/2.
+// Mixed precision: with f+- = (E^ +- A^ Q)/2 the terms regroup into a central part in the
+// metric-weighted fluxes, (1/2) sum_d (n_{-d} + n_{1+d}) (E^_{p-d} + E^_{p+1+d}) plus the
+// midpoint means, taken in double, and a dissipative part in the states,
+// (A^/2) [sum_d (n_{-d} - n_{1+d}) (Q_{p-d} - Q_{p+1+d}) + m0 (Q+ - Q-) + m1 (Q+_{p-1/2} -
+// Q-_{p+3/2})], taken in float.  In a uniform flow every state difference is exactly zero,
+// so the free-stream residual is that of the double part.
 template <int S, typename Real, typename Acc, typename At>
-__device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At& at, const Acc mid0[4],
-                                          const Acc mid1[4], Acc h[4]) {
+__device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At& at, Acc A,
+                                          const Mid<Real, Acc>& c, const Mid<Real, Acc>& lo,
+                                          const Mid<Real, Acc>& hi, Acc h[4]) {
   using Sc = Scheme<S>;
+  if constexpr (Staged<Real, Acc>::SPLIT) {
+    Acc he[4];
+    Real hq[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    if constexpr (Sc::nmp == 1) h[v] = Acc(Sc::m0) * mid0[v];
-    else h[v] = Acc(Sc::m0) * mid0[v] + Acc(Sc::m1) * mid1[v];
-  }
+    for (int v = 0; v < 4; ++v) {
+      if constexpr (Sc::nmp == 1) {
+        he[v] = Acc(Sc::m0) * c.f[0][v];
+        hq[v] = Real(Sc::m0) * c.q[0][v];
+      } else {
+        he[v] = Acc(0.5 * Sc::m0) * (c.f[0][v] + c.f[1][v]) + Acc(0.5 * Sc::m1) * (lo.f[0][v] + hi.f[1][v]);
+        hq[v] = Real(Sc::m0) * (c.q[0][v] - c.q[1][v]) + Real(Sc::m1) * (lo.q[0][v] - hi.q[1][v]);
+      }
+    }
 #pragma unroll
-  for (int kk = -2; kk <= 2; ++kk) {
-    if (Sc::n(kk + 2) == 0.0) continue;
-    Acc a[4], b[4];
-    ld4(st.fp, st.n, at(kk), a);
-    ld4(st.fm, st.n, at(1 - kk), b);
+    for (int d = 0; d <= 2; ++d) {
+      const double ce = 0.5 * (hnode<S>(-d) + hnode<S>(1 + d)), cq = hnode<S>(-d) - hnode<S>(1 + d);
+      if (ce == 0.0 && cq == 0.0) continue;
+      Acc a[4], b[4];
+      Real qa[4], qb[4];
+      ld4(st.fp, st.n, at(-d), a);
+      ld4(st.fp, st.n, at(1 + d), b);
+      ld4(st.q, st.n, at(-d), qa);
+      ld4(st.q, st.n, at(1 + d), qb);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) h[v] += Acc(Sc::n(kk + 2)) * (a[v] + b[v]);
+      for (int v = 0; v < 4; ++v) {
+        if (ce != 0.0) he[v] += Acc(ce) * (a[v] + b[v]);
+        if (cq != 0.0) hq[v] += Real(cq) * (qa[v] - qb[v]);
+      }
+    }
+    const Real hA = Real(0.5) * from_f64<Real>(A);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) h[v] = he[v] + Acc(hA * hq[v]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if constexpr (Sc::nmp == 1) h[v] = Acc(Sc::m0) * (c.f[0][v] + c.f[1][v]);
+      else h[v] = Acc(Sc::m0) * (c.f[0][v] + c.f[1][v]) + Acc(Sc::m1) * (lo.f[0][v] + hi.f[1][v]);
+    }
+#pragma unroll
+    for (int kk = -2; kk <= 2; ++kk) {
+      if (Sc::n(kk + 2) == 0.0) continue;
+      Acc a[4], b[4];
+      ld4(st.fp, st.n, at(kk), a);
+      ld4(st.fm, st.n, at(1 - kk), b);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) h[v] += Acc(Sc::n(kk + 2)) * (a[v] + b[v]);
+    }
   }
 }
+
 
 // One tile (bx along the lines, by across them) of one block.  qtab: every block's state
 // for linked faces (null for a lone block).
@@ -343,7 +471,8 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
   Staged<Real, Acc> st;
   st.carve(smem_raw, NN);
   Acc* sH = reinterpret_cast<Acc*>(smem_raw + Sh::o_h());   // h at interfaces (4 values)
-  Acc* sF = reinterpret_cast<Acc*>(smem_raw + Sh::o_f());   // f+ and f- at midpoints (two-midpoint)
+  MidStore<Real, Acc> sF;                                   // midpoint records (two-midpoint)
+  sF.carve(smem_raw + Sh::o_f(), NW);
   Acc* sA = reinterpret_cast<Acc*>(smem_raw + Sh::o_a());   // A^ per line
 
   const int n = DIR == 0 ? P.ni : P.nj;
@@ -427,17 +556,14 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     if (line >= nlines || base + p > n) continue;
     const int c0 = p + 4;  // staged position of node p
     auto at = [&](int m) { return SI(l, c0 + m); };
-    Acc fs[2][4];
-    interface_fluxes<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, sA[l], fs);
+    Mid<Real, Acc> mo;
+    interface_mid<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, sA[l], mo);
     if constexpr (Sc::nmp == 1) {
-      Acc mid0[4], h[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) mid0[v] = fs[0][v] + fs[1][v];
-      h_combine<S, Real, Acc>(st, at, mid0, mid0, h);
+      Acc h[4];
+      h_combine<S, Real, Acc>(st, at, sA[l], mo, mo, mo, h);
       st4(sH, NW, WI(l, pi), h[0], h[1], h[2], h[3]);
     } else {
-      st4(sF, NW, WI(l, pi), fs[0][0], fs[0][1], fs[0][2], fs[0][3]);
-      st4(sF + 4 * NW, NW, WI(l, pi), fs[1][0], fs[1][1], fs[1][2], fs[1][3]);
+      sF.put(WI(l, pi), mo);
     }
   }
 
@@ -452,14 +578,13 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
       if (line >= nlines || p < -1 || p > T - 1 || base + p > n - 1) continue;
       const int c0 = p + 4;
       auto at = [&](int m) { return SI(l, c0 + m); };
-      Acc a[4], b[4], c[4], d[4], mid0[4], mid1[4], h[4];
-      ld4(sF, NW, WI(l, pi), a);
-      ld4(sF + 4 * NW, NW, WI(l, pi), b);
-      ld4(sF, NW, WI(l, pi - 1), c);
-      ld4(sF + 4 * NW, NW, WI(l, pi + 1), d);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) { mid0[v] = a[v] + b[v]; mid1[v] = c[v] + d[v]; }
-      h_combine<S, Real, Acc>(st, at, mid0, mid1, h);
+      Mid<Real, Acc> c, lo, hi;
+      sF.get(WI(l, pi), 0, c);
+      sF.get(WI(l, pi), 1, c);
+      sF.get(WI(l, pi - 1), 0, lo);
+      sF.get(WI(l, pi + 1), 1, hi);
+      Acc h[4];
+      h_combine<S, Real, Acc>(st, at, sA[l], c, lo, hi, h);
       st4(sH, NW, WI(l, pi), h[0], h[1], h[2], h[3]);
     }
   }
@@ -525,7 +650,8 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
   Staged<Real, Acc> st;
   st.carve(wsm, RING);
   Acc* rH = reinterpret_cast<Acc*>(wsm + Ms::o_h());
-  Acc* rF = reinterpret_cast<Acc*>(wsm + Ms::o_f());
+  MidStore<Real, Acc> rF;
+  rF.carve(wsm + Ms::o_f(), RING);
   Real* rawq = reinterpret_cast<Real*>(wsm + Ms::o_raw());           // [4][32]
   double* rawm = reinterpret_cast<double*>(rawq + 4 * 32);           // [2][32]
   const int n = P.ni;
@@ -585,17 +711,14 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
     const int q = s0 - NMP + 32 * t + L;
     if (q <= s1 + NMP - 2) {   // interfaces s0 - NMP .. s1 + NMP - 2
       auto at = [&](int mm) { return (q + mm) & (RING - 1); };
-      Acc fs[2][4];
-      interface_fluxes<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, fs);
+      Mid<Real, Acc> mo;
+      interface_mid<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
       if constexpr (NMP == 1) {
-        Acc mid0[4], h[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) mid0[v] = fs[0][v] + fs[1][v];
-        h_combine<S, Real, Acc>(st, at, mid0, mid0, h);
+        Acc h[4];
+        h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h);
         st4(rH, RING, q & (RING - 1), h[0], h[1], h[2], h[3]);
       } else {
-        st4(rF, RING, q & (RING - 1), fs[0][0], fs[0][1], fs[0][2], fs[0][3]);
-        st4(rF + 4 * RING, RING, q & (RING - 1), fs[1][0], fs[1][1], fs[1][2], fs[1][3]);
+        rF.put(q & (RING - 1), mo);
       }
     }
     __syncwarp();
@@ -605,14 +728,13 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
       const int p = q - 1;
       if (p >= s0 - 1 && p <= s1 - 1) {
         auto at = [&](int mm) { return (p + mm) & (RING - 1); };
-        Acc a[4], b[4], c[4], d[4], mid0[4], mid1[4], h[4];
-        ld4(rF, RING, p & (RING - 1), a);
-        ld4(rF + 4 * RING, RING, p & (RING - 1), b);
-        ld4(rF, RING, (p - 1) & (RING - 1), c);
-        ld4(rF + 4 * RING, RING, (p + 1) & (RING - 1), d);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) { mid0[v] = a[v] + b[v]; mid1[v] = c[v] + d[v]; }
-        h_combine<S, Real, Acc>(st, at, mid0, mid1, h);
+        Mid<Real, Acc> c, lo, hi;
+        rF.get(p & (RING - 1), 0, c);
+        rF.get(p & (RING - 1), 1, c);
+        rF.get((p - 1) & (RING - 1), 0, lo);
+        rF.get((p + 1) & (RING - 1), 1, hi);
+        Acc h[4];
+        h_combine<S, Real, Acc>(st, at, A, c, lo, hi, h);
         st4(rH, RING, p & (RING - 1), h[0], h[1], h[2], h[3]);
       }
       __syncwarp();
@@ -649,8 +771,212 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
   cp_async_wait_all();
 }
 
+// --------------------------------------------------------------------------------------
+// Marching eta pass.  A CTA of EW warps owns 32 adjacent columns (one per lane) and a row
+// segment [s0, s1) of one block; it walks the segment EW rows per step, warp w taking row
+// r + w of the step starting at row r.  Per step (1MP / 2MP):
+//   nodes       m = r + 2 + w into the ring (row slot m mod ERING), state, metrics and the
+//               epilogue operands of the next step staged by cp.async during this step
+//   interfaces  q = r - NMP + w: midpoint fluxes, h (1MP) or the midpoint record (2MP)
+//   h           (2MP) at q - 1 from the records of q - 2 .. q
+//   outputs     node s = the interface just completed
+// with a block barrier after each phase that hands data to other warps.  The ring holds the
+// 14 rows a step reads and the 8 it stages; the start-up stages the rows below r + 2.
+// --------------------------------------------------------------------------------------
+constexpr int EW = 8;                               // warps (rows per step) of a marching eta CTA
+constexpr int ERING = 16;                           // row slots of its ring
+constexpr int MARCH_ETA = 3;                        // the marching eta variant
+__host__ __device__ constexpr int march_eta_seg(int nmp) { return 8 * EW - (2 * nmp - 1); }
+template <int S, typename Real, typename Acc>
+struct MarchEtaShape {
+  static constexpr int NMP = Scheme<S>::nmp;
+  static constexpr int NS = ERING * 32;             // ring entries (row slot x lane)
+  static constexpr int NT = EW * 32;                // threads
+  static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(NS); }
+  static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * NS; }
+  static constexpr size_t o_raw() { return o_f() + (NMP == 2 ? MidStore<Real, Acc>::bytes(NS) : 0); }
+  // per thread: next node's state and two metrics; epilogue J^-1, other difference, Q^n
+  static constexpr size_t o_ep() { return o_raw() + (size_t)NT * (4 * sizeof(Real) + 16); }
+  static constexpr size_t smem_bytes(int mode) {
+    return o_ep() + (mode == 0 ? 0 : (size_t)NT * (8 + 4 * sizeof(Acc) + (mode == 2 ? 4 * sizeof(Real) : 0)));
+  }
+};
+
+template <int S, int MODE, typename Real, typename Acc>
+__device__ __forceinline__ void march_col(const Params& P, const Real* __restrict__ Q, const Real* const* qtab,
+                                          const double* __restrict__ lam, const Acc* __restrict__ Dacc,
+                                          Acc* __restrict__ Dout, Real* qout, const Real* Qn, double ca, double cb,
+                                          double dt, int c0, int s0, int s1, unsigned char* sm) {
+  using Ms = MarchEtaShape<S, Real, Acc>;
+  constexpr int NMP = Scheme<S>::nmp;
+  constexpr int K = 2;
+  const int L = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
+  const int col = c0 + L;
+  const bool on = col < P.ni;
+  Staged<Real, Acc> st;
+  st.carve(sm, Ms::NS);
+  Acc* rH = reinterpret_cast<Acc*>(sm + Ms::o_h());
+  MidStore<Real, Acc> rF;
+  rF.carve(sm + Ms::o_f(), Ms::NS);
+  Real* rawq = reinterpret_cast<Real*>(sm + Ms::o_raw());              // [4][NT]
+  double* rawm = reinterpret_cast<double*>(rawq + 4 * Ms::NT);         // [2][NT]
+  double* eJ = reinterpret_cast<double*>(sm + Ms::o_ep());              // [NT]
+  Acc* eD = reinterpret_cast<Acc*>(eJ + Ms::NT);                       // [4][NT]
+  Real* eQ = reinterpret_cast<Real*>(eD + 4 * Ms::NT);                  // [4][NT]
+  const int n = P.nj;
+  const Real gamma = Real(P.gamma);
+  const Real eps = sizeof(Real) == 8 ? from_f64<Real>(P.eps) : from_f64<Real>(P.eps < 1e-30 ? 1e-30 : P.eps);
+  const long long plane = (long long)P.nj * P.ld;
+  const Acc A = on ? Acc(P.alpha * lam[col]) : Acc(0);
+  const Acc hA = Acc(0.5) * A;
+  auto slot = [&](int row) { return (row & (ERING - 1)) * 32 + L; };
+
+  auto stage_node = [&](int m, bool staged) {
+    if (!on || m > s1 + 3 || m > n + 3) return;
+    Real q[4];
+    double mx, my;
+    if (staged) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) q[v] = rawq[v * Ms::NT + tid];
+      mx = rawm[tid];
+      my = rawm[Ms::NT + tid];
+    } else {
+      load_state(P, Q, 1, col, m, q, qtab);
+      mx = met_at(P, 2, col, m);
+      my = met_at(P, 3, col, m);
+    }
+    Prim<Real> pw;
+    Acc amx, amy, fp[4], fm[4];
+    node_split<Real, Acc>(q, mx, my, gamma, hA, pw, amx, amy, fp, fm);
+    st.store(slot(m), q, pw, amx, amy, fp, fm, mx, my);
+  };
+  // cp.async of node (col, m) into this thread's staging slot (interior rows only), and of the
+  // epilogue operands of output node (col, s)
+  auto prefetch = [&](int m, int s) -> bool {
+    bool ok = false;
+    if (on && m >= 0 && m < n && m <= s1 + 3) {
+      const long long o = (long long)m * P.ld + col;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) cp_async<sizeof(Real)>(rawq + v * Ms::NT + tid, Q + v * plane + o);
+      const double* mp = P.met + (long long)(m + G) * P.mld + (col + G);
+      cp_async<8>(rawm + tid, mp + 2 * P.mplane);
+      cp_async<8>(rawm + Ms::NT + tid, mp + 3 * P.mplane);
+      ok = true;
+    }
+    if constexpr (MODE != MODE_ACC) {
+      if (on && s >= s0 && s < s1) {
+        const long long o = (long long)s * P.ld + col;
+        cp_async<8>(eJ + tid, P.met + 4 * P.mplane + (long long)(s + G) * P.mld + (col + G));
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cp_async<sizeof(Acc)>(eD + v * Ms::NT + tid, Dacc + v * plane + o);
+        if constexpr (MODE == MODE_STAGE) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) cp_async<sizeof(Real)>(eQ + v * Ms::NT + tid, Qn + v * plane + o);
+        }
+      }
+    }
+    return ok;
+  };
+  const int lag = NMP == 1 ? 1 : 3;                       // output s = r - lag + w
+  // start-up: rows s0 - 2 - NMP .. s0 + K - 1
+  if (w < K + 2 + NMP) stage_node(s0 - 2 - NMP + w, false);
+  bool staged = prefetch(s0 + K + w, s0 - lag + w);
+  cp_async_commit();
+  const int steps = (s1 - s0 + 2 * NMP - 1 + EW - 1) / EW;
+  for (int t = 0; t < steps; ++t) {
+    const int r = s0 + EW * t;
+    const int m = r + K + w;
+    cp_async_wait_all();
+    stage_node(m, staged);
+    // the epilogue operands of this step's output, read now: the slots are refilled below
+    const int s = r - lag + w;
+    double Jv = 0.0;
+    Acc Dv[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+    Real Qv[4] = {Real(0), Real(0), Real(0), Real(0)};
+    if constexpr (MODE != MODE_ACC) {
+      if (on && s >= s0 && s < s1) {
+        Jv = eJ[tid];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Dv[v] = eD[v * Ms::NT + tid];
+        if constexpr (MODE == MODE_STAGE) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) Qv[v] = eQ[v * Ms::NT + tid];
+        }
+      }
+    }
+    staged = prefetch(m + EW, s + EW);
+    cp_async_commit();
+    __syncthreads();
+    const int q = r - NMP + w;
+    Real qs[4] = {Real(0), Real(0), Real(0), Real(0)};
+    if (on && q <= s1 + NMP - 2) {
+      auto at = [&](int mm) { return slot(q + mm); };
+      Mid<Real, Acc> mo;
+      interface_mid<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
+      if constexpr (NMP == 1) {
+        Acc h[4];
+        h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h);
+        st4(rH, Ms::NS, slot(q), h[0], h[1], h[2], h[3]);
+      } else {
+        rF.put(slot(q), mo);
+      }
+    }
+    if constexpr (NMP == 2) {
+      __syncthreads();
+      const int p = q - 1;
+      if (on && p >= s0 - 1 && p <= s1 - 1) {
+        auto at = [&](int mm) { return slot(p + mm); };
+        Mid<Real, Acc> c, lo, hi;
+        rF.get(slot(p), 0, c);
+        rF.get(slot(p), 1, c);
+        rF.get(slot(p - 1), 0, lo);
+        rF.get(slot(p + 1), 1, hi);
+        Acc h[4];
+        h_combine<S, Real, Acc>(st, at, A, c, lo, hi, h);
+        st4(rH, Ms::NS, slot(p), h[0], h[1], h[2], h[3]);
+      }
+    }
+    if constexpr (MODE == MODE_STAGE) {
+      if (on && s >= s0 && s < s1) ld4(st.q, st.n, slot(s), qs);
+    }
+    __syncthreads();
+    // outputs: node s, H_{s+1/2} - H_{s-1/2}
+    if (on && s >= s0 && s < s1) {
+      Acc hp[4], hm[4], R[4];
+      ld4(rH, Ms::NS, slot(s), hp);
+      ld4(rH, Ms::NS, slot(s - 1), hm);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) R[v] = hp[v] - hm[v];
+      const long long o = (long long)s * P.ld + col;
+      if constexpr (MODE == MODE_ACC) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Dout[v * plane + o] = R[v];
+      } else {
+        const Acc mJ = -recip(from_f64<Acc>(Jv));
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const Acc d = (Dv[v] + R[v]) * mJ;
+          if constexpr (MODE == MODE_RHS) {
+            qout[v * plane + o] = Real(d);
+          } else {
+            qout[v * plane + o] = Real(Acc(ca) * Acc(Qv[v]) + Acc(cb) * (Acc(qs[v]) + Acc(dt) * d));
+          }
+        }
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+// Resident CTAs per SM the kernels are compiled for (register budget): FP64 2, FP32 4, mixed 3
+// for the 256-thread tiles; FP64 3, FP32 7, mixed 5 for the 128-thread marching CTAs.
+template <typename Real, typename Acc>
+constexpr int tile_ctas() { return sizeof(Real) == 8 ? 2 : std::is_same<Real, Acc>::value ? 4 : 3; }
+template <typename Real, typename Acc>
+constexpr int march_ctas() { return sizeof(Real) == 8 ? 3 : std::is_same<Real, Acc>::value ? 7 : 5; }
+
 template <int S, int DIR, int MODE, typename Real, typename Acc>
-__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 4)
+__global__ void __launch_bounds__(256, tile_ctas<Real, Acc>())
 sweep_kernel(Params P, const Real* __restrict__ Q, const double* __restrict__ lam,
              const Acc* __restrict__ Dacc, Acc* __restrict__ Dout, Real* qout, const Real* Qn,
              double ca, double cb, double dt) {
@@ -674,7 +1000,7 @@ struct BatchPass {                 // device arrays indexed by block
 };
 
 template <int S, int DIR, int MODE, typename Real, typename Acc, int V>
-__global__ void __launch_bounds__(256, sizeof(Real) == 8 ? 2 : 4)
+__global__ void __launch_bounds__(256, tile_ctas<Real, Acc>())
 sweep_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
   __shared__ Params sp;
   const TileRef t = B.tiles[blockIdx.x];
@@ -690,7 +1016,7 @@ sweep_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
 // Marching xi pass of many blocks: CTA b takes rows 4 by .. 4 by + 3 (one per warp) of
 // block tiles[b].block, segment tiles[b].bx of each row.
 template <int S, int MODE, typename Real, typename Acc>
-__global__ void __launch_bounds__(32 * MARCH_WARPS, sizeof(Real) == 8 ? 3 : 7)
+__global__ void __launch_bounds__(32 * MARCH_WARPS, march_ctas<Real, Acc>())
 march_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
   using Ms = MarchShape<S, Real, Acc>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -709,6 +1035,27 @@ march_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
                                 MODE == MODE_ACC ? B.dout[b] : nullptr, MODE == MODE_ACC ? nullptr : B.qout[b],
                                 MODE == MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, row, s0, s1,
                                 smem_raw + warp * Ms::warp_bytes());
+}
+
+// Marching eta pass of many blocks: CTA b takes the 32 columns from 32 by of block
+// tiles[b].block, row segment bx (bx along the lines, by across them, as for the tiles).
+template <typename Real, typename Acc>
+constexpr int march_eta_ctas() { return sizeof(Real) == 8 ? 1 : std::is_same<Real, Acc>::value ? 3 : 2; }
+
+template <int S, int MODE, typename Real, typename Acc>
+__global__ void __launch_bounds__(32 * EW, march_eta_ctas<Real, Acc>())
+march_eta_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Params sp;
+  const TileRef t = B.tiles[blockIdx.x];
+  if (threadIdx.x == 0) sp = B.params[t.block];
+  __syncthreads();
+  const int b = t.block;
+  const int seg = march_eta_seg(Scheme<S>::nmp);
+  const int s0 = t.bx * seg, s1 = min(sp.nj, s0 + seg);
+  march_col<S, MODE, Real, Acc>(sp, B.q[b], B.q, B.lam[b], MODE == MODE_ACC ? nullptr : B.dacc[b],
+                                MODE == MODE_ACC ? B.dout[b] : nullptr, MODE == MODE_ACC ? nullptr : B.qout[b],
+                                MODE == MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, t.by * 32, s0, s1, smem_raw);
 }
 
 // Untyped pass tables (device arrays of per-block pointers) and their typed view.
@@ -764,11 +1111,25 @@ cudaError_t launch_march_batch(const BatchPass<Real, Acc>& B, int ntiles, double
   return cudaGetLastError();
 }
 
+template <int S, int MODE, typename Real, typename Acc>
+cudaError_t launch_march_eta_batch(const BatchPass<Real, Acc>& B, int ntiles, double ca, double cb, double dt,
+                                   cudaStream_t st) {
+  auto kern = march_eta_batch_kernel<S, MODE, Real, Acc>;
+  const size_t smem = MarchEtaShape<S, Real, Acc>::smem_bytes(MODE);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (ntiles > 0) kern<<<ntiles, 32 * EW, smem, st>>>(B, ca, cb, dt);
+  return cudaGetLastError();
+}
+
 template <int S, int DIR, int MODE, typename Real, typename Acc>
 cudaError_t launch_sweep_batch(const BatchPass<Real, Acc>& B, int ntiles, int v, double ca, double cb, double dt,
                                cudaStream_t st) {
-  if constexpr (DIR == 0) {
-    if (v == MARCH) return launch_march_batch<S, MODE, Real, Acc>(B, ntiles, ca, cb, dt, st);
+  if (v == MARCH) {
+    if constexpr (DIR == 0) return launch_march_batch<S, MODE, Real, Acc>(B, ntiles, ca, cb, dt, st);
+    else return launch_march_eta_batch<S, MODE, Real, Acc>(B, ntiles, ca, cb, dt, st);
   }
   switch (v) {
     case 1: return launch_sweep_batch_v<S, DIR, MODE, Real, Acc, 1>(B, ntiles, ca, cb, dt, st);

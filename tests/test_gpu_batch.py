@@ -75,7 +75,8 @@ def test_batch_metrics_and_rhs_small_cylinder(F, scheme):
     bt.close()
 
 
-def test_batch_rk3_eager_and_graph(F):
+@pytest.mark.parametrize("variant", [0, 3])
+def test_batch_rk3_eager_and_graph(F, variant):
     blocks, states, free = _small_cylinder()
     cfgd = _cfgd(free, 3)
     Ms = O.mb_metrics(cfgd, blocks)
@@ -85,6 +86,8 @@ def test_batch_rk3_eager_and_graph(F):
     bt = F.Batch(F.Config.from_dict(cfgd), blocks, states)
     for k in range(len(blocks)):
         bt.M[k].copy_(torch.as_tensor(Ms[k]))
+    bt.set_tile_shape(0, variant)
+    bt.set_tile_shape(1, variant)
     bt.rk3_step(dt)
     bt.rk3_step(dt)
     torch.cuda.synchronize()
@@ -121,16 +124,32 @@ def test_batch_reversed_links(F):
 
 
 @pytest.mark.parametrize("prec,bound", [(1, 1e-4), (2, 5e-5)])
-def test_batch_fp32_paths(F, prec, bound):
+@pytest.mark.parametrize("scheme", [2, 3])
+def test_batch_fp32_paths(F, prec, bound, scheme):
     blocks, states, free = _small_cylinder()
     qs = [q.astype(np.float32).astype(np.float64) for q in _perturbed(states, 7, 0.05)]
-    cfgd = _cfgd(free, 2)
+    cfgd = _cfgd(free, scheme)
     Ms = O.mb_metrics(cfgd, blocks)
     Ro = O.mb_rhs(cfgd, blocks, Ms, qs)
     bt = F.Batch(F.Config.from_dict(dict(cfgd, precision=prec)), blocks, qs)
     for k in range(len(blocks)):
         bt.M[k].copy_(torch.as_tensor(Ms[k]))
-    assert _maxrel([r.double().cpu().numpy() for r in bt.rhs()], Ro) < bound
+    for v in (0, 3):
+        bt.set_tile_shape(0, v)
+        bt.set_tile_shape(1, v)
+        assert _maxrel([r.double().cpu().numpy() for r in bt.rhs()], Ro) < bound, v
+    # RK3 stages through the tile and the marching passes agree
+    dt = 2e-4
+    q1 = []
+    for v in (0, 3):
+        for k in range(len(blocks)):
+            bt.Q[k].copy_(torch.as_tensor(qs[k]))
+        bt.set_tile_shape(0, v)
+        bt.set_tile_shape(1, v)
+        bt.rk3_step(dt)
+        q1.append([q.double().cpu().numpy() for q in bt.Q])
+    change = [a - b for a, b in zip(q1[0], qs)]
+    assert _maxrel([a - b for a, b in zip(q1[1], qs)], change) < 1e-3
     bt.close()
 
 
@@ -148,7 +167,8 @@ def test_batch_full_size_cylinder(F):
         bt.M[k].copy_(torch.as_tensor(Ms[k]))
     ref = [r.cpu().numpy() for r in bt.rhs()]
     assert _maxrel(ref, Ro) < TOL
-    bt.set_tile_shape(0, 3)                   # marching xi pass
+    bt.set_tile_shape(0, 3)                   # marching passes
+    bt.set_tile_shape(1, 3)
     assert _maxrel([r.cpu().numpy() for r in bt.rhs()], Ro) < TOL
     bt.close()
 
@@ -167,25 +187,28 @@ def test_batch_tile_shapes_agree(F, scheme, prec):
     ref = [r.double().cpu().numpy() for r in bt.rhs()]
     bound = 0.0 if prec == 0 else 1e-5 * max(np.abs(r).max() for r in ref)
     shapes = set()
-    for vx in range(4):          # xi variant 3: marching warps
-        for ve in range(3):
+    for vx in range(4):          # variant 3: marching warps (xi) and marching CTAs (eta)
+        for ve in range(4):
             bt.set_tile_shape(0, vx)
             bt.set_tile_shape(1, ve)
             shapes.add((bt.tile_shape(0), bt.tile_shape(1)))
             got = [r.double().cpu().numpy() for r in bt.rhs()]
-            b = bound if vx < 3 or prec != 0 else 1e-13 * max(np.abs(r).max() for r in ref)
+            b = bound if max(vx, ve) < 3 or prec != 0 else 1e-13 * max(np.abs(r).max() for r in ref)
             assert max(np.abs(a - b_).max() for a, b_ in zip(got, ref)) <= b, (vx, ve)
-    assert len(shapes) == 12
+    assert len(shapes) == 16
     with pytest.raises(F.FspError):
-        bt.set_tile_shape(1, 3)  # the eta pass has no marching variant
+        bt.set_tile_shape(1, 4)
     bt.close()
 
 
 @pytest.mark.parametrize("scheme", [0, 1, 2, 3])
-def test_batch_marching_segments(F, scheme):
-    # rows longer than one marching segment (1100 nodes: three segments of 384, 384, 332),
-    # periodic in both directions, against the oracle and against the tile variant
-    x, y, per = I.periodic_square(1100, 10.0, 0.2, seed=5, nj=6)
+@pytest.mark.parametrize("shape", [(1100, 6), (6, 1100), (45, 70)])
+def test_batch_marching_segments(F, scheme, shape):
+    # lines longer than one marching segment: rows of 1100 nodes (xi: three segments of 384,
+    # 384, 332), columns of 1100 nodes (eta: segments of 63 or 61 rows), partial warps (6 and
+    # 45 columns); periodic in both directions, against the oracle and the tile variants
+    ni, nj = shape
+    x, y, per = I.periodic_square(ni, 10.0, 0.2, seed=5, nj=nj)
     q = I.random_state(x.shape, seed=9)
     cfgd = dict(scheme=scheme, period=per)
     M = O.metrics(cfgd, x, y)
@@ -193,9 +216,11 @@ def test_batch_marching_segments(F, scheme):
     bt = F.Batch(F.Config.from_dict(cfgd), [dict(x=x, y=y, bc=(0, 0, 0, 0), period=per)], [q])
     bt.M[0].copy_(torch.as_tensor(M))
     bt.set_tile_shape(0, 3)
+    bt.set_tile_shape(1, 3)
     got = bt.rhs()[0].cpu().numpy()
     assert np.abs(got - Ro).max() / np.abs(Ro).max() < TOL
     bt.set_tile_shape(0, 0)
+    bt.set_tile_shape(1, 0)
     ref = bt.rhs()[0].cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
     bt.close()
