@@ -132,13 +132,26 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// FP64 reciprocal by Newton-Raphson iteration on f(r) = 1/r - x: the hardware seed (PTX
+// rcp.approx.ftz.f64) refined twice by r <- r + r (1 - x r), two fused multiply-adds per step,
+// each step roughly doubling the number of correct bits.  It replaces the IEEE division on
+// the FP64 pipe for the nonzero normal operands of this code (densities, J^-1, sums of
+// weights); the result is within a few ulps of 1/x.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrt_approx(x); }
-// quotient: IEEE division in FP64; a times the approximate reciprocal in FP32
-__device__ __forceinline__ double quot(double a, double b) { return a / b; }
+// quotient: a times the refined reciprocal in FP64, a times the approximate reciprocal in FP32
+__device__ __forceinline__ double quot(double a, double b) { return a * rcp_nr(b); }
 __device__ __forceinline__ float quot(float a, float b) { return a * rcp_approx(b); }
-// reciprocal: IEEE in FP64; the approximate reciprocal in FP32
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+// reciprocal: refined in FP64; the approximate reciprocal in FP32
+__device__ __forceinline__ double recip(double x) { return rcp_nr(x); }
 __device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
 
 // A double rounded to the state type.  To float with integer operations only (round to
@@ -216,19 +229,6 @@ __device__ __forceinline__ void load_state(const Params& P, const Real* __restri
     }
   }
   rd(b);  // transmissive (and far-field outflow)
-}
-
-// Metric-weighted Euler flux E^ = mx E + my F (Eq. 2.2 in 2-D).
-template <typename Real>
-__device__ __forceinline__ void euler_flux(const Real q[4], Real mx, Real my, Real gm1, Real f[4]) {
-  const Real rinv = Real(1) / q[0];
-  const Real u = q[1] * rinv, v = q[2] * rinv;
-  const Real p = gm1 * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
-  const Real U = mx * u + my * v;
-  f[0] = q[0] * U;
-  f[1] = q[1] * U + mx * p;
-  f[2] = q[2] * U + my * p;
-  f[3] = (q[3] + p) * U;
 }
 
 // |U^| + c |k^| (the quantity maximised along a line for A^, Section 2.3)
@@ -354,7 +354,7 @@ __device__ __forceinline__ void raw_weights(const T* b, const T* C, T* w) {
     T sum = t[0];
 #pragma unroll
     for (int k = 1; k < K; ++k) sum += t[k];
-    const T inv = T(1) / sum;
+    const T inv = recip(sum);
 #pragma unroll
     for (int k = 0; k < K; ++k) w[k] = t[k] * inv;
   } else {
