@@ -35,7 +35,7 @@ __device__ __forceinline__ double weno_fwd_tape(const double* u, double eps, int
                          is_b(d4 - d3, d4 - 3.0 * d3, eps)};
     const double s[3] = {b[0] * b[0], b[1] * b[1], b[2] * b[2]};
     const double tt[3] = {C[0] * (s[1] * s[2]), C[1] * (s[0] * s[2]), C[2] * (s[0] * s[1])};
-    const double iS = 1.0 / (tt[0] + tt[1] + tt[2]);
+    const double iS = rcp_nr(tt[0] + tt[1] + tt[2]);
     const double w[3] = {tt[0] * iS, tt[1] * iS, tt[2] * iS};
     t[4] = b[0]; t[5] = b[1]; t[6] = b[2]; t[7] = w[0]; t[8] = w[1]; t[9] = w[2]; t[10] = iS;
     const double p[3] = {p0, p1, p2};
@@ -50,7 +50,7 @@ __device__ __forceinline__ double weno_fwd_tape(const double* u, double eps, int
         num += g * p[k];
         den += g;
       }
-      const double rden = 1.0 / den;
+      const double rden = rcp_nr(den);
       out = num * rden;
       t[11] = rden;
     } else {
@@ -65,7 +65,7 @@ __device__ __forceinline__ double weno_fwd_tape(const double* u, double eps, int
     const double d1 = u[1] - u[0], d2 = -u[1], d3 = u[3];
     const double b[2] = {is_b(d2 - d1, 3.0 * d2 - d1, eps), is_b(d3 - d2, d2 + d3, eps)};
     const double tt[2] = {C[0] * (b[1] * b[1]), C[1] * (b[0] * b[0])};
-    const double iS = 1.0 / (tt[0] + tt[1]);
+    const double iS = rcp_nr(tt[0] + tt[1]);
     const double w[2] = {tt[0] * iS, tt[1] * iS};
     t[4] = b[0]; t[5] = b[1]; t[7] = w[0]; t[8] = w[1]; t[10] = iS;
     const double p[2] = {p0, p1};
@@ -80,7 +80,7 @@ __device__ __forceinline__ double weno_fwd_tape(const double* u, double eps, int
         num += g * p[k];
         den += g;
       }
-      const double rden = 1.0 / den;
+      const double rden = rcp_nr(den);
       out = num * rden;
       t[11] = rden;
     } else {
@@ -204,7 +204,7 @@ struct PrimBar { double u, v, c, cinv, H, b1, h2; };
 
 __device__ __forceinline__ void prim_bwd(const double q[4], double gamma, PrimBar pb, double* qb) {
   const double gm1 = gamma - 1.0;
-  const double rinv = 1.0 / q[0];
+  const double rinv = rcp_nr(q[0]);
   const double u = q[1] * rinv, v = q[2] * rinv;
   const double h2 = 0.5 * (u * u + v * v);
   const double p = gm1 * (q[3] - q[0] * h2);
@@ -241,7 +241,7 @@ __device__ __forceinline__ void prim_bwd(const double q[4], double gamma, PrimBa
 // ---- metric-weighted Euler flux E^(q; mx, my), reverse -------------------------------
 __device__ __forceinline__ void flux_bwd(const double q[4], double mx, double my, double gm1, const double* fb,
                                          double* qb, double& mxb, double& myb) {
-  const double rinv = 1.0 / q[0];
+  const double rinv = rcp_nr(q[0]);
   const double u = q[1] * rinv, v = q[2] * rinv;
   const double p = gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
   const double U = mx * u + my * v;
@@ -270,7 +270,7 @@ __device__ __forceinline__ void flux_bwd(const double q[4], double mx, double my
 // ---- |U^| + c |k^|, reverse (|x| has derivative +1 at 0, as in the oracle) -------------
 __device__ __forceinline__ void spectral_bwd(const double q[4], double mx, double my, double gamma, double sb,
                                              double* qb, double& mxb, double& myb) {
-  const double rinv = 1.0 / q[0];
+  const double rinv = rcp_nr(q[0]);
   const double u = q[1] * rinv, v = q[2] * rinv;
   const double h = 0.5 * (q[1] * u + q[2] * v);
   const double p = (gamma - 1.0) * (q[3] - h);
