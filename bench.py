@@ -221,8 +221,43 @@ def cpu_baseline(args, seconds=12.0):
         t = time.perf_counter() - t0
         if t > seconds:
             break
-    return {"value": nodes * k / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} right-hand sides of {what} (oracle, one thread)"}
+    out = {"value": nodes * k / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{k} right-hand sides of {what} (oracle, one thread)"}
+    if args.workload == "cylinder64":
+        out["all_cores"] = cpu_all_cores(args)
+    return out
+
+
+def _oracle_block_rhs(job):
+    """One worker process: the oracle's right-hand side of one cylinder block (linked faces
+    read as transmissive), timed after its metrics are built."""
+    scheme, k = job
+    import numpy as np
+    import oracle as O
+    blocks, states, free = cylinder_workload()
+    b = blocks[k]
+    cfg = dict(scheme=scheme, bc=[1 if c == LINK else c for c in b["bc"]], bc_state=np.tile(free, (4, 1)))
+    M = O.metrics(cfg, b["x"], b["y"])
+    t0 = time.perf_counter()
+    O.rhs(cfg, M, states[k])
+    return b["x"].size, time.perf_counter() - t0
+
+
+def cpu_all_cores(args):
+    """The oracle on every host core at once: one right-hand side of each of the 64 cylinder
+    blocks, spread over a pool of worker processes (spawned: this process already holds a CUDA
+    context).  Rate = cores x (nodes / seconds summed over the blocks), the throughput with
+    every core busy."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    nblocks = len(cylinder_workload()[0])
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_block_rhs, [(args.scheme, k) for k in range(nblocks)], chunksize=1)
+    nodes = sum(r[0] for r in res)
+    busy = sum(r[1] for r in res)
+    return {"value": cores * nodes / busy / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one right-hand side of each of the {nblocks} cylinder blocks ({nodes} nodes), "
+                      f"{cores} worker processes"}
 
 
 def run_reference(args, rank):

@@ -154,12 +154,14 @@ __device__ __forceinline__ float quot(float a, float b) { return a * rcp_approx(
 __device__ __forceinline__ double recip(double x) { return rcp_nr(x); }
 __device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
 
-// A double rounded to the state type.  To float with integer operations only (round to
-// nearest even; zero and subnormals to signed zero, overflow to infinity), so the FP32
-// path issues nothing to the FP64 pipe when it reads FP64 metrics.
+// A double rounded to the state type.  from_f64<float> is the hardware conversion (round to
+// nearest even).  from_f64_int rounds the same way with integer operations only (zero and
+// subnormals to signed zero, overflow to infinity), for the mixed path, whose FP64 pipe is its
+// bottleneck.
 template <typename T> __device__ __forceinline__ T from_f64(double d);
 template <> __device__ __forceinline__ double from_f64<double>(double d) { return d; }
-template <> __device__ __forceinline__ float from_f64<float>(double d) {
+template <> __device__ __forceinline__ float from_f64<float>(double d) { return __double2float_rn(d); }
+__device__ __forceinline__ float from_f64_int(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
   const unsigned sign = hi & 0x80000000u;

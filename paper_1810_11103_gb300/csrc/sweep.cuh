@@ -102,7 +102,7 @@ struct Staged {
     st4(fp, n, o, f[0], f[1], f[2], f[3]);
     if constexpr (!SPLIT) st4(fm, n, o, g[0], g[1], g[2], g[3]);
     st2(ma, o, amx, amy);
-    if constexpr (SPLIT) st2(mr, o, from_f64<Real>(mx), from_f64<Real>(my));
+    if constexpr (SPLIT) st2(mr, o, from_f64_int(mx), from_f64_int(my));
     st4(q, n, o, qq[0], qq[1], qq[2], qq[3]);
     st4(p0, n, o, w.u, w.v, w.c, w.cinv);
     st4(p1, n, o, w.H, w.b1, w.h2, Real(0));
@@ -433,7 +433,7 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
         if (cq != 0.0) hq[v] += Real(cq) * (qa[v] - qb[v]);
       }
     }
-    const Real hA = Real(0.5) * from_f64<Real>(A);
+    const Real hA = Real(0.5) * from_f64_int(A);
 #pragma unroll
     for (int v = 0; v < 4; ++v) h[v] = he[v] + Acc(hA * hq[v]);
   } else {
@@ -515,8 +515,28 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     }
     cp_async_commit();
   }
-  // ---- phase 1: nodes.  The global loads of both rounds are issued before any arithmetic,
-  // so the second (partial) round does not wait for a second memory latency.
+  // ---- phase 1: nodes.  FP64: one node per thread and round.  Otherwise the global loads of
+  // both rounds are issued before any arithmetic, so the second (partial) round does not wait
+  // for a second memory latency.
+  if constexpr (sizeof(Real) == 8) {
+    __syncthreads();  // A^ in shared memory
+    for (int k = threadIdx.x; k < NN; k += Sh::THREADS) {
+      const int l = DIR == 0 ? k / NP : k % NL;
+      const int s = DIR == 0 ? k % NP : k / NL;
+      const int line = line0 + l;
+      if (line >= nlines) continue;
+      const int g = min(base + s - 4, n + 3);
+      Real q[4];
+      load_state(P, Q, DIR, line, g, q, qtab);
+      double mx, my;
+      if (DIR == 0) { mx = met_at(P, 0, g, line); my = met_at(P, 1, g, line); }
+      else          { mx = met_at(P, 2, line, g); my = met_at(P, 3, line, g); }
+      Prim<Real> w;
+      Acc amx, amy, fp[4], fm[4];
+      node_split<Real, Acc>(q, mx, my, gamma, Acc(0.5) * sA[l], w, amx, amy, fp, fm);
+      st.store(SI(l, s), q, w, amx, amy, fp, fm, mx, my);
+    }
+  } else {
   constexpr int NR = (NN + Sh::THREADS - 1) / Sh::THREADS;
   Real qv[NR][4];
   double mxv[NR], myv[NR];
@@ -544,6 +564,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     Acc amx, amy, fp[4], fm[4];
     node_split<Real, Acc>(qv[r], mxv[r], myv[r], gamma, Acc(0.5) * sA[l], w, amx, amy, fp, fm);
     st.store(SI(l, s), qv[r], w, amx, amy, fp, fm, mxv[r], myv[r]);
+  }
   }
   __syncthreads();
 
