@@ -287,16 +287,24 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------------------------------
 # GPU measurement
 # ------------------------------------------------------------------------------------------
+def job_rhs(nodes, steps, world):
+    """Right-hand sides x nodes of the whole job: every rank advances its own copy of the
+    workload (weak scaling), three right-hand sides per RK3 step; divided by the slowest
+    rank's time this is the job's Mcell-RHS/s."""
+    return nodes * 3 * steps * world
+
+
 class Ctx:
     def __init__(self, torch, fsp, dist, dev, world):
         self.torch, self.fsp, self.dist, self.dev, self.world = torch, fsp, dist, dev, world
-        self.stream = torch.cuda.current_stream()
+        self.stream = torch.cuda.current_stream() if dev.type == "cuda" else None
         self.flush = None
 
     def barrier(self):
         if self.world > 1:
             self.dist.barrier()
-        self.torch.cuda.synchronize()
+        if self.dev.type == "cuda":
+            self.torch.cuda.synchronize()
 
     def timed(self, body, reps, flush=False):
         torch = self.torch
@@ -379,7 +387,7 @@ def measure_cylinder(args, prec, C, per_block=False):
     t_dev, t_e2e = C.max_over_ranks(t_dev, t_e2e)
     fl = algorithmic_flops(args)
     achieved = fl["sweep_xi_per_node"] * nodes / t_k / 1e12
-    rhs_total = nodes * 3 * args.steps * C.world
+    rhs_total = job_rhs(nodes, args.steps, C.world)
     kname = ("march_batch_kernel xi (marching warps)" if tiles["xi"]["variant"] == 3 else "sweep_batch_kernel xi") \
         + ", all 64 blocks (fsp_batch_flux_difference dir 0)"
     roof = {"bound": "alu", "kernel": kname,
@@ -484,7 +492,7 @@ def measure_vortex(args, prec, C):
     t_dev, t_e2e = C.max_over_ranks(t_dev, t_e2e)
     fl = algorithmic_flops(args)
     achieved = fl["sweep_xi_per_node"] * nodes / t_k / 1e12
-    rhs_total = nodes * 3 * args.steps * C.world
+    rhs_total = job_rhs(nodes, args.steps, C.world)
     sb = Q.numel() * Q.element_size()
     return {
         "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps, "nodes": nodes, "nblocks": 1,
