@@ -2,7 +2,9 @@
 //
 // A plain, slow CPU restatement of the WENO-interpolation-based, upwind-biased,
 // free-stream-preserving (WENOIU) schemes of Q. Li and D. Sun, "WENO interpolation-based
-// and upwind-biased schemes with free-stream preservation" (arXiv:1810.11103).
+// and upwind-biased schemes with free-stream preservation" (arXiv:1810.11103): the
+// third- and fifth-order one- and two-midpoint schemes of Section 3 and the seventh-order
+// one-midpoint scheme of the Appendix (scheme index 4).
 // It is the oracle that the CUDA library is checked against.  Only the test suite,
 // the smoke check and the CPU-baseline leg of the benchmark may load it; the product
 // path never does.  It shares no code, header or table with the CUDA library.
@@ -103,7 +105,7 @@ template <> inline long double cst<long double>(long double c) { return c; }
 // ----------------------------------------------------------------------------------
 // Scheme tables (Section 3).  All four variants, with the printed coefficients.
 // ----------------------------------------------------------------------------------
-enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3 };
+enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3, S71 = 4 };
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, BC_FARFIELD = 4,
        BC_LINK = 5 };
 
@@ -136,26 +138,33 @@ static const int G = 4;  // ghost layers of the stored metrics
 struct SchemeTab {
   int r;                  // points of each WENO candidate stencil (Table 1)
   long double hmid[2];    // h+ coefficient of f+_{j+1/2+m}, m = 0, -1
-  long double hnode[5];   // h+ coefficient of f+_{j+k}, k = -2..2
-  long double cnode[3];   // delta^{c,(1)}: a_k multiplying (f_{j+k} - f_{j-k}), k = 1..3
+  long double hnode[7];   // h+ coefficient of f+_{j+k}, k = -3..3
+  long double cnode[4];   // delta^{c,(1)}: a_k multiplying (f_{j+k} - f_{j-k}), k = 1..4
   long double cmid[2];    // delta^{c,(1)}: b_m multiplying (f~_{j+m} - f~_{j-m}), m = 1/2, 3/2
 };
 
-static const SchemeTab TAB[4] = {
+static const SchemeTab TAB[5] = {
   // WENOIU3-1MP: h+ of Eq. (3.4); delta^{c,(1)} of Eq. (3.7).
-  {2, {1.0L, 0.0L}, {0.0L, -1.0L / 24, 2.0L / 24, -1.0L / 24, 0.0L},
-   {2.0L / 48, -1.0L / 48, 0.0L}, {1.0L, 0.0L}},
+  {2, {1.0L, 0.0L}, {0.0L, 0.0L, -1.0L / 24, 2.0L / 24, -1.0L / 24, 0.0L, 0.0L},
+   {2.0L / 48, -1.0L / 48, 0.0L, 0.0L}, {1.0L, 0.0L}},
   // WENOIU3-2MP: h+ of Eq. (3.8), f_{j+1/2} + (-f_{j-1/2} + 2 f_j - f_{j+1/2})/6;
   // delta^{c,(1)} of Eq. (3.9).
-  {2, {1.0L - 1.0L / 6, -1.0L / 6}, {0.0L, 0.0L, 2.0L / 6, 0.0L, 0.0L},
-   {2.0L / 12, 0.0L, 0.0L}, {11.0L / 12, -1.0L / 12}},
+  {2, {1.0L - 1.0L / 6, -1.0L / 6}, {0.0L, 0.0L, 0.0L, 2.0L / 6, 0.0L, 0.0L, 0.0L},
+   {2.0L / 12, 0.0L, 0.0L, 0.0L}, {11.0L / 12, -1.0L / 12}},
   // WENOIU5-1MP: h+ of Eq. (3.16); delta^{c,(1)} of Eq. (3.19).
-  {3, {1.0L, 0.0L}, {19.0L / 1920, -29.0L / 480, 77.0L / 960, -3.0L / 160, -7.0L / 640},
-   {17.0L / 256, -13.0L / 320, 19.0L / 3840}, {1.0L, 0.0L}},
+  {3, {1.0L, 0.0L}, {0.0L, 19.0L / 1920, -29.0L / 480, 77.0L / 960, -3.0L / 160, -7.0L / 640, 0.0L},
+   {17.0L / 256, -13.0L / 320, 19.0L / 3840, 0.0L}, {1.0L, 0.0L}},
   // WENOIU5-2MP: h+ of Eq. (3.20), f_{j+1/2} + [(-4 f_{j+1} + f_j + f_{j-1}) + (6 f_{j+1/2}
   // - 4 f_{j-1/2})]/30; delta^{c,(1)} of Eq. (3.21).
-  {3, {1.0L + 6.0L / 30, -4.0L / 30}, {0.0L, 1.0L / 30, 1.0L / 30, -4.0L / 30, 0.0L},
-   {-4.0L / 60, 1.0L / 60, 0.0L}, {19.0L / 15, -1.0L / 15}},
+  {3, {1.0L + 6.0L / 30, -4.0L / 30}, {0.0L, 0.0L, 1.0L / 30, 1.0L / 30, -4.0L / 30, 0.0L, 0.0L},
+   {-4.0L / 60, 1.0L / 60, 0.0L, 0.0L}, {19.0L / 15, -1.0L / 15}},
+  // WENOIU7-1MP: h+ of the Appendix, scheme (1) with alpha = 1, f_{j+1/2} + (-243 f_{j-3} +
+  // 1990 f_{j-2} - 7481 f_{j-1} + 8164 f_j - 341 f_{j+1} - 2378 f_{j+2} + 289 f_{j+3}) / 107520;
+  // its eighth-order delta^{c,(1)}: a_1..a_4 = (8841, -6069, 1261, -243/2) / 107520.
+  {4, {1.0L, 0.0L},
+   {-243.0L / 107520, 1990.0L / 107520, -7481.0L / 107520, 8164.0L / 107520, -341.0L / 107520,
+    -2378.0L / 107520, 289.0L / 107520},
+   {8841.0L / 107520, -6069.0L / 107520, 1261.0L / 107520, -121.5L / 107520}, {1.0L, 0.0L}},
 };
 
 // ----------------------------------------------------------------------------------
@@ -200,6 +209,10 @@ static T interp_mid(int scheme, int interp, F phi) {
   if (interp == 1) return (phi(0) + phi(1)) * cst<T>(0.5L);
   if (scheme == S31 || scheme == S32)   // 4-point Lagrange
     return (cst<T>(-1) * phi(-1) + cst<T>(9) * phi(0) + cst<T>(9) * phi(1) - phi(2)) / cst<T>(16);
+  if (scheme == S71)                    // 8-point Lagrange
+    return (cst<T>(-5) * phi(-3) + cst<T>(49) * phi(-2) - cst<T>(245) * phi(-1) + cst<T>(1225) * phi(0)
+            + cst<T>(1225) * phi(1) - cst<T>(245) * phi(2) + cst<T>(49) * phi(3) - cst<T>(5) * phi(4))
+           / cst<T>(2048);
   // 6-point Lagrange
   return (cst<T>(3) * phi(-2) - cst<T>(25) * phi(-1) + cst<T>(150) * phi(0) + cst<T>(150) * phi(1)
           - cst<T>(25) * phi(2) + cst<T>(3) * phi(3)) / cst<T>(256);
@@ -276,7 +289,7 @@ static T central_D(const Par<T>& P, const Coords<T>& C, int dir, int comp, int i
     return interp_mid<T>(P.scheme, P.interp, [&](int l) { return node(k + l); });
   };
   T d = T(0);
-  for (int k = 1; k <= 3; ++k)
+  for (int k = 1; k <= 4; ++k)
     if (S.cnode[k - 1] != 0.0L) d = d + cst<T>(S.cnode[k - 1]) * (node(k) - node(-k));
   // b_{1/2} (f~_{j+1/2} - f~_{j-1/2}) + b_{3/2} (f~_{j+3/2} - f~_{j-3/2})
   d = d + cst<T>(S.cmid[0]) * (mid(0) - mid(-1));
@@ -392,12 +405,40 @@ static T is2(T a, T b, T c) {
   return cst<T>(13.0L / 12) * d2 * d2 + cst<T>(0.25L) * d1 * d1;
 }
 
-// Piecewise-polynomial mapping g(omega) about C (Eq. 3.15 for order 2, Eq. 3.23 for 3).
+// Smoothness indicators of the r = 4 candidates (WENOIU7).  Reading: the paper gives none
+// for r = 4; Eq. (3.22) is the integral over [x_{j-1/2}, x_{j+1/2}] of the squared first and
+// second derivatives (times h and h^3) of each candidate's interpolating polynomial, and the
+// same definition is applied to the cubics of Table A1 (first to third derivatives, times h,
+// h^3, h^5).  Each is the quadratic form d^T A_k d in the differences d_i = u_{o_i} - u_{o_{i-1}}
+// of the candidate's four values (stencil j-3+k .. j+k); entries are in units of 1/2880.
+static const long double IS4[4][3][3] = {
+  {{6649, -16958, 11389}, {-16958, 45076, -31718}, {11389, -31718, 25729}},
+  {{3169, -6518, 2989}, {-6518, 17236, -8558}, {2989, -8558, 6649}},
+  {{6649, -8558, 2989}, {-8558, 17236, -6518}, {2989, -6518, 3169}},
+  {{25729, -31718, 11389}, {-31718, 45076, -16958}, {11389, -16958, 6649}},
+};
+
+template <class T>
+static T is_r4(int k, const T* v) {
+  T d[3] = {v[1] - v[0], v[2] - v[1], v[3] - v[2]};
+  T s = T(0);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) s = s + cst<T>(IS4[k][a][b] / 2880.0L) * d[a] * d[b];
+  return s;
+}
+
+// Piecewise-polynomial mapping g(omega) about C: Eq. (3.15) for order 2, Eq. (3.23) for 3,
+// and the fourth-order mapping of the Appendix for r = 4.
 template <class T>
 static T ppm_map(int order, T w, T C) {
   if (order == 2) {
     if (w <= C) { T s = w / C - cst<T>(1); return C * (cst<T>(1) - s * s); }
     T d = w - C; return C - d * d / (C - cst<T>(1));
+  }
+  if (order == 4) {
+    if (w <= C) { T s = w / C - cst<T>(1); return C * (cst<T>(1) - s * s * s * s); }
+    T d = w - C, e = C - cst<T>(1);
+    return C - d * d * d * d / (e * e * e);
   }
   if (w <= C) { T s = w / C - cst<T>(1); return C * (cst<T>(1) + s * s * s); }
   T d = w - C, e = C - cst<T>(1);
@@ -406,47 +447,60 @@ static T ppm_map(int order, T w, T C) {
 
 struct WenoOpt { int ppm, linw; };
 
+// WENO interpolation to x_{j+1/2} from u[m + 3] = u_{j+m}, m = -3..3 (Eqs. 3.10-3.13;
+// candidates of Table 1, or Table A1 for r = 4).
 template <class T>
 static T weno_mid(int r, const T* u, const WenoOpt& o, T eps) {
-  // Table 1 coefficients b^r_{k,l} and C^r_k
   static const long double b2[2][2] = {{-0.5L, 1.5L}, {0.5L, 0.5L}};
   static const long double c2[2] = {0.25L, 0.75L};
   static const long double b3[3][3] = {{3.0L / 8, -10.0L / 8, 15.0L / 8},
                                        {-1.0L / 8, 6.0L / 8, 3.0L / 8},
                                        {3.0L / 8, 6.0L / 8, -1.0L / 8}};
   static const long double c3[3] = {1.0L / 16, 10.0L / 16, 5.0L / 16};
-  // u_{j+m} = u[m + 2]
-  T p[3], IS[3], Ck[3];
-  if (r == 3) {
-    for (int k = 0; k < 3; ++k) {
+  static const long double b4[4][4] = {{-5.0L / 16, 21.0L / 16, -35.0L / 16, 35.0L / 16},
+                                       {1.0L / 16, -5.0L / 16, 15.0L / 16, 5.0L / 16},
+                                       {-1.0L / 16, 9.0L / 16, 9.0L / 16, -1.0L / 16},
+                                       {5.0L / 16, 15.0L / 16, -5.0L / 16, 1.0L / 16}};
+  static const long double c4[4] = {1.0L / 64, 21.0L / 64, 35.0L / 64, 7.0L / 64};
+  const T* uj = u + 3;   // uj[m] = u_{j+m}
+  T p[4], IS[4], Ck[4];
+  if (r == 4) {
+    for (int k = 0; k < 4; ++k) {
       // p_k = sum_l b_{k,l} u_{j-r+k+l+1} (Eq. 3.11)
       p[k] = T(0);
-      for (int l = 0; l < 3; ++l) p[k] = p[k] + cst<T>(b3[k][l]) * u[(k + l - 2) + 2];
+      for (int l = 0; l < 4; ++l) p[k] = p[k] + cst<T>(b4[k][l]) * uj[k + l - 3];
+      Ck[k] = cst<T>(c4[k]);
+      IS[k] = is_r4(k, uj + k - 3);
+    }
+  } else if (r == 3) {
+    for (int k = 0; k < 3; ++k) {
+      p[k] = T(0);
+      for (int l = 0; l < 3; ++l) p[k] = p[k] + cst<T>(b3[k][l]) * uj[k + l - 2];
       Ck[k] = cst<T>(c3[k]);
     }
-    IS[0] = is0(u[0], u[1], u[2]);
-    IS[1] = is1(u[1], u[2], u[3]);
-    IS[2] = is2(u[2], u[3], u[4]);
+    IS[0] = is0(uj[-2], uj[-1], uj[0]);
+    IS[1] = is1(uj[-1], uj[0], uj[1]);
+    IS[2] = is2(uj[0], uj[1], uj[2]);
   } else {
     for (int k = 0; k < 2; ++k) {
       p[k] = T(0);
-      for (int l = 0; l < 2; ++l) p[k] = p[k] + cst<T>(b2[k][l]) * u[(k + l - 1) + 2];
+      for (int l = 0; l < 2; ++l) p[k] = p[k] + cst<T>(b2[k][l]) * uj[k + l - 1];
       Ck[k] = cst<T>(c2[k]);
     }
-    IS[0] = is0(u[0], u[1], u[2]);
-    IS[1] = is1(u[1], u[2], u[3]);
+    IS[0] = is0(uj[-2], uj[-1], uj[0]);
+    IS[1] = is1(uj[-1], uj[0], uj[1]);
   }
-  T w[3];
+  T w[4];
   if (o.linw) {
     for (int k = 0; k < r; ++k) w[k] = Ck[k];
   } else {
     // alpha_k = C_k / (eps + IS_k)^2, omega_k = alpha_k / sum alpha (Eqs. 3.12-3.13)
-    T a[3], s = T(0);
+    T a[4], s = T(0);
     for (int k = 0; k < r; ++k) { T d = eps + IS[k]; a[k] = Ck[k] / (d * d); s = s + a[k]; }
     for (int k = 0; k < r; ++k) w[k] = a[k] / s;
     if (o.ppm) {
       // map each omega_k with its own C_k, then normalise the mapped values
-      T g[3], sg = T(0);
+      T g[4], sg = T(0);
       for (int k = 0; k < r; ++k) { g[k] = ppm_map(r, w[k], Ck[k]); sg = sg + g[k]; }
       for (int k = 0; k < r; ++k) w[k] = g[k] / sg;
     }
@@ -590,13 +644,14 @@ static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
         T Lm[4][4], Rm[4][4];
         eigvec(&q[4 * ce], nx, ny, P.gamma, Lm, Rm);
         T Wmid[4];
+        const int half = S.r == 4 ? 3 : 2;     // stencil j-half .. j+half of the side
         for (int k = 0; k < 4; ++k) {
-          T u[5];
-          for (int m = -2; m <= 2; ++m) {
+          T u[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+          for (int m = -half; m <= half; ++m) {
             const int node = side == 0 ? c0 + m : c0 + 1 - m;
             T w = T(0);
             for (int v = 0; v < 4; ++v) w = w + Lm[k][v] * q[4 * node + v];
-            u[m + 2] = w;
+            u[m + 3] = w;
           }
           Wmid[k] = weno_mid(S.r, u, wo, P.eps);
         }
@@ -627,10 +682,10 @@ static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
           hp = hp + cst<T>(S.hmid[-m]) * fpm[4 * (p + m + 2) + v];
           hm = hm + cst<T>(S.hmid[-m]) * fmm[4 * (p - m + 2) + v];
         }
-        for (int k = -2; k <= 2; ++k) {
-          if (S.hnode[k + 2] == 0.0L) continue;
-          hp = hp + cst<T>(S.hnode[k + 2]) * fp[4 * (p + k + 4) + v];
-          hm = hm + cst<T>(S.hnode[k + 2]) * fm[4 * (p + 1 - k + 4) + v];
+        for (int k = -3; k <= 3; ++k) {
+          if (S.hnode[k + 3] == 0.0L) continue;
+          hp = hp + cst<T>(S.hnode[k + 3]) * fp[4 * (p + k + 4) + v];
+          hm = hm + cst<T>(S.hnode[k + 3]) * fm[4 * (p + 1 - k + 4) + v];
         }
         Hh[4 * (p + 2) + v] = hp + hm;
       }
@@ -713,28 +768,28 @@ static void advect_rhs(int scheme, int N, double dx, const std::vector<double>& 
   auto U = [&](int k) { return u[(size_t)(((k % N) + N) % N)]; };
   std::vector<double> fmid(N), h(N);
   for (int p = 0; p < N; ++p) {              // f+_{p+1/2}
-    double st[5];
-    for (int m = -2; m <= 2; ++m) st[m + 2] = U(p + m);
+    double st[7];
+    for (int m = -3; m <= 3; ++m) st[m + 3] = U(p + m);
     fmid[p] = weno_mid<double>(S.r, st, wo, 1e-40);
   }
   for (int p = 0; p < N; ++p) {              // h_{p+1/2}
     double hp = 0.0;
     for (int m = 0; m >= -1; --m)
       if (S.hmid[-m] != 0.0L) hp += (double)S.hmid[-m] * fmid[(size_t)(((p + m) % N + N) % N)];
-    for (int k = -2; k <= 2; ++k)
-      if (S.hnode[k + 2] != 0.0L) hp += (double)S.hnode[k + 2] * U(p + k);
+    for (int k = -3; k <= 3; ++k)
+      if (S.hnode[k + 3] != 0.0L) hp += (double)S.hnode[k + 3] * U(p + k);
     h[p] = hp;
   }
   for (int p = 0; p < N; ++p) du[p] = -(h[p] - h[(p + N - 1) % N]) / dx;
 }
 
-static void advect1d(int scheme, int N, double tfinal, double* out) {
+static void advect1d(int scheme, int N, double tfinal, double* out, double dt_exp = 1.25) {
   const double PI = 3.14159265358979323846;
   const double dx = 2.0 / N;
   auto u0 = [&](double x) { return std::sin(PI * x - std::sin(PI * x) / PI); };
   std::vector<double> u(N), k1(N), k2(N), k3(N), k4(N), tmp(N);
   for (int i = 0; i < N; ++i) u[i] = u0(-1.0 + dx * i);
-  const int nsteps = (int)std::ceil(tfinal / std::pow(dx, 1.25));
+  const int nsteps = (int)std::ceil(tfinal / std::pow(dx, dt_exp));
   const double dt = tfinal / nsteps;
   for (int st = 0; st < nsteps; ++st) {
     advect_rhs(scheme, N, dx, u, k1);
@@ -845,7 +900,7 @@ static int check(const int* ip, int ni, int nj) {
   if (ni < 1 || nj < 1) return 1;
   for (int f = 0; f < 4; ++f)
     if (ip[4 + f] < 0 || ip[4 + f] > BC_FARFIELD) return 5;   // links need the multi-block entry
-  if (ip[0] < 0 || ip[0] > 3) return 2;
+  if (ip[0] < 0 || ip[0] > 4) return 2;
   if ((ip[4] == BC_PERIODIC) != (ip[5] == BC_PERIODIC)) return 3;
   if ((ip[6] == BC_PERIODIC) != (ip[7] == BC_PERIODIC)) return 3;
   if (ip[4] != BC_PERIODIC && ni < 9) return 4;
@@ -1056,9 +1111,9 @@ double orc_fsp_residual(const int* ip, const double* dp, int ni, int nj, const d
 
 int orc_long_double_digits(void) { return (int)__LDBL_MANT_DIG__; }
 
-double orc_weno(int r, int ppm, int linw, double eps, const double* u5) {
+double orc_weno(int r, int ppm, int linw, double eps, const double* u7) {
   WenoOpt o{ppm, linw};
-  return weno_mid<double>(r, u5, o, eps);
+  return weno_mid<double>(r, u7, o, eps);
 }
 
 double orc_ppm(int order, double w, double C) { return ppm_map<double>(order, w, C); }
@@ -1076,19 +1131,31 @@ void orc_eig(double gamma, const double* q, double nx, double ny, double* L, dou
     for (int b = 0; b < 4; ++b) { L[4 * a + b] = Lm[a][b]; R[4 * a + b] = Rm[a][b]; }
 }
 
-void orc_scheme_table(int scheme, double* out /* r, hmid[2], hnode[5], cnode[3], cmid[2] */) {
+void orc_scheme_table(int scheme, double* out /* r, hmid[2], hnode[7], cnode[4], cmid[2] */) {
   const SchemeTab& S = TAB[scheme];
   out[0] = S.r;
   for (int k = 0; k < 2; ++k) out[1 + k] = (double)S.hmid[k];
-  for (int k = 0; k < 5; ++k) out[3 + k] = (double)S.hnode[k];
-  for (int k = 0; k < 3; ++k) out[8 + k] = (double)S.cnode[k];
-  for (int k = 0; k < 2; ++k) out[11 + k] = (double)S.cmid[k];
+  for (int k = 0; k < 7; ++k) out[3 + k] = (double)S.hnode[k];
+  for (int k = 0; k < 4; ++k) out[10 + k] = (double)S.cnode[k];
+  for (int k = 0; k < 2; ++k) out[14 + k] = (double)S.cmid[k];
 }
 
 int orc_advect1d(int scheme, int N, double tfinal, double* out) {
-  if (scheme < 0 || scheme > 3 || N < 5) return 1;
+  if (scheme < 0 || scheme > 4 || N < 7) return 1;
   advect1d(scheme, N, tfinal, out);
   return 0;
+}
+
+// The same with dt = 2 / ceil(2 / dx^dt_exp) (dt_exp = 7/4 keeps the RK4 error below the
+// seventh-order spatial error).
+int orc_advect1d_dt(int scheme, int N, double tfinal, double dt_exp, double* out) {
+  if (scheme < 0 || scheme > 4 || N < 7 || !(dt_exp > 0.0)) return 1;
+  advect1d(scheme, N, tfinal, out, dt_exp);
+  return 0;
+}
+
+void orc_smoothness4(const double* u7, double* is4) {
+  for (int k = 0; k < 4; ++k) is4[k] = is_r4<double>(k, u7 + k);
 }
 
 int orc_riemann_exact(double gamma, const double* WL, const double* WR, double x0, double t, int n,

@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "build", "lib", "metrics", "metrics_jvp", "line_lambda", "rhs", "rhs_jvp", "rk3", "rk3_jvp",
     "cfl_dt", "count_flops", "count_flops_parts", "fsp_residual", "weno", "ppm", "smoothness", "eig",
-    "scheme_table", "advect1d", "riemann_exact", "long_double_digits", "G",
+    "scheme_table", "advect1d", "advect1d_dt", "smoothness4", "riemann_exact", "long_double_digits", "G",
     "mb_metrics", "mb_rhs", "mb_rk3",
 ]
 
@@ -82,6 +82,8 @@ def lib():
                 "orc_eig": (None, [ctypes.c_double, _D, ctypes.c_double, ctypes.c_double, _D, _D]),
                 "orc_scheme_table": (None, [ctypes.c_int, _D]),
                 "orc_advect1d": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]),
+                "orc_advect1d_dt": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]),
+                "orc_smoothness4": (None, [_D, _D]),
                 "orc_riemann_exact": (ctypes.c_int, [ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_int, _D, _D]),
                 "orc_long_double_digits": (ctypes.c_int, []),
@@ -225,9 +227,12 @@ def fsp_residual(cfg, x, y, q0, wide=False):
                                   _dp(q0), int(bool(wide)))
 
 
-def weno(r, u5, ppm=1, linw=0, eps=1e-40):
-    u5 = _f64(u5)
-    return lib().orc_weno(int(r), int(ppm), int(linw), float(eps), _dp(u5))
+def weno(r, u, ppm=1, linw=0, eps=1e-40):
+    """WENO interpolation to x_{j+1/2} from u_{j-2..j+2} (5 values) or u_{j-3..j+3} (7)."""
+    u = _f64(u)
+    if u.size == 5:
+        u = np.concatenate(([0.0], u, [0.0]))
+    return lib().orc_weno(int(r), int(ppm), int(linw), float(eps), _dp(u))
 
 
 def ppm(order, w, C):
@@ -249,9 +254,25 @@ def eig(gamma, q, nx, ny):
 
 
 def scheme_table(scheme):
-    out = np.empty(13)
+    """r, h+ midpoint coefficients (m = 0, -1), h+ node coefficients of f_{j+k} (k = -3..3),
+    central-operator node coefficients a_k (k = 1..4) and midpoint coefficients (1/2, 3/2)."""
+    out = np.empty(16)
     lib().orc_scheme_table(int(scheme), _dp(out))
-    return {"r": int(out[0]), "hmid": out[1:3], "hnode": out[3:8], "cnode": out[8:11], "cmid": out[11:13]}
+    return {"r": int(out[0]), "hmid": out[1:3], "hnode": out[3:10], "cnode": out[10:14], "cmid": out[14:16]}
+
+
+def smoothness4(u7):
+    """The four r = 4 indicators of u_{j-3..j+3}."""
+    u7 = _f64(u7)
+    out = np.empty(4)
+    lib().orc_smoothness4(_dp(u7), _dp(out))
+    return out
+
+
+def advect1d_dt(scheme, N, dt_exp, tfinal=2.0):
+    out = np.empty(3)
+    _ck(lib().orc_advect1d_dt(int(scheme), int(N), float(tfinal), float(dt_exp), _dp(out)), "advect1d_dt")
+    return out[0], out[1], int(out[2])
 
 
 def advect1d(scheme, N, tfinal=2.0):

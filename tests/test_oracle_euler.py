@@ -34,7 +34,7 @@ def _affine(ni, nj, h=0.5, s=0.2, periodic=True):
     return X, Y, per
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("periodic", [True, False])
 def test_metrics_exact_on_affine_grid(scheme, periodic):
     ni, nj, h, s = 12, 11, 0.5, 0.2
@@ -46,11 +46,12 @@ def test_metrics_exact_on_affine_grid(scheme, periodic):
         assert np.allclose(M[p], want, atol=1e-13), p
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_metrics_exact_on_polynomial_grid(scheme):
     # a curved, non-periodic grid whose coordinates are polynomials of degree <= 4 (third
-    # order schemes) or 6 (fifth order): the central operators differentiate them exactly
-    deg = 4 if scheme < 2 else 6
+    # order schemes), 6 (fifth order) or 8 (seventh): the central operators differentiate
+    # them exactly
+    deg = 4 if scheme < 2 else 6 if scheme < 4 else 8
     n = 30
     s = np.arange(n, dtype=float) / n
     XI, ETA = np.meshgrid(s, s)
@@ -74,7 +75,7 @@ def _uniform_q(u=1.0, v=1.0, rho=1.0, p=1.0):
     return np.array([rho, rho * u, rho * v, p / (GAMMA - 1) + 0.5 * rho * (u * u + v * v)])
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("interp", [0, 1])
 def test_free_stream_preservation_randomized_grid(scheme, interp):
     x, y, per = I.periodic_square(32, 10.0, 0.2, seed=1810)
@@ -122,7 +123,7 @@ def test_table4_free_stream_on_paper_grid(scheme):
 
 def test_conservation_periodic():
     x, y, per = I.periodic_square(24, 6.0, 0.2, seed=11, nj=20)
-    for scheme in range(4):
+    for scheme in range(5):
         cfg = _cfg(scheme=scheme, period=per)
         M = O.metrics(cfg, x, y)
         q = I.random_state(x.shape, seed=5)
@@ -133,7 +134,7 @@ def test_conservation_periodic():
             assert abs(s) < 1e-13 * np.abs(J * R[v]).sum(), (scheme, v, s)
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_mirror_symmetry(scheme):
     ni = nj = 20
     x, y, per = I.periodic_square(ni, 8.0, 0.2, seed=3)
@@ -150,7 +151,7 @@ def test_mirror_symmetry(scheme):
     assert np.allclose(back, R, rtol=0, atol=1e-12 * np.abs(R).max())
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_transpose_symmetry(scheme):
     x, y, per = I.periodic_square(18, 8.0, 0.2, seed=4)
     q = I.isentropic_vortex(x, y, (4.3, 3.7), strength=4.0, free=(1.0, 0.3, -0.2, 1.0), period=(8.0, 8.0))
@@ -184,7 +185,12 @@ def _closed_form_linear_rhs(scheme, q, h, alpha=1.1, gamma=GAMMA):
         c = np.sqrt(gamma * p / rho)
         sp = np.abs(mx * u + my * v) + c * math.hypot(mx, my)
         A = alpha * (sp.max(axis=1, keepdims=True) if axis == 2 else sp.max(axis=0, keepdims=True))
-        if r == 3:
+        if r == 4:
+            # the 7-point interpolant at j + 1/2 (nodes j-3 .. j+3), and its mirror
+            cs = np.array([-5, 42, -175, 700, 525, -70, 7]) / 1024
+            lin = lambda a: sum(c * sh(a, m) for c, m in zip(cs, range(-3, 4)))
+            linm = lambda a: sum(c * sh(a, 1 - m) for c, m in zip(cs, range(-3, 4)))
+        elif r == 3:
             lin = lambda a: (3 * sh(a, -2) - 20 * sh(a, -1) + 90 * a + 60 * sh(a, 1) - 5 * sh(a, 2)) / 128
             linm = lambda a: (3 * sh(a, 3) - 20 * sh(a, 2) + 90 * sh(a, 1) + 60 * a - 5 * sh(a, -1)) / 128
         else:
@@ -196,13 +202,13 @@ def _closed_form_linear_rhs(scheme, q, h, alpha=1.1, gamma=GAMMA):
         fpm = 0.5 * (_euler_x_flux(qp, mx, my) + A * qp)
         fmm = 0.5 * (_euler_x_flux(qm, mx, my) - A * qm)
         H = tab["hmid"][0] * (fpm + fmm) + tab["hmid"][1] * (sh(fpm, -1) + sh(fmm, 1))
-        for k in range(-2, 3):
-            H = H + tab["hnode"][k + 2] * (sh(fp, k) + sh(fm, 1 - k))
+        for k in range(-3, 4):
+            H = H + tab["hnode"][k + 3] * (sh(fp, k) + sh(fm, 1 - k))
         total += H - sh(H, -1)
     return -total / (h * h)
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_linear_weights_reduce_to_linear_upwind_operator(scheme):
     n, L = 16, 8.0
     x, y, per = I.periodic_square(n, L, 0.0, seed=0)
@@ -213,12 +219,13 @@ def test_linear_weights_reduce_to_linear_upwind_operator(scheme):
     assert np.allclose(R, want, rtol=0, atol=1e-12 * np.abs(want).max())
 
 
-@pytest.mark.parametrize("scheme,order", [(0, 3), (1, 3), (2, 5), (3, 5)])
-def test_design_order_on_curved_grid(scheme, order):
+@pytest.mark.parametrize("scheme,order,ns", [(0, 3, (128, 256)), (1, 3, (128, 256)), (2, 5, (128, 256)),
+                                            (3, 5, (128, 256)), (4, 7, (128, 256))])
+def test_design_order_on_curved_grid(scheme, order, ns):
     # a stationary isentropic vortex is an exact steady solution: the residual converges
     # at the design order (linear weights isolate the scheme's order)
     errs = []
-    for n in (128, 256):
+    for n in ns:
         x, y, per = I.curved_periodic(n, 16.0, 0.1, origin=(-8.0, -8.0))
         cfg = _cfg(scheme=scheme, period=per, linear_weights=1)
         q = I.isentropic_vortex(x, y, (0.0, 0.0), free=(1.0, 0.0, 0.0, 1.0))
@@ -297,7 +304,7 @@ def test_exact_riemann_solver_jump_conditions():
     assert np.allclose(u[fan] + 2 * c / (g - 1), 2 * math.sqrt(g) / (g - 1), rtol=1e-12)
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_sod_against_exact_solution(scheme):
     x, y, q, per = I.sod_1d(200)
     cfg = _cfg(scheme=scheme, period=per, bc=(1, 1, 0, 0))

@@ -1,7 +1,8 @@
 """Pins of the oracle's scheme algebra against what the paper fixes (CPU only).
 
-* the printed central operators (Eqs. 3.7, 3.9, 3.19, 3.21) equal the central-scheme
-  decomposition (Eq. 2.7) of the printed h+ formulas (Eqs. 3.4, 3.8, 3.16, 3.20);
+* the printed central operators (Eqs. 3.7, 3.9, 3.19, 3.21, and the Appendix's eighth-order
+  one for WENOIU7-1MP) equal the central-scheme decomposition (Eq. 2.7) of the printed h+
+  formulas (Eqs. 3.4, 3.8, 3.16, 3.20, Appendix scheme (1) with alpha = 1);
 * every h+ formula and central operator has its design order on polynomials;
 * the WENO interpolation of Table 1 is exact on polynomials with linear weights,
   non-oscillatory at a step, and the indicators equal the printed Eq. (3.22);
@@ -15,13 +16,13 @@ import pytest
 
 import oracle as O
 
-SCHEMES = [0, 1, 2, 3]
-ORDER = {0: 3, 1: 3, 2: 5, 3: 5}
+SCHEMES = [0, 1, 2, 3, 4]
+ORDER = {0: 3, 1: 3, 2: 5, 3: 5, 4: 7}
 
 
 def _csd(tab):
     """Node and midpoint coefficients of (H_{j+1/2} - H_{j-1/2}) with H = (h+ + h-)/2."""
-    hn = {k: tab["hnode"][k + 2] for k in range(-2, 3)}
+    hn = {k: tab["hnode"][k + 3] for k in range(-3, 4)}
     hm = {0: tab["hmid"][0], -1: tab["hmid"][1]}
     cH = {}
     for k, c in hn.items():               # h+ node offsets k, h- mirrored to 1 - k
@@ -31,8 +32,8 @@ def _csd(tab):
     for m, c in hm.items():               # h+ midpoint offsets m, h- mirrored to -m
         cM[m] = cM.get(m, 0.0) + 0.5 * c
         cM[-m] = cM.get(-m, 0.0) + 0.5 * c
-    node = {o: cH.get(o, 0.0) - cH.get(o + 1, 0.0) for o in range(-4, 5)}
-    mid = {o: cM.get(o, 0.0) - cM.get(o + 1, 0.0) for o in range(-4, 5)}
+    node = {o: cH.get(o, 0.0) - cH.get(o + 1, 0.0) for o in range(-5, 6)}
+    mid = {o: cM.get(o, 0.0) - cM.get(o + 1, 0.0) for o in range(-5, 6)}
     return node, mid
 
 
@@ -40,11 +41,12 @@ def _csd(tab):
 def test_printed_central_operator_is_csd_of_printed_h(scheme):
     tab = O.scheme_table(scheme)
     node, mid = _csd(tab)
-    for k in (1, 2, 3):
+    for k in (1, 2, 3, 4):
         a = tab["cnode"][k - 1]
         assert node[k] == pytest.approx(a, abs=1e-15)
         assert node[-k] == pytest.approx(-a, abs=1e-15)
     assert node[0] == pytest.approx(0.0, abs=1e-15)
+    assert node[5] == pytest.approx(0.0, abs=1e-15) and node[-5] == pytest.approx(0.0, abs=1e-15)
     # midpoint j+1/2+m' <-> offset m'; b_{1/2} on (f~_{j+1/2} - f~_{j-1/2}), b_{3/2} likewise
     b12, b32 = tab["cmid"]
     assert mid[0] == pytest.approx(b12, abs=1e-15) and mid[-1] == pytest.approx(-b12, abs=1e-15)
@@ -56,7 +58,7 @@ def test_printed_central_operator_is_csd_of_printed_h(scheme):
 def _h_plus(tab, f, j):
     """h+_{j+1/2} on unit spacing with exact midpoint values f(j + 1/2 + m)."""
     h = sum(tab["hmid"][-m] * f(j + 0.5 + m) for m in (0, -1))
-    return h + sum(tab["hnode"][k + 2] * f(j + k) for k in range(-2, 3))
+    return h + sum(tab["hnode"][k + 3] * f(j + k) for k in range(-3, 4))
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
@@ -77,11 +79,11 @@ def test_h_formula_design_order(scheme):
 @pytest.mark.parametrize("scheme", SCHEMES)
 def test_central_operator_order(scheme):
     tab = O.scheme_table(scheme)
-    q = ORDER[scheme] + 1  # 4 or 6
+    q = ORDER[scheme] + 1  # 4, 6 or 8
     j = -0.2
     for d in range(0, q + 2):
         f = lambda x, d=d: x ** d
-        got = sum(tab["cnode"][k - 1] * (f(j + k) - f(j - k)) for k in (1, 2, 3))
+        got = sum(tab["cnode"][k - 1] * (f(j + k) - f(j - k)) for k in (1, 2, 3, 4))
         got += tab["cmid"][0] * (f(j + 0.5) - f(j - 0.5)) + tab["cmid"][1] * (f(j + 1.5) - f(j - 1.5))
         want = d * j ** (d - 1) if d > 0 else 0.0
         if d <= q:
