@@ -61,8 +61,12 @@ typedef enum {
   FSP_ERR_NOMEM = 6
 } fsp_status;
 
-/* Schemes of Section 3: third- and fifth-order, one or two midpoints. */
-enum { FSP_WENOIU3_1MP = 0, FSP_WENOIU3_2MP = 1, FSP_WENOIU5_1MP = 2, FSP_WENOIU5_2MP = 3 };
+/* Schemes of Section 3: third- and fifth-order, one or two midpoints; and the seventh-order
+ * one-midpoint scheme of the Appendix (scheme (1) with alpha = 1: Table A1 candidates, the
+ * fourth-order mapping, an eighth-order central operator and eight-point midpoint metrics;
+ * its smoothness indicators are those of Eq. 3.22's definition applied to the cubics of
+ * Table A1).  The adjoint entry points do not cover FSP_WENOIU7_1MP. */
+enum { FSP_WENOIU3_1MP = 0, FSP_WENOIU3_2MP = 1, FSP_WENOIU5_1MP = 2, FSP_WENOIU5_2MP = 3, FSP_WENOIU7_1MP = 4 };
 /* Arithmetic of the right-hand side.  Metrics are FP64 in every mode.
  * FSP_FP64        everything in double.
  * FSP_FP32        state, WENO and fluxes in float (metrics rounded to float on load); the
@@ -218,7 +222,7 @@ fsp_status fsp_norms(const fsp_block* blk, int precision, const void* A, const v
  * lowest index attaining it.  Adjoint outputs are accumulated (+=) into the caller's
  * buffers, which the caller zeroes.  The workspace must hold fsp_vjp_workspace_size bytes.
  * Every adjoint entry point, the size queries included, returns FSP_ERR_UNSUPPORTED for a
- * precision other than FSP_FP64.
+ * precision other than FSP_FP64 or for FSP_WENOIU7_1MP.
  */
 fsp_status fsp_vjp_workspace_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes);
 
@@ -254,7 +258,8 @@ fsp_status fsp_rk3_step_vjp_tape(const fsp_config* cfg, const fsp_block* blk, co
                                  double* metrics_bar, void* ws, size_t ws_bytes, void* stream);
 
 /* x_bar, y_bar += (d metrics / d(x, y))^T metrics_bar: the reverse of fsp_metrics through
- * the ghost-coordinate rule (periodic offsets are constants). */
+ * the ghost-coordinate rule (periodic offsets are constants).  FSP_ERR_UNSUPPORTED for
+ * FSP_WENOIU7_1MP. */
 fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const double* x, const double* y,
                            const double* metrics_bar, double* x_bar, double* y_bar, void* stream);
 

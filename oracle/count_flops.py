@@ -41,8 +41,8 @@ def main():
     res = {"workload": "periodic vortex 256x256, randomised grid A=0.2, seed 1810",
            "how": "oracle with an operation-counting scalar; + - * / sqrt = 1 flop each",
            "schemes": {}}
-    names = ["WENOIU3-1MP", "WENOIU3-2MP", "WENOIU5-1MP", "WENOIU5-2MP"]
-    for s in range(4):
+    names = ["WENOIU3-1MP", "WENOIU3-2MP", "WENOIU5-1MP", "WENOIU5-2MP", "WENOIU7-1MP"]
+    for s in range(5):
         cfg = dict(scheme=s, period=per)
         M = O.metrics(cfg, x, y)
         lx, sx, le, se, fin = O.count_flops_parts(cfg, M, q)
@@ -53,7 +53,7 @@ def main():
             "sweep_eta_per_node": (se + fin) / n,
         }
     res["cylinder64"] = {"workload": "64-block cylinder (seed 1812), linked faces counted as transmissive",
-                         "schemes": {names[s]: cylinder_counts(s) for s in (2,)}}
+                         "schemes": {names[s]: cylinder_counts(s) for s in (2, 4)}}
     with open(OUT, "w") as f:
         json.dump(res, f, indent=1)
     print(OUT)

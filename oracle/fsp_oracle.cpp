@@ -420,10 +420,20 @@ static const long double IS4[4][3][3] = {
 
 template <class T>
 static T is_r4(int k, const T* v) {
+  // the coefficients in the scalar type, converted once (long double is software arithmetic
+  // on some hosts)
+  static const struct Coef {
+    T c[4][3][3];
+    Coef() {
+      for (int q = 0; q < 4; ++q)
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) c[q][a][b] = cst<T>(IS4[q][a][b] / 2880.0L);
+    }
+  } A;
   T d[3] = {v[1] - v[0], v[2] - v[1], v[3] - v[2]};
   T s = T(0);
   for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) s = s + cst<T>(IS4[k][a][b] / 2880.0L) * d[a] * d[b];
+    for (int b = 0; b < 3; ++b) s = s + A.c[k][a][b] * d[a] * d[b];
   return s;
 }
 
@@ -465,11 +475,20 @@ static T weno_mid(int r, const T* u, const WenoOpt& o, T eps) {
   const T* uj = u + 3;   // uj[m] = u_{j+m}
   T p[4], IS[4], Ck[4];
   if (r == 4) {
+    static const struct Tab4 {
+      T b[4][4], c[4];
+      Tab4() {
+        for (int k = 0; k < 4; ++k) {
+          c[k] = cst<T>(c4[k]);
+          for (int l = 0; l < 4; ++l) b[k][l] = cst<T>(b4[k][l]);
+        }
+      }
+    } tab4;
     for (int k = 0; k < 4; ++k) {
       // p_k = sum_l b_{k,l} u_{j-r+k+l+1} (Eq. 3.11)
       p[k] = T(0);
-      for (int l = 0; l < 4; ++l) p[k] = p[k] + cst<T>(b4[k][l]) * uj[k + l - 3];
-      Ck[k] = cst<T>(c4[k]);
+      for (int l = 0; l < 4; ++l) p[k] = p[k] + tab4.b[k][l] * uj[k + l - 3];
+      Ck[k] = tab4.c[k];
       IS[k] = is_r4(k, uj + k - 3);
     }
   } else if (r == 3) {

@@ -569,7 +569,7 @@ Params params_of(const fsp_config& c, const fsp_block& b, const double* metrics)
 extern "C" fsp_status fsp_vjp_workspace_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes) {
   size_t fwd = 0;
   if (fsp_status s = fsp_workspace_size(cfg, blk, &fwd)) return s;
-  if (cfg->precision != FSP_FP64) return FSP_ERR_UNSUPPORTED;
+  if (cfg->precision != FSP_FP64 || cfg->scheme == S71) return FSP_ERR_UNSUPPORTED;
   if (!bytes) return FSP_ERR_INVALID_ARG;
   *bytes = vjp_ws(*cfg, *blk, fwd).total;
   return FSP_OK;
@@ -675,9 +675,10 @@ static fsp_status reverse_stages(const fsp_config& c, const fsp_block& b, const 
   return FSP_OK;
 }
 
+// The adjoint covers the FP64 third- and fifth-order schemes (not WENOIU7-1MP).
 static fsp_status check_vjp(const fsp_config* cfg, const fsp_block* blk, size_t* fwd) {
   if (fsp_status s = fsp_workspace_size(cfg, blk, fwd)) return s;
-  if (cfg->precision != FSP_FP64) return FSP_ERR_UNSUPPORTED;
+  if (cfg->precision != FSP_FP64 || cfg->scheme == S71) return FSP_ERR_UNSUPPORTED;
   return FSP_OK;
 }
 
@@ -772,6 +773,7 @@ fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const do
                            const double* metrics_bar, double* x_bar, double* y_bar, void* stream) {
   size_t fwd = 0;
   if (fsp_status s = fsp_workspace_size(cfg, blk, &fwd)) return s;
+  if (cfg->scheme == S71) return FSP_ERR_UNSUPPORTED;
   if (!dptr(x) || !dptr(y) || !dptr(metrics_bar) || !dptr(x_bar) || !dptr(y_bar)) return FSP_ERR_INVALID_ARG;
   W9 w;
   central_weights(cfg->scheme, cfg->interp, w.w);

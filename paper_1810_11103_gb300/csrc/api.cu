@@ -46,7 +46,7 @@ bool device_pointer(const void* p) {
 
 fsp_status check_cfg(const fsp_config* c, const fsp_block* b) {
   if (!c || !b) return FSP_ERR_INVALID_ARG;
-  if (c->scheme < 0 || c->scheme > 3) return FSP_ERR_INVALID_ARG;
+  if (c->scheme < 0 || c->scheme > 4) return FSP_ERR_INVALID_ARG;
   if (c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED) return FSP_ERR_INVALID_ARG;
   if (c->interp < 0 || c->interp > 1) return FSP_ERR_INVALID_ARG;
   for (int f = 0; f < 4; ++f)

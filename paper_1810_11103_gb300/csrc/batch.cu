@@ -77,14 +77,17 @@ __device__ void coord_mb(const CoordBlock* __restrict__ B, int b, int i, int j, 
   }
 }
 
-__device__ __forceinline__ double central_diff9(const Central& c, int interp, bool sixth, const double* f) {
-  double d = c.a1 * (f[5] - f[3]) + c.a2 * (f[6] - f[2]) + c.a3 * (f[7] - f[1]);
+// f[k] = f_{j+k-4}; pts = points of the midpoint interpolation (4, 6, or 8 for WENOIU7)
+__device__ __forceinline__ double central_diff9(const Central& c, int interp, int pts, const double* f) {
+  double d = c.a1 * (f[5] - f[3]) + c.a2 * (f[6] - f[2]) + c.a3 * (f[7] - f[1]) + c.a4 * (f[8] - f[0]);
+  if (pts == 8) return d + c.b12 * (mid_interp8(interp, f + 1) - mid_interp8(interp, f + 0));
+  const bool sixth = pts == 6;
   d += c.b12 * (mid_interp(interp, sixth, f + 2) - mid_interp(interp, sixth, f + 1));
   if (c.b32 != 0.0) d += c.b32 * (mid_interp(interp, sixth, f + 3) - mid_interp(interp, sixth, f + 0));
   return d;
 }
 
-__global__ void metrics_mb_kernel(const CoordBlock* __restrict__ B, int b, Central cen, int interp, int sixth,
+__global__ void metrics_mb_kernel(const CoordBlock* __restrict__ B, int b, Central cen, int interp, int pts,
                                   double* __restrict__ M) {
   const int ni = B[b].ni, nj = B[b].nj;
   const int W = ni + 2 * G, H = nj + 2 * G;
@@ -97,8 +100,8 @@ __global__ void metrics_mb_kernel(const CoordBlock* __restrict__ B, int b, Centr
       coord_mb(B, b, i + k - 4, j, fx[k], fy[k]);
       coord_mb(B, b, i, j + k - 4, gx[k], gy[k]);
     }
-    const double x_xi = central_diff9(cen, interp, sixth, fx), y_xi = central_diff9(cen, interp, sixth, fy);
-    const double x_eta = central_diff9(cen, interp, sixth, gx), y_eta = central_diff9(cen, interp, sixth, gy);
+    const double x_xi = central_diff9(cen, interp, pts, fx), y_xi = central_diff9(cen, interp, pts, fy);
+    const double x_eta = central_diff9(cen, interp, pts, gx), y_eta = central_diff9(cen, interp, pts, gy);
     M[0 * plane + t] = y_eta;
     M[1 * plane + t] = -x_eta;
     M[2 * plane + t] = -y_xi;
@@ -205,7 +208,7 @@ size_t acc_elem(int prec) { return prec == FSP_FP32 ? 4 : 8; }
 
 fsp_status check_batch(const fsp_config* c, int nb, const fsp_block* blk, const int* bc, const fsp_link* lk) {
   if (!c || nb < 1 || !blk || !bc || !lk) return FSP_ERR_INVALID_ARG;
-  if (c->scheme < 0 || c->scheme > 3 || c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED ||
+  if (c->scheme < 0 || c->scheme > 4 || c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED ||
       c->interp < 0 || c->interp > 1 || !(c->gamma > 1.0) || !(c->lf_alpha > 0.0) || !(c->eps > 0.0))
     return FSP_ERR_INVALID_ARG;
   for (int b = 0; b < nb; ++b) {
@@ -402,7 +405,7 @@ fsp_status fsp_batch_metrics(fsp_batch* h, void* stream) {
     const long long n = (long long)(h->blk[b].ni + 2 * G) * (h->blk[b].nj + 2 * G);
     const long long want = (n + 255) / 256;
     metrics_mb_kernel<<<(int)(want < 152 * 8 ? want : 152 * 8), 256, 0, st>>>(
-        h->d_coords, b, cen, h->cfg.interp, h->cfg.scheme >= S51 ? 1 : 0, h->M[b]);
+        h->d_coords, b, cen, h->cfg.interp, h->cfg.scheme == S71 ? 8 : h->cfg.scheme >= S51 ? 6 : 4, h->M[b]);
     if (cudaGetLastError() != cudaSuccess) return FSP_ERR_CUDA;
   }
   return FSP_OK;

@@ -10,7 +10,7 @@ namespace fsp {
 
 constexpr int G = 4;  // ghost layers of the stored metrics
 
-enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3 };
+enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3, S71 = 4 };
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, BC_FARFIELD = 4,
        BC_LINK = 5 };
 
@@ -18,7 +18,8 @@ enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, 
 // Scheme coefficients (Section 3)
 // --------------------------------------------------------------------------------------
 // Scheme<S>: r = points per WENO candidate, nmp = midpoints in h+, m0/m1 = h+ coefficients
-// of f+_{j+1/2} and f+_{j-1/2}, n(k) = h+ coefficient of f+_{j+k-2} (k = 0..4).
+// of f+_{j+1/2} and f+_{j-1/2}, n(k) = h+ coefficient of f+_{j+k-2} (k = 0..4), hn(k) = h+
+// coefficient of f+_{j+k} for any offset k (zero outside the scheme's stencil).
 template <int S> struct Scheme;
 // WENOIU3-1MP, Eq. (3.4): h+ = f_{j+1/2} + (-f_{j-1} + 2 f_j - f_{j+1}) / 24
 template <> struct Scheme<S31> {
@@ -27,12 +28,14 @@ template <> struct Scheme<S31> {
   __host__ __device__ static constexpr double n(int k) {
     return k == 1 || k == 3 ? -1.0 / 24 : k == 2 ? 2.0 / 24 : 0.0;
   }
+  __host__ __device__ static constexpr double hn(int k) { return k < -2 || k > 2 ? 0.0 : n(k + 2); }
 };
 // WENOIU3-2MP, Eq. (3.8): h+ = f_{j+1/2} + (-f_{j-1/2} + 2 f_j - f_{j+1/2}) / 6
 template <> struct Scheme<S32> {
   static constexpr int r = 2, nmp = 2;
   static constexpr double m0 = 5.0 / 6, m1 = -1.0 / 6;
   __host__ __device__ static constexpr double n(int k) { return k == 2 ? 2.0 / 6 : 0.0; }
+  __host__ __device__ static constexpr double hn(int k) { return k < -2 || k > 2 ? 0.0 : n(k + 2); }
 };
 // WENOIU5-1MP, Eq. (3.16)
 template <> struct Scheme<S51> {
@@ -41,6 +44,7 @@ template <> struct Scheme<S51> {
   __host__ __device__ static constexpr double n(int k) {
     return k == 0 ? 19.0 / 1920 : k == 1 ? -29.0 / 480 : k == 2 ? 77.0 / 960 : k == 3 ? -3.0 / 160 : -7.0 / 640;
   }
+  __host__ __device__ static constexpr double hn(int k) { return k < -2 || k > 2 ? 0.0 : n(k + 2); }
 };
 // WENOIU5-2MP, Eq. (3.20): h+ = f_{j+1/2} + [(-4 f_{j+1} + f_j + f_{j-1}) + (6 f_{j+1/2}
 // - 4 f_{j-1/2})] / 30
@@ -50,18 +54,32 @@ template <> struct Scheme<S52> {
   __host__ __device__ static constexpr double n(int k) {
     return k == 1 || k == 2 ? 1.0 / 30 : k == 3 ? -4.0 / 30 : 0.0;
   }
+  __host__ __device__ static constexpr double hn(int k) { return k < -2 || k > 2 ? 0.0 : n(k + 2); }
+};
+// WENOIU7-1MP (Appendix, scheme (1) with alpha = 1): h+ = f_{j+1/2} + (-243 f_{j-3} +
+// 1990 f_{j-2} - 7481 f_{j-1} + 8164 f_j - 341 f_{j+1} - 2378 f_{j+2} + 289 f_{j+3}) / 107520
+template <> struct Scheme<S71> {
+  static constexpr int r = 4, nmp = 1;
+  static constexpr double m0 = 1.0, m1 = 0.0;
+  __host__ __device__ static constexpr double hn(int k) {
+    return k == -3 ? -243.0 / 107520 : k == -2 ? 1990.0 / 107520 : k == -1 ? -7481.0 / 107520
+         : k == 0 ? 8164.0 / 107520 : k == 1 ? -341.0 / 107520 : k == 2 ? -2378.0 / 107520
+         : k == 3 ? 289.0 / 107520 : 0.0;
+  }
 };
 
 // Central operator delta^{c,(1)} of each scheme (Eq. 2.7), used for the metrics:
 //   D f_j = sum_k a_k (f_{j+k} - f_{j-k}) + b_{1/2}(f~_{j+1/2} - f~_{j-1/2})
-//           + b_{3/2}(f~_{j+3/2} - f~_{j-3/2})
-struct Central { double a1, a2, a3, b12, b32; };
+//           + b_{3/2}(f~_{j+3/2} - f~_{j-3/2}),  k = 1..4
+struct Central { double a1, a2, a3, b12, b32, a4; };
 __host__ __device__ inline Central central_of(int scheme) {
   switch (scheme) {
     case S31: return {2.0 / 48, -1.0 / 48, 0.0, 1.0, 0.0};              // Eq. (3.7)
     case S32: return {2.0 / 12, 0.0, 0.0, 11.0 / 12, -1.0 / 12};        // Eq. (3.9)
     case S51: return {17.0 / 256, -13.0 / 320, 19.0 / 3840, 1.0, 0.0};  // Eq. (3.19)
-    default:  return {-4.0 / 60, 1.0 / 60, 0.0, 19.0 / 15, -1.0 / 15};  // Eq. (3.21)
+    case S52: return {-4.0 / 60, 1.0 / 60, 0.0, 19.0 / 15, -1.0 / 15};  // Eq. (3.21)
+    default:  // the Appendix's eighth-order operator of WENOIU7-1MP
+      return {8841.0 / 107520, -6069.0 / 107520, 1261.0 / 107520, 1.0, 0.0, -121.5 / 107520};
   }
 }
 
@@ -72,6 +90,14 @@ __device__ __forceinline__ T mid_interp(int interp, bool sixth, const T* v) {
   if (interp == 1) return T(0.5) * (v[2] + v[3]);
   if (!sixth) return (T(9) * (v[2] + v[3]) - (v[1] + v[4])) * T(1.0 / 16);
   return (T(150) * (v[2] + v[3]) - T(25) * (v[1] + v[4]) + T(3) * (v[0] + v[5])) * T(1.0 / 256);
+}
+
+// The same for WENOIU7 from v[k] = f_{j+k-3}, k = 0..7: eight-point Lagrange.
+template <typename T>
+__device__ __forceinline__ T mid_interp8(int interp, const T* v) {
+  if (interp == 1) return T(0.5) * (v[3] + v[4]);
+  return (T(1225) * (v[3] + v[4]) - T(245) * (v[2] + v[5]) + T(49) * (v[1] + v[6]) - T(5) * (v[0] + v[7])) *
+         T(1.0 / 2048);
 }
 
 // --------------------------------------------------------------------------------------
@@ -345,7 +371,13 @@ __device__ __forceinline__ void raw_weights(const T* b, const T* C, T* w) {
 #pragma unroll
     for (int k = 0; k < K; ++k) s[k] = b[k] * b[k];
     T t[K];
-    if constexpr (K == 3) {
+    if constexpr (K == 4) {
+      const T s01 = s[0] * s[1], s23 = s[2] * s[3];
+      t[0] = C[0] * (s[1] * s23);
+      t[1] = C[1] * (s[0] * s23);
+      t[2] = C[2] * (s01 * s[3]);
+      t[3] = C[3] * (s01 * s[2]);
+    } else if constexpr (K == 3) {
       t[0] = C[0] * (s[1] * s[2]);
       t[1] = C[1] * (s[0] * s[2]);
       t[2] = C[2] * (s[0] * s[1]);
@@ -376,9 +408,58 @@ __device__ __forceinline__ void raw_weights(const T* b, const T* C, T* w) {
   }
 }
 
+// Indicators of the r = 4 candidates (WENOIU7): the quadratic form, in the three consecutive
+// differences (d1, d2, d3) of a candidate's values, of the integral over [x_{j-1/2}, x_{j+1/2}]
+// of the squared first to third derivatives of its interpolating cubic (times h, h^3, h^5),
+// the definition that gives Eq. (3.22) for r = 3.  Rows (a11, a22, a33, 2 a12, 2 a13,
+// 2 a23) / 2880 per candidate k = 0..3.
+__host__ __device__ constexpr double is4c(int k, int i) {
+  constexpr double A[4][6] = {{6649, 45076, 25729, -33916, 22778, -63436},
+                              {3169, 17236, 6649, -13036, 5978, -17116},
+                              {6649, 17236, 3169, -17116, 5978, -13036},
+                              {25729, 45076, 6649, -63436, 22778, -33916}};
+  return A[k][i] / 2880.0;
+}
+template <typename T>
+__device__ __forceinline__ T is_b4(int k, T d1, T d2, T d3, T eps) {
+  return eps + d1 * (T(is4c(k, 0)) * d1 + T(is4c(k, 3)) * d2 + T(is4c(k, 4)) * d3) +
+         d2 * (T(is4c(k, 1)) * d2 + T(is4c(k, 5)) * d3) + T(is4c(k, 2)) * d3 * d3;
+}
+
 template <int R, typename T>
 __device__ __forceinline__ T weno_delta(const T* u, T eps, int ppm, int linw) {
-  if constexpr (R == 3) {
+  if constexpr (R == 4) {
+    // Table A1 candidates relative to w_j, u[m+3] = w_{j+m} - w_j (u[3] is not read)
+    const T p[4] = {T(-5.0 / 16) * u[0] + T(21.0 / 16) * u[1] - T(35.0 / 16) * u[2],
+                    T(1.0 / 16) * u[1] - T(5.0 / 16) * u[2] + T(5.0 / 16) * u[4],
+                    T(-1.0 / 16) * u[2] + T(9.0 / 16) * u[4] - T(1.0 / 16) * u[5],
+                    T(15.0 / 16) * u[4] - T(5.0 / 16) * u[5] + T(1.0 / 16) * u[6]};
+    const T C[4] = {T(1.0 / 64), T(21.0 / 64), T(35.0 / 64), T(7.0 / 64)};
+    if (linw) return C[0] * p[0] + C[1] * p[1] + C[2] * p[2] + C[3] * p[3];
+    const T D[6] = {u[1] - u[0], u[2] - u[1], -u[2], u[4], u[5] - u[4], u[6] - u[5]};
+    T b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b[k] = is_b4(k, D[k], D[k + 1], D[k + 2], eps);
+    T w[4];
+    raw_weights<T, 4>(b, C, w);
+    if (ppm) {
+      // fourth-order mapping of the Appendix: g = C - (w - C)^4 / C^3 (w <= C),
+      // C - (w - C)^4 / (C - 1)^3 (w > C)
+      constexpr double c4[4] = {1.0 / 64, 21.0 / 64, 35.0 / 64, 7.0 / 64};
+      T num = T(0), den = T(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const T q = w[k] - C[k], q2 = q * q;
+        const T K = nonpos(q) ? T(1.0 / (c4[k] * c4[k] * c4[k]))
+                              : T(1.0 / ((c4[k] - 1.0) * (c4[k] - 1.0) * (c4[k] - 1.0)));
+        const T g = C[k] - q2 * q2 * K;
+        num += g * p[k];
+        den += g;
+      }
+      return quot(num, den);
+    }
+    return w[0] * p[0] + w[1] * p[1] + w[2] * p[2] + w[3] * p[3];
+  } else if constexpr (R == 3) {
     // candidates of Table 1 relative to w_j
     const T p0 = T(0.375) * u[0] - T(1.25) * u[1];
     const T p1 = T(-0.125) * u[1] + T(0.375) * u[3];
@@ -471,7 +552,46 @@ __device__ __forceinline__ void raw_weights2(const float2* b, const float* C, fl
 template <int R>
 __device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int ppm, int linw) {
   const float2 eps = bc2(eps_);
-  if constexpr (R == 3) {
+  if constexpr (R == 4) {
+    const float2 p[4] = {
+        fma2(bc2(-5.0f / 16), u[0], fma2(bc2(21.0f / 16), u[1], mul2(bc2(-35.0f / 16), u[2]))),
+        fma2(bc2(1.0f / 16), u[1], fma2(bc2(-5.0f / 16), u[2], mul2(bc2(5.0f / 16), u[4]))),
+        fma2(bc2(-1.0f / 16), u[2], fma2(bc2(9.0f / 16), u[4], mul2(bc2(-1.0f / 16), u[5]))),
+        fma2(bc2(15.0f / 16), u[4], fma2(bc2(-5.0f / 16), u[5], mul2(bc2(1.0f / 16), u[6])))};
+    const float C[4] = {1.0f / 64, 21.0f / 64, 35.0f / 64, 7.0f / 64};
+    if (linw)
+      return fma2(bc2(C[0]), p[0], fma2(bc2(C[1]), p[1], fma2(bc2(C[2]), p[2], mul2(bc2(C[3]), p[3]))));
+    const float2 m1 = bc2(-1.0f);
+    const float2 D[6] = {fma2(u[0], m1, u[1]), fma2(u[1], m1, u[2]), mul2(u[2], m1), u[4], fma2(u[4], m1, u[5]),
+                         fma2(u[5], m1, u[6])};
+    float2 b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 d1 = D[k], d2 = D[k + 1], d3 = D[k + 2];
+      const float2 r1 = fma2(bc2((float)is4c(k, 0)), d1, fma2(bc2((float)is4c(k, 3)), d2, mul2(bc2((float)is4c(k, 4)), d3)));
+      const float2 r2 = fma2(bc2((float)is4c(k, 1)), d2, mul2(bc2((float)is4c(k, 5)), d3));
+      b[k] = fma2(d1, r1, fma2(d2, r2, fma2(mul2(bc2((float)is4c(k, 2)), d3), d3, eps)));
+    }
+    float2 w[4];
+    raw_weights2<4>(b, C, w);
+    if (ppm) {
+      // g = C - (w - C)^4 / C^3 (w <= C), C - (w - C)^4 / (C - 1)^3 (w > C)
+      constexpr float K0[4] = {262144.0f, 262144.0f / 9261, 262144.0f / 42875, 262144.0f / 343};
+      constexpr float K1[4] = {-262144.0f / 250047, -262144.0f / 79507, -262144.0f / 24389, -262144.0f / 185193};
+      float2 num, den;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 q = add2(w[k], bc2(-C[k]));
+        const float2 q2 = mul2(q, q);
+        const float2 K = make_float2(nonpos(q.x) ? -K0[k] : -K1[k], nonpos(q.y) ? -K0[k] : -K1[k]);
+        const float2 g = fma2(mul2(q2, q2), K, bc2(C[k]));
+        num = k == 0 ? mul2(g, p[0]) : fma2(g, p[k], num);
+        den = k == 0 ? g : add2(den, g);
+      }
+      return quot2(num, den);
+    }
+    return fma2(w[0], p[0], fma2(w[1], p[1], fma2(w[2], p[2], mul2(w[3], p[3]))));
+  } else if constexpr (R == 3) {
     const float2 p[3] = {fma2(bc2(0.375f), u[0], mul2(bc2(-1.25f), u[1])),
                          fma2(bc2(-0.125f), u[1], mul2(bc2(0.375f), u[3])),
                          fma2(bc2(0.75f), u[3], mul2(bc2(-0.125f), u[4]))};

@@ -49,13 +49,18 @@ __device__ __forceinline__ void coord(const CoordParams& C, int i, int j, double
     }
 }
 
-// Central derivative of x and y along one direction from 9 nodal values f[k] = f_{j+k-4}.
-__device__ __forceinline__ double central_diff(const Central& c, int interp, bool sixth,
-                                               const double* f) {
+// Central derivative of x and y along one direction from 9 nodal values f[k] = f_{j+k-4};
+// pts = points of the midpoint interpolation (4, 6, or 8 for WENOIU7).
+__device__ __forceinline__ double central_diff(const Central& c, int interp, int pts, const double* f) {
+  double d = c.a1 * (f[5] - f[3]) + c.a2 * (f[6] - f[2]) + c.a3 * (f[7] - f[1]) + c.a4 * (f[8] - f[0]);
+  if (pts == 8) {
+    // midpoint j + m + 1/2 uses f_{j+m-3} .. f_{j+m+4} = f[m+1 .. m+8]
+    return d + c.b12 * (mid_interp8(interp, f + 1) - mid_interp8(interp, f + 0));
+  }
   // midpoint j + m + 1/2 uses f_{j+m-2} .. f_{j+m+3} = f[m+2 .. m+7]
+  const bool sixth = pts == 6;
   const double mp0 = mid_interp(interp, sixth, f + 2);   // j + 1/2
   const double mm0 = mid_interp(interp, sixth, f + 1);   // j - 1/2
-  double d = c.a1 * (f[5] - f[3]) + c.a2 * (f[6] - f[2]) + c.a3 * (f[7] - f[1]);
   d += c.b12 * (mp0 - mm0);
   if (c.b32 != 0.0) {
     const double mp1 = mid_interp(interp, sixth, f + 3); // j + 3/2
@@ -65,7 +70,10 @@ __device__ __forceinline__ double central_diff(const Central& c, int interp, boo
   return d;
 }
 
-__global__ void metrics_kernel(CoordParams C, Central cen, int interp, int sixth, double* __restrict__ M) {
+// Points of the midpoint interpolation of a scheme.
+inline int interp_points(int scheme) { return scheme == S71 ? 8 : scheme >= S51 ? 6 : 4; }
+
+__global__ void metrics_kernel(CoordParams C, Central cen, int interp, int pts, double* __restrict__ M) {
   const int W = C.ni + 2 * G, H = C.nj + 2 * G;
   const long long plane = (long long)W * H;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
@@ -77,10 +85,10 @@ __global__ void metrics_kernel(CoordParams C, Central cen, int interp, int sixth
       coord(C, i + k - 4, j, fx[k], fy[k]);   // along xi
       coord(C, i, j + k - 4, gx[k], gy[k]);   // along eta
     }
-    const double x_xi = central_diff(cen, interp, sixth, fx);
-    const double y_xi = central_diff(cen, interp, sixth, fy);
-    const double x_eta = central_diff(cen, interp, sixth, gx);
-    const double y_eta = central_diff(cen, interp, sixth, gy);
+    const double x_xi = central_diff(cen, interp, pts, fx);
+    const double y_xi = central_diff(cen, interp, pts, fy);
+    const double x_eta = central_diff(cen, interp, pts, gx);
+    const double y_eta = central_diff(cen, interp, pts, gy);
     M[0 * plane + t] = y_eta;
     M[1 * plane + t] = -x_eta;
     M[2 * plane + t] = -y_xi;
@@ -101,8 +109,7 @@ cudaError_t launch_metrics(const fsp_config& cfg, const fsp_block& blk, const do
   const int threads = 256;
   const long long blocks = (n + threads - 1) / threads;
   const int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
-  metrics_kernel<<<grid, threads, 0, st>>>(C, central_of(cfg.scheme), cfg.interp,
-                                           cfg.scheme >= S51 ? 1 : 0, M);
+  metrics_kernel<<<grid, threads, 0, st>>>(C, central_of(cfg.scheme), cfg.interp, interp_points(cfg.scheme), M);
   return cudaGetLastError();
 }
 

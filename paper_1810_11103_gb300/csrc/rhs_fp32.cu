@@ -19,7 +19,8 @@ static cudaError_t rhs_f32(int scheme, const Params& P, const void* Q, const dou
     case S31: return rhs_passes<S31, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
     case S32: return rhs_passes<S32, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
     case S51: return rhs_passes<S51, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
-    default:  return rhs_passes<S52, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
+    case S52: return rhs_passes<S52, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
+    default:  return rhs_passes<S71, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
   }
 }
 
@@ -39,7 +40,8 @@ static cudaError_t fd_f32(int scheme, const Params& P, const void* Q, const doub
     case S31: return flux_difference_passes<S31, float, Acc>(P, q, lam, dir, mode, a, out, st);
     case S32: return flux_difference_passes<S32, float, Acc>(P, q, lam, dir, mode, a, out, st);
     case S51: return flux_difference_passes<S51, float, Acc>(P, q, lam, dir, mode, a, out, st);
-    default:  return flux_difference_passes<S52, float, Acc>(P, q, lam, dir, mode, a, out, st);
+    case S52: return flux_difference_passes<S52, float, Acc>(P, q, lam, dir, mode, a, out, st);
+    default:  return flux_difference_passes<S71, float, Acc>(P, q, lam, dir, mode, a, out, st);
   }
 }
 

@@ -289,11 +289,13 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
     E.build(w, nx, ny);
     Real qc[4];
     ld4(st.q, st.n, oc, qc);
-    // state differences to the centre at the stencil offsets -2, -1, +1, +2
-    Real dq[4][4];
+    // state differences to the centre at the stencil offsets -H..-1, +1..+H (H = 2, or 3
+    // for r = 4); the "-" side reads the mirrored nodes
+    constexpr int H = Sc::r == 4 ? 3 : 2, NA = 2 * H;
+    Real dq[NA][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int m = a < 2 ? a - 2 : a - 1;
+    for (int a = 0; a < NA; ++a) {
+      const int m = a < H ? a - H : a - H + 1;
       if (Sc::r == 2 && m == 2) { dq[a][0] = dq[a][1] = dq[a][2] = dq[a][3] = Real(0); continue; }
       Real t[4];
       ld4(st.q, st.n, at(side == 0 ? m : 1 - m), t);
@@ -305,14 +307,14 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
       // components (0, 1) and (2, 3) in the two lanes of packed float arithmetic
 #pragma unroll
       for (int kp = 0; kp < 2; ++kp) {
-        float2 u[5];
+        float2 u[NA + 1];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          if (Sc::r == 2 && a == 3) { u[4] = make_float2(0.f, 0.f); continue; }
-          u[a < 2 ? a : a + 1] = make_float2(E.project(2 * kp, dq[a][0], dq[a][1], dq[a][2], dq[a][3]),
+        for (int a = 0; a < NA; ++a) {
+          if (Sc::r == 2 && a == NA - 1) { u[NA] = make_float2(0.f, 0.f); continue; }
+          u[a < H ? a : a + 1] = make_float2(E.project(2 * kp, dq[a][0], dq[a][1], dq[a][2], dq[a][3]),
                                              E.project(2 * kp + 1, dq[a][0], dq[a][1], dq[a][2], dq[a][3]));
         }
-        u[2] = make_float2(0.f, 0.f);
+        u[H] = make_float2(0.f, 0.f);
         const float2 W2 = weno_delta_x2<Sc::r>(u, eps, ppm, linw);
         Wm[2 * kp] = W2.x;
         Wm[2 * kp + 1] = W2.y;
@@ -320,12 +322,13 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
     } else {
 #pragma unroll
       for (int kc = 0; kc < 4; ++kc) {
-        Real u[5];
-        u[0] = E.project(kc, dq[0][0], dq[0][1], dq[0][2], dq[0][3]);
-        u[1] = E.project(kc, dq[1][0], dq[1][1], dq[1][2], dq[1][3]);
-        u[2] = Real(0);
-        u[3] = E.project(kc, dq[2][0], dq[2][1], dq[2][2], dq[2][3]);
-        u[4] = Sc::r == 3 ? E.project(kc, dq[3][0], dq[3][1], dq[3][2], dq[3][3]) : Real(0);
+        Real u[NA + 1];
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+          u[a < H ? a : a + 1] = (Sc::r == 2 && a == NA - 1)
+                                     ? Real(0)
+                                     : E.project(kc, dq[a][0], dq[a][1], dq[a][2], dq[a][3]);
+        u[H] = Real(0);
         Wm[kc] = weno_delta<Sc::r, Real>(u, eps, ppm, linw);
       }
     }
@@ -335,11 +338,20 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
     for (int v = 0; v < 4; ++v) Qs[side][v] = qc[v] + dQm[v];
   }
 
-  Acc vx[6], vy[6];
+  Acc mmx, mmy;
+  if constexpr (Sc::r == 4) {
+    Acc vx[8], vy[8];
 #pragma unroll
-  for (int kk = 0; kk < 6; ++kk) ld2(st.ma, at(kk - 2), vx[kk], vy[kk]);
-  const Acc mmx = mid_interp(interp, Sc::r == 3, vx);
-  const Acc mmy = mid_interp(interp, Sc::r == 3, vy);
+    for (int kk = 0; kk < 8; ++kk) ld2(st.ma, at(kk - 3), vx[kk], vy[kk]);
+    mmx = mid_interp8(interp, vx);
+    mmy = mid_interp8(interp, vy);
+  } else {
+    Acc vx[6], vy[6];
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk) ld2(st.ma, at(kk - 2), vx[kk], vy[kk]);
+    mmx = mid_interp(interp, Sc::r == 3, vx);
+    mmy = mid_interp(interp, Sc::r == 3, vy);
+  }
   if constexpr (Staged<Real, Acc>::SPLIT) {
     // Cartesian fluxes of Q+ and Q- in float
     Real ex[2][4], ey[2][4];
@@ -385,9 +397,9 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
   }
 }
 
-// h+ coefficient n_k of the node flux f+_{p+k}, k = -2..2 (0 outside)
+// h+ coefficient n_k of the node flux f+_{p+k} (0 outside the scheme's stencil)
 template <int S>
-__host__ __device__ constexpr double hnode(int k) { return k < -2 || k > 2 ? 0.0 : Scheme<S>::n(k + 2); }
+__host__ __device__ constexpr double hnode(int k) { return Scheme<S>::hn(k); }
 
 // h = h+ + h- at p + 1/2 (Eqs. 3.4, 3.8, 3.16, 3.20; h- the mirror of h+), the midpoint
 // terms m0 (f+_{p+1/2} + f-_{p+1/2}) + m1 (f+_{p-1/2} + f-_{p+3/2}) plus the node terms
@@ -418,7 +430,7 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
       }
     }
 #pragma unroll
-    for (int d = 0; d <= 2; ++d) {
+    for (int d = 0; d <= 3; ++d) {
       const double ce = 0.5 * (hnode<S>(-d) + hnode<S>(1 + d)), cq = hnode<S>(-d) - hnode<S>(1 + d);
       if (ce == 0.0 && cq == 0.0) continue;
       Acc a[4], b[4];
@@ -443,13 +455,13 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
       else h[v] = Acc(Sc::m0) * (c.f[0][v] + c.f[1][v]) + Acc(Sc::m1) * (lo.f[0][v] + hi.f[1][v]);
     }
 #pragma unroll
-    for (int kk = -2; kk <= 2; ++kk) {
-      if (Sc::n(kk + 2) == 0.0) continue;
+    for (int kk = -3; kk <= 3; ++kk) {
+      if (Sc::hn(kk) == 0.0) continue;
       Acc a[4], b[4];
       ld4(st.fp, st.n, at(kk), a);
       ld4(st.fm, st.n, at(1 - kk), b);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) h[v] += Acc(Sc::n(kk + 2)) * (a[v] + b[v]);
+      for (int v = 0; v < 4; ++v) h[v] += Acc(Sc::hn(kk)) * (a[v] + b[v]);
     }
   }
 }
@@ -574,7 +586,8 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const int pi = DIR == 0 ? k % W : k / NL;
     const int line = line0 + l;
     const int p = PLO + pi;
-    if (line >= nlines || base + p > n) continue;
+    // one-midpoint schemes use interfaces -1 .. T-1 (the last slot is spare)
+    if (line >= nlines || base + p > n || (Sc::nmp == 1 && p > T - 1)) continue;
     const int c0 = p + 4;  // staged position of node p
     auto at = [&](int m) { return SI(l, c0 + m); };
     Mid<Real, Acc> mo;
@@ -656,8 +669,9 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
 //   h           (two-midpoint schemes) at q - 1, from the midpoint ring
 //   outputs     node s = the interface just completed, H_s - H_{s-1} from the h ring
 // with K = 3 (one midpoint) or 2 (two midpoints), so that every stencil node of a step's
-// interfaces is in the ring; a start-up pass stages the six nodes before s0 + K.  The ring
-// holds the 38 nodes a step reads; the warp synchronises between the phases only.
+// interfaces is in the ring; a start-up pass stages the nodes s0 - NMP - H .. s0 + K - 1
+// (H = 2, or 3 for WENOIU7).  The ring holds the 39 nodes a step reads at most; the warp
+// synchronises between the phases only.
 // --------------------------------------------------------------------------------------
 template <int S, int MODE, typename Real, typename Acc>
 __device__ __forceinline__ void march_row(const Params& P, const Real* __restrict__ Q, const Real* const* qtab,
@@ -667,6 +681,7 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
   using Ms = MarchShape<S, Real, Acc>;
   constexpr int NMP = Scheme<S>::nmp;
   constexpr int K = NMP == 1 ? 3 : 2;
+  constexpr int H = Scheme<S>::r == 4 ? 3 : 2;     // stencil half-width of the interpolation
   const int L = threadIdx.x & 31;
   Staged<Real, Acc> st;
   st.carve(wsm, RING);
@@ -717,7 +732,7 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
   };
 
   // start-up: the six nodes s0 + K - 6 .. s0 + K - 1, and the first step's nodes in flight
-  if (L < 6) stage_node(s0 + K - 6 + L, false);
+  if (L < K + NMP + H) stage_node(s0 - NMP - H + L, false);
   bool staged = prefetch(s0 + K + L);
   cp_async_commit();
   const int steps = (s1 - s0 + 2 * NMP - 1 + 31) / 32;   // until the output s1 - 1
@@ -796,13 +811,14 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
 // Marching eta pass.  A CTA of EW warps owns 32 adjacent columns (one per lane) and a row
 // segment [s0, s1) of one block; it walks the segment EW rows per step, warp w taking row
 // r + w of the step starting at row r.  Per step (1MP / 2MP):
-//   nodes       m = r + 2 + w into the ring (row slot m mod ERING), state, metrics and the
+//   nodes       m = r + K + w (K = 2, 3 for WENOIU7) into the ring (row slot m mod ERING),
+//               state, metrics and the
 //               epilogue operands of the next step staged by cp.async during this step
 //   interfaces  q = r - NMP + w: midpoint fluxes, h (1MP) or the midpoint record (2MP)
 //   h           (2MP) at q - 1 from the records of q - 2 .. q
 //   outputs     node s = the interface just completed
 // with a block barrier after each phase that hands data to other warps.  The ring holds the
-// 14 rows a step reads and the 8 it stages; the start-up stages the rows below r + 2.
+// at most 15 rows a step reads or stages; the start-up stages the rows below r + K.
 // --------------------------------------------------------------------------------------
 constexpr int EW = 8;                               // warps (rows per step) of a marching eta CTA
 constexpr int ERING = 16;                           // row slots of its ring
@@ -830,7 +846,8 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
                                           double dt, int c0, int s0, int s1, unsigned char* sm) {
   using Ms = MarchEtaShape<S, Real, Acc>;
   constexpr int NMP = Scheme<S>::nmp;
-  constexpr int K = 2;
+  constexpr int H = Scheme<S>::r == 4 ? 3 : 2;     // stencil half-width of the interpolation
+  constexpr int K = H == 3 ? 3 : 2;                 // rows staged ahead of the step's first row
   const int L = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
   const int col = c0 + L;
   const bool on = col < P.ni;
@@ -900,7 +917,7 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
   };
   const int lag = NMP == 1 ? 1 : 3;                       // output s = r - lag + w
   // start-up: rows s0 - 2 - NMP .. s0 + K - 1
-  if (w < K + 2 + NMP) stage_node(s0 - 2 - NMP + w, false);
+  if (w < K + NMP + H) stage_node(s0 - NMP - H + w, false);
   bool staged = prefetch(s0 + K + w, s0 - lag + w);
   cp_async_commit();
   const int steps = (s1 - s0 + 2 * NMP - 1 + EW - 1) / EW;
@@ -1226,7 +1243,8 @@ cudaError_t batch_dispatch(int scheme, int mode, const PassTables& xi, int ntx, 
     case S31: return batch_scheme<S31, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
     case S32: return batch_scheme<S32, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
     case S51: return batch_scheme<S51, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
-    default:  return batch_scheme<S52, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
+    case S52: return batch_scheme<S52, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
+    default:  return batch_scheme<S71, Real, Acc>(mode, xi, ntx, vx, eta, nte, ve, ca, cb, dt, st);
   }
 }
 
@@ -1243,7 +1261,9 @@ cudaError_t batch_one_direction(int scheme, int dir, const PassTables& t, int nt
     case 4: return launch_sweep_batch<S51, 0, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
     case 5: return launch_sweep_batch<S51, 1, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
     case 6: return launch_sweep_batch<S52, 0, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
-    default: return launch_sweep_batch<S52, 1, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    case 7: return launch_sweep_batch<S52, 1, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    case 8: return launch_sweep_batch<S71, 0, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
+    default: return launch_sweep_batch<S71, 1, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
   }
 }
 // Batch passes (shape variants vx, ve for the xi and eta tiles): FP64 in batch_fp64.cu;

@@ -86,6 +86,12 @@ def test_argument_validation_on_the_host(so):
     c32 = fsp.Config(scheme=2, bc=(0, 0, 0, 0), precision=1)
     assert fsp.lib().fsp_vjp_workspace_size(ctypes.byref(c32._c()), ctypes.byref(b), ctypes.byref(n)) == 2
     assert fsp.lib().fsp_rk3_tape_size(ctypes.byref(c32._c()), ctypes.byref(b), ctypes.byref(n)) == 2
+    # ... and does not cover WENOIU7-1MP, whose forward right-hand side is accepted
+    c7 = fsp.Config(scheme=4, bc=(0, 0, 0, 0))
+    assert _ws_code(fsp, c7, 16, 16) == 0
+    assert fsp.lib().fsp_vjp_workspace_size(ctypes.byref(c7._c()), ctypes.byref(b), ctypes.byref(n)) == 2
+    assert fsp.lib().fsp_rk3_tape_size(ctypes.byref(c7._c()), ctypes.byref(b), ctypes.byref(n)) == 2
+    assert _ws_code(fsp, fsp.Config(scheme=5, bc=(0, 0, 0, 0)), 16, 16) == 1
     # null and host pointers are refused
     assert fsp.lib().fsp_rhs(ctypes.byref(per._c()), ctypes.byref(b), None, None, None, None, 0, None) == 1
     host = (ctypes.c_double * 4096)()

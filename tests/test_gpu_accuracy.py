@@ -76,7 +76,7 @@ def test_sod_final_time(F):
             assert np.abs(q_s[0, 0] - ex).mean() < 5e-3
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_vortex_one_period(F, scheme):
     x, y, per = I.periodic_square(48, 10.0, 0.2, seed=1810)
     q = I.isentropic_vortex(x, y, (5.0, 5.0), strength=5.0, free=(1.0, 1.0, 1.0, 1.0), period=(10.0, 10.0))

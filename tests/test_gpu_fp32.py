@@ -44,7 +44,7 @@ def _run(F, cfgd, x, y, q, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_fp32_rhs_vortex_256(F, prec, scheme):
     x, y, per = I.periodic_square(256, 10.0, 0.2, seed=1810)
     q = I.isentropic_vortex(x, y, (5.0, 5.0), strength=5.0, free=(1.0, 1.0, 1.0, 1.0), period=(10.0, 10.0))
@@ -64,7 +64,7 @@ def test_fp32_rhs_riemann_and_boundaries(F, prec):
 def test_free_stream_fp32_paths(F):
     x, y, per = I.periodic_square(256, 10.0, 0.2, seed=1810)
     q0 = np.array([1.0, 1.0, 1.0, 1.0 / (GAMMA - 1) + 1.0])
-    for scheme in range(4):
+    for scheme in range(5):
         cfgd = dict(scheme=scheme, period=per)
         r64 = O.fsp_residual(cfgd, x, y, q0)
         for prec in (1, 2):

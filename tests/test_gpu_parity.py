@@ -89,13 +89,13 @@ def _check_case(F, cfgd, x, y, q, tol=TOL_RHS):
     return err
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_rhs_parity_vortex_256(F, scheme):
     x, y, per, q = _vortex256()
     _check_case(F, _cfg(scheme=scheme, period=per), x, y, q)
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_rhs_parity_ragged_tiles(F, scheme):
     x, y, per, q = _ragged()
     _check_case(F, _cfg(scheme=scheme, period=per), x, y, q)
@@ -109,7 +109,7 @@ def test_rhs_parity_options(F, variant):
         _check_case(F, _cfg(scheme=scheme, period=per, **variant), x, y, q)
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_rhs_parity_transmissive_riemann(F, scheme):
     x, y, per, q = _riemann()
     _check_case(F, _cfg(scheme=scheme, bc=(1, 1, 1, 1)), x, y, q)
@@ -157,7 +157,7 @@ def test_line_lambda_and_cfl_parity(F):
     assert dt_g == pytest.approx(O.cfl_dt(cfgd, M, q, 0.5), rel=1e-14)
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_rk3_parity(F, scheme):
     x, y, per, q = _ragged(96, 40, seed=6)
     cfgd = _cfg(scheme=scheme, period=per)
@@ -177,7 +177,7 @@ def test_rk3_parity(F, scheme):
 def test_free_stream_residual_on_gpu(F):
     x, y, per = I.periodic_square(256, 10.0, 0.2, seed=1810)
     q0 = np.array([1.0, 1.0, 1.0, 1.0 / (GAMMA - 1) + 1.0])
-    for scheme in range(4):
+    for scheme in range(5):
         cfgd = _cfg(scheme=scheme, period=per)
         cfg = F.Config.from_dict(cfgd)
         Mg = F.metrics(cfg, _dev(x), _dev(y))
