@@ -1007,11 +1007,12 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
 }
 
 // Resident CTAs per SM the kernels are compiled for (register budget): FP64 2, FP32 4, mixed 3
-// for the 256-thread tiles; FP64 3, FP32 7, mixed 5 for the 128-thread marching CTAs.
+// for the 256-thread tiles; FP64 3, FP32 6, mixed 5 for the 128-thread marching xi CTAs (six
+// rather than seven FP32 CTAs: 80 registers without spills measured 3 % faster).
 template <typename Real, typename Acc>
 constexpr int tile_ctas() { return sizeof(Real) == 8 ? 2 : std::is_same<Real, Acc>::value ? 4 : 3; }
 template <typename Real, typename Acc>
-constexpr int march_ctas() { return sizeof(Real) == 8 ? 3 : std::is_same<Real, Acc>::value ? 7 : 5; }
+constexpr int march_ctas() { return sizeof(Real) == 8 ? 3 : std::is_same<Real, Acc>::value ? 6 : 5; }
 
 template <int S, int DIR, int MODE, typename Real, typename Acc>
 __global__ void __launch_bounds__(256, tile_ctas<Real, Acc>())
@@ -1077,8 +1078,10 @@ march_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
 
 // Marching eta pass of many blocks: CTA b takes the 32 columns from 32 by of block
 // tiles[b].block, row segment bx (bx along the lines, by across them, as for the tiles).
+// Register budget: two 256-thread CTAs per SM for the float paths (128 registers measured
+// faster than three CTAs at 80), one for FP64.
 template <typename Real, typename Acc>
-constexpr int march_eta_ctas() { return sizeof(Real) == 8 ? 1 : std::is_same<Real, Acc>::value ? 3 : 2; }
+constexpr int march_eta_ctas() { return sizeof(Real) == 8 ? 1 : 2; }
 
 template <int S, int MODE, typename Real, typename Acc>
 __global__ void __launch_bounds__(32 * EW, march_eta_ctas<Real, Acc>())
