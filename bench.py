@@ -55,6 +55,9 @@ def parse():
                     help="also measure the other two precisions and report them beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint cost measurement")
+    ap.add_argument("--seventh", action=argparse.BooleanOptionalAction, default=True,
+                    help="also measure WENOIU7-1MP (the Appendix's seventh-order scheme) on the same workload, "
+                         "FP64 and FP32")
     ap.add_argument("--accuracy", choices=["none", "quick", "full"], default="quick",
                     help="final-time errors per precision: quick = the 256 x 256 vortex over one period and "
                          "the free-stream residual; full adds the 1024 x 1024 Riemann problem to t = 0.3")
@@ -742,6 +745,16 @@ def main():
     # the adjoint covers the third- and fifth-order schemes
     adjoint = None if args.no_adjoint or args.scheme == 4 else measure_adjoint(args, C)
     accuracy = None if args.accuracy == "none" else measure_accuracy(args, C, full=args.accuracy == "full")
+    seventh = None
+    if args.seventh and args.scheme != 4 and args.workload == "cylinder64":
+        a7 = argparse.Namespace(**dict(vars(args), scheme=4, steps=max(3, args.steps // 4)))
+        seventh = {"scheme": SCHEME_NAMES[4]}
+        for p in ("fp64", "fp32"):
+            r = measure_cylinder(a7, p, C)
+            seventh[p] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                          "roofline": {k: r["roofline"][k] for k in ("kernel", "achieved", "peak", "unit", "frac",
+                                                                   "flops_per_node", "kernel_ms")},
+                          "tiles": r["tiles"]}
     if rank == 0:
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
@@ -766,6 +779,8 @@ def main():
             line["adjoint"] = adjoint
         if accuracy is not None:
             line["accuracy"] = accuracy
+        if seventh is not None:
+            line["wenoiu7"] = seventh
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)
