@@ -211,6 +211,17 @@ fsp_status fsp_norms(const fsp_block* blk, int precision, const void* A, const v
                      double* out, void* stream);
 
 /*
+ * fsp_check_state -- failure detection (the paper has no counterpart): *first_bad (one device
+ * int64, written asynchronously on `stream`) receives the smallest linear index j ni + i of a
+ * node whose state Q (state layout, cfg->precision) is not finite or not physical (rho <= 0 or
+ * p <= 0, p = (gamma - 1)(E - |rho u|^2 / (2 rho))), or -1 when every node is valid.  The
+ * caller reads it after the stream and maps a non-negative value to FSP_ERR_NONFINITE.
+ * Argument errors: FSP_ERR_INVALID_ARG before anything is enqueued.
+ */
+fsp_status fsp_check_state(const fsp_config* cfg, const fsp_block* blk, const void* Q, long long* first_bad,
+                           void* stream);
+
+/*
  * ---- Discrete adjoint (FP64) --------------------------------------------------------
  * Vector-Jacobian products of the right-hand side, of one RK3 step and of the metrics, for
  * gradients of a scalar functional with respect to the state and the grid coordinates.

@@ -222,6 +222,13 @@ fsp_status fsp_norms(const fsp_block* blk, int precision, const void* A, const v
   return cuda_status(launch_norms(*blk, precision, A, B, out, (cudaStream_t)stream));
 }
 
+fsp_status fsp_check_state(const fsp_config* cfg, const fsp_block* blk, const void* Q, long long* first_bad,
+                           void* stream) {
+  if (fsp_status s = check_cfg(cfg, blk)) return s;
+  if (!device_pointer(Q) || !device_pointer(first_bad)) return FSP_ERR_INVALID_ARG;
+  return cuda_status(launch_check_state(*blk, cfg->precision, cfg->gamma, Q, first_bad, (cudaStream_t)stream));
+}
+
 fsp_status fsp_fma_peak(int precision, int blocks, int iters, void* sink, void* stream) {
   if ((precision != FSP_FP64 && precision != FSP_FP32) || blocks < 1 || iters < 1)
     return FSP_ERR_INVALID_ARG;

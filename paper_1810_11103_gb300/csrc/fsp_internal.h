@@ -31,6 +31,8 @@ cudaError_t launch_flux_difference(int scheme, int precision, const Params& P, c
 
 cudaError_t launch_cfl_finish(const double* cfl_max, double cfl, double* dt_out, cudaStream_t st);
 
+cudaError_t launch_check_state(const fsp_block& blk, int precision, double gamma, const void* Q, long long* first,
+                               cudaStream_t st);
 cudaError_t launch_norms(const fsp_block& blk, int precision, const void* A, const void* B,
                          double* out, cudaStream_t st);
 

@@ -173,6 +173,38 @@ __global__ void norms_finish_kernel(double* acc, double n) {
   }
 }
 
+// State health: the smallest linear index j ni + i of a node whose state is not finite or not
+// physical (rho <= 0 or p <= 0), by an atomic minimum over the unsigned index (all-ones, which
+// reads -1 as a signed integer, when every node is valid).
+template <typename Real>
+__global__ void __launch_bounds__(256) check_state_kernel(int ni, int nj, long long ld, double gm1,
+                                                          const Real* __restrict__ Q,
+                                                          unsigned long long* __restrict__ first) {
+  const long long N = (long long)ni * nj, plane = (long long)nj * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    const long long o = (t / ni) * ld + t % ni;
+    const double r = Q[o], mu = Q[plane + o], mv = Q[2 * plane + o], e = Q[3 * plane + o];
+    const double p = gm1 * (e - 0.5 * (mu * mu + mv * mv) / r);
+    const bool ok = isfinite(r) && isfinite(mu) && isfinite(mv) && isfinite(e) && r > 0.0 && p > 0.0;
+    if (!ok) atomicMin(first, (unsigned long long)t);
+  }
+}
+
+cudaError_t launch_check_state(const fsp_block& blk, int precision, double gamma, const void* Q, long long* first,
+                               cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(first, 0xff, sizeof(long long), st);
+  if (e != cudaSuccess) return e;
+  const long long N = (long long)blk.ni * blk.nj;
+  const long long want = (N + 255) / 256;
+  const int grid = (int)(want < 152 * 4 ? want : 152 * 4);
+  auto f = reinterpret_cast<unsigned long long*>(first);
+  if (precision == FSP_FP64)
+    check_state_kernel<double><<<grid, 256, 0, st>>>(blk.ni, blk.nj, blk.ld, gamma - 1.0, static_cast<const double*>(Q), f);
+  else
+    check_state_kernel<float><<<grid, 256, 0, st>>>(blk.ni, blk.nj, blk.ld, gamma - 1.0, static_cast<const float*>(Q), f);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_norms(const fsp_block& blk, int precision, const void* A, const void* B,
                          double* out, cudaStream_t st) {
   // out doubles as the accumulator space, then is rewritten in place by one thread

@@ -113,6 +113,7 @@ def lib():
                 "fsp_rk3_step": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, ctypes.c_size_t, _P]),
                 "fsp_cfl_dt": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_norms": (ctypes.c_int, [B, ctypes.c_int, _P, _P, _P, _P]),
+                "fsp_check_state": (ctypes.c_int, [C, B, _P, _P, _P]),
                 "fsp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
                 "fsp_vjp_workspace_size": (ctypes.c_int, [C, B, ctypes.POINTER(ctypes.c_size_t)]),
                 "fsp_rhs_vjp": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -346,6 +347,26 @@ def norms(A: torch.Tensor, B: Optional[torch.Tensor] = None, out=None, stream=No
         out = torch.empty(8, dtype=torch.float64, device=A.device)
     _check("fsp_norms", lib().fsp_norms(ctypes.byref(b), prec, _ptr(A), _ptr(B), _ptr(out), _stream(stream)))
     return out
+
+
+def check_state(cfg: Config, Q: torch.Tensor, out=None, stream=None) -> int:
+    """Index j ni + i of the first node whose state is not finite or not physical, -1 if none
+    (fsp_check_state; waits for the stream).  raise_on_bad(): FspError with FSP_ERR_NONFINITE."""
+    b = block_of(cfg, Q)
+    if out is None:
+        out = torch.empty(1, dtype=torch.int64, device=Q.device)
+    _check("fsp_check_state", lib().fsp_check_state(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(Q), _ptr(out),
+                                                    _stream(stream)))
+    return int(out.item())
+
+
+def raise_on_bad(cfg: Config, Q: torch.Tensor, stream=None) -> None:
+    """FspError (status 4, non-finite value) naming the first bad node, if any."""
+    k = check_state(cfg, Q, stream=stream)
+    if k >= 0:
+        err = FspError("fsp_check_state", 4)
+        err.node = (k // Q.shape[2], k % Q.shape[2])
+        raise err
 
 
 def fma_peak(precision: int, blocks: int, iters: int, sink: torch.Tensor, stream=None):

@@ -92,6 +92,9 @@ def test_argument_validation_on_the_host(so):
     assert fsp.lib().fsp_vjp_workspace_size(ctypes.byref(c7._c()), ctypes.byref(b), ctypes.byref(n)) == 2
     assert fsp.lib().fsp_rk3_tape_size(ctypes.byref(c7._c()), ctypes.byref(b), ctypes.byref(n)) == 2
     assert _ws_code(fsp, fsp.Config(scheme=5, bc=(0, 0, 0, 0)), 16, 16) == 1
+    # the state check refuses a host pointer for its result
+    one = (ctypes.c_longlong * 1)()
+    assert fsp.lib().fsp_check_state(ctypes.byref(per._c()), ctypes.byref(b), None, one, None) == 1
     # null and host pointers are refused
     assert fsp.lib().fsp_rhs(ctypes.byref(per._c()), ctypes.byref(b), None, None, None, None, 0, None) == 1
     host = (ctypes.c_double * 4096)()
