@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--accuracy", choices=["none", "quick", "full"], default="quick",
                     help="final-time errors per precision: quick = the 256 x 256 vortex over one period and "
                          "the free-stream residual; full adds the 1024 x 1024 Riemann problem to t = 0.3")
+    ap.add_argument("--tune-table", default=None,
+                    help="text file of tile choices for fsp_batch_tune: a workload found there takes the "
+                         "stored variants without timing, otherwise the timed choice is appended (lets a "
+                         "run under a profiler launch the kernels an unprofiled run chose)")
     ap.add_argument("--profile-tiles", default="2,1",
                     help="profiling run: tile shape variants 'vx,ve' of the xi and eta passes (the tuner's "
                          "choice on this workload), set without timing")
@@ -104,8 +108,7 @@ def workload_config(args, nodes, nblocks):
 
 
 # the sources the batched sweep kernels (the roofline kernels) are built from
-SWEEP_SOURCES = ("sweep.cuh", "fsp_device.cuh", "fsp_internal.h", "batch.cu", "batch_fp64.cu", "batch_fp32.cu",
-                 "batch_mixed.cu")
+SWEEP_SOURCES = ("sweep.cuh", "fsp_device.cuh", "fsp_internal.h", "batch_fp64.cu", "batch_fp32.cu", "batch_mixed.cu")
 
 
 def source_hash():
@@ -350,7 +353,7 @@ def measure_cylinder(args, prec, C, per_block=False):
     bt = fsp.Batch(cfg, blocks, states, device=C.dev)
     bt.metrics()
     # tile shapes chosen by timing each variant's pass on this batch (fsp_batch_tune)
-    tiles = {d: dict(zip(("variant", "lines", "outputs_per_line"), t)) for d, t in zip(("xi", "eta"), bt.tune())}
+    tiles = {d: dict(zip(("variant", "lines", "outputs_per_line"), t)) for d, t in zip(("xi", "eta"), bt.tune(args.tune_table))}
     nodes = sum(b["x"].size for b in blocks)
     # a stable step: CFL 0.3 on the initial state, from the per-block CFL rate
     dts = []

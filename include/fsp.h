@@ -340,7 +340,9 @@ fsp_status fsp_batch_capture_graph(fsp_batch* b, double dt, void* stream);
  * xi variant 3 marches: each warp walks one row segment (rows longer than 512 nodes are cut
  * into equal segments) 32 nodes at a time, keeping the stencil nodes in a shared-memory
  * ring, with four rows per 128-thread CTA; fsp_batch_tile_shape reports 4 lines and 512
- * output nodes for it.  The eta pass has variants 0-2 only.
+ * output nodes for it.  eta variant 3 marches too: a CTA of eight warps owns 32 adjacent
+ * columns (one per lane) and walks a segment of them eight rows per step through a 16-row
+ * shared-memory ring; fsp_batch_tile_shape reports 32 lines and the segment length.
  * Results do not depend on the variant (each interface is computed the same way); the
  * speed does.  fsp_batch_tune picks, for each direction, the fastest variant on this
  * handle's blocks and bound state: it times five launches of each variant's pass (after two

@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(256) lambda_batch_kernel(const Params* __restr
 #pragma unroll
     for (int v = 0; v < 4; ++v) qq[v] = Q[v * plane + o];
     const Real g = from_f64<Real>(P.gamma);
-    sx = spectral_radius(qq, from_f64<Real>(met_at(P, 0, i, j)), from_f64<Real>(met_at(P, 1, i, j)), g);
-    se = spectral_radius(qq, from_f64<Real>(met_at(P, 2, i, j)), from_f64<Real>(met_at(P, 3, i, j)), g);
+    sx = spectral_radius(qq, from_f64_alu<Real>(met_at(P, 0, i, j)), from_f64_alu<Real>(met_at(P, 1, i, j)), g);
+    se = spectral_radius(qq, from_f64_alu<Real>(met_at(P, 2, i, j)), from_f64_alu<Real>(met_at(P, 3, i, j)), g);
   }
   Real rx = sx;
 #pragma unroll

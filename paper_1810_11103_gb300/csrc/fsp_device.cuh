@@ -200,6 +200,13 @@ __device__ __forceinline__ float from_f64_int(double d) {
   return __uint_as_float(sign | (((unsigned)e << 23) + m));   // a mantissa carry bumps the exponent
 }
 
+// A double rounded to the state type on the integer pipe (identity for double), for kernels
+// that convert several metrics per node and leave most issue slots free: there the narrow
+// FP64 pipe, which carries the hardware conversion, would be the bound.
+template <typename T> __device__ __forceinline__ T from_f64_alu(double d);
+template <> __device__ __forceinline__ double from_f64_alu<double>(double d) { return d; }
+template <> __device__ __forceinline__ float from_f64_alu<float>(double d) { return from_f64_int(d); }
+
 // x <= 0 from the sign and magnitude bits (integer compare, no floating-point pipe)
 __device__ __forceinline__ bool nonpos(double x) { return __double_as_longlong(x) <= 0LL; }
 __device__ __forceinline__ bool nonpos(float x) { return __float_as_int(x) <= 0; }
@@ -303,9 +310,9 @@ __device__ __forceinline__ void node_speeds(const Params& P, const Real* __restr
 #pragma unroll
   for (int v = 0; v < 4; ++v) q[v] = Q[v * plane + o];
   const Real g = from_f64<Real>(P.gamma);
-  sx = spectral_radius(q, from_f64<Real>(met_at(P, 0, i, j)), from_f64<Real>(met_at(P, 1, i, j)), g);
-  se = spectral_radius(q, from_f64<Real>(met_at(P, 2, i, j)), from_f64<Real>(met_at(P, 3, i, j)), g);
-  rate = (sx + se) * recip(from_f64<Real>(met_at(P, 4, i, j)));
+  sx = spectral_radius(q, from_f64_alu<Real>(met_at(P, 0, i, j)), from_f64_alu<Real>(met_at(P, 1, i, j)), g);
+  se = spectral_radius(q, from_f64_alu<Real>(met_at(P, 2, i, j)), from_f64_alu<Real>(met_at(P, 3, i, j)), g);
+  rate = (sx + se) * recip(from_f64_alu<Real>(met_at(P, 4, i, j)));
 }
 
 // --------------------------------------------------------------------------------------
