@@ -368,23 +368,20 @@ def measure_cylinder(args, prec, C, per_block=False):
     clocks.start()
     t_dev = C.timed(lambda: bt.rk3_step(dt), args.steps)
     clk = clocks.stop()
-    # end to end: every block's state from pinned host memory, the step, the states back
-    sdt = torch.float64 if prec == "fp64" else torch.float32
-    host_in = [torch.as_tensor(q, dtype=sdt).pin_memory() for q in states]
-    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    # end to end: every block's state from pinned host memory, the step, the states back (the
+    # batch keeps every block's state in one buffer, so one copy each way per step)
+    host_in = bt.Qflat.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
 
     def e2e():
-        for d, h in zip(bt.Q, host_in):
-            d.copy_(h, non_blocking=True)
+        bt.Qflat.copy_(host_in, non_blocking=True)
         bt.rk3_step(dt)
-        for h, d in zip(host_out, bt.Q):
-            h.copy_(d, non_blocking=True)
+        host_out.copy_(bt.Qflat, non_blocking=True)
     e2e()
     t_e2e = C.timed(e2e, args.steps)
-    state_bytes = sum(q.numel() * q.element_size() for q in bt.Q)
+    state_bytes = host_in.numel() * host_in.element_size()
     # the dominant kernel alone: the xi sweep of every block (one launch)
-    for d, h in zip(bt.Q, host_in):
-        d.copy_(h)
+    bt.Qflat.copy_(host_in)
     bt.rhs()
     D = [torch.empty(q.shape, dtype=torch.float32 if prec == "fp32" else torch.float64, device=C.dev) for q in bt.Q]
     bt.flux_difference(0, D)

@@ -382,7 +382,8 @@ class Batch:
     optional ``offsets`` (4 entries: None or (dx, dy)) and ``period``.  states: the
     initial (4, nj, ni) state of every block (copied to the device in the precision's
     dtype).  Device memory for coordinates, metrics and states is held here; the library
-    handle holds its own scratch."""
+    handle holds its own scratch.  ``Qflat`` is the one device buffer behind the states
+    ``Q[k]`` (views, each block padded to 128 elements), for whole-batch host copies."""
 
     def __init__(self, cfg: Config, blocks, states, device="cuda"):
         self.cfg = cfg
@@ -390,7 +391,20 @@ class Batch:
         dt = torch.float64 if cfg.precision == FP64 else torch.float32
         self.x = [torch.as_tensor(b["x"], dtype=torch.float64, device=device).contiguous() for b in blocks]
         self.y = [torch.as_tensor(b["y"], dtype=torch.float64, device=device).contiguous() for b in blocks]
-        self.Q = [torch.as_tensor(q, dtype=dt, device=device).contiguous() for q in states]
+        # every block's state in one allocation (Q[k] are views at 512-byte aligned offsets),
+        # so a host round trip of the whole batch is one copy each way
+        sizes = [4 * x.shape[0] * x.shape[1] for x in self.x]
+        offs, tot = [], 0
+        for sz in sizes:
+            offs.append(tot)
+            tot += (sz + 127) // 128 * 128
+        self.Qflat = torch.zeros(tot, dtype=dt, device=device)
+        self.Q = []
+        for k, q in enumerate(states):
+            nj, ni = self.x[k].shape
+            v = self.Qflat[offs[k]:offs[k] + sizes[k]].view(4, nj, ni)
+            v.copy_(torch.as_tensor(q, dtype=dt))
+            self.Q.append(v)
         self.M = [torch.empty((5, x.shape[0] + 2 * G, x.shape[1] + 2 * G), dtype=torch.float64, device=device)
                   for x in self.x]
         blk = (_Block * n)()

@@ -247,3 +247,25 @@ def test_batch_tune_table(F, tmp_path):
     torch.cuda.synchronize()
     assert _maxrel([q.cpu().numpy() for q in bt.Q], q1) < TOL
     bt.close()
+
+
+def test_batch_flat_state_round_trip(F):
+    """The states are views of one buffer: a whole-batch host copy in, one RK3 step, one copy
+    out gives the same states as the per-block tensors."""
+    blocks, states, free = _small_cylinder()
+    cfgd = _cfgd(free, 2)
+    bt = F.Batch(F.Config.from_dict(cfgd), blocks, _perturbed(states, 7, 0.01))
+    bt.metrics()
+    for k, q in enumerate(bt.Q):
+        assert q.data_ptr() % 512 == 0 and q.untyped_storage().data_ptr() == bt.Qflat.untyped_storage().data_ptr()
+    host = bt.Qflat.cpu().pin_memory()
+    bt.Qflat.zero_()
+    bt.Qflat.copy_(host, non_blocking=True)
+    bt.rk3_step(1e-3)
+    out = torch.empty_like(host).pin_memory()
+    out.copy_(bt.Qflat, non_blocking=True)
+    torch.cuda.synchronize()
+    for q in bt.Q:
+        off = (q.data_ptr() - bt.Qflat.data_ptr()) // q.element_size()
+        assert torch.equal(out[off:off + q.numel()].view(q.shape), q.cpu())
+        assert not torch.equal(q.cpu(), host[off:off + q.numel()].view(q.shape))   # the step changed it
