@@ -128,7 +128,9 @@ def algorithmic_flops(args):
     return d["schemes"][SCHEME_NAMES[args.scheme]]
 
 
-def traffic_of(args, prec):
+def traffic_of(args, prec, variant):
+    """DRAM bytes of one launch of the xi sweep in tile variant `variant`, from an ncu capture of
+    the current kernel sources (None if there is none)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -136,7 +138,8 @@ def traffic_of(args, prec):
         entries = json.load(f)
     for tr in entries if isinstance(entries, list) else [entries]:
         if (tr.get("source_hash") == source_hash() and tr.get("workload") == args.workload
-                and tr.get("scheme") == args.scheme and tr.get("precision") == prec):
+                and tr.get("scheme") == args.scheme and tr.get("precision") == prec
+                and tr.get("variant") == variant):
             return tr.get("bytes_per_launch")
     return None
 
@@ -395,7 +398,7 @@ def measure_cylinder(args, prec, C, per_block=False):
         + ", all 64 blocks (fsp_batch_flux_difference dir 0)"
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic_of(args, prec),
+            "traffic": traffic_of(args, prec, tiles["xi"]["variant"]),
             "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
             "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
             "kernel_ms": 1e3 * t_k}
@@ -502,7 +505,7 @@ def measure_vortex(args, prec, C):
         "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps, "nodes": nodes, "nblocks": 1,
         "e2e": {"value": rhs_total / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": sb, "d2h_bytes_per_step": sb},
         "roofline": {"bound": "alu", "kernel": "sweep_kernel xi (fsp_flux_difference dir 0)", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_of(args, prec),
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_of(args, prec, -1),
                      "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
                      "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
                      "kernel_ms": 1e3 * t_k},

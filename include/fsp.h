@@ -344,7 +344,8 @@ fsp_status fsp_batch_capture_graph(fsp_batch* b, double dt, void* stream);
  * columns (one per lane) and walks a segment of them eight rows per step through a 16-row
  * shared-memory ring; fsp_batch_tile_shape reports 32 lines and the segment length.
  * Results do not depend on the variant (each interface is computed the same way); the
- * speed does.  fsp_batch_tune picks, for each direction, the fastest variant on this
+ * speed does.  Tiles are launched longest first, so that blocks of different sizes end the
+ * pass with short tiles rather than a few long ones.  fsp_batch_tune picks, for each direction, the fastest variant on this
  * handle's blocks and bound state: it times five launches of each variant's pass (after two
  * untimed ones) with CUDA events on `stream` and waits for them.  With table_path non-null
  * it first looks up a key made of the device name and SM count, the scheme and arithmetic
