@@ -111,43 +111,64 @@ __global__ void metrics_mb_kernel(const CoordBlock* __restrict__ B, int b, Centr
 }
 
 // ---- line maxima of every block in one launch ------------------------------------------
+// Rows per thread of the line maxima: four in float (the kernel waits on memory, and four
+// independent rows keep more loads in flight), one in double (bound by the FP64 pipe's
+// square roots, where more resident warps hide their latency better).
+template <typename Real>
+constexpr int lam_rows() { return sizeof(Real) == 4 ? 4 : 1; }
+
 template <typename Real>
 __global__ void __launch_bounds__(256) lambda_batch_kernel(const Params* __restrict__ Ps,
                                                            const TileRef* __restrict__ tiles,
                                                            const Real* const* q, double* const* lamx,
                                                            double* const* lame) {
-  // maxima in the state's arithmetic, one conversion per line at the atomic
+  // maxima in the state's arithmetic, one conversion per line at the atomic; a tile is 32
+  // columns by 8 x lam_rows() rows, thread (x, y) taking rows y, y + 8, ...
+  constexpr int NR = lam_rows<Real>();
   __shared__ Real col[8][33];
   const TileRef t = tiles[blockIdx.x];
   const Params& P = Ps[t.block];
   const Real* Q = q[t.block];
   const int ni = P.ni, nj = P.nj;
-  const int i = t.bx * 32 + threadIdx.x, j = t.by * 8 + threadIdx.y;
-  Real sx = Real(0), se = Real(0);
-  if (i < ni && j < nj) {
-    // |U^| + c|k^| in the state's arithmetic (the splitting only needs A^ constant per line)
-    const long long plane = (long long)nj * P.ld, o = (long long)j * P.ld + i;
-    Real qq[4];
+  const int i = t.bx * 32 + threadIdx.x;
+  const long long plane = (long long)nj * P.ld;
+  const Real g = from_f64<Real>(P.gamma);
+  Real qq[NR][4];
+  double m[NR][4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) qq[v] = Q[v * plane + o];
-    const Real g = from_f64<Real>(P.gamma);
-    sx = spectral_radius(qq, from_f64_alu<Real>(met_at(P, 0, i, j)), from_f64_alu<Real>(met_at(P, 1, i, j)), g);
-    se = spectral_radius(qq, from_f64_alu<Real>(met_at(P, 2, i, j)), from_f64_alu<Real>(met_at(P, 3, i, j)), g);
+  for (int r = 0; r < NR; ++r) {
+    const int j = t.by * 8 * NR + threadIdx.y + 8 * r;
+    if (i >= ni || j >= nj) continue;
+    const long long o = (long long)j * P.ld + i;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qq[r][v] = Q[v * plane + o];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) m[r][c] = met_at(P, c, i, j);
   }
-  Real rx = sx;
+  Real se = Real(0);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) rx = max(rx, __shfl_xor_sync(0xffffffffu, rx, off));
-  if (threadIdx.x == 0 && j < nj)
-    atomicMax(reinterpret_cast<unsigned long long*>(lamx[t.block] + j),
-              (unsigned long long)__double_as_longlong((double)rx));
+  for (int r = 0; r < NR; ++r) {
+    const int j = t.by * 8 * NR + threadIdx.y + 8 * r;
+    Real sx = Real(0);
+    if (i < ni && j < nj) {
+      // |U^| + c|k^| in the state's arithmetic (the splitting only needs A^ constant per line)
+      sx = spectral_radius(qq[r], from_f64_alu<Real>(m[r][0]), from_f64_alu<Real>(m[r][1]), g);
+      se = max(se, spectral_radius(qq[r], from_f64_alu<Real>(m[r][2]), from_f64_alu<Real>(m[r][3]), g));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sx = max(sx, __shfl_xor_sync(0xffffffffu, sx, off));
+    if (threadIdx.x == 0 && j < nj)
+      atomicMax(reinterpret_cast<unsigned long long*>(lamx[t.block] + j),
+                (unsigned long long)__double_as_longlong((double)sx));
+  }
   col[threadIdx.y][threadIdx.x] = se;
   __syncthreads();
   if (threadIdx.y == 0 && i < ni) {
-    Real m = col[0][threadIdx.x];
+    Real mx = col[0][threadIdx.x];
 #pragma unroll
-    for (int r = 1; r < 8; ++r) m = max(m, col[r][threadIdx.x]);
+    for (int r = 1; r < 8; ++r) mx = max(mx, col[r][threadIdx.x]);
     atomicMax(reinterpret_cast<unsigned long long*>(lame[t.block] + i),
-              (unsigned long long)__double_as_longlong((double)m));
+              (unsigned long long)__double_as_longlong((double)mx));
   }
 }
 
@@ -340,7 +361,8 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
     acc += al(4 * (size_t)B.nj * B.ld * acc_elem(cfg->precision));
     h->st_off.push_back(st);
     st += al(4 * (size_t)B.nj * B.ld * state_size(cfg->precision));
-    for (int by = 0; by < (B.nj + 7) / 8; ++by)
+    const int lr = 8 * (cfg->precision == FSP_FP64 ? lam_rows<double>() : lam_rows<float>());
+    for (int by = 0; by < (B.nj + lr - 1) / lr; ++by)
       for (int bx = 0; bx < (B.ni + 31) / 32; ++bx) h->tl.push_back({b, bx, by});
   }
   h->lam_count = lam;
