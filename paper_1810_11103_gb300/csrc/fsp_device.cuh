@@ -200,6 +200,31 @@ __device__ __forceinline__ float from_f64_int(double d) {
   return __uint_as_float(sign | (((unsigned)e << 23) + m));   // a mantissa carry bumps the exponent
 }
 
+// A float widened to double with integer operations: exact, so the same bits as the hardware
+// conversion, which the mixed path would otherwise queue on its bottleneck, the FP64 pipe.
+// A normal float's exponent is rebiased (127 -> 1023) and its 23 mantissa bits become the top
+// of the 52; zero keeps its sign; subnormals, infinities and NaN (never met on this path) take
+// the hardware conversion.
+__device__ __forceinline__ double to_f64_int(float x) {
+  const unsigned b = __float_as_uint(x), mag = b & 0x7fffffffu;
+  if (mag - 0x00800000u >= 0x7f000000u) {
+    if (mag == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return (double)x;
+  }
+  const unsigned hi = (b & 0x80000000u) | ((mag >> 23) + 896u) << 20 | (mag & 0x7fffffu) >> 3;
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+// Conversions between the state type and the accumulation type, on the integer pipe where
+// they would cost FP64-pipe issue (float <-> double); identity otherwise.
+template <typename Acc> __device__ __forceinline__ Acc widen(float x);
+template <> __device__ __forceinline__ float widen<float>(float x) { return x; }
+template <> __device__ __forceinline__ double widen<double>(float x) { return to_f64_int(x); }
+template <typename Acc> __device__ __forceinline__ Acc widen(double x) { return x; }
+template <typename Real> __device__ __forceinline__ Real narrow(float x) { return x; }
+template <typename Real> __device__ __forceinline__ Real narrow(double x);
+template <> __device__ __forceinline__ double narrow<double>(double x) { return x; }
+template <> __device__ __forceinline__ float narrow<float>(double x) { return from_f64_int(x); }
+
 // A double rounded to the state type on the integer pipe (identity for double), for kernels
 // that convert several metrics per node and leave most issue slots free: there the narrow
 // FP64 pipe, which carries the hardware conversion, would be the bound.

@@ -246,7 +246,7 @@ __device__ __forceinline__ void node_split(const Real q[4], double mx, double my
     const Real ex[4] = {q[1], q[1] * w.u + p, q[2] * w.u, (q[3] + p) * w.u};
     const Real ey[4] = {q[2], q[1] * w.v, q[2] * w.v + p, (q[3] + p) * w.v};
 #pragma unroll
-    for (int v = 0; v < 4; ++v) fp[v] = amx * Acc(ex[v]) + amy * Acc(ey[v]);
+    for (int v = 0; v < 4; ++v) fp[v] = amx * widen<Acc>(ex[v]) + amy * widen<Acc>(ey[v]);
   } else {
     const Acc U = amx * Acc(w.u) + amy * Acc(w.v);
     const Acc E[4] = {Acc(q[0]) * U, Acc(q[1]) * U + amx * Acc(p), Acc(q[2]) * U + amy * Acc(p),
@@ -367,7 +367,8 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
     if constexpr (Sc::nmp == 1) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        mo.f[0][v] = mmx * Acc(Real(0.5) * (ex[0][v] + ex[1][v])) + mmy * Acc(Real(0.5) * (ey[0][v] + ey[1][v]));
+        mo.f[0][v] = mmx * widen<Acc>(Real(0.5) * (ex[0][v] + ex[1][v])) +
+                     mmy * widen<Acc>(Real(0.5) * (ey[0][v] + ey[1][v]));
         mo.q[0][v] = Qs[0][v] - Qs[1][v];
       }
     } else {
@@ -375,7 +376,7 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
       for (int side = 0; side < 2; ++side)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          mo.f[side][v] = mmx * Acc(ex[side][v]) + mmy * Acc(ey[side][v]);
+          mo.f[side][v] = mmx * widen<Acc>(ex[side][v]) + mmy * widen<Acc>(ey[side][v]);
           mo.q[side][v] = Qs[side][v];
         }
     }
@@ -447,7 +448,7 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
     }
     const Real hA = Real(0.5) * from_f64_int(A);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) h[v] = he[v] + Acc(hA * hq[v]);
+    for (int v = 0; v < 4; ++v) h[v] = he[v] + widen<Acc>(hA * hq[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -651,9 +652,10 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
       for (int v = 0; v < 4; ++v) {
         const Acc d = (sDa[v * Sh::NO + k] + R[v]) * mJ;
         if constexpr (MODE == MODE_RHS) {
-          qout[v * plane + o] = Real(d);
+          qout[v * plane + o] = narrow<Real>(d);
         } else {
-          qout[v * plane + o] = Real(Acc(ca) * Acc(sQn[v * Sh::NO + k]) + Acc(cb) * (Acc(qs[v]) + Acc(dt) * d));
+          qout[v * plane + o] =
+              narrow<Real>(Acc(ca) * widen<Acc>(sQn[v * Sh::NO + k]) + Acc(cb) * (widen<Acc>(qs[v]) + Acc(dt) * d));
         }
       }
     }
@@ -795,9 +797,10 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
         for (int v = 0; v < 4; ++v) {
           const Acc d = (Dacc[v * plane + o] + R[v]) * mJ;
           if constexpr (MODE == MODE_RHS) {
-            qout[v * plane + o] = Real(d);
+            qout[v * plane + o] = narrow<Real>(d);
           } else {
-            qout[v * plane + o] = Real(Acc(ca) * Acc(Qn[v * plane + o]) + Acc(cb) * (Acc(qs[v]) + Acc(dt) * d));
+            qout[v * plane + o] =
+                narrow<Real>(Acc(ca) * widen<Acc>(Qn[v * plane + o]) + Acc(cb) * (widen<Acc>(qs[v]) + Acc(dt) * d));
           }
         }
       }
@@ -995,9 +998,9 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
         for (int v = 0; v < 4; ++v) {
           const Acc d = (Dv[v] + R[v]) * mJ;
           if constexpr (MODE == MODE_RHS) {
-            qout[v * plane + o] = Real(d);
+            qout[v * plane + o] = narrow<Real>(d);
           } else {
-            qout[v * plane + o] = Real(Acc(ca) * Acc(Qv[v]) + Acc(cb) * (Acc(qs[v]) + Acc(dt) * d));
+            qout[v * plane + o] = narrow<Real>(Acc(ca) * widen<Acc>(Qv[v]) + Acc(cb) * (widen<Acc>(qs[v]) + Acc(dt) * d));
           }
         }
       }
