@@ -60,7 +60,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            # FSP_ORACLE_LIB: a separately built copy of the oracle (the mutation tests build
+            # copies with a planted mistake and run the pins against them)
+            L = ctypes.CDLL(os.environ.get("FSP_ORACLE_LIB") or build())
             sig = {
                 "orc_metrics": (ctypes.c_int, [_I, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]),
                 "orc_metrics_jvp": (ctypes.c_int, [_I, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D]),

@@ -1,0 +1,134 @@
+"""The oracle's pins catch plausible mistakes (CPU).
+
+Each entry plants one mistake in a copy of ``oracle/fsp_oracle.cpp``: a flipped sign, a
+transposed operand or index, a dropped term, or a mistyped digit in a printed coefficient.
+The copy is built with the oracle's own flags. Then the pins named beside the mistake run
+against it, through ``FSP_ORACLE_LIB``, and at least one of them must fail. The unmodified
+oracle passes the same pins in the rest of the suite.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "fsp_oracle.cpp")
+
+ADV = "test_oracle_advection.py::"
+EUL = "test_oracle_euler.py::"
+MBK = "test_oracle_multiblock.py::"
+W7 = "test_oracle_weno7.py::"
+
+# (name, text in the oracle, planted replacement, pins that catch it: tests/ node ids)
+MUTANTS = [
+    # printed coefficients (Section 3, Appendix)
+    ("h5_1mp_sign", "-29.0L / 480", "29.0L / 480", [ADV + "test_table3[2]", ADV + "test_table3_orders[2-5]"]),
+    ("h3_2mp_midpoint", "{1.0L - 1.0L / 6, -1.0L / 6}", "{1.0L + 1.0L / 6, -1.0L / 6}",
+     [ADV + "test_table3[1]", ADV + "test_table3_orders[1-3]"]),
+    ("central5_sign", "-13.0L / 320", "13.0L / 320",
+     [EUL + "test_metrics_exact_on_affine_grid[True-2]", EUL + "test_metrics_exact_on_polynomial_grid[2]"]),
+    ("central3_2mp_mid", "{11.0L / 12, -1.0L / 12}", "{11.0L / 12, 1.0L / 12}",
+     [EUL + "test_metrics_exact_on_affine_grid[True-1]", EUL + "test_metrics_exact_on_polynomial_grid[1]"]),
+    ("h7_digit", "-7481.0L / 107520", "-7418.0L / 107520",
+     [EUL + "test_free_stream_preservation_randomized_grid[0-4]", EUL + "test_design_order_on_curved_grid[4-7-ns4]"]),
+    ("is4_digit", "{3169, -6518, 2989}", "{3169, -6518, 2998}", [W7 + "test_r4_indicators_follow_the_definition"]),
+    # midpoint interpolation and metrics (Sections 2.3-2.4)
+    ("interp6_index", "cst<T>(3) * phi(-2) - cst<T>(25) * phi(-1)", "cst<T>(3) * phi(-1) - cst<T>(25) * phi(-2)",
+     [EUL + "test_metrics_exact_on_polynomial_grid[2]", EUL + "test_mirror_symmetry[2]"]),
+    ("metric_sign", "M[1 * plane + o] = -x_eta;", "M[1 * plane + o] = x_eta;",
+     [EUL + "test_metrics_exact_on_affine_grid[True-0]", EUL + "test_metrics_exact_on_polynomial_grid[0]"]),
+    ("jacobian_sign", "M[4 * plane + o] = x_xi * y_eta - x_eta * y_xi;",
+     "M[4 * plane + o] = x_xi * y_eta + x_eta * y_xi;",
+     [EUL + "test_metrics_exact_on_polynomial_grid[0]", MBK + "test_small_cylinder_blocks_are_valid"]),
+    # Euler flux, spectral radius, eigenvectors (Sections 2.1, 2.3, 3.4)
+    ("flux_metric_swap", "f[1] = rho * u * U + mx * p;", "f[1] = rho * u * U + my * p;",
+     [EUL + "test_mirror_symmetry[0]", EUL + "test_transpose_symmetry[0]"]),
+    ("flux_energy_drop", "f[3] = (q[3] + p) * U;", "f[3] = q[3] * U;",
+     [EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]", EUL + "test_sod_against_exact_solution[0]"]),
+    ("spectral_norm_drop", "return fabs(mx * u + my * v) + c * sqrt(mx * mx + my * my);",
+     "return fabs(mx * u + my * v) + c;",
+     [EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]", EUL + "test_line_lambda_closed_form"]),
+    ("eig_right_index", "R[2][0] = v - c * ny;", "R[2][0] = v - c * nx;",
+     [EUL + "test_free_stream_preservation_randomized_grid[0-0]", EUL + "test_table4_free_stream_on_paper_grid[0]"]),
+    ("eig_left_sign", "L[1][3] = -b1;", "L[1][3] = b1;",
+     [EUL + "test_free_stream_preservation_randomized_grid[0-0]", EUL + "test_table4_free_stream_on_paper_grid[2]"]),
+    # WENO interpolation (Eqs. 3.10-3.15, 3.22-3.23, Table 1)
+    ("is1_sign", "T d2 = db - da, d1 = da + db;", "T d2 = db - da, d1 = da - db;",
+     [ADV + "test_table3[0]", ADV + "test_table3_orders[0-3]"]),
+    ("is0_sign", "T d2 = db - da, d1 = cst<T>(3) * db - da;", "T d2 = db - da, d1 = cst<T>(3) * db + da;",
+     [ADV + "test_table3[0]", ADV + "test_table3_orders[0-3]"]),
+    ("candidate_index", "cst<T>(b3[k][l]) * uj[k + l - 2]", "cst<T>(b3[k][l]) * uj[k + l - 1]",
+     [ADV + "test_table3[2]", ADV + "test_table3_orders[2-5]"]),
+    ("linear_weights_swap", "{1.0L / 16, 10.0L / 16, 5.0L / 16}", "{1.0L / 16, 5.0L / 16, 10.0L / 16}",
+     [ADV + "test_table3[2]", ADV + "test_table3_orders[2-5]"]),
+    ("alpha_square_drop", "a[k] = Ck[k] / (d * d);", "a[k] = Ck[k] / d;", [ADV + "test_table3[0]"]),
+    ("ppm3_sign", "return C * (cst<T>(1) + s * s * s);", "return C * (cst<T>(1) - s * s * s);",
+     [ADV + "test_table3[2]", EUL + "test_rk3_third_order_in_time"]),
+    ("ppm2_sign", "T d = w - C; return C - d * d / (C - cst<T>(1));", "T d = w - C; return C + d * d / (C - cst<T>(1));",
+     [ADV + "test_table3[0]", EUL + "test_table4_free_stream_on_paper_grid[0]"]),
+    # splitting and the right-hand side (Sections 2.3, 3, 3.4)
+    ("lf_alpha_drop", "return F.P.alpha * best;", "return best;",
+     [EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]", EUL + "test_line_lambda_closed_form"]),
+    ("split_sign", "fm[4 * (s + 4) + v] = cst<T>(0.5L) * (f[v] - A * qs[v]);",
+     "fm[4 * (s + 4) + v] = cst<T>(0.5L) * (f[v] + A * qs[v]);",
+     [EUL + "test_mirror_symmetry[0]", EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]"]),
+    ("direction_swap", "T nx = mbx / mb, ny = mby / mb;", "T nx = mby / mb, ny = mbx / mb;",
+     [EUL + "test_rotation_equivariance[2]"]),
+    ("mirror_stencil", "const int node = side == 0 ? c0 + m : c0 + 1 - m;",
+     "const int node = side == 0 ? c0 + m : c0 + 1 + m;",
+     [EUL + "test_mirror_symmetry[0]", EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]"]),
+    ("h_minus_index", "fm[4 * (p + 1 - k + 4) + v]", "fm[4 * (p + k + 4) + v]",
+     [EUL + "test_free_stream_preservation_randomized_grid[0-0]", EUL + "test_table4_free_stream_on_paper_grid[0]"]),
+    ("difference_index", "R[o] = R[o] + (Hh[4 * (s + 2) + v] - Hh[4 * (s + 1) + v]);",
+     "R[o] = R[o] + (Hh[4 * (s + 2) + v] - Hh[4 * (s + 0) + v]);",
+     [EUL + "test_free_stream_preservation_randomized_grid[0-0]", EUL + "test_conservation_periodic"]),
+    ("jacobian_multiply", "dQ[o] = -R[o] / Jinv;", "dQ[o] = -R[o] * Jinv;",
+     [EUL + "test_conservation_periodic", EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]"]),
+    ("midpoint_metric_shift", "return mxs[c0 + l]; });", "return mxs[c0 + l + 1]; });",
+     [EUL + "test_free_stream_preservation_randomized_grid[0-0]", EUL + "test_table4_free_stream_on_paper_grid[0]"]),
+    # time stepping (Section 6)
+    ("rk3_weights", "cst<T>(0.75L) * Q[k] + cst<T>(0.25L) * (Q1[k] + dt * R[k])",
+     "cst<T>(0.25L) * Q[k] + cst<T>(0.75L) * (Q1[k] + dt * R[k])",
+     [EUL + "test_rk3_third_order_in_time", EUL + "test_sod_against_exact_solution[0]"]),
+    ("cfl_invert", "return cfl / best;", "return cfl * best;",
+     [EUL + "test_line_lambda_closed_form", EUL + "test_sod_against_exact_solution[0]"]),
+]
+
+
+def _build(tmp, name, old, new, src):
+    d = os.path.join(tmp, name)
+    os.makedirs(d, exist_ok=True)
+    cpp, so = os.path.join(d, "fsp_oracle.cpp"), os.path.join(d, "libfsp_oracle.so")
+    with open(cpp, "w") as f:
+        f.write(src.replace(old, new))
+    r = subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, cpp],
+                       capture_output=True, text=True)
+    return so if r.returncode == 0 else None
+
+
+def _pins_fail(so, pins):
+    env = dict(os.environ, FSP_ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                        *[os.path.join("tests", t) for t in pins]],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode != 0, (r.stdout.strip().splitlines() or [""])[-1]
+
+
+def test_every_planted_mistake_is_caught(tmp_path):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ is needed to build the mutated oracles")
+    with open(SRC) as f:
+        src = f.read()
+    for name, old, new, _ in MUTANTS:
+        assert src.count(old) == 1, f"{name}: the planted text must occur once in the oracle"
+    workers = min(8, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(workers) as ex:
+        libs = list(ex.map(lambda m: _build(str(tmp_path), m[0], m[1], m[2], src), MUTANTS))
+    assert all(libs), [m[0] for m, so in zip(MUTANTS, libs) if so is None]
+    with cf.ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(lambda a: _pins_fail(a[0], a[1][3]), zip(libs, MUTANTS)))
+    missed = [(m[0], last) for m, (caught, last) in zip(MUTANTS, results) if not caught]
+    assert not missed, f"mistakes the pins did not catch: {missed}"
