@@ -297,6 +297,81 @@ def test_uniform_flow_kept_by_boundaries(bc):
     assert np.abs(R).max() < 1e-11
 
 
+# Boundary rules (readings: the paper treats no boundaries) pinned to what each rule means,
+# on a uniform grid turned by 0.3 rad (so that both velocity components cross the i-faces),
+# periodic in j, with a state that varies at the faces.
+_TH = 0.3
+
+
+def _turned_grid(i0, ni, nj, h=0.25):
+    c, s = math.cos(_TH), math.sin(_TH)
+    i, j = np.arange(i0, i0 + ni, dtype=np.float64), np.arange(nj, dtype=np.float64)
+    X, Y = np.broadcast_to(h * i[None, :], (nj, ni)), np.broadcast_to(h * j[:, None], (nj, ni))
+    return c * X - s * Y, s * X + c * Y, ((0.0, 0.0), (-s * h * nj, c * h * nj))
+
+
+def _face_state(x, y):
+    c, s = math.cos(_TH), math.sin(_TH)
+    X, Y = c * x + s * y, -s * x + c * y
+    rng = np.random.default_rng(4)
+    rho = 1 + 0.2 * np.exp(-((X - 1.0) ** 2 + (Y - 2.0) ** 2)) + 0.02 * rng.standard_normal(X.shape)
+    u = 0.3 + 0.2 * np.sin(Y) + 0.02 * rng.standard_normal(X.shape)
+    v = -0.2 + 0.1 * np.cos(X)
+    p = 1 + 0.1 * np.exp(-((X - 0.5) ** 2 + (Y - 1.0) ** 2))
+    return I.conservative(rho, c * u - s * v, s * u + c * v, p)
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
+def test_slip_wall_is_a_symmetry_plane(scheme):
+    """Next to a slip wall the right-hand side is that of the doubled domain: the block and
+    its mirror image about the wall line, velocity reflected (node 0 lies on the wall)."""
+    n, nj = 14, 16
+    x, y, per = _turned_grid(0, n, nj)
+    q = _face_state(x, y)
+    cfg = _cfg(scheme=scheme, bc=(3, 1, 0, 0), period=per)
+    R = O.rhs(cfg, O.metrics(cfg, x, y), q)
+    xd, yd, _ = _turned_grid(-(n - 1), 2 * n - 1, nj)
+    qd = np.concatenate([q[:, :, :0:-1], q], axis=2)
+    m = qd[:, :, :n - 1]
+    c, s = math.cos(_TH), math.sin(_TH)
+    un = m[1] * c + m[2] * s
+    m[1] -= 2 * un * c
+    m[2] -= 2 * un * s
+    cfgd = _cfg(scheme=scheme, bc=(1, 1, 0, 0), period=per)
+    Rd = O.rhs(cfgd, O.metrics(cfgd, xd, yd), qd)
+    assert np.abs(Rd[:, :, n - 1:] - R).max() < 1e-12 * np.abs(R).max()
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
+def test_transmissive_face_is_a_constant_continuation(scheme):
+    """A transmissive face gives the right-hand side of the block continued by copies of its
+    boundary node (on a uniform grid the continued metrics equal the boundary node's, so the
+    line maxima do not change either)."""
+    n, nj, pad = 14, 16, 12
+    x, y, per = _turned_grid(0, n, nj)
+    q = _face_state(x, y)
+    cfg = _cfg(scheme=scheme, bc=(1, 1, 0, 0), period=per)
+    R = O.rhs(cfg, O.metrics(cfg, x, y), q)
+    xp, yp, _ = _turned_grid(-pad, n + pad, nj)
+    qp = np.concatenate([np.repeat(q[:, :, :1], pad, axis=2), q], axis=2)
+    Rp = O.rhs(cfg, O.metrics(cfg, xp, yp), qp)
+    assert np.abs(Rp[:, :, pad:] - R).max() < 1e-12 * np.abs(R).max()
+
+
+@pytest.mark.parametrize("scheme", [0, 2, 4])
+def test_far_field_is_dirichlet_on_inflow_and_transmissive_on_outflow(scheme):
+    x, y, per = _turned_grid(0, 14, 16)
+    q = _face_state(x, y)
+    c, s = math.cos(_TH), math.sin(_TH)
+    for speed, same_as in ((0.5, 2), (-0.5, 1)):   # prescribed velocity into / out of the i- face
+        st = np.tile(I.conservative(1.1, c * speed, s * speed, 0.9), (4, 1))
+        out = []
+        for bc0 in (4, same_as):
+            cfg = _cfg(scheme=scheme, bc=(bc0, 1, 0, 0), period=per, bc_state=st)
+            out.append(O.rhs(cfg, O.metrics(cfg, x, y), q))
+        assert np.array_equal(out[0], out[1])
+
+
 def test_rk3_third_order_in_time():
     n, L = 24, 8.0
     x, y, per = I.periodic_square(n, L, 0.0, seed=0)

@@ -21,6 +21,7 @@ ADV = "test_oracle_advection.py::"
 EUL = "test_oracle_euler.py::"
 MBK = "test_oracle_multiblock.py::"
 W7 = "test_oracle_weno7.py::"
+TAN = "test_oracle_tangent.py::"
 
 # (name, text in the oracle, planted replacement, pins that catch it: tests/ node ids)
 MUTANTS = [
@@ -89,6 +90,42 @@ MUTANTS = [
      [EUL + "test_conservation_periodic", EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]"]),
     ("midpoint_metric_shift", "return mxs[c0 + l]; });", "return mxs[c0 + l + 1]; });",
      [EUL + "test_free_stream_preservation_randomized_grid[0-0]", EUL + "test_table4_free_stream_on_paper_grid[0]"]),
+    # seventh-order pieces (Appendix)
+    ("ppm4_sign", "return C - d * d * d * d / (e * e * e);", "return C + d * d * d * d / (e * e * e);",
+     [W7 + "test_fourth_order_mapping[0.015625]", EUL + "test_rotation_equivariance[4]"]),
+    ("c4_digit", "{1.0L / 64, 21.0L / 64, 35.0L / 64, 7.0L / 64}", "{1.0L / 64, 21.0L / 64, 35.0L / 64, 8.0L / 64}",
+     [W7 + "test_table_a1_candidates_and_linear_weights", W7 + "test_seventh_order_advection"]),
+    ("b4_sign", "{-1.0L / 16, 9.0L / 16, 9.0L / 16, -1.0L / 16}", "{-1.0L / 16, 9.0L / 16, 9.0L / 16, 1.0L / 16}",
+     [W7 + "test_table_a1_candidates_and_linear_weights", W7 + "test_weno7_constant_and_step"]),
+    ("interp8_digit", "cst<T>(49) * phi(-2) - cst<T>(245) * phi(-1)", "cst<T>(49) * phi(-2) - cst<T>(254) * phi(-1)",
+     [EUL + "test_metrics_exact_on_affine_grid[True-4]", EUL + "test_metrics_exact_on_polynomial_grid[4]"]),
+    ("is4_symmetric_digit", "{-31718, 45076, -16958}", "{-31718, 45067, -16958}",
+     [W7 + "test_r4_indicators_follow_the_definition"]),
+    # boundary rules, ghost coordinates and linked faces (readings)
+    ("slipwall_mirror", "int sm = 2 * b - s;", "int sm = 2 * b - s - 1;",
+     [EUL + "test_slip_wall_is_a_symmetry_plane[2]"]),
+    ("slipwall_sign", "out[2] = out[2] - cst<T>(2) * un * ny;", "out[2] = out[2] + cst<T>(2) * un * ny;",
+     [EUL + "test_slip_wall_is_a_symmetry_plane[2]"]),
+    ("farfield_inflow", "if (vn < T(0))", "if (vn > T(0))",
+     [EUL + "test_far_field_is_dirichlet_on_inflow_and_transmissive_on_outflow[2]"]),
+    ("transmissive_node", "case BC_TRANSMISSIVE: rd(b, out); return;",
+     "case BC_TRANSMISSIVE: rd(s < 0 ? 1 : n - 2, out); return;",
+     [EUL + "test_transmissive_face_is_a_constant_continuation[2]"]),
+    ("ghost_reflect", "at(ib, j, X0, Y0); at(2 * ib - i, j, X1, Y1);", "at(ib, j, X0, Y0); at(2 * ib - i + 1, j, X1, Y1);",
+     [EUL + "test_metrics_exact_on_affine_grid[False-0]"]),
+    ("period_sign", "X = X + T(double(q)) * per[0][0];", "X = X - T(double(q)) * per[0][0];",
+     [EUL + "test_metrics_exact_on_affine_grid[True-0]", EUL + "test_transpose_symmetry[0]"]),
+    ("link_reverse", "if (L.rev) t = nt - 1 - t;", "if (!L.rev) t = nt - 1 - t;",
+     [MBK + "test_reversed_link_metrics_on_randomised_grid", MBK + "test_reversed_link_rhs"]),
+    ("link_depth", "else if (L.face == 1) depth = nni - 1 - k;", "else if (L.face == 1) depth = nni - 2 - k;",
+     [MBK + "test_cut_grid_reproduces_rhs[0]", MBK + "test_reversed_link_rhs"]),
+    # forward tangents (the dual numbers behind the adjoint checks)
+    ("dual_product", "a.d * b.v + a.v * b.d", "a.d * b.v + a.d * b.d",
+     [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_metrics_tangent_matches_finite_differences[0]"]),
+    ("dual_quotient", "(a.d - q * b.d) / b.v", "(a.d + q * b.d) / b.v",
+     [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_rk3_tangent_matches_finite_differences"]),
+    ("dual_sqrt", "a.d / (2.0 * s)", "a.d / s",
+     [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_rk3_tangent_matches_finite_differences"]),
     # time stepping (Section 6)
     ("rk3_weights", "cst<T>(0.75L) * Q[k] + cst<T>(0.25L) * (Q1[k] + dt * R[k])",
      "cst<T>(0.25L) * Q[k] + cst<T>(0.75L) * (Q1[k] + dt * R[k])",
