@@ -359,6 +359,25 @@ def test_transmissive_face_is_a_constant_continuation(scheme):
 
 
 @pytest.mark.parametrize("scheme", [0, 2, 4])
+def test_dirichlet_face_holds_its_own_state(scheme):
+    """A Dirichlet face gives the right-hand side of the block continued by nodes that hold
+    that face's prescribed state.  Each face has its own state, and each is slower than the
+    interior's fastest wave, so the continued nodes leave the line maxima alone."""
+    n, nj, pad = 14, 16, 12
+    x, y, per = _turned_grid(0, n, nj)
+    q = _face_state(x, y)
+    st = np.stack([I.conservative(1.1, 0.05, 0.0, 0.9), I.conservative(0.9, -0.05, 0.02, 1.05),
+                   I.conservative(1.0, 0.0, 0.0, 1.0), I.conservative(1.0, 0.0, 0.0, 1.0)])
+    cfg = _cfg(scheme=scheme, bc=(2, 2, 0, 0), period=per, bc_state=st)
+    R = O.rhs(cfg, O.metrics(cfg, x, y), q)
+    xp, yp, _ = _turned_grid(0, n + pad, nj)
+    qp = np.concatenate([q, np.repeat(st[1][:, None, None], nj, axis=1).repeat(pad, axis=2)], axis=2)
+    cfgp = _cfg(scheme=scheme, bc=(2, 1, 0, 0), period=per, bc_state=st)
+    Rp = O.rhs(cfgp, O.metrics(cfgp, xp, yp), qp)
+    assert np.abs(Rp[:, :, :n] - R).max() < 1e-12 * np.abs(R).max()
+
+
+@pytest.mark.parametrize("scheme", [0, 2, 4])
 def test_far_field_is_dirichlet_on_inflow_and_transmissive_on_outflow(scheme):
     x, y, per = _turned_grid(0, 14, 16)
     q = _face_state(x, y)

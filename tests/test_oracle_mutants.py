@@ -39,6 +39,10 @@ MUTANTS = [
     # midpoint interpolation and metrics (Sections 2.3-2.4)
     ("interp6_index", "cst<T>(3) * phi(-2) - cst<T>(25) * phi(-1)", "cst<T>(3) * phi(-1) - cst<T>(25) * phi(-2)",
      [EUL + "test_metrics_exact_on_polynomial_grid[2]", EUL + "test_mirror_symmetry[2]"]),
+    ("interp4_digit", "cst<T>(9) * phi(1) - phi(2)) / cst<T>(16)", "cst<T>(9) * phi(1) - phi(2)) / cst<T>(15)",
+     [EUL + "test_metrics_exact_on_affine_grid[True-0]", EUL + "test_metrics_exact_on_polynomial_grid[0]"]),
+    ("metric_eta_x_sign", "M[2 * plane + o] = -y_xi;", "M[2 * plane + o] = y_xi;",
+     [EUL + "test_metrics_exact_on_polynomial_grid[0]", EUL + "test_free_stream_preservation_randomized_grid[0-0]"]),
     ("metric_sign", "M[1 * plane + o] = -x_eta;", "M[1 * plane + o] = x_eta;",
      [EUL + "test_metrics_exact_on_affine_grid[True-0]", EUL + "test_metrics_exact_on_polynomial_grid[0]"]),
     ("jacobian_sign", "M[4 * plane + o] = x_xi * y_eta - x_eta * y_xi;",
@@ -47,6 +51,8 @@ MUTANTS = [
     # Euler flux, spectral radius, eigenvectors (Sections 2.1, 2.3, 3.4)
     ("flux_metric_swap", "f[1] = rho * u * U + mx * p;", "f[1] = rho * u * U + my * p;",
      [EUL + "test_mirror_symmetry[0]", EUL + "test_transpose_symmetry[0]"]),
+    ("flux_y_pressure", "f[2] = rho * v * U + my * p;", "f[2] = rho * v * U + mx * p;",
+     [EUL + "test_mirror_symmetry[0]", EUL + "test_rotation_equivariance[0]"]),
     ("flux_energy_drop", "f[3] = (q[3] + p) * U;", "f[3] = q[3] * U;",
      [EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]", EUL + "test_sod_against_exact_solution[0]"]),
     ("spectral_norm_drop", "return fabs(mx * u + my * v) + c * sqrt(mx * mx + my * my);",
@@ -65,6 +71,12 @@ MUTANTS = [
      [ADV + "test_table3[2]", ADV + "test_table3_orders[2-5]"]),
     ("linear_weights_swap", "{1.0L / 16, 10.0L / 16, 5.0L / 16}", "{1.0L / 16, 5.0L / 16, 10.0L / 16}",
      [ADV + "test_table3[2]", ADV + "test_table3_orders[2-5]"]),
+    ("b2_digit", "{{-0.5L, 1.5L}, {0.5L, 0.5L}}", "{{-0.5L, 1.5L}, {0.5L, 1.5L}}",
+     [ADV + "test_table3[0]", ADV + "test_table3_orders[0-3]"]),
+    ("c2_swap", "static const long double c2[2] = {0.25L, 0.75L};", "static const long double c2[2] = {0.75L, 0.25L};",
+     [ADV + "test_table3[0]", EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]"]),
+    ("ppm_renorm_drop", "for (int k = 0; k < r; ++k) w[k] = g[k] / sg;", "for (int k = 0; k < r; ++k) w[k] = g[k];",
+     [ADV + "test_table3[2]", EUL + "test_table4_free_stream_on_paper_grid[2]"]),
     ("alpha_square_drop", "a[k] = Ck[k] / (d * d);", "a[k] = Ck[k] / d;", [ADV + "test_table3[0]"]),
     ("ppm3_sign", "return C * (cst<T>(1) + s * s * s);", "return C * (cst<T>(1) - s * s * s);",
      [ADV + "test_table3[2]", EUL + "test_rk3_third_order_in_time"]),
@@ -76,6 +88,16 @@ MUTANTS = [
     ("split_sign", "fm[4 * (s + 4) + v] = cst<T>(0.5L) * (f[v] - A * qs[v]);",
      "fm[4 * (s + 4) + v] = cst<T>(0.5L) * (f[v] + A * qs[v]);",
      [EUL + "test_mirror_symmetry[0]", EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]"]),
+    ("minus_side_eigen", "const int ce = side == 0 ? c0 : c0 + 1;", "const int ce = side == 0 ? c0 : c0;",
+     [EUL + "test_mirror_symmetry[0]"]),
+    ("h2mp_plus_index", "hp = hp + cst<T>(S.hmid[-m]) * fpm[4 * (p + m + 2) + v];",
+     "hp = hp + cst<T>(S.hmid[-m]) * fpm[4 * (p - m + 2) + v];",
+     [EUL + "test_free_stream_preservation_randomized_grid[0-1]", EUL + "test_mirror_symmetry[1]"]),
+    ("h2mp_minus_index", "hm = hm + cst<T>(S.hmid[-m]) * fmm[4 * (p - m + 2) + v];",
+     "hm = hm + cst<T>(S.hmid[-m]) * fmm[4 * (p + m + 2) + v];",
+     [EUL + "test_free_stream_preservation_randomized_grid[0-1]", EUL + "test_mirror_symmetry[1]"]),
+    ("line_max_min", "if (s == 0 || sp > best) best = sp;", "if (s == 0 || sp < best) best = sp;",
+     [EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]"]),
     ("direction_swap", "T nx = mbx / mb, ny = mby / mb;", "T nx = mby / mb, ny = mbx / mb;",
      [EUL + "test_rotation_equivariance[2]"]),
     ("mirror_stencil", "const int node = side == 0 ? c0 + m : c0 + 1 - m;",
@@ -119,6 +141,11 @@ MUTANTS = [
      [MBK + "test_reversed_link_metrics_on_randomised_grid", MBK + "test_reversed_link_rhs"]),
     ("link_depth", "else if (L.face == 1) depth = nni - 1 - k;", "else if (L.face == 1) depth = nni - 2 - k;",
      [MBK + "test_cut_grid_reproduces_rhs[0]", MBK + "test_reversed_link_rhs"]),
+    ("dirichlet_face", "case BC_DIRICHLET: for (int v = 0; v < 4; ++v) out[v] = P.bcq[face][v]; return;",
+     "case BC_DIRICHLET: for (int v = 0; v < 4; ++v) out[v] = P.bcq[0][v]; return;",
+     [EUL + "test_dirichlet_face_holds_its_own_state[2]"]),
+    ("link_offset_sign", "X = X + T(L.off[0]); Y = Y + T(L.off[1]);", "X = X - T(L.off[0]); Y = Y + T(L.off[1]);",
+     [MBK + "test_cut_periodic_grid_reproduces_metrics[0]", MBK + "test_cut_grid_reproduces_rhs[0]"]),
     # forward tangents (the dual numbers behind the adjoint checks)
     ("dual_product", "a.d * b.v + a.v * b.d", "a.d * b.v + a.d * b.d",
      [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_metrics_tangent_matches_finite_differences[0]"]),
@@ -129,6 +156,8 @@ MUTANTS = [
     # time stepping (Section 6)
     ("rk3_weights", "cst<T>(0.75L) * Q[k] + cst<T>(0.25L) * (Q1[k] + dt * R[k])",
      "cst<T>(0.25L) * Q[k] + cst<T>(0.75L) * (Q1[k] + dt * R[k])",
+     [EUL + "test_rk3_third_order_in_time", EUL + "test_sod_against_exact_solution[0]"]),
+    ("rk3_last_stage", "cst<T>(2.0L / 3) * (Q2[k] + dt * R[k]);", "cst<T>(2.0L / 3) * (Q2[k] + dt * R[k] * cst<T>(0.5L));",
      [EUL + "test_rk3_third_order_in_time", EUL + "test_sod_against_exact_solution[0]"]),
     ("cfl_invert", "return cfl / best;", "return cfl * best;",
      [EUL + "test_line_lambda_closed_form", EUL + "test_sod_against_exact_solution[0]"]),
