@@ -275,6 +275,11 @@ def run_reference(args, rank):
     import oracle as O
     O.build()
     cfg, M, q, nodes, what = oracle_sample(args)
+    if args.workload == "cylinder64":
+        blocks = cylinder_workload()[0]
+        job_nodes, nblocks = sum(b["x"].size for b in blocks), len(blocks)
+    else:
+        job_nodes, nblocks = nodes, 1
     for _ in range(args.warmup):
         O.rhs(cfg, M, q)
     t0 = time.perf_counter()
@@ -286,9 +291,12 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": dict(workload_config(args, nodes, 1), step=f"one right-hand side of {what} (oracle, one host thread)"),
+            "config": workload_config(args, job_nodes, nblocks),
+            "reference_step": f"one right-hand side of {what} (oracle, one host thread); the rate is per "
+                              f"node and right-hand side, as on the GPU arm",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} right-hand sides of {what}"},
+                             "sample": f"a bounded sample of the workload: {args.steps} right-hand sides of {what} "
+                                       f"(oracle, one host thread)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
