@@ -34,24 +34,33 @@ def cylinder_counts(scheme):
             "sweep_xi_per_node": sx / nodes, "sweep_eta_per_node": (se + fin) / nodes, "nodes": nodes}
 
 
-def main():
+NAMES = ["WENOIU3-1MP", "WENOIU3-2MP", "WENOIU5-1MP", "WENOIU5-2MP", "WENOIU7-1MP"]
+
+
+def vortex_counts():
+    """Per-node flops of every scheme on the 256 x 256 periodic vortex."""
     x, y, per = I.periodic_square(256, 10.0, 0.2, seed=1810)
     q = I.isentropic_vortex(x, y, (5.0, 5.0), strength=5.0, free=(1.0, 1.0, 1.0, 1.0), period=(10.0, 10.0))
     n = x.size
-    res = {"workload": "periodic vortex 256x256, randomised grid A=0.2, seed 1810",
-           "how": "oracle with an operation-counting scalar; + - * / sqrt = 1 flop each",
-           "schemes": {}}
-    names = ["WENOIU3-1MP", "WENOIU3-2MP", "WENOIU5-1MP", "WENOIU5-2MP", "WENOIU7-1MP"]
+    out = {}
     for s in range(5):
         cfg = dict(scheme=s, period=per)
         M = O.metrics(cfg, x, y)
         lx, sx, le, se, fin = O.count_flops_parts(cfg, M, q)
-        res["schemes"][names[s]] = {
+        out[NAMES[s]] = {
             "rhs_per_node": (lx + sx + le + se + fin) / n,
             "lambda_per_node": (lx + le) / n,
             "sweep_xi_per_node": sx / n,
             "sweep_eta_per_node": (se + fin) / n,
         }
+    return out
+
+
+def main():
+    res = {"workload": "periodic vortex 256x256, randomised grid A=0.2, seed 1810",
+           "how": "oracle with an operation-counting scalar; + - * / sqrt = 1 flop each",
+           "schemes": vortex_counts()}
+    names = NAMES
     res["cylinder64"] = {"workload": "64-block cylinder (seed 1812), linked faces counted as transmissive",
                          "schemes": {names[s]: cylinder_counts(s) for s in (2, 4)}}
     with open(OUT, "w") as f:

@@ -1,0 +1,54 @@
+"""Pins of the operation counter behind the roofline's algorithmic flops (CPU).
+
+The counter runs the oracle with a scalar type that counts each + - * / and square root once.
+* The final division by J^-1 (Eq. 2.2) is one operation per conserved variable and node.
+* The line maxima: |U^| + c|k^| written out costs 22 operations per node, and alpha times the
+  maximum one more per line.  The 22 are: u and v (2 divisions), the pressure
+  (gamma - 1)(E - rho (u^2 + v^2)/2) (8), c = sqrt(gamma p / rho) (3), |mx u + my v| (3),
+  c sqrt(mx^2 + my^2) (5) and the sum (1).
+* With linear weights nothing depends on the data, so a sweep's count is exactly affine in
+  the line length.
+* The stored per-node counts are what the committed script computes now.
+"""
+import importlib
+import json
+import os
+
+import pytest
+
+import oracle as O
+from paper_1810_11103_gb300 import inputs as I
+
+CF = importlib.import_module("oracle.count_flops")   # the script (the package re-exports a function of that name)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _parts(scheme, ni, nj, **kw):
+    x, y, per = I.periodic_square(ni, 6.0, 0.2, seed=11, nj=nj)
+    q = I.isentropic_vortex(x, y, (3.1, 2.9), strength=3.0, free=(1.0, 0.5, 0.2, 1.0), period=(6.0, 6.0))
+    cfg = dict(scheme=scheme, period=per, **kw)
+    return O.count_flops_parts(cfg, O.metrics(cfg, x, y), q)
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
+def test_closed_forms(scheme):
+    ni, nj = 20, 14
+    lx, sx, le, se, fin = _parts(scheme, ni, nj)
+    assert fin == 4 * ni * nj
+    assert lx == nj * (22 * ni + 1)
+    assert le == ni * (22 * nj + 1)
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
+def test_sweep_count_affine_in_line_length(scheme):
+    nj = 12
+    xi = [_parts(scheme, n, nj, linear_weights=1)[1] for n in (16, 24, 32)]
+    assert xi[2] - xi[1] == xi[1] - xi[0] > 0
+    assert (xi[1] - xi[0]) % (8 * nj) == 0          # the same whole count per node of every line
+
+
+def test_stored_counts_match_the_script():
+    with open(os.path.join(ROOT, "paper_1810_11103_gb300", "algorithmic_flops.json")) as f:
+        stored = json.load(f)["schemes"]
+    assert CF.vortex_counts() == stored

@@ -22,6 +22,7 @@ EUL = "test_oracle_euler.py::"
 MBK = "test_oracle_multiblock.py::"
 W7 = "test_oracle_weno7.py::"
 TAN = "test_oracle_tangent.py::"
+FLO = "test_oracle_flops.py::"
 
 # (name, text in the oracle, planted replacement, pins that catch it: tests/ node ids)
 MUTANTS = [
@@ -153,6 +154,11 @@ MUTANTS = [
      [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_rk3_tangent_matches_finite_differences"]),
     ("dual_sqrt", "a.d / (2.0 * s)", "a.d / s",
      [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_rk3_tangent_matches_finite_differences"]),
+    # the operation counter (the roofline's algorithmic flops)
+    ("count_sqrt_drop", "inline Counted sqrt(Counted a) { ++g_flops; return", "inline Counted sqrt(Counted a) { return",
+     [FLO + "test_closed_forms[2]"]),
+    ("count_div_drop", "inline Counted operator/(Counted a, Counted b) { ++g_flops;",
+     "inline Counted operator/(Counted a, Counted b) {", [FLO + "test_closed_forms[2]"]),
     # time stepping (Section 6)
     ("rk3_weights", "cst<T>(0.75L) * Q[k] + cst<T>(0.25L) * (Q1[k] + dt * R[k])",
      "cst<T>(0.25L) * Q[k] + cst<T>(0.75L) * (Q1[k] + dt * R[k])",
