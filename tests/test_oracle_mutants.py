@@ -44,6 +44,8 @@ MUTANTS = [
      [EUL + "test_metrics_exact_on_affine_grid[True-0]", EUL + "test_metrics_exact_on_polynomial_grid[0]"]),
     ("metric_eta_x_sign", "M[2 * plane + o] = -y_xi;", "M[2 * plane + o] = y_xi;",
      [EUL + "test_metrics_exact_on_polynomial_grid[0]", EUL + "test_free_stream_preservation_randomized_grid[0-0]"]),
+    ("metric_dir_swap", "y_xi = central_D(P, C, 0, 1, i, j);", "y_xi = central_D(P, C, 1, 1, i, j);",
+     [EUL + "test_metrics_exact_on_affine_grid[True-0]", EUL + "test_metrics_exact_on_polynomial_grid[0]"]),
     ("metric_sign", "M[1 * plane + o] = -x_eta;", "M[1 * plane + o] = x_eta;",
      [EUL + "test_metrics_exact_on_affine_grid[True-0]", EUL + "test_metrics_exact_on_polynomial_grid[0]"]),
     ("jacobian_sign", "M[4 * plane + o] = x_xi * y_eta - x_eta * y_xi;",
@@ -78,6 +80,10 @@ MUTANTS = [
      [ADV + "test_table3[0]", EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]"]),
     ("ppm_renorm_drop", "for (int k = 0; k < r; ++k) w[k] = g[k] / sg;", "for (int k = 0; k < r; ++k) w[k] = g[k];",
      [ADV + "test_table3[2]", EUL + "test_table4_free_stream_on_paper_grid[2]"]),
+    ("alpha_cube", "a[k] = Ck[k] / (d * d); s = s + a[k];", "a[k] = Ck[k] / (d * d * d); s = s + a[k];",
+     [ADV + "test_table3[0]"]),
+    ("cand2_index", "cst<T>(b2[k][l]) * uj[k + l - 1]", "cst<T>(b2[k][l]) * uj[k + l]",
+     [ADV + "test_table3[0]", ADV + "test_table3_orders[0-3]"]),
     ("alpha_square_drop", "a[k] = Ck[k] / (d * d);", "a[k] = Ck[k] / d;", [ADV + "test_table3[0]"]),
     ("ppm3_sign", "return C * (cst<T>(1) + s * s * s);", "return C * (cst<T>(1) - s * s * s);",
      [ADV + "test_table3[2]", EUL + "test_rk3_third_order_in_time"]),
@@ -122,6 +128,10 @@ MUTANTS = [
      [W7 + "test_table_a1_candidates_and_linear_weights", W7 + "test_weno7_constant_and_step"]),
     ("interp8_digit", "cst<T>(49) * phi(-2) - cst<T>(245) * phi(-1)", "cst<T>(49) * phi(-2) - cst<T>(254) * phi(-1)",
      [EUL + "test_metrics_exact_on_affine_grid[True-4]", EUL + "test_metrics_exact_on_polynomial_grid[4]"]),
+    ("cand4_index", "tab4.b[k][l] * uj[k + l - 3]", "tab4.b[k][l] * uj[k + l - 2]",
+     [EUL + "test_free_stream_preservation_randomized_grid[0-4]", EUL + "test_mirror_symmetry[4]"]),
+    ("is4_scale", "cst<T>(IS4[q][a][b] / 2880.0L)", "cst<T>(IS4[q][a][b] / 2800.0L)",
+     [W7 + "test_r4_indicators_follow_the_definition"]),
     ("is4_symmetric_digit", "{-31718, 45076, -16958}", "{-31718, 45067, -16958}",
      [W7 + "test_r4_indicators_follow_the_definition"]),
     # boundary rules, ghost coordinates and linked faces (readings)
@@ -165,6 +175,9 @@ MUTANTS = [
      [EUL + "test_rk3_third_order_in_time", EUL + "test_sod_against_exact_solution[0]"]),
     ("rk3_last_stage", "cst<T>(2.0L / 3) * (Q2[k] + dt * R[k]);", "cst<T>(2.0L / 3) * (Q2[k] + dt * R[k] * cst<T>(0.5L));",
      [EUL + "test_rk3_third_order_in_time", EUL + "test_sod_against_exact_solution[0]"]),
+    ("cfl_one_direction", "spectral(q, F.met(2, i, j), F.met(3, i, j), P.gamma)) / F.met(4, i, j);",
+     "T(0) * spectral(q, F.met(2, i, j), F.met(3, i, j), P.gamma)) / F.met(4, i, j);",
+     [EUL + "test_line_lambda_closed_form"]),
     ("cfl_invert", "return cfl / best;", "return cfl * best;",
      [EUL + "test_line_lambda_closed_form", EUL + "test_sod_against_exact_solution[0]"]),
 ]
