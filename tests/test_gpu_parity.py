@@ -117,9 +117,11 @@ def test_rhs_parity_transmissive_riemann(F, scheme):
 
 def test_rhs_parity_boundary_kinds(F):
     x, y, per, q = _riemann(48, seed=3)
-    free = I.conservative(1.0, 0.8, 0.3, 1.0 / GAMMA)
-    st = np.tile(free, (4, 1))
-    for bc in [(2, 2, 3, 3), (4, 4, 4, 4), (3, 4, 2, 1), (1, 3, 4, 2)]:
+    # a different state on every face, so that each face must read its own (the far-field
+    # velocities enter through some faces and leave through others)
+    st = np.stack([I.conservative(1.0, 0.8, 0.3, 1.0 / GAMMA), I.conservative(1.1, 0.7, 0.2, 0.8),
+                   I.conservative(0.9, -0.5, 0.1, 0.75), I.conservative(1.05, 0.6, -0.3, 0.7)])
+    for bc in [(2, 2, 3, 3), (4, 4, 4, 4), (3, 4, 2, 1), (1, 3, 4, 2), (2, 2, 2, 2)]:
         for scheme in (1, 2):
             _check_case(F, _cfg(scheme=scheme, bc=bc, bc_state=st), x, y, q)
     # periodic in one direction, walls in the other
