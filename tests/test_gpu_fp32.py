@@ -55,8 +55,10 @@ def test_fp32_rhs_vortex_256(F, prec, scheme):
 def test_fp32_rhs_riemann_and_boundaries(F, prec):
     x, y = I.riemann_grid(96, 0.3, 1811)
     q = I.riemann_quadrants(x, y)
-    st = np.tile(I.conservative(1.0, 0.8, 0.3, 1.0 / GAMMA), (4, 1))
-    for bc in [(1, 1, 1, 1), (2, 3, 4, 1)]:
+    # a different state on every face, so that each face must read its own
+    st = np.stack([I.conservative(1.0, 0.8, 0.3, 1.0 / GAMMA), I.conservative(1.1, 0.7, 0.2, 0.8),
+                   I.conservative(0.9, -0.5, 0.1, 0.75), I.conservative(1.05, 0.6, -0.3, 0.7)])
+    for bc in [(1, 1, 1, 1), (2, 3, 4, 1), (4, 2, 2, 4)]:
         for scheme in (0, 3):
             assert _run(F, dict(scheme=scheme, bc=bc, bc_state=st), x, y, q, prec) < BOUND[prec]
 
