@@ -118,3 +118,35 @@ def test_batch_argument_validation_on_the_host(so):
     blk[1] = fsp._block_shape(cfg, 16, 12)
     assert L.fsp_batch_create(ctypes.byref(cfg._c()), 2, blk, bad, links, ctypes.byref(h)) == 1
     assert not h.value
+
+
+def _prototypes():
+    """name -> list of parameter declarations, from the header's prototypes."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(fsp_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", text):
+        params = [p.strip() for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(1)] = params
+    return out
+
+
+def test_binding_argument_lists_match_the_header(so):
+    from paper_1810_11103_gb300 import fsp
+    L = fsp.lib()
+    scalar = {"int": ctypes.c_int, "double": ctypes.c_double, "long long": ctypes.c_longlong,
+              "size_t": ctypes.c_size_t}
+    checked = 0
+    for name, params in _prototypes().items():
+        f = getattr(L, name)
+        if f.argtypes is None:      # not used by the binding
+            continue
+        assert len(f.argtypes) == len(params), (name, params, f.argtypes)
+        for decl, t in zip(params, f.argtypes):
+            if "*" in decl:
+                assert t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer), (name, decl, t)
+            else:
+                base = re.sub(r"\b(const)\b", "", decl).rsplit(None, 1)[0].strip()
+                if base in scalar:
+                    assert t is scalar[base], (name, decl, t)
+        checked += 1
+    assert checked >= 30
