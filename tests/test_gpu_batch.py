@@ -123,6 +123,28 @@ def test_batch_reversed_links(F):
     bt.close()
 
 
+def test_batch_full_size_cylinder_float_paths(F):
+    # FP32 and mixed at full size, the tuner's marching passes and the tiles, against the
+    # oracle on the float-rounded state, under the bounds of the float tests (1e-4, 5e-5).
+    # Float round-off grows with max|flux| / max|flux difference|: 7.5 here against 43 on
+    # the 256 x 256 vortex (measured 3.8e-5 and 2.2e-5 there), so about 7e-6 and 4e-6 are
+    # expected.
+    blocks, states, free = I.cylinder_blocks()
+    qs = [q.astype(np.float32).astype(np.float64) for q in _perturbed(states, 11, 0.02)]
+    cfgd = _cfgd(free, 2)
+    Ms = O.mb_metrics(cfgd, blocks)
+    Ro = O.mb_rhs(cfgd, blocks, Ms, qs)
+    for prec, bound in ((1, 1e-4), (2, 5e-5)):
+        bt = F.Batch(F.Config.from_dict(dict(cfgd, precision=prec)), blocks, qs)
+        for k in range(len(blocks)):
+            bt.M[k].copy_(torch.as_tensor(Ms[k]))
+        for v in (3, 2):
+            bt.set_tile_shape(0, v)
+            bt.set_tile_shape(1, v)
+            assert _maxrel([r.double().cpu().numpy() for r in bt.rhs()], Ro) < bound, (prec, v)
+        bt.close()
+
+
 @pytest.mark.parametrize("prec,bound", [(1, 1e-4), (2, 5e-5)])
 @pytest.mark.parametrize("scheme", [2, 3])
 def test_batch_fp32_paths(F, prec, bound, scheme):
