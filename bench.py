@@ -11,10 +11,11 @@ graph through fsp_batch_rk3_step.  Metric: Mcell-RHS/s = nodes x right-hand side
                     [--no-all-precisions] [--no-cpu-baseline] [--accuracy none|quick|full]
 
 The headline `value` is the FP64 path.  Beside it: the FP32 and mixed FP32/FP64 paths of the
-same workload ("fp32", "fp32_mixed"), each with its own roofline, and the same FP64 step as a
-loop of per-block fsp_rk3_step calls ("per_block_fp64", links read as transmissive).
-Beside them ("accuracy"): final-time density errors of each precision on the 256 x 256 vortex
-(and with --accuracy full the 1024 x 1024 Riemann problem) and the free-stream residual.
+same workload ("fp32", "fp32_mixed"), each with its own roofline, and the same FP64 and FP32
+steps as loops of per-block fsp_rk3_step calls ("per_block_fp64", "fp32.per_block", links read
+as transmissive).  With --accuracy quick|full ("accuracy"): final-time density errors of each
+precision on the 256 x 256 vortex (full adds the 1024 x 1024 Riemann problem) and the
+free-stream residual.  The line ends with "summary", the compact figures of every path.
 Under torchrun every rank runs the workload on its own GPU (independent problems, weak
 scaling, no data-path collective); rank 0 prints one JSON line.
 """
@@ -58,7 +59,7 @@ def parse():
     ap.add_argument("--seventh", action=argparse.BooleanOptionalAction, default=True,
                     help="also measure WENOIU7-1MP (the Appendix's seventh-order scheme) on the same workload, "
                          "FP64 and FP32")
-    ap.add_argument("--accuracy", choices=["none", "quick", "full"], default="quick",
+    ap.add_argument("--accuracy", choices=["none", "quick", "full"], default="none",
                     help="final-time errors per precision: quick = the 256 x 256 vortex over one period and "
                          "the free-stream residual; full adds the 1024 x 1024 Riemann problem to t = 0.3")
     ap.add_argument("--tune-table", default=None,
@@ -70,10 +71,13 @@ def parse():
                          "choice on this workload), set without timing")
     ap.add_argument("--profile-dir", type=int, default=0, choices=[0, 1],
                     help="profiling run: the direction whose batched sweep is launched three times")
-    ap.add_argument("--profile", choices=list(PRECISIONS) + ["adjoint"], default=None,
+    ap.add_argument("--profile", choices=list(PRECISIONS) + ["adjoint", "probe"], default=None,
                     help="profiling run for ncu: build the cylinder batch in this precision, evaluate one "
                          "right-hand side, then launch the batched xi sweep three times; 'adjoint': three "
-                         "fsp_rhs_vjp calls on the 512 x 512 shock-vortex case; no timing")
+                         "fsp_rhs_vjp calls on the 512 x 512 shock-vortex case; 'probe': the FP64 and the "
+                         "FP32 FMA probe once each, as the bench launches them; no timing")
+    ap.add_argument("--per-block", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the FP64 and FP32 steps as loops of per-block fsp_rk3_step calls")
     return ap.parse_args()
 
 
@@ -338,14 +342,26 @@ class Ctx:
         self.barrier()
         return sum(a.elapsed_time(b) for a, b in ev) / 1e3
 
+    def sm_count(self):
+        return int(self.torch.cuda.get_device_properties(self.dev).multi_processor_count)
+
     def peak(self, prec):
+        """FMA rate of the path's pipe measured by fsp_fma_peak (8 resident 256-thread CTAs
+        per SM of this device, 8 independent FMA chains per thread), in TFLOP/s."""
         fsp, torch = self.fsp, self.torch
         pipe = 0 if prec == "fp64" else 1
-        blocks, iters = 152 * 8, 4096 if pipe == 0 else 65536
+        blocks, iters = self.sm_count() * 8, 4096 if pipe == 0 else 65536
         sink = torch.empty(blocks * 256, dtype=torch.float64 if pipe == 0 else torch.float32, device=self.dev)
         fsp.fma_peak(pipe, blocks, iters, sink)
         t = self.timed(lambda: fsp.fma_peak(pipe, blocks, iters, sink), 3) / 3
         return 2.0 * 8 * iters * blocks * 256 / t / 1e12, ("FP64" if pipe == 0 else "FP32")
+
+    def nominal(self, prec, mhz):
+        """Nominal FMA rate at the SM clock sampled during the run: SMs x FMA lanes per SM per
+        clock x 2 flops x clock (FP64: 2 lanes per SM on this part, the 1.25 TFLOP/s of its
+        data sheet at 2.07 GHz; FP32: 128 lanes)."""
+        lanes = 2 if prec == "fp64" else 128
+        return self.sm_count() * lanes * 2.0 * (mhz or 2070.0) * 1e6 / 1e12
 
     def max_over_ranks(self, *vals):
         if self.world == 1:
@@ -404,14 +420,16 @@ def measure_cylinder(args, prec, C, per_block=False):
     rhs_total = job_rhs(nodes, args.steps, C.world)
     kname = ("march_batch_kernel xi (marching warps)" if tiles["xi"]["variant"] == 3 else "sweep_batch_kernel xi") \
         + ", all 64 blocks (fsp_batch_flux_difference dir 0)"
+    nom = C.nominal(prec, clk.get("sm_mhz"))
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic_of(args, prec, tiles["xi"]["variant"]),
             "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
+            "nominal_peak": nom, "frac_vs_nominal": achieved / nom,
             "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
             "kernel_ms": 1e3 * t_k}
     if prec == "mixed":
-        roof = mixed_roofline(args, C, roof, fl["sweep_xi_per_node"], nodes, t_k)
+        roof = mixed_roofline(args, C, roof, fl["sweep_xi_per_node"], nodes, t_k, clk.get("sm_mhz"))
     out = {
         "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps, "nodes": nodes,
         "nblocks": len(blocks),
@@ -422,7 +440,7 @@ def measure_cylinder(args, prec, C, per_block=False):
         "tiles": tiles,
     }
     if per_block:
-        # the same FP64 step as a loop of single-block calls (links read as transmissive)
+        # the same step as a loop of single-block calls (links read as transmissive)
         cbs, wss = [], []
         for k, b in enumerate(blocks):
             cb = fsp.Config.from_dict(dict(cfgd, bc=[1 if c == LINK else c for c in b["bc"]]))
@@ -435,9 +453,9 @@ def measure_cylinder(args, prec, C, per_block=False):
         loop()
         reps = max(3, args.steps // 4)
         t_loop = C.timed(loop, reps)
-        out["per_block_fp64"] = {"value": nodes * 3 * reps / t_loop / 1e6, "unit": UNIT,
-                                 "ms_per_step": 1e3 * t_loop / reps,
-                                 "how": "64 fsp_rk3_step calls per step, one block each, eager launches"}
+        out["per_block"] = {"value": nodes * 3 * reps / t_loop / 1e6, "unit": UNIT,
+                            "ms_per_step": 1e3 * t_loop / reps,
+                            "how": "64 fsp_rk3_step calls per step, one block each, eager launches"}
     bt.close()
     return out
 
@@ -452,7 +470,7 @@ def measure_cylinder(args, prec, C, per_block=False):
 MIXED_FP64_FLOPS = {0: 70, 1: 86, 2: 90, 3: 106, 4: 108}
 
 
-def mixed_roofline(args, C, roof, flops_node, nodes, t_k):
+def mixed_roofline(args, C, roof, flops_node, nodes, t_k, mhz):
     """Roofline of the mixed path: t_roof = max(FP32 flops / FP32 peak, FP64 flops / FP64
     peak); the FP64 part bounds it.  The FP32 part is the rest of the algorithmic count."""
     f64 = MIXED_FP64_FLOPS[args.scheme]
@@ -460,13 +478,17 @@ def mixed_roofline(args, C, roof, flops_node, nodes, t_k):
     p64, _ = C.peak("fp64")
     p32 = roof["peak"]
     t32, t64 = f32 * nodes / (p32 * 1e12), f64 * nodes / (p64 * 1e12)
+    n32, n64 = C.nominal("fp32", mhz), C.nominal("fp64", mhz)
     part32 = {"flops_per_node": f32, "achieved": f32 * nodes / t_k / 1e12, "peak": p32,
-              "frac": f32 * nodes / t_k / 1e12 / p32}
+              "frac": f32 * nodes / t_k / 1e12 / p32, "nominal_peak": n32,
+              "frac_vs_nominal": f32 * nodes / t_k / 1e12 / n32}
     part64 = {"flops_per_node": f64, "achieved": f64 * nodes / t_k / 1e12, "peak": p64,
-              "frac": f64 * nodes / t_k / 1e12 / p64}
+              "frac": f64 * nodes / t_k / 1e12 / p64, "nominal_peak": n64,
+              "frac_vs_nominal": f64 * nodes / t_k / 1e12 / n64}
     head, other = (part64, part32) if t64 >= t32 else (part32, part64)
     out = dict(roof)
     out.update({"bound": "alu", "achieved": head["achieved"], "peak": head["peak"], "frac": head["frac"],
+                "nominal_peak": head["nominal_peak"], "frac_vs_nominal": head["frac_vs_nominal"],
                 "flops_per_node": head["flops_per_node"],
                 "part": "FP64 part" if head is part64 else "FP32 part",
                 "peak_source": ("FP64" if head is part64 else "FP32") + " FMA probe (fsp_fma_peak) in this run",
@@ -509,12 +531,14 @@ def measure_vortex(args, prec, C):
     achieved = fl["sweep_xi_per_node"] * nodes / t_k / 1e12
     rhs_total = job_rhs(nodes, args.steps, C.world)
     sb = Q.numel() * Q.element_size()
+    nom = C.nominal(prec, clk.get("sm_mhz"))
     return {
         "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps, "nodes": nodes, "nblocks": 1,
         "e2e": {"value": rhs_total / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": sb, "d2h_bytes_per_step": sb},
         "roofline": {"bound": "alu", "kernel": "sweep_kernel xi (fsp_flux_difference dir 0)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_of(args, prec, -1),
                      "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
+                     "nominal_peak": nom, "frac_vs_nominal": achieved / nom,
                      "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
                      "kernel_ms": 1e3 * t_k},
         "clocks": clk,
@@ -715,10 +739,61 @@ def profile_adjoint(args):
     print("profile run done: adjoint, 262144 nodes")
 
 
+def _r(v, d=4):
+    return None if v is None else float(f"{v:.{d}g}")
+
+
+def summary(args, head, others, adjoint, seventh):
+    """Compact per-path figures: Mcell-RHS/s, ms per RK3 step, the roofline kernel's fraction of
+    the measured and of the nominal FMA rate, and the per-block loop with the batching gain."""
+    out = {}
+    for p, r in [(args.precision, head)] + list(others.items()):
+        rf = r["roofline"]
+        e = {"value": _r(r["value"]), "ms_step": _r(r["ms_per_step"]), "e2e": _r(r["e2e"]["value"]),
+             "frac": _r(rf["frac"], 3), "frac_nominal": _r(rf.get("frac_vs_nominal"), 3),
+             "xi_ms": _r(rf["kernel_ms"])}
+        if p == "mixed":
+            e["part"] = rf.get("part")
+        if r.get("per_block"):
+            e["per_block"] = _r(r["per_block"]["value"])
+            e["batch_gain"] = _r(r["value"] / r["per_block"]["value"], 3)
+        out["fp32_mixed" if p == "mixed" else p] = e
+    if adjoint is not None:
+        out["adjoint"] = {"rhs": _r(adjoint["rhs_vjp_over_rhs"], 3), "rk3": _r(adjoint["rk3_step_vjp_over_rk3_step"], 3),
+                          "grad_ckpt": _r(adjoint["gradient_over_forward"], 3),
+                          "grad_tape": _r(adjoint["full_tape"]["gradient_over_forward"], 3)}
+        if adjoint.get("roofline"):
+            out["adjoint"]["frac"] = _r(adjoint["roofline"]["frac"], 3)
+    if seventh is not None:
+        out["wenoiu7"] = {p: {"value": _r(seventh[p]["value"]), "frac": _r(seventh[p]["roofline"]["frac"], 3)}
+                          for p in ("fp64", "fp32")}
+    return out
+
+
+def profile_probe(args):
+    """Minimal launch sequence for a profiler: the FP64 FMA probe, then the FP32 one, each once
+    with the launch shape of the bench's roofline peak."""
+    import torch
+    from paper_1810_11103_gb300 import build as B
+    B.build()
+    from paper_1810_11103_gb300 import fsp
+    dev = torch.device("cuda", 0)
+    C = Ctx(torch, fsp, None, dev, 1)
+    blocks = C.sm_count() * 8
+    for pipe, iters, dt in ((0, 4096, torch.float64), (1, 65536, torch.float32)):
+        sink = torch.empty(blocks * 256, dtype=dt, device=dev)
+        fsp.fma_peak(pipe, blocks, iters, sink)
+    torch.cuda.synchronize()
+    print(f"profile run done: FMA probes, {blocks} CTAs of 256 threads")
+
+
 def main():
     args = parse()
     if args.profile == "adjoint":
         profile_adjoint(args)
+        return
+    if args.profile == "probe":
+        profile_probe(args)
         return
     if args.profile:
         profile_run(args, args.profile)
@@ -744,7 +819,7 @@ def main():
 
     def measure(prec, head=False):
         if args.workload == "cylinder64":
-            return measure_cylinder(args, prec, C, per_block=head and prec == "fp64")
+            return measure_cylinder(args, prec, C, per_block=args.per_block and prec in ("fp64", "fp32"))
         return measure_vortex(args, prec, C)
 
     head = measure(args.precision, head=True)
@@ -780,20 +855,24 @@ def main():
         }
         if head.get("tiles"):
             line["config"]["tiles"] = head["tiles"]
-        for p, r in others.items():
-            line["fp32_mixed" if p == "mixed" else p] = {
-                "value": r["value"], "unit": UNIT, "dtype": DTYPES[p], "ms_per_step": r["ms_per_step"],
-                "e2e": r["e2e"]["value"], "roofline": r["roofline"], "clocks": r["clocks"], "tiles": r.get("tiles")}
-        if "per_block_fp64" in head:
-            line["per_block_fp64"] = head["per_block_fp64"]
-        if adjoint is not None:
-            line["adjoint"] = adjoint
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args)
+        # the bulky tables first ...
         if accuracy is not None:
             line["accuracy"] = accuracy
         if seventh is not None:
             line["wenoiu7"] = seventh
-        if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args)
+        if adjoint is not None:
+            line["adjoint"] = adjoint
+        for p, r in others.items():
+            line["fp32_mixed" if p == "mixed" else p] = {
+                "value": r["value"], "unit": UNIT, "dtype": DTYPES[p], "ms_per_step": r["ms_per_step"],
+                "e2e": r["e2e"]["value"], "roofline": r["roofline"], "clocks": r["clocks"], "tiles": r.get("tiles"),
+                "per_block": r.get("per_block")}
+        if "per_block" in head:
+            line["per_block_" + args.precision] = head["per_block"]
+        # ... and a compact summary of every path last
+        line["summary"] = summary(args, head, others, adjoint, seventh)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -283,6 +283,16 @@ fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const do
 fsp_status fsp_fma_peak(int precision, int blocks, int iters, void* sink, void* stream);
 
 /*
+ * fsp_round_to_float -- diagnostic of the FP32 paths' double-to-float rounding: for each of
+ * the n doubles in[k] (device), out_int[k] receives the rounding done with integer operations
+ * (the mixed path keeps its float-double conversions off the FP64 pipe) and out_hw[k] the
+ * hardware conversion (round to nearest even).  They agree except that the integer rounding
+ * flushes results below the float normal range to signed zero.  No counterpart in the paper.
+ * FSP_ERR_INVALID_ARG for n < 0 or a pointer that is not device memory.
+ */
+fsp_status fsp_round_to_float(const double* in, float* out_int, float* out_hw, long long n, void* stream);
+
+/*
  * ---- Multi-block grids --------------------------------------------------------------
  * The paper's motivating case (Section 1): many structured blocks, of uneven sizes,
  * joined face to face.  The blocks partition the nodes of one larger grid: behind a face

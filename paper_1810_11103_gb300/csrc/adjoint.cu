@@ -547,18 +547,7 @@ VjpWs vjp_ws(const fsp_config& c, const fsp_block& b, size_t fwd_bytes) {
 }
 
 Params params_of(const fsp_config& c, const fsp_block& b, const double* metrics) {
-  Params P;
-  std::memset(&P, 0, sizeof(P));
-  P.ni = b.ni; P.nj = b.nj; P.ld = b.ld;
-  for (int f = 0; f < 4; ++f) P.bc[f] = c.bc[f];
-  P.interp = c.interp; P.ppm = c.ppm; P.linw = c.linear_weights;
-  P.gamma = c.gamma; P.alpha = c.lf_alpha; P.eps = c.eps;
-  for (int f = 0; f < 4; ++f)
-    for (int v = 0; v < 4; ++v) P.bcq[f][v] = c.bc_state[f][v];
-  P.met = metrics;
-  P.mld = (long long)b.ni + 2 * G;
-  P.mplane = P.mld * ((long long)b.nj + 2 * G);
-  return P;
+  return make_params(c, b, metrics);
 }
 
 #define TRY(expr) \

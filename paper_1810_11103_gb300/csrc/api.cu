@@ -63,6 +63,18 @@ fsp_status check_cfg(const fsp_config* c, const fsp_block* b) {
   return FSP_OK;
 }
 
+fsp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FSP_OK : FSP_ERR_CUDA; }
+
+#define FSP_TRY(expr)                                  \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return FSP_ERR_CUDA;        \
+  } while (0)
+
+}  // namespace
+
+namespace fsp {
+
 Params make_params(const fsp_config& c, const fsp_block& b, const double* metrics) {
   Params P;
   std::memset(&P, 0, sizeof(P));
@@ -78,15 +90,12 @@ Params make_params(const fsp_config& c, const fsp_block& b, const double* metric
   return P;
 }
 
-fsp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FSP_OK : FSP_ERR_CUDA; }
+fsp_status rhs_status(cudaError_t e) {
+  if (e == cudaErrorNotSupported) return FSP_ERR_UNSUPPORTED;
+  return e == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
+}
 
-#define FSP_TRY(expr)                                  \
-  do {                                                 \
-    cudaError_t e_ = (expr);                           \
-    if (e_ != cudaSuccess) return FSP_ERR_CUDA;        \
-  } while (0)
-
-}  // namespace
+}  // namespace fsp
 
 extern "C" {
 
@@ -151,10 +160,8 @@ static fsp_status rhs_eval(const fsp_config& c, const fsp_block& b, const double
   const Params P = make_params(c, b, metrics);
   FSP_TRY(cudaMemsetAsync(lam, 0, sizeof(double) * (b.ni + b.nj), st));
   FSP_TRY(launch_lambda(P, c.precision, Q, lam, lam + b.nj, nullptr, st));
-  cudaError_t e = launch_rhs(c.scheme, c.precision, P, Q, lam, lam + b.nj, ws + L.racc, out, mode, Qn,
-                             ca, cb, dt, st);
-  if (e == cudaErrorNotSupported) return FSP_ERR_UNSUPPORTED;
-  return cuda_status(e);
+  return rhs_status(launch_rhs(c.scheme, c.precision, P, Q, lam, lam + b.nj, ws + L.racc, out, mode, Qn,
+                               ca, cb, dt, st));
 }
 
 fsp_status fsp_rhs(const fsp_config* cfg, const fsp_block* blk, const double* metrics,
@@ -234,6 +241,13 @@ fsp_status fsp_fma_peak(int precision, int blocks, int iters, void* sink, void* 
     return FSP_ERR_INVALID_ARG;
   if (!device_pointer(sink)) return FSP_ERR_INVALID_ARG;
   return cuda_status(launch_fma_peak(precision, blocks, iters, sink, (cudaStream_t)stream));
+}
+
+fsp_status fsp_round_to_float(const double* in, float* out_int, float* out_hw, long long n, void* stream) {
+  if (n < 0) return FSP_ERR_INVALID_ARG;
+  if (n == 0) return FSP_OK;
+  if (!device_pointer(in) || !device_pointer(out_int) || !device_pointer(out_hw)) return FSP_ERR_INVALID_ARG;
+  return cuda_status(launch_round_to_float(in, out_int, out_hw, n, (cudaStream_t)stream));
 }
 
 }  // extern "C"

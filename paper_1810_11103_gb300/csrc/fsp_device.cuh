@@ -182,8 +182,8 @@ __device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
 
 // A double rounded to the state type.  from_f64<float> is the hardware conversion (round to
 // nearest even).  from_f64_int rounds the same way with integer operations only (zero and
-// subnormals to signed zero, overflow to infinity), for the mixed path, whose FP64 pipe is its
-// bottleneck.
+// subnormals to signed zero, overflow to infinity, NaN to a quiet NaN, infinity kept), for the
+// mixed path, whose FP64 pipe is its bottleneck.
 template <typename T> __device__ __forceinline__ T from_f64(double d);
 template <> __device__ __forceinline__ double from_f64<double>(double d) { return d; }
 template <> __device__ __forceinline__ float from_f64<float>(double d) { return __double2float_rn(d); }
@@ -191,7 +191,9 @@ __device__ __forceinline__ float from_f64_int(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
   const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex == 0x7ffu && ((hi & 0xfffffu) | lo)) return __uint_as_float(sign | 0x7fc00000u);   // NaN
+  const int e = (int)ex - 1023 + 127;
   if (e <= 0) return __uint_as_float(sign);
   if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
   unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 of the 52 mantissa bits

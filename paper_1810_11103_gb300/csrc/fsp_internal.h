@@ -8,6 +8,13 @@
 
 namespace fsp {
 
+// Kernel parameters of one block from the public configuration (host side).
+Params make_params(const fsp_config& cfg, const fsp_block& blk, const double* metrics);
+
+// Status of a right-hand-side launch sequence: a scheme/precision pair without kernels
+// (cudaErrorNotSupported) is FSP_ERR_UNSUPPORTED, any other failure FSP_ERR_CUDA.
+fsp_status rhs_status(cudaError_t e);
+
 // Launchers (enqueue only; return the launch status).
 cudaError_t launch_metrics(const fsp_config& cfg, const fsp_block& blk, const double* x,
                            const double* y, double* M, cudaStream_t st);
@@ -37,5 +44,6 @@ cudaError_t launch_norms(const fsp_block& blk, int precision, const void* A, con
                          double* out, cudaStream_t st);
 
 cudaError_t launch_fma_peak(int precision, int blocks, int iters, void* sink, cudaStream_t st);
+cudaError_t launch_round_to_float(const double* in, float* oi, float* oh, long long n, cudaStream_t st);
 
 }  // namespace fsp

@@ -14,7 +14,6 @@
 // (different streams, or different host threads on one device) race on it and must be
 // serialised by the caller.  The array keeps the previous call's contents; the per-line
 // maxima are cleared at the start of every call, and the accumulator is fully overwritten.
-#include <cstring>
 #include <mutex>
 
 #include "fsp_internal.h"
@@ -35,7 +34,9 @@ void* g_addr[kMaxDevices] = {};
 
 // Device address of `scratch` on the current device, looked up on the first call per
 // device (the lookup may load the module, so that first call must not be inside a stream
-// capture).
+// capture).  The address is cached per device index for the primary context: a caller that
+// resets the device (cudaDeviceReset) or switches to another context between calls would be
+// handed a stale address, so such callers must not use this entry point across a reset.
 fsp_status scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FSP_ERR_CUDA;
@@ -84,23 +85,12 @@ extern "C" fsp_status fsp_rhs_noalloc(const fsp_config* cfg, const fsp_block* bl
   double* lam = static_cast<double*>(base);
   void* acc = static_cast<char*>(base) + acc_off;
 
-  Params P;
-  std::memset(&P, 0, sizeof(P));
-  P.ni = blk->ni; P.nj = blk->nj; P.ld = blk->ld;
-  for (int f = 0; f < 4; ++f) P.bc[f] = cfg->bc[f];
-  P.interp = cfg->interp; P.ppm = cfg->ppm; P.linw = cfg->linear_weights;
-  P.gamma = cfg->gamma; P.alpha = cfg->lf_alpha; P.eps = cfg->eps;
-  for (int f = 0; f < 4; ++f)
-    for (int v = 0; v < 4; ++v) P.bcq[f][v] = cfg->bc_state[f][v];
-  P.met = metrics;
-  P.mld = (long long)blk->ni + 2 * G;
-  P.mplane = P.mld * ((long long)blk->nj + 2 * G);
+  const Params P = make_params(*cfg, *blk, metrics);
 
   cudaStream_t st = (cudaStream_t)stream;
   // the maxima are accumulated by atomic max and must start at zero on every call
   if (cudaMemsetAsync(lam, 0, lam_bytes, st) != cudaSuccess) return FSP_ERR_CUDA;
   if (launch_lambda(P, cfg->precision, Q, lam, lam + blk->nj, nullptr, st) != cudaSuccess) return FSP_ERR_CUDA;
-  cudaError_t e = launch_rhs(cfg->scheme, cfg->precision, P, Q, lam, lam + blk->nj, acc, dQdt, 0, nullptr,
-                             0.0, 0.0, 0.0, st);
-  return e == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
+  return rhs_status(launch_rhs(cfg->scheme, cfg->precision, P, Q, lam, lam + blk->nj, acc, dQdt, 0, nullptr,
+                               0.0, 0.0, 0.0, st));
 }

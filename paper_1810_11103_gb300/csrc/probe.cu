@@ -20,6 +20,18 @@ __global__ void __launch_bounds__(256) fma_peak_kernel(int iters, T* sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void round_to_float_kernel(const double* in, float* oi, float* oh, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    oi[k] = from_f64_int(in[k]);
+    oh[k] = __double2float_rn(in[k]);
+  }
+}
+
+cudaError_t launch_round_to_float(const double* in, float* oi, float* oh, long long n, cudaStream_t st) {
+  if (n > 0) round_to_float_kernel<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(in, oi, oh, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fma_peak(int precision, int blocks, int iters, void* sink, cudaStream_t st) {
   if (precision == FSP_FP64)
     fma_peak_kernel<double><<<blocks, 256, 0, st>>>(iters, static_cast<double*>(sink));

@@ -109,12 +109,14 @@ def lib():
                 "fsp_metrics": (ctypes.c_int, [C, B, _P, _P, _P, _P]),
                 "fsp_line_lambda": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P]),
                 "fsp_rhs": (ctypes.c_int, [C, B, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+                "fsp_rhs_noalloc": (ctypes.c_int, [C, B, _P, _P, _P, _P]),
                 "fsp_flux_difference": (ctypes.c_int, [C, B, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
                 "fsp_rk3_step": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, ctypes.c_size_t, _P]),
                 "fsp_cfl_dt": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_norms": (ctypes.c_int, [B, ctypes.c_int, _P, _P, _P, _P]),
                 "fsp_check_state": (ctypes.c_int, [C, B, _P, _P, _P]),
                 "fsp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+                "fsp_round_to_float": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
                 "fsp_vjp_workspace_size": (ctypes.c_int, [C, B, ctypes.POINTER(ctypes.c_size_t)]),
                 "fsp_rhs_vjp": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_rk3_step_vjp": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -305,6 +307,22 @@ def rhs(cfg: Config, M: torch.Tensor, Q: torch.Tensor, out=None, ws=None, stream
     return out
 
 
+def rhs_noalloc_status(cfg: Config, M: torch.Tensor, Q: torch.Tensor, out: torch.Tensor, stream=None) -> int:
+    """fsp_rhs_noalloc: the right-hand side with the library's fixed scratch array instead of a
+    workspace (for callers that cannot allocate device memory).  Returns the status code."""
+    b = block_of(cfg, Q)
+    return int(lib().fsp_rhs_noalloc(ctypes.byref(cfg._c()), ctypes.byref(b), _ptr(M), _ptr(Q), _ptr(out),
+                                     _stream(stream)))
+
+
+def rhs_noalloc(cfg: Config, M: torch.Tensor, Q: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """The same as rhs() through fsp_rhs_noalloc (raises on a nonzero status)."""
+    if out is None:
+        out = torch.empty_like(Q)
+    _check("fsp_rhs_noalloc", rhs_noalloc_status(cfg, M, Q, out, stream))
+    return out
+
+
 def flux_difference(cfg: Config, M: torch.Tensor, Q: torch.Tensor, lam: torch.Tensor, dir: int,
                     mode: int = 0, acc=None, out=None, stream=None) -> torch.Tensor:
     """One direction of the right-hand side (see fsp_flux_difference)."""
@@ -367,6 +385,15 @@ def raise_on_bad(cfg: Config, Q: torch.Tensor, stream=None) -> None:
         err = FspError("fsp_check_state", 4)
         err.node = (k // Q.shape[2], k % Q.shape[2])
         raise err
+
+
+def round_to_float(x: torch.Tensor, stream=None):
+    """(integer rounding, hardware rounding) of a float64 device tensor to float32."""
+    x = x.contiguous()
+    a, b = torch.empty(x.shape, dtype=torch.float32, device=x.device), torch.empty(x.shape, dtype=torch.float32,
+                                                                                     device=x.device)
+    _check("fsp_round_to_float", lib().fsp_round_to_float(_ptr(x), _ptr(a), _ptr(b), x.numel(), _stream(stream)))
+    return a, b
 
 
 def fma_peak(precision: int, blocks: int, iters: int, sink: torch.Tensor, stream=None):

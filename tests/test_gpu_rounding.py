@@ -1,0 +1,49 @@
+"""The integer double-to-float rounding of the float paths (`from_f64_int`, which keeps the
+mixed path's conversions off the FP64 pipe) against the hardware conversion and against
+numpy's round-to-nearest-even, through fsp_round_to_float: equal bit for bit on inputs in the
+float normal range and above (ties, the overflow edge, infinities); NaN stays NaN; inputs below
+the float normal range are flushed to signed zero by the integer rounding only."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1810_11103_gb300 import build, fsp
+    build.build()
+    return fsp
+
+
+def _cases():
+    fmax = float(np.finfo(np.float32).max)
+    ulp_top = 2.0 ** (127 - 23)                 # spacing of floats just below FLT_MAX
+    one_ulp = 2.0 ** -23
+    vals = [0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan, -np.nan,
+            fmax, -fmax, fmax + 0.25 * ulp_top, fmax + 0.5 * ulp_top, fmax + 0.75 * ulp_top, 1e300, -1e300,
+            1.0 + 0.5 * one_ulp, 1.0 + 1.5 * one_ulp,                 # ties to even: down, up
+            1.0 + 0.5 * one_ulp + 2.0 ** -60, -(1.0 + 1.5 * one_ulp),
+            float(np.finfo(np.float32).tiny), 2.0 ** -126 * (1 - 2.0 ** -25)]
+    rng = np.random.default_rng(1810)
+    rnd = rng.standard_normal(4096) * 10.0 ** rng.uniform(-30, 30, 4096)
+    return np.concatenate([np.array(vals, dtype=np.float64), rnd])
+
+
+def test_integer_rounding_matches_the_hardware(F):
+    x = _cases()
+    a, b = F.round_to_float(torch.as_tensor(x, device="cuda"))
+    torch.cuda.synchronize()
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32)
+    nan = np.isnan(x)
+    assert np.isnan(a[nan]).all() and np.isnan(b[nan]).all()
+    normal_or_big = ~nan & ((np.abs(x) >= np.finfo(np.float32).tiny) | (x == 0))
+    assert np.array_equal(a[normal_or_big].view(np.uint32), ref[normal_or_big].view(np.uint32))
+    assert np.array_equal(b[normal_or_big].view(np.uint32), ref[normal_or_big].view(np.uint32))
+    tiny = ~nan & ~normal_or_big
+    assert tiny.any()
+    assert (a[tiny] == 0).all() and np.array_equal(np.signbit(a[tiny]), np.signbit(x[tiny]))

@@ -3,8 +3,6 @@
 scratch is a fixed array inside the library.  Called through the C ABI, twice in a row on
 different states, it must match fsp_rhs (which takes a caller-allocated workspace) within
 the parity tolerance of the other GPU tests; a block too large for the array is refused."""
-import ctypes
-
 import numpy as np
 import pytest
 
@@ -21,19 +19,13 @@ TOL_RHS = 1e-12
 def F():
     from paper_1810_11103_gb300 import build, fsp
     build.build()
-    L = fsp.lib()
-    f = L.fsp_rhs_noalloc
-    f.restype = ctypes.c_int
-    f.argtypes = [ctypes.POINTER(fsp._Config), ctypes.POINTER(fsp._Block), ctypes.c_void_p, ctypes.c_void_p,
-                  ctypes.c_void_p, ctypes.c_void_p]
+    fsp.lib()
     return fsp
 
 
 def _noalloc(F, cfg, M, Q, out):
-    b = F.block_of(cfg, Q)
-    return F.lib().fsp_rhs_noalloc(ctypes.byref(cfg._c()), ctypes.byref(b), ctypes.c_void_p(M.data_ptr()),
-                                   ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    # the binding's argument list for fsp_rhs_noalloc is declared with the others in fsp.py
+    return F.rhs_noalloc_status(cfg, M, Q, out)
 
 
 def test_noalloc_matches_rhs_twice_in_a_row(F):
