@@ -18,6 +18,7 @@
 //   long double  higher precision; shows the free-stream residual is round-off
 //   Dual         forward-mode tangent (value + one directional derivative)
 //   Counted      counts floating-point operations (+ - * / sqrt, one each)
+//   Rev          reverse mode: tapes the operations, then accumulates adjoints backwards
 //
 // Conventions (identical in meaning, not in code, to the CUDA library):
 //   * nodes (i, j), i fastest; unit computational spacing (d xi = d eta = 1);
@@ -93,6 +94,84 @@ inline bool operator>=(Counted a, Counted b) { return a.v >= b.v; }
 inline Counted sqrt(Counted a) { ++g_flops; return Counted(std::sqrt(a.v)); }
 inline Counted fabs(Counted a) { return Counted(std::fabs(a.v)); }
 inline double val(Counted a) { return a.v; }
+
+// Reverse mode (the adjoint, a vector-Jacobian product).  Every operation whose result
+// depends on an active value appends one record to a tape: the indices of its at most two
+// active operands and the partial derivative of the result with respect to each, taken from
+// the values of this evaluation (the branches the evaluation takes are the ones
+// differentiated: the mapping branch, the boundary decisions, and a line maximum's lowest
+// maximising index).  Walking the tape backwards, each record passes its adjoint to its
+// operands, adjoint(operand) += partial * adjoint(result), which gives the transposed
+// Jacobian of the whole computation applied to a seed.  Elementary adjoints:
+//   c = a + b:  da += dc, db += dc           c = a - b:  da += dc, db -= dc
+//   c = a * b:  da += b dc, db += a dc       c = a / b:  da += dc / b, db -= (c / b) dc
+//   c = sqrt(a): da += dc / (2 c) (0 at a = 0)           c = |a|: the sign of a, +1 at 0
+// Constants (i < 0) record nothing.
+struct TapeRec { double pa, pb; int a, b; };
+static std::vector<TapeRec> g_tape;
+static long long g_rev_extra = 0;   // operations spent on partial derivatives (for the count)
+struct Rev {
+  double v;
+  int i;
+  Rev() : v(0), i(-1) {}
+  Rev(double a) : v(a), i(-1) {}
+  Rev(double a, int idx) : v(a), i(idx) {}
+};
+static inline Rev rev_rec(double v, int a, double pa, int b, double pb) {
+  if (a < 0 && b < 0) return Rev(v);
+  g_tape.push_back(TapeRec{pa, pb, a, b});
+  return Rev(v, (int)(g_tape.size() - 1));
+}
+static inline Rev rev_leaf(double v) {   // an independent variable: a record with no operands
+  g_tape.push_back(TapeRec{0.0, 0.0, -1, -1});
+  return Rev(v, (int)(g_tape.size() - 1));
+}
+inline Rev operator+(Rev a, Rev b) { return rev_rec(a.v + b.v, a.i, 1.0, b.i, 1.0); }
+inline Rev operator-(Rev a, Rev b) { return rev_rec(a.v - b.v, a.i, 1.0, b.i, -1.0); }
+inline Rev operator-(Rev a) { return rev_rec(-a.v, a.i, -1.0, -1, 0.0); }
+inline Rev operator*(Rev a, Rev b) { return rev_rec(a.v * b.v, a.i, b.v, b.i, a.v); }
+inline Rev operator/(Rev a, Rev b) {
+  const double q = a.v / b.v;
+  if (a.i >= 0 || b.i >= 0) g_rev_extra += 1 + (b.i >= 0);   // 1 / b, and q (1 / b) for b
+  return rev_rec(q, a.i, 1.0 / b.v, b.i, -q / b.v);
+}
+inline Rev& operator+=(Rev& a, Rev b) { a = a + b; return a; }
+inline Rev& operator-=(Rev& a, Rev b) { a = a - b; return a; }
+inline Rev& operator*=(Rev& a, Rev b) { a = a * b; return a; }
+inline bool operator<(Rev a, Rev b) { return a.v < b.v; }
+inline bool operator>(Rev a, Rev b) { return a.v > b.v; }
+inline bool operator<=(Rev a, Rev b) { return a.v <= b.v; }
+inline bool operator>=(Rev a, Rev b) { return a.v >= b.v; }
+inline Rev sqrt(Rev a) {
+  const double s = std::sqrt(a.v);
+  if (a.i >= 0) g_rev_extra += 1;                               // 0.5 / s
+  return rev_rec(s, a.i, s > 0 ? 0.5 / s : 0.0, -1, 0.0);
+}
+inline Rev fabs(Rev a) { return a.v >= 0 ? a : -a; }
+inline double val(Rev a) { return a.v; }
+
+// The reverse sweep: adj[k] holds the adjoint of tape record k on entry (the seeds) and the
+// accumulated adjoints on return.
+static void rev_sweep(std::vector<double>& adj) {
+  for (size_t k = g_tape.size(); k-- > 0;) {
+    const double g = adj[k];
+    if (g == 0.0) continue;
+    const TapeRec& r = g_tape[k];
+    if (r.a >= 0) adj[r.a] += r.pa * g;
+    if (r.b >= 0) adj[r.b] += r.pb * g;
+  }
+}
+
+// Operations of the reverse sweep taken densely (whatever the seed): one per operand edge
+// whose partial is +-1, two (a multiply-add) for any other partial.
+static long long rev_edge_flops() {
+  long long n = 0;
+  for (const TapeRec& r : g_tape) {
+    if (r.a >= 0) n += (r.pa == 1.0 || r.pa == -1.0) ? 1 : 2;
+    if (r.b >= 0) n += (r.pb == 1.0 || r.pb == -1.0) ? 1 : 2;
+  }
+  return n;
+}
 
 inline double val(double a) { return a; }
 inline double val(long double a) { return (double)a; }
@@ -1183,6 +1262,101 @@ int orc_riemann_exact(double gamma, const double* WL, const double* WR, double x
   return 0;
 }
 
+
+// ---- reverse mode (adjoints) ----
+// Each entry point tapes one evaluation with the Rev scalar (every input value a tape
+// leaf), seeds the outputs' adjoints and walks the tape backwards.  The outputs are
+// accumulated (+=) into the caller's arrays, which the caller zeroes.
+
+// Q_bar += (d dQ/dt / dQ)^T g and M_bar += (d dQ/dt / dM)^T g over the haloed metrics.
+int orc_rhs_vjp(const int* ip, const double* dp, int ni, int nj, const double* M, const double* Q,
+                const double* g, double* Qbar, double* Mbar) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<Rev> P; unpack(ip, dp, ni, nj, P);
+  const size_t NM = orc_metrics_len(ni, nj), NQ = 4 * (size_t)ni * nj;
+  g_tape.clear();
+  std::vector<Rev> Mr(NM), Qr(NQ), Rr(NQ);
+  for (size_t k = 0; k < NM; ++k) Mr[k] = rev_leaf(M[k]);
+  for (size_t k = 0; k < NQ; ++k) Qr[k] = rev_leaf(Q[k]);
+  rhs(P, Mr.data(), Qr.data(), Rr.data());
+  std::vector<double> adj(g_tape.size(), 0.0);
+  for (size_t k = 0; k < NQ; ++k)
+    if (Rr[k].i >= 0) adj[Rr[k].i] += g[k];
+  rev_sweep(adj);
+  for (size_t k = 0; k < NM; ++k) if (Mbar) Mbar[k] += adj[Mr[k].i];
+  for (size_t k = 0; k < NQ; ++k) Qbar[k] += adj[Qr[k].i];
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return 0;
+}
+
+// Reverse of one RK3 step from Q_n: on entry Qbar = dJ/dQ^{n+1}, on return dJ/dQ^n;
+// M_bar (nullable) += the step's metric adjoint.  dt is a constant.
+int orc_rk3_vjp(const int* ip, const double* dp, int ni, int nj, const double* M, const double* Qn, double dt,
+                double* Qbar, double* Mbar) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<Rev> P; unpack(ip, dp, ni, nj, P);
+  const size_t NM = orc_metrics_len(ni, nj), NQ = 4 * (size_t)ni * nj;
+  g_tape.clear();
+  std::vector<Rev> Mr(NM), Q0(NQ), Q(NQ);
+  for (size_t k = 0; k < NM; ++k) Mr[k] = rev_leaf(M[k]);
+  for (size_t k = 0; k < NQ; ++k) { Q0[k] = rev_leaf(Qn[k]); Q[k] = Q0[k]; }
+  rk3(P, Mr.data(), Q.data(), Rev(dt));
+  std::vector<double> adj(g_tape.size(), 0.0);
+  for (size_t k = 0; k < NQ; ++k)
+    if (Q[k].i >= 0) adj[Q[k].i] += Qbar[k];
+  rev_sweep(adj);
+  for (size_t k = 0; k < NM; ++k) if (Mbar) Mbar[k] += adj[Mr[k].i];
+  for (size_t k = 0; k < NQ; ++k) Qbar[k] = adj[Q0[k].i];
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return 0;
+}
+
+// x_bar += (d M / d x)^T M_bar, y_bar likewise (periodic offsets are constants).
+int orc_metrics_vjp(const int* ip, int ni, int nj, const double* period, const double* x, const double* y,
+                    const double* Mbar, double* xbar, double* ybar) {
+  if (int e = check(ip, ni, nj)) return e;
+  Par<Rev> P; double dp[19] = {1.4, 1.1, 1e-40};
+  unpack(ip, dp, ni, nj, P);
+  const size_t N = (size_t)ni * nj, NM = orc_metrics_len(ni, nj);
+  g_tape.clear();
+  std::vector<Rev> X(N), Y(N), Mr(NM);
+  for (size_t k = 0; k < N; ++k) { X[k] = rev_leaf(x[k]); Y[k] = rev_leaf(y[k]); }
+  Coords<Rev> C = make_coords(P, period, X.data(), Y.data());
+  metrics(P, C, Mr.data());
+  std::vector<double> adj(g_tape.size(), 0.0);
+  for (size_t k = 0; k < NM; ++k)
+    if (Mr[k].i >= 0) adj[Mr[k].i] += Mbar[k];
+  rev_sweep(adj);
+  for (size_t k = 0; k < N; ++k) { xbar[k] += adj[X[k].i]; ybar[k] += adj[Y[k].i]; }
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return 0;
+}
+
+// Operation count of one right-hand-side adjoint, dense in the seed: out = {the forward
+// right-hand side (as orc_count_flops), the partial derivatives the forward pass forms for
+// its divisions and square roots, the reverse sweep (rev_edge_flops), tape records}.
+int orc_count_vjp_flops(const int* ip, const double* dp, int ni, int nj, const double* M, const double* Q,
+                        long long* out) {
+  if (int e = check(ip, ni, nj)) return e;
+  out[0] = orc_count_flops(ip, dp, ni, nj, M, Q);
+  Par<Rev> P; unpack(ip, dp, ni, nj, P);
+  const size_t NM = orc_metrics_len(ni, nj), NQ = 4 * (size_t)ni * nj;
+  g_tape.clear();
+  g_rev_extra = 0;
+  std::vector<Rev> Mr(NM), Qr(NQ), Rr(NQ);
+  for (size_t k = 0; k < NM; ++k) Mr[k] = rev_leaf(M[k]);
+  for (size_t k = 0; k < NQ; ++k) Qr[k] = rev_leaf(Q[k]);
+  rhs(P, Mr.data(), Qr.data(), Rr.data());
+  out[1] = g_rev_extra;
+  out[2] = rev_edge_flops();
+  out[3] = (long long)g_tape.size();
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return 0;
+}
 
 // ---- multi-block entry points ----
 // dims: ni, nj per block; bcs: 4 codes per block (BC_LINK = 5 joins a face); lk: per

@@ -30,7 +30,7 @@ __all__ = [
     "build", "lib", "metrics", "metrics_jvp", "line_lambda", "rhs", "rhs_jvp", "rk3", "rk3_jvp",
     "cfl_dt", "count_flops", "count_flops_parts", "fsp_residual", "weno", "ppm", "smoothness", "eig",
     "scheme_table", "advect1d", "advect1d_dt", "smoothness4", "riemann_exact", "long_double_digits", "G",
-    "mb_metrics", "mb_rhs", "mb_rk3",
+    "mb_metrics", "mb_rhs", "mb_rk3", "rhs_vjp", "rk3_vjp", "metrics_vjp", "count_vjp_flops",
 ]
 
 G = 4
@@ -89,6 +89,11 @@ def lib():
                 "orc_riemann_exact": (ctypes.c_int, [ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_int, _D, _D]),
                 "orc_long_double_digits": (ctypes.c_int, []),
+                "orc_rhs_vjp": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]),
+                "orc_rk3_vjp": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double, _D, _D]),
+                "orc_metrics_vjp": (ctypes.c_int, [_I, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D]),
+                "orc_count_vjp_flops": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D,
+                                                       ctypes.POINTER(ctypes.c_longlong)]),
                 "orc_mb_metrics": (ctypes.c_int, [_I, ctypes.c_int, _I, _I, _I, _D, _D, _D, _D, _D]),
                 "orc_mb_rhs": (ctypes.c_int, [_I, _D, ctypes.c_int, _I, _I, _I, _D, _D, _D]),
                 "orc_mb_rk3": (ctypes.c_int, [_I, _D, ctypes.c_int, _I, _I, _I, _D, _D, ctypes.c_double,
@@ -194,6 +199,54 @@ def rk3_jvp(cfg, M, Q, dQ, dt, nsteps=1, dM=None):
     _ck(lib().orc_rk3_jvp(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(dM), _dp(Q), _dp(dQ),
                           float(dt), int(nsteps)), "rk3_jvp")
     return Q, dQ
+
+
+def rhs_vjp(cfg, M, Q, g):
+    """(Q_bar, M_bar) = (d rhs / d(Q, M))^T g by reverse mode over the oracle's own right-hand
+    side (the Rev scalar's tape); M_bar spans the haloed metric array."""
+    M, Q, g = _f64(M), _f64(Q), _f64(g)
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    Qb, Mb = np.zeros_like(Q), np.zeros_like(M)
+    _ck(lib().orc_rhs_vjp(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q), _dp(g), _dp(Qb), _dp(Mb)),
+        "rhs_vjp")
+    return Qb, Mb
+
+
+def rk3_vjp(cfg, M, Qn, dt, Qbar):
+    """Reverse of one RK3 step at Q_n: (dJ/dQ^n, metric adjoint of the step) from
+    Qbar = dJ/dQ^{n+1}."""
+    M, Qn = _f64(M), _f64(Qn)
+    Qb = np.array(Qbar, dtype=np.float64, copy=True, order="C")
+    _, nj, ni = Qn.shape
+    ip, dp, _ = _params(cfg)
+    Mb = np.zeros_like(M)
+    _ck(lib().orc_rk3_vjp(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Qn), float(dt), _dp(Qb), _dp(Mb)),
+        "rk3_vjp")
+    return Qb, Mb
+
+
+def metrics_vjp(cfg, x, y, Mbar):
+    """(x_bar, y_bar) = (d metrics / d(x, y))^T Mbar."""
+    x, y, Mbar = _f64(x), _f64(y), _f64(Mbar)
+    nj, ni = x.shape
+    ip, _, per = _params(cfg)
+    xb, yb = np.zeros_like(x), np.zeros_like(y)
+    _ck(lib().orc_metrics_vjp(ip.ctypes.data_as(_I), ni, nj, _dp(per), _dp(x), _dp(y), _dp(Mbar), _dp(xb),
+                              _dp(yb)), "metrics_vjp")
+    return xb, yb
+
+
+def count_vjp_flops(cfg, M, Q):
+    """{forward, partials, reverse, records}: operations of one right-hand-side adjoint
+    (the forward right-hand side, the partial derivatives its divisions and square roots
+    need, and the dense reverse sweep of its tape) and the tape's length."""
+    M, Q = _f64(M), _f64(Q)
+    _, nj, ni = Q.shape
+    ip, dp, _ = _params(cfg)
+    out = (ctypes.c_longlong * 4)()
+    _ck(lib().orc_count_vjp_flops(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q), out), "count_vjp_flops")
+    return {"forward": out[0], "partials": out[1], "reverse": out[2], "records": out[3]}
 
 
 def cfl_dt(cfg, M, Q, cfl):

@@ -23,6 +23,7 @@ MBK = "test_oracle_multiblock.py::"
 W7 = "test_oracle_weno7.py::"
 TAN = "test_oracle_tangent.py::"
 FLO = "test_oracle_flops.py::"
+VJP = "test_oracle_vjp.py::"
 
 # (name, text in the oracle, planted replacement, pins that catch it: tests/ node ids)
 MUTANTS = [
@@ -164,6 +165,17 @@ MUTANTS = [
      [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_rk3_tangent_matches_finite_differences"]),
     ("dual_sqrt", "a.d / (2.0 * s)", "a.d / s",
      [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_rk3_tangent_matches_finite_differences"]),
+    # reverse mode (the tape behind the oracle's adjoints)
+    ("rev_sub_sign", "rev_rec(a.v - b.v, a.i, 1.0, b.i, -1.0)", "rev_rec(a.v - b.v, a.i, 1.0, b.i, 1.0)",
+     [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_rhs_vjp_matches_finite_differences"]),
+    ("rev_product_swap", "rev_rec(a.v * b.v, a.i, b.v, b.i, a.v)", "rev_rec(a.v * b.v, a.i, a.v, b.i, b.v)",
+     [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_metrics_vjp_is_the_transposed_tangent[0]"]),
+    ("rev_quotient_sign", "1.0 / b.v, b.i, -q / b.v", "1.0 / b.v, b.i, q / b.v",
+     [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_rk3_vjp_is_the_transposed_tangent"]),
+    ("rev_sqrt_half", "s > 0 ? 0.5 / s : 0.0", "s > 0 ? 1.0 / s : 0.0",
+     [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_rhs_vjp_matches_finite_differences"]),
+    ("rev_sweep_operand", "if (r.b >= 0) adj[r.b] += r.pb * g;", "if (r.b >= 0) adj[r.b] += r.pa * g;",
+     [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_metrics_vjp_is_the_transposed_tangent[0]"]),
     # the operation counter (the roofline's algorithmic flops)
     ("count_sqrt_drop", "inline Counted sqrt(Counted a) { ++g_flops; return", "inline Counted sqrt(Counted a) { return",
      [FLO + "test_closed_forms[2]"]),
