@@ -382,6 +382,82 @@ struct Eig {
 };
 
 // --------------------------------------------------------------------------------------
+// The same projection and reconstruction for the right-hand-side sweeps, arranged for fewer
+// operations.  Node quantities that do not depend on the direction are computed once per
+// staged node (NodeChar), for a reconstruction scale S (weno_scale: the interpolated
+// characteristic values arrive multiplied by S, which the reconstruction divides out exactly).
+// The rows of L satisfy L_0 + L_3 = e_0 - L_1 and L_0 - L_3 = (Un, -nx, -ny, 0) / c, so
+//   w_1 = L_1 dq,  w_0, w_3 = (dq_0 - w_1) / 2 +- (Un dq_0 - nx dq_1 - ny dq_2) / (2c),
+//   w_2 = -Ut dq_0 - ny dq_1 + nx dq_2
+// (the same values as Eig::project up to rounding), and the reconstruction adds R W / S to
+// the centre state in one chain of fused multiply-adds.
+// --------------------------------------------------------------------------------------
+template <typename Real>
+struct NodeChar {
+  Real u, v, hc, a10;      // u, v, 1/(2c), 1 - b2            (b1 = (gamma-1)/c^2, b2 = b1 |u|^2/2)
+  Real b1u, b1v, b1, cs;   // b1 u, b1 v, b1, c/S
+  Real us, vs, Hs, h2s;    // u/S, v/S, H/S, |u|^2/(2S)
+};
+
+// Node quantities and the pressure of state q (reconstruction scale SC).
+template <typename Real, int SC>
+__device__ __forceinline__ NodeChar<Real> node_char(const Real q[4], Real gamma, Real& p) {
+  NodeChar<Real> w;
+  const Real rinv = recip(q[0]);
+  const Real u = q[1] * rinv, v = q[2] * rinv;
+  const Real h2 = Real(0.5) * (u * u + v * v);
+  const Real gm1 = gamma - Real(1);
+  p = gm1 * (q[3] - q[0] * h2);
+  const Real c2 = gamma * p * rinv;
+  const Real cinv = rsq(c2);
+  const Real c = c2 * cinv;
+  const Real H = (q[3] + p) * rinv;
+  const Real b1 = gm1 * cinv * cinv;
+  constexpr Real is = Real(1.0 / SC);
+  w.u = u; w.v = v; w.hc = Real(0.5) * cinv; w.a10 = fma(-b1, h2, Real(1));
+  w.b1u = b1 * u; w.b1v = b1 * v; w.b1 = b1; w.cs = c * is;
+  w.us = u * is; w.vs = v * is; w.Hs = H * is; w.h2s = h2 * is;
+  return w;
+}
+
+// One side of an interface: the eigen-system of the centre node along the unit direction
+// (nx, ny), and the reconstruction back to the state (scale SC).
+template <typename Real, int SC>
+struct CharSide {
+  Real Ut, Unc, nxc, nyc, nx, ny, a10, b1u, b1v, b1;
+  Real us, vs, Hs, h2s, csnx, csny, csUn, Uts;
+  __device__ __forceinline__ void build(const NodeChar<Real>& w, Real nx_, Real ny_) {
+    nx = nx_; ny = ny_;
+    const Real Un = w.u * nx + w.v * ny;
+    Ut = w.v * nx - w.u * ny;
+    Unc = Un * w.hc; nxc = nx * w.hc; nyc = ny * w.hc;
+    a10 = w.a10; b1u = w.b1u; b1v = w.b1v; b1 = w.b1;
+    us = w.us; vs = w.vs; Hs = w.Hs; h2s = w.h2s;
+    csnx = w.cs * nx; csny = w.cs * ny; csUn = w.cs * Un; Uts = Ut * Real(1.0 / SC);
+  }
+  // characteristic values (w_0 .. w_3) of the state difference d
+  __device__ __forceinline__ void project(Real d0, Real d1, Real d2, Real d3, Real w[4]) const {
+    const Real A = fma(a10, d0, fma(b1u, d1, fma(b1v, d2, -b1 * d3)));
+    const Real S = Real(0.5) * (d0 - A);
+    const Real B = fma(Unc, d0, -fma(nxc, d1, nyc * d2));
+    w[0] = S + B;
+    w[1] = A;
+    w[2] = fma(-Ut, d0, fma(-ny, d1, nx * d2));
+    w[3] = S - B;
+  }
+  // Q = qc + R W / S, with R's columns (1, u - c nx, v - c ny, H - c Un), (1, u, v, |u|^2/2),
+  // (0, -ny, nx, Ut), (1, u + c nx, v + c ny, H + c Un)
+  __device__ __forceinline__ void recon(const Real W[4], const Real qc[4], Real Q[4]) const {
+    const Real s = W[0] + W[3], dd = W[3] - W[0], a = s + W[1];
+    constexpr Real is = Real(1.0 / SC);
+    Q[0] = fma(a, is, qc[0]);
+    Q[1] = fma(us, a, fma(csnx, dd, fma(-ny * is, W[2], qc[1])));
+    Q[2] = fma(vs, a, fma(csny, dd, fma(nx * is, W[2], qc[2])));
+    Q[3] = fma(Hs, s, fma(csUn, dd, fma(h2s, W[1], fma(Uts, W[2], qc[3]))));
+  }
+};
+
+// --------------------------------------------------------------------------------------
 // WENO interpolation to x_{j+1/2} (Eqs. 3.10-3.13, Table 1), indicators of Eq. (3.22) on
 // consecutive differences (for r = 2 the three-point IS_0, IS_1 of Section 5.1), mapping
 // of Eq. (3.15) (r = 2) or (3.23) (r = 3).  Written on values relative to the stencil
@@ -442,6 +518,38 @@ __device__ __forceinline__ void raw_weights(const T* b, const T* C, T* w) {
   }
 }
 
+// The unnormalised weight terms t_k and the reciprocal of their sum (omega_k = t_k inv), as
+// raw_weights: FP64 t_k = C_k prod_{l!=k} b_l^2; FP32 t_k = C_k (b_min / b_k)^2.
+template <typename T, int K>
+__device__ __forceinline__ void raw_terms(const T* b, const T* C, T* t, T& inv) {
+  if constexpr (sizeof(T) == 8) {
+    T s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] = b[k] * b[k];
+    if constexpr (K == 3) {
+      t[0] = C[0] * (s[1] * s[2]);
+      t[1] = C[1] * (s[0] * s[2]);
+      t[2] = C[2] * (s[0] * s[1]);
+    } else {
+      t[0] = C[0] * s[1];
+      t[1] = C[1] * s[0];
+    }
+  } else {
+    T bmin = b[0];
+#pragma unroll
+    for (int k = 1; k < K; ++k) bmin = fminf(bmin, b[k]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const T r = quot(bmin, b[k]);
+      t[k] = (C[k] * r) * r;
+    }
+  }
+  T sum = t[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) sum += t[k];
+  inv = recip(sum);
+}
+
 // Indicators of the r = 4 candidates (WENOIU7): the quadratic form, in the three consecutive
 // differences (d1, d2, d3) of a candidate's values, of the integral over [x_{j-1/2}, x_{j+1/2}]
 // of the squared first to third derivatives of its interpolating cubic (times h, h^3, h^5),
@@ -458,6 +566,24 @@ template <typename T>
 __device__ __forceinline__ T is_b4(int k, T d1, T d2, T d3, T eps) {
   return eps + d1 * (T(is4c(k, 0)) * d1 + T(is4c(k, 3)) * d2 + T(is4c(k, 4)) * d3) +
          d2 * (T(is4c(k, 1)) * d2 + T(is4c(k, 5)) * d3) + T(is4c(k, 2)) * d3 * d3;
+}
+
+// The value weno_delta / weno_delta_x2 return is the interpolant times weno_scale<R>():
+// the candidates are formed with integer-free coefficients (below), and the caller divides
+// by the scale exactly (a power of two) where it adds the reconstruction to the centre state.
+template <int R>
+__host__ __device__ constexpr int weno_scale() { return R == 2 ? 4 : R == 3 ? 8 : 1; }
+
+// The three-point differences of Eq. (3.22) on values relative to the centre (u_j = 0):
+// IS_0 uses e0 = u_{j-2} - 2 u_{j-1} and f0 = u_{j-2} - 4 u_{j-1}; IS_1 uses e1 = u_{j+1} + u_{j-1}
+// and f1 = u_{j+1} - u_{j-1}; IS_2 uses e2 = u_{j+2} - 2 u_{j+1} and f2 = u_{j+2} - 4 u_{j+1}
+// (each IS = 13/12 e^2 + 1/4 f^2).  The same differences give the candidates of Table 1:
+// 8 p_0 = e0 + 2 f0, 8 p_1 = e1 + 2 f1, 8 p_2 = e2 - 2 f2 (r = 3), and 4 p_0 = f1 - e1,
+// 4 p_1 = e1 + f1 (r = 2).  The indicators are taken four times over, b = 4 (eps + IS) =
+// 4 eps + 13/3 e^2 + f^2: the weights depend on ratios of the b only.
+template <typename T>
+__device__ __forceinline__ T is_b4x(T e, T f, T eps4) {
+  return fma(T(13.0 / 3) * e, e, fma(f, f, eps4));
 }
 
 template <int R, typename T>
@@ -494,58 +620,56 @@ __device__ __forceinline__ T weno_delta(const T* u, T eps, int ppm, int linw) {
     }
     return w[0] * p[0] + w[1] * p[1] + w[2] * p[2] + w[3] * p[3];
   } else if constexpr (R == 3) {
-    // candidates of Table 1 relative to w_j
-    const T p0 = T(0.375) * u[0] - T(1.25) * u[1];
-    const T p1 = T(-0.125) * u[1] + T(0.375) * u[3];
-    const T p2 = T(0.75) * u[3] - T(0.125) * u[4];
+    const T e0 = fma(T(-2), u[1], u[0]), f0 = fma(T(-4), u[1], u[0]);
+    const T e1 = u[3] + u[1], f1 = u[3] - u[1];
+    const T e2 = fma(T(-2), u[3], u[4]), f2 = fma(T(-4), u[3], u[4]);
+    const T P[3] = {fma(T(2), f0, e0), fma(T(2), f1, e1), fma(T(-2), f2, e2)};   // 8 p_k
     const T C[3] = {T(1.0 / 16), T(10.0 / 16), T(5.0 / 16)};
-    if (linw) return C[0] * p0 + C[1] * p1 + C[2] * p2;
-    const T d1 = u[1] - u[0], d2 = -u[1], d3 = u[3], d4 = u[4] - u[3];
-    const T b[3] = {is_b(d2 - d1, T(3) * d2 - d1, eps), is_b(d3 - d2, d2 + d3, eps),
-                    is_b(d4 - d3, d4 - T(3) * d3, eps)};
-    T w[3];
-    raw_weights<T, 3>(b, C, w);
+    if (linw) return fma(C[0], P[0], fma(C[1], P[1], C[2] * P[2]));
+    const T eps4 = T(4) * eps;
+    const T b[3] = {is_b4x(e0, f0, eps4), is_b4x(e1, f1, eps4), is_b4x(e2, f2, eps4)};
+    T t[3], inv;
+    raw_terms<T, 3>(b, C, t, inv);
     if (ppm) {
       // g = C + (w - C)^3 / C^2 (w <= C), C + (w - C)^3 / (C - 1)^2 (w > C)   [Eq. 3.23]
       const T K0[3] = {T(256.0), T(256.0 / 100), T(256.0 / 25)};          // 1 / C^2
       const T K1[3] = {T(256.0 / 225), T(256.0 / 36), T(256.0 / 121)};   // 1 / (C - 1)^2
       T num = T(0), den = T(0);
-      const T p[3] = {p0, p1, p2};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const T q = w[k] - C[k];
-        const T g = C[k] + q * q * q * (nonpos(q) ? K0[k] : K1[k]);
-        num += g * p[k];
-        den += g;
+        const T q = fma(t[k], inv, -C[k]);                                  // w_k - C_k
+        const T g = fma(q * q * q, nonpos(q) ? K0[k] : K1[k], C[k]);
+        num = k == 0 ? g * P[0] : fma(g, P[k], num);
+        den = k == 0 ? g : den + g;
       }
       return quot(num, den);
     }
-    return w[0] * p0 + w[1] * p1 + w[2] * p2;
+    return (t[0] * P[0] + t[1] * P[1] + t[2] * P[2]) * inv;
   } else {
-    const T p0 = T(-0.5) * u[1];
-    const T p1 = T(0.5) * u[3];
+    const T e0 = fma(T(-2), u[1], u[0]), f0 = fma(T(-4), u[1], u[0]);
+    const T e1 = u[3] + u[1], f1 = u[3] - u[1];
+    const T P[2] = {f1 - e1, e1 + f1};                                      // 4 p_k
     const T C[2] = {T(0.25), T(0.75)};
-    if (linw) return C[0] * p0 + C[1] * p1;
-    const T d1 = u[1] - u[0], d2 = -u[1], d3 = u[3];
-    const T b[2] = {is_b(d2 - d1, T(3) * d2 - d1, eps), is_b(d3 - d2, d2 + d3, eps)};
-    T w[2];
-    raw_weights<T, 2>(b, C, w);
+    if (linw) return fma(C[0], P[0], C[1] * P[1]);
+    const T eps4 = T(4) * eps;
+    const T b[2] = {is_b4x(e0, f0, eps4), is_b4x(e1, f1, eps4)};
+    T t[2], inv;
+    raw_terms<T, 2>(b, C, t, inv);
     if (ppm) {
       // g = C - (w - C)^2 / C (w <= C), C - (w - C)^2 / (C - 1) (w > C)   [Eq. 3.15]
-      const T K0[2] = {T(4.0), T(4.0 / 3)};        // 1 / C
-      const T K1[2] = {T(-4.0 / 3), T(-4.0)};      // 1 / (C - 1)
-      const T p[2] = {p0, p1};
+      const T K0[2] = {T(-4.0), T(-4.0 / 3)};        // -1 / C
+      const T K1[2] = {T(4.0 / 3), T(4.0)};          // -1 / (C - 1)
       T num = T(0), den = T(0);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const T q = w[k] - C[k];
-        const T g = C[k] - q * q * (nonpos(q) ? K0[k] : K1[k]);
-        num += g * p[k];
-        den += g;
+        const T q = fma(t[k], inv, -C[k]);
+        const T g = fma(q * q, nonpos(q) ? K0[k] : K1[k], C[k]);
+        num = k == 0 ? g * P[0] : fma(g, P[k], num);
+        den = k == 0 ? g : den + g;
       }
       return quot(num, den);
     }
-    return w[0] * p0 + w[1] * p1;
+    return (t[0] * P[0] + t[1] * P[1]) * inv;
   }
 }
 
@@ -581,6 +705,25 @@ __device__ __forceinline__ void raw_weights2(const float2* b, const float* C, fl
   const float2 inv = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
 #pragma unroll
   for (int k = 0; k < K; ++k) w[k] = mul2(t[k], inv);
+}
+
+// raw terms of two lanes: t_k = C_k (b_min / b_k)^2 and the reciprocal of their sum
+template <int K>
+__device__ __forceinline__ void raw_terms2(const float2* b, const float* C, float2* t, float2& inv) {
+  float2 bmin = b[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) bmin = make_float2(fminf(bmin.x, b[k].x), fminf(bmin.y, b[k].y));
+  float2 sum;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float2 r = quot2(bmin, b[k]);
+    t[k] = mul2(mul2(bc2(C[k]), r), r);
+    sum = k == 0 ? t[0] : add2(sum, t[k]);
+  }
+  inv = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
+}
+__device__ __forceinline__ float2 is_b4x2(float2 e, float2 f, float2 eps4) {
+  return fma2(mul2(bc2(13.0f / 3), e), e, fma2(f, f, eps4));
 }
 
 template <int R>
@@ -626,58 +769,59 @@ __device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int
     }
     return fma2(w[0], p[0], fma2(w[1], p[1], fma2(w[2], p[2], mul2(w[3], p[3]))));
   } else if constexpr (R == 3) {
-    const float2 p[3] = {fma2(bc2(0.375f), u[0], mul2(bc2(-1.25f), u[1])),
-                         fma2(bc2(-0.125f), u[1], mul2(bc2(0.375f), u[3])),
-                         fma2(bc2(0.75f), u[3], mul2(bc2(-0.125f), u[4]))};
+    // the differences and candidates of weno_delta<3> (8 p_k), lane by lane
+    const float2 m1 = bc2(-1.0f), m2 = bc2(-2.0f), m4 = bc2(-4.0f), two = bc2(2.0f);
+    const float2 e0 = fma2(m2, u[1], u[0]), f0 = fma2(m4, u[1], u[0]);
+    const float2 e1 = add2(u[3], u[1]), f1 = fma2(u[1], m1, u[3]);
+    const float2 e2 = fma2(m2, u[3], u[4]), f2 = fma2(m4, u[3], u[4]);
+    const float2 P[3] = {fma2(two, f0, e0), fma2(two, f1, e1), fma2(m2, f2, e2)};
     const float C[3] = {1.0f / 16, 10.0f / 16, 5.0f / 16};
-    if (linw) return fma2(bc2(C[0]), p[0], fma2(bc2(C[1]), p[1], mul2(bc2(C[2]), p[2])));
-    const float2 m1 = bc2(-1.0f);
-    const float2 d1 = fma2(u[0], m1, u[1]), d2 = mul2(u[1], m1), d3 = u[3], d4 = fma2(u[3], m1, u[4]);
-    const float2 b[3] = {is_b2(fma2(d1, m1, d2), fma2(bc2(3.0f), d2, mul2(d1, m1)), eps),
-                         is_b2(fma2(d2, m1, d3), add2(d2, d3), eps),
-                         is_b2(fma2(d3, m1, d4), fma2(bc2(-3.0f), d3, d4), eps)};
-    float2 w[3];
-    raw_weights2<3>(b, C, w);
+    if (linw) return fma2(bc2(C[0]), P[0], fma2(bc2(C[1]), P[1], mul2(bc2(C[2]), P[2])));
+    const float2 eps4 = bc2(4.0f * eps_);
+    const float2 b[3] = {is_b4x2(e0, f0, eps4), is_b4x2(e1, f1, eps4), is_b4x2(e2, f2, eps4)};
+    float2 t[3], inv;
+    raw_terms2<3>(b, C, t, inv);
     if (ppm) {
       // g = C + (w - C)^3 / C^2 (w <= C), C + (w - C)^3 / (C - 1)^2 (w > C)   [Eq. 3.23]
       const float K0[3] = {256.0f, 256.0f / 100, 256.0f / 25}, K1[3] = {256.0f / 225, 256.0f / 36, 256.0f / 121};
       float2 num, den;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float2 q = add2(w[k], bc2(-C[k]));
+        const float2 q = fma2(t[k], inv, bc2(-C[k]));
         const float2 K = make_float2(nonpos(q.x) ? K0[k] : K1[k], nonpos(q.y) ? K0[k] : K1[k]);
         const float2 g = fma2(mul2(mul2(q, q), q), K, bc2(C[k]));
-        num = k == 0 ? mul2(g, p[0]) : fma2(g, p[k], num);
+        num = k == 0 ? mul2(g, P[0]) : fma2(g, P[k], num);
         den = k == 0 ? g : add2(den, g);
       }
       return quot2(num, den);
     }
-    return fma2(w[0], p[0], fma2(w[1], p[1], mul2(w[2], p[2])));
+    return mul2(fma2(t[0], P[0], fma2(t[1], P[1], mul2(t[2], P[2]))), inv);
   } else {
-    const float2 p[2] = {mul2(bc2(-0.5f), u[1]), mul2(bc2(0.5f), u[3])};
+    const float2 m1 = bc2(-1.0f), m2 = bc2(-2.0f), m4 = bc2(-4.0f);
+    const float2 e0 = fma2(m2, u[1], u[0]), f0 = fma2(m4, u[1], u[0]);
+    const float2 e1 = add2(u[3], u[1]), f1 = fma2(u[1], m1, u[3]);
+    const float2 P[2] = {fma2(e1, m1, f1), add2(e1, f1)};                  // 4 p_k
     const float C[2] = {0.25f, 0.75f};
-    if (linw) return fma2(bc2(C[0]), p[0], mul2(bc2(C[1]), p[1]));
-    const float2 m1 = bc2(-1.0f);
-    const float2 d1 = fma2(u[0], m1, u[1]), d2 = mul2(u[1], m1), d3 = u[3];
-    const float2 b[2] = {is_b2(fma2(d1, m1, d2), fma2(bc2(3.0f), d2, mul2(d1, m1)), eps),
-                         is_b2(fma2(d2, m1, d3), add2(d2, d3), eps)};
-    float2 w[2];
-    raw_weights2<2>(b, C, w);
+    if (linw) return fma2(bc2(C[0]), P[0], mul2(bc2(C[1]), P[1]));
+    const float2 eps4 = bc2(4.0f * eps_);
+    const float2 b[2] = {is_b4x2(e0, f0, eps4), is_b4x2(e1, f1, eps4)};
+    float2 t[2], inv;
+    raw_terms2<2>(b, C, t, inv);
     if (ppm) {
       // g = C - (w - C)^2 / C (w <= C), C - (w - C)^2 / (C - 1) (w > C)   [Eq. 3.15]
-      const float K0[2] = {4.0f, 4.0f / 3}, K1[2] = {-4.0f / 3, -4.0f};
+      const float K0[2] = {-4.0f, -4.0f / 3}, K1[2] = {4.0f / 3, 4.0f};
       float2 num, den;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const float2 q = add2(w[k], bc2(-C[k]));
-        const float2 K = make_float2(nonpos(q.x) ? -K0[k] : -K1[k], nonpos(q.y) ? -K0[k] : -K1[k]);
+        const float2 q = fma2(t[k], inv, bc2(-C[k]));
+        const float2 K = make_float2(nonpos(q.x) ? K0[k] : K1[k], nonpos(q.y) ? K0[k] : K1[k]);
         const float2 g = fma2(mul2(q, q), K, bc2(C[k]));
-        num = k == 0 ? mul2(g, p[0]) : fma2(g, p[k], num);
+        num = k == 0 ? mul2(g, P[0]) : fma2(g, P[k], num);
         den = k == 0 ? g : add2(den, g);
       }
       return quot2(num, den);
     }
-    return fma2(w[0], p[0], mul2(w[1], p[1]));
+    return mul2(fma2(t[0], P[0], mul2(t[1], P[1])), inv);
   }
 }
 

@@ -72,19 +72,19 @@ __device__ __forceinline__ void ld2(const T* b, int o, T& x, T& y) {
 //           holds the metric-weighted flux E^ and there is no fm
 //   ma      direction metrics in Acc (2 values)
 //   q       state (Real, 4 values)
-//   p0, p1  primitives (u, v, c, 1/c) and (H, b1, |u|^2/2, 0) of the projection
+//   p0..p2  the node's characteristic data (NodeChar: 12 values)
 //   mr      direction metrics rounded to Real (only when Real differs from Acc)
 template <typename Real, typename Acc>
 struct Staged {
   static constexpr bool SPLIT = !std::is_same<Real, Acc>::value;
   Acc *fp, *fm, *ma;
-  Real *q, *p0, *p1, *mr;
+  Real *q, *p0, *p1, *p2, *mr;
   int n;
   // arrays of padded length (a multiple of 4 nodes keeps every array 16-byte aligned)
   static constexpr int padded(int nn) { return (nn + 3) / 4 * 4; }
   static constexpr size_t bytes(int nn) {
     return sizeof(Acc) * (size_t)padded(nn) * (SPLIT ? 6 : 10) +
-           sizeof(Real) * (size_t)padded(nn) * (12 + (SPLIT ? 2 : 0));
+           sizeof(Real) * (size_t)padded(nn) * (16 + (SPLIT ? 2 : 0));
   }
   __device__ __forceinline__ void carve(unsigned char* base, int nn0) {
     const int nn = padded(nn0);
@@ -95,33 +95,37 @@ struct Staged {
     q = reinterpret_cast<Real*>(ma + 2 * nn);
     p0 = q + 4 * nn;
     p1 = p0 + 4 * nn;
-    mr = SPLIT ? p1 + 4 * nn : nullptr;
+    p2 = p1 + 4 * nn;
+    mr = SPLIT ? p2 + 4 * nn : nullptr;
   }
-  __device__ __forceinline__ void store(int o, const Real qq[4], const Prim<Real>& w, Acc amx, Acc amy,
+  __device__ __forceinline__ void store(int o, const Real qq[4], const NodeChar<Real>& w, Acc amx, Acc amy,
                                         const Acc f[4], const Acc g[4], double mx, double my) const {
     st4(fp, n, o, f[0], f[1], f[2], f[3]);
     if constexpr (!SPLIT) st4(fm, n, o, g[0], g[1], g[2], g[3]);
     st2(ma, o, amx, amy);
     if constexpr (SPLIT) st2(mr, o, from_f64_int(mx), from_f64_int(my));
     st4(q, n, o, qq[0], qq[1], qq[2], qq[3]);
-    st4(p0, n, o, w.u, w.v, w.c, w.cinv);
-    st4(p1, n, o, w.H, w.b1, w.h2, Real(0));
+    st4(p0, n, o, w.u, w.v, w.hc, w.a10);
+    st4(p1, n, o, w.b1u, w.b1v, w.b1, w.cs);
+    st4(p2, n, o, w.us, w.vs, w.Hs, w.h2s);
   }
   __device__ __forceinline__ void met_real(int o, Real& x, Real& y) const {
     if constexpr (SPLIT) ld2(mr, o, x, y);
     else ld2(ma, o, x, y);
   }
-  __device__ __forceinline__ void prim(int o, Prim<Real>& w) const {
-    Real a[4], b[4];
+  __device__ __forceinline__ void chr(int o, NodeChar<Real>& w) const {
+    Real a[4], b[4], c[4];
     ld4(p0, n, o, a);
     ld4(p1, n, o, b);
-    w.u = a[0]; w.v = a[1]; w.c = a[2]; w.cinv = a[3];
-    w.H = b[0]; w.b1 = b[1]; w.h2 = b[2];
+    ld4(p2, n, o, c);
+    w.u = a[0]; w.v = a[1]; w.hc = a[2]; w.a10 = a[3];
+    w.b1u = b[0]; w.b1v = b[1]; w.b1 = b[2]; w.cs = b[3];
+    w.us = c[0]; w.vs = c[1]; w.Hs = c[2]; w.h2s = c[3];
   }
 };
 
 // What the h combination needs from one interface (midpoint p + 1/2).  Same precision: f[0],
-// f[1] = the split midpoint fluxes f+, f-.  Mixed: f[s] = E^(Q_s) = mm_x E(Q_s) + mm_y F(Q_s)
+// f[1] = twice the split midpoint fluxes, 2 f+, 2 f- (the 1/2 is taken in h_combine).  Mixed: f[s] = E^(Q_s) = mm_x E(Q_s) + mm_y F(Q_s)
 // (double products of float Cartesian fluxes) and q[s] = Q_s, s = +, -; for one-midpoint
 // schemes only their combinations are kept: f[0] = (E^(Q+) + E^(Q-))/2, q[0] = Q+ - Q-.
 template <typename Real, typename Acc>
@@ -235,11 +239,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // precision (float state, double Acc): only the metric-weighted flux E^ = mx E + my F, with the
 // Cartesian fluxes E, F in float and the two metric products in double, stored in fp; the
 // dissipative part A^ Q of the split is taken at the interfaces from the staged state.
-template <typename Real, typename Acc>
+template <int SC, typename Real, typename Acc>
 __device__ __forceinline__ void node_split(const Real q[4], double mx, double my, Real gamma, Acc hA,
-                                           Prim<Real>& w, Acc& amx, Acc& amy, Acc fp[4], Acc fm[4]) {
-  w = prim_of(q, gamma);
-  const Real p = (gamma - Real(1)) * (q[3] - q[0] * w.h2);
+                                           NodeChar<Real>& w, Acc& amx, Acc& amy, Acc fp[4], Acc fm[4]) {
+  Real p;
+  w = node_char<Real, SC>(q, gamma, p);
   amx = from_f64<Acc>(mx);
   amy = from_f64<Acc>(my);
   if constexpr (Staged<Real, Acc>::SPLIT) {
@@ -270,12 +274,13 @@ template <int S, typename Real, typename Acc, typename At>
 __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
                                               int ppm, int linw, int interp, Acc A, Mid<Real, Acc>& mo) {
   using Sc = Scheme<S>;
+  constexpr int SC = weno_scale<Sc::r>();
   const int o0 = at(0), o1 = at(1);
+  // unit direction of the averaged metrics (the mean's factor 1/2 cancels in the normalisation)
   Real m0x, m0y, m1x, m1y;
   st.met_real(o0, m0x, m0y);
   st.met_real(o1, m1x, m1y);
-  const Real mbx = Real(0.5) * (m0x + m1x);
-  const Real mby = Real(0.5) * (m0y + m1y);
+  const Real mbx = m0x + m1x, mby = m0y + m1y;
   const Real rn = rsq(mbx * mbx + mby * mby);
   const Real nx = mbx * rn, ny = mby * rn;
 
@@ -283,24 +288,23 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     const int oc = side == 0 ? o0 : o1;
-    Prim<Real> w;
-    st.prim(oc, w);
-    Eig<Real> E;
+    NodeChar<Real> w;
+    st.chr(oc, w);
+    CharSide<Real, SC> E;
     E.build(w, nx, ny);
     Real qc[4];
     ld4(st.q, st.n, oc, qc);
-    // state differences to the centre at the stencil offsets -H..-1, +1..+H (H = 2, or 3
-    // for r = 4); the "-" side reads the mirrored nodes
+    // characteristic differences to the centre at the stencil offsets -H..-1, +1..+H (H = 2,
+    // or 3 for r = 4); the "-" side reads the mirrored nodes
     constexpr int H = Sc::r == 4 ? 3 : 2, NA = 2 * H;
-    Real dq[NA][4];
+    Real wd[NA][4];
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
       const int m = a < H ? a - H : a - H + 1;
-      if (Sc::r == 2 && m == 2) { dq[a][0] = dq[a][1] = dq[a][2] = dq[a][3] = Real(0); continue; }
+      if (Sc::r == 2 && m == 2) { wd[a][0] = wd[a][1] = wd[a][2] = wd[a][3] = Real(0); continue; }
       Real t[4];
       ld4(st.q, st.n, at(side == 0 ? m : 1 - m), t);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) dq[a][v] = t[v] - qc[v];
+      E.project(t[0] - qc[0], t[1] - qc[1], t[2] - qc[2], t[3] - qc[3], wd[a]);
     }
     Real Wm[4];
     if constexpr (std::is_same<Real, float>::value) {
@@ -309,11 +313,7 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
       for (int kp = 0; kp < 2; ++kp) {
         float2 u[NA + 1];
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-          if (Sc::r == 2 && a == NA - 1) { u[NA] = make_float2(0.f, 0.f); continue; }
-          u[a < H ? a : a + 1] = make_float2(E.project(2 * kp, dq[a][0], dq[a][1], dq[a][2], dq[a][3]),
-                                             E.project(2 * kp + 1, dq[a][0], dq[a][1], dq[a][2], dq[a][3]));
-        }
+        for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = make_float2(wd[a][2 * kp], wd[a][2 * kp + 1]);
         u[H] = make_float2(0.f, 0.f);
         const float2 W2 = weno_delta_x2<Sc::r>(u, eps, ppm, linw);
         Wm[2 * kp] = W2.x;
@@ -324,18 +324,12 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
       for (int kc = 0; kc < 4; ++kc) {
         Real u[NA + 1];
 #pragma unroll
-        for (int a = 0; a < NA; ++a)
-          u[a < H ? a : a + 1] = (Sc::r == 2 && a == NA - 1)
-                                     ? Real(0)
-                                     : E.project(kc, dq[a][0], dq[a][1], dq[a][2], dq[a][3]);
+        for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = wd[a][kc];
         u[H] = Real(0);
         Wm[kc] = weno_delta<Sc::r, Real>(u, eps, ppm, linw);
       }
     }
-    Real dQm[4];
-    E.recon(Wm, dQm);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) Qs[side][v] = qc[v] + dQm[v];
+    E.recon(Wm, qc, Qs[side]);
   }
 
   Acc mmx, mmy;
@@ -381,7 +375,8 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
         }
     }
   } else {
-    // split midpoint fluxes f+ = (E^(Q+) + A^ Q+)/2, f- = (E^(Q-) - A^ Q-)/2
+    // twice the split midpoint fluxes: E^(Q+) + A^ Q+ and E^(Q-) - A^ Q-, with
+    // E^ = (rho U, rho u U + mx p, rho v U + my p, (E + p) U)
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const Real* q = Qs[side];
@@ -389,11 +384,11 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
       const Real u = q[1] * rinv, v = q[2] * rinv;
       const Real pr = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
       const Acc U = mmx * Acc(u) + mmy * Acc(v);
-      const Acc sg = side == 0 ? A : -A;
-      mo.f[side][0] = Acc(0.5) * (Acc(q[0]) * U + sg * Acc(q[0]));
-      mo.f[side][1] = Acc(0.5) * (Acc(q[1]) * U + mmx * Acc(pr) + sg * Acc(q[1]));
-      mo.f[side][2] = Acc(0.5) * (Acc(q[2]) * U + mmy * Acc(pr) + sg * Acc(q[2]));
-      mo.f[side][3] = Acc(0.5) * (Acc(q[3] + pr) * U + sg * Acc(q[3]));
+      const Acc Us = side == 0 ? U + A : U - A;
+      mo.f[side][0] = Acc(q[0]) * Us;
+      mo.f[side][1] = fma(Acc(q[1]), Us, mmx * Acc(pr));
+      mo.f[side][2] = fma(Acc(q[2]), Us, mmy * Acc(pr));
+      mo.f[side][3] = fma(Acc(q[3]), Us, Acc(pr) * U);
     }
   }
 }
@@ -452,8 +447,8 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
   } else {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      if constexpr (Sc::nmp == 1) h[v] = Acc(Sc::m0) * (c.f[0][v] + c.f[1][v]);
-      else h[v] = Acc(Sc::m0) * (c.f[0][v] + c.f[1][v]) + Acc(Sc::m1) * (lo.f[0][v] + hi.f[1][v]);
+      if constexpr (Sc::nmp == 1) h[v] = Acc(0.5 * Sc::m0) * (c.f[0][v] + c.f[1][v]);
+      else h[v] = Acc(0.5 * Sc::m0) * (c.f[0][v] + c.f[1][v]) + Acc(0.5 * Sc::m1) * (lo.f[0][v] + hi.f[1][v]);
     }
 #pragma unroll
     for (int kk = -3; kk <= 3; ++kk) {
@@ -544,9 +539,9 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
       double mx, my;
       if (DIR == 0) { mx = met_at(P, 0, g, line); my = met_at(P, 1, g, line); }
       else          { mx = met_at(P, 2, line, g); my = met_at(P, 3, line, g); }
-      Prim<Real> w;
+      NodeChar<Real> w;
       Acc amx, amy, fp[4], fm[4];
-      node_split<Real, Acc>(q, mx, my, gamma, Acc(0.5) * sA[l], w, amx, amy, fp, fm);
+      node_split<weno_scale<Sc::r>(), Real, Acc>(q, mx, my, gamma, Acc(0.5) * sA[l], w, amx, amy, fp, fm);
       st.store(SI(l, s), q, w, amx, amy, fp, fm, mx, my);
     }
   } else {
@@ -573,9 +568,9 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const int s = DIR == 0 ? k % NP : k / NL;
     const int line = line0 + l;
     if (k >= NN || line >= nlines) continue;
-    Prim<Real> w;
+    NodeChar<Real> w;
     Acc amx, amy, fp[4], fm[4];
-    node_split<Real, Acc>(qv[r], mxv[r], myv[r], gamma, Acc(0.5) * sA[l], w, amx, amy, fp, fm);
+    node_split<weno_scale<Sc::r>(), Real, Acc>(qv[r], mxv[r], myv[r], gamma, Acc(0.5) * sA[l], w, amx, amy, fp, fm);
     st.store(SI(l, s), qv[r], w, amx, amy, fp, fm, mxv[r], myv[r]);
   }
   }
@@ -718,9 +713,9 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
       mx = met_at(P, 0, m, row);
       my = met_at(P, 1, m, row);
     }
-    Prim<Real> w;
+    NodeChar<Real> w;
     Acc amx, amy, fp[4], fm[4];
-    node_split<Real, Acc>(q, mx, my, gamma, hA, w, amx, amy, fp, fm);
+    node_split<weno_scale<Scheme<S>::r>(), Real, Acc>(q, mx, my, gamma, hA, w, amx, amy, fp, fm);
     st.store(m & (RING - 1), q, w, amx, amy, fp, fm, mx, my);
   };
   // cp.async of node m's state and metrics into this lane's staging slot (interior only)
@@ -886,9 +881,9 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
       mx = met_at(P, 2, col, m);
       my = met_at(P, 3, col, m);
     }
-    Prim<Real> pw;
+    NodeChar<Real> pw;
     Acc amx, amy, fp[4], fm[4];
-    node_split<Real, Acc>(q, mx, my, gamma, hA, pw, amx, amy, fp, fm);
+    node_split<weno_scale<Scheme<S>::r>(), Real, Acc>(q, mx, my, gamma, hA, pw, amx, amy, fp, fm);
     st.store(slot(m), q, pw, amx, amy, fp, fm, mx, my);
   };
   // cp.async of node (col, m) into this thread's staging slot (interior rows only), and of the
