@@ -364,7 +364,10 @@ fsp_status fsp_batch_capture_graph(fsp_batch* b, double dt, void* stream);
  * stored choice without timing; otherwise it times and appends the choice.  Changing a
  * shape synchronises the device and drops a captured graph (capture again after tuning).
  * Returns FSP_ERR_INVALID_ARG for an unbound handle or an unwritable table (the timed
- * choice is applied all the same).  fsp_batch_set_tile_shape forces a variant;
+ * choice is applied all the same).  The marching variants (3) are built for the default
+ * options only (ppm = 1, linear_weights = 0, interp = 0): for other options the tuner skips
+ * them and fsp_batch_set_tile_shape returns FSP_ERR_UNSUPPORTED for variant 3, leaving the
+ * current variant.  fsp_batch_set_tile_shape forces a variant;
  * fsp_batch_tile_shape reports the current variant, lines per tile and output nodes per
  * line (any output pointer may be null). */
 fsp_status fsp_batch_tune(fsp_batch* b, const char* table_path, void* stream);

@@ -110,6 +110,7 @@ inline double val(Counted a) { return a.v; }
 struct TapeRec { double pa, pb; int a, b; };
 static std::vector<TapeRec> g_tape;
 static long long g_rev_extra = 0;   // operations spent on partial derivatives (for the count)
+static long long g_rev_edges = 0;   // operations of the reverse sweep (for the count)
 struct Rev {
   double v;
   int i;
@@ -117,8 +118,11 @@ struct Rev {
   Rev(double a) : v(a), i(-1) {}
   Rev(double a, int idx) : v(a), i(idx) {}
 };
-static inline Rev rev_rec(double v, int a, double pa, int b, double pb) {
+// `cost`: operations of one operand edge in the reverse sweep (1 for a sum or difference,
+// adj += adj_c; 2 for any other operation, a multiply-add).
+static inline Rev rev_rec(double v, int a, double pa, int b, double pb, int cost) {
   if (a < 0 && b < 0) return Rev(v);
+  g_rev_edges += cost * ((a >= 0) + (b >= 0));
   g_tape.push_back(TapeRec{pa, pb, a, b});
   return Rev(v, (int)(g_tape.size() - 1));
 }
@@ -126,14 +130,14 @@ static inline Rev rev_leaf(double v) {   // an independent variable: a record wi
   g_tape.push_back(TapeRec{0.0, 0.0, -1, -1});
   return Rev(v, (int)(g_tape.size() - 1));
 }
-inline Rev operator+(Rev a, Rev b) { return rev_rec(a.v + b.v, a.i, 1.0, b.i, 1.0); }
-inline Rev operator-(Rev a, Rev b) { return rev_rec(a.v - b.v, a.i, 1.0, b.i, -1.0); }
-inline Rev operator-(Rev a) { return rev_rec(-a.v, a.i, -1.0, -1, 0.0); }
-inline Rev operator*(Rev a, Rev b) { return rev_rec(a.v * b.v, a.i, b.v, b.i, a.v); }
+inline Rev operator+(Rev a, Rev b) { return rev_rec(a.v + b.v, a.i, 1.0, b.i, 1.0, 1); }
+inline Rev operator-(Rev a, Rev b) { return rev_rec(a.v - b.v, a.i, 1.0, b.i, -1.0, 1); }
+inline Rev operator-(Rev a) { return rev_rec(-a.v, a.i, -1.0, -1, 0.0, 1); }
+inline Rev operator*(Rev a, Rev b) { return rev_rec(a.v * b.v, a.i, b.v, b.i, a.v, 2); }
 inline Rev operator/(Rev a, Rev b) {
   const double q = a.v / b.v;
   if (a.i >= 0 || b.i >= 0) g_rev_extra += 1 + (b.i >= 0);   // 1 / b, and q (1 / b) for b
-  return rev_rec(q, a.i, 1.0 / b.v, b.i, -q / b.v);
+  return rev_rec(q, a.i, 1.0 / b.v, b.i, -q / b.v, 2);
 }
 inline Rev& operator+=(Rev& a, Rev b) { a = a + b; return a; }
 inline Rev& operator-=(Rev& a, Rev b) { a = a - b; return a; }
@@ -145,9 +149,13 @@ inline bool operator>=(Rev a, Rev b) { return a.v >= b.v; }
 inline Rev sqrt(Rev a) {
   const double s = std::sqrt(a.v);
   if (a.i >= 0) g_rev_extra += 1;                               // 0.5 / s
-  return rev_rec(s, a.i, s > 0 ? 0.5 / s : 0.0, -1, 0.0);
+  return rev_rec(s, a.i, s > 0 ? 0.5 / s : 0.0, -1, 0.0, 2);
 }
-inline Rev fabs(Rev a) { return a.v >= 0 ? a : -a; }
+inline Rev fabs(Rev a) {
+  if (a.v < 0) return -a;
+  g_rev_edges += a.i >= 0;   // the reverse passes the adjoint through with the sign +1: one operation
+  return a;
+}
 inline double val(Rev a) { return a.v; }
 
 // The reverse sweep: adj[k] holds the adjoint of tape record k on entry (the seeds) and the
@@ -160,17 +168,6 @@ static void rev_sweep(std::vector<double>& adj) {
     if (r.a >= 0) adj[r.a] += r.pa * g;
     if (r.b >= 0) adj[r.b] += r.pb * g;
   }
-}
-
-// Operations of the reverse sweep taken densely (whatever the seed): one per operand edge
-// whose partial is +-1, two (a multiply-add) for any other partial.
-static long long rev_edge_flops() {
-  long long n = 0;
-  for (const TapeRec& r : g_tape) {
-    if (r.a >= 0) n += (r.pa == 1.0 || r.pa == -1.0) ? 1 : 2;
-    if (r.b >= 0) n += (r.pb == 1.0 || r.pb == -1.0) ? 1 : 2;
-  }
-  return n;
 }
 
 inline double val(double a) { return a; }
@@ -1337,7 +1334,8 @@ int orc_metrics_vjp(const int* ip, int ni, int nj, const double* period, const d
 
 // Operation count of one right-hand-side adjoint, dense in the seed: out = {the forward
 // right-hand side (as orc_count_flops), the partial derivatives the forward pass forms for
-// its divisions and square roots, the reverse sweep (rev_edge_flops), tape records}.
+// its divisions and square roots, the reverse sweep taken densely (whatever the seed: one
+// operation per operand edge of a sum or difference, two for any other), tape records}.
 int orc_count_vjp_flops(const int* ip, const double* dp, int ni, int nj, const double* M, const double* Q,
                         long long* out) {
   if (int e = check(ip, ni, nj)) return e;
@@ -1346,12 +1344,13 @@ int orc_count_vjp_flops(const int* ip, const double* dp, int ni, int nj, const d
   const size_t NM = orc_metrics_len(ni, nj), NQ = 4 * (size_t)ni * nj;
   g_tape.clear();
   g_rev_extra = 0;
+  g_rev_edges = 0;
   std::vector<Rev> Mr(NM), Qr(NQ), Rr(NQ);
   for (size_t k = 0; k < NM; ++k) Mr[k] = rev_leaf(M[k]);
   for (size_t k = 0; k < NQ; ++k) Qr[k] = rev_leaf(Q[k]);
   rhs(P, Mr.data(), Qr.data(), Rr.data());
   out[1] = g_rev_extra;
-  out[2] = rev_edge_flops();
+  out[2] = g_rev_edges;
   out[3] = (long long)g_tape.size();
   g_tape.clear();
   g_tape.shrink_to_fit();

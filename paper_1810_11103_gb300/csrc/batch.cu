@@ -293,8 +293,12 @@ void tiles_for(const fsp_batch* h, int dir, int v, std::vector<TileRef>& out) {
 
 // Switch one direction to shape variant v: the host and device tile tables (the device is
 // synchronised first, since queued launches may read the table) and any captured graph.
+// The marching passes are compiled for the default options only (sweep.cuh).
+bool default_options(const fsp_config& c) { return c.ppm == 1 && c.linear_weights == 0 && c.interp == 0; }
+
 fsp_status set_tiles(fsp_batch* h, int dir, int v) {
   if (v < 0 || v >= nvariant(dir)) return FSP_ERR_INVALID_ARG;
+  if (v == MARCH && !default_options(h->cfg)) return FSP_ERR_UNSUPPORTED;
   std::vector<TileRef>& t = dir == 0 ? h->tx : h->te;
   tiles_for(h, dir, v, t);
   if (cudaDeviceSynchronize() != cudaSuccess) return FSP_ERR_CUDA;
@@ -653,6 +657,7 @@ fsp_status fsp_batch_tune(fsp_batch* h, const char* table_path, void* stream) {
   float best_ms[2] = {0, 0};
   for (int dir = 0; dir < 2; ++dir) {
     for (int v = 0; v < nvariant(dir); ++v) {
+      if (v == MARCH && !default_options(h->cfg)) continue;
       if (fsp_status s = set_tiles(h, dir, v)) return s;
       float ms = 0;
       if (fsp_status s = time_direction(h, dir, st, &ms)) return s;

@@ -190,7 +190,9 @@ struct TileShape {
 };
 
 // Marching xi pass: each warp owns one grid row segment of at most MARCH_SEG nodes and
-// walks along it 32 nodes at a time; four warps (four rows of one block) per CTA.
+// walks along it 32 nodes at a time; four warps (four rows of one block) per CTA.  The
+// marching passes (xi and eta) are compiled for the default options only (ppm = 1,
+// linear_weights = 0, interp = 0); a batch with other options runs the tile variants.
 constexpr int MARCH_WARPS = 4;
 constexpr int MARCH_SEG = 512;
 constexpr int RING = 64;                             // node ring slots per warp
@@ -270,11 +272,15 @@ __device__ __forceinline__ void node_split(const Real q[4], double mx, double my
 // Q_{p+1} ("-" side, the mirror), WENO interpolation of the characteristic differences, the
 // states Q+- at the midpoint, and the midpoint fluxes with the midpoint metrics interpolated
 // as in the metric evaluation (Section 2.4).
-template <int S, typename Real, typename Acc, typename At>
+// DEF: the configuration options take their defaults as compile-time constants (mapped
+// nonlinear weights, order-matched midpoint interpolation), so the marching kernels carry no
+// branches on them; the tile kernels read them at run time.
+template <int S, typename Real, typename Acc, bool DEF = false, typename At>
 __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
-                                              int ppm, int linw, int interp, Acc A, Mid<Real, Acc>& mo) {
+                                              int ppm_, int linw_, int interp_, Acc A, Mid<Real, Acc>& mo) {
   using Sc = Scheme<S>;
   constexpr int SC = weno_scale<Sc::r>();
+  const int ppm = DEF ? 1 : ppm_, linw = DEF ? 0 : linw_, interp = DEF ? 0 : interp_;
   const int o0 = at(0), o1 = at(1);
   // unit direction of the averaged metrics (the mean's factor 1/2 cancels in the normalisation)
   Real m0x, m0y, m1x, m1y;
@@ -745,7 +751,7 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
     if (q <= s1 + NMP - 2) {   // interfaces s0 - NMP .. s1 + NMP - 2
       auto at = [&](int mm) { return (q + mm) & (RING - 1); };
       Mid<Real, Acc> mo;
-      interface_mid<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
+      interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
       if constexpr (NMP == 1) {
         Acc h[4];
         h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h);
@@ -948,7 +954,7 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
     if (on && q <= s1 + NMP - 2) {
       auto at = [&](int mm) { return slot(q + mm); };
       Mid<Real, Acc> mo;
-      interface_mid<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
+      interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
       if constexpr (NMP == 1) {
         Acc h[4];
         h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h);

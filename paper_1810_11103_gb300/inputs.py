@@ -377,3 +377,126 @@ def smooth_field(shape, seed: int, modes: int = 3, block: int = 11) -> np.ndarra
             amp, ph1, ph2 = 2.0 * r[k] - 1.0, 2.0 * math.pi * r[k + 1], 2.0 * math.pi * r[k + 2]
             out += amp * np.sin(math.pi * (a + 1) * s + ph1)[None, :] * np.sin(math.pi * (b + 1) * t + ph2)[:, None]
     return out / max(np.abs(out).max(), 1e-300)
+
+
+# ----------------------------------------------------------------------------------------
+# The paper's own test problems (Sections 6.1-6.3), at the paper's sizes
+# ----------------------------------------------------------------------------------------
+def _line_1d(n: int, lo: float, hi: float):
+    """n uniform nodes on [lo, hi] (both ends included) as a single periodic row."""
+    xs = lo + (hi - lo) * np.arange(n, dtype=np.float64) / (n - 1)
+    return xs[None, :].copy(), np.zeros((1, n)), ((0.0, 0.0), (0.0, (hi - lo) / (n - 1)))
+
+
+def paper_sod(n: int = 100, gamma: float = GAMMA):
+    """Section 6.2 (1): [-5, 5] with n uniform nodes; (rho, u, p) = (0.125, 0, 0.1) for
+    x < 0 and (1, 0, 1) for x >= 0 (the low-pressure side on the left); the paper runs to
+    t = 2 with dt = 0.01.  Returns x (1, n), y (1, n), Q (4, 1, n), period."""
+    x, y, per = _line_1d(n, -5.0, 5.0)
+    left = x < 0.0
+    Q = conservative(np.where(left, 0.125, 1.0), np.zeros_like(x), np.zeros_like(x), np.where(left, 0.1, 1.0),
+                     gamma)
+    return x, y, Q, per
+
+
+def shu_osher(n: int = 400, gamma: float = GAMMA):
+    """Section 6.2 (2): [-5, 5] with n uniform nodes; (rho, u, p) = (3.857143, 2.629369,
+    10.3333) for x < -4 and (1 + 0.2 sin 5x, 0, 1) for x >= -4; the paper runs to t = 1.8
+    with dt = 0.001.  Returns x (1, n), y (1, n), Q (4, 1, n), period."""
+    x, y, per = _line_1d(n, -5.0, 5.0)
+    left = x < -4.0
+    Q = conservative(np.where(left, 3.857143, 1.0 + 0.2 * np.sin(5.0 * x)), np.where(left, 2.629369, 0.0),
+                     np.zeros_like(x), np.where(left, 10.3333, 1.0), gamma)
+    return x, y, Q, per
+
+
+def paper_vortex_grid(imax: int = 81, length: float = 16.0, amp: float = 0.45, seed: int = 1814,
+                      randomized: bool = True):
+    """Section 6.1 (1) with the periodic boundaries of Section 6.3 (1): the imax x imax grid
+    lines of [-L/2, L/2]^2, whose last line is the periodic image of the first, so imax - 1
+    unique nodes per direction (h = L/(imax - 1)); nodes of the window 1-based i, j =
+    5..imax-4 moved by the formula of Section 6.1 (1) with A = amp.  Returns x, y, period."""
+    n = imax - 1
+    h = length / n
+    s = -length / 2 + h * np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(s, s)
+    if randomized:
+        A = np.zeros((n, n))
+        A[4:imax - 4, 4:imax - 4] = amp
+        X, Y = randomize(X, Y, h, h, A, seed)
+    return X, Y, ((length, 0.0), (0.0, length))
+
+
+def paper_vortex_state(x, y, period, gamma: float = GAMMA) -> np.ndarray:
+    """Section 6.3 (1): free stream of density 1 and sound speed 1 (p = 1/gamma) at Mach 1
+    along +x, with the isentropic vortex at the origin (r_c = 1, alpha = 0.204,
+    epsilon = 0.3).  Over t = 16 (one period of the L = 16 box) it returns to its start."""
+    L = period[0][0]
+    return isentropic_vortex(x, y, (0.0, 0.0), strength=0.3 * 2.0 * math.pi, free=(1.0, 1.0, 0.0, 1.0 / gamma),
+                             period=(L, L), alpha=0.204, rc=1.0, gamma=gamma)
+
+
+def paper_cylinder(imax: int = 121, jmax: int = 41, randomized: bool = True, seed: int = 1815, amp: float = 0.2,
+                   r_body: float = 0.5, outer=(1.6, 3.2), mach: float = 4.0, gamma: float = GAMMA):
+    """Section 6.1 (2): the upstream half of a cylinder of diameter one in a Mach 4 stream
+    along +x, imax streamwise x jmax wall-normal nodes.  The smooth grid is the ordinary
+    transfinite (linear) interpolation between the body, r = 0.5 for theta from 270 down to
+    90 degrees, and an outer ellipse (semi-axes outer[0] along x, outer[1] along y) that holds
+    the bow shock; the randomised grid moves the nodes of the window (6, imax - 5) x
+    (7, jmax - 6) (1-based) by amp times the local spacing along one grid direction.
+    Faces: i-min and i-max transmissive (supersonic outflow), j-min slip wall, j-max far
+    field (the free stream enters).  Free stream: rho = 1, p = 1/gamma, u = mach.
+    Returns x, y, bc, bc_state."""
+    # theta from 270 down to 90 degrees: with the wall-normal index outward the grid is right-handed
+    th = 1.5 * math.pi - math.pi * np.arange(imax, dtype=np.float64) / (imax - 1)
+    s = np.arange(jmax, dtype=np.float64) / (jmax - 1)
+    xb, yb = r_body * np.cos(th), r_body * np.sin(th)
+    xo, yo = outer[0] * np.cos(th), outer[1] * np.sin(th)
+    x = (1.0 - s)[:, None] * xb[None, :] + s[:, None] * xo[None, :]
+    y = (1.0 - s)[:, None] * yb[None, :] + s[:, None] * yo[None, :]
+    if randomized:
+        A = np.zeros((jmax, imax))
+        A[6:jmax - 6, 5:imax - 5] = amp
+        x, y = randomize_local(x, y, A, seed)
+    free = conservative(1.0, mach, 0.0, 1.0 / gamma, gamma)
+    return x, y, (1, 1, BC_WALL, BC_FAR), np.tile(free, (4, 1))
+
+
+def _box_grid(n: int, lo, hi, amp: float, margin: int, seed: int, randomized: bool):
+    """n x n grid lines of the box [lo, hi]; with `randomized`, the nodes more than `margin`
+    layers inside the boundary moved by the formula of Section 6.1 (1) (h = the spacing)."""
+    hx, hy = (hi[0] - lo[0]) / (n - 1), (hi[1] - lo[1]) / (n - 1)
+    X, Y = np.meshgrid(lo[0] + hx * np.arange(n, dtype=np.float64), lo[1] + hy * np.arange(n, dtype=np.float64))
+    if randomized:
+        A = np.zeros((n, n))
+        A[margin:n - margin, margin:n - margin] = amp
+        X, Y = randomize(X, Y, hx, hy, A, seed)
+    return X, Y
+
+
+def paper_riemann_grid(n: int = 401, randomized: bool = True, seed: int = 1816):
+    """Section 6.1 (3): [0, 1]^2 with n x n grid lines (the paper's 400 x 400 cells), four
+    uniform layers at the boundaries, A = 0.2 inside."""
+    return _box_grid(n, (0.0, 0.0), (1.0, 1.0), 0.2, 4, seed, randomized)
+
+
+def paper_riemann_state(x, y, gamma: float = GAMMA) -> np.ndarray:
+    """Section 6.3 (3): (rho, u, v, p) = (1, 0, -0.3, 1) on [0.5, 1]^2, (2, 0, 0.3, 1) on
+    [0, 0.5] x [0.5, 1], (1.0625, 0, 0.8145, 0.4) on [0, 0.5]^2, (0.5313, 0, 0.4276, 0.4) on
+    [0.5, 1] x [0, 0.5]; the paper runs to t = 0.3 with dt = 0.001 (uniform grid) or 0.0001
+    (randomised grid)."""
+    right, up = x >= 0.5, y >= 0.5
+    states = ((right & up, (1.0, 0.0, -0.3, 1.0)), (~right & up, (2.0, 0.0, 0.3, 1.0)),
+              (~right & ~up, (1.0625, 0.0, 0.8145, 0.4)), (right & ~up, (0.5313, 0.0, 0.4276, 0.4)))
+    out = np.zeros((4,) + x.shape)
+    for mask, w in states:
+        q = conservative(*(np.full(x.shape, c) for c in w), gamma=gamma)
+        out[:, mask] = q[:, mask]
+    return out
+
+
+def paper_shock_vortex_grid(n: int = 601, randomized: bool = True, seed: int = 1817):
+    """Section 6.1 (3): [-20, 10] x [-15, 15] with n x n grid lines (the paper's 600 x 600
+    cells), nine uniform layers at the boundaries, A = 0.2 inside; the state is
+    shock_vortex_state with the paper's Mach 3 shock, run to t = 15 with dt = 0.01."""
+    return _box_grid(n, (-20.0, -15.0), (10.0, 15.0), 0.2, 9, seed, randomized)

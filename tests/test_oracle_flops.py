@@ -50,5 +50,6 @@ def test_sweep_count_affine_in_line_length(scheme):
 
 def test_stored_counts_match_the_script():
     with open(os.path.join(ROOT, "paper_1810_11103_gb300", "algorithmic_flops.json")) as f:
-        stored = json.load(f)["schemes"]
-    assert CF.vortex_counts() == stored
+        stored = json.load(f)
+    assert CF.vortex_counts() == stored["schemes"]
+    assert CF.adjoint_counts() == stored["adjoint"]["schemes"]

@@ -166,9 +166,9 @@ MUTANTS = [
     ("dual_sqrt", "a.d / (2.0 * s)", "a.d / s",
      [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_rk3_tangent_matches_finite_differences"]),
     # reverse mode (the tape behind the oracle's adjoints)
-    ("rev_sub_sign", "rev_rec(a.v - b.v, a.i, 1.0, b.i, -1.0)", "rev_rec(a.v - b.v, a.i, 1.0, b.i, 1.0)",
+    ("rev_sub_sign", "rev_rec(a.v - b.v, a.i, 1.0, b.i, -1.0, 1)", "rev_rec(a.v - b.v, a.i, 1.0, b.i, 1.0, 1)",
      [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_rhs_vjp_matches_finite_differences"]),
-    ("rev_product_swap", "rev_rec(a.v * b.v, a.i, b.v, b.i, a.v)", "rev_rec(a.v * b.v, a.i, a.v, b.i, b.v)",
+    ("rev_product_swap", "rev_rec(a.v * b.v, a.i, b.v, b.i, a.v, 2)", "rev_rec(a.v * b.v, a.i, a.v, b.i, b.v, 2)",
      [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_metrics_vjp_is_the_transposed_tangent[0]"]),
     ("rev_quotient_sign", "1.0 / b.v, b.i, -q / b.v", "1.0 / b.v, b.i, q / b.v",
      [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_rk3_vjp_is_the_transposed_tangent"]),

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from oracle import oracle as OO   # the functions (oracle.count_flops is also a submodule name)
 from paper_1810_11103_gb300 import inputs as I
 
 DOT_TOL = 1e-12
@@ -116,5 +117,20 @@ def test_vjp_operation_count():
     c = O.count_vjp_flops(cfg, M, q)
     ops = c["records"] - (M.size + q.size)
     assert 0 < ops <= c["reverse"] <= 4 * ops
-    assert c["forward"] == O.count_flops(cfg, M, q)
+    assert c["forward"] == OO.count_flops(cfg, M, q)
     assert 0 < c["partials"] < c["forward"]
+
+
+def test_vjp_count_affine_in_line_length():
+    """With the line count fixed, the count is affine in the line length (each line is the same
+    program); with linear weights no data-dependent branch (the mapping's two sides) changes it,
+    so the affinity is exact.  This lets the stored per-node figure be evaluated at the
+    workload's size from two smaller grids."""
+    tot = []
+    for ni in (16, 24, 32):
+        x, y, per = I.periodic_square(ni, 8.0, 0.2, seed=21, nj=12)
+        q = I.random_state(x.shape, seed=3)
+        cfg = dict(scheme=2, period=per, linear_weights=1)
+        c = O.count_vjp_flops(cfg, O.metrics(cfg, x, y), q)
+        tot.append(c["forward"] + c["partials"] + c["reverse"])
+    assert tot[2] - tot[1] == tot[1] - tot[0] > 0
