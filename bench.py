@@ -413,6 +413,8 @@ def measure_cylinder(args, prec, C, per_block=False):
     D = [torch.empty(q.shape, dtype=torch.float32 if prec == "fp32" else torch.float64, device=C.dev) for q in bt.Q]
     bt.flux_difference(0, D)
     t_k = C.timed(lambda: bt.flux_difference(0, D), 20) / 20
+    bt.flux_difference(1, D)
+    t_e = C.timed(lambda: bt.flux_difference(1, D), 20) / 20
     peak, pipe = C.peak(prec)
     t_dev, t_e2e = C.max_over_ranks(t_dev, t_e2e)
     fl = algorithmic_flops(args)
@@ -427,7 +429,11 @@ def measure_cylinder(args, prec, C, per_block=False):
             "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
             "nominal_peak": nom, "frac_vs_nominal": achieved / nom,
             "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
-            "kernel_ms": 1e3 * t_k}
+            "kernel_ms": 1e3 * t_k,
+            # the other sweep and the whole step against the same peak
+            "eta": {"kernel_ms": 1e3 * t_e, "flops_per_node": fl["sweep_eta_per_node"] - 4.0,
+                    "frac": (fl["sweep_eta_per_node"] - 4.0) * nodes / t_e / 1e12 / peak},
+            "step_frac": 3 * fl["rhs_per_node"] * nodes / (t_dev / args.steps) / 1e12 / peak}
     if prec == "mixed":
         roof = mixed_roofline(args, C, roof, fl["sweep_xi_per_node"], nodes, t_k, clk.get("sm_mhz"))
     out = {
@@ -487,6 +493,12 @@ def mixed_roofline(args, C, roof, flops_node, nodes, t_k, mhz):
               "frac_vs_nominal": f64 * nodes / t_k / 1e12 / n64}
     head, other = (part64, part32) if t64 >= t32 else (part32, part64)
     out = dict(roof)
+    # the eta sweep and the whole step against the bounding part as well (FP64 operations of the
+    # two sweeps; the float line maxima are left out of the bound)
+    te = roof["eta"]["kernel_ms"] / 1e3
+    out["eta"] = {"kernel_ms": roof["eta"]["kernel_ms"], "flops_per_node": f64,
+                  "frac": f64 * nodes / te / 1e12 / p64, "part": "FP64 part"}
+    out["step_frac"] = None
     out.update({"bound": "alu", "achieved": head["achieved"], "peak": head["peak"], "frac": head["frac"],
                 "nominal_peak": head["nominal_peak"], "frac_vs_nominal": head["frac_vs_nominal"],
                 "flops_per_node": head["flops_per_node"],
@@ -596,6 +608,17 @@ def measure_adjoint(args, C, nsteps=200, every=14):
     gradient(0)
     t_grad_tape = C.timed(lambda: gradient(0), 1)
     tape_gb = nsteps * fsp.rk3_tape(cfg, Q).numel() / 1e9
+    # roofline of fsp_rhs_vjp: the oracle's operation count of one right-hand-side adjoint
+    # (its forward right-hand side, the partial derivatives and the reverse sweep), per node
+    with open(os.path.join(ROOT, "paper_1810_11103_gb300", "algorithmic_flops.json")) as f:
+        vjp_flops = json.load(f)["adjoint"]["schemes"][SCHEME_NAMES[args.scheme]]["vjp_per_node"]
+    peak, _ = C.peak("fp64")
+    achieved = vjp_flops * x.size / t_rhs_vjp / 1e12
+    nom = C.nominal("fp64", None)
+    roof = {"bound": "alu", "kernel": "fsp_rhs_vjp (its forward right-hand side and the adjoint kernels)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "nominal_peak": nom, "frac_vs_nominal": achieved / nom, "flops_per_node": vjp_flops,
+            "units_per_launch": x.size, "peak_source": "FP64 FMA probe (fsp_fma_peak) in this run"}
     return {
         "workload": f"shock_vortex512: 512x512 stretched grid, Mach 1.1 shock + vortex, {SCHEME_NAMES[args.scheme]}, "
                     f"FP64, {nsteps} RK3 steps at CFL 0.5, checkpoint every {every}",
@@ -604,6 +627,7 @@ def measure_adjoint(args, C, nsteps=200, every=14):
         "march_forward_s": t_fwd, "march_gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd,
         "full_tape": {"march_gradient_s": t_grad_tape, "gradient_over_forward": t_grad_tape / t_fwd,
                       "tape_gb": tape_gb, "how": "every step recorded in the forward pass, no replay"},
+        "roofline": roof,
     }
 
 
@@ -752,6 +776,10 @@ def summary(args, head, others, adjoint, seventh):
         e = {"value": _r(r["value"]), "ms_step": _r(r["ms_per_step"]), "e2e": _r(r["e2e"]["value"]),
              "frac": _r(rf["frac"], 3), "frac_nominal": _r(rf.get("frac_vs_nominal"), 3),
              "xi_ms": _r(rf["kernel_ms"])}
+        if rf.get("eta"):
+            e["eta_ms"], e["eta_frac"] = _r(rf["eta"]["kernel_ms"]), _r(rf["eta"]["frac"], 3)
+        if rf.get("step_frac"):
+            e["step_frac"] = _r(rf["step_frac"], 3)
         if p == "mixed":
             e["part"] = rf.get("part")
         if r.get("per_block"):

@@ -243,6 +243,40 @@ static const SchemeTab TAB[5] = {
    {8841.0L / 107520, -6069.0L / 107520, 1261.0L / 107520, -121.5L / 107520}, {1.0L, 0.0L}},
 };
 
+// The one-midpoint forms with their free parameter alpha (Eq. 3.5 for WENOIU3-1MP, Eq. 3.17
+// for WENOIU5-1MP, the Appendix's scheme (1) for WENOIU7-1MP): h+ = alpha f_{j+1/2} +
+// sum_k n_k(alpha) f_{j+k}; alpha = 1 gives the schemes of TAB.  The central operator that the
+// metrics need is the central part of the scheme (Eq. 2.7): delta^{c,(1)} = (delta+ + delta-)/2
+// with delta+ f_j = h+_{j+1/2} - h+_{j-1/2} and delta- its mirror, which gives
+//   b_{1/2} = alpha,  a_d = (n_d - n_{d+1} + n_{1-d} - n_{-d}) / 2  (d = 1..4).
+// For alpha = 1 the printed coefficients of TAB are used as they stand.
+static SchemeTab scheme_tab(int scheme, long double alpha) {
+  if (alpha == 1.0L || scheme < 0 || scheme > 4) return TAB[scheme < 0 || scheme > 4 ? 0 : scheme];
+  SchemeTab S = TAB[scheme];
+  long double n[7] = {0, 0, 0, 0, 0, 0, 0};   // n[k + 3] = n_k
+  const long double a = alpha;
+  if (scheme == S31) {          // Eq. (3.5)
+    n[2] = a / 8 - 1.0L / 6; n[3] = -3 * a / 4 + 5.0L / 6; n[4] = -3 * a / 8 + 1.0L / 3;
+  } else if (scheme == S51) {   // Eq. (3.17)
+    n[1] = -3 * a / 128 + 1.0L / 30; n[2] = 5 * a / 32 - 13.0L / 60; n[3] = -45 * a / 64 + 47.0L / 60;
+    n[4] = -15 * a / 32 + 9.0L / 20; n[5] = 5 * a / 128 - 1.0L / 20;
+  } else if (scheme == S71) {   // Appendix, scheme (1)
+    n[0] = 5 * a / 1024 - 1.0L / 140; n[1] = -21 * a / 512 + 5.0L / 84; n[2] = 175 * a / 1024 - 101.0L / 420;
+    n[3] = -175 * a / 256 + 319.0L / 420; n[4] = -525 * a / 1024 + 107.0L / 210; n[5] = 35 * a / 512 - 19.0L / 210;
+    n[6] = -7 * a / 1024 + 1.0L / 105;
+  } else {
+    return S;                   // the two-midpoint schemes have no free parameter (checked by the callers)
+  }
+  auto nk = [&](int k) { return k < -3 || k > 3 ? 0.0L : n[k + 3]; };
+  S.hmid[0] = a;
+  S.hmid[1] = 0.0L;
+  for (int k = 0; k < 7; ++k) S.hnode[k] = n[k];
+  for (int d = 1; d <= 4; ++d) S.cnode[d - 1] = (nk(d) - nk(d + 1) + nk(1 - d) - nk(-d)) / 2;
+  S.cmid[0] = a;
+  S.cmid[1] = 0.0L;
+  return S;
+}
+
 // ----------------------------------------------------------------------------------
 // Run parameters
 // ----------------------------------------------------------------------------------
@@ -255,19 +289,29 @@ struct Par {
                        // 1 = two-point average.
   int ppm = 1;         // 1: piecewise-polynomial mapping of the weights, Eq. (3.15)/(3.23)
   int linw = 0;        // 1: linear weights omega_k = C_k (no mapping)
+  int weights = 0;     // 0: the weights of Eqs. (3.12)-(3.13); 1: WENO-Z weights (Section 7)
+  int midsplit = 0;    // splitting of the midpoint flux: 0 Lax-Friedrichs type (Section 2.3),
+                       // 1 Steger-Warming, 2 Van Leer (Section 7)
   int bc[4] = {0, 0, 0, 0};
   T gamma = T(1.4), alpha = cst<T>(1.1L), eps = cst<T>(1e-40L);
+  long double halpha = 1.0L;   // the free parameter of the one-midpoint forms (3.5), (3.17), Appendix (1)
+  SchemeTab tab;               // coefficients of the scheme at halpha
   T bcq[4][4];
   int ni = 0, nj = 0;
 };
 
+// ip = {scheme, interp, ppm, linear_weights, bc[4], weights, midsplit}; dp = {gamma, lf_alpha,
+// eps, bc_state[4][4], scheme alpha}
 template <class T>
 static void unpack(const int* ip, const double* dp, int ni, int nj, Par<T>& P) {
   P.scheme = ip[0]; P.interp = ip[1]; P.ppm = ip[2]; P.linw = ip[3];
   for (int f = 0; f < 4; ++f) P.bc[f] = ip[4 + f];
+  P.weights = ip[8]; P.midsplit = ip[9];
   P.gamma = T(dp[0]); P.alpha = T(dp[1]); P.eps = T(dp[2]);
   for (int f = 0; f < 4; ++f)
     for (int v = 0; v < 4; ++v) P.bcq[f][v] = T(dp[3 + 4 * f + v]);
+  P.halpha = dp[19];
+  P.tab = scheme_tab(P.scheme, P.halpha);
   P.ni = ni; P.nj = nj;
 }
 
@@ -354,7 +398,7 @@ struct Coords {
 // (0 = x, 1 = y).  Midpoint values f~ come from the interpolation I above.
 template <class T>
 static T central_D(const Par<T>& P, const Coords<T>& C, int dir, int comp, int i, int j) {
-  const SchemeTab& S = TAB[P.scheme];
+  const SchemeTab& S = P.tab;
   auto node = [&](int k) {
     T X, Y;
     if (dir == 0) C.at(i + k, j, X, Y); else C.at(i, j + k, X, Y);
@@ -421,6 +465,60 @@ static T spectral(const T* q, T mx, T my, T gamma) {
   T p = (gamma - cst<T>(1)) * (q[3] - cst<T>(0.5L) * rho * (u * u + v * v));
   T c = sqrt(gamma * p / rho);
   return fabs(mx * u + my * v) + c * sqrt(mx * mx + my * my);
+}
+
+// Splittings of the metric-weighted flux E^ = mx E + my F along k = (mx, my) for the midpoint
+// flux f_{j+1/2}; Section 7 names Steger-Warming and Van Leer as alternatives that keep
+// free-stream preservation.  sign = +1 gives F+, -1 gives F-; F+ + F- = E^.  With
+// n = k/|k|, Un = u.n and the eigenvalues |k| (Un - c, Un, Un + c):
+// Steger-Warming: F+- = rho/(2 gamma) [l1+- (1, u - c nx, v - c ny, H - c Un)
+//   + 2 (gamma - 1) l2+- (1, u, v, |u|^2/2) + l3+- (1, u + c nx, v + c ny, H + c Un)],
+//   l+- = (l +- |l|)/2.
+template <class T>
+static void split_sw(const T* q, T mx, T my, T gamma, int sign, T* f) {
+  T rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  T q2 = u * u + v * v;
+  T p = (gamma - cst<T>(1)) * (q[3] - cst<T>(0.5L) * rho * q2);
+  T c = sqrt(gamma * p / rho);
+  T kn = sqrt(mx * mx + my * my), nx = mx / kn, ny = my / kn;
+  T Un = u * nx + v * ny, H = (q[3] + p) / rho;
+  T l[3] = {kn * (Un - c), kn * Un, kn * (Un + c)};
+  for (int i = 0; i < 3; ++i) l[i] = cst<T>(0.5L) * (l[i] + (sign > 0 ? fabs(l[i]) : -fabs(l[i])));
+  T a = rho / (cst<T>(2) * gamma), g2 = cst<T>(2) * (gamma - cst<T>(1));
+  f[0] = a * (l[0] + g2 * l[1] + l[2]);
+  f[1] = a * (l[0] * (u - c * nx) + g2 * l[1] * u + l[2] * (u + c * nx));
+  f[2] = a * (l[0] * (v - c * ny) + g2 * l[1] * v + l[2] * (v + c * ny));
+  f[3] = a * (l[0] * (H - c * Un) + (gamma - cst<T>(1)) * l[1] * q2 + l[2] * (H + c * Un));
+}
+// Van Leer, with the normal Mach number M = Un/c: for M >= 1, F+ = E^ and F- = 0 (and the
+// reverse for M <= -1); otherwise the mass flux m+- = +- rho c |k| (M +- 1)^2 / 4 and
+// F+- = m+- (1, u + nx (-Un +- 2c)/gamma, v + ny (-Un +- 2c)/gamma,
+//             ((gamma - 1) Un +- 2c)^2 / (2 (gamma^2 - 1)) + (|u|^2 - Un^2)/2).
+template <class T>
+static void split_vl(const T* q, T mx, T my, T gamma, int sign, T* f) {
+  T rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  T q2 = u * u + v * v;
+  T p = (gamma - cst<T>(1)) * (q[3] - cst<T>(0.5L) * rho * q2);
+  T c = sqrt(gamma * p / rho);
+  T kn = sqrt(mx * mx + my * my), nx = mx / kn, ny = my / kn;
+  T Un = u * nx + v * ny, M = Un / c;
+  if (M >= T(1) || M <= T(-1)) {
+    if ((M >= T(1)) == (sign > 0)) {
+      flux(q, mx, my, gamma, f);
+    } else {
+      for (int i = 0; i < 4; ++i) f[i] = T(0);
+    }
+    return;
+  }
+  T s = sign > 0 ? T(1) : T(-1);
+  T mp = M + s;
+  T fm = s * rho * c * kn * mp * mp / cst<T>(4);
+  T w = (s * cst<T>(2) * c - Un) / gamma;
+  T e = (gamma - cst<T>(1)) * Un + s * cst<T>(2) * c;
+  f[0] = fm;
+  f[1] = fm * (u + nx * w);
+  f[2] = fm * (v + ny * w);
+  f[3] = fm * (e * e / (cst<T>(2) * (gamma * gamma - cst<T>(1))) + cst<T>(0.5L) * (q2 - Un * Un));
 }
 
 // Left/right eigenvectors of the Jacobian of the flux in direction n (unit vector),
@@ -531,7 +629,7 @@ static T ppm_map(int order, T w, T C) {
   return C + d * d * d / (e * e);
 }
 
-struct WenoOpt { int ppm, linw; };
+struct WenoOpt { int ppm, linw, z = 0; };   // z: WENO-Z weights (no mapping)
 
 // WENO interpolation to x_{j+1/2} from u[m + 3] = u_{j+m}, m = -3..3 (Eqs. 3.10-3.13;
 // candidates of Table 1, or Table A1 for r = 4).
@@ -588,6 +686,19 @@ static T weno_mid(int r, const T* u, const WenoOpt& o, T eps) {
   T w[4];
   if (o.linw) {
     for (int k = 0; k < r; ++k) w[k] = Ck[k];
+  } else if (o.z) {
+    // WENO-Z weights (Section 7 names them; Borges et al.'s form with the squared ratio):
+    // alpha_k = C_k (1 + (tau / (eps + IS_k))^2), omega_k = alpha_k / sum alpha, with the
+    // global indicator tau = |IS_0 - IS_{r-1}| (r = 2, 3) or |IS_0 + 3 IS_1 - 3 IS_2 - IS_3|
+    // (r = 4).  The mapping is not applied.
+    T tau = r == 4 ? fabs(IS[0] + cst<T>(3) * IS[1] - cst<T>(3) * IS[2] - IS[3]) : fabs(IS[0] - IS[r - 1]);
+    T a[4], s = T(0);
+    for (int k = 0; k < r; ++k) {
+      T q = tau / (eps + IS[k]);
+      a[k] = Ck[k] * (cst<T>(1) + q * q);
+      s = s + a[k];
+    }
+    for (int k = 0; k < r; ++k) w[k] = a[k] / s;
   } else {
     // alpha_k = C_k / (eps + IS_k)^2, omega_k = alpha_k / sum alpha (Eqs. 3.12-3.13)
     T a[4], s = T(0);
@@ -699,11 +810,11 @@ static T line_lambda(const Field<T>& F, int dir, int L) {
 template <class T>
 static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
   const Par<T>& P = F.P;
-  const SchemeTab& S = TAB[P.scheme];
+  const SchemeTab& S = P.tab;
   const int n = dir == 0 ? P.ni : P.nj, nl = dir == 0 ? P.nj : P.ni;
   const int NB = n + 8;           // nodes s = -4 .. n+3, stored at s + 4
   const int NI = n + 3;           // interfaces p + 1/2, p = -2 .. n, stored at p + 2
-  const WenoOpt wo{P.ppm, P.linw};
+  const WenoOpt wo{P.ppm, P.linw, P.weights};
   std::vector<T> q(4 * NB), mxs(NB), mys(NB), fp(4 * NB), fm(4 * NB);
   std::vector<T> fpm(4 * NI), fmm(4 * NI), Hh(4 * NI);
   for (int L = 0; L < nl; ++L) {
@@ -760,11 +871,22 @@ static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
       T mmx = interp_mid<T>(P.scheme, P.interp, [&](int l) { return mxs[c0 + l]; });
       T mmy = interp_mid<T>(P.scheme, P.interp, [&](int l) { return mys[c0 + l]; });
       T fpl[4], fmi[4];
-      flux(Qs[0], mmx, mmy, P.gamma, fpl);
-      flux(Qs[1], mmx, mmy, P.gamma, fmi);
-      for (int v = 0; v < 4; ++v) {
-        fpm[4 * (p + 2) + v] = cst<T>(0.5L) * (fpl[v] + A * Qs[0][v]);
-        fmm[4 * (p + 2) + v] = cst<T>(0.5L) * (fmi[v] - A * Qs[1][v]);
+      if (P.midsplit == 0) {
+        // the Lax-Friedrichs-type splitting of the nodes (Section 2.3)
+        flux(Qs[0], mmx, mmy, P.gamma, fpl);
+        flux(Qs[1], mmx, mmy, P.gamma, fmi);
+        for (int v = 0; v < 4; ++v) {
+          fpm[4 * (p + 2) + v] = cst<T>(0.5L) * (fpl[v] + A * Qs[0][v]);
+          fmm[4 * (p + 2) + v] = cst<T>(0.5L) * (fmi[v] - A * Qs[1][v]);
+        }
+      } else {
+        // Steger-Warming or Van Leer at the midpoint (Section 7)
+        if (P.midsplit == 1) { split_sw(Qs[0], mmx, mmy, P.gamma, 1, fpl); split_sw(Qs[1], mmx, mmy, P.gamma, -1, fmi); }
+        else { split_vl(Qs[0], mmx, mmy, P.gamma, 1, fpl); split_vl(Qs[1], mmx, mmy, P.gamma, -1, fmi); }
+        for (int v = 0; v < 4; ++v) {
+          fpm[4 * (p + 2) + v] = fpl[v];
+          fmm[4 * (p + 2) + v] = fmi[v];
+        }
       }
     }
     // h = h+ + h-; h- mirrors h+ about x_{p+1/2}: f_{p+k} -> f_{p+1-k},
@@ -857,9 +979,9 @@ static T cfl_dt(const Par<T>& P, const T* M, const T* Q, T cfl) {
 // dt = 2 / ceil(2 / dx^{5/4}), final time t.
 // ----------------------------------------------------------------------------------
 static void advect_rhs(int scheme, int N, double dx, const std::vector<double>& u,
-                       std::vector<double>& du) {
+                       std::vector<double>& du, int z = 0) {
   const SchemeTab& S = TAB[scheme];
-  const WenoOpt wo{1, 0};
+  const WenoOpt wo{1, 0, z};
   auto U = [&](int k) { return u[(size_t)(((k % N) + N) % N)]; };
   std::vector<double> fmid(N), h(N);
   for (int p = 0; p < N; ++p) {              // f+_{p+1/2}
@@ -878,7 +1000,7 @@ static void advect_rhs(int scheme, int N, double dx, const std::vector<double>& 
   for (int p = 0; p < N; ++p) du[p] = -(h[p] - h[(p + N - 1) % N]) / dx;
 }
 
-static void advect1d(int scheme, int N, double tfinal, double* out, double dt_exp = 1.25) {
+static void advect1d(int scheme, int N, double tfinal, double* out, double dt_exp = 1.25, int z = 0) {
   const double PI = 3.14159265358979323846;
   const double dx = 2.0 / N;
   auto u0 = [&](double x) { return std::sin(PI * x - std::sin(PI * x) / PI); };
@@ -887,13 +1009,13 @@ static void advect1d(int scheme, int N, double tfinal, double* out, double dt_ex
   const int nsteps = (int)std::ceil(tfinal / std::pow(dx, dt_exp));
   const double dt = tfinal / nsteps;
   for (int st = 0; st < nsteps; ++st) {
-    advect_rhs(scheme, N, dx, u, k1);
+    advect_rhs(scheme, N, dx, u, k1, z);
     for (int i = 0; i < N; ++i) tmp[i] = u[i] + 0.5 * dt * k1[i];
-    advect_rhs(scheme, N, dx, tmp, k2);
+    advect_rhs(scheme, N, dx, tmp, k2, z);
     for (int i = 0; i < N; ++i) tmp[i] = u[i] + 0.5 * dt * k2[i];
-    advect_rhs(scheme, N, dx, tmp, k3);
+    advect_rhs(scheme, N, dx, tmp, k3, z);
     for (int i = 0; i < N; ++i) tmp[i] = u[i] + dt * k3[i];
-    advect_rhs(scheme, N, dx, tmp, k4);
+    advect_rhs(scheme, N, dx, tmp, k4, z);
     for (int i = 0; i < N; ++i) u[i] += dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
   }
   double s2 = 0.0, smax = 0.0;
@@ -996,6 +1118,7 @@ static int check(const int* ip, int ni, int nj) {
   for (int f = 0; f < 4; ++f)
     if (ip[4 + f] < 0 || ip[4 + f] > BC_FARFIELD) return 5;   // links need the multi-block entry
   if (ip[0] < 0 || ip[0] > 4) return 2;
+  if (ip[8] < 0 || ip[8] > 1 || ip[9] < 0 || ip[9] > 2) return 7;
   if ((ip[4] == BC_PERIODIC) != (ip[5] == BC_PERIODIC)) return 3;
   if ((ip[6] == BC_PERIODIC) != (ip[7] == BC_PERIODIC)) return 3;
   if (ip[4] != BC_PERIODIC && ni < 9) return 4;
@@ -1062,18 +1185,26 @@ static int mb_setup(const int* ip, const double* dp, int nb, const int* dims, co
 
 using namespace orc;
 
+// the metric entry points: the defaults, then the caller's options (nullable); only the
+// scheme's free parameter dp[19] matters for the metrics
+static void opts(const double* in, double* dp) {
+  for (int k = 3; k < 19; ++k) dp[k] = 0.0;
+  dp[19] = 1.0;
+  if (in) for (int k = 0; k < 20; ++k) dp[k] = in[k];
+}
+
 extern "C" {
 
-// ip = {scheme, interp, ppm, linear_weights, bc[0..3]}
-// dp = {gamma, lf_alpha, eps, bc_state[4][4] (conservative, per face)}
+// ip = {scheme, interp, ppm, linear_weights, bc[0..3], weights, midsplit}
+// dp = {gamma, lf_alpha, eps, bc_state[4][4] (conservative, per face), scheme alpha}
 // period = {dx_i, dy_i, dx_j, dy_j}
 
 size_t orc_metrics_len(int ni, int nj) { return (size_t)5 * (ni + 2 * G) * (nj + 2 * G); }
 
-int orc_metrics(const int* ip, int ni, int nj, const double* period, const double* x,
+int orc_metrics(const int* ip, const double* dpin, int ni, int nj, const double* period, const double* x,
                 const double* y, double* M) {
   if (int e = check(ip, ni, nj)) return e;
-  Par<double> P; double dp[19] = {1.4, 1.1, 1e-40};
+  Par<double> P; double dp[20] = {1.4, 1.1, 1e-40}; opts(dpin, dp);
   unpack(ip, dp, ni, nj, P);
   Coords<double> C = make_coords(P, period, x, y);
   metrics(P, C, M);
@@ -1081,10 +1212,10 @@ int orc_metrics(const int* ip, int ni, int nj, const double* period, const doubl
 }
 
 // Tangent of the metrics along (dx, dy).
-int orc_metrics_jvp(const int* ip, int ni, int nj, const double* period, const double* x,
+int orc_metrics_jvp(const int* ip, const double* dpin, int ni, int nj, const double* period, const double* x,
                     const double* y, const double* dx, const double* dy, double* M, double* dM) {
   if (int e = check(ip, ni, nj)) return e;
-  Par<Dual> P; double dp[19] = {1.4, 1.1, 1e-40};
+  Par<Dual> P; double dp[20] = {1.4, 1.1, 1e-40}; opts(dpin, dp);
   unpack(ip, dp, ni, nj, P);
   const size_t N = (size_t)ni * nj;
   std::vector<Dual> X(N), Y(N);
@@ -1226,8 +1357,8 @@ void orc_eig(double gamma, const double* q, double nx, double ny, double* L, dou
     for (int b = 0; b < 4; ++b) { L[4 * a + b] = Lm[a][b]; R[4 * a + b] = Rm[a][b]; }
 }
 
-void orc_scheme_table(int scheme, double* out /* r, hmid[2], hnode[7], cnode[4], cmid[2] */) {
-  const SchemeTab& S = TAB[scheme];
+void orc_scheme_table(int scheme, double alpha, double* out /* r, hmid[2], hnode[7], cnode[4], cmid[2] */) {
+  const SchemeTab S = scheme_tab(scheme, alpha);
   out[0] = S.r;
   for (int k = 0; k < 2; ++k) out[1 + k] = (double)S.hmid[k];
   for (int k = 0; k < 7; ++k) out[3 + k] = (double)S.hnode[k];
@@ -1246,6 +1377,30 @@ int orc_advect1d(int scheme, int N, double tfinal, double* out) {
 int orc_advect1d_dt(int scheme, int N, double tfinal, double dt_exp, double* out) {
   if (scheme < 0 || scheme > 4 || N < 7 || !(dt_exp > 0.0)) return 1;
   advect1d(scheme, N, tfinal, out, dt_exp);
+  return 0;
+}
+
+// The same with the weight option (weights = 1: WENO-Z).
+int orc_advect1d_opts(int scheme, int N, double tfinal, double dt_exp, int weights, double* out) {
+  if (scheme < 0 || scheme > 4 || N < 7 || !(dt_exp > 0.0) || weights < 0 || weights > 1) return 1;
+  advect1d(scheme, N, tfinal, out, dt_exp, weights);
+  return 0;
+}
+
+// WENO-Z interpolation to x_{j+1/2} from u7[m + 3] = u_{j+m} (r = 2, 3, 4).
+double orc_weno_z(int r, double eps, const double* u7) {
+  WenoOpt o{0, 0, 1};
+  return weno_mid<double>(r, u7, o, eps);
+}
+
+// Midpoint flux splitting mode (1 Steger-Warming, 2 Van Leer) of state q along (mx, my):
+// fp = F+, fm = F-, e = E^.
+int orc_split_flux(int mode, const double* q, double mx, double my, double gamma, double* fp, double* fm,
+                   double* e) {
+  if (mode == 1) { split_sw(q, mx, my, gamma, 1, fp); split_sw(q, mx, my, gamma, -1, fm); }
+  else if (mode == 2) { split_vl(q, mx, my, gamma, 1, fp); split_vl(q, mx, my, gamma, -1, fm); }
+  else return 1;
+  flux(q, mx, my, gamma, e);
   return 0;
 }
 
@@ -1311,10 +1466,10 @@ int orc_rk3_vjp(const int* ip, const double* dp, int ni, int nj, const double* M
 }
 
 // x_bar += (d M / d x)^T M_bar, y_bar likewise (periodic offsets are constants).
-int orc_metrics_vjp(const int* ip, int ni, int nj, const double* period, const double* x, const double* y,
+int orc_metrics_vjp(const int* ip, const double* dpin, int ni, int nj, const double* period, const double* x, const double* y,
                     const double* Mbar, double* xbar, double* ybar) {
   if (int e = check(ip, ni, nj)) return e;
-  Par<Rev> P; double dp[19] = {1.4, 1.1, 1e-40};
+  Par<Rev> P; double dp[20] = {1.4, 1.1, 1e-40}; opts(dpin, dp);
   unpack(ip, dp, ni, nj, P);
   const size_t N = (size_t)ni * nj, NM = orc_metrics_len(ni, nj);
   g_tape.clear();
@@ -1361,12 +1516,12 @@ int orc_count_vjp_flops(const int* ip, const double* dp, int ni, int nj, const d
 // dims: ni, nj per block; bcs: 4 codes per block (BC_LINK = 5 joins a face); lk: per
 // block and face (nbr, face, rev); loff: per block and face the ghost coordinate offset
 // (nullable); periods: per block the periodic vectors (dx_i, dy_i, dx_j, dy_j).
-int orc_mb_metrics(const int* ip, int nb, const int* dims, const int* bcs, const int* lk,
+int orc_mb_metrics(const int* ip, const double* dpin, int nb, const int* dims, const int* bcs, const int* lk,
                    const double* loff, const double* periods, const double* x, const double* y,
                    double* M) {
   std::vector<Par<double>> P;
   std::vector<Link> L;
-  double dp[19] = {1.4, 1.1, 1e-40};
+  double dp[20] = {1.4, 1.1, 1e-40}; opts(dpin, dp);
   if (int e = mb_setup(ip, dp, nb, dims, bcs, lk, loff, P, L)) return e;
   std::vector<Coords<double>> C(nb);
   size_t xo = 0;

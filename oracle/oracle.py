@@ -31,6 +31,7 @@ __all__ = [
     "cfl_dt", "count_flops", "count_flops_parts", "fsp_residual", "weno", "ppm", "smoothness", "eig",
     "scheme_table", "advect1d", "advect1d_dt", "smoothness4", "riemann_exact", "long_double_digits", "G",
     "mb_metrics", "mb_rhs", "mb_rk3", "rhs_vjp", "rk3_vjp", "metrics_vjp", "count_vjp_flops",
+    "advect1d_opts", "weno_z", "split_flux",
 ]
 
 G = 4
@@ -64,8 +65,8 @@ def lib():
             # copies with a planted mistake and run the pins against them)
             L = ctypes.CDLL(os.environ.get("FSP_ORACLE_LIB") or build())
             sig = {
-                "orc_metrics": (ctypes.c_int, [_I, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]),
-                "orc_metrics_jvp": (ctypes.c_int, [_I, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D]),
+                "orc_metrics": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]),
+                "orc_metrics_jvp": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D]),
                 "orc_lambda": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]),
                 "orc_rhs": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
                 "orc_rhs_jvp": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D]),
@@ -82,19 +83,24 @@ def lib():
                 "orc_ppm": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double]),
                 "orc_smoothness": (None, [_D, _D]),
                 "orc_eig": (None, [ctypes.c_double, _D, ctypes.c_double, ctypes.c_double, _D, _D]),
-                "orc_scheme_table": (None, [ctypes.c_int, _D]),
+                "orc_scheme_table": (None, [ctypes.c_int, ctypes.c_double, _D]),
                 "orc_advect1d": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]),
                 "orc_advect1d_dt": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]),
                 "orc_smoothness4": (None, [_D, _D]),
+                "orc_advect1d_opts": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_int, _D]),
+                "orc_weno_z": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, _D]),
+                "orc_split_flux": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                  _D, _D, _D]),
                 "orc_riemann_exact": (ctypes.c_int, [ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_int, _D, _D]),
                 "orc_long_double_digits": (ctypes.c_int, []),
                 "orc_rhs_vjp": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]),
                 "orc_rk3_vjp": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double, _D, _D]),
-                "orc_metrics_vjp": (ctypes.c_int, [_I, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D]),
+                "orc_metrics_vjp": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D]),
                 "orc_count_vjp_flops": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D,
                                                        ctypes.POINTER(ctypes.c_longlong)]),
-                "orc_mb_metrics": (ctypes.c_int, [_I, ctypes.c_int, _I, _I, _I, _D, _D, _D, _D, _D]),
+                "orc_mb_metrics": (ctypes.c_int, [_I, _D, ctypes.c_int, _I, _I, _I, _D, _D, _D, _D, _D]),
                 "orc_mb_rhs": (ctypes.c_int, [_I, _D, ctypes.c_int, _I, _I, _I, _D, _D, _D]),
                 "orc_mb_rk3": (ctypes.c_int, [_I, _D, ctypes.c_int, _I, _I, _I, _D, _D, ctypes.c_double,
                                               ctypes.c_int]),
@@ -116,11 +122,17 @@ def _f64(a):
 
 
 def _params(cfg):
+    """ip = (scheme, interp, ppm, linear_weights, bc[4], weights, mid_split); dp = (gamma,
+    lf_alpha, eps, bc_state[4][4], scheme_alpha)."""
+    alpha = float(cfg.get("scheme_alpha", 1.0))
+    if alpha != 1.0 and cfg.get("scheme", 2) in (1, 3):
+        raise ValueError("oracle: the two-midpoint schemes have no free parameter")
     ip = np.array([cfg.get("scheme", 2), cfg.get("interp", 0), cfg.get("ppm", 1),
-                   cfg.get("linear_weights", 0)] + list(cfg.get("bc", (0, 0, 0, 0))), dtype=np.int32)
+                   cfg.get("linear_weights", 0)] + list(cfg.get("bc", (0, 0, 0, 0)))
+                  + [cfg.get("weights", 0), cfg.get("mid_split", 0)], dtype=np.int32)
     st = np.zeros((4, 4)) if cfg.get("bc_state") is None else np.asarray(cfg["bc_state"], dtype=np.float64)
     dp = np.concatenate([[cfg.get("gamma", 1.4), cfg.get("lf_alpha", 1.1), cfg.get("eps", 1e-40)],
-                         st.reshape(16)]).astype(np.float64)
+                         st.reshape(16), [alpha]]).astype(np.float64)
     per = np.asarray(cfg.get("period", ((0.0, 0.0), (0.0, 0.0))), dtype=np.float64).reshape(4)
     return ip, dp, per
 
@@ -133,19 +145,19 @@ def _ck(rc, name):
 def metrics(cfg, x, y):
     x, y = _f64(x), _f64(y)
     nj, ni = x.shape
-    ip, _, per = _params(cfg)
+    ip, dp, per = _params(cfg)
     M = np.empty((5, nj + 2 * G, ni + 2 * G))
-    _ck(lib().orc_metrics(ip.ctypes.data_as(_I), ni, nj, _dp(per), _dp(x), _dp(y), _dp(M)), "metrics")
+    _ck(lib().orc_metrics(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(per), _dp(x), _dp(y), _dp(M)), "metrics")
     return M
 
 
 def metrics_jvp(cfg, x, y, dx, dy):
     x, y, dx, dy = _f64(x), _f64(y), _f64(dx), _f64(dy)
     nj, ni = x.shape
-    ip, _, per = _params(cfg)
+    ip, dp, per = _params(cfg)
     M = np.empty((5, nj + 2 * G, ni + 2 * G))
     dM = np.empty_like(M)
-    _ck(lib().orc_metrics_jvp(ip.ctypes.data_as(_I), ni, nj, _dp(per), _dp(x), _dp(y), _dp(dx), _dp(dy),
+    _ck(lib().orc_metrics_jvp(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(per), _dp(x), _dp(y), _dp(dx), _dp(dy),
                               _dp(M), _dp(dM)), "metrics_jvp")
     return M, dM
 
@@ -230,9 +242,9 @@ def metrics_vjp(cfg, x, y, Mbar):
     """(x_bar, y_bar) = (d metrics / d(x, y))^T Mbar."""
     x, y, Mbar = _f64(x), _f64(y), _f64(Mbar)
     nj, ni = x.shape
-    ip, _, per = _params(cfg)
+    ip, dp, per = _params(cfg)
     xb, yb = np.zeros_like(x), np.zeros_like(y)
-    _ck(lib().orc_metrics_vjp(ip.ctypes.data_as(_I), ni, nj, _dp(per), _dp(x), _dp(y), _dp(Mbar), _dp(xb),
+    _ck(lib().orc_metrics_vjp(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(per), _dp(x), _dp(y), _dp(Mbar), _dp(xb),
                               _dp(yb)), "metrics_vjp")
     return xb, yb
 
@@ -308,11 +320,12 @@ def eig(gamma, q, nx, ny):
     return L, R
 
 
-def scheme_table(scheme):
+def scheme_table(scheme, alpha=1.0):
     """r, h+ midpoint coefficients (m = 0, -1), h+ node coefficients of f_{j+k} (k = -3..3),
-    central-operator node coefficients a_k (k = 1..4) and midpoint coefficients (1/2, 3/2)."""
+    central-operator node coefficients a_k (k = 1..4) and midpoint coefficients (1/2, 3/2);
+    alpha: the free parameter of the one-midpoint forms."""
     out = np.empty(16)
-    lib().orc_scheme_table(int(scheme), _dp(out))
+    lib().orc_scheme_table(int(scheme), float(alpha), _dp(out))
     return {"r": int(out[0]), "hmid": out[1:3], "hnode": out[3:10], "cnode": out[10:14], "cmid": out[14:16]}
 
 
@@ -328,6 +341,28 @@ def advect1d_dt(scheme, N, dt_exp, tfinal=2.0):
     out = np.empty(3)
     _ck(lib().orc_advect1d_dt(int(scheme), int(N), float(tfinal), float(dt_exp), _dp(out)), "advect1d_dt")
     return out[0], out[1], int(out[2])
+
+
+def advect1d_opts(scheme, N, tfinal=2.0, dt_exp=1.25, weights=0):
+    """Scalar advection (Table 3 setup) with the weight option (1: WENO-Z)."""
+    out = np.empty(3)
+    _ck(lib().orc_advect1d_opts(int(scheme), int(N), float(tfinal), float(dt_exp), int(weights), _dp(out)),
+        "advect1d_opts")
+    return out[0], out[1], int(out[2])
+
+
+def weno_z(r, eps, u7):
+    """WENO-Z interpolation to x_{j+1/2} of u7[m + 3] = u_{j+m}."""
+    return float(lib().orc_weno_z(int(r), float(eps), _dp(_f64(u7))))
+
+
+def split_flux(mode, q, mx, my, gamma=1.4):
+    """(F+, F-, E^) of the midpoint splitting `mode` (1 Steger-Warming, 2 Van Leer)."""
+    q = _f64(np.asarray(q).reshape(4))
+    fp, fm, e = np.empty(4), np.empty(4), np.empty(4)
+    _ck(lib().orc_split_flux(int(mode), _dp(q), float(mx), float(my), float(gamma), _dp(fp), _dp(fm), _dp(e)),
+        "split_flux")
+    return fp, fm, e
 
 
 def advect1d(scheme, N, tfinal=2.0):
@@ -374,12 +409,12 @@ def _mb_tables(blocks):
 
 def mb_metrics(cfg, blocks):
     nb, dims, bcs, lk, off, per = _mb_tables(blocks)
-    ip, _, _ = _params(cfg)
+    ip, dp, _ = _params(cfg)
     x = np.concatenate([_f64(b["x"]).reshape(-1) for b in blocks])
     y = np.concatenate([_f64(b["y"]).reshape(-1) for b in blocks])
     sizes = [5 * (b["x"].shape[0] + 2 * G) * (b["x"].shape[1] + 2 * G) for b in blocks]
     M = np.empty(sum(sizes))
-    _ck(lib().orc_mb_metrics(ip.ctypes.data_as(_I), nb, dims.ctypes.data_as(_I), bcs.ctypes.data_as(_I),
+    _ck(lib().orc_mb_metrics(ip.ctypes.data_as(_I), _dp(dp), nb, dims.ctypes.data_as(_I), bcs.ctypes.data_as(_I),
                              lk.ctypes.data_as(_I), _dp(off), _dp(per), _dp(x), _dp(y), _dp(M)), "mb_metrics")
     out, o = [], 0
     for b, n in zip(blocks, sizes):

@@ -420,29 +420,34 @@ __device__ __forceinline__ NodeChar<Real> node_char(const Real q[4], Real gamma,
   return w;
 }
 
-// One side of an interface: the eigen-system of the centre node along the unit direction
-// (nx, ny), and the reconstruction back to the state (scale SC).
+// The direction-independent part of the projection of a state difference d at a node:
+// A = L_1 d (the entropy row does not depend on the direction) and S = (d_0 - A) / 2.
+template <typename Real>
+__device__ __forceinline__ void char_common(const NodeChar<Real>& w, const Real d[4], Real& A, Real& S) {
+  A = fma(w.a10, d[0], fma(w.b1u, d[1], fma(w.b1v, d[2], -w.b1 * d[3])));
+  S = Real(0.5) * (d[0] - A);
+}
+
+// The direction-dependent part of one side of an interface: the eigen-system of the centre
+// node along the unit direction (nx, ny), and the reconstruction back to the state (scale SC).
 template <typename Real, int SC>
-struct CharSide {
-  Real Ut, Unc, nxc, nyc, nx, ny, a10, b1u, b1v, b1;
+struct CharDir {
+  Real Ut, Unc, nxc, nyc, nx, ny;
   Real us, vs, Hs, h2s, csnx, csny, csUn, Uts;
   __device__ __forceinline__ void build(const NodeChar<Real>& w, Real nx_, Real ny_) {
     nx = nx_; ny = ny_;
     const Real Un = w.u * nx + w.v * ny;
     Ut = w.v * nx - w.u * ny;
     Unc = Un * w.hc; nxc = nx * w.hc; nyc = ny * w.hc;
-    a10 = w.a10; b1u = w.b1u; b1v = w.b1v; b1 = w.b1;
     us = w.us; vs = w.vs; Hs = w.Hs; h2s = w.h2s;
     csnx = w.cs * nx; csny = w.cs * ny; csUn = w.cs * Un; Uts = Ut * Real(1.0 / SC);
   }
-  // characteristic values (w_0 .. w_3) of the state difference d
-  __device__ __forceinline__ void project(Real d0, Real d1, Real d2, Real d3, Real w[4]) const {
-    const Real A = fma(a10, d0, fma(b1u, d1, fma(b1v, d2, -b1 * d3)));
-    const Real S = Real(0.5) * (d0 - A);
-    const Real B = fma(Unc, d0, -fma(nxc, d1, nyc * d2));
+  // characteristic values (w_0 .. w_3) of the state difference d, from its common part
+  __device__ __forceinline__ void project(const Real d[4], Real A, Real S, Real w[4]) const {
+    const Real B = fma(Unc, d[0], -fma(nxc, d[1], nyc * d[2]));
     w[0] = S + B;
     w[1] = A;
-    w[2] = fma(-Ut, d0, fma(-ny, d1, nx * d2));
+    w[2] = fma(-Ut, d[0], fma(-ny, d[1], nx * d[2]));
     w[3] = S - B;
   }
   // Q = qc + R W / S, with R's columns (1, u - c nx, v - c ny, H - c Un), (1, u, v, |u|^2/2),
@@ -455,6 +460,24 @@ struct CharSide {
     Q[2] = fma(vs, a, fma(csny, dd, fma(nx * is, W[2], qc[2])));
     Q[3] = fma(Hs, s, fma(csUn, dd, fma(h2s, W[1], fma(Uts, W[2], qc[3]))));
   }
+};
+
+// One side of an interface (both parts together).
+template <typename Real, int SC>
+struct CharSide {
+  NodeChar<Real> w;
+  CharDir<Real, SC> dir;
+  __device__ __forceinline__ void build(const NodeChar<Real>& w_, Real nx_, Real ny_) {
+    w = w_;
+    dir.build(w_, nx_, ny_);
+  }
+  __device__ __forceinline__ void project(Real d0, Real d1, Real d2, Real d3, Real out[4]) const {
+    const Real d[4] = {d0, d1, d2, d3};
+    Real A, S;
+    char_common(w, d, A, S);
+    dir.project(d, A, S, out);
+  }
+  __device__ __forceinline__ void recon(const Real W[4], const Real qc[4], Real Q[4]) const { dir.recon(W, qc, Q); }
 };
 
 // --------------------------------------------------------------------------------------

@@ -68,8 +68,9 @@ __device__ __forceinline__ void ld2(const T* b, int o, T& x, T& y) {
 }
 
 // Staged node data of n nodes (tile positions or ring slots), 16-byte vectors:
-//   fp, fm  split node fluxes f+- = (E^ +- A^ Q)/2 (Acc, 4 values); in mixed precision fp
-//           holds the metric-weighted flux E^ and there is no fm
+//   fp, fm  twice the split node fluxes, 2 f+- = E^ +- A^ Q (Acc, 4 values; the 1/2 is taken
+//           in h_combine); in mixed precision fp holds the metric-weighted flux E^ and there
+//           is no fm
 //   ma      direction metrics in Acc (2 values)
 //   q       state (Real, 4 values)
 //   p0..p2  the node's characteristic data (NodeChar: 12 values)
@@ -201,14 +202,26 @@ __host__ __device__ constexpr int march_seg_len(int n) {
   const int per = (n + nseg - 1) / nseg;
   return (per + 31) / 32 * 32;
 }
+// Whether the marching xi pass evaluates the interface sides per centre node (centre_sides,
+// which shares each node's stencil differences between its two sides) or per interface
+// (interface_mid, both sides of one interface in one lane).  Same results either way.  The
+// FP64 pass is bound by its FP64 instructions, which the centre layout cuts (9.12 against
+// 9.48 ms on the 64-block cylinder); the float passes are bound by issue at 80-102 registers,
+// where the centre layout's extra live state costs more than it saves (FP32 0.212 against
+// 0.207 ms).
+template <typename Real>
+constexpr bool march_centres() { return sizeof(Real) == 8; }
+
 template <int S, typename Real, typename Acc>
 struct MarchShape {
   static constexpr int NMP = Scheme<S>::nmp;
   // per warp: the node ring, h per ring slot (4 Acc), f+- at the midpoints (two-midpoint
-  // schemes, 8 Acc per slot), and the raw node prefetch (state, two metrics) of 32 lanes
+  // schemes, 8 Acc per slot), Q+ of the interface to the right of each centre node (4 Real
+  // per slot), and the raw node prefetch (state, two metrics) of 32 lanes
   static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(RING); }
   static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * RING; }
-  static constexpr size_t o_raw() { return o_f() + (NMP == 2 ? MidStore<Real, Acc>::bytes(RING) : 0); }
+  static constexpr size_t o_qp() { return o_f() + (NMP == 2 ? MidStore<Real, Acc>::bytes(RING) : 0); }
+  static constexpr size_t o_raw() { return o_qp() + (march_centres<Real>() ? sizeof(Real) * 4 * RING : 0); }
   static constexpr size_t warp_bytes() { return o_raw() + 32 * (4 * sizeof(Real) + 16); }
   static constexpr size_t smem_bytes() { return MARCH_WARPS * warp_bytes(); }
 };
@@ -254,90 +267,36 @@ __device__ __forceinline__ void node_split(const Real q[4], double mx, double my
 #pragma unroll
     for (int v = 0; v < 4; ++v) fp[v] = amx * widen<Acc>(ex[v]) + amy * widen<Acc>(ey[v]);
   } else {
+    // twice the split fluxes, E^ +- A^ Q (the 1/2 is taken in h_combine)
     const Acc U = amx * Acc(w.u) + amy * Acc(w.v);
     const Acc E[4] = {Acc(q[0]) * U, Acc(q[1]) * U + amx * Acc(p), Acc(q[2]) * U + amy * Acc(p),
                       Acc(q[3] + p) * U};
+    const Acc A = hA + hA;
+    if constexpr (std::is_same<Acc, float>::value) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const Acc e = Acc(0.5) * E[v], aq = hA * Acc(q[v]);
-      fp[v] = e + aq;
-      fm[v] = e - aq;
+      for (int v = 0; v < 4; v += 2) {
+        const float2 e = make_float2(E[v], E[v + 1]), qq = make_float2(q[v], q[v + 1]);
+        const float2 a = fma2(bc2(A), qq, e), b = fma2(bc2(-A), qq, e);
+        fp[v] = a.x; fp[v + 1] = a.y;
+        fm[v] = b.x; fm[v + 1] = b.y;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        fp[v] = fma(A, Acc(q[v]), E[v]);
+        fm[v] = fma(-A, Acc(q[v]), E[v]);
+      }
     }
   }
 }
 
-// The interface p + 1/2 between staged nodes at(0) (node p) and at(1) (node p + 1); at(m)
-// gives the staged index of node p + m, m = -2..3.  Characteristic direction from the
-// averaged metrics (Section 3.4), eigenvectors at Q_p ("+" side, stencil p-2..p+2) and at
-// Q_{p+1} ("-" side, the mirror), WENO interpolation of the characteristic differences, the
-// states Q+- at the midpoint, and the midpoint fluxes with the midpoint metrics interpolated
-// as in the metric evaluation (Section 2.4).
-// DEF: the configuration options take their defaults as compile-time constants (mapped
-// nonlinear weights, order-matched midpoint interpolation), so the marching kernels carry no
-// branches on them; the tile kernels read them at run time.
-template <int S, typename Real, typename Acc, bool DEF = false, typename At>
-__device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
-                                              int ppm_, int linw_, int interp_, Acc A, Mid<Real, Acc>& mo) {
+// The midpoint part of interface p + 1/2 from its two reconstructed states Qs[0] = Q+ and
+// Qs[1] = Q-: the midpoint metrics interpolated as in the metric evaluation (Section 2.4) and
+// the midpoint fluxes (Section 2.3); at(m) gives the staged index of node p + m.
+template <int S, typename Real, typename Acc, typename At>
+__device__ __forceinline__ void mid_fluxes(const Staged<Real, Acc>& st, const At& at, const Real Qs[2][4], Real gamma,
+                                           int interp, Acc A, Mid<Real, Acc>& mo) {
   using Sc = Scheme<S>;
-  constexpr int SC = weno_scale<Sc::r>();
-  const int ppm = DEF ? 1 : ppm_, linw = DEF ? 0 : linw_, interp = DEF ? 0 : interp_;
-  const int o0 = at(0), o1 = at(1);
-  // unit direction of the averaged metrics (the mean's factor 1/2 cancels in the normalisation)
-  Real m0x, m0y, m1x, m1y;
-  st.met_real(o0, m0x, m0y);
-  st.met_real(o1, m1x, m1y);
-  const Real mbx = m0x + m1x, mby = m0y + m1y;
-  const Real rn = rsq(mbx * mbx + mby * mby);
-  const Real nx = mbx * rn, ny = mby * rn;
-
-  Real Qs[2][4];
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const int oc = side == 0 ? o0 : o1;
-    NodeChar<Real> w;
-    st.chr(oc, w);
-    CharSide<Real, SC> E;
-    E.build(w, nx, ny);
-    Real qc[4];
-    ld4(st.q, st.n, oc, qc);
-    // characteristic differences to the centre at the stencil offsets -H..-1, +1..+H (H = 2,
-    // or 3 for r = 4); the "-" side reads the mirrored nodes
-    constexpr int H = Sc::r == 4 ? 3 : 2, NA = 2 * H;
-    Real wd[NA][4];
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      const int m = a < H ? a - H : a - H + 1;
-      if (Sc::r == 2 && m == 2) { wd[a][0] = wd[a][1] = wd[a][2] = wd[a][3] = Real(0); continue; }
-      Real t[4];
-      ld4(st.q, st.n, at(side == 0 ? m : 1 - m), t);
-      E.project(t[0] - qc[0], t[1] - qc[1], t[2] - qc[2], t[3] - qc[3], wd[a]);
-    }
-    Real Wm[4];
-    if constexpr (std::is_same<Real, float>::value) {
-      // components (0, 1) and (2, 3) in the two lanes of packed float arithmetic
-#pragma unroll
-      for (int kp = 0; kp < 2; ++kp) {
-        float2 u[NA + 1];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = make_float2(wd[a][2 * kp], wd[a][2 * kp + 1]);
-        u[H] = make_float2(0.f, 0.f);
-        const float2 W2 = weno_delta_x2<Sc::r>(u, eps, ppm, linw);
-        Wm[2 * kp] = W2.x;
-        Wm[2 * kp + 1] = W2.y;
-      }
-    } else {
-#pragma unroll
-      for (int kc = 0; kc < 4; ++kc) {
-        Real u[NA + 1];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = wd[a][kc];
-        u[H] = Real(0);
-        Wm[kc] = weno_delta<Sc::r, Real>(u, eps, ppm, linw);
-      }
-    }
-    E.recon(Wm, qc, Qs[side]);
-  }
-
   Acc mmx, mmy;
   if constexpr (Sc::r == 4) {
     Acc vx[8], vy[8];
@@ -399,13 +358,166 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
   }
 }
 
+// The WENO interpolation of one side's four characteristic components from their
+// differences wd[a][k] at the stencil offsets -H..-1, +1..+H (the result scaled by
+// weno_scale<R>); FP32 runs components (0, 1) and (2, 3) in the two lanes of packed float
+// arithmetic.
+template <int R, typename Real>
+__device__ __forceinline__ void side_weno(const Real (*wd)[4], Real eps, int ppm, int linw, Real Wm[4]) {
+  constexpr int H = R == 4 ? 3 : 2, NA = 2 * H;
+  if constexpr (std::is_same<Real, float>::value) {
+#pragma unroll
+    for (int kp = 0; kp < 2; ++kp) {
+      float2 u[NA + 1];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = make_float2(wd[a][2 * kp], wd[a][2 * kp + 1]);
+      u[H] = make_float2(0.f, 0.f);
+      const float2 W2 = weno_delta_x2<R>(u, eps, ppm, linw);
+      Wm[2 * kp] = W2.x;
+      Wm[2 * kp + 1] = W2.y;
+    }
+  } else {
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      Real u[NA + 1];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = wd[a][kc];
+      u[H] = Real(0);
+      Wm[kc] = weno_delta<R, Real>(u, eps, ppm, linw);
+    }
+  }
+}
+
+// Unit characteristic direction of interface p + 1/2 from the staged metrics of nodes p and
+// p + 1 (the average's factor 1/2 cancels in the normalisation).
+template <typename Real, typename Acc>
+__device__ __forceinline__ void char_direction(const Staged<Real, Acc>& st, int o0, int o1, Real& nx, Real& ny) {
+  Real m0x, m0y, m1x, m1y;
+  st.met_real(o0, m0x, m0y);
+  st.met_real(o1, m1x, m1y);
+  const Real mbx = m0x + m1x, mby = m0y + m1y;
+  const Real rn = rsq(mbx * mbx + mby * mby);
+  nx = mbx * rn;
+  ny = mby * rn;
+}
+
+// The two interface sides centred at node c (at(m) = the staged index of node c + m): the
+// "+" side of interface c + 1/2 (eigenvectors of Q_c along n+ = n_{c+1/2}, stencil c-H..c+H)
+// and the "-" side of interface c - 1/2 (eigenvectors of Q_c along n- = n_{c-1/2}, the
+// mirrored stencil).  Both read the same state differences, whose direction-free projection
+// part is taken once; each side's arithmetic is that of interface_mid, so the results agree
+// bit for bit.  Qp = Q+_{c+1/2}, Qm = Q-_{c-1/2}.
+template <int S, typename Real, typename Acc, typename At>
+__device__ __forceinline__ void centre_sides(const Staged<Real, Acc>& st, const At& at, Real npx, Real npy,
+                                             Real nmx, Real nmy, Real eps, Real Qp[4], Real Qm[4]) {
+  using Sc = Scheme<S>;
+  constexpr int SC = weno_scale<Sc::r>();
+  constexpr int H = Sc::r == 4 ? 3 : 2, NA = 2 * H;
+  const int oc = at(0);
+  NodeChar<Real> w;
+  st.chr(oc, w);
+  Real qc[4];
+  ld4(st.q, st.n, oc, qc);
+  CharDir<Real, SC> Ep, Em;
+  Ep.build(w, npx, npy);
+  Em.build(w, nmx, nmy);
+  // neighbour k = -H..-1, 1..H at index a (k = a - H, or a - H + 1): difference and common part
+  Real d[NA][4], cA[NA], cS[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int k = a < H ? a - H : a - H + 1;
+    Real t[4];
+    ld4(st.q, st.n, at(k), t);
+    if constexpr (std::is_same<Real, float>::value) {
+#pragma unroll
+      for (int v = 0; v < 4; v += 2) {
+        const float2 dd = fma2(make_float2(qc[v], qc[v + 1]), bc2(-1.0f), make_float2(t[v], t[v + 1]));
+        d[a][v] = dd.x;
+        d[a][v + 1] = dd.y;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) d[a][v] = t[v] - qc[v];
+    }
+    char_common(w, d[a], cA[a], cS[a]);
+  }
+  // "+" side: offset m reads neighbour m; "-" side: offset m reads neighbour -m (index NA-1-a)
+  Real wp[NA][4], wm[NA][4];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int m = a < H ? a - H : a - H + 1;
+    if (Sc::r == 2 && m == 2) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) wp[a][v] = wm[a][v] = Real(0);
+      continue;
+    }
+    Ep.project(d[a], cA[a], cS[a], wp[a]);
+    Em.project(d[NA - 1 - a], cA[NA - 1 - a], cS[NA - 1 - a], wm[a]);
+  }
+  Real Wp[4], Wm[4];
+  side_weno<Sc::r, Real>(wp, eps, 1, 0, Wp);
+  side_weno<Sc::r, Real>(wm, eps, 1, 0, Wm);
+  Ep.recon(Wp, qc, Qp);
+  Em.recon(Wm, qc, Qm);
+}
+
+// The interface p + 1/2 between staged nodes at(0) (node p) and at(1) (node p + 1); at(m)
+// gives the staged index of node p + m, m = -2..3.  Characteristic direction from the
+// averaged metrics (Section 3.4), eigenvectors at Q_p ("+" side, stencil p-2..p+2) and at
+// Q_{p+1} ("-" side, the mirror), WENO interpolation of the characteristic differences, the
+// states Q+- at the midpoint, and the midpoint fluxes with the midpoint metrics interpolated
+// as in the metric evaluation (Section 2.4).
+// DEF: the configuration options take their defaults as compile-time constants (mapped
+// nonlinear weights, order-matched midpoint interpolation), so the marching kernels carry no
+// branches on them; the tile kernels read them at run time.
+template <int S, typename Real, typename Acc, bool DEF = false, typename At>
+__device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
+                                              int ppm_, int linw_, int interp_, Acc A, Mid<Real, Acc>& mo) {
+  using Sc = Scheme<S>;
+  constexpr int SC = weno_scale<Sc::r>();
+  const int ppm = DEF ? 1 : ppm_, linw = DEF ? 0 : linw_, interp = DEF ? 0 : interp_;
+  const int o0 = at(0), o1 = at(1);
+  Real nx, ny;
+  char_direction(st, o0, o1, nx, ny);
+
+  Real Qs[2][4];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int oc = side == 0 ? o0 : o1;
+    NodeChar<Real> w;
+    st.chr(oc, w);
+    CharSide<Real, SC> E;
+    E.build(w, nx, ny);
+    Real qc[4];
+    ld4(st.q, st.n, oc, qc);
+    // characteristic differences to the centre at the stencil offsets -H..-1, +1..+H (H = 2,
+    // or 3 for r = 4); the "-" side reads the mirrored nodes
+    constexpr int H = Sc::r == 4 ? 3 : 2, NA = 2 * H;
+    Real wd[NA][4];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      const int m = a < H ? a - H : a - H + 1;
+      if (Sc::r == 2 && m == 2) { wd[a][0] = wd[a][1] = wd[a][2] = wd[a][3] = Real(0); continue; }
+      Real t[4];
+      ld4(st.q, st.n, at(side == 0 ? m : 1 - m), t);
+      E.project(t[0] - qc[0], t[1] - qc[1], t[2] - qc[2], t[3] - qc[3], wd[a]);
+    }
+    Real Wm[4];
+    side_weno<Sc::r, Real>(wd, eps, ppm, linw, Wm);
+    E.recon(Wm, qc, Qs[side]);
+  }
+
+  mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, interp, A, mo);
+}
+
 // h+ coefficient n_k of the node flux f+_{p+k} (0 outside the scheme's stencil)
 template <int S>
 __host__ __device__ constexpr double hnode(int k) { return Scheme<S>::hn(k); }
 
 // h = h+ + h- at p + 1/2 (Eqs. 3.4, 3.8, 3.16, 3.20; h- the mirror of h+), the midpoint
 // terms m0 (f+_{p+1/2} + f-_{p+1/2}) + m1 (f+_{p-1/2} + f-_{p+3/2}) plus the node terms
-// n_k (f+_{p+k} + f-_{p+1-k}).  `c` is the interface p + 1/2; for two-midpoint schemes
+// n_k (f+_{p+k} + f-_{p+1-k}), from the staged and midpoint values of 2 f+- (coefficients
+// halved).  `c` is the interface p + 1/2; for two-midpoint schemes
 // `lo` holds the plus side at p - 1/2 and `hi` the minus side at p + 3/2.
 // Mixed precision: with f+- = (E^ +- A^ Q)/2 the terms regroup into a central part in the
 // metric-weighted fluxes, (1/2) sum_d (n_{-d} + n_{1+d}) (E^_{p-d} + E^_{p+1+d}) plus the
@@ -450,6 +562,34 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
     const Real hA = Real(0.5) * from_f64_int(A);
 #pragma unroll
     for (int v = 0; v < 4; ++v) h[v] = he[v] + widen<Acc>(hA * hq[v]);
+  } else if constexpr (std::is_same<Acc, float>::value) {
+    // the same in the two lanes of packed float arithmetic, components (0, 1) and (2, 3)
+#pragma unroll
+    for (int v = 0; v < 4; v += 2) {
+      const float2 c0 = make_float2(c.f[0][v], c.f[0][v + 1]), c1 = make_float2(c.f[1][v], c.f[1][v + 1]);
+      float2 hh = mul2(bc2(float(0.5 * Sc::m0)), add2(c0, c1));
+      if constexpr (Sc::nmp == 2) {
+        const float2 l0 = make_float2(lo.f[0][v], lo.f[0][v + 1]), h1 = make_float2(hi.f[1][v], hi.f[1][v + 1]);
+        hh = fma2(bc2(float(0.5 * Sc::m1)), add2(l0, h1), hh);
+      }
+      h[v] = hh.x;
+      h[v + 1] = hh.y;
+    }
+#pragma unroll
+    for (int kk = -3; kk <= 3; ++kk) {
+      if (Sc::hn(kk) == 0.0) continue;
+      Acc a[4], b[4];
+      ld4(st.fp, st.n, at(kk), a);
+      ld4(st.fm, st.n, at(1 - kk), b);
+#pragma unroll
+      for (int v = 0; v < 4; v += 2) {
+        const float2 hh = fma2(bc2(float(0.5 * Sc::hn(kk))),
+                               add2(make_float2(a[v], a[v + 1]), make_float2(b[v], b[v + 1])),
+                               make_float2(h[v], h[v + 1]));
+        h[v] = hh.x;
+        h[v + 1] = hh.y;
+      }
+    }
   } else {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -463,7 +603,7 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
       ld4(st.fp, st.n, at(kk), a);
       ld4(st.fm, st.n, at(1 - kk), b);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) h[v] += Acc(Sc::hn(kk)) * (a[v] + b[v]);
+      for (int v = 0; v < 4; ++v) h[v] += Acc(0.5 * Sc::hn(kk)) * (a[v] + b[v]);
     }
   }
 }
@@ -668,13 +808,17 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
 // Every step t (lane L):
 //   nodes       m = s0 + K + 32 t + L  into ring slot m mod 64 (state and metrics staged by
 //               cp.async during the previous step when the node is interior)
-//   interfaces  q = s0 - NMP + 32 t + L: midpoint fluxes (and for one-midpoint schemes h)
+//   centres     c = s0 - NMP + 32 t + L: the "+" side of interface c + 1/2 and the "-" side of
+//               interface c - 1/2, which share the node's stencil differences (centre_sides);
+//               Q+ goes to the ring, Q- stays in the lane
+//   interfaces  q = c - 1: Q+ from the centre q (lane L - 1, or lane 31 a step earlier) and
+//               this lane's Q-; midpoint fluxes (and for one-midpoint schemes h)
 //   h           (two-midpoint schemes) at q - 1, from the midpoint ring
 //   outputs     node s = the interface just completed, H_s - H_{s-1} from the h ring
 // with K = 3 (one midpoint) or 2 (two midpoints), so that every stencil node of a step's
-// interfaces is in the ring; a start-up pass stages the nodes s0 - NMP - H .. s0 + K - 1
-// (H = 2, or 3 for WENOIU7).  The ring holds the 39 nodes a step reads at most; the warp
-// synchronises between the phases only.
+// centres and interfaces is in the ring; a start-up pass stages the nodes s0 - NMP - H ..
+// s0 + K - 1 (H = 2, or 3 for WENOIU7).  The ring holds the at most 40 nodes a step reads;
+// the warp synchronises between the phases only.
 // --------------------------------------------------------------------------------------
 template <int S, int MODE, typename Real, typename Acc>
 __device__ __forceinline__ void march_row(const Params& P, const Real* __restrict__ Q, const Real* const* qtab,
@@ -685,12 +829,14 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
   constexpr int NMP = Scheme<S>::nmp;
   constexpr int K = NMP == 1 ? 3 : 2;
   constexpr int H = Scheme<S>::r == 4 ? 3 : 2;     // stencil half-width of the interpolation
+  constexpr bool CENTRE = march_centres<Real>();
   const int L = threadIdx.x & 31;
   Staged<Real, Acc> st;
   st.carve(wsm, RING);
   Acc* rH = reinterpret_cast<Acc*>(wsm + Ms::o_h());
   MidStore<Real, Acc> rF;
   rF.carve(wsm + Ms::o_f(), RING);
+  Real* rQp = reinterpret_cast<Real*>(wsm + Ms::o_qp());              // Q+ per centre slot
   Real* rawq = reinterpret_cast<Real*>(wsm + Ms::o_raw());           // [4][32]
   double* rawm = reinterpret_cast<double*>(rawq + 4 * 32);           // [2][32]
   const int n = P.ni;
@@ -734,11 +880,11 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
     return true;
   };
 
-  // start-up: the six nodes s0 + K - 6 .. s0 + K - 1, and the first step's nodes in flight
+  // start-up: the nodes s0 - NMP - H .. s0 + K - 1, and the first step's nodes in flight
   if (L < K + NMP + H) stage_node(s0 - NMP - H + L, false);
   bool staged = prefetch(s0 + K + L);
   cp_async_commit();
-  const int steps = (s1 - s0 + 2 * NMP - 1 + 31) / 32;   // until the output s1 - 1
+  const int steps = (s1 - s0 + 2 * NMP + 31) / 32;   // until the interface s1 + NMP - 2
   for (int t = 0; t < steps; ++t) {
     const int m = s0 + K + 32 * t + L;
     cp_async_wait_all();
@@ -746,12 +892,35 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
     __syncwarp();
     staged = prefetch(m + 32);       // the next step's node, in flight during this step
     cp_async_commit();
-    // interfaces
-    const int q = s0 - NMP + 32 * t + L;
-    if (q <= s1 + NMP - 2) {   // interfaces s0 - NMP .. s1 + NMP - 2
+    // centres s0 - NMP .. s1 + NMP - 1
+    const int c = s0 - NMP + 32 * t + L;
+    Real Qm[4];
+    if constexpr (CENTRE) {
+      if (c <= s1 + NMP - 1) {
+        auto at = [&](int mm) { return (c + mm) & (RING - 1); };
+        Real npx, npy, nmx, nmy;
+        char_direction(st, at(0), at(1), npx, npy);
+        char_direction(st, at(-1), at(0), nmx, nmy);
+        Real Qp[4];
+        centre_sides<S, Real, Acc>(st, at, npx, npy, nmx, nmy, eps, Qp, Qm);
+        st4(rQp, RING, c & (RING - 1), Qp[0], Qp[1], Qp[2], Qp[3]);
+      }
+      __syncwarp();
+    }
+    // interfaces s0 - NMP .. s1 + NMP - 2
+    const int q = c - 1;
+    if (q >= s0 - NMP && q <= s1 + NMP - 2) {
       auto at = [&](int mm) { return (q + mm) & (RING - 1); };
       Mid<Real, Acc> mo;
-      interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
+      if constexpr (CENTRE) {
+        Real Qs[2][4];
+        ld4(rQp, RING, q & (RING - 1), Qs[0]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Qs[1][v] = Qm[v];
+        mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, 0, A, mo);
+      } else {
+        interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
+      }
       if constexpr (NMP == 1) {
         Acc h[4];
         h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h);
@@ -767,13 +936,13 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
       const int p = q - 1;
       if (p >= s0 - 1 && p <= s1 - 1) {
         auto at = [&](int mm) { return (p + mm) & (RING - 1); };
-        Mid<Real, Acc> c, lo, hi;
-        rF.get(p & (RING - 1), 0, c);
-        rF.get(p & (RING - 1), 1, c);
+        Mid<Real, Acc> cm, lo, hi;
+        rF.get(p & (RING - 1), 0, cm);
+        rF.get(p & (RING - 1), 1, cm);
         rF.get((p - 1) & (RING - 1), 0, lo);
         rF.get((p + 1) & (RING - 1), 1, hi);
         Acc h[4];
-        h_combine<S, Real, Acc>(st, at, A, c, lo, hi, h);
+        h_combine<S, Real, Acc>(st, at, A, cm, lo, hi, h);
         st4(rH, RING, p & (RING - 1), h[0], h[1], h[2], h[3]);
       }
       __syncwarp();
@@ -1011,12 +1180,12 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
 }
 
 // Resident CTAs per SM the kernels are compiled for (register budget): FP64 2, FP32 4, mixed 3
-// for the 256-thread tiles; FP64 3, FP32 6, mixed 5 for the 128-thread marching xi CTAs (six
-// rather than seven FP32 CTAs: 80 registers, with 8 bytes of spills left, measured 3 % faster).
+// for the 256-thread tiles; FP64 3, FP32 and mixed 5 for the 128-thread marching xi CTAs (102
+// registers for the float passes: five FP32 CTAs measured 3 % faster than six at 80).
 template <typename Real, typename Acc>
 constexpr int tile_ctas() { return sizeof(Real) == 8 ? 2 : std::is_same<Real, Acc>::value ? 4 : 3; }
 template <typename Real, typename Acc>
-constexpr int march_ctas() { return sizeof(Real) == 8 ? 3 : std::is_same<Real, Acc>::value ? 6 : 5; }
+constexpr int march_ctas() { return sizeof(Real) == 8 ? 3 : 5; }
 
 template <int S, int DIR, int MODE, typename Real, typename Acc>
 __global__ void __launch_bounds__(256, tile_ctas<Real, Acc>())

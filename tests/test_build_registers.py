@@ -20,10 +20,10 @@ SRC = os.path.join(ROOT, "paper_1810_11103_gb300", "csrc")
 BUDGETS = [
     ("batch_fp64.cu", "_ZN3fsp18march_batch_kernelILi2ELi0EddE", 0),
     ("batch_fp64.cu", "_ZN3fsp22march_eta_batch_kernelILi2ELi2EddE", 0),
-    ("batch_fp64.cu", "_ZN3fsp18sweep_batch_kernelILi2ELi0ELi0EddLi2EE", 24),
-    ("batch_fp32.cu", "_ZN3fsp18march_batch_kernelILi2ELi0EffE", 8),
+    ("batch_fp64.cu", "_ZN3fsp18sweep_batch_kernelILi2ELi0ELi0EddLi2EE", 0),
+    ("batch_fp32.cu", "_ZN3fsp18march_batch_kernelILi2ELi0EffE", 0),
     ("batch_fp32.cu", "_ZN3fsp22march_eta_batch_kernelILi2ELi2EffE", 0),
-    ("batch_mixed.cu", "_ZN3fsp18march_batch_kernelILi2ELi0EfdE", 0),
+    ("batch_mixed.cu", "_ZN3fsp18march_batch_kernelILi2ELi0EfdE", 16),
     ("batch_mixed.cu", "_ZN3fsp22march_eta_batch_kernelILi2ELi2EfdE", 0),
 ]
 

@@ -24,6 +24,7 @@ W7 = "test_oracle_weno7.py::"
 TAN = "test_oracle_tangent.py::"
 FLO = "test_oracle_flops.py::"
 VJP = "test_oracle_vjp.py::"
+OPT = "test_oracle_options.py::"
 
 # (name, text in the oracle, planted replacement, pins that catch it: tests/ node ids)
 MUTANTS = [
@@ -165,6 +166,17 @@ MUTANTS = [
      [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_rk3_tangent_matches_finite_differences"]),
     ("dual_sqrt", "a.d / (2.0 * s)", "a.d / s",
      [TAN + "test_rhs_tangent_matches_finite_differences[0]", TAN + "test_rk3_tangent_matches_finite_differences"]),
+    # options: free parameter, WENO-Z, midpoint splittings
+    ("alpha5_digit", "n[2] = 5 * a / 32 - 13.0L / 60;", "n[2] = 5 * a / 32 - 13.0L / 50;",
+     [OPT + "test_alpha_accuracy_relations[0.7]", OPT + "test_alpha_one_is_the_printed_scheme[2]"]),
+    ("alpha_csd_index", "(nk(d) - nk(d + 1) + nk(1 - d) - nk(-d)) / 2", "(nk(d) - nk(d + 1) + nk(-d) - nk(1 - d)) / 2",
+     [OPT + "test_alpha_one_is_the_printed_scheme[0]", OPT + "test_alpha_central_operator_is_exact_and_preserves_free_stream[0]"]),
+    ("wenoz_tau", "fabs(IS[0] - IS[r - 1])", "fabs(IS[0] - IS[1])",
+     [OPT + "test_weno_z_weights_approach_the_linear_ones[3-9]", OPT + "test_weno_z_design_order[2-5]"]),
+    ("sw_acoustic", "l[2] * (u + c * nx));", "l[2] * (u - c * nx));",
+     [OPT + "test_midpoint_splittings_are_consistent[1]", OPT + "test_midpoint_splittings_sod[1]"]),
+    ("vl_energy", "(gamma * gamma - cst<T>(1))", "(gamma * gamma + cst<T>(1))",
+     [OPT + "test_midpoint_splittings_are_consistent[2]", OPT + "test_midpoint_splittings_upwind_limits"]),
     # reverse mode (the tape behind the oracle's adjoints)
     ("rev_sub_sign", "rev_rec(a.v - b.v, a.i, 1.0, b.i, -1.0, 1)", "rev_rec(a.v - b.v, a.i, 1.0, b.i, 1.0, 1)",
      [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_rhs_vjp_matches_finite_differences"]),
