@@ -92,6 +92,20 @@ typedef struct {
   double lf_alpha;     /* alpha of the Lax-Friedrichs-type splitting, 1.1-1.2 (Sec. 2.3) */
   double eps;          /* epsilon of Eq. (3.13): 1e-40 with the mapping, else 1e-6     */
   double bc_state[4][4]; /* conservative state per face (Dirichlet, far field)         */
+  /* Options beyond the schemes the paper tests (Section 7 names them; the free parameter is
+   * the alpha of Eqs. 3.5 and 3.17 and of the Appendix's scheme (1)).  All zero = the paper's
+   * schemes.  The adjoint entry points and the batch's marching tile variants take only the
+   * defaults.                                                                             */
+  int weights;         /* 0 = the weights of Eqs. 3.12-3.13 (with ppm); 1 = WENO-Z weights
+                          C_k (1 + (tau/(eps + IS_k))^2), tau = |IS_0 - IS_{r-1}| (r = 2, 3)
+                          or |IS_0 + 3 IS_1 - 3 IS_2 - IS_3| (r = 4), no mapping          */
+  int mid_split;       /* splitting of the midpoint flux f_{j+1/2}: 0 = Lax-Friedrichs type
+                          (Section 2.3), 1 = Steger-Warming, 2 = Van Leer; FSP_FP64 and
+                          FSP_FP32 only                                                    */
+  double scheme_alpha; /* free parameter of the one-midpoint schemes (WENOIU3-1MP, -5-1MP,
+                          -7-1MP); 0 or 1 = the printed schemes; any other value > 0 for a
+                          one-midpoint scheme only; the metrics use the scheme's own central
+                          operator                                                        */
 } fsp_config;
 
 typedef struct {

@@ -384,8 +384,8 @@ static cudaError_t vjp_scheme(const Params& P, const double* Q, const double* lx
 }
 
 // the transposed central operator: D phi_j = sum_k w[k+4] phi_{j+k}, k = -4..4
-static void central_weights(int scheme, int interp, double w[9]) {
-  const Central c = central_of(scheme);
+static void central_weights(int scheme, int interp, double alpha, double w[9]) {
+  const Central c = central_of(scheme, alpha);
   double cl[6] = {0, 0, 0, 0, 0, 0};  // I(m) = sum_l cl[l+2] phi_{m+l}, l = -2..3
   if (interp == 1) { cl[2] = cl[3] = 0.5; }
   else if (scheme >= S51) { cl[0] = cl[5] = 3.0 / 256; cl[1] = cl[4] = -25.0 / 256; cl[2] = cl[3] = 150.0 / 256; }
@@ -546,6 +546,8 @@ VjpWs vjp_ws(const fsp_config& c, const fsp_block& b, size_t fwd_bytes) {
   return L;
 }
 
+bool adjoint_options(const fsp_config& c) { return c.weights == 0 && c.mid_split == 0 && scheme_alpha_of(c) == 1.0; }
+
 Params params_of(const fsp_config& c, const fsp_block& b, const double* metrics) {
   return make_params(c, b, metrics);
 }
@@ -558,7 +560,7 @@ Params params_of(const fsp_config& c, const fsp_block& b, const double* metrics)
 extern "C" fsp_status fsp_vjp_workspace_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes) {
   size_t fwd = 0;
   if (fsp_status s = fsp_workspace_size(cfg, blk, &fwd)) return s;
-  if (cfg->precision != FSP_FP64 || cfg->scheme == S71) return FSP_ERR_UNSUPPORTED;
+  if (cfg->precision != FSP_FP64 || cfg->scheme == S71 || !adjoint_options(*cfg)) return FSP_ERR_UNSUPPORTED;
   if (!bytes) return FSP_ERR_INVALID_ARG;
   *bytes = vjp_ws(*cfg, *blk, fwd).total;
   return FSP_OK;
@@ -664,10 +666,12 @@ static fsp_status reverse_stages(const fsp_config& c, const fsp_block& b, const 
   return FSP_OK;
 }
 
-// The adjoint covers the FP64 third- and fifth-order schemes (not WENOIU7-1MP).
+// The adjoint covers the FP64 third- and fifth-order schemes (not WENOIU7-1MP) with the
+// paper's weights, midpoint splitting and printed schemes (the ppm, linear-weight and
+// interpolation options included).
 static fsp_status check_vjp(const fsp_config* cfg, const fsp_block* blk, size_t* fwd) {
   if (fsp_status s = fsp_workspace_size(cfg, blk, fwd)) return s;
-  if (cfg->precision != FSP_FP64 || cfg->scheme == S71) return FSP_ERR_UNSUPPORTED;
+  if (cfg->precision != FSP_FP64 || cfg->scheme == S71 || !adjoint_options(*cfg)) return FSP_ERR_UNSUPPORTED;
   return FSP_OK;
 }
 
@@ -765,7 +769,7 @@ fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const do
   if (cfg->scheme == S71) return FSP_ERR_UNSUPPORTED;
   if (!dptr(x) || !dptr(y) || !dptr(metrics_bar) || !dptr(x_bar) || !dptr(y_bar)) return FSP_ERR_INVALID_ARG;
   W9 w;
-  central_weights(cfg->scheme, cfg->interp, w.w);
+  central_weights(cfg->scheme, cfg->interp, scheme_alpha_of(*cfg), w.w);
   VjpCoord C{blk->ni, blk->nj, cfg->bc[0] == FSP_BC_PERIODIC, cfg->bc[2] == FSP_BC_PERIODIC,
              blk->period[0][0], blk->period[0][1], blk->period[1][0], blk->period[1][1]};
   const long long n = (long long)(blk->ni + 2 * G) * (blk->nj + 2 * G);

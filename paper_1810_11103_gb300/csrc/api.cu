@@ -54,6 +54,7 @@ fsp_status check_cfg(const fsp_config* c, const fsp_block* b) {
   if ((c->bc[0] == FSP_BC_PERIODIC) != (c->bc[1] == FSP_BC_PERIODIC)) return FSP_ERR_INVALID_ARG;
   if ((c->bc[2] == FSP_BC_PERIODIC) != (c->bc[3] == FSP_BC_PERIODIC)) return FSP_ERR_INVALID_ARG;
   if (!(c->gamma > 1.0) || !(c->lf_alpha > 0.0) || !(c->eps > 0.0)) return FSP_ERR_INVALID_ARG;
+  if (fsp_status s = check_options(*c)) return s;
   if (b->ni < 1 || b->nj < 1 || b->ld < b->ni) return FSP_ERR_INVALID_ARG;
   if (c->bc[0] != FSP_BC_PERIODIC && b->ni < 9) return FSP_ERR_INVALID_ARG;
   if (c->bc[2] != FSP_BC_PERIODIC && b->nj < 9) return FSP_ERR_INVALID_ARG;
@@ -81,13 +82,31 @@ Params make_params(const fsp_config& c, const fsp_block& b, const double* metric
   P.ni = b.ni; P.nj = b.nj; P.ld = b.ld;
   for (int f = 0; f < 4; ++f) P.bc[f] = c.bc[f];
   P.interp = c.interp; P.ppm = c.ppm; P.linw = c.linear_weights;
+  P.wz = c.weights; P.msplit = c.mid_split;
   P.gamma = c.gamma; P.alpha = c.lf_alpha; P.eps = c.eps;
+  set_scheme_coefs(P, c.scheme, scheme_alpha_of(c));
   for (int f = 0; f < 4; ++f)
     for (int v = 0; v < 4; ++v) P.bcq[f][v] = c.bc_state[f][v];
   P.met = metrics;
   P.mld = (long long)b.ni + 2 * G;
   P.mplane = P.mld * ((long long)b.nj + 2 * G);
   return P;
+}
+
+double scheme_alpha_of(const fsp_config& c) { return c.scheme_alpha == 0.0 ? 1.0 : c.scheme_alpha; }
+
+bool default_options(const fsp_config& c) {
+  return c.ppm == 1 && c.linear_weights == 0 && c.interp == 0 && c.weights == 0 && c.mid_split == 0 &&
+         scheme_alpha_of(c) == 1.0;
+}
+
+fsp_status check_options(const fsp_config& c) {
+  if (c.weights < 0 || c.weights > 1 || c.mid_split < 0 || c.mid_split > 2) return FSP_ERR_INVALID_ARG;
+  const double a = scheme_alpha_of(c);
+  if (!(a > 0.0) || !(a < 1e6)) return FSP_ERR_INVALID_ARG;
+  if (a != 1.0 && (c.scheme == S32 || c.scheme == S52)) return FSP_ERR_INVALID_ARG;   // no free parameter
+  if (c.mid_split != 0 && c.precision == FSP_FP32_MIXED) return FSP_ERR_UNSUPPORTED;
+  return FSP_OK;
 }
 
 fsp_status rhs_status(cudaError_t e) {

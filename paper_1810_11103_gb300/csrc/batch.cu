@@ -232,6 +232,7 @@ fsp_status check_batch(const fsp_config* c, int nb, const fsp_block* blk, const 
   if (c->scheme < 0 || c->scheme > 4 || c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED ||
       c->interp < 0 || c->interp > 1 || !(c->gamma > 1.0) || !(c->lf_alpha > 0.0) || !(c->eps > 0.0))
     return FSP_ERR_INVALID_ARG;
+  if (fsp_status s = check_options(*c)) return s;
   for (int b = 0; b < nb; ++b) {
     const fsp_block& B = blk[b];
     if (B.ni < 1 || B.nj < 1 || B.ld < B.ni || B.ni > 8 * 65535 || B.nj > 2 * 65535) return FSP_ERR_INVALID_ARG;
@@ -293,9 +294,7 @@ void tiles_for(const fsp_batch* h, int dir, int v, std::vector<TileRef>& out) {
 
 // Switch one direction to shape variant v: the host and device tile tables (the device is
 // synchronised first, since queued launches may read the table) and any captured graph.
-// The marching passes are compiled for the default options only (sweep.cuh).
-bool default_options(const fsp_config& c) { return c.ppm == 1 && c.linear_weights == 0 && c.interp == 0; }
-
+// The marching passes are compiled for the default options only (sweep.cuh, default_options).
 fsp_status set_tiles(fsp_batch* h, int dir, int v) {
   if (v < 0 || v >= nvariant(dir)) return FSP_ERR_INVALID_ARG;
   if (v == MARCH && !default_options(h->cfg)) return FSP_ERR_UNSUPPORTED;
@@ -337,7 +336,9 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
     std::memset(&P, 0, sizeof(P));
     P.ni = B.ni; P.nj = B.nj; P.ld = B.ld;
     P.interp = cfg->interp; P.ppm = cfg->ppm; P.linw = cfg->linear_weights;
+    P.wz = cfg->weights; P.msplit = cfg->mid_split;
     P.gamma = cfg->gamma; P.alpha = cfg->lf_alpha; P.eps = cfg->eps;
+    set_scheme_coefs(P, cfg->scheme, scheme_alpha_of(*cfg));
     for (int f = 0; f < 4; ++f) {
       P.bc[f] = bc[4 * b + f];
       for (int v = 0; v < 4; ++v) P.bcq[f][v] = cfg->bc_state[f][v];
@@ -439,7 +440,7 @@ fsp_status fsp_batch_bind(fsp_batch* h, const double* const* x, const double* co
 fsp_status fsp_batch_metrics(fsp_batch* h, void* stream) {
   if (!h || !h->bound) return FSP_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  const Central cen = central_of(h->cfg.scheme);
+  const Central cen = central_of(h->cfg.scheme, scheme_alpha_of(h->cfg));
   for (int b = 0; b < h->nb; ++b) {
     const long long n = (long long)(h->blk[b].ni + 2 * G) * (h->blk[b].nj + 2 * G);
     const long long want = (n + 255) / 256;
@@ -617,7 +618,14 @@ std::string tune_key(const fsp_batch* h) {
   char buf[320];
   std::snprintf(buf, sizeof buf, "%s|sm%d|scheme%d|prec%d|interp%d|ppm%d|linw%d|nb%d|%016llx", name.c_str(), sms,
                 h->cfg.scheme, h->cfg.precision, h->cfg.interp, h->cfg.ppm, h->cfg.linear_weights, h->nb, x);
-  return buf;
+  std::string key = buf;
+  if (h->cfg.weights || h->cfg.mid_split || scheme_alpha_of(h->cfg) != 1.0) {
+    // the options beyond the paper's schemes (keys of the printed schemes stay as they were)
+    std::snprintf(buf, sizeof buf, "|wz%d|split%d|alpha%.17g", h->cfg.weights, h->cfg.mid_split,
+                  scheme_alpha_of(h->cfg));
+    key += buf;
+  }
+  return key;
 }
 
 bool table_lookup(const char* path, const std::string& key, int* vx, int* ve) {

@@ -68,6 +68,39 @@ template <> struct Scheme<S71> {
   }
 };
 
+// The h+ coefficients of a scheme at its free parameter alpha (the one-midpoint forms: Eq. 3.5
+// for WENOIU3-1MP, Eq. 3.17 for WENOIU5-1MP, the Appendix's scheme (1) for WENOIU7-1MP; alpha =
+// 1 is the printed scheme): m0, m1 multiply f+_{j+1/2}, f+_{j-1/2}; hn[k + 3] multiplies f+_{j+k}.
+inline void scheme_coefs(int scheme, double a, double& m0, double& m1, double hn[7]) {
+  for (int k = 0; k < 7; ++k) hn[k] = 0.0;
+  m1 = 0.0;
+  switch (scheme) {
+    case S31:
+      m0 = a; hn[2] = a / 8 - 1.0 / 6; hn[3] = -3 * a / 4 + 5.0 / 6; hn[4] = -3 * a / 8 + 1.0 / 3;
+      if (a == 1.0) for (int k = 0; k < 7; ++k) hn[k] = Scheme<S31>::hn(k - 3);
+      break;
+    case S32:
+      m0 = Scheme<S32>::m0; m1 = Scheme<S32>::m1;
+      for (int k = 0; k < 7; ++k) hn[k] = Scheme<S32>::hn(k - 3);
+      break;
+    case S51:
+      m0 = a; hn[1] = -3 * a / 128 + 1.0 / 30; hn[2] = 5 * a / 32 - 13.0 / 60; hn[3] = -45 * a / 64 + 47.0 / 60;
+      hn[4] = -15 * a / 32 + 9.0 / 20; hn[5] = 5 * a / 128 - 1.0 / 20;
+      if (a == 1.0) for (int k = 0; k < 7; ++k) hn[k] = Scheme<S51>::hn(k - 3);
+      break;
+    case S52:
+      m0 = Scheme<S52>::m0; m1 = Scheme<S52>::m1;
+      for (int k = 0; k < 7; ++k) hn[k] = Scheme<S52>::hn(k - 3);
+      break;
+    default:
+      m0 = a; hn[0] = 5 * a / 1024 - 1.0 / 140; hn[1] = -21 * a / 512 + 5.0 / 84; hn[2] = 175 * a / 1024 - 101.0 / 420;
+      hn[3] = -175 * a / 256 + 319.0 / 420; hn[4] = -525 * a / 1024 + 107.0 / 210; hn[5] = 35 * a / 512 - 19.0 / 210;
+      hn[6] = -7 * a / 1024 + 1.0 / 105;
+      if (a == 1.0) for (int k = 0; k < 7; ++k) hn[k] = Scheme<S71>::hn(k - 3);
+      break;
+  }
+}
+
 // Central operator delta^{c,(1)} of each scheme (Eq. 2.7), used for the metrics:
 //   D f_j = sum_k a_k (f_{j+k} - f_{j-k}) + b_{1/2}(f~_{j+1/2} - f~_{j-1/2})
 //           + b_{3/2}(f~_{j+3/2} - f~_{j-3/2}),  k = 1..4
@@ -81,6 +114,19 @@ __host__ __device__ inline Central central_of(int scheme) {
     default:  // the Appendix's eighth-order operator of WENOIU7-1MP
       return {8841.0 / 107520, -6069.0 / 107520, 1261.0 / 107520, 1.0, 0.0, -121.5 / 107520};
   }
+}
+// The same at the free parameter alpha of a one-midpoint scheme: the central part of the
+// scheme, (delta+ + delta-)/2 with delta+ f_j = h+_{j+1/2} - h+_{j-1/2}, whose node
+// coefficients are a_d = (n_d - n_{d+1} + n_{1-d} - n_{-d}) / 2 and whose midpoint coefficient is
+// alpha.  alpha = 1 gives the printed operators above.
+inline Central central_of(int scheme, double alpha) {
+  if (alpha == 1.0 || scheme == S32 || scheme == S52) return central_of(scheme);
+  double m0, m1, hn[7];
+  scheme_coefs(scheme, alpha, m0, m1, hn);
+  auto n = [&](int k) { return k < -3 || k > 3 ? 0.0 : hn[k + 3]; };
+  double a[4];
+  for (int d = 1; d <= 4; ++d) a[d - 1] = 0.5 * (n(d) - n(d + 1) + n(1 - d) - n(-d));
+  return {a[0], a[1], a[2], m0, 0.0, a[3]};
 }
 
 // Midpoint value at j+1/2 from nodal values v[k] = f_{j+k-2}, k = 0..5 (f_{j-2}..f_{j+3}).
@@ -108,7 +154,12 @@ struct Params {
   long long ld;             // row stride of Q-shaped arrays
   int bc[4];
   int interp, ppm, linw;
+  int wz, msplit;           // WENO-Z weights; midpoint splitting (0 LF, 1 Steger-Warming, 2 Van Leer)
   double gamma, alpha, eps;
+  // halved h+ coefficients (the h combination adds twice the split fluxes): [0] m0/2 of
+  // f+_{j+1/2}, [1] m1/2 of f+_{j-1/2}, [5 + k] n_k/2 of f+_{j+k}, k = -3..3; and as float
+  double hc[9];
+  float hcf[9];
   double bcq[4][4];
   const double* met;        // haloed metrics
   long long mld;            // ni + 2G
@@ -118,6 +169,16 @@ struct Params {
   int lnb[4], lface[4], lrev[4], lni[4], lnj[4];
   long long lld[4];
 };
+
+// The scheme's coefficients at its free parameter into the kernel parameters.
+inline void set_scheme_coefs(Params& P, int scheme, double alpha) {
+  double m0, m1, hn[7];
+  scheme_coefs(scheme, alpha, m0, m1, hn);
+  P.hc[0] = 0.5 * m0;
+  P.hc[1] = 0.5 * m1;
+  for (int k = 0; k < 7; ++k) P.hc[2 + k] = 0.5 * hn[k];
+  for (int i = 0; i < 9; ++i) P.hcf[i] = (float)P.hc[i];
+}
 
 // Node of the neighbour behind linked face f for the ghost (gi, gj) of a block of size
 // ni x nj: the blocks partition one larger grid, so the ghost at depth k beyond face f is
@@ -340,6 +401,59 @@ __device__ __forceinline__ void node_speeds(const Params& P, const Real* __restr
   sx = spectral_radius(q, from_f64_alu<Real>(met_at(P, 0, i, j)), from_f64_alu<Real>(met_at(P, 1, i, j)), g);
   se = spectral_radius(q, from_f64_alu<Real>(met_at(P, 2, i, j)), from_f64_alu<Real>(met_at(P, 3, i, j)), g);
   rate = (sx + se) * recip(from_f64_alu<Real>(met_at(P, 4, i, j)));
+}
+
+// Steger-Warming (mode 1) and Van Leer (mode 2) splittings of the metric-weighted flux along
+// k = (mx, my) for the midpoint flux (an option beyond the paper's, Section 7); returns twice
+// F+ (sign > 0) or twice F- (sign < 0), F+ + F- = E^.  With n = k/|k|, Un = u.n:
+// Steger-Warming F+- = rho/(2 gamma) [l0+- (1, u - c nx, v - c ny, H - c Un) + 2 (gamma - 1)
+// l1+- (1, u, v, |u|^2/2) + l2+- (1, u + c nx, v + c ny, H + c Un)], l = |k| (Un - c, Un, Un + c),
+// l+- = (l +- |l|)/2; Van Leer with M = Un/c: F+ = E^, F- = 0 for M >= 1 (the reverse for
+// M <= -1), else m+- = +- rho c |k| (M +- 1)^2 / 4 and F+- = m+- (1, u + nx (-Un +- 2c)/gamma,
+// v + ny (-Un +- 2c)/gamma, ((gamma - 1) Un +- 2c)^2 / (2 (gamma^2 - 1)) + (|u|^2 - Un^2)/2).
+template <typename T>
+__device__ __forceinline__ void split_mid2(int mode, int sign, const T q[4], T mx, T my, T gamma, T f[4]) {
+  const T rinv = recip(q[0]);
+  const T u = q[1] * rinv, v = q[2] * rinv, q2 = u * u + v * v;
+  const T p = (gamma - T(1)) * (q[3] - T(0.5) * q[0] * q2);
+  const T c = sqrt(gamma * p * rinv);
+  const T kn = sqrt(mx * mx + my * my), ki = recip(kn), nx = mx * ki, ny = my * ki;
+  const T Un = u * nx + v * ny;
+  const T s = sign > 0 ? T(1) : T(-1);
+  if (mode == 1) {
+    const T H = (q[3] + p) * rinv;
+    T l0 = kn * (Un - c), l1 = kn * Un, l2 = kn * (Un + c);
+    l0 = T(0.5) * (l0 + s * fabs(l0));
+    l1 = T(0.5) * (l1 + s * fabs(l1));
+    l2 = T(0.5) * (l2 + s * fabs(l2));
+    const T a = q[0] / gamma, g2 = T(2) * (gamma - T(1));
+    f[0] = a * (l0 + g2 * l1 + l2);
+    f[1] = a * (l0 * (u - c * nx) + g2 * l1 * u + l2 * (u + c * nx));
+    f[2] = a * (l0 * (v - c * ny) + g2 * l1 * v + l2 * (v + c * ny));
+    f[3] = a * (l0 * (H - c * Un) + (gamma - T(1)) * l1 * q2 + l2 * (H + c * Un));
+    return;
+  }
+  const T M = Un * recip(c);
+  if (M >= T(1) || M <= T(-1)) {
+    if ((M >= T(1)) == (sign > 0)) {
+      const T U = kn * Un;
+      f[0] = T(2) * q[0] * U;
+      f[1] = T(2) * (q[1] * U + mx * p);
+      f[2] = T(2) * (q[2] * U + my * p);
+      f[3] = T(2) * (q[3] + p) * U;
+    } else {
+      f[0] = f[1] = f[2] = f[3] = T(0);
+    }
+    return;
+  }
+  const T mp = M + s;
+  const T fm = T(0.5) * s * q[0] * c * kn * mp * mp;   // twice the mass flux
+  const T w = (s * T(2) * c - Un) / gamma;
+  const T e = (gamma - T(1)) * Un + s * T(2) * c;
+  f[0] = fm;
+  f[1] = fm * (u + nx * w);
+  f[2] = fm * (v + ny * w);
+  f[3] = fm * (e * e / (T(2) * (gamma * gamma - T(1))) + T(0.5) * (q2 - Un * Un));
 }
 
 // --------------------------------------------------------------------------------------
@@ -609,8 +723,43 @@ __device__ __forceinline__ T is_b4x(T e, T f, T eps4) {
   return fma(T(13.0 / 3) * e, e, fma(f, f, eps4));
 }
 
+// WENO-Z weights (an option beyond the paper's, Section 7): t_k = C_k (1 + (tau / b_k)^2) with
+// the global indicator tau of the b (differences of the b cancel eps), normalised by the
+// reciprocal of their sum; result sum t_k P_k inv.  FP64 forms the ratios directly; FP32
+// scales them by b_min (s_k = b_min / b_k <= 1) and writes t_k = C_k (beta + (1 - beta) s_k^2),
+// beta = b_min^2 / (b_min^2 + tau^2), so that no term overflows.
+template <typename T, int K>
+__device__ __forceinline__ T weno_z_combine(const T* b, T tau, const T* C, const T* P) {
+  T t[K], sum = T(0);
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const T q = quot(tau, b[k]);
+      t[k] = C[k] * fma(q, q, T(1));
+      sum += t[k];
+    }
+  } else {
+    T bmin = b[0];
+#pragma unroll
+    for (int k = 1; k < K; ++k) bmin = fminf(bmin, b[k]);
+    T beta;
+    if (tau <= bmin) { const T x = quot(tau, bmin); beta = recip(fma(x, x, T(1))); }
+    else { const T y = quot(bmin, tau), y2 = y * y; beta = quot(y2, y2 + T(1)); }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const T sk = quot(bmin, b[k]);
+      t[k] = C[k] * fma(T(1) - beta, sk * sk, beta);
+      sum += t[k];
+    }
+  }
+  T num = t[0] * P[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) num = fma(t[k], P[k], num);
+  return num * recip(sum);
+}
+
 template <int R, typename T>
-__device__ __forceinline__ T weno_delta(const T* u, T eps, int ppm, int linw) {
+__device__ __forceinline__ T weno_delta(const T* u, T eps, int ppm, int linw, int wz = 0) {
   if constexpr (R == 4) {
     // Table A1 candidates relative to w_j, u[m+3] = w_{j+m} - w_j (u[3] is not read)
     const T p[4] = {T(-5.0 / 16) * u[0] + T(21.0 / 16) * u[1] - T(35.0 / 16) * u[2],
@@ -623,6 +772,7 @@ __device__ __forceinline__ T weno_delta(const T* u, T eps, int ppm, int linw) {
     T b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) b[k] = is_b4(k, D[k], D[k + 1], D[k + 2], eps);
+    if (wz) return weno_z_combine<T, 4>(b, fabs(b[0] + T(3) * b[1] - T(3) * b[2] - b[3]), C, p);
     T w[4];
     raw_weights<T, 4>(b, C, w);
     if (ppm) {
@@ -651,6 +801,7 @@ __device__ __forceinline__ T weno_delta(const T* u, T eps, int ppm, int linw) {
     if (linw) return fma(C[0], P[0], fma(C[1], P[1], C[2] * P[2]));
     const T eps4 = T(4) * eps;
     const T b[3] = {is_b4x(e0, f0, eps4), is_b4x(e1, f1, eps4), is_b4x(e2, f2, eps4)};
+    if (wz) return weno_z_combine<T, 3>(b, fabs(b[0] - b[2]), C, P);
     T t[3], inv;
     raw_terms<T, 3>(b, C, t, inv);
     if (ppm) {
@@ -676,6 +827,7 @@ __device__ __forceinline__ T weno_delta(const T* u, T eps, int ppm, int linw) {
     if (linw) return fma(C[0], P[0], C[1] * P[1]);
     const T eps4 = T(4) * eps;
     const T b[2] = {is_b4x(e0, f0, eps4), is_b4x(e1, f1, eps4)};
+    if (wz) return weno_z_combine<T, 2>(b, fabs(b[0] - b[1]), C, P);
     T t[2], inv;
     raw_terms<T, 2>(b, C, t, inv);
     if (ppm) {
@@ -750,7 +902,7 @@ __device__ __forceinline__ float2 is_b4x2(float2 e, float2 f, float2 eps4) {
 }
 
 template <int R>
-__device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int ppm, int linw) {
+__device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int ppm, int linw, int wz = 0) {
   const float2 eps = bc2(eps_);
   if constexpr (R == 4) {
     const float2 p[4] = {
@@ -771,6 +923,13 @@ __device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int
       const float2 r1 = fma2(bc2((float)is4c(k, 0)), d1, fma2(bc2((float)is4c(k, 3)), d2, mul2(bc2((float)is4c(k, 4)), d3)));
       const float2 r2 = fma2(bc2((float)is4c(k, 1)), d2, mul2(bc2((float)is4c(k, 5)), d3));
       b[k] = fma2(d1, r1, fma2(d2, r2, fma2(mul2(bc2((float)is4c(k, 2)), d3), d3, eps)));
+    }
+    if (wz) {
+      float bx[4], by[4], px[4], py[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { bx[k] = b[k].x; by[k] = b[k].y; px[k] = p[k].x; py[k] = p[k].y; }
+      return make_float2(weno_z_combine<float, 4>(bx, fabsf(bx[0] + 3.f * bx[1] - 3.f * bx[2] - bx[3]), C, px),
+                         weno_z_combine<float, 4>(by, fabsf(by[0] + 3.f * by[1] - 3.f * by[2] - by[3]), C, py));
     }
     float2 w[4];
     raw_weights2<4>(b, C, w);
@@ -802,6 +961,12 @@ __device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int
     if (linw) return fma2(bc2(C[0]), P[0], fma2(bc2(C[1]), P[1], mul2(bc2(C[2]), P[2])));
     const float2 eps4 = bc2(4.0f * eps_);
     const float2 b[3] = {is_b4x2(e0, f0, eps4), is_b4x2(e1, f1, eps4), is_b4x2(e2, f2, eps4)};
+    if (wz) {
+      const float bx[3] = {b[0].x, b[1].x, b[2].x}, by[3] = {b[0].y, b[1].y, b[2].y};
+      const float px[3] = {P[0].x, P[1].x, P[2].x}, py[3] = {P[0].y, P[1].y, P[2].y};
+      return make_float2(weno_z_combine<float, 3>(bx, fabsf(bx[0] - bx[2]), C, px),
+                         weno_z_combine<float, 3>(by, fabsf(by[0] - by[2]), C, py));
+    }
     float2 t[3], inv;
     raw_terms2<3>(b, C, t, inv);
     if (ppm) {
@@ -828,6 +993,12 @@ __device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int
     if (linw) return fma2(bc2(C[0]), P[0], mul2(bc2(C[1]), P[1]));
     const float2 eps4 = bc2(4.0f * eps_);
     const float2 b[2] = {is_b4x2(e0, f0, eps4), is_b4x2(e1, f1, eps4)};
+    if (wz) {
+      const float bx[2] = {b[0].x, b[1].x}, by[2] = {b[0].y, b[1].y};
+      const float px[2] = {P[0].x, P[1].x}, py[2] = {P[0].y, P[1].y};
+      return make_float2(weno_z_combine<float, 2>(bx, fabsf(bx[0] - bx[1]), C, px),
+                         weno_z_combine<float, 2>(by, fabsf(by[0] - by[1]), C, py));
+    }
     float2 t[2], inv;
     raw_terms2<2>(b, C, t, inv);
     if (ppm) {

@@ -8,6 +8,15 @@
 
 namespace fsp {
 
+// The scheme's free parameter (0 in the configuration means the printed scheme, 1).
+double scheme_alpha_of(const fsp_config& c);
+// Whether every option beyond the paper's schemes is at its default (the marching kernels
+// and the adjoint take only these).
+bool default_options(const fsp_config& c);
+// FSP_ERR_INVALID_ARG for an option out of range, FSP_ERR_UNSUPPORTED for a combination without
+// kernels (the midpoint splittings in mixed precision).
+fsp_status check_options(const fsp_config& c);
+
 // Kernel parameters of one block from the public configuration (host side).
 Params make_params(const fsp_config& cfg, const fsp_block& blk, const double* metrics);
 

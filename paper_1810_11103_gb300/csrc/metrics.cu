@@ -109,7 +109,7 @@ cudaError_t launch_metrics(const fsp_config& cfg, const fsp_block& blk, const do
   const int threads = 256;
   const long long blocks = (n + threads - 1) / threads;
   const int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
-  metrics_kernel<<<grid, threads, 0, st>>>(C, central_of(cfg.scheme), cfg.interp, interp_points(cfg.scheme), M);
+  metrics_kernel<<<grid, threads, 0, st>>>(C, central_of(cfg.scheme, scheme_alpha_of(cfg)), cfg.interp, interp_points(cfg.scheme), M);
   return cudaGetLastError();
 }
 

@@ -293,9 +293,11 @@ __device__ __forceinline__ void node_split(const Real q[4], double mx, double my
 // The midpoint part of interface p + 1/2 from its two reconstructed states Qs[0] = Q+ and
 // Qs[1] = Q-: the midpoint metrics interpolated as in the metric evaluation (Section 2.4) and
 // the midpoint fluxes (Section 2.3); at(m) gives the staged index of node p + m.
+// msplit (same precision only): 1 Steger-Warming, 2 Van Leer splitting of the midpoint flux
+// (an option beyond the paper's, Section 7) instead of the Lax-Friedrichs type.
 template <int S, typename Real, typename Acc, typename At>
 __device__ __forceinline__ void mid_fluxes(const Staged<Real, Acc>& st, const At& at, const Real Qs[2][4], Real gamma,
-                                           int interp, Acc A, Mid<Real, Acc>& mo) {
+                                           int interp, Acc A, Mid<Real, Acc>& mo, int msplit = 0) {
   using Sc = Scheme<S>;
   Acc mmx, mmy;
   if constexpr (Sc::r == 4) {
@@ -340,6 +342,11 @@ __device__ __forceinline__ void mid_fluxes(const Staged<Real, Acc>& st, const At
         }
     }
   } else {
+    if (msplit) {
+      split_mid2<Real>(msplit, 1, Qs[0], mmx, mmy, gamma, mo.f[0]);
+      split_mid2<Real>(msplit, -1, Qs[1], mmx, mmy, gamma, mo.f[1]);
+      return;
+    }
     // twice the split midpoint fluxes: E^(Q+) + A^ Q+ and E^(Q-) - A^ Q-, with
     // E^ = (rho U, rho u U + mx p, rho v U + my p, (E + p) U)
 #pragma unroll
@@ -363,7 +370,7 @@ __device__ __forceinline__ void mid_fluxes(const Staged<Real, Acc>& st, const At
 // weno_scale<R>); FP32 runs components (0, 1) and (2, 3) in the two lanes of packed float
 // arithmetic.
 template <int R, typename Real>
-__device__ __forceinline__ void side_weno(const Real (*wd)[4], Real eps, int ppm, int linw, Real Wm[4]) {
+__device__ __forceinline__ void side_weno(const Real (*wd)[4], Real eps, int ppm, int linw, Real Wm[4], int wz = 0) {
   constexpr int H = R == 4 ? 3 : 2, NA = 2 * H;
   if constexpr (std::is_same<Real, float>::value) {
 #pragma unroll
@@ -372,7 +379,7 @@ __device__ __forceinline__ void side_weno(const Real (*wd)[4], Real eps, int ppm
 #pragma unroll
       for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = make_float2(wd[a][2 * kp], wd[a][2 * kp + 1]);
       u[H] = make_float2(0.f, 0.f);
-      const float2 W2 = weno_delta_x2<R>(u, eps, ppm, linw);
+      const float2 W2 = weno_delta_x2<R>(u, eps, ppm, linw, wz);
       Wm[2 * kp] = W2.x;
       Wm[2 * kp + 1] = W2.y;
     }
@@ -383,7 +390,7 @@ __device__ __forceinline__ void side_weno(const Real (*wd)[4], Real eps, int ppm
 #pragma unroll
       for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = wd[a][kc];
       u[H] = Real(0);
-      Wm[kc] = weno_delta<R, Real>(u, eps, ppm, linw);
+      Wm[kc] = weno_delta<R, Real>(u, eps, ppm, linw, wz);
     }
   }
 }
@@ -472,10 +479,12 @@ __device__ __forceinline__ void centre_sides(const Staged<Real, Acc>& st, const 
 // branches on them; the tile kernels read them at run time.
 template <int S, typename Real, typename Acc, bool DEF = false, typename At>
 __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
-                                              int ppm_, int linw_, int interp_, Acc A, Mid<Real, Acc>& mo) {
+                                              int ppm_, int linw_, int interp_, Acc A, Mid<Real, Acc>& mo,
+                                              int wz_ = 0, int msplit_ = 0) {
   using Sc = Scheme<S>;
   constexpr int SC = weno_scale<Sc::r>();
   const int ppm = DEF ? 1 : ppm_, linw = DEF ? 0 : linw_, interp = DEF ? 0 : interp_;
+  const int wz = DEF ? 0 : wz_, msplit = DEF ? 0 : msplit_;
   const int o0 = at(0), o1 = at(1);
   Real nx, ny;
   char_direction(st, o0, o1, nx, ny);
@@ -503,16 +512,31 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
       E.project(t[0] - qc[0], t[1] - qc[1], t[2] - qc[2], t[3] - qc[3], wd[a]);
     }
     Real Wm[4];
-    side_weno<Sc::r, Real>(wd, eps, ppm, linw, Wm);
+    side_weno<Sc::r, Real>(wd, eps, ppm, linw, Wm, wz);
     E.recon(Wm, qc, Qs[side]);
   }
 
-  mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, interp, A, mo);
+  mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, interp, A, mo, msplit);
 }
 
 // h+ coefficient n_k of the node flux f+_{p+k} (0 outside the scheme's stencil)
 template <int S>
 __host__ __device__ constexpr double hnode(int k) { return Scheme<S>::hn(k); }
+
+// The halved h+ coefficients of the h combination: the printed scheme's as compile-time
+// constants (RT false: the marching kernels), or those at the free parameter of the
+// one-midpoint forms from the kernel parameters (RT true: the tile kernels).  The stencil's
+// support is the same for every alpha, so which terms exist stays a compile-time fact.
+template <int S, bool RT>
+struct HalfCoef {
+  const Params& P;
+  __device__ __forceinline__ double m0() const { return RT ? P.hc[0] : 0.5 * Scheme<S>::m0; }
+  __device__ __forceinline__ double m1() const { return RT ? P.hc[1] : 0.5 * Scheme<S>::m1; }
+  __device__ __forceinline__ double n(int k) const { return RT ? P.hc[5 + k] : 0.5 * Scheme<S>::hn(k); }
+  __device__ __forceinline__ float m0f() const { return RT ? P.hcf[0] : float(0.5 * Scheme<S>::m0); }
+  __device__ __forceinline__ float m1f() const { return RT ? P.hcf[1] : float(0.5 * Scheme<S>::m1); }
+  __device__ __forceinline__ float nf(int k) const { return RT ? P.hcf[5 + k] : float(0.5 * Scheme<S>::hn(k)); }
+};
 
 // h = h+ + h- at p + 1/2 (Eqs. 3.4, 3.8, 3.16, 3.20; h- the mirror of h+), the midpoint
 // terms m0 (f+_{p+1/2} + f-_{p+1/2}) + m1 (f+_{p-1/2} + f-_{p+3/2}) plus the node terms
@@ -525,28 +549,31 @@ __host__ __device__ constexpr double hnode(int k) { return Scheme<S>::hn(k); }
 // (A^/2) [sum_d (n_{-d} - n_{1+d}) (Q_{p-d} - Q_{p+1+d}) + m0 (Q+ - Q-) + m1 (Q+_{p-1/2} -
 // Q-_{p+3/2})], taken in float.  In a uniform flow every state difference is exactly zero,
 // so the free-stream residual is that of the double part.
-template <int S, typename Real, typename Acc, typename At>
+template <int S, typename Real, typename Acc, bool RT = false, typename At>
 __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At& at, Acc A,
                                           const Mid<Real, Acc>& c, const Mid<Real, Acc>& lo,
-                                          const Mid<Real, Acc>& hi, Acc h[4]) {
+                                          const Mid<Real, Acc>& hi, Acc h[4], const Params& P) {
   using Sc = Scheme<S>;
+  const HalfCoef<S, RT> K{P};
   if constexpr (Staged<Real, Acc>::SPLIT) {
     Acc he[4];
     Real hq[4];
+    const double m0 = 2.0 * K.m0(), m1 = 2.0 * K.m1();
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       if constexpr (Sc::nmp == 1) {
-        he[v] = Acc(Sc::m0) * c.f[0][v];
-        hq[v] = Real(Sc::m0) * c.q[0][v];
+        he[v] = Acc(m0) * c.f[0][v];
+        hq[v] = Real(m0) * c.q[0][v];
       } else {
-        he[v] = Acc(0.5 * Sc::m0) * (c.f[0][v] + c.f[1][v]) + Acc(0.5 * Sc::m1) * (lo.f[0][v] + hi.f[1][v]);
-        hq[v] = Real(Sc::m0) * (c.q[0][v] - c.q[1][v]) + Real(Sc::m1) * (lo.q[0][v] - hi.q[1][v]);
+        he[v] = Acc(K.m0()) * (c.f[0][v] + c.f[1][v]) + Acc(K.m1()) * (lo.f[0][v] + hi.f[1][v]);
+        hq[v] = Real(m0) * (c.q[0][v] - c.q[1][v]) + Real(m1) * (lo.q[0][v] - hi.q[1][v]);
       }
     }
 #pragma unroll
     for (int d = 0; d <= 3; ++d) {
-      const double ce = 0.5 * (hnode<S>(-d) + hnode<S>(1 + d)), cq = hnode<S>(-d) - hnode<S>(1 + d);
-      if (ce == 0.0 && cq == 0.0) continue;
+      // which terms exist is the printed scheme's (the same support at every alpha)
+      if (0.5 * (hnode<S>(-d) + hnode<S>(1 + d)) == 0.0 && hnode<S>(-d) - hnode<S>(1 + d) == 0.0) continue;
+      const double ce = K.n(-d) + K.n(1 + d), cq = 2.0 * (K.n(-d) - K.n(1 + d));
       Acc a[4], b[4];
       Real qa[4], qb[4];
       ld4(st.fp, st.n, at(-d), a);
@@ -555,8 +582,8 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
       ld4(st.q, st.n, at(1 + d), qb);
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        if (ce != 0.0) he[v] += Acc(ce) * (a[v] + b[v]);
-        if (cq != 0.0) hq[v] += Real(cq) * (qa[v] - qb[v]);
+        if (RT || ce != 0.0) he[v] += Acc(ce) * (a[v] + b[v]);
+        if (RT || cq != 0.0) hq[v] += Real(cq) * (qa[v] - qb[v]);
       }
     }
     const Real hA = Real(0.5) * from_f64_int(A);
@@ -567,10 +594,10 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
 #pragma unroll
     for (int v = 0; v < 4; v += 2) {
       const float2 c0 = make_float2(c.f[0][v], c.f[0][v + 1]), c1 = make_float2(c.f[1][v], c.f[1][v + 1]);
-      float2 hh = mul2(bc2(float(0.5 * Sc::m0)), add2(c0, c1));
+      float2 hh = mul2(bc2(K.m0f()), add2(c0, c1));
       if constexpr (Sc::nmp == 2) {
         const float2 l0 = make_float2(lo.f[0][v], lo.f[0][v + 1]), h1 = make_float2(hi.f[1][v], hi.f[1][v + 1]);
-        hh = fma2(bc2(float(0.5 * Sc::m1)), add2(l0, h1), hh);
+        hh = fma2(bc2(K.m1f()), add2(l0, h1), hh);
       }
       h[v] = hh.x;
       h[v + 1] = hh.y;
@@ -583,7 +610,7 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
       ld4(st.fm, st.n, at(1 - kk), b);
 #pragma unroll
       for (int v = 0; v < 4; v += 2) {
-        const float2 hh = fma2(bc2(float(0.5 * Sc::hn(kk))),
+        const float2 hh = fma2(bc2(K.nf(kk)),
                                add2(make_float2(a[v], a[v + 1]), make_float2(b[v], b[v + 1])),
                                make_float2(h[v], h[v + 1]));
         h[v] = hh.x;
@@ -593,8 +620,8 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
   } else {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      if constexpr (Sc::nmp == 1) h[v] = Acc(0.5 * Sc::m0) * (c.f[0][v] + c.f[1][v]);
-      else h[v] = Acc(0.5 * Sc::m0) * (c.f[0][v] + c.f[1][v]) + Acc(0.5 * Sc::m1) * (lo.f[0][v] + hi.f[1][v]);
+      if constexpr (Sc::nmp == 1) h[v] = Acc(K.m0()) * (c.f[0][v] + c.f[1][v]);
+      else h[v] = Acc(K.m0()) * (c.f[0][v] + c.f[1][v]) + Acc(K.m1()) * (lo.f[0][v] + hi.f[1][v]);
     }
 #pragma unroll
     for (int kk = -3; kk <= 3; ++kk) {
@@ -603,7 +630,7 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
       ld4(st.fp, st.n, at(kk), a);
       ld4(st.fm, st.n, at(1 - kk), b);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) h[v] += Acc(0.5 * Sc::hn(kk)) * (a[v] + b[v]);
+      for (int v = 0; v < 4; ++v) h[v] += Acc(K.n(kk)) * (a[v] + b[v]);
     }
   }
 }
@@ -733,10 +760,10 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const int c0 = p + 4;  // staged position of node p
     auto at = [&](int m) { return SI(l, c0 + m); };
     Mid<Real, Acc> mo;
-    interface_mid<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, sA[l], mo);
+    interface_mid<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, sA[l], mo, P.wz, P.msplit);
     if constexpr (Sc::nmp == 1) {
       Acc h[4];
-      h_combine<S, Real, Acc>(st, at, sA[l], mo, mo, mo, h);
+      h_combine<S, Real, Acc, true>(st, at, sA[l], mo, mo, mo, h, P);
       st4(sH, NW, WI(l, pi), h[0], h[1], h[2], h[3]);
     } else {
       sF.put(WI(l, pi), mo);
@@ -760,7 +787,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
       sF.get(WI(l, pi - 1), 0, lo);
       sF.get(WI(l, pi + 1), 1, hi);
       Acc h[4];
-      h_combine<S, Real, Acc>(st, at, sA[l], c, lo, hi, h);
+      h_combine<S, Real, Acc, true>(st, at, sA[l], c, lo, hi, h, P);
       st4(sH, NW, WI(l, pi), h[0], h[1], h[2], h[3]);
     }
   }
@@ -923,7 +950,7 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
       }
       if constexpr (NMP == 1) {
         Acc h[4];
-        h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h);
+        h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h, P);
         st4(rH, RING, q & (RING - 1), h[0], h[1], h[2], h[3]);
       } else {
         rF.put(q & (RING - 1), mo);
@@ -942,7 +969,7 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
         rF.get((p - 1) & (RING - 1), 0, lo);
         rF.get((p + 1) & (RING - 1), 1, hi);
         Acc h[4];
-        h_combine<S, Real, Acc>(st, at, A, cm, lo, hi, h);
+        h_combine<S, Real, Acc>(st, at, A, cm, lo, hi, h, P);
         st4(rH, RING, p & (RING - 1), h[0], h[1], h[2], h[3]);
       }
       __syncwarp();
@@ -1126,7 +1153,7 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
       interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
       if constexpr (NMP == 1) {
         Acc h[4];
-        h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h);
+        h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h, P);
         st4(rH, Ms::NS, slot(q), h[0], h[1], h[2], h[3]);
       } else {
         rF.put(slot(q), mo);
@@ -1143,7 +1170,7 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
         rF.get(slot(p - 1), 0, lo);
         rF.get(slot(p + 1), 1, hi);
         Acc h[4];
-        h_combine<S, Real, Acc>(st, at, A, c, lo, hi, h);
+        h_combine<S, Real, Acc>(st, at, A, c, lo, hi, h, P);
         st4(rH, Ms::NS, slot(p), h[0], h[1], h[2], h[3]);
       }
     }

@@ -40,7 +40,8 @@ class _Config(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("precision", ctypes.c_int), ("interp", ctypes.c_int),
                 ("ppm", ctypes.c_int), ("linear_weights", ctypes.c_int), ("bc", ctypes.c_int * 4),
                 ("gamma", ctypes.c_double), ("lf_alpha", ctypes.c_double), ("eps", ctypes.c_double),
-                ("bc_state", (ctypes.c_double * 4) * 4)]
+                ("bc_state", (ctypes.c_double * 4) * 4), ("weights", ctypes.c_int), ("mid_split", ctypes.c_int),
+                ("scheme_alpha", ctypes.c_double)]
 
 
 class _Block(ctypes.Structure):
@@ -67,6 +68,9 @@ class Config:
     eps: float = 1e-40
     bc_state: Optional[Sequence[Sequence[float]]] = None
     period: Sequence[Sequence[float]] = ((0.0, 0.0), (0.0, 0.0))
+    weights: int = 0
+    mid_split: int = 0
+    scheme_alpha: float = 1.0
 
     @classmethod
     def from_dict(cls, d):
@@ -84,6 +88,7 @@ class Config:
         for f in range(4):
             for v in range(4):
                 c.bc_state[f][v] = float(st[f][v])
+        c.weights, c.mid_split, c.scheme_alpha = int(self.weights), int(self.mid_split), float(self.scheme_alpha)
         return c
 
 

@@ -13,7 +13,7 @@ from paper_1810_11103_gb300 import fsp
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 FIELDS = {
     "fsp_config": (fsp._Config, ["scheme", "precision", "interp", "ppm", "linear_weights", "bc", "gamma",
-                                 "lf_alpha", "eps", "bc_state"]),
+                                 "lf_alpha", "eps", "bc_state", "weights", "mid_split", "scheme_alpha"]),
     "fsp_block": (fsp._Block, ["ni", "nj", "ld", "period"]),
     "fsp_link": (fsp._Link, ["nbr", "face", "reversed", "offset"]),
 }
