@@ -73,7 +73,8 @@ def parse():
                     help="profiling run: the direction whose batched sweep is launched three times")
     ap.add_argument("--profile", choices=list(PRECISIONS) + ["adjoint", "probe"], default=None,
                     help="profiling run for ncu: build the cylinder batch in this precision, evaluate one "
-                         "right-hand side, then launch the batched xi sweep three times; 'adjoint': three "
+                         "right-hand side, launch one direction's batched sweep three times, then take one "
+                         "RK3 step; 'adjoint': three "
                          "fsp_rhs_vjp calls on the 512 x 512 shock-vortex case; 'probe': the FP64 and the "
                          "FP32 FMA probe once each, as the bench launches them; no timing")
     ap.add_argument("--per-block", action=argparse.BooleanOptionalAction, default=True,
@@ -721,7 +722,8 @@ def measure_accuracy(args, C, full=False):
 
 def profile_run(args, prec):
     """Minimal launch sequence for a profiler: metrics, one right-hand side (line maxima,
-    xi sweep, eta sweep), then three launches of one direction's batched sweep alone."""
+    xi sweep, eta sweep), three launches of one direction's batched sweep alone, then one RK3
+    step (the stage kernels)."""
     import numpy as np
     import torch
     from paper_1810_11103_gb300 import build as B
@@ -737,6 +739,7 @@ def profile_run(args, prec):
     D = [torch.empty(q.shape, dtype=torch.float32 if prec == "fp32" else torch.float64, device="cuda") for q in bt.Q]
     for _ in range(3):
         bt.flux_difference(args.profile_dir, D)
+    bt.rk3_step(1e-5)   # the stage kernels: line maxima, xi, eta with the stage epilogue
     torch.cuda.synchronize()
     print(f"profile run done: {prec}, {sum(b['x'].size for b in blocks)} nodes")
     bt.close()

@@ -194,7 +194,7 @@ struct fsp_batch {
   Params* d_params = nullptr;
   CoordBlock* d_coords = nullptr;
   TileRef *d_tx = nullptr, *d_te = nullptr, *d_tl = nullptr;
-  double* d_lam = nullptr;
+  double* d_lam = nullptr;            // line maxima, two buffers (A, then B) of lam_count each
   size_t lam_count = 0;
   std::vector<size_t> lam_off, acc_off, st_off;
   char* d_acc = nullptr;             // xi differences, one per block
@@ -210,7 +210,7 @@ struct fsp_batch {
 namespace {
 
 // pointer tables inside d_tab
-enum Tab { T_Q0 = 0, T_Q1, T_Q2, T_ACC, T_LX, T_LE, T_OUT, T_COUNT };
+enum Tab { T_Q0 = 0, T_Q1, T_Q2, T_ACC, T_LX, T_LE, T_LX2, T_LE2, T_OUT, T_COUNT };
 
 size_t al(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -382,7 +382,7 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   tiles_for(h, 1, 0, h->te);
   const size_t bytes = al(sizeof(Params) * nblocks) + al(sizeof(CoordBlock) * nblocks) +
                        al(sizeof(TileRef) * h->tx_cap) + al(sizeof(TileRef) * h->te_cap) +
-                       al(sizeof(TileRef) * h->tl.size()) + al(sizeof(double) * lam) + acc + 2 * st +
+                       al(sizeof(TileRef) * h->tl.size()) + al(sizeof(double) * 2 * lam) + acc + 2 * st +
                        al(sizeof(void*) * T_COUNT * nblocks);
   if (cudaMalloc(&h->dmem, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -395,7 +395,7 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   h->d_tx = carve<TileRef>(cur, h->tx_cap);
   h->d_te = carve<TileRef>(cur, h->te_cap);
   h->d_tl = carve<TileRef>(cur, h->tl.size());
-  h->d_lam = carve<double>(cur, lam);
+  h->d_lam = carve<double>(cur, 2 * lam);
   h->d_acc = cur; cur += acc;
   h->d_q1 = cur; cur += st;
   h->d_q2 = cur; cur += st;
@@ -427,6 +427,8 @@ fsp_status fsp_batch_bind(fsp_batch* h, const double* const* x, const double* co
     tab[T_ACC * nb + b] = h->d_acc + h->acc_off[b];
     tab[T_LX * nb + b] = h->d_lam + h->lam_off[b];
     tab[T_LE * nb + b] = h->d_lam + h->lam_off[b] + h->blk[b].nj;
+    tab[T_LX2 * nb + b] = h->d_lam + h->lam_count + h->lam_off[b];
+    tab[T_LE2 * nb + b] = h->d_lam + h->lam_count + h->lam_off[b] + h->blk[b].nj;
   }
   if (cudaMemcpy(h->d_params, h->params.data(), sizeof(Params) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(h->d_coords, h->coords.data(), sizeof(CoordBlock) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -473,14 +475,30 @@ fsp_status batch_lambda(fsp_batch* h, int in, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
 }
 
-fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, double cb, double dt, cudaStream_t st) {
+// Line maxima of a stage: LAM_KERNEL takes them from the input state into buffer A;
+// LAM_A / LAM_B find them already in that buffer, written by the previous stage's marching
+// eta pass.  lam_out (mode 1 only): the buffer (0 A, 1 B) that this stage's marching eta pass
+// fills with the maxima of the state it writes, or -1.
+enum { LAM_KERNEL = 0, LAM_A = 1, LAM_B = 2 };
+
+fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, double cb, double dt, cudaStream_t st,
+                       int lam_in = LAM_KERNEL, int lam_out = -1) {
   const int nb = h->nb;
   void** T = h->d_tab;
-  if (fsp_status s = batch_lambda(h, in, st)) return s;
-  const PassTables xi{h->d_params, h->d_tx, T + in * nb, T + T_LX * nb, nullptr, T + T_ACC * nb, nullptr,
-                      nullptr};
-  const PassTables eta{h->d_params, h->d_te, T + in * nb, T + T_LE * nb, T + T_ACC * nb, nullptr, T + out * nb,
-                       T + T_Q0 * nb};
+  if (lam_in == LAM_KERNEL)
+    if (fsp_status s = batch_lambda(h, in, st)) return s;
+  if (lam_out >= 0 &&
+      cudaMemsetAsync(h->d_lam + lam_out * h->lam_count, 0, sizeof(double) * h->lam_count, st) != cudaSuccess)
+    return FSP_ERR_CUDA;
+  const int lx = lam_in == LAM_B ? T_LX2 : T_LX, le = lam_in == LAM_B ? T_LE2 : T_LE;
+  const PassTables xi{h->d_params, h->d_tx, T + in * nb, T + lx * nb, nullptr, T + T_ACC * nb, nullptr, nullptr};
+  PassTables eta{h->d_params, h->d_te, T + in * nb, T + le * nb, T + T_ACC * nb, nullptr, T + out * nb,
+                 T + T_Q0 * nb};
+  if (lam_out >= 0) {
+    eta.lxo = T + (lam_out ? T_LX2 : T_LX) * nb;
+    eta.leo = T + (lam_out ? T_LE2 : T_LE) * nb;
+    mode = 2;
+  }
   const int ntx = (int)h->tx.size(), nte = (int)h->te.size();
   cudaError_t e = h->cfg.precision == FSP_FP64
                       ? batch_fp64(h->cfg.scheme, mode, xi, ntx, h->vx, eta, nte, h->ve, ca, cb, dt, st)
@@ -489,10 +507,16 @@ fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, doubl
   return e == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
 }
 
+// One TVD-RK3 step.  The first stage's line maxima come from the line-maxima kernel (the
+// caller may have written Q between steps); with the marching eta pass, stages 1 and 2 take
+// the maxima of the states they write (Q1 into B, Q2 into A) for the stage after.  Not in
+// mixed precision, whose eta CTAs would no longer fit two to an SM with the extra operands.
 fsp_status batch_rk3(fsp_batch* h, double dt, cudaStream_t st) {
-  if (fsp_status s = batch_stage(h, T_Q0, T_Q1, 1, 0.0, 1.0, dt, st)) return s;
-  if (fsp_status s = batch_stage(h, T_Q1, T_Q2, 1, 0.75, 0.25, dt, st)) return s;
-  return batch_stage(h, T_Q2, T_Q0, 1, 1.0 / 3.0, 2.0 / 3.0, dt, st);
+  const bool fuse = h->ve == MARCH && h->cfg.precision != FSP_FP32_MIXED;
+  if (fsp_status s = batch_stage(h, T_Q0, T_Q1, 1, 0.0, 1.0, dt, st, LAM_KERNEL, fuse ? 1 : -1)) return s;
+  if (fsp_status s = batch_stage(h, T_Q1, T_Q2, 1, 0.75, 0.25, dt, st, fuse ? LAM_B : LAM_KERNEL, fuse ? 0 : -1))
+    return s;
+  return batch_stage(h, T_Q2, T_Q0, 1, 1.0 / 3.0, 2.0 / 3.0, dt, st, fuse ? LAM_A : LAM_KERNEL);
 }
 
 }  // namespace

@@ -21,7 +21,9 @@
 
 namespace fsp {
 
-enum { MODE_ACC = 0, MODE_RHS = 1, MODE_STAGE = 2 };
+// MODE_STAGE_L: the RK stage of the marching eta pass that also takes the next stage's line
+// maxima (Section 2.3's A^ of both directions) from the states it writes.
+enum { MODE_ACC = 0, MODE_RHS = 1, MODE_STAGE = 2, MODE_STAGE_L = 3 };
 
 // Tile shapes: 256 threads, NL grid lines x W interface slots per CTA.  Variant 0 is the
 // default; fsp_batch_tune may pick another per direction for a batch.
@@ -1032,19 +1034,25 @@ struct MarchEtaShape {
   static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(NS); }
   static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * NS; }
   static constexpr size_t o_raw() { return o_f() + (NMP == 2 ? MidStore<Real, Acc>::bytes(NS) : 0); }
-  // per thread: next node's state and two metrics; epilogue J^-1, other difference, Q^n
+  // per thread: next node's state and two metrics; then two buffers (steps t even and odd)
+  // of the epilogue operands: J^-1, the xi metrics (MODE_STAGE_L), the other direction's
+  // difference, Q^n (stage modes)
   static constexpr size_t o_ep() { return o_raw() + (size_t)NT * (4 * sizeof(Real) + 16); }
-  static constexpr size_t smem_bytes(int mode) {
-    return o_ep() + (mode == 0 ? 0 : (size_t)NT * (8 + 4 * sizeof(Acc) + (mode == 2 ? 4 * sizeof(Real) : 0)));
+  static constexpr size_t ep_bytes(int mode) {
+    return mode == 0 ? 0
+                     : (size_t)NT * (8 + (mode == 3 ? 16 : 0) + 4 * sizeof(Acc) + (mode >= 2 ? 4 * sizeof(Real) : 0));
   }
+  static constexpr size_t smem_bytes(int mode) { return o_ep() + 2 * ep_bytes(mode); }
 };
 
 template <int S, int MODE, typename Real, typename Acc>
 __device__ __forceinline__ void march_col(const Params& P, const Real* __restrict__ Q, const Real* const* qtab,
                                           const double* __restrict__ lam, const Acc* __restrict__ Dacc,
                                           Acc* __restrict__ Dout, Real* qout, const Real* Qn, double ca, double cb,
-                                          double dt, int c0, int s0, int s1, unsigned char* sm) {
+                                          double dt, int c0, int s0, int s1, unsigned char* sm,
+                                          double* lxo = nullptr, double* leo = nullptr) {
   using Ms = MarchEtaShape<S, Real, Acc>;
+  constexpr bool STAGE = MODE >= MODE_STAGE, LAM = MODE == MODE_STAGE_L;
   constexpr int NMP = Scheme<S>::nmp;
   constexpr int H = Scheme<S>::r == 4 ? 3 : 2;     // stencil half-width of the interpolation
   constexpr int K = H == 3 ? 3 : 2;                 // rows staged ahead of the step's first row
@@ -1058,9 +1066,11 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
   rF.carve(sm + Ms::o_f(), Ms::NS);
   Real* rawq = reinterpret_cast<Real*>(sm + Ms::o_raw());              // [4][NT]
   double* rawm = reinterpret_cast<double*>(rawq + 4 * Ms::NT);         // [2][NT]
-  double* eJ = reinterpret_cast<double*>(sm + Ms::o_ep());              // [NT]
-  Acc* eD = reinterpret_cast<Acc*>(eJ + Ms::NT);                       // [4][NT]
-  Real* eQ = reinterpret_cast<Real*>(eD + 4 * Ms::NT);                  // [4][NT]
+  // epilogue buffer k: J^-1 [NT], xi metrics [2][NT] (MODE_STAGE_L), difference [4][NT], Q^n [4][NT]
+  auto eJ = [&](int k) { return reinterpret_cast<double*>(sm + Ms::o_ep() + k * Ms::ep_bytes(MODE)); };
+  auto eX = [&](int k) { return eJ(k) + Ms::NT; };
+  auto eD = [&](int k) { return reinterpret_cast<Acc*>(eJ(k) + (LAM ? 3 : 1) * Ms::NT); };
+  auto eQ = [&](int k) { return reinterpret_cast<Real*>(eD(k) + 4 * Ms::NT); };
   const int n = P.nj;
   const Real gamma = Real(P.gamma);
   const Real eps = sizeof(Real) == 8 ? from_f64<Real>(P.eps) : from_f64<Real>(P.eps < 1e-30 ? 1e-30 : P.eps);
@@ -1089,8 +1099,9 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
     st.store(slot(m), q, pw, amx, amy, fp, fm, mx, my);
   };
   // cp.async of node (col, m) into this thread's staging slot (interior rows only), and of the
-  // epilogue operands of output node (col, s)
-  auto prefetch = [&](int m, int s) -> bool {
+  // epilogue operands of output node (col, s) into epilogue buffer k (every slot is private
+  // to its thread)
+  auto prefetch = [&](int m, int s, int k) -> bool {
     bool ok = false;
     if (on && m >= 0 && m < n && m <= s1 + 3) {
       const long long o = (long long)m * P.ld + col;
@@ -1104,21 +1115,27 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
     if constexpr (MODE != MODE_ACC) {
       if (on && s >= s0 && s < s1) {
         const long long o = (long long)s * P.ld + col;
-        cp_async<8>(eJ + tid, P.met + 4 * P.mplane + (long long)(s + G) * P.mld + (col + G));
+        const double* ms = P.met + (long long)(s + G) * P.mld + (col + G);
+        cp_async<8>(eJ(k) + tid, ms + 4 * P.mplane);
+        if constexpr (LAM) {
+          cp_async<8>(eX(k) + tid, ms);
+          cp_async<8>(eX(k) + Ms::NT + tid, ms + P.mplane);
+        }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) cp_async<sizeof(Acc)>(eD + v * Ms::NT + tid, Dacc + v * plane + o);
-        if constexpr (MODE == MODE_STAGE) {
+        for (int v = 0; v < 4; ++v) cp_async<sizeof(Acc)>(eD(k) + v * Ms::NT + tid, Dacc + v * plane + o);
+        if constexpr (STAGE) {
 #pragma unroll
-          for (int v = 0; v < 4; ++v) cp_async<sizeof(Real)>(eQ + v * Ms::NT + tid, Qn + v * plane + o);
+          for (int v = 0; v < 4; ++v) cp_async<sizeof(Real)>(eQ(k) + v * Ms::NT + tid, Qn + v * plane + o);
         }
       }
     }
     return ok;
   };
+  Real colmax = Real(0);                                   // MODE_STAGE_L: this thread's eta maximum
   const int lag = NMP == 1 ? 1 : 3;                       // output s = r - lag + w
   // start-up: rows s0 - 2 - NMP .. s0 + K - 1
   if (w < K + NMP + H) stage_node(s0 - NMP - H + w, false);
-  bool staged = prefetch(s0 + K + w, s0 - lag + w);
+  bool staged = prefetch(s0 + K + w, s0 - lag + w, 0);
   cp_async_commit();
   const int steps = (s1 - s0 + 2 * NMP - 1 + EW - 1) / EW;
   for (int t = 0; t < steps; ++t) {
@@ -1126,23 +1143,10 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
     const int m = r + K + w;
     cp_async_wait_all();
     stage_node(m, staged);
-    // the epilogue operands of this step's output, read now: the slots are refilled below
+    // this step's output node; its epilogue operands stay in buffer t & 1 until the output
+    // phase, while the next step's arrive in the other buffer
     const int s = r - lag + w;
-    double Jv = 0.0;
-    Acc Dv[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-    Real Qv[4] = {Real(0), Real(0), Real(0), Real(0)};
-    if constexpr (MODE != MODE_ACC) {
-      if (on && s >= s0 && s < s1) {
-        Jv = eJ[tid];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) Dv[v] = eD[v * Ms::NT + tid];
-        if constexpr (MODE == MODE_STAGE) {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) Qv[v] = eQ[v * Ms::NT + tid];
-        }
-      }
-    }
-    staged = prefetch(m + EW, s + EW);
+    staged = prefetch(m + EW, s + EW, (t + 1) & 1);
     cp_async_commit();
     __syncthreads();
     const int q = r - NMP + w;
@@ -1174,11 +1178,18 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
         st4(rH, Ms::NS, slot(p), h[0], h[1], h[2], h[3]);
       }
     }
-    if constexpr (MODE == MODE_STAGE) {
-      if (on && s >= s0 && s < s1) ld4(st.q, st.n, slot(s), qs);
+    // node s's staged state (and eta metrics) before the barrier: after it, warps that run
+    // ahead restage the ring
+    Real emx = Real(0), emy = Real(0);
+    if constexpr (STAGE) {
+      if (on && s >= s0 && s < s1) {
+        ld4(st.q, st.n, slot(s), qs);
+        if constexpr (LAM) st.met_real(slot(s), emx, emy);
+      }
     }
     __syncthreads();
     // outputs: node s, H_{s+1/2} - H_{s-1/2}
+    Real sx = Real(0);
     if (on && s >= s0 && s < s1) {
       Acc hp[4], hm[4], R[4];
       ld4(rH, Ms::NS, slot(s), hp);
@@ -1190,20 +1201,48 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
 #pragma unroll
         for (int v = 0; v < 4; ++v) Dout[v * plane + o] = R[v];
       } else {
-        const Acc mJ = -recip(from_f64<Acc>(Jv));
+        const int k = t & 1;
+        const Acc mJ = -recip(from_f64<Acc>(eJ(k)[tid]));
+        Real qo[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const Acc d = (Dv[v] + R[v]) * mJ;
+          const Acc d = (eD(k)[v * Ms::NT + tid] + R[v]) * mJ;
           if constexpr (MODE == MODE_RHS) {
-            qout[v * plane + o] = narrow<Real>(d);
+            qo[v] = narrow<Real>(d);
           } else {
-            qout[v * plane + o] = narrow<Real>(Acc(ca) * widen<Acc>(Qv[v]) + Acc(cb) * (widen<Acc>(qs[v]) + Acc(dt) * d));
+            qo[v] = narrow<Real>(Acc(ca) * widen<Acc>(eQ(k)[v * Ms::NT + tid]) +
+                                 Acc(cb) * (widen<Acc>(qs[v]) + Acc(dt) * d));
           }
+          qout[v * plane + o] = qo[v];
+        }
+        if constexpr (LAM) {
+          // |U^| + c|k^| of the written state, as the line-maxima kernel takes it
+          sx = spectral_radius(qo, from_f64_alu<Real>(eX(k)[tid]), from_f64_alu<Real>(eX(k)[Ms::NT + tid]), gamma);
+          colmax = max(colmax, spectral_radius(qo, emx, emy, gamma));
         }
       }
     }
+    if constexpr (LAM) {
+      // row s's maximum over this CTA's 32 columns (the step is uniform over the warp)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) sx = max(sx, __shfl_xor_sync(0xffffffffu, sx, off));
+      if (L == 0 && s >= s0 && s < s1)
+        atomicMax(reinterpret_cast<unsigned long long*>(lxo + s), (unsigned long long)__double_as_longlong((double)sx));
+    }
   }
   cp_async_wait_all();
+  if constexpr (LAM) {
+    // each column's maximum over the CTA's segment (the staging area is free now)
+    __syncthreads();
+    rawq[tid] = colmax;
+    __syncthreads();
+    if (w == 0 && on) {
+      Real mc = rawq[L];
+#pragma unroll
+      for (int k = 1; k < EW; ++k) mc = max(mc, rawq[k * 32 + L]);
+      atomicMax(reinterpret_cast<unsigned long long*>(leo + col), (unsigned long long)__double_as_longlong((double)mc));
+    }
+  }
 }
 
 // Resident CTAs per SM the kernels are compiled for (register budget): FP64 2, FP32 4, mixed 3
@@ -1236,6 +1275,8 @@ struct BatchPass {                 // device arrays indexed by block
   Acc* const* dout;                // this direction's difference (mode 0)
   Real* const* qout;               // dQ/dt or the stage state (modes 1, 2)
   const Real* const* qn;           // Q^n of the RK step (mode 2)
+  double* const* lxo;              // line maxima of the written state, xi and eta (MODE_STAGE_L)
+  double* const* leo;
 };
 
 template <int S, int DIR, int MODE, typename Real, typename Acc, int V>
@@ -1296,7 +1337,8 @@ march_eta_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) 
   const int s0 = t.bx * seg, s1 = min(sp.nj, s0 + seg);
   march_col<S, MODE, Real, Acc>(sp, B.q[b], B.q, B.lam[b], MODE == MODE_ACC ? nullptr : B.dacc[b],
                                 MODE == MODE_ACC ? B.dout[b] : nullptr, MODE == MODE_ACC ? nullptr : B.qout[b],
-                                MODE == MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, t.by * 32, s0, s1, smem_raw);
+                                MODE >= MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, t.by * 32, s0, s1, smem_raw,
+                                MODE == MODE_STAGE_L ? B.lxo[b] : nullptr, MODE == MODE_STAGE_L ? B.leo[b] : nullptr);
 }
 
 // Untyped pass tables (device arrays of per-block pointers) and their typed view.
@@ -1309,6 +1351,8 @@ struct PassTables {
   void* const* dout;
   void* const* qout;
   void* const* qn;
+  void* const* lxo;     // MODE_STAGE_L only
+  void* const* leo;
 };
 
 template <typename Real, typename Acc>
@@ -1322,6 +1366,8 @@ BatchPass<Real, Acc> typed_pass(const PassTables& t) {
   B.dout = reinterpret_cast<Acc* const*>(t.dout);
   B.qout = reinterpret_cast<Real* const*>(t.qout);
   B.qn = reinterpret_cast<const Real* const*>(t.qn);
+  B.lxo = reinterpret_cast<double* const*>(t.lxo);
+  B.leo = reinterpret_cast<double* const*>(t.leo);
   return B;
 }
 
@@ -1368,6 +1414,11 @@ cudaError_t launch_march_eta_batch(const BatchPass<Real, Acc>& B, int ntiles, do
 template <int S, int DIR, int MODE, typename Real, typename Acc>
 cudaError_t launch_sweep_batch(const BatchPass<Real, Acc>& B, int ntiles, int v, double ca, double cb, double dt,
                                cudaStream_t st) {
+  if constexpr (MODE == MODE_STAGE_L) {
+    // the line maxima are taken by the marching eta pass only
+    if (DIR == 1 && v == MARCH) return launch_march_eta_batch<S, MODE, Real, Acc>(B, ntiles, ca, cb, dt, st);
+    return cudaErrorNotSupported;
+  }
   if (v == MARCH) {
     if constexpr (DIR == 0) return launch_march_batch<S, MODE, Real, Acc>(B, ntiles, ca, cb, dt, st);
     else return launch_march_eta_batch<S, MODE, Real, Acc>(B, ntiles, ca, cb, dt, st);
@@ -1427,8 +1478,9 @@ cudaError_t flux_difference_passes(const Params& P, const Real* Q, const double*
                                                        nullptr, 0, 0, 0, st);
 }
 
-// Both directions of every block for one scheme (mode 0: dQ/dt, mode 1: RK stage), xi tiles
-// of shape variant vx, eta tiles of variant ve.
+// Both directions of every block for one scheme, xi tiles of shape variant vx, eta tiles of
+// variant ve.  Mode 0: dQ/dt; 1: RK stage; 2: RK stage that also takes the next stage's line
+// maxima (marching eta only).
 template <int S, typename Real, typename Acc>
 cudaError_t batch_scheme(int mode, const PassTables& xi, int ntx, int vx, const PassTables& eta, int nte, int ve,
                          double ca, double cb, double dt, cudaStream_t st) {
@@ -1436,6 +1488,11 @@ cudaError_t batch_scheme(int mode, const PassTables& xi, int ntx, int vx, const 
   cudaError_t e = launch_sweep_batch<S, 0, MODE_ACC, Real, Acc>(X, ntx, vx, 0, 0, 0, st);
   if (e != cudaSuccess) return e;
   if (mode == 0) return launch_sweep_batch<S, 1, MODE_RHS, Real, Acc>(E, nte, ve, 0, 0, 0, st);
+  if (mode == 2) {
+    if constexpr (std::is_same<Real, Acc>::value)
+      return launch_sweep_batch<S, 1, MODE_STAGE_L, Real, Acc>(E, nte, ve, ca, cb, dt, st);
+    return cudaErrorNotSupported;   // not built for mixed precision
+  }
   return launch_sweep_batch<S, 1, MODE_STAGE, Real, Acc>(E, nte, ve, ca, cb, dt, st);
 }
 
@@ -1469,8 +1526,8 @@ cudaError_t batch_one_direction(int scheme, int dir, const PassTables& t, int nt
     default: return launch_sweep_batch<S71, 1, MODE_ACC, Real, Acc>(B, ntiles, v, 0, 0, 0, st);
   }
 }
-// Batch passes (shape variants vx, ve for the xi and eta tiles): FP64 in batch_fp64.cu;
-// FP32 and mixed in batch_fp32.cu and batch_mixed.cu.
+// Batch passes (shape variants vx, ve for the xi and eta tiles; mode as for batch_scheme):
+// FP64 in batch_fp64.cu; FP32 and mixed in batch_fp32.cu and batch_mixed.cu.
 cudaError_t batch_fp64(int scheme, int mode, const PassTables& xi, int ntx, int vx, const PassTables& eta, int nte,
                        int ve, double ca, double cb, double dt, cudaStream_t st);
 cudaError_t batch_direction_fp64(int scheme, int dir, const PassTables& t, int ntiles, int v, cudaStream_t st);

@@ -23,6 +23,9 @@ BUDGETS = [
     ("batch_fp64.cu", "_ZN3fsp18sweep_batch_kernelILi2ELi0ELi0EddLi2EE", 0),
     ("batch_fp32.cu", "_ZN3fsp18march_batch_kernelILi2ELi0EffE", 0),
     ("batch_fp32.cu", "_ZN3fsp22march_eta_batch_kernelILi2ELi2EffE", 0),
+    # the RK stage that also takes the next stage's line maxima (8 bytes: the column maximum)
+    ("batch_fp32.cu", "_ZN3fsp22march_eta_batch_kernelILi2ELi3EffE", 8),
+    ("batch_fp64.cu", "_ZN3fsp22march_eta_batch_kernelILi2ELi3EddE", 0),
     ("batch_mixed.cu", "_ZN3fsp18march_batch_kernelILi2ELi0EfdE", 16),
     ("batch_mixed.cu", "_ZN3fsp22march_eta_batch_kernelILi2ELi2EfdE", 0),
 ]

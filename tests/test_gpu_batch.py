@@ -246,6 +246,34 @@ def test_batch_marching_segments(F, scheme, shape):
     bt.close()
 
 
+@pytest.mark.parametrize("shape", [(1100, 6), (6, 1100), (45, 70)])
+def test_batch_rk3_marching_line_maxima(F, shape):
+    # with the marching eta pass, stages 1 and 2 take the next stage's line maxima from the
+    # states they write (per row across the CTAs of a row, per column across the segments of
+    # a column); two RK3 steps against the oracle, eagerly and from the captured graph
+    ni, nj = shape
+    x, y, per = I.periodic_square(ni, 10.0, 0.2, seed=6, nj=nj)
+    q = I.random_state(x.shape, seed=10)
+    cfgd = dict(scheme=2, period=per)
+    M = O.metrics(cfgd, x, y)
+    dt = 1e-3
+    q2 = O.rk3(cfgd, M, q, dt, 2)
+    for graph in (False, True):
+        bt = F.Batch(F.Config.from_dict(cfgd), [dict(x=x, y=y, bc=(0, 0, 0, 0), period=per)], [q])
+        bt.M[0].copy_(torch.as_tensor(M))
+        bt.set_tile_shape(0, 3)
+        bt.set_tile_shape(1, 3)
+        if graph:
+            bt.capture_graph(dt)          # one eager step, then the captured step
+        else:
+            bt.rk3_step(dt)
+        bt.rk3_step(dt)
+        torch.cuda.synchronize()
+        got = bt.Q[0].cpu().numpy()
+        assert np.abs(got - q2).max() / np.abs(q2).max() < TOL, graph
+        bt.close()
+
+
 def test_batch_tune_table(F, tmp_path):
     blocks, states, free = _small_cylinder()
     bt = F.Batch(F.Config.from_dict(_cfgd(free, 2)), blocks, states)
