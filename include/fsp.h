@@ -65,7 +65,7 @@ typedef enum {
  * one-midpoint scheme of the Appendix (scheme (1) with alpha = 1: Table A1 candidates, the
  * fourth-order mapping, an eighth-order central operator and eight-point midpoint metrics;
  * its smoothness indicators are those of Eq. 3.22's definition applied to the cubics of
- * Table A1).  The adjoint entry points do not cover FSP_WENOIU7_1MP. */
+ * Table A1).  Every scheme has the adjoint entry points. */
 enum { FSP_WENOIU3_1MP = 0, FSP_WENOIU3_2MP = 1, FSP_WENOIU5_1MP = 2, FSP_WENOIU5_2MP = 3, FSP_WENOIU7_1MP = 4 };
 /* Arithmetic of the right-hand side.  Metrics are FP64 in every mode.
  * FSP_FP64        everything in double.
@@ -247,7 +247,8 @@ fsp_status fsp_check_state(const fsp_config* cfg, const fsp_block* blk, const vo
  * lowest index attaining it.  Adjoint outputs are accumulated (+=) into the caller's
  * buffers, which the caller zeroes.  The workspace must hold fsp_vjp_workspace_size bytes.
  * Every adjoint entry point, the size queries included, returns FSP_ERR_UNSUPPORTED for a
- * precision other than FSP_FP64 or for FSP_WENOIU7_1MP.
+ * precision other than FSP_FP64 and for the options beyond the printed schemes (weights,
+ * mid_split, scheme_alpha other than their defaults).
  */
 fsp_status fsp_vjp_workspace_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes);
 
@@ -283,8 +284,8 @@ fsp_status fsp_rk3_step_vjp_tape(const fsp_config* cfg, const fsp_block* blk, co
                                  double* metrics_bar, void* ws, size_t ws_bytes, void* stream);
 
 /* x_bar, y_bar += (d metrics / d(x, y))^T metrics_bar: the reverse of fsp_metrics through
- * the ghost-coordinate rule (periodic offsets are constants).  FSP_ERR_UNSUPPORTED for
- * FSP_WENOIU7_1MP. */
+ * the ghost-coordinate rule (periodic offsets are constants), with the scheme's own central
+ * operator (scheme_alpha included). */
 fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const double* x, const double* y,
                            const double* metrics_bar, double* x_bar, double* y_bar, void* stream);
 

@@ -152,9 +152,9 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
     double Ab = 0.0;
     // node terms of h: n_k (E^ +- A Q)/2 at nodes p+k and p+1-k
 #pragma unroll
-    for (int kk = -2; kk <= 2; ++kk) {
-      if (Sc::n(kk + 2) == 0.0) continue;
-      const double cn = 0.5 * Sc::n(kk + 2);
+    for (int kk = -3; kk <= 3; ++kk) {
+      if (Sc::hn(kk) == 0.0) continue;
+      const double cn = 0.5 * Sc::hn(kk);
       const int a = SI(l, c0 + kk), b = SI(l, c0 + 1 - kk);
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -171,14 +171,23 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
     const double mbx = 0.5 * (sM[o0] + sM[o1]), mby = 0.5 * (sM[NN + o0] + sM[NN + o1]);
     const double rn = rsqrt(mbx * mbx + mby * mby);
     const double nx = mbx * rn, ny = mby * rn;
-    double vx[6], vy[6];
+    // midpoint interpolation over nodes p-2..p+3, or p-3..p+4 for r = 4
+    constexpr int NI = Sc::r == 4 ? 8 : 6, IOFF = Sc::r == 4 ? 3 : 2;
+    double vx[NI], vy[NI];
 #pragma unroll
-    for (int kk = 0; kk < 6; ++kk) {
-      const int o = SI(l, c0 - 2 + kk);
+    for (int kk = 0; kk < NI; ++kk) {
+      const int o = SI(l, c0 - IOFF + kk);
       vx[kk] = sM[o];
       vy[kk] = sM[NN + o];
     }
-    const double mmx = mid_interp(P.interp, Sc::r == 3, vx), mmy = mid_interp(P.interp, Sc::r == 3, vy);
+    double mmx, mmy;
+    if constexpr (Sc::r == 4) {
+      mmx = mid_interp8(P.interp, vx);
+      mmy = mid_interp8(P.interp, vy);
+    } else {
+      mmx = mid_interp(P.interp, Sc::r == 3, vx);
+      mmy = mid_interp(P.interp, Sc::r == 3, vy);
+    }
     double mmxb = 0.0, mmyb = 0.0, nxb = 0.0, nyb = 0.0;
     // each side: forward once (WENO internals to the tape), then its reverse
 #pragma unroll 1
@@ -188,10 +197,12 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
       w.u = sP[0 * NN + oc]; w.v = sP[1 * NN + oc]; w.c = sP[2 * NN + oc]; w.cinv = sP[3 * NN + oc];
       w.H = sP[4 * NN + oc]; w.b1 = sP[5 * NN + oc]; w.h2 = sP[6 * NN + oc];
       const double qc[4] = {sQ[oc], sQ[NN + oc], sQ[2 * NN + oc], sQ[3 * NN + oc]};
-      double dq[4][4];
+      // stencil offsets -H..-1, +1..+H (H = 2, or 3 for r = 4); the "-" side mirrored
+      constexpr int H = Sc::r == 4 ? 3 : 2, NA = 2 * H;
+      double dq[NA][4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int m = a < 2 ? a - 2 : a - 1;
+      for (int a = 0; a < NA; ++a) {
+        const int m = a < H ? a - H : a - H + 1;
         if (Sc::r == 2 && m == 2) { dq[a][0] = dq[a][1] = dq[a][2] = dq[a][3] = 0.0; continue; }
         const int o = SI(l, side == 0 ? c0 + m : c0 + 1 - m);
 #pragma unroll
@@ -202,12 +213,11 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
       double Wm[4], dQm[4], Qs[4];
 #pragma unroll
       for (int kc = 0; kc < 4; ++kc) {
-        double u[5];
-        u[0] = E.project(kc, dq[0][0], dq[0][1], dq[0][2], dq[0][3]);
-        u[1] = E.project(kc, dq[1][0], dq[1][1], dq[1][2], dq[1][3]);
-        u[2] = 0.0;
-        u[3] = E.project(kc, dq[2][0], dq[2][1], dq[2][2], dq[2][3]);
-        u[4] = Sc::r == 3 ? E.project(kc, dq[3][0], dq[3][1], dq[3][2], dq[3][3]) : 0.0;
+        double u[2 * H + 1];
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+          u[a < H ? a : a + 1] = (Sc::r == 2 && a == 3) ? 0.0 : E.project(kc, dq[a][0], dq[a][1], dq[a][2], dq[a][3]);
+        u[H] = 0.0;
         Wm[kc] = weno_fwd_tape<Sc::r>(u, eps, P.ppm, P.linw, tape[kc]);
       }
       E.recon(Wm, dQm);
@@ -225,13 +235,13 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
       }
       flux_bwd(Qs, mmx, mmy, gm1, eb, Qsb, mmxb, mmyb);
       // the characteristic interpolation, reverse
-      double qcb[4] = {0, 0, 0, 0}, dqb[4][4] = {};
+      double qcb[4] = {0, 0, 0, 0}, dqb[NA][4] = {};
       PrimBar pb{0, 0, 0, 0, 0, 0, 0};
       side_bwd_tape<Sc::r>(E, w, nx, ny, dq, Wm, P.ppm, P.linw, tape, Qsb, qcb, dqb, pb, nxb, nyb);
       prim_bwd(qc, gamma, pb, qcb);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int m = a < 2 ? a - 2 : a - 1;
+      for (int a = 0; a < NA; ++a) {
+        const int m = a < H ? a - H : a - H + 1;
         if (Sc::r == 2 && m == 2) continue;
         const int o = SI(l, side == 0 ? c0 + m : c0 + 1 - m);
 #pragma unroll
@@ -245,14 +255,20 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
     }
     // midpoint metrics, reverse
     {
-      double cw[6];
-      if (P.interp == 1) { cw[0] = cw[1] = cw[4] = cw[5] = 0.0; cw[2] = cw[3] = 0.5; }
-      else if (Sc::r == 3) { cw[0] = cw[5] = 3.0 / 256; cw[1] = cw[4] = -25.0 / 256; cw[2] = cw[3] = 150.0 / 256; }
-      else { cw[0] = cw[5] = 0.0; cw[1] = cw[4] = -1.0 / 16; cw[2] = cw[3] = 9.0 / 16; }
+      double cw[NI];
 #pragma unroll
-      for (int kk = 0; kk < 6; ++kk) {
+      for (int kk = 0; kk < NI; ++kk) cw[kk] = 0.0;
+      if (P.interp == 1) { cw[IOFF] = cw[IOFF + 1] = 0.5; }
+      else if (Sc::r == 4) {
+        cw[0] = cw[7] = -5.0 / 2048; cw[1] = cw[6] = 49.0 / 2048; cw[2] = cw[5] = -245.0 / 2048;
+        cw[3] = cw[4] = 1225.0 / 2048;
+      }
+      else if (Sc::r == 3) { cw[0] = cw[5] = 3.0 / 256; cw[1] = cw[4] = -25.0 / 256; cw[2] = cw[3] = 150.0 / 256; }
+      else { cw[1] = cw[4] = -1.0 / 16; cw[2] = cw[3] = 9.0 / 16; }
+#pragma unroll
+      for (int kk = 0; kk < NI; ++kk) {
         if (cw[kk] == 0.0) continue;
-        const int o = SI(l, c0 - 2 + kk);
+        const int o = SI(l, c0 - IOFF + kk);
         atomicAdd(sMb + o, cw[kk] * mmxb);
         atomicAdd(sMb + NN + o, cw[kk] * mmyb);
       }
@@ -386,16 +402,20 @@ static cudaError_t vjp_scheme(const Params& P, const double* Q, const double* lx
 // the transposed central operator: D phi_j = sum_k w[k+4] phi_{j+k}, k = -4..4
 static void central_weights(int scheme, int interp, double alpha, double w[9]) {
   const Central c = central_of(scheme, alpha);
-  double cl[6] = {0, 0, 0, 0, 0, 0};  // I(m) = sum_l cl[l+2] phi_{m+l}, l = -2..3
-  if (interp == 1) { cl[2] = cl[3] = 0.5; }
-  else if (scheme >= S51) { cl[0] = cl[5] = 3.0 / 256; cl[1] = cl[4] = -25.0 / 256; cl[2] = cl[3] = 150.0 / 256; }
-  else { cl[1] = cl[4] = -1.0 / 16; cl[2] = cl[3] = 9.0 / 16; }
-  auto C = [&](int l) { return (l >= -2 && l <= 3) ? cl[l + 2] : 0.0; };
-  const double a[4] = {0.0, c.a1, c.a2, c.a3};
+  double cl[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // I(m) = sum_l cl[l+3] phi_{m+l}, l = -3..4
+  if (interp == 1) { cl[3] = cl[4] = 0.5; }
+  else if (scheme == S71) {
+    cl[0] = cl[7] = -5.0 / 2048; cl[1] = cl[6] = 49.0 / 2048; cl[2] = cl[5] = -245.0 / 2048;
+    cl[3] = cl[4] = 1225.0 / 2048;
+  }
+  else if (scheme >= S51) { cl[1] = cl[6] = 3.0 / 256; cl[2] = cl[5] = -25.0 / 256; cl[3] = cl[4] = 150.0 / 256; }
+  else { cl[2] = cl[5] = -1.0 / 16; cl[3] = cl[4] = 9.0 / 16; }
+  auto C = [&](int l) { return (l >= -3 && l <= 4) ? cl[l + 3] : 0.0; };
+  const double a[5] = {0.0, c.a1, c.a2, c.a3, c.a4};
   for (int k = -4; k <= 4; ++k) {
     double v = 0.0;
-    if (k > 0 && k <= 3) v += a[k];
-    if (k < 0 && k >= -3) v -= a[-k];
+    if (k > 0) v += a[k];
+    if (k < 0) v -= a[-k];
     v += c.b12 * (C(k) - C(k + 1)) + c.b32 * (C(k - 1) - C(k + 2));
     w[k + 4] = v;
   }
@@ -560,7 +580,7 @@ Params params_of(const fsp_config& c, const fsp_block& b, const double* metrics)
 extern "C" fsp_status fsp_vjp_workspace_size(const fsp_config* cfg, const fsp_block* blk, size_t* bytes) {
   size_t fwd = 0;
   if (fsp_status s = fsp_workspace_size(cfg, blk, &fwd)) return s;
-  if (cfg->precision != FSP_FP64 || cfg->scheme == S71 || !adjoint_options(*cfg)) return FSP_ERR_UNSUPPORTED;
+  if (cfg->precision != FSP_FP64 || !adjoint_options(*cfg)) return FSP_ERR_UNSUPPORTED;
   if (!bytes) return FSP_ERR_INVALID_ARG;
   *bytes = vjp_ws(*cfg, *blk, fwd).total;
   return FSP_OK;
@@ -585,7 +605,8 @@ static fsp_status vjp_core(const fsp_config& c, const fsp_block& b, const double
     case S31: e = vjp_scheme<S31>(P, Q, lam, lam + b.nj, gbar, Qbar, Mbar, abar, st); break;
     case S32: e = vjp_scheme<S32>(P, Q, lam, lam + b.nj, gbar, Qbar, Mbar, abar, st); break;
     case S51: e = vjp_scheme<S51>(P, Q, lam, lam + b.nj, gbar, Qbar, Mbar, abar, st); break;
-    default:  e = vjp_scheme<S52>(P, Q, lam, lam + b.nj, gbar, Qbar, Mbar, abar, st); break;
+    case S52: e = vjp_scheme<S52>(P, Q, lam, lam + b.nj, gbar, Qbar, Mbar, abar, st); break;
+    default:  e = vjp_scheme<S71>(P, Q, lam, lam + b.nj, gbar, Qbar, Mbar, abar, st); break;
   }
   TRY(e);
   dim3 blk(32, 8), grd((b.ni + 31) / 32, (b.nj + 7) / 8);
@@ -671,7 +692,7 @@ static fsp_status reverse_stages(const fsp_config& c, const fsp_block& b, const 
 // interpolation options included).
 static fsp_status check_vjp(const fsp_config* cfg, const fsp_block* blk, size_t* fwd) {
   if (fsp_status s = fsp_workspace_size(cfg, blk, fwd)) return s;
-  if (cfg->precision != FSP_FP64 || cfg->scheme == S71 || !adjoint_options(*cfg)) return FSP_ERR_UNSUPPORTED;
+  if (cfg->precision != FSP_FP64 || !adjoint_options(*cfg)) return FSP_ERR_UNSUPPORTED;
   return FSP_OK;
 }
 
@@ -766,7 +787,6 @@ fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const do
                            const double* metrics_bar, double* x_bar, double* y_bar, void* stream) {
   size_t fwd = 0;
   if (fsp_status s = fsp_workspace_size(cfg, blk, &fwd)) return s;
-  if (cfg->scheme == S71) return FSP_ERR_UNSUPPORTED;
   if (!dptr(x) || !dptr(y) || !dptr(metrics_bar) || !dptr(x_bar) || !dptr(y_bar)) return FSP_ERR_INVALID_ARG;
   W9 w;
   central_weights(cfg->scheme, cfg->interp, scheme_alpha_of(*cfg), w.w);

@@ -8,10 +8,12 @@
 namespace fsp {
 
 // ---- WENO with a tape: the forward pass keeps what the reverse pass needs -------------
-// One component's tape, WT slots in shared memory, slot i at p[i * stride]: the stencil
-// differences u (4: offsets -2, -1, +1, +2), b = eps + IS_k (3), the raw weights (3),
+// One component's tape, WT slots in shared memory, slot i at p[i * stride].  r = 2, 3: the
+// stencil differences u (4: offsets -2, -1, +1, +2), b = eps + IS_k (3), the raw weights (3),
 // 1 / sum of the unnormalised weights, 1 / sum of the mapped weights, the interpolant.
-constexpr int WT = 13;
+// r = 4: u (6: offsets -3..-1, +1..+3), b (4), the weights (4), 1 / sum of the mapped
+// weights, the interpolant.
+constexpr int WT = 16;
 
 struct Tape {
   double* p;
@@ -23,6 +25,52 @@ struct Tape {
 // num * (1/den) so that the reverse pass reuses the reciprocal.
 template <int R>
 __device__ __forceinline__ double weno_fwd_tape(const double* u, double eps, int ppm, int linw, Tape t) {
+  if constexpr (R == 4) {
+    // u[m + 3] = w_{j+m} - w_j, m = -3..3 (u[3] is not read): Table A1 candidates, the r = 4
+    // indicators, C_k / b_k^2 weights and the fourth-order mapping, as weno_delta<4>
+    t[0] = u[0]; t[1] = u[1]; t[2] = u[2]; t[3] = u[4]; t[4] = u[5]; t[5] = u[6];
+    const double p[4] = {-5.0 / 16 * u[0] + 21.0 / 16 * u[1] - 35.0 / 16 * u[2],
+                         1.0 / 16 * u[1] - 5.0 / 16 * u[2] + 5.0 / 16 * u[4],
+                         -1.0 / 16 * u[2] + 9.0 / 16 * u[4] - 1.0 / 16 * u[5],
+                         15.0 / 16 * u[4] - 5.0 / 16 * u[5] + 1.0 / 16 * u[6]};
+    const double C[4] = {1.0 / 64, 21.0 / 64, 35.0 / 64, 7.0 / 64};
+    if (linw) return C[0] * p[0] + C[1] * p[1] + C[2] * p[2] + C[3] * p[3];
+    const double D[6] = {u[1] - u[0], u[2] - u[1], -u[2], u[4], u[5] - u[4], u[6] - u[5]};
+    double b[4], a[4], sa = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      b[k] = is_b4(k, D[k], D[k + 1], D[k + 2], eps);
+      a[k] = C[k] * rcp_nr(b[k] * b[k]);
+      sa += a[k];
+    }
+    const double isa = rcp_nr(sa);
+    double w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      w[k] = a[k] * isa;
+      t[6 + k] = b[k];
+      t[10 + k] = w[k];
+    }
+    double out;
+    if (ppm) {
+      double num = 0.0, den = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double q = w[k] - C[k], q2 = q * q;
+        const double K = nonpos(q) ? 1.0 / (C[k] * C[k] * C[k]) : 1.0 / ((C[k] - 1.0) * (C[k] - 1.0) * (C[k] - 1.0));
+        const double g = C[k] - q2 * q2 * K;
+        num += g * p[k];
+        den += g;
+      }
+      const double rden = rcp_nr(den);
+      out = num * rden;
+      t[14] = rden;
+    } else {
+      out = w[0] * p[0] + w[1] * p[1] + w[2] * p[2] + w[3] * p[3];
+    }
+    t[15] = out;
+    return out;
+  } else {
   t[0] = u[0]; t[1] = u[1]; t[2] = u[3]; t[3] = u[4];
   if constexpr (R == 3) {
     const double p0 = 0.375 * u[0] - 1.25 * u[1];
@@ -89,12 +137,65 @@ __device__ __forceinline__ double weno_fwd_tape(const double* u, double eps, int
     t[12] = out;
     return out;
   }
+  }
 }
 
-// Reverse of weno_fwd_tape: adds d(out)/du * obar to ub[0], ub[1], ub[3], ub[4] (the
-// layout of weno_delta_bwd), reading the forward values from the tape.
+// Reverse of weno_fwd_tape: adds d(out)/du * obar to ub[0], ub[1], ub[3], ub[4] (r = 2, 3;
+// the layout of weno_delta_bwd) or ub[0..6] except ub[3] (r = 4), reading the forward values
+// from the tape.
 template <int R>
 __device__ __forceinline__ void weno_bwd_tape(Tape t, int ppm, int linw, double obar, double* ub) {
+  if constexpr (R == 4) {
+    const double u[7] = {t[0], t[1], t[2], 0.0, t[3], t[4], t[5]};
+    const double C[4] = {1.0 / 64, 21.0 / 64, 35.0 / 64, 7.0 / 64};
+    double pb[4], Db[6] = {0, 0, 0, 0, 0, 0};
+    if (linw) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) pb[k] = obar * C[k];
+    } else {
+      const double p[4] = {-5.0 / 16 * u[0] + 21.0 / 16 * u[1] - 35.0 / 16 * u[2],
+                           1.0 / 16 * u[1] - 5.0 / 16 * u[2] + 5.0 / 16 * u[4],
+                           -1.0 / 16 * u[2] + 9.0 / 16 * u[4] - 1.0 / 16 * u[5],
+                           15.0 / 16 * u[4] - 5.0 / 16 * u[5] + 1.0 / 16 * u[6]};
+      const double b[4] = {t[6], t[7], t[8], t[9]}, w[4] = {t[10], t[11], t[12], t[13]};
+      double wb[4];
+      if (ppm) {
+        const double rden = t[14];
+        const double numb = obar * rden, denb = -obar * t[15] * rden;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double q = w[k] - C[k];
+          const double K = nonpos(q) ? 1.0 / (C[k] * C[k] * C[k]) : 1.0 / ((C[k] - 1.0) * (C[k] - 1.0) * (C[k] - 1.0));
+          const double g = C[k] - q * q * q * q * K;
+          pb[k] = numb * g;
+          wb[k] = (numb * p[k] + denb) * (-4.0 * q * q * q * K);   // dg/dw = -4 (w - C)^3 K
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { wb[k] = obar * p[k]; pb[k] = obar * w[k]; }
+      }
+      // w_k = a_k / sum a, a_k = C_k b_k^-2: d w_k / d b_j = -2 w_j (delta_kj - w_k) / b_j
+      const double dotw = wb[0] * w[0] + wb[1] * w[1] + wb[2] * w[2] + wb[3] * w[3];
+      const double D[6] = {u[1] - u[0], u[2] - u[1], -u[2], u[4], u[5] - u[4], u[6] - u[5]};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double bb = -2.0 * w[k] * (wb[k] - dotw) * rcp_nr(b[k]);
+        // b_k = eps + c0 d1^2 + c1 d2^2 + c2 d3^2 + c3 d1 d2 + c4 d1 d3 + c5 d2 d3
+        const double d1 = D[k], d2 = D[k + 1], d3 = D[k + 2];
+        Db[k] += bb * (2.0 * is4c(k, 0) * d1 + is4c(k, 3) * d2 + is4c(k, 4) * d3);
+        Db[k + 1] += bb * (is4c(k, 3) * d1 + 2.0 * is4c(k, 1) * d2 + is4c(k, 5) * d3);
+        Db[k + 2] += bb * (is4c(k, 4) * d1 + is4c(k, 5) * d2 + 2.0 * is4c(k, 2) * d3);
+      }
+    }
+    // candidates and the consecutive differences D, back to u
+    ub[0] += -5.0 / 16 * pb[0] - Db[0];
+    ub[1] += 21.0 / 16 * pb[0] + 1.0 / 16 * pb[1] + Db[0] - Db[1];
+    ub[2] += -35.0 / 16 * pb[0] - 5.0 / 16 * pb[1] - 1.0 / 16 * pb[2] + Db[1] - Db[2];
+    ub[4] += 5.0 / 16 * pb[1] + 9.0 / 16 * pb[2] + 15.0 / 16 * pb[3] + Db[3] - Db[4];
+    ub[5] += -1.0 / 16 * pb[2] - 5.0 / 16 * pb[3] + Db[4] - Db[5];
+    ub[6] += 1.0 / 16 * pb[3] + Db[5];
+    return;
+  } else {
   const double u0 = t[0], u1 = t[1], u3 = t[2], u4 = t[3];
   if constexpr (R == 3) {
     const double C[3] = {1.0 / 16, 10.0 / 16, 5.0 / 16};
@@ -196,6 +297,7 @@ __device__ __forceinline__ void weno_bwd_tape(Tape t, int ppm, int linw, double 
     ub[0] += -d1b;
     ub[1] += -0.5 * pb[0] + d1b - d2b;
     ub[3] += 0.5 * pb[1] + d3b;
+  }
   }
 }
 
@@ -305,11 +407,12 @@ __device__ __forceinline__ void spectral_bwd(const double q[4], double mx, doubl
 // and the unit direction (nx, ny); E, W and the WENO tapes (one per characteristic
 // component) come from that forward pass.  Given Qsb (adjoint of Q^s), adds the adjoints
 // of the centre state (qcb), of the stencil differences (dqb[a][4], a = offsets -2, -1,
-// +1, +2), of the primitives (pbar) and of the direction (nxb, nyb).
+// +1, +2, or -3..-1, +1..+3 for r = 4), of the primitives (pbar) and of the direction (nxb,
+// nyb).
 template <int R>
 __device__ __forceinline__ void side_bwd_tape(const Eig<double>& E, const Prim<double>& w, double nx, double ny,
-                                              const double dq[4][4], const double W[4], int ppm, int linw,
-                                              const Tape* tape, const double* Qsb, double* qcb, double dqb[4][4],
+                                              const double (*dq)[4], const double W[4], int ppm, int linw,
+                                              const Tape* tape, const double* Qsb, double* qcb, double (*dqb)[4],
                                               PrimBar& pbar, double& nxb, double& nyb) {
   // Q^s = Q_c + dQ
 #pragma unroll
@@ -339,11 +442,14 @@ __device__ __forceinline__ void side_bwd_tape(const Eig<double>& E, const Prim<d
   double Lb[4][4] = {};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    double ubk[5] = {0, 0, 0, 0, 0};
+    double ubk[7] = {0, 0, 0, 0, 0, 0, 0};
     weno_bwd_tape<R>(tape[k], ppm, linw, Wb[k], ubk);
-    const int mlist[4] = {0, 1, 3, 4};
+    // stencil offset index aa -> position in ubk
+    constexpr int NA = R == 4 ? 6 : 4;
+    constexpr int m4[6] = {0, 1, 2, 4, 5, 6}, m3[6] = {0, 1, 3, 4, 0, 0};
+    const int* mlist = R == 4 ? m4 : m3;
 #pragma unroll
-    for (int aa = 0; aa < 4; ++aa) {
+    for (int aa = 0; aa < NA; ++aa) {
       if (R == 2 && aa == 3) continue;
       const double g = ubk[mlist[aa]];
 #pragma unroll

@@ -86,11 +86,15 @@ def test_argument_validation_on_the_host(so):
     c32 = fsp.Config(scheme=2, bc=(0, 0, 0, 0), precision=1)
     assert fsp.lib().fsp_vjp_workspace_size(ctypes.byref(c32._c()), ctypes.byref(b), ctypes.byref(n)) == 2
     assert fsp.lib().fsp_rk3_tape_size(ctypes.byref(c32._c()), ctypes.byref(b), ctypes.byref(n)) == 2
-    # ... and does not cover WENOIU7-1MP, whose forward right-hand side is accepted
+    # ... covers WENOIU7-1MP, and refuses the options beyond the printed schemes
     c7 = fsp.Config(scheme=4, bc=(0, 0, 0, 0))
     assert _ws_code(fsp, c7, 16, 16) == 0
-    assert fsp.lib().fsp_vjp_workspace_size(ctypes.byref(c7._c()), ctypes.byref(b), ctypes.byref(n)) == 2
-    assert fsp.lib().fsp_rk3_tape_size(ctypes.byref(c7._c()), ctypes.byref(b), ctypes.byref(n)) == 2
+    assert fsp.lib().fsp_vjp_workspace_size(ctypes.byref(c7._c()), ctypes.byref(b), ctypes.byref(n)) == 0
+    assert fsp.lib().fsp_rk3_tape_size(ctypes.byref(c7._c()), ctypes.byref(b), ctypes.byref(n)) == 0
+    for opt in (dict(weights=1), dict(mid_split=2), dict(scheme_alpha=1.2)):
+        co = fsp.Config(**dict(dict(scheme=2, bc=(0, 0, 0, 0)), **opt))
+        assert _ws_code(fsp, co, 16, 16) == 0
+        assert fsp.lib().fsp_vjp_workspace_size(ctypes.byref(co._c()), ctypes.byref(b), ctypes.byref(n)) == 2
     assert _ws_code(fsp, fsp.Config(scheme=5, bc=(0, 0, 0, 0)), 16, 16) == 1
     # the state check refuses a host pointer for its result
     one = (ctypes.c_longlong * 1)()

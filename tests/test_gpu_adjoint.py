@@ -60,7 +60,7 @@ def _dot_check(F, cfgd, x, y, q, seed=0):
     assert abs(float((g * dRm).sum()) - float((_host(Mb) * dM).sum())) < TOL * abs(float((g * dRm).sum())) + 1e-12
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_rhs_vjp_periodic(F, scheme):
     x, y, per, q = _periodic_case()
     _dot_check(F, dict(scheme=scheme, period=per), x, y, q, seed=scheme)
@@ -70,7 +70,7 @@ def test_rhs_vjp_periodic(F, scheme):
 def test_rhs_vjp_boundaries(F, bc):
     x, y, per, q = _wall_case()
     st = np.tile(I.conservative(1.0, 0.3, -0.2, 1.0 / GAMMA), (4, 1))
-    for scheme in (0, 3):
+    for scheme in (0, 3, 4):
         _dot_check(F, dict(scheme=scheme, bc=bc, bc_state=st), x, y, q, seed=7)
 
 
@@ -80,7 +80,7 @@ def test_rhs_vjp_options(F):
         _dot_check(F, dict(scheme=2, period=per, **opt), x, y, q, seed=3)
 
 
-@pytest.mark.parametrize("scheme,bc", [(2, (0, 0, 0, 0)), (1, (1, 1, 3, 3))])
+@pytest.mark.parametrize("scheme,bc", [(2, (0, 0, 0, 0)), (1, (1, 1, 3, 3)), (4, (1, 1, 3, 3))])
 def test_metrics_vjp(F, scheme, bc):
     if bc[0] == 0:
         x, y, per = I.periodic_square(20, 8.0, 0.2, seed=5, nj=18)
@@ -98,7 +98,7 @@ def test_metrics_vjp(F, scheme, bc):
     assert abs(lhs - rhs) < 1e-11 * np.abs(Mb).sum() * np.abs(dM).max()
 
 
-@pytest.mark.parametrize("scheme", [2, 3])
+@pytest.mark.parametrize("scheme", [2, 3, 4])
 def test_rk3_step_vjp(F, scheme):
     x, y, per, q = _periodic_case(20, 16)
     cfgd = dict(scheme=scheme, period=per)

@@ -9,7 +9,8 @@ FP64, evaluated in different orders; the adjoint of a right-hand side sums a few
 products per entry, so its rounding is a few hundred ulps of the largest contribution, and
 the bar leaves an order of magnitude above what is measured.  Cases: a periodic grid whose
 xi and eta tiles end ragged (140 x 40), every boundary kind, the smooth vortex with the
-unmapped-weight epsilon, one RK3 step, and the metrics."""
+unmapped-weight epsilon, one RK3 step, and the metrics; WENOIU7-1MP (the Appendix's r = 4
+interpolation) in each."""
 import numpy as np
 import pytest
 
@@ -52,7 +53,7 @@ def _rhs_case(F, cfgd, x, y, q, seed):
     return _rel(_host(Qb), Qb_o), _rel(_host(Mb), Mb_o)
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_rhs_vjp_equals_oracle_ragged_tiles(F, scheme):
     x, y, per = I.periodic_square(140, 8.0, 0.2, seed=21, nj=40)
     q = I.random_state(x.shape, seed=31)
@@ -66,7 +67,7 @@ def test_rhs_vjp_equals_oracle_boundaries(F, bc):
     q = I.random_state(x.shape, seed=32)
     st = np.array([I.conservative(1.0, 0.3, -0.2, 1.0 / GAMMA), I.conservative(0.9, -0.4, 0.1, 0.8),
                    I.conservative(1.1, 0.2, 0.5, 0.7), I.conservative(1.0, 0.0, -0.3, 0.75)])
-    for scheme in (0, 2, 3):
+    for scheme in (0, 2, 3, 4):
         eq, em = _rhs_case(F, dict(scheme=scheme, bc=bc, bc_state=st), x, y, q, seed=7)
         assert eq <= TOL and em <= TOL, (scheme, eq, em)
 
@@ -79,10 +80,11 @@ def test_rhs_vjp_equals_oracle_smooth_vortex(F):
     assert eq <= TOL and em <= TOL, (eq, em)
 
 
-def test_rk3_step_vjp_equals_oracle(F):
+@pytest.mark.parametrize("scheme", [2, 4])
+def test_rk3_step_vjp_equals_oracle(F, scheme):
     x, y, per = I.periodic_square(40, 8.0, 0.2, seed=21, nj=24)
     q = I.random_state(x.shape, seed=33)
-    cfgd = dict(scheme=2, period=per)
+    cfgd = dict(scheme=scheme, period=per)
     M = O.metrics(cfgd, x, y)
     g = np.random.default_rng(2).standard_normal(q.shape)
     dt = 0.02
@@ -92,7 +94,7 @@ def test_rk3_step_vjp_equals_oracle(F):
     assert _rel(_host(Qb), Qb_o) <= TOL and _rel(_host(Mb), Mb_o) <= TOL
 
 
-@pytest.mark.parametrize("scheme,bc", [(2, None), (0, (1, 1, 1, 1)), (3, (3, 2, 4, 1))])
+@pytest.mark.parametrize("scheme,bc", [(2, None), (0, (1, 1, 1, 1)), (3, (3, 2, 4, 1)), (4, None), (4, (1, 1, 1, 1))])
 def test_metrics_vjp_equals_oracle(F, scheme, bc):
     if bc is None:
         x, y, per = I.periodic_square(36, 8.0, 0.2, seed=21, nj=28)

@@ -27,10 +27,12 @@ def _grid(n=14, seed=21):
     return I.periodic_square(n, 8.0, 0.2, seed=seed)
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("smooth", [False, True])
 def test_rhs_vjp_is_the_transposed_tangent(scheme, smooth):
-    x, y, per = _grid()
+    # WENOIU7's 7-node stencils see the 14-node vortex as barely resolved, where the weights'
+    # derivatives (b^-3 with eps = 1e-6) amplify rounding to 2e-11: its case takes 20 nodes
+    x, y, per = _grid(20 if scheme == 4 else 14)
     if smooth:
         cfg = dict(scheme=scheme, period=per, eps=1e-6)
         q = I.isentropic_vortex(x, y, (4.0, 4.0), strength=5.0, free=(1.0, 1.0, 1.0, 1.0), period=(8.0, 8.0))
