@@ -1598,3 +1598,517 @@ int orc_mb_rk3(const int* ip, const double* dp, int nb, const int* dims, const i
   return 0;
 }
 }  // extern "C"
+
+// ==================================================================================
+// Three dimensions (Sections 2.1-2.2): Q = (rho, rho u, rho v, rho w, e), the symmetric
+// conservative metrics of Eq. (2.4), the Jacobian of Eq. (2.5), and one sweep per grid
+// direction xi, eta, zeta, each built exactly like the two-dimensional sweep.
+//
+// Conventions: nodes (i, j, k), i fastest; state 5 planes [5][nk][nj][ni]; metrics 10
+// planes on the grid extended by G = 4 ghost layers on every side: plane 3 d + c holds
+// the component c (x, y, z) of the metric of direction d (xi, eta, zeta), i.e. xi_x^,
+// xi_y^, xi_z^, eta_x^, ..., zeta_z^, and plane 9 holds J^-1; plane p, node (i, j, k) at
+// M[p*P + ((k+4)*(nj+8) + (j+4))*(ni+8) + (i+4)], P = (ni+8)(nj+8)(nk+8).  Faces 0..5 =
+// i-min, i-max, j-min, j-max, k-min, k-max; codes PERIODIC = 0, TRANSMISSIVE = 1.
+// ==================================================================================
+namespace orc {
+
+template <class T>
+struct Par3 {
+  int scheme = S51, interp = 0, ppm = 1, linw = 0;
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  T gamma = T(1.4), alpha = cst<T>(1.1L), eps = cst<T>(1e-40L);
+  SchemeTab tab;
+  int n[3] = {0, 0, 0};     // ni, nj, nk
+  T per[3][3];              // per[a] = (dx, dy, dz) added per wrap in direction a
+};
+
+// ip = {scheme, interp, ppm, linear_weights, bc[6]}; dp = {gamma, lf_alpha, eps, period[3][3]}
+template <class T>
+static void unpack3(const int* ip, const double* dp, int ni, int nj, int nk, Par3<T>& P) {
+  P.scheme = ip[0]; P.interp = ip[1]; P.ppm = ip[2]; P.linw = ip[3];
+  for (int f = 0; f < 6; ++f) P.bc[f] = ip[4 + f];
+  P.gamma = T(dp[0]); P.alpha = T(dp[1]); P.eps = T(dp[2]);
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) P.per[a][c] = T(dp[3 + 3 * a + c]);
+  P.tab = TAB[P.scheme];
+  P.n[0] = ni; P.n[1] = nj; P.n[2] = nk;
+}
+
+// A grid extended by e layers: index of node (i, j, k).
+struct Ext3 {
+  int e, n[3];
+  size_t size() const { return (size_t)(n[0] + 2 * e) * (n[1] + 2 * e) * (n[2] + 2 * e); }
+  size_t at(int i, int j, int k) const {
+    return ((size_t)(k + e) * (n[1] + 2 * e) + (j + e)) * (n[0] + 2 * e) + (i + e);
+  }
+};
+
+// Coordinate c of node (i, j, k) of the extended grid.  Reading (as in two dimensions): a
+// periodic direction wraps and adds its period vector per wrap; any other direction extends
+// the grid by odd reflection about its boundary node, x_{-m} = 2 x_0 - x_m.
+template <class T>
+static T coord3(const Par3<T>& P, const T* const X[3], int c, int i, int j, int k) {
+  int id[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    const int n = P.n[a];
+    if (id[a] >= 0 && id[a] < n) continue;
+    if (P.bc[2 * a] == BC_PERIODIC) {
+      const int q = floordiv(id[a], n);
+      id[a] -= q * n;
+      return coord3(P, X, c, id[0], id[1], id[2]) + T(double(q)) * P.per[a][c];
+    }
+    const int b = id[a] < 0 ? 0 : n - 1;
+    int m[3] = {id[0], id[1], id[2]};
+    m[a] = 2 * b - id[a];
+    id[a] = b;
+    return cst<T>(2) * coord3(P, X, c, id[0], id[1], id[2]) - coord3(P, X, c, m[0], m[1], m[2]);
+  }
+  return X[c][((size_t)k * P.n[1] + j) * P.n[0] + i];
+}
+
+// The scheme's central operator delta^{c,(1)} (Eq. 2.7, as central_D) of nodal values
+// node(m), m = offset along the direction.
+template <class T, class F>
+static T central1(const Par3<T>& P, F node) {
+  const SchemeTab& S = P.tab;
+  auto mid = [&](int m) { return interp_mid<T>(P.scheme, P.interp, [&](int l) { return node(m + l); }); };
+  T d = T(0);
+  for (int m = 1; m <= 4; ++m)
+    if (S.cnode[m - 1] != 0.0L) d = d + cst<T>(S.cnode[m - 1]) * (node(m) - node(-m));
+  d = d + cst<T>(S.cmid[0]) * (mid(0) - mid(-1));
+  if (S.cmid[1] != 0.0L) d = d + cst<T>(S.cmid[1]) * (mid(1) - mid(-2));
+  return d;
+}
+
+// Metrics (Eq. 2.4) and Jacobian (Eq. 2.5) on the grid extended by G layers.  For direction
+// d with the next two directions (a, b) = (d+1, d+2) mod 3, and component c with the next
+// two coordinates (p, q) = (c+1, c+2) mod 3:
+//   m_{d,c} = 1/2 [ (p_a q)_b - (p_b q)_a + (q_b p)_a - (q_a p)_b ],
+// which for d = xi, c = x is Eq. (2.4) as printed; J^-1 = 1/3 sum_{d,c} m_{d,c} (c)_d.  Every
+// derivative, inner and outer, is the scheme's central operator (Section 2.3).  Staged as
+// coordinates on the grid extended by 12 layers, their derivatives on the grid extended by
+// 8, then the metrics.
+template <class T>
+static void metrics3(const Par3<T>& P, const T* const X[3], T* M) {
+  const Ext3 E12{12, {P.n[0], P.n[1], P.n[2]}}, E8{8, {P.n[0], P.n[1], P.n[2]}}, E4{G, {P.n[0], P.n[1], P.n[2]}};
+  std::vector<T> C[3], D[3][3];   // C[c]: coordinates; D[a][c]: derivative of c along a
+  for (int c = 0; c < 3; ++c) {
+    C[c].resize(E12.size());
+    for (int k = -12; k < P.n[2] + 12; ++k)
+      for (int j = -12; j < P.n[1] + 12; ++j)
+        for (int i = -12; i < P.n[0] + 12; ++i) C[c][E12.at(i, j, k)] = coord3(P, X, c, i, j, k);
+  }
+  auto step = [](int a, int m, int& i, int& j, int& k) { if (a == 0) i += m; else if (a == 1) j += m; else k += m; };
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      D[a][c].resize(E8.size());
+      for (int k = -8; k < P.n[2] + 8; ++k)
+        for (int j = -8; j < P.n[1] + 8; ++j)
+          for (int i = -8; i < P.n[0] + 8; ++i)
+            D[a][c][E8.at(i, j, k)] = central1(P, [&](int m) {
+              int ii = i, jj = j, kk = k;
+              step(a, m, ii, jj, kk);
+              return C[c][E12.at(ii, jj, kk)];
+            });
+    }
+  const size_t plane = E4.size();
+  for (int k = -G; k < P.n[2] + G; ++k)
+    for (int j = -G; j < P.n[1] + G; ++j)
+      for (int i = -G; i < P.n[0] + G; ++i) {
+        // (f_s g)_t: the derivative along t of the product of the derivative of f along s and g
+        auto dprod = [&](int t, int s, int f, int g) {
+          return central1(P, [&](int m) {
+            int ii = i, jj = j, kk = k;
+            step(t, m, ii, jj, kk);
+            return D[s][f][E8.at(ii, jj, kk)] * C[g][E12.at(ii, jj, kk)];
+          });
+        };
+        T Jv = T(0);
+        for (int d = 0; d < 3; ++d)
+          for (int c = 0; c < 3; ++c) {
+            const int a = (d + 1) % 3, b = (d + 2) % 3, p = (c + 1) % 3, q = (c + 2) % 3;
+            const T m = cst<T>(0.5L) * (dprod(b, a, p, q) - dprod(a, b, p, q) + dprod(a, b, q, p) - dprod(b, a, q, p));
+            M[(3 * d + c) * plane + E4.at(i, j, k)] = m;
+            Jv = Jv + m * D[d][c][E8.at(i, j, k)];
+          }
+        M[9 * plane + E4.at(i, j, k)] = Jv / cst<T>(3);
+      }
+}
+
+// Pressure, metric-weighted flux E^ = m_x E + m_y F + m_z G (Eq. 2.2) and |U^| + c |k^|.
+template <class T>
+static T pressure3(const T* q, T gamma) {
+  T u = q[1] / q[0], v = q[2] / q[0], w = q[3] / q[0];
+  return (gamma - cst<T>(1)) * (q[4] - cst<T>(0.5L) * q[0] * (u * u + v * v + w * w));
+}
+template <class T>
+static void flux3(const T* q, const T* m, T gamma, T* f) {
+  T rho = q[0], u = q[1] / rho, v = q[2] / rho, w = q[3] / rho;
+  T p = (gamma - cst<T>(1)) * (q[4] - cst<T>(0.5L) * rho * (u * u + v * v + w * w));
+  T U = m[0] * u + m[1] * v + m[2] * w;
+  f[0] = rho * U;
+  f[1] = rho * u * U + m[0] * p;
+  f[2] = rho * v * U + m[1] * p;
+  f[3] = rho * w * U + m[2] * p;
+  f[4] = (q[4] + p) * U;
+}
+template <class T>
+static T spectral3(const T* q, const T* m, T gamma) {
+  T rho = q[0], u = q[1] / rho, v = q[2] / rho, w = q[3] / rho;
+  T p = (gamma - cst<T>(1)) * (q[4] - cst<T>(0.5L) * rho * (u * u + v * v + w * w));
+  T c = sqrt(gamma * p / rho);
+  return fabs(m[0] * u + m[1] * v + m[2] * w) + c * sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+}
+
+// Left/right eigenvectors of the Jacobian of the flux along the unit direction n at state q
+// (Section 3.4 in three dimensions).  Reading: the Un eigenspace takes the entropy wave and two
+// shear waves along unit tangents t1, t2: t1 = (a x n)/|a x n| with a the coordinate axis
+// least aligned with n (smallest |n_i|, ties to the larger index), t2 = n x t1.  For n in
+// the x-y plane this is a = z, t1 = (-ny, nx, 0), t2 = (0, 0, 1): the two-dimensional
+// eigenvectors plus a shear wave in w.  R columns: (1, u - c n, H - c Un), (1, u, |u|^2/2),
+// (0, t1, u.t1), (0, t2, u.t2), (1, u + c n, H + c Un); L its inverse, with b1 = (gamma - 1)
+// / c^2 and b2 = b1 |u|^2 / 2: rows 1/2 (b2 + Un/c, -b1 u - n/c, b1), (1 - b2, b1 u, -b1),
+// (-u.t1, t1, 0), (-u.t2, t2, 0), 1/2 (b2 - Un/c, -b1 u + n/c, b1).
+template <class T>
+static void tangents3(const T* n, T* t1, T* t2) {
+  int a = 2;
+  for (int i = 1; i >= 0; --i)
+    if (fabs(n[i]) < fabs(n[a])) a = i;
+  // a x n with a the unit axis
+  T x[3];
+  if (a == 0) { x[0] = T(0); x[1] = -n[2]; x[2] = n[1]; }
+  else if (a == 1) { x[0] = n[2]; x[1] = T(0); x[2] = -n[0]; }
+  else { x[0] = -n[1]; x[1] = n[0]; x[2] = T(0); }
+  T s = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  for (int i = 0; i < 3; ++i) t1[i] = x[i] / s;
+  t2[0] = n[1] * t1[2] - n[2] * t1[1];
+  t2[1] = n[2] * t1[0] - n[0] * t1[2];
+  t2[2] = n[0] * t1[1] - n[1] * t1[0];
+}
+template <class T>
+static void eigvec3(const T* q, const T* n, T gamma, T L[5][5], T R[5][5]) {
+  T rho = q[0], u[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+  T q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  T p = (gamma - cst<T>(1)) * (q[4] - cst<T>(0.5L) * rho * q2);
+  T c = sqrt(gamma * p / rho);
+  T H = (q[4] + p) / rho;
+  T t1[3], t2[3];
+  tangents3(n, t1, t2);
+  T Un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  T U1 = u[0] * t1[0] + u[1] * t1[1] + u[2] * t1[2];
+  T U2 = u[0] * t2[0] + u[1] * t2[1] + u[2] * t2[2];
+  T b1 = (gamma - cst<T>(1)) / (c * c), b2 = cst<T>(0.5L) * b1 * q2;
+  const T h = cst<T>(0.5L);
+  R[0][0] = T(1); R[0][1] = T(1); R[0][2] = T(0); R[0][3] = T(0); R[0][4] = T(1);
+  for (int i = 0; i < 3; ++i) {
+    R[1 + i][0] = u[i] - c * n[i];
+    R[1 + i][1] = u[i];
+    R[1 + i][2] = t1[i];
+    R[1 + i][3] = t2[i];
+    R[1 + i][4] = u[i] + c * n[i];
+  }
+  R[4][0] = H - c * Un; R[4][1] = h * q2; R[4][2] = U1; R[4][3] = U2; R[4][4] = H + c * Un;
+  L[0][0] = h * (b2 + Un / c); L[4][0] = h * (b2 - Un / c);
+  L[1][0] = T(1) - b2; L[2][0] = -U1; L[3][0] = -U2;
+  for (int i = 0; i < 3; ++i) {
+    L[0][1 + i] = h * (-b1 * u[i] - n[i] / c);
+    L[1][1 + i] = b1 * u[i];
+    L[2][1 + i] = t1[i];
+    L[3][1 + i] = t2[i];
+    L[4][1 + i] = h * (-b1 * u[i] + n[i] / c);
+  }
+  L[0][4] = h * b1; L[1][4] = -b1; L[2][4] = T(0); L[3][4] = T(0); L[4][4] = h * b1;
+}
+
+}  // namespace orc
+
+namespace orc {
+
+template <class T>
+struct Field3 {
+  const Par3<T>& P;
+  const T* M;   // haloed metrics, 10 planes
+  const T* Q;   // [5][nk][nj][ni]
+  Ext3 E4() const { return Ext3{G, {P.n[0], P.n[1], P.n[2]}}; }
+  T met(int p, int i, int j, int k) const { return M[(size_t)p * E4().size() + E4().at(i, j, k)]; }
+  T q(int v, int i, int j, int k) const {
+    return Q[(size_t)v * P.n[0] * P.n[1] * P.n[2] + ((size_t)k * P.n[1] + j) * P.n[0] + i];
+  }
+  // node (i, j, k) of position s on line (l1, l2) of direction d (the other two indices in order)
+  void node(int d, int l1, int l2, int s, int& i, int& j, int& k) const {
+    if (d == 0) { i = s; j = l1; k = l2; }
+    else if (d == 1) { i = l1; j = s; k = l2; }
+    else { i = l1; j = l2; k = s; }
+  }
+  // State at position s with ghosts by the face rule: periodic wraps, transmissive copies the
+  // boundary node (the reading of two dimensions).
+  void state(int d, int l1, int l2, int s, T* out) const {
+    const int n = P.n[d];
+    int ss = s;
+    if (s < 0 || s >= n) {
+      const int face = 2 * d + (s < 0 ? 0 : 1);
+      ss = P.bc[face] == BC_PERIODIC ? s - floordiv(s, n) * n : (s < 0 ? 0 : n - 1);
+    }
+    int i, j, k;
+    node(d, l1, l2, ss, i, j, k);
+    for (int v = 0; v < 5; ++v) out[v] = q(v, i, j, k);
+  }
+  void nodemet(int d, int l1, int l2, int s, T* m) const {
+    int i, j, k;
+    node(d, l1, l2, s, i, j, k);
+    for (int c = 0; c < 3; ++c) m[c] = met(3 * d + c, i, j, k);
+  }
+};
+
+// A^ for line (l1, l2) of direction d: alpha x max over the line's nodes of |U^| + c|k^|.
+template <class T>
+static T line_lambda3(const Field3<T>& F, int d, int l1, int l2) {
+  T best = T(0);
+  for (int s = 0; s < F.P.n[d]; ++s) {
+    T q[5], m[3];
+    F.state(d, l1, l2, s, q);
+    F.nodemet(d, l1, l2, s, m);
+    T sp = spectral3(q, m, F.P.gamma);
+    if (s == 0 || sp > best) best = sp;
+  }
+  return F.P.alpha * best;
+}
+
+// One direction: adds H_{s+1/2} - H_{s-1/2} to R for every node of every line (the
+// two-dimensional sweep with five variables and three metric components).
+template <class T>
+static void sweep3(const Field3<T>& F, int d, std::vector<T>& R) {
+  const Par3<T>& P = F.P;
+  const SchemeTab& S = P.tab;
+  const int n = P.n[d];
+  const int n1 = P.n[d == 0 ? 1 : 0], n2 = P.n[d == 2 ? 1 : 2];
+  const int NB = n + 8, NI = n + 3;
+  const WenoOpt wo{P.ppm, P.linw, 0};
+  std::vector<T> q(5 * NB), ms(3 * NB), fp(5 * NB), fm(5 * NB), fpm(5 * NI), fmm(5 * NI), Hh(5 * NI);
+  const size_t N = (size_t)P.n[0] * P.n[1] * P.n[2];
+  for (int l2 = 0; l2 < n2; ++l2)
+    for (int l1 = 0; l1 < n1; ++l1) {
+      const T A = line_lambda3(F, d, l1, l2);
+      for (int s = -4; s < n + 4; ++s) {
+        T qs[5], f[5];
+        F.state(d, l1, l2, s, qs);
+        F.nodemet(d, l1, l2, s, &ms[3 * (s + 4)]);
+        flux3(qs, &ms[3 * (s + 4)], P.gamma, f);
+        for (int v = 0; v < 5; ++v) {
+          q[5 * (s + 4) + v] = qs[v];
+          fp[5 * (s + 4) + v] = cst<T>(0.5L) * (f[v] + A * qs[v]);
+          fm[5 * (s + 4) + v] = cst<T>(0.5L) * (f[v] - A * qs[v]);
+        }
+      }
+      const int nmp = S.hmid[1] != 0.0L ? 2 : 1;
+      for (int p = -nmp; p <= n - 2 + nmp; ++p) {
+        const int c0 = p + 4;
+        T mb[3], nn[3], mm[3];
+        for (int c = 0; c < 3; ++c) mb[c] = cst<T>(0.5L) * (ms[3 * c0 + c] + ms[3 * (c0 + 1) + c]);
+        T mbn = sqrt(mb[0] * mb[0] + mb[1] * mb[1] + mb[2] * mb[2]);
+        for (int c = 0; c < 3; ++c) nn[c] = mb[c] / mbn;
+        T Qs[2][5];
+        for (int side = 0; side < 2; ++side) {
+          const int ce = side == 0 ? c0 : c0 + 1;
+          T Lm[5][5], Rm[5][5];
+          eigvec3(&q[5 * ce], nn, P.gamma, Lm, Rm);
+          T Wmid[5];
+          const int half = S.r == 4 ? 3 : 2;
+          for (int kc = 0; kc < 5; ++kc) {
+            T u[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+            for (int m = -half; m <= half; ++m) {
+              const int nd = side == 0 ? c0 + m : c0 + 1 - m;
+              T w = T(0);
+              for (int v = 0; v < 5; ++v) w = w + Lm[kc][v] * q[5 * nd + v];
+              u[m + 3] = w;
+            }
+            Wmid[kc] = weno_mid(S.r, u, wo, P.eps);
+          }
+          for (int v = 0; v < 5; ++v) {
+            T acc = T(0);
+            for (int kc = 0; kc < 5; ++kc) acc = acc + Rm[v][kc] * Wmid[kc];
+            Qs[side][v] = acc;
+          }
+        }
+        for (int c = 0; c < 3; ++c)
+          mm[c] = interp_mid<T>(P.scheme, P.interp, [&](int l) { return ms[3 * (c0 + l) + c]; });
+        T fpl[5], fmi[5];
+        flux3(Qs[0], mm, P.gamma, fpl);
+        flux3(Qs[1], mm, P.gamma, fmi);
+        for (int v = 0; v < 5; ++v) {
+          fpm[5 * (p + 2) + v] = cst<T>(0.5L) * (fpl[v] + A * Qs[0][v]);
+          fmm[5 * (p + 2) + v] = cst<T>(0.5L) * (fmi[v] - A * Qs[1][v]);
+        }
+      }
+      for (int p = -1; p <= n - 1; ++p)
+        for (int v = 0; v < 5; ++v) {
+          T hp = T(0), hm = T(0);
+          for (int m = 0; m >= -1; --m) {
+            if (S.hmid[-m] == 0.0L) continue;
+            hp = hp + cst<T>(S.hmid[-m]) * fpm[5 * (p + m + 2) + v];
+            hm = hm + cst<T>(S.hmid[-m]) * fmm[5 * (p - m + 2) + v];
+          }
+          for (int k = -3; k <= 3; ++k) {
+            if (S.hnode[k + 3] == 0.0L) continue;
+            hp = hp + cst<T>(S.hnode[k + 3]) * fp[5 * (p + k + 4) + v];
+            hm = hm + cst<T>(S.hnode[k + 3]) * fm[5 * (p + 1 - k + 4) + v];
+          }
+          Hh[5 * (p + 2) + v] = hp + hm;
+        }
+      for (int s = 0; s < n; ++s) {
+        int i, j, k;
+        F.node(d, l1, l2, s, i, j, k);
+        for (int v = 0; v < 5; ++v) {
+          size_t o = (size_t)v * N + ((size_t)k * P.n[1] + j) * P.n[0] + i;
+          R[o] = R[o] + (Hh[5 * (s + 2) + v] - Hh[5 * (s + 1) + v]);
+        }
+      }
+    }
+}
+
+// dQ/dt = -(dE^/dxi + dF^/deta + dG^/dzeta) / J^-1 (Eq. 2.2)
+template <class T>
+static void rhs3(const Par3<T>& P, const T* M, const T* Q, T* dQ) {
+  Field3<T> F{P, M, Q};
+  const size_t N = (size_t)P.n[0] * P.n[1] * P.n[2];
+  std::vector<T> R(5 * N, T(0));
+  for (int d = 0; d < 3; ++d) sweep3(F, d, R);
+  for (int k = 0; k < P.n[2]; ++k)
+    for (int j = 0; j < P.n[1]; ++j)
+      for (int i = 0; i < P.n[0]; ++i) {
+        T Jinv = F.met(9, i, j, k);
+        for (int v = 0; v < 5; ++v) {
+          size_t o = (size_t)v * N + ((size_t)k * P.n[1] + j) * P.n[0] + i;
+          dQ[o] = -R[o] / Jinv;
+        }
+      }
+}
+
+template <class T>
+static void rk3_3(const Par3<T>& P, const T* M, T* Q, T dt) {
+  const size_t N = 5 * (size_t)P.n[0] * P.n[1] * P.n[2];
+  std::vector<T> R(N), Q1(N), Q2(N);
+  rhs3(P, M, Q, R.data());
+  for (size_t k = 0; k < N; ++k) Q1[k] = Q[k] + dt * R[k];
+  rhs3(P, M, Q1.data(), R.data());
+  for (size_t k = 0; k < N; ++k) Q2[k] = cst<T>(0.75L) * Q[k] + cst<T>(0.25L) * (Q1[k] + dt * R[k]);
+  rhs3(P, M, Q2.data(), R.data());
+  for (size_t k = 0; k < N; ++k) Q[k] = cst<T>(1.0L / 3) * Q[k] + cst<T>(2.0L / 3) * (Q2[k] + dt * R[k]);
+}
+
+static int check3(const int* ip, int ni, int nj, int nk) {
+  if (ip[0] < 0 || ip[0] > 4 || ip[1] < 0 || ip[1] > 1) return 1;
+  const int n[3] = {ni, nj, nk};
+  for (int a = 0; a < 3; ++a) {
+    if (ip[4 + 2 * a] < 0 || ip[4 + 2 * a] > 1 || ip[5 + 2 * a] < 0 || ip[5 + 2 * a] > 1) return 2;
+    if ((ip[4 + 2 * a] == BC_PERIODIC) != (ip[5 + 2 * a] == BC_PERIODIC)) return 3;
+    if (ip[4 + 2 * a] != BC_PERIODIC && n[a] < 13) return 4;   // the reflected ghosts reach 12 nodes in
+    if (n[a] < 1) return 4;
+  }
+  return 0;
+}
+
+}  // namespace orc
+
+extern "C" {
+
+// 3-D: ip = {scheme, interp, ppm, linear_weights, bc[6]}; dp = {gamma, lf_alpha, eps,
+// period[3][3]}; x, y, z and Q as documented above the three-dimensional section.
+size_t orc3_metrics_len(int ni, int nj, int nk) { return (size_t)10 * (ni + 2 * G) * (nj + 2 * G) * (nk + 2 * G); }
+
+int orc3_metrics(const int* ip, const double* dp, int ni, int nj, int nk, const double* x, const double* y,
+                 const double* z, double* M) {
+  if (int e = check3(ip, ni, nj, nk)) return e;
+  Par3<double> P;
+  unpack3(ip, dp, ni, nj, nk, P);
+  const double* X[3] = {x, y, z};
+  metrics3(P, X, M);
+  return 0;
+}
+
+int orc3_rhs(const int* ip, const double* dp, int ni, int nj, int nk, const double* M, const double* Q, double* dQ) {
+  if (int e = check3(ip, ni, nj, nk)) return e;
+  Par3<double> P;
+  unpack3(ip, dp, ni, nj, nk, P);
+  rhs3(P, M, Q, dQ);
+  return 0;
+}
+
+int orc3_rk3(const int* ip, const double* dp, int ni, int nj, int nk, const double* M, double* Q, double dt,
+             int nsteps) {
+  if (int e = check3(ip, ni, nj, nk)) return e;
+  Par3<double> P;
+  unpack3(ip, dp, ni, nj, nk, P);
+  for (int s = 0; s < nsteps; ++s) rk3_3(P, M, Q, dt);
+  return 0;
+}
+
+// line maxima A^ of every line of direction d, lines ordered (l1 fastest, l2)
+int orc3_lambda(const int* ip, const double* dp, int ni, int nj, int nk, int d, const double* M, const double* Q,
+                double* out) {
+  if (int e = check3(ip, ni, nj, nk)) return e;
+  Par3<double> P;
+  unpack3(ip, dp, ni, nj, nk, P);
+  Field3<double> F{P, M, Q};
+  const int n1 = P.n[d == 0 ? 1 : 0], n2 = P.n[d == 2 ? 1 : 2];
+  for (int l2 = 0; l2 < n2; ++l2)
+    for (int l1 = 0; l1 < n1; ++l1) out[(size_t)l2 * n1 + l1] = line_lambda3(F, d, l1, l2);
+  return 0;
+}
+
+// operation count of one right-hand side (Counted scalar) and of its three sweeps
+int orc3_count_flops(const int* ip, const double* dp, int ni, int nj, int nk, const double* M, const double* Q,
+                     long long* out) {
+  if (int e = check3(ip, ni, nj, nk)) return e;
+  Par3<Counted> P;
+  unpack3(ip, dp, ni, nj, nk, P);
+  const size_t NM = orc3_metrics_len(ni, nj, nk), NQ = 5 * (size_t)ni * nj * nk;
+  std::vector<Counted> Mc(M, M + NM), Qc(Q, Q + NQ), R(NQ);
+  Field3<Counted> F{P, Mc.data(), Qc.data()};
+  g_flops = 0;
+  rhs3(P, Mc.data(), Qc.data(), R.data());
+  out[0] = g_flops;
+  for (int d = 0; d < 3; ++d) {
+    std::vector<Counted> Rd(NQ, Counted(0.0));
+    g_flops = 0;
+    sweep3(F, d, Rd);
+    out[1 + d] = g_flops;
+  }
+  return 0;
+}
+
+// the eigenvectors along unit direction n (for the pins)
+void orc3_eig(double gamma, const double* q, const double* n, double* L, double* R) {
+  double Lm[5][5], Rm[5][5];
+  eigvec3(q, n, gamma, Lm, Rm);
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) { L[5 * a + b] = Lm[a][b]; R[5 * a + b] = Rm[a][b]; }
+}
+
+// the metrics in long double (to show the free-stream residual shrinks with the precision):
+// residual max |dQ/dt| of the uniform state q0 on the grid, in the given precision
+double orc3_fsp_residual(const int* ip, const double* dp, int ni, int nj, int nk, const double* x, const double* y,
+                         const double* z, const double* q0, int wide) {
+  if (check3(ip, ni, nj, nk)) return -1.0;
+  const size_t NN = (size_t)ni * nj * nk;
+  auto run = [&](auto zero) -> double {
+    using T = decltype(zero);
+    Par3<T> P;
+    unpack3(ip, dp, ni, nj, nk, P);
+    std::vector<T> X[3];
+    const double* src[3] = {x, y, z};
+    for (int c = 0; c < 3; ++c) { X[c].resize(NN); for (size_t o = 0; o < NN; ++o) X[c][o] = T(src[c][o]); }
+    const T* Xp[3] = {X[0].data(), X[1].data(), X[2].data()};
+    std::vector<T> M(orc3_metrics_len(ni, nj, nk)), Q(5 * NN), R(5 * NN);
+    metrics3(P, Xp, M.data());
+    for (int v = 0; v < 5; ++v) for (size_t o = 0; o < NN; ++o) Q[v * NN + o] = T(q0[v]);
+    rhs3(P, M.data(), Q.data(), R.data());
+    double worst = 0.0;
+    for (auto& r : R) worst = std::max(worst, (double)std::fabs((long double)r));
+    return worst;
+  };
+  return wide ? run((long double)0) : run(0.0);
+}
+
+}  // extern "C"

@@ -32,6 +32,7 @@ __all__ = [
     "scheme_table", "advect1d", "advect1d_dt", "smoothness4", "riemann_exact", "long_double_digits", "G",
     "mb_metrics", "mb_rhs", "mb_rk3", "rhs_vjp", "rk3_vjp", "metrics_vjp", "count_vjp_flops",
     "advect1d_opts", "weno_z", "split_flux",
+    "metrics3", "rhs3", "rk3_3", "lambda3", "count_flops3", "eig3", "fsp_residual3",
 ]
 
 G = 4
@@ -104,6 +105,18 @@ def lib():
                 "orc_mb_rhs": (ctypes.c_int, [_I, _D, ctypes.c_int, _I, _I, _I, _D, _D, _D]),
                 "orc_mb_rk3": (ctypes.c_int, [_I, _D, ctypes.c_int, _I, _I, _I, _D, _D, ctypes.c_double,
                                               ctypes.c_int]),
+                "orc3_metrics_len": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                "orc3_metrics": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]),
+                "orc3_rhs": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
+                "orc3_rk3": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                                            ctypes.c_double, ctypes.c_int]),
+                "orc3_lambda": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               _D, _D, _D]),
+                "orc3_count_flops": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                                                    ctypes.POINTER(ctypes.c_longlong)]),
+                "orc3_eig": (None, [ctypes.c_double, _D, _D, _D, _D]),
+                "orc3_fsp_residual": (ctypes.c_double, [_I, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                                                        _D, _D, ctypes.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -454,3 +467,81 @@ def mb_rk3(cfg, blocks, Ms, Qs, dt, nsteps=1):
         out.append(Q[o:o + q.size].reshape(q.shape))
         o += q.size
     return out
+
+
+# ---- three dimensions ------------------------------------------------------------------------
+# cfg keys as above, with ``bc`` six face codes (i-min, i-max, j-min, j-max, k-min, k-max: 0
+# periodic, 1 transmissive) and ``period`` three vectors (added per wrap in i, j, k).  Arrays:
+# coordinates (nk, nj, ni); state (5, nk, nj, ni); metrics (10, nk+8, nj+8, ni+8): the planes
+# xi_x^, xi_y^, xi_z^, eta_x^, eta_y^, eta_z^, zeta_x^, zeta_y^, zeta_z^, J^-1.
+def _params3(cfg):
+    ip = np.array([cfg.get("scheme", 2), cfg.get("interp", 0), cfg.get("ppm", 1), cfg.get("linear_weights", 0)]
+                  + list(cfg.get("bc", (0, 0, 0, 0, 0, 0))), dtype=np.int32)
+    per = np.asarray(cfg.get("period", ((0.0,) * 3,) * 3), dtype=np.float64).reshape(9)
+    dp = np.concatenate([[cfg.get("gamma", 1.4), cfg.get("lf_alpha", 1.1), cfg.get("eps", 1e-40)], per])
+    return ip, dp.astype(np.float64)
+
+
+def metrics3(cfg, x, y, z):
+    ip, dp = _params3(cfg)
+    nk, nj, ni = x.shape
+    M = np.zeros((10, nk + 2 * G, nj + 2 * G, ni + 2 * G))
+    _ck(lib().orc3_metrics(ip.ctypes.data_as(_I), _dp(dp), ni, nj, nk, _dp(_f64(x)), _dp(_f64(y)), _dp(_f64(z)),
+                           _dp(M)), "metrics3")
+    return M
+
+
+def rhs3(cfg, M, Q):
+    ip, dp = _params3(cfg)
+    _, nk, nj, ni = Q.shape
+    R = np.zeros_like(Q, dtype=np.float64)
+    _ck(lib().orc3_rhs(ip.ctypes.data_as(_I), _dp(dp), ni, nj, nk, _dp(_f64(M)), _dp(_f64(Q)), _dp(R)), "rhs3")
+    return R
+
+
+def rk3_3(cfg, M, Q, dt, nsteps=1):
+    ip, dp = _params3(cfg)
+    _, nk, nj, ni = Q.shape
+    out = np.array(Q, dtype=np.float64, copy=True)
+    _ck(lib().orc3_rk3(ip.ctypes.data_as(_I), _dp(dp), ni, nj, nk, _dp(_f64(M)), _dp(out), float(dt), int(nsteps)),
+        "rk3_3")
+    return out
+
+
+def lambda3(cfg, M, Q, d):
+    """A^ of every line of direction d (0 xi, 1 eta, 2 zeta), shape (n2, n1): the other two
+    indices in the order (i, j, k) with the first fastest."""
+    ip, dp = _params3(cfg)
+    _, nk, nj, ni = Q.shape
+    n = (ni, nj, nk)
+    others = [n[a] for a in range(3) if a != d]
+    out = np.zeros((others[1], others[0]))
+    _ck(lib().orc3_lambda(ip.ctypes.data_as(_I), _dp(dp), ni, nj, nk, int(d), _dp(_f64(M)), _dp(_f64(Q)), _dp(out)),
+        "lambda3")
+    return out
+
+
+def count_flops3(cfg, M, Q):
+    """Operations of one right-hand side and of its xi, eta and zeta sweeps."""
+    ip, dp = _params3(cfg)
+    _, nk, nj, ni = Q.shape
+    out = (ctypes.c_longlong * 4)()
+    _ck(lib().orc3_count_flops(ip.ctypes.data_as(_I), _dp(dp), ni, nj, nk, _dp(_f64(M)), _dp(_f64(Q)), out),
+        "count_flops3")
+    return dict(rhs=out[0], xi=out[1], eta=out[2], zeta=out[3])
+
+
+def eig3(gamma, q, n):
+    L, R = np.zeros((5, 5)), np.zeros((5, 5))
+    lib().orc3_eig(float(gamma), _dp(_f64(q)), _dp(_f64(n)), _dp(L), _dp(R))
+    return L, R
+
+
+def fsp_residual3(cfg, x, y, z, q0, wide=False):
+    ip, dp = _params3(cfg)
+    nk, nj, ni = x.shape
+    r = lib().orc3_fsp_residual(ip.ctypes.data_as(_I), _dp(dp), ni, nj, nk, _dp(_f64(x)), _dp(_f64(y)),
+                                _dp(_f64(z)), _dp(_f64(q0)), int(bool(wide)))
+    if r < 0:
+        raise ValueError("oracle fsp_residual3: invalid arguments")
+    return r

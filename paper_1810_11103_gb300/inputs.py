@@ -500,3 +500,61 @@ def paper_shock_vortex_grid(n: int = 601, randomized: bool = True, seed: int = 1
     cells), nine uniform layers at the boundaries, A = 0.2 inside; the state is
     shock_vortex_state with the paper's Mach 3 shock, run to t = 15 with dt = 0.01."""
     return _box_grid(n, (-20.0, -15.0), (10.0, 15.0), 0.2, 9, seed, randomized)
+
+
+# ----------------------------------------------------------------------------------------
+# Three dimensions: arrays are (nk, nj, ni), i fastest; states (5, nk, nj, ni)
+# ----------------------------------------------------------------------------------------
+def conservative3(rho, u, v, w, p, gamma: float = GAMMA) -> np.ndarray:
+    return np.stack([rho, rho * u, rho * v, rho * w, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def periodic_cube(n: int, length: float, amp: float, seed: int, nj: int | None = None, nk: int | None = None):
+    """ni x nj x nk unique nodes of a periodic box [0, length)^3.  Every node moves along one
+    of the three coordinates (chosen by a uniform draw, as the two-dimensional randomisation
+    picks one of two) by h 2 amp (r - 1/2).  Returns x, y, z, period (3 x 3)."""
+    ni, nj, nk = n, (n if nj is None else nj), (n if nk is None else nk)
+    h = (length / ni, length / nj, length / nk)
+    k, j, i = np.meshgrid(np.arange(nk, dtype=np.float64), np.arange(nj, dtype=np.float64),
+                          np.arange(ni, dtype=np.float64), indexing="ij")
+    X = [h[0] * i, h[1] * j, h[2] * k]
+    if amp > 0:
+        N = ni * nj * nk
+        which = np.floor(3.0 * uniform(seed, 0, N, 3)).reshape(nk, nj, ni)
+        for c in range(3):
+            r = uniform(seed, 0, N, c).reshape(nk, nj, ni)
+            X[c] = X[c] + h[c] * 2.0 * amp * (r - 0.5) * (which == c)
+    period = ((length, 0.0, 0.0), (0.0, length, 0.0), (0.0, 0.0, length))
+    return X[0], X[1], X[2], period
+
+
+def extrude(x, y, nk: int, dz: float = 1.0):
+    """A two-dimensional grid repeated along k with spacing dz: x, y, z of shape (nk, nj, ni)."""
+    X = np.broadcast_to(x[None], (nk,) + x.shape).copy()
+    Y = np.broadcast_to(y[None], (nk,) + y.shape).copy()
+    Z = np.broadcast_to(dz * np.arange(nk, dtype=np.float64)[:, None, None], X.shape).copy()
+    return X, Y, Z
+
+
+def vortex3(x, y, z, center, strength=5.0, free=(1.0, 1.0, 1.0, 0.5, 1.0), period=None, gamma: float = GAMMA):
+    """The isentropic vortex about an axis parallel to z through (cx, cy), on a free stream
+    (rho, u, v, w, p), modulated along z by a smooth density wave of small amplitude, so the
+    state varies in all three directions (a smooth input for parity and order checks)."""
+    q2 = isentropic_vortex(x.reshape(-1, x.shape[-1]), y.reshape(-1, y.shape[-1]), center, strength,
+                           (free[0], free[1], free[2], free[4]),
+                           None if period is None else (period[0][0], period[1][1]), gamma=gamma)
+    q2 = q2.reshape((4,) + x.shape)
+    rho, u, v = q2[0], q2[1] / q2[0], q2[2] / q2[0]
+    p = (gamma - 1.0) * (q2[3] - 0.5 * rho * (u * u + v * v))
+    Lz = 2.0 * np.pi if period is None else period[2][2]
+    rho = rho * (1.0 + 0.05 * np.sin(2.0 * np.pi * z / Lz))
+    return conservative3(rho, u, v, np.full_like(rho, free[3]), p, gamma)
+
+
+def random_state3(shape, seed: int, rho=(0.8, 1.2), vel=(-0.3, 0.3), p=(0.8, 1.2), gamma: float = GAMMA,
+                  block: int = 17) -> np.ndarray:
+    """Every node independent (algebraic tests), shape (nk, nj, ni)."""
+    n = int(np.prod(shape))
+    r = [uniform(seed, block + k, n, 0).reshape(shape) for k in range(5)]
+    s = lambda lo_hi, t: lo_hi[0] + (lo_hi[1] - lo_hi[0]) * t
+    return conservative3(s(rho, r[0]), s(vel, r[1]), s(vel, r[2]), s(vel, r[3]), s(p, r[4]), gamma)
