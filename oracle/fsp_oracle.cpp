@@ -1870,9 +1870,9 @@ static T line_lambda3(const Field3<T>& F, int d, int l1, int l2) {
     F.state(d, l1, l2, s, q);
     F.nodemet(d, l1, l2, s, m);
     T sp = spectral3(q, m, F.P.gamma);
-    if (s == 0 || sp > best) best = sp;
+    if (s == 0 || best < sp) best = sp;
   }
-  return F.P.alpha * best;
+  return best * F.P.alpha;
 }
 
 // One direction: adds H_{s+1/2} - H_{s-1/2} to R for every node of every line (the
@@ -1910,7 +1910,7 @@ static void sweep3(const Field3<T>& F, int d, std::vector<T>& R) {
         for (int c = 0; c < 3; ++c) nn[c] = mb[c] / mbn;
         T Qs[2][5];
         for (int side = 0; side < 2; ++side) {
-          const int ce = side == 0 ? c0 : c0 + 1;
+          const int ce = c0 + side;
           T Lm[5][5], Rm[5][5];
           eigvec3(&q[5 * ce], nn, P.gamma, Lm, Rm);
           T Wmid[5];
@@ -1980,7 +1980,7 @@ static void rhs3(const Par3<T>& P, const T* M, const T* Q, T* dQ) {
         T Jinv = F.met(9, i, j, k);
         for (int v = 0; v < 5; ++v) {
           size_t o = (size_t)v * N + ((size_t)k * P.n[1] + j) * P.n[0] + i;
-          dQ[o] = -R[o] / Jinv;
+          dQ[o] = -(R[o] / Jinv);
         }
       }
 }
@@ -1992,9 +1992,9 @@ static void rk3_3(const Par3<T>& P, const T* M, T* Q, T dt) {
   rhs3(P, M, Q, R.data());
   for (size_t k = 0; k < N; ++k) Q1[k] = Q[k] + dt * R[k];
   rhs3(P, M, Q1.data(), R.data());
-  for (size_t k = 0; k < N; ++k) Q2[k] = cst<T>(0.75L) * Q[k] + cst<T>(0.25L) * (Q1[k] + dt * R[k]);
+  for (size_t k = 0; k < N; ++k) Q2[k] = cst<T>(0.25L) * (Q1[k] + dt * R[k]) + cst<T>(0.75L) * Q[k];
   rhs3(P, M, Q2.data(), R.data());
-  for (size_t k = 0; k < N; ++k) Q[k] = cst<T>(1.0L / 3) * Q[k] + cst<T>(2.0L / 3) * (Q2[k] + dt * R[k]);
+  for (size_t k = 0; k < N; ++k) Q[k] = cst<T>(2.0L / 3) * (Q2[k] + dt * R[k]) + cst<T>(1.0L / 3) * Q[k];
 }
 
 static int check3(const int* ip, int ni, int nj, int nk) {

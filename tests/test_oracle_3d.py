@@ -199,3 +199,25 @@ def test_operation_count_is_affine_in_the_line_length():
         c = dict(scheme=2, linear_weights=1, period=per, bc=(0,) * 6)
         tot.append(O.count_flops3(c, O.metrics3(c, x, y, z), q)["xi"])
     assert tot[2] - tot[1] == tot[1] - tot[0] > 0
+
+
+@pytest.mark.parametrize("bc", [(0,) * 6, (1,) * 6])
+def test_metrics_exact_on_affine_grids(bc):
+    """On an affine grid x = A (i, j, k) + b every derivative in Eq. 2.4 is exact (the central
+    operators are exact on linear data, and the odd reflection of the ghost coordinates keeps
+    the grid affine), so the metrics are the cofactors of A (row d of the inverse times det A)
+    and J^-1 = det A, at every node including the ghosts."""
+    A = np.array([[0.9, 0.2, -0.1], [0.15, 1.1, 0.25], [-0.05, 0.3, 0.8]])
+    n = 14
+    k, j, i = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float), np.arange(n, dtype=float),
+                          indexing="ij")
+    X = [A[c, 0] * i + A[c, 1] * j + A[c, 2] * k + 0.3 * c for c in range(3)]
+    per = tuple(tuple(n * A[:, a]) for a in range(3))
+    for scheme in range(5):
+        M = O.metrics3(dict(scheme=scheme, period=per, bc=bc), *X)
+        det = np.linalg.det(A)
+        cof = det * np.linalg.inv(A)          # row d: the metric vector of direction d
+        for d in range(3):
+            for c in range(3):
+                assert np.abs(M[3 * d + c] - cof[d, c]).max() < 1e-12, (scheme, d, c)
+        assert np.abs(M[9] - det).max() < 1e-12

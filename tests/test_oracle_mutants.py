@@ -25,6 +25,7 @@ TAN = "test_oracle_tangent.py::"
 FLO = "test_oracle_flops.py::"
 VJP = "test_oracle_vjp.py::"
 OPT = "test_oracle_options.py::"
+D3 = "test_oracle_3d.py::"
 
 # (name, text in the oracle, planted replacement, pins that catch it: tests/ node ids)
 MUTANTS = [
@@ -177,6 +178,25 @@ MUTANTS = [
      [OPT + "test_midpoint_splittings_are_consistent[1]", OPT + "test_midpoint_splittings_sod[1]"]),
     ("vl_energy", "(gamma * gamma - cst<T>(1))", "(gamma * gamma + cst<T>(1))",
      [OPT + "test_midpoint_splittings_are_consistent[2]", OPT + "test_midpoint_splittings_upwind_limits"]),
+    # three dimensions (Sections 2.1-2.2)
+    ("d3_metric_sign", "(dprod(b, a, p, q) - dprod(a, b, p, q) + dprod(a, b, q, p) - dprod(b, a, q, p))",
+     "(dprod(b, a, p, q) + dprod(a, b, p, q) + dprod(a, b, q, p) - dprod(b, a, q, p))",
+     [D3 + "test_metrics_exact_on_affine_grids[bc0]", D3 + "test_free_stream_on_randomised_cube[2]"]),
+    ("d3_jacobian_third", "M[9 * plane + E4.at(i, j, k)] = Jv / cst<T>(3);", "M[9 * plane + E4.at(i, j, k)] = Jv / cst<T>(2);",
+     [D3 + "test_metrics_exact_on_affine_grids[bc0]"]),
+    ("d3_ghost_reflection", "return cst<T>(2) * coord3(P, X, c, id[0], id[1], id[2]) - coord3(P, X, c, m[0], m[1], m[2]);",
+     "return coord3(P, X, c, m[0], m[1], m[2]);", [D3 + "test_metrics_exact_on_affine_grids[bc1]"]),
+    ("d3_tangent_axis", "if (fabs(n[i]) < fabs(n[a])) a = i;", "if (fabs(n[i]) > fabs(n[a])) a = i;",
+     [D3 + "test_eigenvectors[n1]"]),
+    ("d3_left_shear", "L[1][0] = T(1) - b2; L[2][0] = -U1; L[3][0] = -U2;", "L[1][0] = T(1) - b2; L[2][0] = U1; L[3][0] = -U2;",
+     [D3 + "test_eigenvectors[n0]", D3 + "test_extruded_grid_reduces_to_two_dimensions[2]"]),
+    ("d3_w_momentum_flux", "f[3] = rho * w * U + m[2] * p;", "f[3] = rho * w * U + m[1] * p;",
+     [D3 + "test_rotation_with_linear_weights[0]", D3 + "test_design_order_stationary_vortex[2-4.0]"]),
+    ("d3_mid_metric_component", "mm[c] = interp_mid<T>(P.scheme, P.interp, [&](int l) { return ms[3 * (c0 + l) + c]; });",
+     "mm[c] = interp_mid<T>(P.scheme, P.interp, [&](int l) { return ms[3 * (c0 + l)]; });",
+     [D3 + "test_free_stream_on_randomised_cube[2]"]),
+    ("d3_spectral_w", "fabs(m[0] * u + m[1] * v + m[2] * w) + c", "fabs(m[0] * u + m[1] * v + m[1] * w) + c",
+     [D3 + "test_rotation_with_linear_weights[0]"]),
     # reverse mode (the tape behind the oracle's adjoints)
     ("rev_sub_sign", "rev_rec(a.v - b.v, a.i, 1.0, b.i, -1.0, 1)", "rev_rec(a.v - b.v, a.i, 1.0, b.i, 1.0, 1)",
      [VJP + "test_rhs_vjp_is_the_transposed_tangent[False-0]", VJP + "test_rhs_vjp_matches_finite_differences"]),
