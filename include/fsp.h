@@ -390,6 +390,62 @@ fsp_status fsp_batch_set_tile_shape(fsp_batch* b, int dir, int variant);
 fsp_status fsp_batch_tile_shape(const fsp_batch* b, int dir, int* variant, int* lines, int* outputs);
 fsp_status fsp_batch_destroy(fsp_batch* b);
 
+/* ---- three dimensions (Sections 2.1-2.2) ------------------------------------------------
+ * Q = (rho, rho u, rho v, rho w, e) with e = p/(gamma - 1) + rho |u|^2 / 2 (Eq. 2.1), on one
+ * block of ni x nj x nk nodes.  Layouts (device memory, caller-owned): coordinates x, y, z
+ * [nk][nj][ni] doubles; state [5][nk][nj][ni] doubles (i fastest, no row padding); metrics
+ * fsp3_metrics_elems() doubles, 10 planes on the node range extended by FSP_G layers:
+ * plane 3 d + c is component c (x, y, z) of the metric of direction d (xi, eta, zeta), i.e.
+ * xi_x^, xi_y^, xi_z^, eta_x^, ..., zeta_z^, and plane 9 is J^-1; node (i, j, k) of plane p
+ * at p P + ((k + G)(nj + 2G) + (j + G))(ni + 2G) + (i + G), P = (ni+2G)(nj+2G)(nk+2G).
+ * FP64 only and the printed schemes' options only (cfg->precision FSP_FP64, weights,
+ * mid_split and scheme_alpha at their defaults), else FSP_ERR_UNSUPPORTED; cfg->bc is not
+ * used.  Faces FSP_BC_PERIODIC or FSP_BC_TRANSMISSIVE (others: FSP_ERR_UNSUPPORTED), both
+ * faces of a direction periodic or neither, and a non-periodic direction needs >= 13 nodes
+ * (FSP_ERR_INVALID_ARG otherwise).  Ghost states: periodic wrap or a copy of the boundary
+ * node; ghost coordinates: periodic wrap plus the period vector, else odd reflection about
+ * the boundary node.  Host pointers and short workspaces give FSP_ERR_INVALID_ARG.  No
+ * adjoint. */
+typedef struct fsp3_block {
+  int ni, nj, nk;
+  int bc[6];               /* faces i-min, i-max, j-min, j-max, k-min, k-max */
+  double period[3][3];     /* (dx, dy, dz) added per periodic wrap in i, j and k */
+} fsp3_block;
+
+/* Doubles of the metric array (10 planes on the extended node range). */
+long long fsp3_metrics_elems(const fsp3_block* blk);
+
+/* Bytes of workspace for every fsp3_* call (the largest of the metric scratch and the RK3
+ * step's line maxima, accumulator and two stage states). */
+fsp_status fsp3_workspace_size(const fsp_config* cfg, const fsp3_block* blk, size_t* bytes);
+
+/* fsp3_metrics -- the symmetric conservative metrics of Eq. 2.4,
+ *   m_{d,c} = 1/2 [(p_a q)_b - (p_b q)_a + (q_b p)_a - (q_a p)_b],
+ * (a, b) the directions after d and (p, q) the coordinates after c, cyclically (for xi_x^
+ * this is Eq. 2.4 as printed), and J^-1 = 1/3 sum_{d,c} m_{d,c} (c)_d (Eq. 2.5).  Every
+ * derivative, inner and outer, is the scheme's central operator delta^{c,(1)} (Eq. 2.7)
+ * with the midpoint interpolation of cfg->interp, so that the metric identities hold to
+ * round-off and a uniform flow is preserved on any grid. */
+fsp_status fsp3_metrics(const fsp_config* cfg, const fsp3_block* blk, const double* x, const double* y,
+                        const double* z, double* metrics, void* ws, size_t ws_bytes, void* stream);
+
+/* Line maxima of |U^| + c|k^| (without the factor lf_alpha) into lam: the xi lines
+ * [nk][nj], then the eta lines [nk][ni], then the zeta lines [nj][ni]. */
+fsp_status fsp3_line_lambda(const fsp_config* cfg, const fsp3_block* blk, const double* metrics, const double* Q,
+                            double* lam, void* stream);
+
+/* fsp3_rhs -- dQ/dt = -(dE^/dxi + dF^/deta + dG^/dzeta) / J^-1 (Eq. 2.2), each direction
+ * with the splitting of Section 2.3 and the upwind-biased combination of Section 3; the
+ * characteristic projection uses the direction n of the averaged metrics and, for the
+ * eigenspace of Un, the entropy wave and two shear waves along t1 = a x n / |a x n| (a the
+ * coordinate axis least aligned with n, ties to the later axis) and t2 = n x t1. */
+fsp_status fsp3_rhs(const fsp_config* cfg, const fsp3_block* blk, const double* metrics, const double* Q,
+                    double* dQdt, void* ws, size_t ws_bytes, void* stream);
+
+/* fsp3_rk3_step -- one TVD-RK3 step of size dt, Q updated in place. */
+fsp_status fsp3_rk3_step(const fsp_config* cfg, const fsp3_block* blk, const double* metrics, double* Q, double dt,
+                         void* ws, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,6 +49,11 @@ class _Block(ctypes.Structure):
                 ("period", (ctypes.c_double * 2) * 2)]
 
 
+class _Block3(ctypes.Structure):
+    _fields_ = [("ni", ctypes.c_int), ("nj", ctypes.c_int), ("nk", ctypes.c_int), ("bc", ctypes.c_int * 6),
+                ("period", (ctypes.c_double * 3) * 3)]
+
+
 class _Link(ctypes.Structure):
     _fields_ = [("nbr", ctypes.c_int), ("face", ctypes.c_int), ("reversed", ctypes.c_int),
                 ("offset", ctypes.c_double * 2)]
@@ -145,6 +150,13 @@ def lib():
                 "fsp_batch_tile_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
                 "fsp_batch_destroy": (ctypes.c_int, [_P]),
+                "fsp3_metrics_elems": (ctypes.c_longlong, [ctypes.POINTER(_Block3)]),
+                "fsp3_workspace_size": (ctypes.c_int, [C, ctypes.POINTER(_Block3), ctypes.POINTER(ctypes.c_size_t)]),
+                "fsp3_metrics": (ctypes.c_int, [C, ctypes.POINTER(_Block3), _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+                "fsp3_line_lambda": (ctypes.c_int, [C, ctypes.POINTER(_Block3), _P, _P, _P, _P]),
+                "fsp3_rhs": (ctypes.c_int, [C, ctypes.POINTER(_Block3), _P, _P, _P, _P, ctypes.c_size_t, _P]),
+                "fsp3_rk3_step": (ctypes.c_int, [C, ctypes.POINTER(_Block3), _P, _P, ctypes.c_double, _P,
+                                                 ctypes.c_size_t, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -513,3 +525,59 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---- three dimensions (fsp3_*): state (5, nk, nj, ni), coordinates (nk, nj, ni), FP64 ----------
+def block3_of(Q: torch.Tensor, bc=(0, 0, 0, 0, 0, 0), period=((0.0,) * 3,) * 3) -> _Block3:
+    """The fsp3_block of a state or coordinate tensor whose last three extents are (nk, nj, ni)."""
+    nk, nj, ni = Q.shape[-3:]
+    b = _Block3()
+    b.ni, b.nj, b.nk = int(ni), int(nj), int(nk)
+    for f in range(6):
+        b.bc[f] = int(bc[f])
+    for a in range(3):
+        for c in range(3):
+            b.period[a][c] = float(period[a][c])
+    return b
+
+
+def workspace3(cfg: Config, blk: _Block3, device="cuda") -> torch.Tensor:
+    n = ctypes.c_size_t()
+    _check("fsp3_workspace_size", lib().fsp3_workspace_size(ctypes.byref(cfg._c()), ctypes.byref(blk), ctypes.byref(n)))
+    return torch.empty(int(n.value), dtype=torch.uint8, device=device)
+
+
+def metrics3(cfg: Config, blk: _Block3, x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, out=None, ws=None,
+             stream=None) -> torch.Tensor:
+    out = torch.empty((10, blk.nk + 2 * G, blk.nj + 2 * G, blk.ni + 2 * G), dtype=torch.float64,
+                      device=x.device) if out is None else out
+    ws = workspace3(cfg, blk, x.device) if ws is None else ws
+    _check("fsp3_metrics", lib().fsp3_metrics(ctypes.byref(cfg._c()), ctypes.byref(blk), _ptr(x.contiguous()),
+                                              _ptr(y.contiguous()), _ptr(z.contiguous()), _ptr(out), _ptr(ws),
+                                              ws.numel(), _stream(stream)))
+    return out
+
+
+def line_lambda3(cfg: Config, blk: _Block3, M: torch.Tensor, Q: torch.Tensor, stream=None):
+    """The xi, eta and zeta line maxima (without lf_alpha): shapes (nk, nj), (nk, ni), (nj, ni)."""
+    n = blk.nj * blk.nk + blk.ni * blk.nk + blk.ni * blk.nj
+    lam = torch.empty(n, dtype=torch.float64, device=Q.device)
+    _check("fsp3_line_lambda", lib().fsp3_line_lambda(ctypes.byref(cfg._c()), ctypes.byref(blk), _ptr(M), _ptr(Q),
+                                                      _ptr(lam), _stream(stream)))
+    a, b = blk.nj * blk.nk, blk.nj * blk.nk + blk.ni * blk.nk
+    return (lam[:a].view(blk.nk, blk.nj), lam[a:b].view(blk.nk, blk.ni), lam[b:].view(blk.nj, blk.ni))
+
+
+def rhs3(cfg: Config, blk: _Block3, M: torch.Tensor, Q: torch.Tensor, out=None, ws=None, stream=None):
+    out = torch.empty_like(Q) if out is None else out
+    ws = workspace3(cfg, blk, Q.device) if ws is None else ws
+    _check("fsp3_rhs", lib().fsp3_rhs(ctypes.byref(cfg._c()), ctypes.byref(blk), _ptr(M), _ptr(Q), _ptr(out),
+                                      _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def rk3_step3(cfg: Config, blk: _Block3, M: torch.Tensor, Q: torch.Tensor, dt: float, ws=None, stream=None):
+    ws = workspace3(cfg, blk, Q.device) if ws is None else ws
+    _check("fsp3_rk3_step", lib().fsp3_rk3_step(ctypes.byref(cfg._c()), ctypes.byref(blk), _ptr(M), _ptr(Q),
+                                                float(dt), _ptr(ws), ws.numel(), _stream(stream)))
+    return Q

@@ -1,4 +1,4 @@
-"""The binding's ctypes mirrors of fsp_config, fsp_block and fsp_link have the C layout of
+"""The binding's ctypes mirrors of fsp_config, fsp_block, fsp_link and fsp3_block have the C layout of
 include/fsp.h: gcc prints sizeof and offsetof of every field from the header, and the
 binding's structures must agree (CPU; a mismatch would hand the library shifted arguments)."""
 import ctypes
@@ -16,6 +16,7 @@ FIELDS = {
                                  "lf_alpha", "eps", "bc_state", "weights", "mid_split", "scheme_alpha"]),
     "fsp_block": (fsp._Block, ["ni", "nj", "ld", "period"]),
     "fsp_link": (fsp._Link, ["nbr", "face", "reversed", "offset"]),
+    "fsp3_block": (fsp._Block3, ["ni", "nj", "nk", "bc", "period"]),
 }
 
 

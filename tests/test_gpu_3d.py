@@ -1,0 +1,139 @@
+"""The three-dimensional CUDA path (fsp3_*) against the oracle's three-dimensional path,
+element by element on the same seeded inputs.  FP64 bar as in two dimensions: relative
+max-norm <= 1e-12 for metrics (the nine direction planes against their common maximum, J^-1
+against its own), right-hand sides and RK3 states; line maxima to 1e-13.  Extents are chosen
+so that the tiles of every direction end ragged (30 output nodes per tile line for the
+one-midpoint schemes, 29 for the two-midpoint ones; 8 xi lines and 16 eta or zeta lines per
+tile)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1810_11103_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+G = 4
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1810_11103_gb300 import build, fsp
+    build.build()
+    return fsp
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _case(shape=(40, 35, 33), seed=5, bc=(0,) * 6, smooth=True):
+    ni, nj, nk = shape
+    x, y, z, per = I.periodic_cube(ni, 8.0, 0.2, seed=seed, nj=nj, nk=nk)
+    if smooth:
+        q = I.vortex3(x, y, z, (4.0, 4.0), strength=4.0, free=(1.0, 0.7, -0.4, 0.3, 1.0), period=per)
+    else:
+        q = I.random_state3(x.shape, seed=seed + 1)
+    return x, y, z, per, q
+
+
+def _metrics(F, cfgd, blk, x, y, z):
+    cfg = F.Config.from_dict(cfgd)
+    M_o = O.metrics3(cfgd, x, y, z)
+    M_g = _host(F.metrics3(cfg, blk, _dev(x), _dev(y), _dev(z)))
+    assert np.abs(M_g[:9] - M_o[:9]).max() < TOL * np.abs(M_o[:9]).max()
+    assert np.abs(M_g[9] - M_o[9]).max() < TOL * np.abs(M_o[9]).max()
+    return M_o
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
+def test_metrics_and_rhs_parity_ragged_tiles(F, scheme):
+    x, y, z, per, q = _case()
+    cfgd = dict(scheme=scheme, period=per, bc=(0,) * 6)
+    blk = F.block3_of(_dev(x), (0,) * 6, per)
+    M = _metrics(F, cfgd, blk, x, y, z)
+    R_o = O.rhs3(cfgd, M, q)
+    R_g = _host(F.rhs3(F.Config.from_dict(cfgd), blk, _dev(M), _dev(q)))
+    assert _rel(R_g, R_o) < TOL, _rel(R_g, R_o)
+
+
+@pytest.mark.parametrize("scheme", [0, 3, 4])
+def test_rhs_parity_random_state_and_transmissive_faces(F, scheme):
+    """Every node independent (the weights far from linear), with transmissive faces in i and k."""
+    bc = (1, 1, 0, 0, 1, 1)
+    x, y, z, per, q = _case((36, 20, 30), seed=9, smooth=False)
+    cfgd = dict(scheme=scheme, period=per, bc=bc)
+    blk = F.block3_of(_dev(x), bc, per)
+    M = _metrics(F, cfgd, blk, x, y, z)
+    R_o = O.rhs3(cfgd, M, q)
+    R_g = _host(F.rhs3(F.Config.from_dict(cfgd), blk, _dev(M), _dev(q)))
+    assert _rel(R_g, R_o) < TOL, _rel(R_g, R_o)
+
+
+def test_line_maxima_parity(F):
+    x, y, z, per, q = _case((40, 35, 33))
+    cfgd = dict(scheme=2, period=per, bc=(0,) * 6)
+    blk = F.block3_of(_dev(x), (0,) * 6, per)
+    M = O.metrics3(cfgd, x, y, z)
+    lam = [l.cpu().numpy() for l in F.line_lambda3(F.Config.from_dict(cfgd), blk, _dev(M), _dev(q))]
+    for d in range(3):
+        ref = O.lambda3(cfgd, M, q, d) / 1.1
+        assert np.abs(lam[d] - ref).max() < 1e-13 * np.abs(ref).max(), d
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_rk3_parity(F, scheme):
+    x, y, z, per, q = _case((34, 31, 17), seed=11)
+    cfgd = dict(scheme=scheme, period=per, bc=(0,) * 6)
+    cfg = F.Config.from_dict(cfgd)
+    blk = F.block3_of(_dev(x), (0,) * 6, per)
+    M = O.metrics3(cfgd, x, y, z)
+    dt = 0.02
+    q_o = O.rk3_3(cfgd, M, q, dt, 2)
+    Q, Md = _dev(q), _dev(M)
+    ws = F.workspace3(cfg, blk)
+    for _ in range(2):
+        F.rk3_step3(cfg, blk, Md, Q, dt, ws=ws)
+    assert _rel(_host(Q), q_o) < TOL
+
+
+def test_free_stream_on_randomised_cube(F):
+    x, y, z, per = I.periodic_cube(48, 6.0, 0.2, seed=5, nj=40, nk=36)
+    q0 = np.array([1.0, 0.5, 0.3, -0.2, 2.5])
+    for scheme in range(5):
+        cfgd = dict(scheme=scheme, period=per, bc=(0,) * 6)
+        cfg = F.Config.from_dict(cfgd)
+        blk = F.block3_of(_dev(x), (0,) * 6, per)
+        Mg = F.metrics3(cfg, blk, _dev(x), _dev(y), _dev(z))
+        Q = _dev(q0[:, None, None, None] * np.ones((5,) + x.shape))
+        assert float(F.rhs3(cfg, blk, Mg, Q).abs().max()) < 1e-12, scheme
+
+
+def test_refusals(F):
+    x, y, z, per, q = _case((20, 16, 14))
+    blk = F.block3_of(_dev(x), (0,) * 6, per)
+    for bad, code in ((dict(scheme=2, precision=1), 2), (dict(scheme=2, weights=1), 2), (dict(scheme=7), 1)):
+        with pytest.raises(F.FspError) as e:
+            F.workspace3(F.Config.from_dict(bad), blk)
+        assert e.value.code == code, bad
+    cfg = F.Config.from_dict(dict(scheme=2))
+    for bc, code in (((2, 2, 0, 0, 0, 0), 2), ((0, 1, 0, 0, 0, 0), 1)):
+        with pytest.raises(F.FspError) as e:
+            F.workspace3(cfg, F.block3_of(_dev(x), bc, per))
+        assert e.value.code == code, bc
+    # a non-periodic direction needs 13 nodes (the reflected ghost coordinates)
+    xs, ys, zs, pers, _ = _case((20, 16, 12))
+    with pytest.raises(F.FspError):
+        F.workspace3(cfg, F.block3_of(_dev(xs), (0, 0, 0, 0, 1, 1), pers))
