@@ -56,6 +56,9 @@ def parse():
                     help="also measure the other two precisions and report them beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint cost measurement")
+    ap.add_argument("--three-d", action=argparse.BooleanOptionalAction, default=True,
+                    help="also measure the three-dimensional path (fsp3_*) on a 128^3 randomised periodic cube, "
+                         "WENOIU5-1MP, FP64")
     ap.add_argument("--seventh", action=argparse.BooleanOptionalAction, default=True,
                     help="also measure WENOIU7-1MP (the Appendix's seventh-order scheme) on the same workload, "
                          "FP64 and FP32")
@@ -370,6 +373,16 @@ class Ctx:
         t = self.torch.tensor(vals, dtype=self.torch.float64, device=self.dev)
         self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
         return tuple(float(v) for v in t)
+
+
+def launches_per_step(args, head):
+    """Kernels of one batched RK3 step: per stage an xi and an eta sweep, plus the line maxima of
+    every stage, or of the first only when the marching eta pass takes them (not in mixed
+    precision); the vortex workload's single-block step always has three."""
+    if args.workload != "cylinder64":
+        return 9
+    fused = (head.get("tiles") or {}).get("eta", {}).get("variant") == 3 and args.precision != "mixed"
+    return 7 if fused else 9
 
 
 def measure_cylinder(args, prec, C, per_block=False):
@@ -766,11 +779,51 @@ def profile_adjoint(args):
     print("profile run done: adjoint, 262144 nodes")
 
 
+def measure_3d(args, C, n=128, steps=10):
+    """The three-dimensional path (Sections 2.1-2.2, fsp3_*): a randomised periodic cube of n^3
+    nodes (A = 0.2, seed 1810) carrying the vortex about the z axis on the free stream (1, 1, 1,
+    1, 1), WENOIU5-1MP, FP64.  One step = one RK3 step (3 right-hand sides); the roofline is the
+    whole right-hand side (line maxima and the three sweeps, timed together through fsp3_rhs)
+    against the oracle's operation count per node.  State and metrics (290 MB) exceed L2."""
+    import numpy as np
+    torch, fsp = C.torch, C.fsp
+    from paper_1810_11103_gb300 import inputs as I
+    x, y, z, per = I.periodic_cube(n, 10.0, 0.2, seed=1810)
+    q = I.vortex3(x, y, z, (5.0, 5.0), strength=5.0, free=(1.0, 1.0, 1.0, 1.0, 1.0), period=per)
+    cfg = fsp.Config.from_dict(dict(scheme=2))
+
+    def dev(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=C.dev)
+
+    blk = fsp.block3_of(dev(x), (0,) * 6, per)
+    ws = fsp.workspace3(cfg, blk, C.dev)
+    M = fsp.metrics3(cfg, blk, dev(x), dev(y), dev(z), ws=ws)
+    Q, out = dev(q), torch.empty((5,) + x.shape, dtype=torch.float64, device=C.dev)
+    dt = 1e-4
+    for _ in range(max(3, args.warmup)):
+        fsp.rk3_step3(cfg, blk, M, Q, dt, ws=ws)
+    t = C.timed(lambda: fsp.rk3_step3(cfg, blk, M, Q, dt, ws=ws), steps)
+    t_rhs = C.timed(lambda: fsp.rhs3(cfg, blk, M, Q, out=out, ws=ws), steps) / steps
+    (t, t_rhs) = C.max_over_ranks(t, t_rhs)
+    with open(os.path.join(ROOT, "paper_1810_11103_gb300", "algorithmic_flops.json")) as f:
+        flops = json.load(f)["three_d"]["schemes"][SCHEME_NAMES[2]]["rhs_per_node"]
+    nodes = n ** 3
+    peak, _ = C.peak("fp64")
+    achieved = flops * nodes / t_rhs / 1e12
+    nominal = C.nominal("fp64", None)
+    return {"workload": f"{n}^3 randomised periodic cube (A = 0.2), vortex about z, WENOIU5-1MP, FP64, TVD-RK3",
+            "value": job_rhs(nodes, steps, C.world) / t / 1e6, "unit": UNIT, "ms_per_step": t / steps * 1e3,
+            "roofline": {"bound": "alu", "kernel": "fsp3_rhs (line maxima + xi, eta, zeta sweeps)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "nominal_peak": nominal, "frac_vs_nominal": achieved / nominal, "flops_per_node": flops,
+                         "rhs_ms": t_rhs * 1e3, "peak_source": "FP64 FMA probe (fsp_fma_peak) in this run"}}
+
+
 def _r(v, d=4):
     return None if v is None else float(f"{v:.{d}g}")
 
 
-def summary(args, head, others, adjoint, seventh):
+def summary(args, head, others, adjoint, seventh, three_d=None):
     """Compact per-path figures: Mcell-RHS/s, ms per RK3 step, the roofline kernel's fraction of
     the measured and of the nominal FMA rate, and the per-block loop with the batching gain."""
     out = {}
@@ -798,6 +851,9 @@ def summary(args, head, others, adjoint, seventh):
     if seventh is not None:
         out["wenoiu7"] = {p: {"value": _r(seventh[p]["value"]), "frac": _r(seventh[p]["roofline"]["frac"], 3)}
                           for p in ("fp64", "fp32")}
+    if three_d is not None:
+        out["three_d"] = {"value": _r(three_d["value"]), "ms_step": _r(three_d["ms_per_step"]),
+                          "frac": _r(three_d["roofline"]["frac"], 3)}
     return out
 
 
@@ -872,6 +928,7 @@ def main():
                           "roofline": {k: r["roofline"][k] for k in ("kernel", "achieved", "peak", "unit", "frac",
                                                                    "flops_per_node", "kernel_ms")},
                           "tiles": r["tiles"]}
+    three_d = measure_3d(args, C) if args.three_d and args.workload == "cylinder64" else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
@@ -879,8 +936,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic", "config": workload_config(args, head["nodes"], head["nblocks"]),
             "e2e": head["e2e"],
-            # per RK3 step: 3 x (line maxima, xi sweep, eta sweep) of all blocks
-            "gpu_launches": 9 * args.steps,
+            # per RK3 step of all blocks: 3 x (xi sweep, eta sweep) and the line maxima, one launch
+            # per stage, or only the first stage's with the marching eta pass (FP64, FP32), whose
+            # stages 1 and 2 take the next stage's maxima
+            "gpu_launches": launches_per_step(args, head) * args.steps,
             "roofline": head["roofline"],
             "clocks": head["clocks"],
         }
@@ -893,6 +952,8 @@ def main():
             line["accuracy"] = accuracy
         if seventh is not None:
             line["wenoiu7"] = seventh
+        if three_d is not None:
+            line["three_d"] = three_d
         if adjoint is not None:
             line["adjoint"] = adjoint
         for p, r in others.items():
@@ -903,7 +964,7 @@ def main():
         if "per_block" in head:
             line["per_block_" + args.precision] = head["per_block"]
         # ... and a compact summary of every path last
-        line["summary"] = summary(args, head, others, adjoint, seventh)
+        line["summary"] = summary(args, head, others, adjoint, seventh, three_d)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -89,6 +89,29 @@ def adjoint_counts(n_work: int = 512):
     return out
 
 
+def three_d_counts(n_work: int = 128):
+    """Per-node operations of one three-dimensional right-hand side (and of its xi, eta and
+    zeta sweeps) for an n_work^3 cube: a + b / n fits (every line of n nodes costs c1 n + c2)
+    of 24^3 and 32^3 randomised periodic cubes carrying the three-dimensional vortex, as the
+    bench's workload does (WENOIU5-1MP; with nonlinear weights the mapping's two sides differ
+    by a few operations, so the fit is exact up to the data's branch mix)."""
+    sizes = (24, 32)
+    per = {}
+    for n in sizes:
+        x, y, z, pr = I.periodic_cube(n, 10.0, 0.2, seed=1810)
+        q = I.vortex3(x, y, z, (5.0, 5.0), strength=5.0, free=(1.0, 1.0, 1.0, 1.0, 1.0), period=pr)
+        cfg = dict(scheme=2, period=pr, bc=(0,) * 6)
+        c = O.count_flops3(cfg, O.metrics3(cfg, x, y, z), q)
+        per[n] = {k: v / x.size for k, v in c.items()}
+    n0, n1 = sizes
+    e = {}
+    for k in ("rhs", "xi", "eta", "zeta"):
+        b = (per[n0][k] - per[n1][k]) / (1.0 / n0 - 1.0 / n1)
+        a = per[n1][k] - b / n1
+        e[k + "_per_node"] = a + b / n_work
+    return {NAMES[2]: e}
+
+
 def main():
     res = {"workload": "periodic vortex 256x256, randomised grid A=0.2, seed 1810",
            "how": "oracle with an operation-counting scalar; + - * / sqrt = 1 flop each",
@@ -100,6 +123,10 @@ def main():
                                   "48x48 and 64x64 periodic vortices, randomised grid A=0.2, seed 1810, eps 1e-6",
                       "how": "oracle reverse mode: forward + partial derivatives + dense reverse sweep",
                       "schemes": adjoint_counts()}
+    res["three_d"] = {"workload": "128^3 randomised periodic cube (A = 0.2, seed 1810) with the three-dimensional "
+                                  "vortex, from a + b/n fits of 24^3 and 32^3 cubes",
+                      "how": "oracle three-dimensional path with the operation-counting scalar",
+                      "schemes": three_d_counts()}
     with open(OUT, "w") as f:
         json.dump(res, f, indent=1)
     print(OUT)

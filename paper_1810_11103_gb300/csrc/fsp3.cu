@@ -230,12 +230,12 @@ struct Tile3 {
 // wave and two shear waves along t1 = (a x n)/|a x n|, a the coordinate axis least aligned with
 // n (ties to the larger index), and t2 = n x t1.
 struct Char3 {
-  double n[3], t1[3], t2[3], u[3];
+  double nx, ny, nz, t1x, t1y, t1z, t2x, t2y, t2z, ux, uy, uz;
   double c, ci, H, Un, U1, U2, b1, b2, h2;
   __device__ __forceinline__ void build(const double q[5], const double nn[3], double gamma) {
     const double ri = rcp_nr(q[0]);
-    u[0] = q[1] * ri; u[1] = q[2] * ri; u[2] = q[3] * ri;
-    h2 = 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    ux = q[1] * ri; uy = q[2] * ri; uz = q[3] * ri;
+    h2 = 0.5 * (ux * ux + uy * uy + uz * uz);
     const double p = (gamma - 1.0) * (q[4] - q[0] * h2);
     const double c2 = gamma * p * ri;
     ci = rsq(c2);
@@ -243,54 +243,51 @@ struct Char3 {
     H = (q[4] + p) * ri;
     b1 = (gamma - 1.0) * ci * ci;
     b2 = b1 * h2;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) n[a] = nn[a];
-    int ax = 2;
-    if (fabs(n[1]) < fabs(n[ax])) ax = 1;
-    if (fabs(n[0]) < fabs(n[ax])) ax = 0;
-    double x[3];
-    if (ax == 0) { x[0] = 0.0; x[1] = -n[2]; x[2] = n[1]; }
-    else if (ax == 1) { x[0] = n[2]; x[1] = 0.0; x[2] = -n[0]; }
-    else { x[0] = -n[1]; x[1] = n[0]; x[2] = 0.0; }
-    const double s = rsq(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) t1[a] = x[a] * s;
-    t2[0] = n[1] * t1[2] - n[2] * t1[1];
-    t2[1] = n[2] * t1[0] - n[0] * t1[2];
-    t2[2] = n[0] * t1[1] - n[1] * t1[0];
-    Un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
-    U1 = u[0] * t1[0] + u[1] * t1[1] + u[2] * t1[2];
-    U2 = u[0] * t2[0] + u[1] * t2[1] + u[2] * t2[2];
+    nx = nn[0]; ny = nn[1]; nz = nn[2];
+    // a x n for the least aligned axis a (ties to the later axis)
+    double x0, x1, x2;
+    const double ax = fabs(nx), ay = fabs(ny), az = fabs(nz);
+    if (ax < ay && ax < az) { x0 = 0.0; x1 = -nz; x2 = ny; }
+    else if (ay < az) { x0 = nz; x1 = 0.0; x2 = -nx; }
+    else { x0 = -ny; x1 = nx; x2 = 0.0; }
+    const double s = rsq(x0 * x0 + x1 * x1 + x2 * x2);
+    t1x = x0 * s; t1y = x1 * s; t1z = x2 * s;
+    t2x = ny * t1z - nz * t1y;
+    t2y = nz * t1x - nx * t1z;
+    t2z = nx * t1y - ny * t1x;
+    Un = ux * nx + uy * ny + uz * nz;
+    U1 = ux * t1x + uy * t1y + uz * t1z;
+    U2 = ux * t2x + uy * t2y + uz * t2z;
   }
   // left eigenvector row k applied to dq
   __device__ __forceinline__ double project(int k, const double dq[5]) const {
-    if (k == 2) return -U1 * dq[0] + t1[0] * dq[1] + t1[1] * dq[2] + t1[2] * dq[3];
-    if (k == 3) return -U2 * dq[0] + t2[0] * dq[1] + t2[1] * dq[2] + t2[2] * dq[3];
-    const double bu = b1 * (u[0] * dq[1] + u[1] * dq[2] + u[2] * dq[3]) - b1 * dq[4];
+    if (k == 2) return -U1 * dq[0] + t1x * dq[1] + t1y * dq[2] + t1z * dq[3];
+    if (k == 3) return -U2 * dq[0] + t2x * dq[1] + t2y * dq[2] + t2z * dq[3];
+    const double bu = b1 * (ux * dq[1] + uy * dq[2] + uz * dq[3]) - b1 * dq[4];
     if (k == 1) return (1.0 - b2) * dq[0] + bu;
     const double s = k == 0 ? 1.0 : -1.0;
-    const double nc = ci * (n[0] * dq[1] + n[1] * dq[2] + n[2] * dq[3]);
+    const double nc = ci * (nx * dq[1] + ny * dq[2] + nz * dq[3]);
     return 0.5 * ((b2 + s * Un * ci) * dq[0] - bu - s * nc);
   }
   // q += W_k times right eigenvector column k
   __device__ __forceinline__ void recon_add(int k, double Wk, double q[5]) const {
     if (k == 2) {
-      q[1] += Wk * t1[0]; q[2] += Wk * t1[1]; q[3] += Wk * t1[2]; q[4] += Wk * U1;
+      q[1] += Wk * t1x; q[2] += Wk * t1y; q[3] += Wk * t1z; q[4] += Wk * U1;
       return;
     }
     if (k == 3) {
-      q[1] += Wk * t2[0]; q[2] += Wk * t2[1]; q[3] += Wk * t2[2]; q[4] += Wk * U2;
+      q[1] += Wk * t2x; q[2] += Wk * t2y; q[3] += Wk * t2z; q[4] += Wk * U2;
       return;
     }
     if (k == 1) {
-      q[0] += Wk; q[1] += Wk * u[0]; q[2] += Wk * u[1]; q[3] += Wk * u[2]; q[4] += Wk * h2;
+      q[0] += Wk; q[1] += Wk * ux; q[2] += Wk * uy; q[3] += Wk * uz; q[4] += Wk * h2;
       return;
     }
     const double s = k == 0 ? -c : c;
     q[0] += Wk;
-    q[1] += Wk * (u[0] + s * n[0]);
-    q[2] += Wk * (u[1] + s * n[1]);
-    q[3] += Wk * (u[2] + s * n[2]);
+    q[1] += Wk * (ux + s * nx);
+    q[2] += Wk * (uy + s * ny);
+    q[3] += Wk * (uz + s * nz);
     q[4] += Wk * (H + s * Un);
   }
 };

@@ -53,3 +53,4 @@ def test_stored_counts_match_the_script():
         stored = json.load(f)
     assert CF.vortex_counts() == stored["schemes"]
     assert CF.adjoint_counts() == stored["adjoint"]["schemes"]
+    assert CF.three_d_counts() == stored["three_d"]["schemes"]
