@@ -74,12 +74,13 @@ def parse():
                          "choice on this workload), set without timing")
     ap.add_argument("--profile-dir", type=int, default=0, choices=[0, 1],
                     help="profiling run: the direction whose batched sweep is launched three times")
-    ap.add_argument("--profile", choices=list(PRECISIONS) + ["adjoint", "probe"], default=None,
+    ap.add_argument("--profile", choices=list(PRECISIONS) + ["adjoint", "probe", "three_d"], default=None,
                     help="profiling run for ncu: build the cylinder batch in this precision, evaluate one "
                          "right-hand side, launch one direction's batched sweep three times, then take one "
                          "RK3 step; 'adjoint': three "
                          "fsp_rhs_vjp calls on the 512 x 512 shock-vortex case; 'probe': the FP64 and the "
-                         "FP32 FMA probe once each, as the bench launches them; no timing")
+                         "FP32 FMA probe once each, as the bench launches them; 'three_d': the 3-D metrics and "
+                         "one 3-D right-hand side of the bench's 128^3 cube; no timing")
     ap.add_argument("--per-block", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the FP64 and FP32 steps as loops of per-block fsp_rk3_step calls")
     return ap.parse_args()
@@ -857,6 +858,29 @@ def summary(args, head, others, adjoint, seventh, three_d=None):
     return out
 
 
+def profile_three_d(args):
+    """Minimal launch sequence for a profiler: the three-dimensional metrics and one right-hand
+    side (line maxima, xi, eta and zeta sweeps) of the bench's 128^3 cube."""
+    import numpy as np
+    import torch
+    from paper_1810_11103_gb300 import build as B
+    B.build()
+    from paper_1810_11103_gb300 import fsp, inputs as I
+    x, y, z, per = I.periodic_cube(128, 10.0, 0.2, seed=1810)
+    q = I.vortex3(x, y, z, (5.0, 5.0), strength=5.0, free=(1.0, 1.0, 1.0, 1.0, 1.0), period=per)
+    cfg = fsp.Config.from_dict(dict(scheme=2))
+
+    def dev(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+    blk = fsp.block3_of(dev(x), (0,) * 6, per)
+    ws = fsp.workspace3(cfg, blk)
+    M = fsp.metrics3(cfg, blk, dev(x), dev(y), dev(z), ws=ws)
+    fsp.rhs3(cfg, blk, M, dev(q), ws=ws)
+    torch.cuda.synchronize()
+    print("profile run done: three_d, 2097152 nodes")
+
+
 def profile_probe(args):
     """Minimal launch sequence for a profiler: the FP64 FMA probe, then the FP32 one, each once
     with the launch shape of the bench's roofline peak."""
@@ -881,6 +905,9 @@ def main():
         return
     if args.profile == "probe":
         profile_probe(args)
+        return
+    if args.profile == "three_d":
+        profile_three_d(args)
         return
     if args.profile:
         profile_run(args, args.profile)
