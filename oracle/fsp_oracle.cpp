@@ -181,7 +181,7 @@ template <> inline long double cst<long double>(long double c) { return c; }
 // ----------------------------------------------------------------------------------
 // Scheme tables (Section 3).  All four variants, with the printed coefficients.
 // ----------------------------------------------------------------------------------
-enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3, S71 = 4 };
+enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3, S71 = 4, S74 = 5 };
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, BC_FARFIELD = 4,
        BC_LINK = 5 };
 
@@ -217,9 +217,11 @@ struct SchemeTab {
   long double hnode[7];   // h+ coefficient of f+_{j+k}, k = -3..3
   long double cnode[4];   // delta^{c,(1)}: a_k multiplying (f_{j+k} - f_{j-k}), k = 1..4
   long double cmid[2];    // delta^{c,(1)}: b_m multiplying (f~_{j+m} - f~_{j-m}), m = 1/2, 3/2
+  long double hmidx[2];   // four-midpoint scheme: h+ coefficient of f+_{j+1/2+m}, m = -2, +1
+  long double cmid3;      // four-midpoint scheme: b_{5/2}
 };
 
-static const SchemeTab TAB[5] = {
+static const SchemeTab TAB[6] = {
   // WENOIU3-1MP: h+ of Eq. (3.4); delta^{c,(1)} of Eq. (3.7).
   {2, {1.0L, 0.0L}, {0.0L, 0.0L, -1.0L / 24, 2.0L / 24, -1.0L / 24, 0.0L, 0.0L},
    {2.0L / 48, -1.0L / 48, 0.0L, 0.0L}, {1.0L, 0.0L}},
@@ -241,6 +243,12 @@ static const SchemeTab TAB[5] = {
    {-243.0L / 107520, 1990.0L / 107520, -7481.0L / 107520, 8164.0L / 107520, -341.0L / 107520,
     -2378.0L / 107520, 289.0L / 107520},
    {8841.0L / 107520, -6069.0L / 107520, 1261.0L / 107520, -121.5L / 107520}, {1.0L, 0.0L}},
+  // WENOIU7-4MP: h+ of the Appendix, scheme (3), f_{j+1/2} + [(18 f_{j-1} - 66 f_j - 108 f_{j+1})
+  // + (-3 f_{j-3/2} - 31 f_{j-1/2} + 179 f_{j+1/2} + 11 f_{j+3/2})] / 420; its delta^{c,(1)}:
+  // [3 (f_{j+2} - f_{j-2}) - 32 (f_{j+1} - f_{j-1})] / 140 + [-3 (f~_{j+5/2} - f~_{j-5/2})
+  // - 17 (f~_{j+3/2} - f~_{j-3/2}) + 1218 (f~_{j+1/2} - f~_{j-1/2})] / 840.
+  {4, {1.0L + 179.0L / 420, -31.0L / 420}, {0.0L, 0.0L, 18.0L / 420, -66.0L / 420, -108.0L / 420, 0.0L, 0.0L},
+   {-32.0L / 140, 3.0L / 140, 0.0L, 0.0L}, {1218.0L / 840, -17.0L / 840}, {-3.0L / 420, 11.0L / 420}, -3.0L / 840},
 };
 
 // The one-midpoint forms with their free parameter alpha (Eq. 3.5 for WENOIU3-1MP, Eq. 3.17
@@ -251,7 +259,7 @@ static const SchemeTab TAB[5] = {
 //   b_{1/2} = alpha,  a_d = (n_d - n_{d+1} + n_{1-d} - n_{-d}) / 2  (d = 1..4).
 // For alpha = 1 the printed coefficients of TAB are used as they stand.
 static SchemeTab scheme_tab(int scheme, long double alpha) {
-  if (alpha == 1.0L || scheme < 0 || scheme > 4) return TAB[scheme < 0 || scheme > 4 ? 0 : scheme];
+  if (alpha == 1.0L || scheme < 0 || scheme > 5) return TAB[scheme < 0 || scheme > 5 ? 0 : scheme];
   SchemeTab S = TAB[scheme];
   long double n[7] = {0, 0, 0, 0, 0, 0, 0};   // n[k + 3] = n_k
   const long double a = alpha;
@@ -329,7 +337,7 @@ static T interp_mid(int scheme, int interp, F phi) {
   if (interp == 1) return (phi(0) + phi(1)) * cst<T>(0.5L);
   if (scheme == S31 || scheme == S32)   // 4-point Lagrange
     return (cst<T>(-1) * phi(-1) + cst<T>(9) * phi(0) + cst<T>(9) * phi(1) - phi(2)) / cst<T>(16);
-  if (scheme == S71)                    // 8-point Lagrange
+  if (scheme == S71 || scheme == S74)   // 8-point Lagrange
     return (cst<T>(-5) * phi(-3) + cst<T>(49) * phi(-2) - cst<T>(245) * phi(-1) + cst<T>(1225) * phi(0)
             + cst<T>(1225) * phi(1) - cst<T>(245) * phi(2) + cst<T>(49) * phi(3) - cst<T>(5) * phi(4))
            / cst<T>(2048);
@@ -414,6 +422,7 @@ static T central_D(const Par<T>& P, const Coords<T>& C, int dir, int comp, int i
   // b_{1/2} (f~_{j+1/2} - f~_{j-1/2}) + b_{3/2} (f~_{j+3/2} - f~_{j-3/2})
   d = d + cst<T>(S.cmid[0]) * (mid(0) - mid(-1));
   if (S.cmid[1] != 0.0L) d = d + cst<T>(S.cmid[1]) * (mid(1) - mid(-2));
+  if (S.cmid3 != 0.0L) d = d + cst<T>(S.cmid3) * (mid(2) - mid(-3));
   return d;
 }
 
@@ -783,6 +792,8 @@ struct Field {
     rd(b, out);
   }
   void nodemet(int dir, int L, int s, T& mx, T& my) const {
+    const int n = dir == 0 ? P.ni : P.nj;
+    if (s < -G || s >= n + G) s = s - floordiv(s, n) * n;   // beyond the stored ghosts: periodic
     if (dir == 0) { mx = met(0, s, L); my = met(1, s, L); }
     else { mx = met(2, L, s); my = met(3, L, s); }
   }
@@ -812,15 +823,21 @@ static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
   const Par<T>& P = F.P;
   const SchemeTab& S = P.tab;
   const int n = dir == 0 ? P.ni : P.nj, nl = dir == 0 ? P.nj : P.ni;
-  const int NB = n + 8;           // nodes s = -4 .. n+3, stored at s + 4
-  const int NI = n + 3;           // interfaces p + 1/2, p = -2 .. n, stored at p + 2
+  // nodes s = -OFF .. n+OFF-1 (OFF = 4, or 6 for the four-midpoint scheme) at s + 4 of the
+  // arrays below (which start two nodes into their storage); interfaces p + 1/2, p = -nmp ..
+  // n-2+nmp, at p + 2 (one interface into the storage)
+  const bool four = S.hmidx[0] != 0.0L || S.hmidx[1] != 0.0L;
+  const int OFF = four ? 6 : 4;
+  const int NB = n + 12, NI = n + 5;
   const WenoOpt wo{P.ppm, P.linw, P.weights};
-  std::vector<T> q(4 * NB), mxs(NB), mys(NB), fp(4 * NB), fm(4 * NB);
-  std::vector<T> fpm(4 * NI), fmm(4 * NI), Hh(4 * NI);
+  std::vector<T> sq(4 * NB), smx(NB), smy(NB), sfp(4 * NB), sfm(4 * NB);
+  std::vector<T> sfpm(4 * NI), sfmm(4 * NI), sHh(4 * NI);
+  T *q = sq.data() + 8, *mxs = smx.data() + 2, *mys = smy.data() + 2, *fp = sfp.data() + 8, *fm = sfm.data() + 8;
+  T *fpm = sfpm.data() + 4, *fmm = sfmm.data() + 4, *Hh = sHh.data() + 4;
   for (int L = 0; L < nl; ++L) {
     const T A = line_lambda(F, dir, L);
     // node states, metrics and split fluxes f+- = (E^ +- A^ Q)/2
-    for (int s = -4; s < n + 4; ++s) {
+    for (int s = -OFF; s < n + OFF; ++s) {
       T qs[4], f[4];
       F.state(dir, L, s, qs);
       F.nodemet(dir, L, s, mxs[s + 4], mys[s + 4]);
@@ -834,7 +851,8 @@ static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
     // interfaces: characteristic WENO interpolation from each side, then split fluxes;
     // h at p + 1/2 (p = -1 .. n-1) uses midpoints p + 1/2 only (one-midpoint schemes) or
     // p - 1/2 .. p + 3/2 (two-midpoint schemes)
-    const int nmp = S.hmid[1] != 0.0L ? 2 : 1;
+    // (the four-midpoint scheme: p - 3/2 .. p + 5/2)
+    const int nmp = four ? 3 : S.hmid[1] != 0.0L ? 2 : 1;
     for (int p = -nmp; p <= n - 2 + nmp; ++p) {
       const int c0 = p + 4;                    // node p
       // characteristic direction from the averaged metrics (Section 3.4)
@@ -898,6 +916,10 @@ static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
           if (S.hmid[-m] == 0.0L) continue;
           hp = hp + cst<T>(S.hmid[-m]) * fpm[4 * (p + m + 2) + v];
           hm = hm + cst<T>(S.hmid[-m]) * fmm[4 * (p - m + 2) + v];
+        }
+        if (four) {   // f+_{p-3/2}, f+_{p+3/2} and their mirrors f-_{p+5/2}, f-_{p-1/2}
+          hp = hp + cst<T>(S.hmidx[0]) * fpm[4 * (p - 2 + 2) + v] + cst<T>(S.hmidx[1]) * fpm[4 * (p + 1 + 2) + v];
+          hm = hm + cst<T>(S.hmidx[0]) * fmm[4 * (p + 2 + 2) + v] + cst<T>(S.hmidx[1]) * fmm[4 * (p - 1 + 2) + v];
         }
         for (int k = -3; k <= 3; ++k) {
           if (S.hnode[k + 3] == 0.0L) continue;
@@ -993,6 +1015,8 @@ static void advect_rhs(int scheme, int N, double dx, const std::vector<double>& 
     double hp = 0.0;
     for (int m = 0; m >= -1; --m)
       if (S.hmid[-m] != 0.0L) hp += (double)S.hmid[-m] * fmid[(size_t)(((p + m) % N + N) % N)];
+    if (S.hmidx[0] != 0.0L) hp += (double)S.hmidx[0] * fmid[(size_t)(((p - 2) % N + N) % N)];
+    if (S.hmidx[1] != 0.0L) hp += (double)S.hmidx[1] * fmid[(size_t)(((p + 1) % N + N) % N)];
     for (int k = -3; k <= 3; ++k)
       if (S.hnode[k + 3] != 0.0L) hp += (double)S.hnode[k + 3] * U(p + k);
     h[p] = hp;
@@ -1117,7 +1141,10 @@ static int check(const int* ip, int ni, int nj) {
   if (ni < 1 || nj < 1) return 1;
   for (int f = 0; f < 4; ++f)
     if (ip[4 + f] < 0 || ip[4 + f] > BC_FARFIELD) return 5;   // links need the multi-block entry
-  if (ip[0] < 0 || ip[0] > 4) return 2;
+  if (ip[0] < 0 || ip[0] > 5) return 2;
+  // the four-midpoint scheme reaches six nodes beyond a face (its midpoint fluxes from j - 5/2
+  // to j + 5/2): periodic directions only, whose ghost metrics wrap
+  if (ip[0] == S74 && (ip[4] != BC_PERIODIC || ip[6] != BC_PERIODIC)) return 6;
   if (ip[8] < 0 || ip[8] > 1 || ip[9] < 0 || ip[9] > 2) return 7;
   if ((ip[4] == BC_PERIODIC) != (ip[5] == BC_PERIODIC)) return 3;
   if ((ip[6] == BC_PERIODIC) != (ip[7] == BC_PERIODIC)) return 3;
@@ -1165,7 +1192,7 @@ namespace orc {
 template <class T>
 static int mb_setup(const int* ip, const double* dp, int nb, const int* dims, const int* bcs, const int* lk,
                     const double* loff, std::vector<Par<T>>& P, std::vector<Link>& L) {
-  if (nb < 1) return 1;
+  if (nb < 1 || ip[0] == S74) return 1;
   P.resize(nb);
   L.resize(4 * (size_t)nb);
   for (int b = 0; b < nb; ++b) {
@@ -1357,17 +1384,20 @@ void orc_eig(double gamma, const double* q, double nx, double ny, double* L, dou
     for (int b = 0; b < 4; ++b) { L[4 * a + b] = Lm[a][b]; R[4 * a + b] = Rm[a][b]; }
 }
 
-void orc_scheme_table(int scheme, double alpha, double* out /* r, hmid[2], hnode[7], cnode[4], cmid[2] */) {
+void orc_scheme_table(int scheme, double alpha,
+                      double* out /* r, hmid[2], hnode[7], cnode[4], cmid[2], hmidx[2], cmid3 */) {
   const SchemeTab S = scheme_tab(scheme, alpha);
   out[0] = S.r;
   for (int k = 0; k < 2; ++k) out[1 + k] = (double)S.hmid[k];
   for (int k = 0; k < 7; ++k) out[3 + k] = (double)S.hnode[k];
   for (int k = 0; k < 4; ++k) out[10 + k] = (double)S.cnode[k];
   for (int k = 0; k < 2; ++k) out[14 + k] = (double)S.cmid[k];
+  for (int k = 0; k < 2; ++k) out[16 + k] = (double)S.hmidx[k];
+  out[18] = (double)S.cmid3;
 }
 
 int orc_advect1d(int scheme, int N, double tfinal, double* out) {
-  if (scheme < 0 || scheme > 4 || N < 7) return 1;
+  if (scheme < 0 || scheme > 5 || N < 7) return 1;
   advect1d(scheme, N, tfinal, out);
   return 0;
 }
@@ -1375,14 +1405,14 @@ int orc_advect1d(int scheme, int N, double tfinal, double* out) {
 // The same with dt = 2 / ceil(2 / dx^dt_exp) (dt_exp = 7/4 keeps the RK4 error below the
 // seventh-order spatial error).
 int orc_advect1d_dt(int scheme, int N, double tfinal, double dt_exp, double* out) {
-  if (scheme < 0 || scheme > 4 || N < 7 || !(dt_exp > 0.0)) return 1;
+  if (scheme < 0 || scheme > 5 || N < 7 || !(dt_exp > 0.0)) return 1;
   advect1d(scheme, N, tfinal, out, dt_exp);
   return 0;
 }
 
 // The same with the weight option (weights = 1: WENO-Z).
 int orc_advect1d_opts(int scheme, int N, double tfinal, double dt_exp, int weights, double* out) {
-  if (scheme < 0 || scheme > 4 || N < 7 || !(dt_exp > 0.0) || weights < 0 || weights > 1) return 1;
+  if (scheme < 0 || scheme > 5 || N < 7 || !(dt_exp > 0.0) || weights < 0 || weights > 1) return 1;
   advect1d(scheme, N, tfinal, out, dt_exp, weights);
   return 0;
 }

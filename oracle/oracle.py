@@ -4,7 +4,8 @@ Builds ``_build/libfsp_oracle.so`` from ``fsp_oracle.cpp`` with g++ (``-O2
 -ffp-contract=off``, no OpenMP: the oracle runs on one core) and exposes numpy-level
 functions.  The configuration is a plain dict with the keys
 
-    scheme          0..3 = WENOIU3-1MP, WENOIU3-2MP, WENOIU5-1MP, WENOIU5-2MP
+    scheme          0..5 = WENOIU3-1MP, WENOIU3-2MP, WENOIU5-1MP, WENOIU5-2MP, WENOIU7-1MP,
+                    WENOIU7-4MP (the last on periodic grids only)
     interp          0 = order-matched Lagrange midpoint interpolation, 1 = 2-point average
     ppm             1 = piecewise-polynomial mapping of the weights (Eqs. 3.15/3.23)
     linear_weights  1 = omega_k = C_k (linear interpolation)
@@ -138,7 +139,7 @@ def _params(cfg):
     """ip = (scheme, interp, ppm, linear_weights, bc[4], weights, mid_split); dp = (gamma,
     lf_alpha, eps, bc_state[4][4], scheme_alpha)."""
     alpha = float(cfg.get("scheme_alpha", 1.0))
-    if alpha != 1.0 and cfg.get("scheme", 2) in (1, 3):
+    if alpha != 1.0 and cfg.get("scheme", 2) in (1, 3, 5):
         raise ValueError("oracle: the two-midpoint schemes have no free parameter")
     ip = np.array([cfg.get("scheme", 2), cfg.get("interp", 0), cfg.get("ppm", 1),
                    cfg.get("linear_weights", 0)] + list(cfg.get("bc", (0, 0, 0, 0)))
@@ -335,11 +336,14 @@ def eig(gamma, q, nx, ny):
 
 def scheme_table(scheme, alpha=1.0):
     """r, h+ midpoint coefficients (m = 0, -1), h+ node coefficients of f_{j+k} (k = -3..3),
-    central-operator node coefficients a_k (k = 1..4) and midpoint coefficients (1/2, 3/2);
-    alpha: the free parameter of the one-midpoint forms."""
-    out = np.empty(16)
+    central-operator node coefficients a_k (k = 1..4) and midpoint coefficients (1/2, 3/2); for
+    the four-midpoint scheme also the h+ coefficients of f_{j+1/2+m}, m = -2, +1 (hmidx) and the
+    central operator's 5/2 coefficient (cmid3); alpha: the free parameter of the one-midpoint
+    forms."""
+    out = np.empty(19)
     lib().orc_scheme_table(int(scheme), float(alpha), _dp(out))
-    return {"r": int(out[0]), "hmid": out[1:3], "hnode": out[3:10], "cnode": out[10:14], "cmid": out[14:16]}
+    return {"r": int(out[0]), "hmid": out[1:3], "hnode": out[3:10], "cnode": out[10:14], "cmid": out[14:16],
+            "hmidx": out[16:18], "cmid3": float(out[18])}
 
 
 def smoothness4(u7):

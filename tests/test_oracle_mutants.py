@@ -26,6 +26,7 @@ FLO = "test_oracle_flops.py::"
 VJP = "test_oracle_vjp.py::"
 OPT = "test_oracle_options.py::"
 D3 = "test_oracle_3d.py::"
+W74 = "test_oracle_weno7_4mp.py::"
 
 # (name, text in the oracle, planted replacement, pins that catch it: tests/ node ids)
 MUTANTS = [
@@ -178,6 +179,14 @@ MUTANTS = [
      [OPT + "test_midpoint_splittings_are_consistent[1]", OPT + "test_midpoint_splittings_sod[1]"]),
     ("vl_energy", "(gamma * gamma - cst<T>(1))", "(gamma * gamma + cst<T>(1))",
      [OPT + "test_midpoint_splittings_are_consistent[2]", OPT + "test_midpoint_splittings_upwind_limits"]),
+    # the four-midpoint seventh-order scheme (Appendix, scheme (3))
+    ("s74_node_digit", "-108.0L / 420", "-106.0L / 420",
+     [W74 + "test_h_reproduces_the_flux_through_degree_six", W74 + "test_printed_central_operator_is_the_central_part_of_h"]),
+    ("s74_mirror_index", "cst<T>(S.hmidx[0]) * fmm[4 * (p + 2 + 2) + v]", "cst<T>(S.hmidx[0]) * fmm[4 * (p - 2 + 2) + v]",
+     [W74 + "test_design_order_on_a_curved_grid"]),
+    ("s74_central_b52", "if (S.cmid3 != 0.0L) d = d + cst<T>(S.cmid3) * (mid(2) - mid(-3));",
+     "if (S.cmid3 != 0.0L) d = d + cst<T>(S.cmid3) * (mid(2) - mid(-2));",
+     [W74 + "test_free_stream_and_conservation"]),
     # three dimensions (Sections 2.1-2.2)
     ("d3_metric_sign", "(dprod(b, a, p, q) - dprod(a, b, p, q) + dprod(a, b, q, p) - dprod(b, a, q, p))",
      "(dprod(b, a, p, q) + dprod(a, b, p, q) + dprod(a, b, q, p) - dprod(b, a, q, p))",
