@@ -65,8 +65,15 @@ typedef enum {
  * one-midpoint scheme of the Appendix (scheme (1) with alpha = 1: Table A1 candidates, the
  * fourth-order mapping, an eighth-order central operator and eight-point midpoint metrics;
  * its smoothness indicators are those of Eq. 3.22's definition applied to the cubics of
- * Table A1).  Every scheme has the adjoint entry points. */
-enum { FSP_WENOIU3_1MP = 0, FSP_WENOIU3_2MP = 1, FSP_WENOIU5_1MP = 2, FSP_WENOIU5_2MP = 3, FSP_WENOIU7_1MP = 4 };
+ * Table A1).  The adjoint entry points cover these five. */
+/* FSP_WENOIU7_4MP: the Appendix's scheme (3), four midpoints j - 3/2 .. j + 3/2 in h+ and an
+ * eighth-order central operator with midpoint terms to 5/2.  Its midpoint fluxes reach from
+ * j - 5/2 to j + 5/2, six nodes beyond a face, while every stored array carries FSP_G = 4 ghost
+ * layers: it is built for periodic blocks (ghost metrics wrap) in FP64 and FP32 through the
+ * single-block entry points; other faces, FSP_FP32_MIXED, the batch, the adjoint and the
+ * three-dimensional path return FSP_ERR_UNSUPPORTED. */
+enum { FSP_WENOIU3_1MP = 0, FSP_WENOIU3_2MP = 1, FSP_WENOIU5_1MP = 2, FSP_WENOIU5_2MP = 3, FSP_WENOIU7_1MP = 4,
+       FSP_WENOIU7_4MP = 5 };
 /* Arithmetic of the right-hand side.  Metrics are FP64 in every mode.
  * FSP_FP64        everything in double.
  * FSP_FP32        state, WENO and fluxes in float (metrics rounded to float on load); the

@@ -566,7 +566,9 @@ VjpWs vjp_ws(const fsp_config& c, const fsp_block& b, size_t fwd_bytes) {
   return L;
 }
 
-bool adjoint_options(const fsp_config& c) { return c.weights == 0 && c.mid_split == 0 && scheme_alpha_of(c) == 1.0; }
+bool adjoint_options(const fsp_config& c) {
+  return c.scheme != S74 && c.weights == 0 && c.mid_split == 0 && scheme_alpha_of(c) == 1.0;
+}
 
 Params params_of(const fsp_config& c, const fsp_block& b, const double* metrics) {
   return make_params(c, b, metrics);
@@ -787,6 +789,7 @@ fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const do
                            const double* metrics_bar, double* x_bar, double* y_bar, void* stream) {
   size_t fwd = 0;
   if (fsp_status s = fsp_workspace_size(cfg, blk, &fwd)) return s;
+  if (cfg->scheme == S74) return FSP_ERR_UNSUPPORTED;   // its operator reaches 6 nodes (the weights hold 4)
   if (!dptr(x) || !dptr(y) || !dptr(metrics_bar) || !dptr(x_bar) || !dptr(y_bar)) return FSP_ERR_INVALID_ARG;
   W9 w;
   central_weights(cfg->scheme, cfg->interp, scheme_alpha_of(*cfg), w.w);

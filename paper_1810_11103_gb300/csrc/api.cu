@@ -46,7 +46,7 @@ bool device_pointer(const void* p) {
 
 fsp_status check_cfg(const fsp_config* c, const fsp_block* b) {
   if (!c || !b) return FSP_ERR_INVALID_ARG;
-  if (c->scheme < 0 || c->scheme > 4) return FSP_ERR_INVALID_ARG;
+  if (c->scheme < 0 || c->scheme > 5) return FSP_ERR_INVALID_ARG;
   if (c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED) return FSP_ERR_INVALID_ARG;
   if (c->interp < 0 || c->interp > 1) return FSP_ERR_INVALID_ARG;
   for (int f = 0; f < 4; ++f)
@@ -55,6 +55,10 @@ fsp_status check_cfg(const fsp_config* c, const fsp_block* b) {
   if ((c->bc[2] == FSP_BC_PERIODIC) != (c->bc[3] == FSP_BC_PERIODIC)) return FSP_ERR_INVALID_ARG;
   if (!(c->gamma > 1.0) || !(c->lf_alpha > 0.0) || !(c->eps > 0.0)) return FSP_ERR_INVALID_ARG;
   if (fsp_status s = check_options(*c)) return s;
+  // the four-midpoint scheme reaches six nodes beyond a face: periodic blocks only, and one
+  // precision (its h is not regrouped for the mixed path)
+  if (c->scheme == S74 && (c->bc[0] != FSP_BC_PERIODIC || c->bc[2] != FSP_BC_PERIODIC)) return FSP_ERR_UNSUPPORTED;
+  if (c->scheme == S74 && c->precision == FSP_FP32_MIXED) return FSP_ERR_UNSUPPORTED;
   if (b->ni < 1 || b->nj < 1 || b->ld < b->ni) return FSP_ERR_INVALID_ARG;
   if (c->bc[0] != FSP_BC_PERIODIC && b->ni < 9) return FSP_ERR_INVALID_ARG;
   if (c->bc[2] != FSP_BC_PERIODIC && b->nj < 9) return FSP_ERR_INVALID_ARG;
@@ -104,7 +108,7 @@ fsp_status check_options(const fsp_config& c) {
   if (c.weights < 0 || c.weights > 1 || c.mid_split < 0 || c.mid_split > 2) return FSP_ERR_INVALID_ARG;
   const double a = scheme_alpha_of(c);
   if (!(a > 0.0) || !(a < 1e6)) return FSP_ERR_INVALID_ARG;
-  if (a != 1.0 && (c.scheme == S32 || c.scheme == S52)) return FSP_ERR_INVALID_ARG;   // no free parameter
+  if (a != 1.0 && (c.scheme == S32 || c.scheme == S52 || c.scheme == S74)) return FSP_ERR_INVALID_ARG;   // no free parameter
   if (c.mid_split != 0 && c.precision == FSP_FP32_MIXED) return FSP_ERR_UNSUPPORTED;
   return FSP_OK;
 }

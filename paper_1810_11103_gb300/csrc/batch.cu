@@ -229,10 +229,11 @@ size_t acc_elem(int prec) { return prec == FSP_FP32 ? 4 : 8; }
 
 fsp_status check_batch(const fsp_config* c, int nb, const fsp_block* blk, const int* bc, const fsp_link* lk) {
   if (!c || nb < 1 || !blk || !bc || !lk) return FSP_ERR_INVALID_ARG;
-  if (c->scheme < 0 || c->scheme > 4 || c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED ||
+  if (c->scheme < 0 || c->scheme > 5 || c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED ||
       c->interp < 0 || c->interp > 1 || !(c->gamma > 1.0) || !(c->lf_alpha > 0.0) || !(c->eps > 0.0))
     return FSP_ERR_INVALID_ARG;
   if (fsp_status s = check_options(*c)) return s;
+  if (c->scheme == S74) return FSP_ERR_UNSUPPORTED;   // six ghost layers: linked faces provide four
   for (int b = 0; b < nb; ++b) {
     const fsp_block& B = blk[b];
     if (B.ni < 1 || B.nj < 1 || B.ld < B.ni || B.ni > 8 * 65535 || B.nj > 2 * 65535) return FSP_ERR_INVALID_ARG;

@@ -532,11 +532,11 @@ bool dptr3(const void* p) {
 
 fsp_status check3(const fsp_config* c, const fsp3_block* b) {
   if (!c || !b) return FSP_ERR_INVALID_ARG;
-  if (c->scheme < 0 || c->scheme > 4 || c->interp < 0 || c->interp > 1 || !(c->gamma > 1.0) || !(c->lf_alpha > 0.0) ||
+  if (c->scheme < 0 || c->scheme > 5 || c->interp < 0 || c->interp > 1 || !(c->gamma > 1.0) || !(c->lf_alpha > 0.0) ||
       !(c->eps > 0.0) || c->precision < FSP_FP64 || c->precision > FSP_FP32_MIXED)
     return FSP_ERR_INVALID_ARG;
   if (fsp_status s = check_options(*c)) return s;
-  if (c->precision != FSP_FP64 || !default_options(*c)) return FSP_ERR_UNSUPPORTED;
+  if (c->precision != FSP_FP64 || !default_options(*c) || c->scheme == S74) return FSP_ERR_UNSUPPORTED;
   for (int a = 0; a < 3; ++a) {
     const int n = a == 0 ? b->ni : a == 1 ? b->nj : b->nk;
     const int f0 = b->bc[2 * a], f1 = b->bc[2 * a + 1];

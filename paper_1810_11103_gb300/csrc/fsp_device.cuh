@@ -10,7 +10,7 @@ namespace fsp {
 
 constexpr int G = 4;  // ghost layers of the stored metrics
 
-enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3, S71 = 4 };
+enum { S31 = 0, S32 = 1, S51 = 2, S52 = 3, S71 = 4, S74 = 5 };
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_SLIPWALL = 3, BC_FARFIELD = 4,
        BC_LINK = 5 };
 
@@ -68,6 +68,17 @@ template <> struct Scheme<S71> {
   }
 };
 
+// WENOIU7-4MP (Appendix, scheme (3)): h+ = f_{j+1/2} + [(18 f_{j-1} - 66 f_j - 108 f_{j+1}) +
+// (-3 f_{j-3/2} - 31 f_{j-1/2} + 179 f_{j+1/2} + 11 f_{j+3/2})] / 420.  m0, m1 multiply
+// f_{j+1/2}, f_{j-1/2}; mA, mB multiply f_{j-3/2}, f_{j+3/2} (nmp = 4: four midpoints).
+template <> struct Scheme<S74> {
+  static constexpr int r = 4, nmp = 4;
+  static constexpr double m0 = 1.0 + 179.0 / 420, m1 = -31.0 / 420, mA = -3.0 / 420, mB = 11.0 / 420;
+  __host__ __device__ static constexpr double hn(int k) {
+    return k == -1 ? 18.0 / 420 : k == 0 ? -66.0 / 420 : k == 1 ? -108.0 / 420 : 0.0;
+  }
+};
+
 // The h+ coefficients of a scheme at its free parameter alpha (the one-midpoint forms: Eq. 3.5
 // for WENOIU3-1MP, Eq. 3.17 for WENOIU5-1MP, the Appendix's scheme (1) for WENOIU7-1MP; alpha =
 // 1 is the printed scheme): m0, m1 multiply f+_{j+1/2}, f+_{j-1/2}; hn[k + 3] multiplies f+_{j+k}.
@@ -92,6 +103,10 @@ inline void scheme_coefs(int scheme, double a, double& m0, double& m1, double hn
       m0 = Scheme<S52>::m0; m1 = Scheme<S52>::m1;
       for (int k = 0; k < 7; ++k) hn[k] = Scheme<S52>::hn(k - 3);
       break;
+    case S74:   // no free parameter (its four midpoint coefficients are compile-time constants)
+      m0 = Scheme<S74>::m0; m1 = Scheme<S74>::m1;
+      for (int k = 0; k < 7; ++k) hn[k] = Scheme<S74>::hn(k - 3);
+      break;
     default:
       m0 = a; hn[0] = 5 * a / 1024 - 1.0 / 140; hn[1] = -21 * a / 512 + 5.0 / 84; hn[2] = 175 * a / 1024 - 101.0 / 420;
       hn[3] = -175 * a / 256 + 319.0 / 420; hn[4] = -525 * a / 1024 + 107.0 / 210; hn[5] = 35 * a / 512 - 19.0 / 210;
@@ -104,13 +119,15 @@ inline void scheme_coefs(int scheme, double a, double& m0, double& m1, double hn
 // Central operator delta^{c,(1)} of each scheme (Eq. 2.7), used for the metrics:
 //   D f_j = sum_k a_k (f_{j+k} - f_{j-k}) + b_{1/2}(f~_{j+1/2} - f~_{j-1/2})
 //           + b_{3/2}(f~_{j+3/2} - f~_{j-3/2}),  k = 1..4
-struct Central { double a1, a2, a3, b12, b32, a4; };
+struct Central { double a1, a2, a3, b12, b32, a4, b52; };
 __host__ __device__ inline Central central_of(int scheme) {
   switch (scheme) {
     case S31: return {2.0 / 48, -1.0 / 48, 0.0, 1.0, 0.0};              // Eq. (3.7)
     case S32: return {2.0 / 12, 0.0, 0.0, 11.0 / 12, -1.0 / 12};        // Eq. (3.9)
     case S51: return {17.0 / 256, -13.0 / 320, 19.0 / 3840, 1.0, 0.0};  // Eq. (3.19)
     case S52: return {-4.0 / 60, 1.0 / 60, 0.0, 19.0 / 15, -1.0 / 15};  // Eq. (3.21)
+    case S74:   // the Appendix's operator of WENOIU7-4MP, midpoints to 5/2
+      return {-32.0 / 140, 3.0 / 140, 0.0, 1218.0 / 840, -17.0 / 840, 0.0, -3.0 / 840};
     default:  // the Appendix's eighth-order operator of WENOIU7-1MP
       return {8841.0 / 107520, -6069.0 / 107520, 1261.0 / 107520, 1.0, 0.0, -121.5 / 107520};
   }
@@ -120,7 +137,7 @@ __host__ __device__ inline Central central_of(int scheme) {
 // coefficients are a_d = (n_d - n_{d+1} + n_{1-d} - n_{-d}) / 2 and whose midpoint coefficient is
 // alpha.  alpha = 1 gives the printed operators above.
 inline Central central_of(int scheme, double alpha) {
-  if (alpha == 1.0 || scheme == S32 || scheme == S52) return central_of(scheme);
+  if (alpha == 1.0 || scheme == S32 || scheme == S52 || scheme == S74) return central_of(scheme);
   double m0, m1, hn[7];
   scheme_coefs(scheme, alpha, m0, m1, hn);
   auto n = [&](int k) { return k < -3 || k > 3 ? 0.0 : hn[k + 3]; };

@@ -70,8 +70,19 @@ __device__ __forceinline__ double central_diff(const Central& c, int interp, int
   return d;
 }
 
+// The four-midpoint scheme's operator: node terms to +-2 and midpoint terms to 5/2, with the
+// eight-point interpolation, from 13 nodal values f[k] = f_{j+k-6}; midpoint j + m + 1/2 uses
+// f_{j+m-3} .. f_{j+m+4} = f[m+3 .. m+10].
+__device__ __forceinline__ double central_diff13(const Central& c, int interp, const double* f) {
+  double d = c.a1 * (f[7] - f[5]) + c.a2 * (f[8] - f[4]);
+  d += c.b12 * (mid_interp8(interp, f + 3) - mid_interp8(interp, f + 2));
+  d += c.b32 * (mid_interp8(interp, f + 4) - mid_interp8(interp, f + 1));
+  d += c.b52 * (mid_interp8(interp, f + 5) - mid_interp8(interp, f + 0));
+  return d;
+}
+
 // Points of the midpoint interpolation of a scheme.
-inline int interp_points(int scheme) { return scheme == S71 ? 8 : scheme >= S51 ? 6 : 4; }
+inline int interp_points(int scheme) { return scheme == S71 || scheme == S74 ? 8 : scheme >= S51 ? 6 : 4; }
 
 __global__ void metrics_kernel(CoordParams C, Central cen, int interp, int pts, double* __restrict__ M) {
   const int W = C.ni + 2 * G, H = C.nj + 2 * G;
@@ -79,16 +90,27 @@ __global__ void metrics_kernel(CoordParams C, Central cen, int interp, int pts, 
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % W) - G, j = (int)(t / W) - G;
-    double fx[9], fy[9], gx[9], gy[9];
+    // nodal values at offsets -6..6 (the four-midpoint scheme reaches 6; the others use -4..4)
+    double fx[13], fy[13], gx[13], gy[13];
+    const bool wide = cen.b52 != 0.0;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      coord(C, i + k - 4, j, fx[k], fy[k]);   // along xi
-      coord(C, i, j + k - 4, gx[k], gy[k]);   // along eta
+    for (int k = 0; k < 13; ++k) {
+      if (!wide && (k < 2 || k > 10)) { fx[k] = fy[k] = gx[k] = gy[k] = 0.0; continue; }
+      coord(C, i + k - 6, j, fx[k], fy[k]);   // along xi
+      coord(C, i, j + k - 6, gx[k], gy[k]);   // along eta
     }
-    const double x_xi = central_diff(cen, interp, pts, fx);
-    const double y_xi = central_diff(cen, interp, pts, fy);
-    const double x_eta = central_diff(cen, interp, pts, gx);
-    const double y_eta = central_diff(cen, interp, pts, gy);
+    double x_xi, y_xi, x_eta, y_eta;
+    if (wide) {
+      x_xi = central_diff13(cen, interp, fx);
+      y_xi = central_diff13(cen, interp, fy);
+      x_eta = central_diff13(cen, interp, gx);
+      y_eta = central_diff13(cen, interp, gy);
+    } else {
+      x_xi = central_diff(cen, interp, pts, fx + 2);
+      y_xi = central_diff(cen, interp, pts, fy + 2);
+      x_eta = central_diff(cen, interp, pts, gx + 2);
+      y_eta = central_diff(cen, interp, pts, gy + 2);
+    }
     M[0 * plane + t] = y_eta;
     M[1 * plane + t] = -x_eta;
     M[2 * plane + t] = -y_xi;

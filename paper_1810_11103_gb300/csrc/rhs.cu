@@ -74,6 +74,7 @@ cudaError_t rhs_fp64(int scheme, const Params& P, const void* Q, const double* l
     case S32: return rhs_passes<S32, double, double>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
     case S51: return rhs_passes<S51, double, double>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
     case S52: return rhs_passes<S52, double, double>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
+    case S74: return rhs_passes<S74, double, double>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
     default:  return rhs_passes<S71, double, double>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
   }
 }
@@ -87,6 +88,7 @@ cudaError_t flux_difference_fp64(int scheme, const Params& P, const void* Q, con
     case S32: return flux_difference_passes<S32, double, double>(P, q, lam, dir, mode, a, out, st);
     case S51: return flux_difference_passes<S51, double, double>(P, q, lam, dir, mode, a, out, st);
     case S52: return flux_difference_passes<S52, double, double>(P, q, lam, dir, mode, a, out, st);
+    case S74: return flux_difference_passes<S74, double, double>(P, q, lam, dir, mode, a, out, st);
     default:  return flux_difference_passes<S71, double, double>(P, q, lam, dir, mode, a, out, st);
   }
 }

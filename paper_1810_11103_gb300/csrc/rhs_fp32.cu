@@ -20,6 +20,10 @@ static cudaError_t rhs_f32(int scheme, const Params& P, const void* Q, const dou
     case S32: return rhs_passes<S32, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
     case S51: return rhs_passes<S51, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
     case S52: return rhs_passes<S52, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
+    case S74:   // one precision only (the mixed regrouping of h is not built for four midpoints)
+      if constexpr (std::is_same<Acc, float>::value)
+        return rhs_passes<S74, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
+      return cudaErrorNotSupported;
     default:  return rhs_passes<S71, float, Acc>(P, q, lx, le, r, o, mode, qn, ca, cb, dt, st);
   }
 }
@@ -41,6 +45,10 @@ static cudaError_t fd_f32(int scheme, const Params& P, const void* Q, const doub
     case S32: return flux_difference_passes<S32, float, Acc>(P, q, lam, dir, mode, a, out, st);
     case S51: return flux_difference_passes<S51, float, Acc>(P, q, lam, dir, mode, a, out, st);
     case S52: return flux_difference_passes<S52, float, Acc>(P, q, lam, dir, mode, a, out, st);
+    case S74:
+      if constexpr (std::is_same<Acc, float>::value)
+        return flux_difference_passes<S74, float, Acc>(P, q, lam, dir, mode, a, out, st);
+      return cudaErrorNotSupported;
     default:  return flux_difference_passes<S71, float, Acc>(P, q, lam, dir, mode, a, out, st);
   }
 }

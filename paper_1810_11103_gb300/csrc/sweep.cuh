@@ -171,9 +171,13 @@ struct TileShape {
   static constexpr int NL = shape_nl(DIR, V);       // grid lines per CTA
   static constexpr int W = 256 / NL;                 // interface slots per line
   static constexpr int NMP = Scheme<S>::nmp;
-  static constexpr int T = W - NMP - 1;              // output nodes per line
-  static constexpr int NP = T + 8;                   // staged nodes per line
-  static constexpr int PLO = -NMP;                   // first interface p (of p + 1/2)
+  // the four-midpoint scheme: h at p + 1/2 takes the midpoints p - 3/2 .. p + 5/2, whose
+  // stencils reach six nodes beyond the outputs; the others reach four
+  static constexpr bool FOUR = NMP == 4;
+  static constexpr int OFF = FOUR ? 6 : 4;           // staged ghost nodes on each side
+  static constexpr int T = FOUR ? W - 5 : W - NMP - 1;   // output nodes per line
+  static constexpr int NP = T + 2 * OFF;             // staged nodes per line
+  static constexpr int PLO = FOUR ? -3 : -NMP;       // first interface p (of p + 1/2)
   static constexpr int THREADS = 256;
   static constexpr int NN = NL * NP, NW = NL * W;
   static constexpr int NO = NL * T;                  // output nodes
@@ -181,7 +185,7 @@ struct TileShape {
   // f+- (8 Acc per interface, two-midpoint schemes), A^ per line
   static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(NN); }
   static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * (size_t)NW; }
-  static constexpr size_t o_a() { return o_f() + (NMP == 2 ? MidStore<Real, Acc>::bytes(NW) : 0); }
+  static constexpr size_t o_a() { return o_f() + (NMP >= 2 ? MidStore<Real, Acc>::bytes(NW) : 0); }
   static constexpr size_t base_bytes() { return (o_a() + sizeof(Acc) * NL + 15) / 16 * 16; }
   // epilogue operands prefetched per output node: the other direction's difference (modes
   // 1, 2), Q^n (mode 2), J^-1 (modes 1, 2); 16-byte aligned after the base regions
@@ -235,7 +239,7 @@ inline void tile_dims(int scheme, int dir, int& T, int& NL, int variant = 0) {
   if (dir == 0 && variant == MARCH) { NL = MARCH_WARPS; T = MARCH_SEG; return; }
   if (dir == 1 && variant == MARCH) { NL = 32; T = 8 * 8 - (2 * nmp - 1); return; }   // EW = 8
   NL = shape_nl(dir, variant);
-  T = 256 / NL - nmp - 1;
+  T = scheme == S74 ? 256 / NL - 5 : 256 / NL - nmp - 1;
 }
 
 // Asynchronous global-to-shared copies (cp.async, 4 or 8 bytes).
@@ -638,6 +642,34 @@ __device__ __forceinline__ void h_combine(const Staged<Real, Acc>& st, const At&
 }
 
 
+// h at p + 1/2 for the four-midpoint scheme (same precision only): h+ = m0 f+_{p+1/2} +
+// m1 f+_{p-1/2} + mA f+_{p-3/2} + mB f+_{p+3/2} + sum_k n_k f+_{p+k} and h- its mirror about
+// p + 1/2 (f-_{p+1/2}, f-_{p+3/2}, f-_{p+5/2}, f-_{p-1/2}; f-_{p+1-k}), from the records of
+// the interfaces p - 2 .. p + 2 (mids[m + 2] = interface p + m) and the staged 2 f+- (halved
+// coefficients).
+template <int S, typename Real, typename Acc, typename At>
+__device__ __forceinline__ void h_combine4(const Staged<Real, Acc>& st, const At& at, const Mid<Real, Acc>* mids,
+                                           Acc h[4]) {
+  static_assert(!Staged<Real, Acc>::SPLIT, "the four-midpoint scheme is built for one precision");
+  using Sc = Scheme<S>;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    h[v] = Acc(0.5 * Sc::m0) * (mids[2].f[0][v] + mids[2].f[1][v]) +
+           Acc(0.5 * Sc::m1) * (mids[1].f[0][v] + mids[3].f[1][v]) +
+           Acc(0.5 * Sc::mA) * (mids[0].f[0][v] + mids[4].f[1][v]) +
+           Acc(0.5 * Sc::mB) * (mids[3].f[0][v] + mids[1].f[1][v]);
+  }
+#pragma unroll
+  for (int kk = -3; kk <= 3; ++kk) {
+    if (Sc::hn(kk) == 0.0) continue;
+    Acc a[4], b[4];
+    ld4(st.fp, st.n, at(kk), a);
+    ld4(st.fm, st.n, at(1 - kk), b);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) h[v] += Acc(0.5 * Sc::hn(kk)) * (a[v] + b[v]);
+  }
+}
+
 // One tile (bx along the lines, by across them) of one block.  qtab: every block's state
 // for linked faces (null for a lone block).
 template <int S, int DIR, int MODE, typename Real, typename Acc, int V = 0>
@@ -648,7 +680,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
                                            int bx, int by) {
   using Sh = TileShape<S, DIR, Real, Acc, V>;
   using Sc = Scheme<S>;
-  constexpr int NL = Sh::NL, W = Sh::W, T = Sh::T, NP = Sh::NP, PLO = Sh::PLO;
+  constexpr int NL = Sh::NL, W = Sh::W, T = Sh::T, NP = Sh::NP, PLO = Sh::PLO, OFF = Sh::OFF;
   constexpr int NN = Sh::NN, NW = Sh::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Staged<Real, Acc> st;
@@ -708,12 +740,14 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
       const int s = DIR == 0 ? k % NP : k / NL;
       const int line = line0 + l;
       if (line >= nlines) continue;
-      const int g = min(base + s - 4, n + 3);
+      const int g = min(base + s - OFF, n + OFF - 1);
+      // beyond the stored ghost metrics (the four-midpoint scheme, periodic only): wrap
+      const int gm = (Sh::FOUR && (g < -G || g >= n + G)) ? pmod(g, n) : g;
       Real q[4];
       load_state(P, Q, DIR, line, g, q, qtab);
       double mx, my;
-      if (DIR == 0) { mx = met_at(P, 0, g, line); my = met_at(P, 1, g, line); }
-      else          { mx = met_at(P, 2, line, g); my = met_at(P, 3, line, g); }
+      if (DIR == 0) { mx = met_at(P, 0, gm, line); my = met_at(P, 1, gm, line); }
+      else          { mx = met_at(P, 2, line, gm); my = met_at(P, 3, line, gm); }
       NodeChar<Real> w;
       Acc amx, amy, fp[4], fm[4];
       node_split<weno_scale<Sc::r>(), Real, Acc>(q, mx, my, gamma, Acc(0.5) * sA[l], w, amx, amy, fp, fm);
@@ -730,10 +764,11 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const int s = DIR == 0 ? k % NP : k / NL;
     const int line = line0 + l;
     if (k >= NN || line >= nlines) continue;
-    const int g = min(base + s - 4, n + 3);  // positions past n+3 are never used
+    const int g = min(base + s - OFF, n + OFF - 1);  // positions past n+OFF-1 are never used
+    const int gm = (Sh::FOUR && (g < -G || g >= n + G)) ? pmod(g, n) : g;
     load_state(P, Q, DIR, line, g, qv[r], qtab);
-    if (DIR == 0) { mxv[r] = met_at(P, 0, g, line); myv[r] = met_at(P, 1, g, line); }
-    else          { mxv[r] = met_at(P, 2, line, g); myv[r] = met_at(P, 3, line, g); }
+    if (DIR == 0) { mxv[r] = met_at(P, 0, gm, line); myv[r] = met_at(P, 1, gm, line); }
+    else          { mxv[r] = met_at(P, 2, line, gm); myv[r] = met_at(P, 3, line, gm); }
   }
   __syncthreads();  // A^ in shared memory
 #pragma unroll
@@ -757,9 +792,10 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     const int pi = DIR == 0 ? k % W : k / NL;
     const int line = line0 + l;
     const int p = PLO + pi;
-    // one-midpoint schemes use interfaces -1 .. T-1 (the last slot is spare)
-    if (line >= nlines || base + p > n || (Sc::nmp == 1 && p > T - 1)) continue;
-    const int c0 = p + 4;  // staged position of node p
+    // one-midpoint schemes use interfaces -1 .. T-1 (the last slot is spare); the
+    // four-midpoint scheme's h at n - 1/2 reads the interface n + 3/2
+    if (line >= nlines || base + p > n + (Sh::FOUR ? 1 : 0) || (Sc::nmp == 1 && p > T - 1)) continue;
+    const int c0 = p + OFF;  // staged position of node p
     auto at = [&](int m) { return SI(l, c0 + m); };
     Mid<Real, Acc> mo;
     interface_mid<S, Real, Acc>(st, at, gamma, eps, P.ppm, P.linw, P.interp, sA[l], mo, P.wz, P.msplit);
@@ -772,24 +808,35 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     }
   }
 
-  if constexpr (Sc::nmp == 2) {
+  if constexpr (Sc::nmp >= 2) {
     __syncthreads();
-    // h+ uses f+ at p+1/2 and p-1/2; h- uses f- at p+1/2 and p+3/2
+    // h+ uses f+ at p+1/2 and p-1/2; h- uses f- at p+1/2 and p+3/2 (four midpoints: also
+    // f+ at p-3/2, p+3/2 and f- at p+5/2, p-1/2)
     for (int k = threadIdx.x; k < NW; k += Sh::THREADS) {
       const int l = DIR == 0 ? k / W : k % NL;
       const int pi = DIR == 0 ? k % W : k / NL;
       const int line = line0 + l;
       const int p = PLO + pi;
       if (line >= nlines || p < -1 || p > T - 1 || base + p > n - 1) continue;
-      const int c0 = p + 4;
+      const int c0 = p + OFF;
       auto at = [&](int m) { return SI(l, c0 + m); };
-      Mid<Real, Acc> c, lo, hi;
-      sF.get(WI(l, pi), 0, c);
-      sF.get(WI(l, pi), 1, c);
-      sF.get(WI(l, pi - 1), 0, lo);
-      sF.get(WI(l, pi + 1), 1, hi);
       Acc h[4];
-      h_combine<S, Real, Acc, true>(st, at, sA[l], c, lo, hi, h, P);
+      if constexpr (Sh::FOUR) {
+        Mid<Real, Acc> mids[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          sF.get(WI(l, pi - 2 + m), 0, mids[m]);
+          sF.get(WI(l, pi - 2 + m), 1, mids[m]);
+        }
+        h_combine4<S, Real, Acc>(st, at, mids, h);
+      } else {
+        Mid<Real, Acc> c, lo, hi;
+        sF.get(WI(l, pi), 0, c);
+        sF.get(WI(l, pi), 1, c);
+        sF.get(WI(l, pi - 1), 0, lo);
+        sF.get(WI(l, pi + 1), 1, hi);
+        h_combine<S, Real, Acc, true>(st, at, sA[l], c, lo, hi, h, P);
+      }
       st4(sH, NW, WI(l, pi), h[0], h[1], h[2], h[3]);
     }
   }
@@ -816,7 +863,7 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Real* __restri
     } else {
       cp_async_wait_all();
       Real qs[4];
-      if constexpr (MODE == MODE_STAGE) ld4(st.q, st.n, SI(l, s + 4), qs);
+      if constexpr (MODE == MODE_STAGE) ld4(st.q, st.n, SI(l, s + OFF), qs);
       const Acc mJ = -recip(from_f64<Acc>(sJ[k]));
 #pragma unroll
       for (int v = 0; v < 4; ++v) {

@@ -19,7 +19,7 @@ import torch
 
 G = 4
 FP64, FP32 = 0, 1
-WENOIU3_1MP, WENOIU3_2MP, WENOIU5_1MP, WENOIU5_2MP, WENOIU7_1MP = 0, 1, 2, 3, 4
+WENOIU3_1MP, WENOIU3_2MP, WENOIU5_1MP, WENOIU5_2MP, WENOIU7_1MP, WENOIU7_4MP = 0, 1, 2, 3, 4, 5
 BC_PERIODIC, BC_TRANSMISSIVE, BC_DIRICHLET, BC_SLIPWALL, BC_FARFIELD, BC_LINK = 0, 1, 2, 3, 4, 5
 FP32_MIXED = 2
 

@@ -95,7 +95,11 @@ def test_argument_validation_on_the_host(so):
         co = fsp.Config(**dict(dict(scheme=2, bc=(0, 0, 0, 0)), **opt))
         assert _ws_code(fsp, co, 16, 16) == 0
         assert fsp.lib().fsp_vjp_workspace_size(ctypes.byref(co._c()), ctypes.byref(b), ctypes.byref(n)) == 2
-    assert _ws_code(fsp, fsp.Config(scheme=5, bc=(0, 0, 0, 0)), 16, 16) == 1
+    assert _ws_code(fsp, fsp.Config(scheme=6, bc=(0, 0, 0, 0)), 16, 16) == 1
+    # WENOIU7-4MP: periodic blocks only, one precision
+    assert _ws_code(fsp, fsp.Config(scheme=5, bc=(0, 0, 0, 0)), 16, 16) == 0
+    assert _ws_code(fsp, fsp.Config(scheme=5, bc=(1, 1, 0, 0)), 16, 16) == 2
+    assert _ws_code(fsp, fsp.Config(scheme=5, bc=(0, 0, 0, 0), precision=2), 16, 16) == 2
     # the state check refuses a host pointer for its result
     one = (ctypes.c_longlong * 1)()
     assert fsp.lib().fsp_check_state(ctypes.byref(per._c()), ctypes.byref(b), None, one, None) == 1
