@@ -361,6 +361,17 @@ fsp_status fsp_batch_flux_difference(fsp_batch* b, int dir, void* const* D, void
 /* One TVD-RK3 step of every block in lockstep; launches the captured graph when one was
  * captured for this dt. */
 fsp_status fsp_batch_rk3_step(fsp_batch* b, double dt, void* stream);
+/* fsp_batch_rk3_step end to end from host memory: copies each block's state from the host
+ * array q_in[b] to the bound device state, takes one step as fsp_batch_rk3_step, and copies
+ * the new state to q_out[b] (host arrays of nblocks host pointers, each 4*nj*ld elements in
+ * the state layout and precision; q_in may equal q_out).  Blocks whose states lie the same
+ * distance apart on the device and in both host arrays, under 512 bytes beyond each block's
+ * end, are copied as one range including the padding between them, which the caller owns
+ * on both sides.  Stream-ordered: q_out holds the result once the stream has completed (with
+ * pageable host memory the copies also block the calling thread).  FSP_ERR_INVALID_ARG for
+ * a null or device pointer or an unbound handle. */
+fsp_status fsp_batch_rk3_step_host(fsp_batch* b, const void* const* q_in, void* const* q_out, double dt,
+                                   void* stream);
 /* Runs one step, then records one RK3 step (9 kernels, 3 memsets) as a CUDA graph that
  * later fsp_batch_rk3_step calls with the same dt launch as a whole.  The eager step
  * advances the state like any other step. */

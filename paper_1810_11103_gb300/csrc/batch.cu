@@ -10,6 +10,7 @@
 // balances the uneven blocks.  The whole RK3 step can be captured once as a CUDA graph.
 // Line maxima of the splitting are taken per block line.
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -203,6 +204,7 @@ struct fsp_batch {
   void** d_tab = nullptr;            // pointer tables, nb entries each (see Tab)
   bool bound = false;
   std::vector<double*> M;
+  std::vector<char*> Q;              // bound states (device)
   cudaGraphExec_t gexec = nullptr;
   double gdt = 0.0;
 };
@@ -418,6 +420,8 @@ fsp_status fsp_batch_bind(fsp_batch* h, const double* const* x, const double* co
   const int nb = h->nb;
   std::vector<void*> tab((size_t)T_COUNT * nb, nullptr);
   h->M.assign(metrics, metrics + nb);
+  h->Q.resize(nb);
+  for (int b = 0; b < nb; ++b) h->Q[b] = (char*)Q[b];
   for (int b = 0; b < nb; ++b) {
     h->params[b].met = metrics[b];
     h->coords[b].x = x[b];
@@ -560,6 +564,47 @@ fsp_status fsp_batch_rk3_step(fsp_batch* h, double dt, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (h->gexec && dt == h->gdt) return cudaGraphLaunch(h->gexec, st) == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
   return batch_rk3(h, dt, st);
+}
+
+fsp_status fsp_batch_rk3_step_host(fsp_batch* h, const void* const* q_in, void* const* q_out, double dt,
+                                   void* stream) {
+  if (!h || !h->bound || !q_in || !q_out) return FSP_ERR_INVALID_ARG;
+  const int nb = h->nb;
+  for (int b = 0; b < nb; ++b) {
+    if (!q_in[b] || !q_out[b]) return FSP_ERR_INVALID_ARG;
+    cudaPointerAttributes a;
+    for (const void* p : {q_in[b], (const void*)q_out[b]}) {
+      if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return FSP_ERR_INVALID_ARG; }
+      if (a.type == cudaMemoryTypeDevice) return FSP_ERR_INVALID_ARG;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t es = state_size(h->cfg.precision);
+  // Runs of blocks whose states sit the same distance apart on the device and in both host
+  // arrays, less than 512 bytes beyond each block's end, move as one copy (padding included).
+  auto copy_runs = [&](bool in) -> bool {
+    for (int b = 0; b < nb;) {
+      const char* hs = in ? (const char*)q_in[b] : (const char*)q_out[b];
+      size_t len = 4 * (size_t)h->blk[b].nj * h->blk[b].ld * es;
+      int e = b + 1;
+      for (; e < nb; ++e) {
+        const ptrdiff_t gd = h->Q[e] - h->Q[e - 1];
+        const ptrdiff_t gi = (const char*)q_in[e] - (const char*)q_in[e - 1];
+        const ptrdiff_t go = (const char*)q_out[e] - (const char*)q_out[e - 1];
+        const size_t prev = 4 * (size_t)h->blk[e - 1].nj * h->blk[e - 1].ld * es;
+        if (gd != gi || gd != go || gd < (ptrdiff_t)prev || gd >= (ptrdiff_t)(prev + 512)) break;
+        len = (size_t)(h->Q[e] - h->Q[b]) + 4 * (size_t)h->blk[e].nj * h->blk[e].ld * es;
+      }
+      const cudaError_t r = in ? cudaMemcpyAsync(h->Q[b], hs, len, cudaMemcpyHostToDevice, st)
+                               : cudaMemcpyAsync((char*)q_out[b], h->Q[b], len, cudaMemcpyDeviceToHost, st);
+      if (r != cudaSuccess) return false;
+      b = e;
+    }
+    return true;
+  };
+  if (!copy_runs(true)) return FSP_ERR_CUDA;
+  if (fsp_status s = fsp_batch_rk3_step(h, dt, stream)) return s;
+  return copy_runs(false) ? FSP_OK : FSP_ERR_CUDA;
 }
 
 fsp_status fsp_batch_capture_graph(fsp_batch* h, double dt, void* stream) {

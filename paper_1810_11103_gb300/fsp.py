@@ -143,6 +143,8 @@ def lib():
                 "fsp_batch_metrics": (ctypes.c_int, [_P, _P]),
                 "fsp_batch_rhs": (ctypes.c_int, [_P, ctypes.POINTER(_P), _P]),
                 "fsp_batch_rk3_step": (ctypes.c_int, [_P, ctypes.c_double, _P]),
+                "fsp_batch_rk3_step_host": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_double,
+                                                           _P]),
                 "fsp_batch_flux_difference": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), _P]),
                 "fsp_batch_capture_graph": (ctypes.c_int, [_P, ctypes.c_double, _P]),
                 "fsp_batch_tune": (ctypes.c_int, [_P, ctypes.c_char_p, _P]),
@@ -495,6 +497,24 @@ class Batch:
     def rk3_step(self, dt: float, stream=None):
         _check("fsp_batch_rk3_step", lib().fsp_batch_rk3_step(self._h, float(dt), _stream(stream)))
         return self.Q
+
+    def rk3_step_host(self, dt: float, host_in: torch.Tensor, host_out: torch.Tensor, stream=None):
+        """One step from and to host memory in one library call (fsp_batch_rk3_step_host):
+        host_in and host_out are CPU tensors laid out like Qflat (pinned for asynchronous
+        copies); host_out holds the new states once the stream has completed."""
+        for t in (host_in, host_out):
+            if t.device.type != "cpu" or t.dtype != self.Qflat.dtype or t.numel() != self.Qflat.numel() \
+                    or not t.is_contiguous():
+                raise ValueError("host buffers must be contiguous CPU tensors shaped and typed like Qflat")
+        key = (host_in.data_ptr(), host_out.data_ptr())
+        if getattr(self, "_host_key", None) != key:       # the pointer tables of the last pair
+            offs = [q.data_ptr() - self.Qflat.data_ptr() for q in self.Q]
+            self._host_tabs = tuple((ctypes.c_void_p * self.n)(*[p + o for o in offs]) for p in key)
+            self._host_key = key
+        pin, pout = self._host_tabs
+        _check("fsp_batch_rk3_step_host", lib().fsp_batch_rk3_step_host(self._h, pin, pout, float(dt),
+                                                                        _stream(stream)))
+        return host_out
 
     def capture_graph(self, dt: float, stream=None):
         _check("fsp_batch_capture_graph", lib().fsp_batch_capture_graph(self._h, float(dt), _stream(stream)))

@@ -126,6 +126,7 @@ def test_batch_argument_validation_on_the_host(so):
     blk[1] = fsp._block_shape(cfg, 16, 12)
     assert L.fsp_batch_create(ctypes.byref(cfg._c()), 2, blk, bad, links, ctypes.byref(h)) == 1
     assert not h.value
+    assert L.fsp_batch_rk3_step_host(None, None, None, 1e-3, None) == 1     # no handle
 
 
 def _prototypes():

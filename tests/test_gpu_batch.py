@@ -319,3 +319,76 @@ def test_batch_flat_state_round_trip(F):
         off = (q.data_ptr() - bt.Qflat.data_ptr()) // q.element_size()
         assert torch.equal(out[off:off + q.numel()].view(q.shape), q.cpu())
         assert not torch.equal(q.cpu(), host[off:off + q.numel()].view(q.shape))   # the step changed it
+
+
+def test_batch_rk3_step_host(F):
+    """fsp_batch_rk3_step_host equals the device step bit for bit: with the host arrays laid
+    out like Qflat (merged copies), pinned or pageable, in place, and with each block in a
+    host tensor of its own (one copy per block); device pointers are refused."""
+    import ctypes
+    blocks, states, free = _small_cylinder()
+    cfgd = _cfgd(free, 2)
+    qs = _perturbed(states, 5, 0.01)
+    dt = 2e-4
+    ref = F.Batch(F.Config.from_dict(cfgd), blocks, qs)
+    ref.metrics()
+    ref.rk3_step(dt)
+    want = ref.Qflat.cpu()
+    ref.close()
+    bt = F.Batch(F.Config.from_dict(cfgd), blocks, qs)
+    bt.metrics()
+    start = bt.Qflat.cpu()
+    for pinned, inplace in ((True, False), (False, False), (True, True)):
+        hin = start.clone().pin_memory() if pinned else start.clone()
+        hout = hin if inplace else torch.full_like(hin, np.nan)
+        bt.Qflat.fill_(np.nan)                                 # the step must start from hin
+        bt.rk3_step_host(dt, hin, hout)
+        torch.cuda.synchronize()
+        assert torch.equal(hout, want), (pinned, inplace)
+    # separate host tensors per block: one copy each
+    other = F.Batch(F.Config.from_dict(cfgd), blocks, qs)
+    sep_in = [q.cpu().clone() for q in other.Q]
+    other.close()
+    sep_out = [torch.empty_like(q) for q in sep_in]
+    tab = lambda ts: (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+    rc = F.lib().fsp_batch_rk3_step_host(bt._h, tab(sep_in), tab(sep_out), dt, None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    for q, o in zip(bt.Q, sep_out):
+        off = (q.data_ptr() - bt.Qflat.data_ptr()) // q.element_size()
+        assert torch.equal(o.view(-1), want[off:off + q.numel()])
+    dev = (ctypes.c_void_p * bt.n)(*[q.data_ptr() for q in bt.Q])
+    assert F.lib().fsp_batch_rk3_step_host(bt._h, dev, tab(sep_out), dt, None) == 1
+    with pytest.raises(ValueError):
+        bt.rk3_step_host(dt, bt.Qflat, start)
+    bt.close()
+
+
+def test_batch_full_size_cylinder_rk3(F):
+    """One RK3 step of the 64-block cylinder at full size (5,923,840 nodes) as the bench runs it
+    end to end: tuned tiles, the captured graph, host copies through fsp_batch_rk3_step_host;
+    against the oracle's multi-block step on the same metrics, at the bench's CFL 0.3 step."""
+    blocks, states, free = I.cylinder_blocks()
+    qs = _perturbed(states, 13, 0.02)
+    cfgd = _cfgd(free, 2)
+    cfg = F.Config.from_dict(cfgd)
+    Ms = O.mb_metrics(cfgd, blocks)
+    bt = F.Batch(cfg, blocks, qs)
+    for k in range(len(blocks)):
+        bt.M[k].copy_(torch.as_tensor(Ms[k]))
+    bt.tune()
+    dt = min(float(F.cfl_dt(F.Config.from_dict(dict(cfgd, bc=[1 if c == 5 else c for c in b["bc"]])),
+                            bt.M[k], bt.Q[k], 0.3).item()) for k, b in enumerate(blocks))
+    host = bt.Qflat.cpu().pin_memory()
+    bt.capture_graph(dt)                           # an eager step, then the graph
+    out = torch.empty_like(host).pin_memory()
+    bt.rk3_step_host(dt, host, out)
+    torch.cuda.synchronize()
+    q1 = O.mb_rk3(cfgd, blocks, Ms, qs, dt, 1)
+    got = []
+    for q in bt.Q:
+        off = (q.data_ptr() - bt.Qflat.data_ptr()) // q.element_size()
+        got.append(out[off:off + q.numel()].view(q.shape).numpy())
+    assert _maxrel([g - q for g, q in zip(got, qs)], [a - q for a, q in zip(q1, qs)]) < 1e-11
+    assert _maxrel(got, q1) < TOL
+    bt.close()

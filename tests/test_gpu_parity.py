@@ -221,6 +221,24 @@ def test_full_size_riemann_1024_parity(F):
     _check_case(F, _cfg(scheme=2, bc=(1, 1, 1, 1)), x, y, q)
 
 
+def test_full_size_riemann_1024_rk3(F):
+    """One TVD-RK3 step of the 1024 x 1024 Riemann grid at CFL 0.5 (the single-block
+    workload at full size), FP64: the state and its change over the step."""
+    x, y = I.riemann_grid(1024, 0.3, 1811)
+    q = I.riemann_quadrants(x, y)
+    cfgd = _cfg(scheme=2, bc=(1, 1, 1, 1))
+    cfg = F.Config.from_dict(cfgd)
+    M = O.metrics(cfgd, x, y)
+    Mg, Q = _dev(M), _dev(q)
+    ws = F.workspace(cfg, Q)
+    dt = float(F.cfl_dt(cfg, Mg, Q, 0.5, ws=ws).item())
+    assert abs(dt - O.cfl_dt(cfgd, M, q, 0.5)) < 1e-13 * dt
+    F.rk3_step(cfg, Mg, Q, dt, ws=ws)
+    q_o = O.rk3(cfgd, M, q, dt, 1)
+    assert _rel(_host(Q) - q, q_o - q) < 1e-11
+    assert _rel(_host(Q), q_o) < TOL_RHS
+
+
 @pytest.mark.parametrize("shape", [(9, 2 * 65535), (8 * 65535, 9)])
 def test_rhs_parity_longest_lines(F, shape):
     # the largest line counts the sweep grids allow (65535 CTAs across the lines of the xi
