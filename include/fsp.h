@@ -315,6 +315,15 @@ fsp_status fsp_fma_peak(int precision, int blocks, int iters, void* sink, void* 
 fsp_status fsp_round_to_float(const double* in, float* out_int, float* out_hw, long long n, void* stream);
 
 /*
+ * fsp_widen_to_double -- diagnostic of the mixed path's float-to-double widening: for each of
+ * the n floats in[k] (device), out_int[k] receives the widening done with integer operations
+ * (exact; subnormals, infinities and NaN through the hardware) and out_hw[k]
+ * the hardware conversion.  They agree bit for bit.  No counterpart in the paper.
+ * FSP_ERR_INVALID_ARG for n < 0 or a pointer that is not device memory.
+ */
+fsp_status fsp_widen_to_double(const float* in, double* out_int, double* out_hw, long long n, void* stream);
+
+/*
  * ---- Multi-block grids --------------------------------------------------------------
  * The paper's motivating case (Section 1): many structured blocks, of uneven sizes,
  * joined face to face.  The blocks partition the nodes of one larger grid: behind a face

@@ -32,6 +32,18 @@ cudaError_t launch_round_to_float(const double* in, float* oi, float* oh, long l
   return cudaGetLastError();
 }
 
+__global__ void widen_to_double_kernel(const float* in, double* oi, double* oh, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    oi[k] = to_f64_int(in[k]);
+    oh[k] = (double)in[k];
+  }
+}
+
+cudaError_t launch_widen_to_double(const float* in, double* oi, double* oh, long long n, cudaStream_t st) {
+  if (n > 0) widen_to_double_kernel<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(in, oi, oh, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fma_peak(int precision, int blocks, int iters, void* sink, cudaStream_t st) {
   if (precision == FSP_FP64)
     fma_peak_kernel<double><<<blocks, 256, 0, st>>>(iters, static_cast<double*>(sink));

@@ -127,6 +127,7 @@ def lib():
                 "fsp_check_state": (ctypes.c_int, [C, B, _P, _P, _P]),
                 "fsp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
                 "fsp_round_to_float": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
+                "fsp_widen_to_double": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
                 "fsp_vjp_workspace_size": (ctypes.c_int, [C, B, ctypes.POINTER(ctypes.c_size_t)]),
                 "fsp_rhs_vjp": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_rk3_step_vjp": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -412,6 +413,15 @@ def round_to_float(x: torch.Tensor, stream=None):
     a, b = torch.empty(x.shape, dtype=torch.float32, device=x.device), torch.empty(x.shape, dtype=torch.float32,
                                                                                      device=x.device)
     _check("fsp_round_to_float", lib().fsp_round_to_float(_ptr(x), _ptr(a), _ptr(b), x.numel(), _stream(stream)))
+    return a, b
+
+
+def widen_to_double(x: torch.Tensor, stream=None):
+    """(integer widening, hardware widening) of a float32 device tensor to float64."""
+    x = x.contiguous()
+    a, b = torch.empty(x.shape, dtype=torch.float64, device=x.device), torch.empty(x.shape, dtype=torch.float64,
+                                                                                     device=x.device)
+    _check("fsp_widen_to_double", lib().fsp_widen_to_double(_ptr(x), _ptr(a), _ptr(b), x.numel(), _stream(stream)))
     return a, b
 
 

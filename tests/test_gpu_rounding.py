@@ -47,3 +47,23 @@ def test_integer_rounding_matches_the_hardware(F):
     tiny = ~nan & ~normal_or_big
     assert tiny.any()
     assert (a[tiny] == 0).all() and np.array_equal(np.signbit(a[tiny]), np.signbit(x[tiny]))
+
+
+def test_integer_widening_matches_the_hardware(F):
+    """to_f64_int (the mixed path's float-to-double widening): bit for bit the hardware's on
+    signed zeros, normals across the whole exponent range, the float extremes, subnormals,
+    infinities and NaN."""
+    f32 = np.finfo(np.float32)
+    rng = np.random.default_rng(1103)
+    vals = np.array([0.0, -0.0, 1.0, -1.0, f32.max, -f32.max, f32.tiny, -f32.tiny, f32.tiny / 2, -f32.tiny / 8,
+                     2.0 ** -149, np.inf, -np.inf, np.nan], dtype=np.float32)
+    rnd = (rng.standard_normal(8192) * 10.0 ** rng.uniform(-44, 38, 8192)).astype(np.float32)
+    bits = rng.integers(0, 2 ** 32, 8192, dtype=np.uint64).astype(np.uint32).view(np.float32)   # every pattern kind
+    x = np.concatenate([vals, rnd, bits])
+    a, b = F.widen_to_double(torch.as_tensor(x, device="cuda"))
+    torch.cuda.synchronize()
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    nan = np.isnan(x)
+    assert np.isnan(a[nan]).all()
+    assert np.array_equal(a[~nan].view(np.uint64), b[~nan].view(np.uint64))
+    assert np.array_equal(b[~nan], x[~nan].astype(np.float64))
