@@ -206,33 +206,35 @@ __global__ void __launch_bounds__(256) lambda3_kernel(P3 P, const double* __rest
 // ---- sweeps --------------------------------------------------------------------------------
 enum { W3_WRITE = 0, W3_ADD = 1, W3_RHS = 2, W3_STAGE = 3 };
 
-// A tile: NL lines of direction D (consecutive j for xi, consecutive i for eta and zeta, so that
-// the loads of a warp are contiguous) x W interface slots; T output nodes per line and the
-// nodes base - 4 .. base + T + 3 staged.
+// A tile: NL lines of direction D (consecutive j for xi, consecutive i for eta and zeta) x W
+// interface slots, with the lines across the lanes of a warp (a warp takes two interface
+// positions of 16 lines, so a ragged last tile leaves whole warps idle rather than lanes);
+// T output nodes per line and the nodes base - 4 .. base + T + 3 staged.
 template <int S, int D>
 struct Tile3 {
-  static constexpr int NL = D == 0 ? 8 : 16;
+  static constexpr int NL = 16;
   static constexpr int W = 32;
   static constexpr int NMP = Scheme<S>::nmp;
   static constexpr int T = W - NMP - 1;
   static constexpr int NP = T + 8;
   static constexpr int NN = NL * NP, NW = NL * W;
   static constexpr int THREADS = 256;
-  // shared memory (doubles): state 5, direction metrics 3, split fluxes 5 + 5 per node; h 5
-  // per interface; the two-midpoint schemes' midpoint fluxes 10 per interface; A^ per line
+  // shared memory (doubles): per node the state 5, direction metrics 3, split fluxes 5 + 5 and
+  // the characteristic data 9 (Node3); h 5 per interface; the two-midpoint schemes' midpoint
+  // fluxes 10 per interface; A^ per line
   static constexpr size_t smem_bytes() {
-    return sizeof(double) * ((size_t)18 * NN + 5 * (size_t)NW + (NMP == 2 ? 10 * (size_t)NW : 0) + NL);
+    return sizeof(double) * ((size_t)27 * NN + 5 * (size_t)NW + (NMP == 2 ? 10 * (size_t)NW : 0) + NL);
   }
 };
 
-// The closed-form eigenvectors of the flux Jacobian along the unit direction n at a node with
-// primitives (u, c, H) (Section 3.4 in three dimensions): the Un eigenspace takes the entropy
-// wave and two shear waves along t1 = (a x n)/|a x n|, a the coordinate axis least aligned with
-// n (ties to the larger index), and t2 = n x t1.
-struct Char3 {
-  double nx, ny, nz, t1x, t1y, t1z, t2x, t2y, t2z, ux, uy, uz;
-  double c, ci, H, Un, U1, U2, b1, b2, h2;
-  __device__ __forceinline__ void build(const double q[5], const double nn[3], double gamma) {
+// The direction-free part of the characteristic system at a node (Section 3.4 in three
+// dimensions): velocity, |u|^2/2, sound speed and its reciprocal, enthalpy, and
+// b1 = (gamma - 1)/c^2, b2 = b1 |u|^2/2.  Staged once per node; both interfaces that use the
+// node as a stencil centre read it.
+struct Node3 {
+  double ux, uy, uz, h2, c, ci, H, b1, b2;
+  static constexpr int COUNT = 9;
+  __device__ __forceinline__ void build(const double q[5], double gamma) {
     const double ri = rcp_nr(q[0]);
     ux = q[1] * ri; uy = q[2] * ri; uz = q[3] * ri;
     h2 = 0.5 * (ux * ux + uy * uy + uz * uz);
@@ -243,8 +245,26 @@ struct Char3 {
     H = (q[4] + p) * ri;
     b1 = (gamma - 1.0) * ci * ci;
     b2 = b1 * h2;
-    nx = nn[0]; ny = nn[1]; nz = nn[2];
-    // a x n for the least aligned axis a (ties to the later axis)
+  }
+  __device__ __forceinline__ void store(double* b, int stride, int o) const {
+    b[o] = ux; b[stride + o] = uy; b[2 * stride + o] = uz; b[3 * stride + o] = h2; b[4 * stride + o] = c;
+    b[5 * stride + o] = ci; b[6 * stride + o] = H; b[7 * stride + o] = b1; b[8 * stride + o] = b2;
+  }
+  __device__ __forceinline__ void load(const double* b, int stride, int o) {
+    ux = b[o]; uy = b[stride + o]; uz = b[2 * stride + o]; h2 = b[3 * stride + o]; c = b[4 * stride + o];
+    ci = b[5 * stride + o]; H = b[6 * stride + o]; b1 = b[7 * stride + o]; b2 = b[8 * stride + o];
+  }
+};
+
+// The unit direction n of an interface and its tangents: the Un eigenspace takes the entropy
+// wave and two shear waves along t1 = (a x n)/|a x n|, a the coordinate axis least aligned
+// with n (ties to the later axis), and t2 = n x t1.  Shared by the interface's two sides.
+struct Dir3 {
+  double nx, ny, nz, t1x, t1y, t1z, t2x, t2y, t2z;
+  // from the sum of the two nodes' direction metrics (the average's 1/2 cancels)
+  __device__ __forceinline__ void build(const double mb[3]) {
+    const double rn = rsq(mb[0] * mb[0] + mb[1] * mb[1] + mb[2] * mb[2]);
+    nx = mb[0] * rn; ny = mb[1] * rn; nz = mb[2] * rn;
     double x0, x1, x2;
     const double ax = fabs(nx), ay = fabs(ny), az = fabs(nz);
     if (ax < ay && ax < az) { x0 = 0.0; x1 = -nz; x2 = ny; }
@@ -255,40 +275,41 @@ struct Char3 {
     t2x = ny * t1z - nz * t1y;
     t2y = nz * t1x - nx * t1z;
     t2z = nx * t1y - ny * t1x;
-    Un = ux * nx + uy * ny + uz * nz;
-    U1 = ux * t1x + uy * t1y + uz * t1z;
-    U2 = ux * t2x + uy * t2y + uz * t2z;
   }
-  // left eigenvector row k applied to dq
-  __device__ __forceinline__ double project(int k, const double dq[5]) const {
-    if (k == 2) return -U1 * dq[0] + t1x * dq[1] + t1y * dq[2] + t1z * dq[3];
-    if (k == 3) return -U2 * dq[0] + t2x * dq[1] + t2y * dq[2] + t2z * dq[3];
-    const double bu = b1 * (ux * dq[1] + uy * dq[2] + uz * dq[3]) - b1 * dq[4];
-    if (k == 1) return (1.0 - b2) * dq[0] + bu;
-    const double s = k == 0 ? 1.0 : -1.0;
-    const double nc = ci * (nx * dq[1] + ny * dq[2] + nz * dq[3]);
-    return 0.5 * ((b2 + s * Un * ci) * dq[0] - bu - s * nc);
+};
+
+// One side of an interface: the eigen-system of the centre node along the interface's
+// direction.  Left eigenvectors (rows 0..4 for u - c, u (entropy), the two shear waves, u + c)
+// applied to a state difference dq through its common parts P0 = (b2 dq0 - b1 (u.dq - dq4))/2
+// and B = c^-1 (Un dq0 - n.dq)/2: w0 = P0 + B, w4 = P0 - B, w1 = dq0 - 2 P0; right
+// eigenvectors summed through s = W0 + W4 and c (W4 - W0).
+struct Side3 {
+  const Node3& w;
+  const Dir3& d;
+  double Un, U1, U2;
+  __device__ __forceinline__ Side3(const Node3& w_, const Dir3& d_) : w(w_), d(d_) {
+    Un = w.ux * d.nx + w.uy * d.ny + w.uz * d.nz;
+    U1 = w.ux * d.t1x + w.uy * d.t1y + w.uz * d.t1z;
+    U2 = w.ux * d.t2x + w.uy * d.t2y + w.uz * d.t2z;
   }
-  // q += W_k times right eigenvector column k
-  __device__ __forceinline__ void recon_add(int k, double Wk, double q[5]) const {
-    if (k == 2) {
-      q[1] += Wk * t1x; q[2] += Wk * t1y; q[3] += Wk * t1z; q[4] += Wk * U1;
-      return;
-    }
-    if (k == 3) {
-      q[1] += Wk * t2x; q[2] += Wk * t2y; q[3] += Wk * t2z; q[4] += Wk * U2;
-      return;
-    }
-    if (k == 1) {
-      q[0] += Wk; q[1] += Wk * ux; q[2] += Wk * uy; q[3] += Wk * uz; q[4] += Wk * h2;
-      return;
-    }
-    const double s = k == 0 ? -c : c;
-    q[0] += Wk;
-    q[1] += Wk * (ux + s * nx);
-    q[2] += Wk * (uy + s * ny);
-    q[3] += Wk * (uz + s * nz);
-    q[4] += Wk * (H + s * Un);
+  __device__ __forceinline__ void project(const double dq[5], double o[5]) const {
+    const double bu = w.b1 * (w.ux * dq[1] + w.uy * dq[2] + w.uz * dq[3] - dq[4]);
+    const double P0 = 0.5 * (w.b2 * dq[0] - bu);
+    const double B = 0.5 * w.ci * (Un * dq[0] - (d.nx * dq[1] + d.ny * dq[2] + d.nz * dq[3]));
+    o[0] = P0 + B;
+    o[1] = dq[0] - 2.0 * P0;
+    o[2] = d.t1x * dq[1] + d.t1y * dq[2] + d.t1z * dq[3] - U1 * dq[0];
+    o[3] = d.t2x * dq[1] + d.t2y * dq[2] + d.t2z * dq[3] - U2 * dq[0];
+    o[4] = P0 - B;
+  }
+  // Q = qc + sum_k W_k r_k
+  __device__ __forceinline__ void recon(const double W[5], const double qc[5], double Q[5]) const {
+    const double s = W[0] + W[4], cd = w.c * (W[4] - W[0]), a = s + W[1];
+    Q[0] = qc[0] + a;
+    Q[1] = qc[1] + a * w.ux + cd * d.nx + W[2] * d.t1x + W[3] * d.t2x;
+    Q[2] = qc[2] + a * w.uy + cd * d.ny + W[2] * d.t1y + W[3] * d.t2y;
+    Q[3] = qc[3] + a * w.uz + cd * d.nz + W[2] * d.t1z + W[3] * d.t2z;
+    Q[4] = qc[4] + s * w.H + W[1] * w.h2 + cd * Un + W[2] * U1 + W[3] * U2;
   }
 };
 
@@ -326,7 +347,8 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
   double* smt = sq + 5 * NN;        // [3][NN]
   double* sfp = smt + 3 * NN;       // [5][NN]
   double* sfm = sfp + 5 * NN;       // [5][NN]
-  double* sH = sfm + 5 * NN;        // [5][NW]
+  double* sc = sfm + 5 * NN;        // [Node3::COUNT][NN]
+  double* sH = sc + Node3::COUNT * NN;   // [5][NW]
   double* sF = sH + 5 * NW;         // [10][NW] (two-midpoint schemes)
   double* sA = sF + (NMP == 2 ? 10 * NW : 0);   // [NL]
   const int n = P.n[D];
@@ -336,17 +358,17 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
   const int o2 = blockIdx.y / nblk;                        // k for xi and eta, j for zeta
   const int base = blockIdx.x * T;
   const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
-  auto SI = [](int l, int s) { return D == 0 ? l * NP + s : s * NL + l; };
-  auto WI = [](int l, int p) { return D == 0 ? l * W + p : p * NL + l; };
+  auto SI = [](int l, int s) { return s * NL + l; };
+  auto WI = [](int l, int p) { return p * NL + l; };
   auto lam_index = [&](int l) -> long long {
     const int a = o1 + l;
     return D == 0 ? (long long)o2 * P.n[1] + a : D == 1 ? (long long)o2 * P.n[0] + a : (long long)o2 * P.n[0] + a;
   };
   if (threadIdx.x < NL) sA[threadIdx.x] = o1 + (int)threadIdx.x < nlines ? P.alpha * lam[lam_index(threadIdx.x)] : 0.0;
   __syncthreads();
-  // ---- nodes: state (ghosts by the face rule), direction metrics, split fluxes
+  // ---- nodes: state (ghosts by the face rule), direction metrics, split fluxes, characteristic data
   for (int t = threadIdx.x; t < NN; t += Sh::THREADS) {
-    const int l = D == 0 ? t / NP : t % NL, s = D == 0 ? t % NP : t / NL;
+    const int l = t % NL, s = t / NL;
     if (o1 + l >= nlines) continue;
     const int g = min(base + s - 4, n + 3);   // ghost metrics are stored; ghost states by the face rule
     int gs = g;
@@ -376,12 +398,15 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) smt[c * NN + so] = m[c];
+    Node3 w;
+    w.build(q, P.gamma);
+    w.store(sc, NN, so);
   }
   __syncthreads();
   // ---- interfaces p + 1/2
   const double eps = P.eps;
   for (int t = threadIdx.x; t < NW; t += Sh::THREADS) {
-    const int l = D == 0 ? t / W : t % NL, pi = D == 0 ? t % W : t / NL;
+    const int l = t % NL, pi = t / NL;
     const int p = pi - NMP;
     if (o1 + l >= nlines || base + p > n || (NMP == 1 && p > T - 1)) continue;
     const int c0 = p + 4;
@@ -389,8 +414,8 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
     double mb[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) mb[c] = smt[c * NN + SI(l, c0)] + smt[c * NN + SI(l, c0 + 1)];
-    const double rn = rsq(mb[0] * mb[0] + mb[1] * mb[1] + mb[2] * mb[2]);
-    const double nn[3] = {mb[0] * rn, mb[1] * rn, mb[2] * rn};
+    Dir3 dir;
+    dir.build(mb);
     double Qs[2][5];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
@@ -398,27 +423,36 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
       double qc[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) qc[v] = sq[v * NN + ce];
-      Char3 E;
-      E.build(qc, nn, P.gamma);
-      double dq[NA][5];
+      Node3 w;
+      w.load(sc, NN, ce);
+      const Side3 E(w, dir);
+      // characteristic differences to the centre at the stencil offsets -H..-1, +1..+H (the
+      // "-" side reads the mirrored nodes), component k at u[k][a or a + 1]; u[k][H] = 0
+      double u[5][NA + 1];
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
         const int m = a < H ? a - H : a - H + 1;
+        const int ua = a < H ? a : a + 1;
+        if (R == 2 && m == 2) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) u[k][ua] = 0.0;
+          continue;
+        }
         const int nd = SI(l, side == 0 ? c0 + m : c0 + 1 - m);
+        double dq[5], o[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) dq[a][v] = (R == 2 && m == 2) ? 0.0 : sq[v * NN + nd] - qc[v];
+        for (int v = 0; v < 5; ++v) dq[v] = sq[v * NN + nd] - qc[v];
+        E.project(dq, o);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) u[k][ua] = o[k];
       }
+      double Wk[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Qs[side][v] = qc[v];
-#pragma unroll 1
-      for (int kc = 0; kc < 5; ++kc) {
-        double u[NA + 1];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = E.project(kc, dq[a]);
-        u[H] = 0.0;
-        const double Wk = weno_delta<R, double>(u, eps, P.ppm, P.linw) * (1.0 / SC);
-        E.recon_add(kc, Wk, Qs[side]);
+      for (int k = 0; k < 5; ++k) {
+        u[k][H] = 0.0;
+        Wk[k] = weno_delta<R, double>(u[k], eps, P.ppm, P.linw) * (1.0 / SC);
       }
+      E.recon(Wk, qc, Qs[side]);
     }
     // midpoint metrics by the interpolation of the metric evaluation
     double mm[3];
@@ -467,7 +501,7 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
     __syncthreads();
     // h+ uses f+ at p + 1/2 and p - 1/2; h- uses f- at p + 1/2 and p + 3/2
     for (int t = threadIdx.x; t < NW; t += Sh::THREADS) {
-      const int l = D == 0 ? t / W : t % NL, pi = D == 0 ? t % W : t / NL;
+      const int l = t % NL, pi = t / NL;
       const int p = pi - NMP;
       if (o1 + l >= nlines || p < -1 || p > T - 1 || base + p > n - 1) continue;
       const int c0 = p + 4;
@@ -487,7 +521,7 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
   __syncthreads();
   // ---- outputs: node s, H_{s+1/2} - H_{s-1/2}
   for (int t = threadIdx.x; t < NL * T; t += Sh::THREADS) {
-    const int l = D == 0 ? t / T : t % NL, s = D == 0 ? t % T : t / NL;
+    const int l = t % NL, s = t / NL;
     const int g = base + s;
     if (o1 + l >= nlines || g >= n) continue;
     const int pi = s + NMP;
