@@ -207,18 +207,19 @@ __global__ void __launch_bounds__(256) lambda3_kernel(P3 P, const double* __rest
 enum { W3_WRITE = 0, W3_ADD = 1, W3_RHS = 2, W3_STAGE = 3 };
 
 // A tile: NL lines of direction D (consecutive j for xi, consecutive i for eta and zeta) x W
-// interface slots, with the lines across the lanes of a warp (a warp takes two interface
-// positions of 16 lines, so a ragged last tile leaves whole warps idle rather than lanes);
+// interface slots, with the lines across the lanes of a warp (a warp takes four interface
+// positions of 8 lines, so a ragged last tile leaves whole warps idle rather than lanes);
 // T output nodes per line and the nodes base - 4 .. base + T + 3 staged.
 template <int S, int D>
 struct Tile3 {
-  static constexpr int NL = 16;
+  static constexpr int NL = 8;
   static constexpr int W = 32;
   static constexpr int NMP = Scheme<S>::nmp;
   static constexpr int T = W - NMP - 1;
   static constexpr int NP = T + 8;
   static constexpr int NN = NL * NP, NW = NL * W;
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = 128;
+  static constexpr int CTAS = 2;       // per SM: one CTA's barrier phases overlap the other's sweeps (three: no faster)
   // shared memory (doubles): per node the state 5, direction metrics 3, split fluxes 5 + 5 and
   // the characteristic data 9 (Node3); h 5 per interface; the two-midpoint schemes' midpoint
   // fluxes 10 per interface; A^ per line
@@ -234,11 +235,12 @@ struct Tile3 {
 struct Node3 {
   double ux, uy, uz, h2, c, ci, H, b1, b2;
   static constexpr int COUNT = 9;
-  __device__ __forceinline__ void build(const double q[5], double gamma) {
+  // from the state; p receives the pressure
+  __device__ __forceinline__ void build(const double q[5], double gamma, double& p) {
     const double ri = rcp_nr(q[0]);
     ux = q[1] * ri; uy = q[2] * ri; uz = q[3] * ri;
     h2 = 0.5 * (ux * ux + uy * uy + uz * uz);
-    const double p = (gamma - 1.0) * (q[4] - q[0] * h2);
+    p = (gamma - 1.0) * (q[4] - q[0] * h2);
     const double c2 = gamma * p * ri;
     ci = rsq(c2);
     c = c2 * ci;
@@ -335,7 +337,7 @@ __device__ __forceinline__ void tile_node(int g, int l, int o1, int o2, int& i, 
 }
 
 template <int S, int D, int MODE>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(Tile3<S, D>::THREADS, Tile3<S, D>::CTAS)
 sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam, double* acc, double* out,
               const double* Qn, double ca, double cb, double dt) {
   using Sh = Tile3<S, D>;
@@ -353,9 +355,8 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
   double* sA = sF + (NMP == 2 ? 10 * NW : 0);   // [NL]
   const int n = P.n[D];
   const int nlines = D == 0 ? P.n[1] : P.n[0];             // lines per tile row
-  const int nblk = (nlines + NL - 1) / NL;
-  const int o1 = (blockIdx.y % nblk) * NL;                 // first line (j for xi, i otherwise)
-  const int o2 = blockIdx.y / nblk;                        // k for xi and eta, j for zeta
+  const int o1 = blockIdx.y * NL;                          // first line (j for xi, i otherwise)
+  const int o2 = blockIdx.z;                               // k for xi and eta, j for zeta
   const int base = blockIdx.x * T;
   const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
   auto SI = [](int l, int s) { return s * NL + l; };
@@ -386,8 +387,13 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
     double m[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) m[c] = met3(P, 3 * D + c, i, j, k);
-    double f[5];
-    flux3(q, m, P.gamma, f);
+    // the node's characteristic data, and its metric-weighted flux from the same primitives
+    Node3 w;
+    double pr;
+    w.build(q, P.gamma, pr);
+    const double U = m[0] * w.ux + m[1] * w.uy + m[2] * w.uz;
+    const double f[5] = {q[0] * U, q[1] * U + m[0] * pr, q[2] * U + m[1] * pr, q[3] * U + m[2] * pr,
+                         (q[4] + pr) * U};
     const double A = sA[l];
     const int so = SI(l, s);
 #pragma unroll
@@ -398,8 +404,6 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) smt[c * NN + so] = m[c];
-    Node3 w;
-    w.build(q, P.gamma);
     w.store(sc, NN, so);
   }
   __syncthreads();
@@ -621,8 +625,7 @@ cudaError_t launch_sweep3(const P3& P, const double* Q, const double* lam, doubl
   if (e != cudaSuccess) return e;
   const int n = P.n[D], nlines = D == 0 ? P.n[1] : P.n[0];
   const int outer = D == 2 ? P.n[1] : P.n[2];
-  dim3 grid((n + Sh::T - 1) / Sh::T, ((nlines + Sh::NL - 1) / Sh::NL) * outer);
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((n + Sh::T - 1) / Sh::T, (nlines + Sh::NL - 1) / Sh::NL, outer);   // each within 65535 (n <= 65535)
   kern<<<grid, Sh::THREADS, smem, st>>>(P, Q, lam, acc, out, Qn, ca, cb, dt);
   return cudaGetLastError();
 }
