@@ -50,11 +50,19 @@ def _case(shape=(40, 35, 33), seed=5, bc=(0,) * 6, smooth=True):
 
 
 def _metrics(F, cfgd, blk, x, y, z):
+    """Metrics parity.  Each metric is a difference of products of a coordinate (up to X in
+    size) and a coordinate difference (up to D, the largest spacing), so each side rounds at a
+    few tens of eps X D; J^-1 multiplies them by one more difference: eps X D^2.  These
+    absolute floors matter only where one spacing is far below the others (a long thin
+    block), where the small metrics' own scale sits below them."""
     cfg = F.Config.from_dict(cfgd)
     M_o = O.metrics3(cfgd, x, y, z)
     M_g = _host(F.metrics3(cfg, blk, _dev(x), _dev(y), _dev(z)))
-    assert np.abs(M_g[:9] - M_o[:9]).max() < TOL * np.abs(M_o[:9]).max()
-    assert np.abs(M_g[9] - M_o[9]).max() < TOL * np.abs(M_o[9]).max()
+    X = max(np.abs(c).max() for c in (x, y, z))
+    D = max(np.abs(np.diff(c, axis=a)).max() for c in (x, y, z) for a in range(3) if c.shape[a] > 1)
+    floor = 64 * np.finfo(np.float64).eps * X * D
+    assert np.abs(M_g[:9] - M_o[:9]).max() < TOL * np.abs(M_o[:9]).max() + floor
+    assert np.abs(M_g[9] - M_o[9]).max() < TOL * np.abs(M_o[9]).max() + floor * D
     return M_o
 
 
@@ -137,3 +145,21 @@ def test_refusals(F):
     xs, ys, zs, pers, _ = _case((20, 16, 12))
     with pytest.raises(F.FspError):
         F.workspace3(cfg, F.block3_of(_dev(xs), (0, 0, 0, 0, 1, 1), pers))
+
+
+@pytest.mark.parametrize("shape", [(1500, 13, 14), (13, 1500, 14), (14, 13, 1500)])
+def test_rhs_parity_long_thin_blocks(F, shape):
+    """One long direction of 1500 nodes (50 tiles of 30 output nodes, the last ragged) and two
+    short transmissive ones (13 and 14 nodes: partial tiles of 8 lines, reflected ghost
+    coordinates); a random state, so every weight is far from linear."""
+    ni, nj, nk = shape
+    x, y, z, per = I.periodic_cube(ni, 8.0, 0.2, seed=3, nj=nj, nk=nk)
+    longest = int(np.argmax(shape))
+    bc = tuple(0 if a // 2 == longest else 1 for a in range(6))
+    q = I.random_state3(x.shape, seed=4)
+    cfgd = dict(scheme=2, period=per, bc=bc)
+    blk = F.block3_of(_dev(x), bc, per)
+    M = _metrics(F, cfgd, blk, x, y, z)
+    R_o = O.rhs3(cfgd, M, q)
+    R_g = _host(F.rhs3(F.Config.from_dict(cfgd), blk, _dev(M), _dev(q)))
+    assert _rel(R_g, R_o) < TOL, _rel(R_g, R_o)
