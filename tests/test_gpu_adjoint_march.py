@@ -149,26 +149,29 @@ def test_shock_vortex_512_gradient_vs_finite_differences(F, A):
     for v in range(4):                         # smooth grid directions (0.1 of the finest spacing)
         dirs.append(("grid", zq, _dev(0.004 * I.smooth_field(x.shape, 400 + v)),
                      _dev(0.004 * I.smooth_field(x.shape, 410 + v))))
-    for k, (c, j, i) in enumerate([(0, nj // 2, (i0 + i1) // 2), (3, nj // 2 + 5, i0 + 3), (1, nj // 3, 2),
-                                   (2, nj // 2 + 2, ni - ni // 4)]):
+    # Single nodes, each with its step fixed by where it sits.  The error of the difference is
+    # V-shaped in h: where the kick meets exactly uniform data (the inflow ahead of the shock,
+    # and behind it) the weights bend on the scale h^2/epsilon, so a small step; where its
+    # domain of influence reaches the shock and the vortex inside the window, the differences
+    # of J carry a rounding floor of about 1e-14 after 200 steps, so a large one.
+    nodes = [((0, nj // 2, (i0 + i1) // 2), 1e-4),     # window centre: shock and vortex
+             ((3, nj // 2 + 5, i0 + 3), 1e-4),         # window edge, next to the shock
+             ((1, nj // 3, 2), 1e-5),                  # uniform inflow
+             ((2, nj // 2 + 2, ni - ni // 4), 1e-5)]   # uniform flow behind the shock
+    for (c, j, i), h in nodes:
         dq = torch.zeros_like(gq)
         dq[c, j, i] = 1.0
-        dirs.append(("state node", dq, zc, zc))
-    for name, dq, dx, dy in dirs:
+        dirs.append(("state node", dq, zc, zc, h))
+    for name, dq, dx, dy, *hs in dirs:
         adj = float((grad_q * dq).sum() + (grad_x * dx).sum() + (grad_y * dy).sum())
         # Steps.  Whole-field state kicks: 1e-7 (larger ones start to switch the argmax of
         # nearly tied line maxima of the spectral radius, a kink).  Grid directions: 1e-5
         # (the metrics difference coordinates of size 10 at spacings of 0.04, so smaller
-        # steps drown in their rounding).  Single nodes: the best of 1e-4, 1e-5 and 1e-6 (the
-        # bottom of the error's V-shape in h).  Where the kick meets exactly uniform data the
-        # weights bend on the scale h^2/epsilon and only the small step is accurate; where
-        # its domain of influence reaches the shock, the differences of J carry a rounding
-        # floor of about 1e-14 after 200 steps and only the large step is.
-        steps = {"state": (1e-7,), "grid": (1e-5,)}.get(name, (1e-4, 1e-5, 1e-6))
-        rels = [(abs(adj - v) / abs(v), v, h) for h, v in zip(steps, [fd(dq, dx, dy, h) for h in steps])]
-        for r_, v_, h_ in rels:
-            print(f"{name}: h {h_:.0e} adjoint {adj:.12e} finite difference {v_:.12e} relative {r_:.2e}")
-        rel, num, _ = min(rels)
+        # steps drown in their rounding).
+        h = hs[0] if hs else {"state": 1e-7, "grid": 1e-5}[name]
+        num = fd(dq, dx, dy, h)
+        rel = abs(adj - num) / abs(num)
+        print(f"{name}: h {h:.0e} adjoint {adj:.12e} finite difference {num:.12e} relative {rel:.2e}")
         assert rel < 1e-6, (name, adj, num, rel)
     # Single grid nodes where the flow is uniform (the outflow face, the region behind the
     # shock) have zero derivative: a uniform flow stays uniform on any grid (free-stream
