@@ -66,11 +66,25 @@ __device__ __forceinline__ void scatter_ghost(const Params& P, const double* __r
   add(b, qb);               // transmissive (and far-field outflow)
 }
 
+// Tile of the adjoint sweeps: the forward tiles' interface rows (xi 128 interfaces per line,
+// eta 32) on half as many lines, for 128-thread CTAs with one interface per thread.  Two
+// CTAs fit an SM (about 95 KB of shared memory and 31 K registers each), so the staging,
+// node-flux and scatter phases of one overlap the FP64 interface work of the other.
 template <int S, int DIR>
-__global__ void __launch_bounds__(256, 1)
+struct VjpTile {
+  using Base = TileShape<S, DIR, double, double>;
+  static constexpr int NL = Base::NL / 2;
+  static constexpr int W = Base::W, T = Base::T, NP = Base::NP;
+  static constexpr int THREADS = NL * W;
+  static constexpr int NN = NL * NP;
+  static constexpr size_t smem_bytes() { return sizeof(double) * (27 * (size_t)NN + NL + 4 * (size_t)WT * THREADS); }
+};
+
+template <int S, int DIR>
+__global__ void __launch_bounds__(VjpTile<S, DIR>::THREADS, 2)
 vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restrict__ lam,
                  const double* __restrict__ gbar, double* Qbar, double* Mbar, double* Abar) {
-  using Sh = TileShape<S, DIR, double, double>;
+  using Sh = VjpTile<S, DIR>;
   using Sc = Scheme<S>;
   constexpr int NL = Sh::NL, W = Sh::W, T = Sh::T, NP = Sh::NP, NN = Sh::NN;
   constexpr int NMP = Sc::nmp;
@@ -380,10 +394,10 @@ __global__ void axpby_kernel(long long n, double a, const double* x, double b, c
 template <int S, int DIR>
 static cudaError_t launch_vjp_sweep(const Params& P, const double* Q, const double* lam, const double* gbar,
                                     double* Qbar, double* Mbar, double* Abar, cudaStream_t st) {
-  using Sh = TileShape<S, DIR, double, double>;
+  using Sh = VjpTile<S, DIR>;
   const int n = DIR == 0 ? P.ni : P.nj, nlines = DIR == 0 ? P.nj : P.ni;
   dim3 grid((n + Sh::T - 1) / Sh::T, (nlines + Sh::NL - 1) / Sh::NL);
-  const size_t smem = sizeof(double) * (27 * (size_t)Sh::NN + Sh::NL + 4 * (size_t)WT * Sh::THREADS);
+  const size_t smem = Sh::smem_bytes();
   auto kern = vjp_sweep_kernel<S, DIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
