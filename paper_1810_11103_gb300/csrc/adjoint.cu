@@ -613,7 +613,7 @@ static fsp_status vjp_core(const fsp_config& c, const fsp_block& b, const double
   TRY(cudaMemsetAsync(abar, 0, sizeof(double) * (b.ni + b.nj), st));
   TRY(cudaMemsetAsync(arg, 0x7f, sizeof(int) * (b.ni + b.nj), st));
   const long long N = (long long)b.ni * b.nj;
-  const int g1 = (int)((N + 255) / 256 < 152 * 8 ? (N + 255) / 256 : 152 * 8);
+  const int g1 = stride_grid((N + 255) / 256, 8);
   jac_bwd_kernel<<<g1, 256, 0, st>>>(P, gbar, R, Mbar);
   TRY(cudaGetLastError());
   cudaError_t e;
@@ -645,7 +645,7 @@ static fsp_status rhs_vjp_impl(const fsp_config& c, const fsp_block& b, const do
   return vjp_core(c, b, metrics, Q, dqdt, reinterpret_cast<const double*>(ws), gbar, Qbar, Mbar, ws, L, st);
 }
 
-static int grid_of(long long n) { return (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8); }
+static int grid_of(long long n) { return stride_grid((n + 255) / 256, 8); }
 
 // The stages of one TVD-RK3 step from the tape's Q^n (already in place), each right-hand
 // side and its line maxima kept in the tape; Q^{n+1} written to qout when it is not null.
@@ -810,7 +810,7 @@ fsp_status fsp_metrics_vjp(const fsp_config* cfg, const fsp_block* blk, const do
   VjpCoord C{blk->ni, blk->nj, cfg->bc[0] == FSP_BC_PERIODIC, cfg->bc[2] == FSP_BC_PERIODIC,
              blk->period[0][0], blk->period[0][1], blk->period[1][0], blk->period[1][1]};
   const long long n = (long long)(blk->ni + 2 * G) * (blk->nj + 2 * G);
-  const int grid = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
+  const int grid = stride_grid((n + 255) / 256, 8);
   metrics_vjp_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(C, x, y, metrics_bar, w, x_bar, y_bar);
   return cudaGetLastError() == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
 }

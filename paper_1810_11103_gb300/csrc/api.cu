@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libfsp (include/fsp.h): argument checks on the host, workspace
 // layout, and the launch sequences of each entry point.
+#include <atomic>
 #include <cstring>
 
 #include "fsp_internal.h"
@@ -111,6 +112,22 @@ fsp_status check_options(const fsp_config& c) {
   if (a != 1.0 && (c.scheme == S32 || c.scheme == S52 || c.scheme == S74)) return FSP_ERR_INVALID_ARG;   // no free parameter
   if (c.mid_split != 0 && c.precision == FSP_FP32_MIXED) return FSP_ERR_UNSUPPORTED;
   return FSP_OK;
+}
+
+int stride_grid(long long blocks, int per_sm) {
+  static std::atomic<int> sms[64];   // multiprocessors per device ordinal, 0 until read
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) n = sms[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 1;
+    } else if (dev >= 0 && dev < 64) {
+      sms[dev].store(n, std::memory_order_relaxed);
+    }
+  }
+  const long long cap = (long long)n * per_sm;
+  return (int)(blocks < 1 ? 1 : blocks < cap ? blocks : cap);
 }
 
 fsp_status rhs_status(cudaError_t e) {

@@ -451,7 +451,7 @@ fsp_status fsp_batch_metrics(fsp_batch* h, void* stream) {
   for (int b = 0; b < h->nb; ++b) {
     const long long n = (long long)(h->blk[b].ni + 2 * G) * (h->blk[b].nj + 2 * G);
     const long long want = (n + 255) / 256;
-    metrics_mb_kernel<<<(int)(want < 152 * 8 ? want : 152 * 8), 256, 0, st>>>(
+    metrics_mb_kernel<<<stride_grid(want, 8), 256, 0, st>>>(
         h->d_coords, b, cen, h->cfg.interp, h->cfg.scheme == S71 ? 8 : h->cfg.scheme >= S51 ? 6 : 4, h->M[b]);
     if (cudaGetLastError() != cudaSuccess) return FSP_ERR_CUDA;
   }

@@ -613,7 +613,7 @@ size_t metrics_scratch3(const fsp3_block& b) {
   return al3(8 * 12 * (size_t)((long long)(b.ni + 16) * (b.nj + 16) * (b.nk + 16)));
 }
 
-int grid_of3(long long n) { return (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8); }
+int grid_of3(long long n) { return stride_grid((n + 255) / 256, 8); }
 
 template <int S, int D, int MODE>
 cudaError_t launch_sweep3(const P3& P, const double* Q, const double* lam, double* acc, double* out, const double* Qn,

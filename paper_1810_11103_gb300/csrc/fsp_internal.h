@@ -17,6 +17,10 @@ bool default_options(const fsp_config& c);
 // kernels (the midpoint splittings in mixed precision).
 fsp_status check_options(const fsp_config& c);
 
+// Grid size of a grid-stride launch: the blocks the work needs, at most per_sm resident
+// blocks on each multiprocessor of the current device (its count read once per device).
+int stride_grid(long long blocks, int per_sm);
+
 // Kernel parameters of one block from the public configuration (host side).
 Params make_params(const fsp_config& cfg, const fsp_block& blk, const double* metrics);
 

@@ -130,7 +130,7 @@ cudaError_t launch_metrics(const fsp_config& cfg, const fsp_block& blk, const do
   const long long n = (long long)(blk.ni + 2 * G) * (blk.nj + 2 * G);
   const int threads = 256;
   const long long blocks = (n + threads - 1) / threads;
-  const int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+  const int grid = stride_grid(blocks, 16);
   metrics_kernel<<<grid, threads, 0, st>>>(C, central_of(cfg.scheme, scheme_alpha_of(cfg)), cfg.interp, interp_points(cfg.scheme), M);
   return cudaGetLastError();
 }

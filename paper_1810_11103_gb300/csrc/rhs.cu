@@ -198,7 +198,7 @@ cudaError_t launch_check_state(const fsp_block& blk, int precision, double gamma
   if (e != cudaSuccess) return e;
   const long long N = (long long)blk.ni * blk.nj;
   const long long want = (N + 255) / 256;
-  const int grid = (int)(want < 152 * 4 ? want : 152 * 4);
+  const int grid = stride_grid(want, 4);
   auto f = reinterpret_cast<unsigned long long*>(first);
   if (precision == FSP_FP64)
     check_state_kernel<double><<<grid, 256, 0, st>>>(blk.ni, blk.nj, blk.ld, gamma - 1.0, static_cast<const double*>(Q), f);
@@ -214,7 +214,7 @@ cudaError_t launch_norms(const fsp_block& blk, int precision, const void* A, con
   if (e != cudaSuccess) return e;
   const long long N = (long long)blk.ni * blk.nj;
   const long long want = (N + 255) / 256;
-  const int grid = (int)(want < 152 * 4 ? want : 152 * 4);
+  const int grid = stride_grid(want, 4);
   if (precision == FSP_FP64)
     norms_kernel<double><<<grid, 256, 0, st>>>(blk.ni, blk.nj, blk.ld, static_cast<const double*>(A),
                                                static_cast<const double*>(B), out);

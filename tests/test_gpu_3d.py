@@ -163,3 +163,30 @@ def test_rhs_parity_long_thin_blocks(F, shape):
     R_o = O.rhs3(cfgd, M, q)
     R_g = _host(F.rhs3(F.Config.from_dict(cfgd), blk, _dev(M), _dev(q)))
     assert _rel(R_g, R_o) < TOL, _rel(R_g, R_o)
+
+
+@pytest.mark.parametrize("nk", [1, 2])
+def test_single_layer_blocks_reduce_to_two_dimensions(F, nk):
+    """The degenerate case of a block one or two nodes deep, periodic in k: a two-dimensional
+    grid extruded along k with a state independent of k.  The three-dimensional kernels equal
+    the oracle, and their flux differences equal the two-dimensional kernels' (a separate code
+    path) on the same grid; the w equation stays at round-off."""
+    x, y, per = I.periodic_square(45, 8.0, 0.2, seed=21, nj=37)
+    q2 = I.isentropic_vortex(x, y, (4.0, 4.0), strength=5.0, free=(1.0, 1.0, 0.5, 1.0), period=(8.0, 8.0))
+    X, Y, Z = I.extrude(x, y, nk)
+    per3 = ((8.0, 0.0, 0.0), (0.0, 8.0, 0.0), (0.0, 0.0, float(nk)))
+    Q3 = np.stack([q2[0], q2[1], q2[2], 0.0 * q2[0], q2[3]])[:, None].repeat(nk, axis=1)
+    c3 = dict(scheme=2, period=per3, bc=(0,) * 6)
+    blk = F.block3_of(_dev(X), (0,) * 6, per3)
+    M3 = _metrics(F, c3, blk, X, Y, Z)
+    R3 = _host(F.rhs3(F.Config.from_dict(c3), blk, _dev(M3), _dev(Q3)))
+    assert _rel(R3, O.rhs3(c3, M3, Q3)) < TOL
+    c2 = dict(scheme=2, period=per)
+    M2 = _host(F.metrics(F.Config.from_dict(c2), _dev(x), _dev(y)))
+    R2 = _host(F.rhs(F.Config.from_dict(c2), _dev(M2), _dev(q2)))
+    D3 = R3 * M3[9, G:-G, G:-G, G:-G][None]
+    D2 = R2 * M2[4, G:-G, G:-G][None]
+    scale = np.abs(D2).max()
+    for v3, v2 in ((0, 0), (1, 1), (2, 2), (4, 3)):
+        assert np.abs(D3[v3] - D2[v2][None]).max() < 1e-12 * scale, v3
+    assert np.abs(D3[3]).max() < 1e-14 * scale
