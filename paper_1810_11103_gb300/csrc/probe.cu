@@ -44,6 +44,18 @@ cudaError_t launch_widen_to_double(const float* in, double* oi, double* oh, long
   return cudaGetLastError();
 }
 
+__global__ void reciprocal_check_kernel(const double* in, double* onr, double* oieee, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    onr[k] = rcp_nr(in[k]);
+    oieee[k] = 1.0 / in[k];
+  }
+}
+
+cudaError_t launch_reciprocal_check(const double* in, double* onr, double* oieee, long long n, cudaStream_t st) {
+  if (n > 0) reciprocal_check_kernel<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(in, onr, oieee, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fma_peak(int precision, int blocks, int iters, void* sink, cudaStream_t st) {
   if (precision == FSP_FP64)
     fma_peak_kernel<double><<<blocks, 256, 0, st>>>(iters, static_cast<double*>(sink));

@@ -128,6 +128,7 @@ def lib():
                 "fsp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
                 "fsp_round_to_float": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
                 "fsp_widen_to_double": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
+                "fsp_reciprocal_check": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
                 "fsp_vjp_workspace_size": (ctypes.c_int, [C, B, ctypes.POINTER(ctypes.c_size_t)]),
                 "fsp_rhs_vjp": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_rk3_step_vjp": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -422,6 +423,14 @@ def widen_to_double(x: torch.Tensor, stream=None):
     a, b = torch.empty(x.shape, dtype=torch.float64, device=x.device), torch.empty(x.shape, dtype=torch.float64,
                                                                                      device=x.device)
     _check("fsp_widen_to_double", lib().fsp_widen_to_double(_ptr(x), _ptr(a), _ptr(b), x.numel(), _stream(stream)))
+    return a, b
+
+
+def reciprocal_check(x: torch.Tensor, stream=None):
+    """(the kernels' reciprocal, the IEEE reciprocal) of a float64 device tensor."""
+    x = x.contiguous()
+    a, b = torch.empty_like(x), torch.empty_like(x)
+    _check("fsp_reciprocal_check", lib().fsp_reciprocal_check(_ptr(x), _ptr(a), _ptr(b), x.numel(), _stream(stream)))
     return a, b
 
 

@@ -67,3 +67,20 @@ def test_integer_widening_matches_the_hardware(F):
     assert np.isnan(a[nan]).all()
     assert np.array_equal(a[~nan].view(np.uint64), b[~nan].view(np.uint64))
     assert np.array_equal(b[~nan], x[~nan].astype(np.float64))
+
+
+def test_fp64_reciprocal_within_ulps_of_ieee(F):
+    """rcp_nr (the hardware seed and one third-order Householder step), used by every FP64
+    kernel for densities, J^-1 and weight sums: within 2 ulps of the correctly rounded 1/x
+    over normal operands of both signs across the exponent range (the seed flushes
+    subnormals, so reciprocals of numbers beyond 2^1022 are not taken)."""
+    rng = np.random.default_rng(1810)
+    mag = 2.0 ** rng.uniform(-1000, 1000, 200000)
+    x = mag * np.where(rng.random(200000) < 0.5, -1.0, 1.0)
+    x = np.concatenate([x, [1.0, 3.0, 0.1, 1.0 / 3.0, 2.0 ** -1000, 1.5 * 2.0 ** 1000]])
+    a, b = F.reciprocal_check(torch.as_tensor(x, device="cuda"))
+    torch.cuda.synchronize()
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    assert np.array_equal(b, 1.0 / x)
+    ulp = np.spacing(np.abs(b))
+    assert (np.abs(a - b) <= 2 * ulp).all(), float((np.abs(a - b) / ulp).max())
