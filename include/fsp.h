@@ -324,13 +324,16 @@ fsp_status fsp_round_to_float(const double* in, float* out_int, float* out_hw, l
 fsp_status fsp_widen_to_double(const float* in, double* out_int, double* out_hw, long long n, void* stream);
 
 /*
- * fsp_reciprocal_check -- diagnostic of the FP64 kernels' reciprocal: for each of the n doubles
- * in[k] (device), out_fast[k] receives the reciprocal the kernels use (the hardware's
- * approximate reciprocal refined by one third-order Householder step) and out_ieee[k] the
- * correctly rounded 1/in[k].  They agree to a few ulps for normal operands.  No counterpart in
- * the paper.  FSP_ERR_INVALID_ARG for n < 0 or a pointer that is not device memory.
+ * fsp_reciprocal_check -- diagnostic of the FP64 kernels' reciprocal and reciprocal square
+ * root: for each of the n doubles in[k] (device), out (4 n doubles, device) receives at k the
+ * reciprocal the kernels use (the hardware's approximate reciprocal refined by one third-order
+ * Householder step), at n + k the correctly rounded 1/in[k], at 2 n + k the reciprocal square
+ * root the kernels use (the hardware's approximation refined by one third-order step) and at
+ * 3 n + k the IEEE 1/sqrt(in[k]) (two roundings); both square-root entries are 0 for
+ * in[k] <= 0.  They agree to a few ulps for normal operands.  No counterpart in the paper.
+ * FSP_ERR_INVALID_ARG for n < 0 or a pointer that is not device memory.
  */
-fsp_status fsp_reciprocal_check(const double* in, double* out_fast, double* out_ieee, long long n, void* stream);
+fsp_status fsp_reciprocal_check(const double* in, double* out, long long n, void* stream);
 
 /*
  * ---- Multi-block grids --------------------------------------------------------------

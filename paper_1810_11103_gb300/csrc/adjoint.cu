@@ -183,7 +183,7 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
     // midpoint metrics mm = sum_k c_k m(c0 - 2 + k) and the interface direction
     const int o0 = SI(l, c0), o1 = SI(l, c0 + 1);
     const double mbx = 0.5 * (sM[o0] + sM[o1]), mby = 0.5 * (sM[NN + o0] + sM[NN + o1]);
-    const double rn = rsqrt(mbx * mbx + mby * mby);
+    const double rn = rsq(mbx * mbx + mby * mby);
     const double nx = mbx * rn, ny = mby * rn;
     // midpoint interpolation over nodes p-2..p+3, or p-3..p+4 for r = 4
     constexpr int NI = Sc::r == 4 ? 8 : 6, IOFF = Sc::r == 4 ? 3 : 2;

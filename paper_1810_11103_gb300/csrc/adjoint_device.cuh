@@ -311,7 +311,7 @@ __device__ __forceinline__ void prim_bwd(const double q[4], double gamma, PrimBa
   const double h2 = 0.5 * (u * u + v * v);
   const double p = gm1 * (q[3] - q[0] * h2);
   const double c2 = gamma * p * rinv;
-  const double cinv = rsqrt(c2);
+  const double cinv = rsq(c2);
   // b1 = gm1 cinv^2
   pb.cinv += 2.0 * gm1 * cinv * pb.b1;
   // H = (q3 + p) rinv

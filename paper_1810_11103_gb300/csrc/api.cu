@@ -290,11 +290,11 @@ fsp_status fsp_round_to_float(const double* in, float* out_int, float* out_hw, l
   return cuda_status(launch_round_to_float(in, out_int, out_hw, n, (cudaStream_t)stream));
 }
 
-fsp_status fsp_reciprocal_check(const double* in, double* out_fast, double* out_ieee, long long n, void* stream) {
+fsp_status fsp_reciprocal_check(const double* in, double* out, long long n, void* stream) {
   if (n < 0) return FSP_ERR_INVALID_ARG;
   if (n == 0) return FSP_OK;
-  if (!device_pointer(in) || !device_pointer(out_fast) || !device_pointer(out_ieee)) return FSP_ERR_INVALID_ARG;
-  return cuda_status(launch_reciprocal_check(in, out_fast, out_ieee, n, (cudaStream_t)stream));
+  if (!device_pointer(in) || !device_pointer(out)) return FSP_ERR_INVALID_ARG;
+  return cuda_status(launch_reciprocal_check(in, out, n, (cudaStream_t)stream));
 }
 
 fsp_status fsp_widen_to_double(const float* in, double* out_int, double* out_hw, long long n, void* stream) {

@@ -248,7 +248,18 @@ __device__ __forceinline__ double rcp_nr(double x) {
   const double e = fma(-x, r, 1.0);
   return fma(r, fma(e, e, e), r);
 }
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+// FP64 reciprocal square root: the hardware seed (PTX rsqrt.approx.ftz.f64) refined once by
+// the third-order step of the binomial series 1/sqrt(x) = y / sqrt(1 - e) = y (1 + e/2 +
+// 3 e^2/8 + ...), e = 1 - x y^2: a seed of relative error d leaves about d^3.  Two products
+// and three fused multiply-adds, for the positive normal operands of this code (sound speeds
+// squared, metric norms); within a few ulps of 1/sqrt(x) (fsp_reciprocal_check).
+__device__ __forceinline__ double rsq_nr(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y * y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
+}
+__device__ __forceinline__ double rsq(double x) { return rsq_nr(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrt_approx(x); }
 // quotient: a times the refined reciprocal in FP64, a times the approximate reciprocal in FP32
 __device__ __forceinline__ double quot(double a, double b) { return a * rcp_nr(b); }
@@ -376,8 +387,8 @@ __device__ __forceinline__ Real spectral_radius(const Real q[4], Real mx, Real m
   const Real rinv = recip(q[0]);
   const Real u = q[1] * rinv, v = q[2] * rinv;
   const Real p = (gamma - Real(1)) * (q[3] - Real(0.5) * (q[1] * u + q[2] * v));
-  const Real c = sqrt(gamma * p * rinv);
-  return fabs(mx * u + my * v) + c * sqrt(mx * mx + my * my);
+  // c |k^| = sqrt(gamma p / rho |k^|^2): one square root
+  return fabs(mx * u + my * v) + sqrt(gamma * p * rinv * (mx * mx + my * my));
 }
 
 // Primitive quantities of a node used by the characteristic projection (Section 3.4).

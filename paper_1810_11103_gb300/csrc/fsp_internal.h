@@ -59,6 +59,6 @@ cudaError_t launch_norms(const fsp_block& blk, int precision, const void* A, con
 cudaError_t launch_fma_peak(int precision, int blocks, int iters, void* sink, cudaStream_t st);
 cudaError_t launch_round_to_float(const double* in, float* oi, float* oh, long long n, cudaStream_t st);
 cudaError_t launch_widen_to_double(const float* in, double* oi, double* oh, long long n, cudaStream_t st);
-cudaError_t launch_reciprocal_check(const double* in, double* onr, double* oieee, long long n, cudaStream_t st);
+cudaError_t launch_reciprocal_check(const double* in, double* out, long long n, cudaStream_t st);
 
 }  // namespace fsp

@@ -44,15 +44,19 @@ cudaError_t launch_widen_to_double(const float* in, double* oi, double* oh, long
   return cudaGetLastError();
 }
 
-__global__ void reciprocal_check_kernel(const double* in, double* onr, double* oieee, long long n) {
+// out[0..n): rcp_nr, [n..2n): 1/x; [2n..3n): rsq_nr, [3n..4n): 1/sqrt(x) (two IEEE roundings)
+__global__ void reciprocal_check_kernel(const double* in, double* out, long long n) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    onr[k] = rcp_nr(in[k]);
-    oieee[k] = 1.0 / in[k];
+    const double x = in[k];
+    out[k] = rcp_nr(x);
+    out[n + k] = 1.0 / x;
+    out[2 * n + k] = x > 0.0 ? rsq_nr(x) : 0.0;
+    out[3 * n + k] = x > 0.0 ? 1.0 / sqrt(x) : 0.0;
   }
 }
 
-cudaError_t launch_reciprocal_check(const double* in, double* onr, double* oieee, long long n, cudaStream_t st) {
-  if (n > 0) reciprocal_check_kernel<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(in, onr, oieee, n);
+cudaError_t launch_reciprocal_check(const double* in, double* out, long long n, cudaStream_t st) {
+  if (n > 0) reciprocal_check_kernel<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(in, out, n);
   return cudaGetLastError();
 }
 

@@ -128,7 +128,7 @@ def lib():
                 "fsp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
                 "fsp_round_to_float": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
                 "fsp_widen_to_double": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
-                "fsp_reciprocal_check": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
+                "fsp_reciprocal_check": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
                 "fsp_vjp_workspace_size": (ctypes.c_int, [C, B, ctypes.POINTER(ctypes.c_size_t)]),
                 "fsp_rhs_vjp": (ctypes.c_int, [C, B, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
                 "fsp_rk3_step_vjp": (ctypes.c_int, [C, B, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -427,11 +427,12 @@ def widen_to_double(x: torch.Tensor, stream=None):
 
 
 def reciprocal_check(x: torch.Tensor, stream=None):
-    """(the kernels' reciprocal, the IEEE reciprocal) of a float64 device tensor."""
+    """(the kernels' reciprocal, the IEEE reciprocal, the kernels' reciprocal square root, the
+    IEEE 1/sqrt) of a float64 device tensor (square-root entries 0 where x <= 0)."""
     x = x.contiguous()
-    a, b = torch.empty_like(x), torch.empty_like(x)
-    _check("fsp_reciprocal_check", lib().fsp_reciprocal_check(_ptr(x), _ptr(a), _ptr(b), x.numel(), _stream(stream)))
-    return a, b
+    out = torch.empty((4,) + tuple(x.shape), dtype=x.dtype, device=x.device)
+    _check("fsp_reciprocal_check", lib().fsp_reciprocal_check(_ptr(x), _ptr(out), x.numel(), _stream(stream)))
+    return tuple(out)
 
 
 def fma_peak(precision: int, blocks: int, iters: int, sink: torch.Tensor, stream=None):

@@ -73,14 +73,19 @@ def test_fp64_reciprocal_within_ulps_of_ieee(F):
     """rcp_nr (the hardware seed and one third-order Householder step), used by every FP64
     kernel for densities, J^-1 and weight sums: within 2 ulps of the correctly rounded 1/x
     over normal operands of both signs across the exponent range (the seed flushes
-    subnormals, so reciprocals of numbers beyond 2^1022 are not taken)."""
+    subnormals, so reciprocals of numbers beyond 2^1022 are not taken); rsq_nr, used for
+    sound speeds and metric norms, within 3 ulps of 1/sqrt(x) (itself two roundings)."""
     rng = np.random.default_rng(1810)
     mag = 2.0 ** rng.uniform(-1000, 1000, 200000)
     x = mag * np.where(rng.random(200000) < 0.5, -1.0, 1.0)
     x = np.concatenate([x, [1.0, 3.0, 0.1, 1.0 / 3.0, 2.0 ** -1000, 1.5 * 2.0 ** 1000]])
-    a, b = F.reciprocal_check(torch.as_tensor(x, device="cuda"))
-    torch.cuda.synchronize()
-    a, b = a.cpu().numpy(), b.cpu().numpy()
+    a, b, c, d = (t.cpu().numpy() for t in F.reciprocal_check(torch.as_tensor(x, device="cuda")))
     assert np.array_equal(b, 1.0 / x)
     ulp = np.spacing(np.abs(b))
     assert (np.abs(a - b) <= 2 * ulp).all(), float((np.abs(a - b) / ulp).max())
+    # rsq_nr (the hardware seed and one third-order step) for the positive operands
+    pos = x > 0
+    ref = 1.0 / np.sqrt(x[pos])
+    assert np.array_equal(d[pos], ref) and (c[~pos] == 0).all()
+    ulp = np.spacing(ref)
+    assert (np.abs(c[pos] - ref) <= 3 * ulp).all(), float((np.abs(c[pos] - ref) / ulp).max())
