@@ -888,6 +888,14 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 quot2(float2 a, float2 b) {
   return mul2(a, make_float2(rcp_approx(b.x), rcp_approx(b.y)));
 }
+// K q with K = Kn for q <= 0 and Kp for q > 0, without a per-lane select: the smaller factor
+// times q plus the difference times min(q, 0) or max(q, 0), so that the exact side is the one
+// with the smaller factor and the correction never cancels more than one binary digit.
+__device__ __forceinline__ float2 kq2(float Kn, float Kp, float2 q) {
+  if (fabsf(Kn) >= fabsf(Kp))
+    return fma2(bc2(Kn - Kp), make_float2(fminf(q.x, 0.0f), fminf(q.y, 0.0f)), mul2(bc2(Kp), q));
+  return fma2(bc2(Kp - Kn), make_float2(fmaxf(q.x, 0.0f), fmaxf(q.y, 0.0f)), mul2(bc2(Kn), q));
+}
 __device__ __forceinline__ float2 is_b2(float2 e, float2 f, float2 eps) {
   return fma2(mul2(bc2(13.0f / 12), e), e, fma2(mul2(bc2(0.25f), f), f, eps));
 }
@@ -928,7 +936,10 @@ __device__ __forceinline__ float2 is_b4x2(float2 e, float2 f, float2 eps4) {
   return fma2(mul2(bc2(13.0f / 3), e), e, fma2(f, f, eps4));
 }
 
-template <int R>
+// NOSEL: the mapping's factor without per-lane selects (kq2), for r = 2 and 3; it saves issue
+// slots in the float passes (FP32 marching xi 0.213 -> 0.210 ms) and costs the mixed eta pass
+// registers (0.797 -> 0.822 ms), so the callers take it for the FP32 path only.
+template <int R, bool NOSEL = false>
 __device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int ppm, int linw, int wz = 0) {
   const float2 eps = bc2(eps_);
   if constexpr (R == 4) {
@@ -1003,8 +1014,13 @@ __device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const float2 q = fma2(t[k], inv, bc2(-C[k]));
-        const float2 K = make_float2(nonpos(q.x) ? K0[k] : K1[k], nonpos(q.y) ? K0[k] : K1[k]);
-        const float2 g = fma2(mul2(mul2(q, q), q), K, bc2(C[k]));
+        float2 g;
+        if constexpr (NOSEL) {
+          g = fma2(mul2(q, q), kq2(K0[k], K1[k], q), bc2(C[k]));
+        } else {
+          const float2 K = make_float2(nonpos(q.x) ? K0[k] : K1[k], nonpos(q.y) ? K0[k] : K1[k]);
+          g = fma2(mul2(mul2(q, q), q), K, bc2(C[k]));
+        }
         num = k == 0 ? mul2(g, P[0]) : fma2(g, P[k], num);
         den = k == 0 ? g : add2(den, g);
       }
@@ -1035,8 +1051,13 @@ __device__ __forceinline__ float2 weno_delta_x2(const float2* u, float eps_, int
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const float2 q = fma2(t[k], inv, bc2(-C[k]));
-        const float2 K = make_float2(nonpos(q.x) ? K0[k] : K1[k], nonpos(q.y) ? K0[k] : K1[k]);
-        const float2 g = fma2(mul2(q, q), K, bc2(C[k]));
+        float2 g;
+        if constexpr (NOSEL) {
+          g = fma2(q, kq2(K0[k], K1[k], q), bc2(C[k]));
+        } else {
+          const float2 K = make_float2(nonpos(q.x) ? K0[k] : K1[k], nonpos(q.y) ? K0[k] : K1[k]);
+          g = fma2(mul2(q, q), K, bc2(C[k]));
+        }
         num = k == 0 ? mul2(g, P[0]) : fma2(g, P[k], num);
         den = k == 0 ? g : add2(den, g);
       }

@@ -375,7 +375,7 @@ __device__ __forceinline__ void mid_fluxes(const Staged<Real, Acc>& st, const At
 // differences wd[a][k] at the stencil offsets -H..-1, +1..+H (the result scaled by
 // weno_scale<R>); FP32 runs components (0, 1) and (2, 3) in the two lanes of packed float
 // arithmetic.
-template <int R, typename Real>
+template <int R, typename Real, bool NOSEL = false>
 __device__ __forceinline__ void side_weno(const Real (*wd)[4], Real eps, int ppm, int linw, Real Wm[4], int wz = 0) {
   constexpr int H = R == 4 ? 3 : 2, NA = 2 * H;
   if constexpr (std::is_same<Real, float>::value) {
@@ -385,7 +385,7 @@ __device__ __forceinline__ void side_weno(const Real (*wd)[4], Real eps, int ppm
 #pragma unroll
       for (int a = 0; a < NA; ++a) u[a < H ? a : a + 1] = make_float2(wd[a][2 * kp], wd[a][2 * kp + 1]);
       u[H] = make_float2(0.f, 0.f);
-      const float2 W2 = weno_delta_x2<R>(u, eps, ppm, linw, wz);
+      const float2 W2 = weno_delta_x2<R, NOSEL>(u, eps, ppm, linw, wz);
       Wm[2 * kp] = W2.x;
       Wm[2 * kp + 1] = W2.y;
     }
@@ -518,7 +518,7 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
       E.project(t[0] - qc[0], t[1] - qc[1], t[2] - qc[2], t[3] - qc[3], wd[a]);
     }
     Real Wm[4];
-    side_weno<Sc::r, Real>(wd, eps, ppm, linw, Wm, wz);
+    side_weno<Sc::r, Real, std::is_same<Acc, float>::value>(wd, eps, ppm, linw, Wm, wz);
     E.recon(Wm, qc, Qs[side]);
   }
 
