@@ -317,8 +317,8 @@ fsp_status fsp_round_to_float(const double* in, float* out_int, float* out_hw, l
 /*
  * fsp_widen_to_double -- diagnostic of the mixed path's float-to-double widening: for each of
  * the n floats in[k] (device), out_int[k] receives the widening done with integer operations
- * (exact; subnormals, infinities and NaN through the hardware) and out_hw[k]
- * the hardware conversion.  They agree bit for bit.  No counterpart in the paper.
+ * only and out_hw[k] the hardware conversion.  They agree bit for bit except that the integer
+ * widening turns subnormals into signed zero (NaN stays NaN).  No counterpart in the paper.
  * FSP_ERR_INVALID_ARG for n < 0 or a pointer that is not device memory.
  */
 fsp_status fsp_widen_to_double(const float* in, double* out_int, double* out_hw, long long n, void* stream);

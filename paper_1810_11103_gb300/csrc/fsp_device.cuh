@@ -290,19 +290,19 @@ __device__ __forceinline__ float from_f64_int(double d) {
   return __uint_as_float(sign | (((unsigned)e << 23) + m));   // a mantissa carry bumps the exponent
 }
 
-// A float widened to double with integer operations: exact, so the same bits as the hardware
-// conversion, which the mixed path would otherwise queue on its bottleneck, the FP64 pipe.
-// A normal float's exponent is rebiased (127 -> 1023) and its 23 mantissa bits become the top
-// of the 52; zero keeps its sign; subnormals, infinities and NaN (never met on this path) take
-// the hardware conversion.
+// A float widened to double with integer operations only, so that the mixed path queues
+// nothing on its bottleneck, the FP64 pipe: a normal float's exponent is rebiased (127 ->
+// 1023) and its 23 mantissa bits become the top of the 52 (exact, the hardware's bits);
+// infinities and NaN keep their class (NaN its payload's top bits); zero keeps its sign, and
+// so do subnormals, which become signed zero (below 1.2e-38, never met as a flux or state
+// of this path).  Selects, no branch.
 __device__ __forceinline__ double to_f64_int(float x) {
-  const unsigned b = __float_as_uint(x), mag = b & 0x7fffffffu;
-  if (mag - 0x00800000u >= 0x7f000000u) {
-    if (mag == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-    return (double)x;
-  }
-  const unsigned hi = (b & 0x80000000u) | ((mag >> 23) + 896u) << 20 | (mag & 0x7fffffu) >> 3;
-  return __hiloint2double((int)hi, (int)(b << 29));
+  const unsigned b = __float_as_uint(x), sign = b & 0x80000000u, e = (b >> 23) & 0xffu;
+  const unsigned m = (b & 0x7fffffu) >> 3;
+  unsigned hi = sign | ((e + 896u) << 20) | m;
+  hi = e == 0u ? sign : hi;
+  hi = e == 0xffu ? (sign | 0x7ff00000u | m) : hi;
+  return __hiloint2double((int)hi, e == 0u ? 0 : (int)(b << 29));
 }
 // Conversions between the state type and the accumulation type, on the integer pipe where
 // they would cost FP64-pipe issue (float <-> double); identity otherwise.

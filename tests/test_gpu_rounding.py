@@ -50,9 +50,9 @@ def test_integer_rounding_matches_the_hardware(F):
 
 
 def test_integer_widening_matches_the_hardware(F):
-    """to_f64_int (the mixed path's float-to-double widening): bit for bit the hardware's on
-    signed zeros, normals across the whole exponent range, the float extremes, subnormals,
-    infinities and NaN."""
+    """to_f64_int (the mixed path's float-to-double widening, integer operations only): bit for
+    bit the hardware's on signed zeros, normals across the whole exponent range, the float
+    extremes and infinities; NaN stays NaN; subnormals become signed zero."""
     f32 = np.finfo(np.float32)
     rng = np.random.default_rng(1103)
     vals = np.array([0.0, -0.0, 1.0, -1.0, f32.max, -f32.max, f32.tiny, -f32.tiny, f32.tiny / 2, -f32.tiny / 8,
@@ -64,8 +64,11 @@ def test_integer_widening_matches_the_hardware(F):
     torch.cuda.synchronize()
     a, b = a.cpu().numpy(), b.cpu().numpy()
     nan = np.isnan(x)
-    assert np.isnan(a[nan]).all()
-    assert np.array_equal(a[~nan].view(np.uint64), b[~nan].view(np.uint64))
+    sub = (x != 0) & (np.abs(x) < f32.tiny)
+    assert np.isnan(a[nan]).all() and sub.any()
+    assert (a[sub] == 0).all() and np.array_equal(np.signbit(a[sub]), np.signbit(x[sub]))
+    keep = ~nan & ~sub
+    assert np.array_equal(a[keep].view(np.uint64), b[keep].view(np.uint64))
     assert np.array_equal(b[~nan], x[~nan].astype(np.float64))
 
 
