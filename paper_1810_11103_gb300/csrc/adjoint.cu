@@ -137,7 +137,7 @@ vjp_sweep_kernel(Params P, const double* __restrict__ Q, const double* __restric
     if (graw >= 0 && graw < n) {
       const int i = DIR == 0 ? graw : line, j = DIR == 0 ? line : graw;
       const long long go = (long long)j * P.ld + i;
-      const double mJ = -1.0 / met_at(P, 4, i, j);
+      const double mJ = -rcp_nr(met_at(P, 4, i, j));
 #pragma unroll
       for (int v = 0; v < 4; ++v) sR[v * NN + o] = gbar[v * plane + go] * mJ;
     }
