@@ -379,11 +379,12 @@ class Ctx:
 def launches_per_step(args, head):
     """Kernels of one batched RK3 step: per stage an xi and an eta sweep, plus the line maxima of
     every stage, or of the first only when the marching eta pass takes them (not in mixed
-    precision); the vortex workload's single-block step always has three."""
+    precision), plus the midpoint metrics once per step (FP64 and mixed batches); the vortex
+    workload's single-block step always has three per stage."""
     if args.workload != "cylinder64":
         return 9
     fused = (head.get("tiles") or {}).get("eta", {}).get("variant") == 3 and args.precision != "mixed"
-    return 7 if fused else 9
+    return (7 if fused else 9) + (args.precision != "fp32")
 
 
 def measure_cylinder(args, prec, C, per_block=False):
@@ -432,7 +433,16 @@ def measure_cylinder(args, prec, C, per_block=False):
     peak, pipe = C.peak(prec)
     t_dev, t_e2e = C.max_over_ranks(t_dev, t_e2e)
     fl = algorithmic_flops(args)
-    achieved = fl["sweep_xi_per_node"] * nodes / t_k / 1e12
+    # FP64 and mixed batches store the midpoint metrics once per step (mid_batch_kernel) and the
+    # marching passes read them: their interpolation leaves the passes' counts and enters the
+    # step's once instead of three times
+    mid_if = fl["mid_interp_per_interface"] if prec != "fp32" else 0
+    mid_xi = fl["xi_interfaces_per_node"] * mid_if * (tiles["xi"]["variant"] == 3)
+    mid_eta = fl["eta_interfaces_per_node"] * mid_if * (tiles["eta"]["variant"] == 3)
+    xi_fl = fl["sweep_xi_per_node"] - mid_xi
+    eta_fl = fl["sweep_eta_per_node"] - 4.0 - mid_eta
+    step_fl = 3 * fl["rhs_per_node"] - 2 * (mid_xi + mid_eta)
+    achieved = xi_fl * nodes / t_k / 1e12
     rhs_total = job_rhs(nodes, args.steps, C.world)
     kname = ("march_batch_kernel xi (marching warps)" if tiles["xi"]["variant"] == 3 else "sweep_batch_kernel xi") \
         + ", all 64 blocks (fsp_batch_flux_difference dir 0)"
@@ -442,14 +452,16 @@ def measure_cylinder(args, prec, C, per_block=False):
             "traffic": traffic_of(args, prec, tiles["xi"]["variant"]),
             "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
             "nominal_peak": nom, "frac_vs_nominal": achieved / nom,
-            "flops_per_node": fl["sweep_xi_per_node"], "units_per_launch": nodes,
+            "flops_per_node": xi_fl, "units_per_launch": nodes,
             "kernel_ms": 1e3 * t_k,
             # the other sweep and the whole step against the same peak
-            "eta": {"kernel_ms": 1e3 * t_e, "flops_per_node": fl["sweep_eta_per_node"] - 4.0,
-                    "frac": (fl["sweep_eta_per_node"] - 4.0) * nodes / t_e / 1e12 / peak},
-            "step_frac": 3 * fl["rhs_per_node"] * nodes / (t_dev / args.steps) / 1e12 / peak}
+            "eta": {"kernel_ms": 1e3 * t_e, "flops_per_node": eta_fl, "frac": eta_fl * nodes / t_e / 1e12 / peak},
+            "step_frac": step_fl * nodes / (t_dev / args.steps) / 1e12 / peak,
+            "midpoint_metrics": ({"flops_per_node_per_step": mid_xi + mid_eta,
+                                  "how": "interpolated once per step by mid_batch_kernel; left out of the "
+                                         "passes' counts"} if mid_if else None)}
     if prec == "mixed":
-        roof = mixed_roofline(args, C, roof, fl["sweep_xi_per_node"], nodes, t_k, clk.get("sm_mhz"))
+        roof = mixed_roofline(args, C, roof, xi_fl, nodes, t_k, clk.get("sm_mhz"), hoisted=mid_xi > 0)
     out = {
         "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps, "nodes": nodes,
         "nblocks": len(blocks),
@@ -488,12 +500,15 @@ def measure_cylinder(args, prec, C, per_block=False):
 # midpoint products (one mean flux, 4 x 3; two-midpoint schemes both sides, 4 x 6), central
 # combination of node pairs and midpoint terms, double + float parts and the difference (4 + 4).
 MIXED_FP64_FLOPS = {0: 70, 1: 86, 2: 90, 3: 106, 4: 108}
+# of which the midpoint metric interpolation, which a batch with stored midpoint metrics no
+# longer does in the passes
+MIXED_FP64_MID_FLOPS = {0: 10, 1: 10, 2: 18, 3: 18, 4: 24}
 
 
-def mixed_roofline(args, C, roof, flops_node, nodes, t_k, mhz):
+def mixed_roofline(args, C, roof, flops_node, nodes, t_k, mhz, hoisted=False):
     """Roofline of the mixed path: t_roof = max(FP32 flops / FP32 peak, FP64 flops / FP64
     peak); the FP64 part bounds it.  The FP32 part is the rest of the algorithmic count."""
-    f64 = MIXED_FP64_FLOPS[args.scheme]
+    f64 = MIXED_FP64_FLOPS[args.scheme] - (MIXED_FP64_MID_FLOPS[args.scheme] if hoisted else 0)
     f32 = flops_node - f64
     p64, _ = C.peak("fp64")
     p32 = roof["peak"]

@@ -346,7 +346,11 @@ fsp_status fsp_reciprocal_check(const double* in, double* out, long long n, void
  * ghost coordinates follow links, periodic wraps or odd reflection through up to eight
  * layers, corners included.  Line maxima of the splitting are taken per block line.
  * The handle owns its device memory (descriptors, tile tables, per-block line maxima,
- * xi accumulators and RK stage states) from create to destroy; no other call allocates.
+ * xi accumulators, RK stage states and, for FSP_FP64 and FSP_FP32_MIXED, the midpoint
+ * metrics of every interface) from create to destroy; no other call allocates.  The midpoint
+ * metrics (the interpolation of Section 2.4) are taken from the bound metrics at the start of
+ * each fsp_batch_rhs, fsp_batch_rk3_step and fsp_batch_tune, so the marching passes read them
+ * instead of interpolating per right-hand side.
  * Each pass runs all blocks in one launch over a table of tiles (NL lines x T nodes, see
  * fsp_batch_tune); ghosts of linked faces are read straight from the neighbour's state,
  * so no halo copies are made.  Calls on one handle must not overlap.
@@ -377,7 +381,8 @@ fsp_status fsp_batch_rhs(fsp_batch* b, void* const* dQdt, void* stream);
 /* One direction (dir 0 = xi, 1 = eta) of every block, as fsp_flux_difference mode 0: the
  * difference H_{s+1/2} - H_{s-1/2} into D[b] (host array of device pointers; double for
  * FSP_FP64 and FSP_FP32_MIXED, float for FSP_FP32), for the bound states, with the line
- * maxima left by the last fsp_batch_rhs on this handle.  One launch over all blocks. */
+ * maxima (and midpoint metrics) left by the last fsp_batch_rhs on this handle.  One launch
+ * over all blocks. */
 fsp_status fsp_batch_flux_difference(fsp_batch* b, int dir, void* const* D, void* stream);
 /* One TVD-RK3 step of every block in lockstep; launches the captured graph when one was
  * captured for this dt. */
@@ -393,7 +398,7 @@ fsp_status fsp_batch_rk3_step(fsp_batch* b, double dt, void* stream);
  * a null or device pointer or an unbound handle. */
 fsp_status fsp_batch_rk3_step_host(fsp_batch* b, const void* const* q_in, void* const* q_out, double dt,
                                    void* stream);
-/* Runs one step, then records one RK3 step (9 kernels, 3 memsets) as a CUDA graph that
+/* Runs one step, then records one RK3 step (its kernels and memsets) as a CUDA graph that
  * later fsp_batch_rk3_step calls with the same dt launch as a whole.  The eager step
  * advances the state like any other step. */
 fsp_status fsp_batch_capture_graph(fsp_batch* b, double dt, void* stream);

@@ -1327,6 +1327,17 @@ long long orc_count_flops(const int* ip, const double* dp, int ni, int nj, const
   return g_flops;
 }
 
+// Floating-point operations of one midpoint interpolation I of a nodal quantity (Section 2.4)
+// for a scheme and interpolation option: the work per component that a solver storing the
+// midpoint metrics once per grid no longer repeats in each right-hand side.
+long long orc_count_mid_interp(int scheme, int interp) {
+  if (scheme < 0 || scheme > 5 || interp < 0 || interp > 1) return -1;
+  g_flops = 0;
+  const Counted r = interp_mid<Counted>(scheme, interp, [](int l) { return Counted(1.0 + 0.25 * l); });
+  (void)r;
+  return g_flops;
+}
+
 // Floating-point operations by part of one right-hand side:
 // out = {line maxima xi, xi sweep without its line maxima, line maxima eta,
 //        eta sweep without its line maxima, final division by J^-1}.

@@ -173,6 +173,55 @@ __global__ void __launch_bounds__(256) lambda_batch_kernel(const Params* __restr
   }
 }
 
+// Midpoint metrics of every interface of every block (FP64 and mixed batches): the
+// interpolation I of the metric evaluation (Section 2.4) applied to xi_x^, xi_y^ along each
+// row at the xi interfaces q + 1/2, q = -nmp .. ni + nmp - 2, stored at [c][row][q + 2] of
+// [2][nj][ni + 3], and to eta_x^, eta_y^ along each column at [c][q + 2][col] of
+// [2][nj + 3][ni] -- the same nodal values and the same interpolation as the marching passes
+// would take from their staged nodes, so the results are those of interpolating in the pass.
+// Grid (gx, blocks): the CTAs of row y stride over block y's interfaces.
+template <int R>
+__global__ void __launch_bounds__(256) mid_batch_kernel(const Params* __restrict__ Ps, double* const* mxt,
+                                                        double* const* met, int nmp) {
+  const Params& P = Ps[blockIdx.y];
+  double* MX = mxt[blockIdx.y];
+  double* ME = met[blockIdx.y];
+  const int ni = P.ni, nj = P.nj;
+  const int wx = ni + 2 * nmp - 1, we = nj + 2 * nmp - 1;
+  const long long nx = (long long)nj * wx, n = nx + (long long)ni * we;
+  const long long sx = (long long)nj * (ni + 3), se = (long long)(nj + 3) * ni;
+  constexpr int NP = R == 4 ? 8 : 6, OFF = R == 4 ? 3 : 2;
+  auto interp = [&](const double* v) {
+    if constexpr (R == 4) return mid_interp8(P.interp, v);
+    else return mid_interp(P.interp, R == 3, v);
+  };
+  for (long long t = blockIdx.x * 256LL + threadIdx.x; t < n; t += (long long)gridDim.x * 256) {
+    double vx[NP], vy[NP];
+    if (t < nx) {
+      const int row = (int)(t / wx), q = (int)(t % wx) - nmp;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        vx[k] = met_at(P, 0, q - OFF + k, row);
+        vy[k] = met_at(P, 1, q - OFF + k, row);
+      }
+      const long long o = (long long)row * (ni + 3) + q + 2;
+      MX[o] = interp(vx);
+      MX[o + sx] = interp(vy);
+    } else {
+      const long long u = t - nx;
+      const int q = (int)(u / ni) - nmp, col = (int)(u % ni);
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        vx[k] = met_at(P, 2, col, q - OFF + k);
+        vy[k] = met_at(P, 3, col, q - OFF + k);
+      }
+      const long long o = (long long)(q + 2) * ni + col;
+      ME[o] = interp(vx);
+      ME[o + se] = interp(vy);
+    }
+  }
+}
+
 }  // namespace fsp
 
 using namespace fsp;
@@ -199,6 +248,8 @@ struct fsp_batch {
   size_t lam_count = 0;
   std::vector<size_t> lam_off, acc_off, st_off;
   char* d_acc = nullptr;             // xi differences, one per block
+  double* d_mid = nullptr;           // midpoint metrics per block (FP64 and mixed; see mid_batch_kernel)
+  std::vector<size_t> mid_off;       // in doubles
   char* d_q1 = nullptr;              // RK stage states
   char* d_q2 = nullptr;
   void** d_tab = nullptr;            // pointer tables, nb entries each (see Tab)
@@ -212,7 +263,7 @@ struct fsp_batch {
 namespace {
 
 // pointer tables inside d_tab
-enum Tab { T_Q0 = 0, T_Q1, T_Q2, T_ACC, T_LX, T_LE, T_LX2, T_LE2, T_OUT, T_COUNT };
+enum Tab { T_Q0 = 0, T_Q1, T_Q2, T_ACC, T_LX, T_LE, T_LX2, T_LE2, T_OUT, T_MX, T_ME, T_COUNT };
 
 size_t al(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -332,7 +383,7 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   // host descriptors
   h->params.resize(nblocks);
   h->coords.resize(nblocks);
-  size_t lam = 0, acc = 0, st = 0;
+  size_t lam = 0, acc = 0, st = 0, mid = 0;
   for (int b = 0; b < nblocks; ++b) {
     const fsp_block& B = blocks[b];
     Params& P = h->params[b];
@@ -369,6 +420,9 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
     acc += al(4 * (size_t)B.nj * B.ld * acc_elem(cfg->precision));
     h->st_off.push_back(st);
     st += al(4 * (size_t)B.nj * B.ld * state_size(cfg->precision));
+    // midpoint metrics (double accumulation only): xi [2][nj][ni + 3], eta [2][nj + 3][ni]
+    h->mid_off.push_back(mid);
+    if (cfg->precision != FSP_FP32) mid += al(8 * 2 * ((size_t)B.nj * (B.ni + 3) + (size_t)(B.nj + 3) * B.ni)) / 8;
     const int lr = 8 * (cfg->precision == FSP_FP64 ? lam_rows<double>() : lam_rows<float>());
     for (int by = 0; by < (B.nj + lr - 1) / lr; ++by)
       for (int bx = 0; bx < (B.ni + 31) / 32; ++bx) h->tl.push_back({b, bx, by});
@@ -386,7 +440,7 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   const size_t bytes = al(sizeof(Params) * nblocks) + al(sizeof(CoordBlock) * nblocks) +
                        al(sizeof(TileRef) * h->tx_cap) + al(sizeof(TileRef) * h->te_cap) +
                        al(sizeof(TileRef) * h->tl.size()) + al(sizeof(double) * 2 * lam) + acc + 2 * st +
-                       al(sizeof(void*) * T_COUNT * nblocks);
+                       al(sizeof(void*) * T_COUNT * nblocks) + sizeof(double) * mid;
   if (cudaMalloc(&h->dmem, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -403,6 +457,8 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   h->d_q1 = cur; cur += st;
   h->d_q2 = cur; cur += st;
   h->d_tab = reinterpret_cast<void**>(cur);
+  cur += al(sizeof(void*) * T_COUNT * nblocks);
+  h->d_mid = mid ? reinterpret_cast<double*>(cur) : nullptr;
   bool ok = cudaMemcpy(h->d_params, h->params.data(), sizeof(Params) * nblocks, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(h->d_tx, h->tx.data(), sizeof(TileRef) * h->tx.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(h->d_te, h->te.data(), sizeof(TileRef) * h->te.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -434,6 +490,11 @@ fsp_status fsp_batch_bind(fsp_batch* h, const double* const* x, const double* co
     tab[T_LE * nb + b] = h->d_lam + h->lam_off[b] + h->blk[b].nj;
     tab[T_LX2 * nb + b] = h->d_lam + h->lam_count + h->lam_off[b];
     tab[T_LE2 * nb + b] = h->d_lam + h->lam_count + h->lam_off[b] + h->blk[b].nj;
+    if (h->d_mid) {
+      const fsp_block& B = h->blk[b];
+      tab[T_MX * nb + b] = h->d_mid + h->mid_off[b];
+      tab[T_ME * nb + b] = h->d_mid + h->mid_off[b] + 2 * (size_t)B.nj * (B.ni + 3);
+    }
   }
   if (cudaMemcpy(h->d_params, h->params.data(), sizeof(Params) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(h->d_coords, h->coords.data(), sizeof(CoordBlock) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -461,6 +522,23 @@ fsp_status fsp_batch_metrics(fsp_batch* h, void* stream) {
 }  // extern "C"
 
 namespace {
+
+// The midpoint metrics of every block from the bound metrics (FP64 and mixed batches; a
+// no-op for FP32, whose passes interpolate in float): launched before each right-hand side,
+// RK3 step and tuning run, so metrics written between calls are always taken up.
+fsp_status batch_mids(fsp_batch* h, cudaStream_t st) {
+  if (!h->d_mid) return FSP_OK;
+  const int nb = h->nb, sc = h->cfg.scheme;
+  const int nmp = (sc == S32 || sc == S52) ? 2 : 1;
+  void** T = h->d_tab;
+  const dim3 grid(32, nb);
+  auto mx = reinterpret_cast<double* const*>(T + T_MX * nb);
+  auto me = reinterpret_cast<double* const*>(T + T_ME * nb);
+  if (sc == S71) mid_batch_kernel<4><<<grid, 256, 0, st>>>(h->d_params, mx, me, nmp);
+  else if (sc == S51 || sc == S52) mid_batch_kernel<3><<<grid, 256, 0, st>>>(h->d_params, mx, me, nmp);
+  else mid_batch_kernel<2><<<grid, 256, 0, st>>>(h->d_params, mx, me, nmp);
+  return cudaGetLastError() == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
+}
 
 // one right-hand side of every block; input table `in`, output table `out`; mode 0:
 // dQ/dt, mode 1: RK stage out = ca Q0 + cb (in + dt dQ/dt)
@@ -496,9 +574,13 @@ fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, doubl
       cudaMemsetAsync(h->d_lam + lam_out * h->lam_count, 0, sizeof(double) * h->lam_count, st) != cudaSuccess)
     return FSP_ERR_CUDA;
   const int lx = lam_in == LAM_B ? T_LX2 : T_LX, le = lam_in == LAM_B ? T_LE2 : T_LE;
-  const PassTables xi{h->d_params, h->d_tx, T + in * nb, T + lx * nb, nullptr, T + T_ACC * nb, nullptr, nullptr};
+  PassTables xi{h->d_params, h->d_tx, T + in * nb, T + lx * nb, nullptr, T + T_ACC * nb, nullptr, nullptr};
   PassTables eta{h->d_params, h->d_te, T + in * nb, T + le * nb, T + T_ACC * nb, nullptr, T + out * nb,
                  T + T_Q0 * nb};
+  if (h->d_mid) {
+    xi.mid = T + T_MX * nb;
+    eta.mid = T + T_ME * nb;
+  }
   if (lam_out >= 0) {
     eta.lxo = T + (lam_out ? T_LX2 : T_LX) * nb;
     eta.leo = T + (lam_out ? T_LE2 : T_LE) * nb;
@@ -518,6 +600,7 @@ fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, doubl
 // mixed precision, whose eta CTAs would no longer fit two to an SM with the extra operands.
 fsp_status batch_rk3(fsp_batch* h, double dt, cudaStream_t st) {
   const bool fuse = h->ve == MARCH && h->cfg.precision != FSP_FP32_MIXED;
+  if (fsp_status s = batch_mids(h, st)) return s;
   if (fsp_status s = batch_stage(h, T_Q0, T_Q1, 1, 0.0, 1.0, dt, st, LAM_KERNEL, fuse ? 1 : -1)) return s;
   if (fsp_status s = batch_stage(h, T_Q1, T_Q2, 1, 0.75, 0.25, dt, st, fuse ? LAM_B : LAM_KERNEL, fuse ? 0 : -1))
     return s;
@@ -537,6 +620,7 @@ fsp_status fsp_batch_rhs(fsp_batch* h, void* const* dQdt, void* stream) {
   if (cudaMemcpyAsync(h->d_tab + T_OUT * h->nb, dQdt, sizeof(void*) * h->nb, cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return FSP_ERR_CUDA;
+  if (fsp_status s = batch_mids(h, st)) return s;
   return batch_stage(h, T_Q0, T_OUT, 0, 0.0, 0.0, 0.0, st);
 }
 
@@ -550,7 +634,8 @@ fsp_status fsp_batch_flux_difference(fsp_batch* h, int dir, void* const* D, void
   if (cudaMemcpyAsync(T + T_OUT * nb, D, sizeof(void*) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return FSP_ERR_CUDA;
   const PassTables t{h->d_params, dir == 0 ? h->d_tx : h->d_te, T + T_Q0 * nb, T + (dir == 0 ? T_LX : T_LE) * nb,
-                     nullptr, T + T_OUT * nb, nullptr, nullptr};
+                     nullptr, T + T_OUT * nb, nullptr, nullptr, nullptr, nullptr,
+                     h->d_mid ? T + (dir == 0 ? T_MX : T_ME) * nb : nullptr};
   const int nt = (int)(dir == 0 ? h->tx.size() : h->te.size());
   const int v = dir == 0 ? h->vx : h->ve;
   cudaError_t e = h->cfg.precision == FSP_FP64
@@ -646,7 +731,8 @@ fsp_status time_direction(fsp_batch* h, int dir, cudaStream_t st, float* ms) {
   const int nb = h->nb;
   void** T = h->d_tab;
   const PassTables t{h->d_params, dir == 0 ? h->d_tx : h->d_te, T + T_Q0 * nb, T + (dir == 0 ? T_LX : T_LE) * nb,
-                     nullptr, T + T_ACC * nb, nullptr, nullptr};
+                     nullptr, T + T_ACC * nb, nullptr, nullptr, nullptr, nullptr,
+                     h->d_mid ? T + (dir == 0 ? T_MX : T_ME) * nb : nullptr};
   const int nt = (int)(dir == 0 ? h->tx.size() : h->te.size());
   const int v = dir == 0 ? h->vx : h->ve;
   auto run = [&]() {
@@ -732,6 +818,7 @@ fsp_status fsp_batch_tune(fsp_batch* h, const char* table_path, void* stream) {
     return set_tiles(h, 1, best[1]);
   }
   if (fsp_status s = batch_lambda(h, T_Q0, st)) return s;
+  if (fsp_status s = batch_mids(h, st)) return s;
   float best_ms[2] = {0, 0};
   for (int dir = 0; dir < 2; ++dir) {
     for (int v = 0; v < nvariant(dir); ++v) {

@@ -301,12 +301,18 @@ __device__ __forceinline__ void node_split(const Real q[4], double mx, double my
 // the midpoint fluxes (Section 2.3); at(m) gives the staged index of node p + m.
 // msplit (same precision only): 1 Steger-Warming, 2 Van Leer splitting of the midpoint flux
 // (an option beyond the paper's, Section 7) instead of the Lax-Friedrichs type.
+// pre: the midpoint metrics (pmx, pmy) were interpolated once per grid (the batch's FP64 and
+// mixed passes); otherwise they are interpolated here from the staged nodes.
 template <int S, typename Real, typename Acc, typename At>
 __device__ __forceinline__ void mid_fluxes(const Staged<Real, Acc>& st, const At& at, const Real Qs[2][4], Real gamma,
-                                           int interp, Acc A, Mid<Real, Acc>& mo, int msplit = 0) {
+                                           int interp, Acc A, Mid<Real, Acc>& mo, int msplit = 0, bool pre = false,
+                                           double pmx = 0.0, double pmy = 0.0) {
   using Sc = Scheme<S>;
   Acc mmx, mmy;
-  if constexpr (Sc::r == 4) {
+  if (pre) {
+    mmx = Acc(pmx);
+    mmy = Acc(pmy);
+  } else if constexpr (Sc::r == 4) {
     Acc vx[8], vy[8];
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) ld2(st.ma, at(kk - 3), vx[kk], vy[kk]);
@@ -486,7 +492,8 @@ __device__ __forceinline__ void centre_sides(const Staged<Real, Acc>& st, const 
 template <int S, typename Real, typename Acc, bool DEF = false, typename At>
 __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
                                               int ppm_, int linw_, int interp_, Acc A, Mid<Real, Acc>& mo,
-                                              int wz_ = 0, int msplit_ = 0) {
+                                              int wz_ = 0, int msplit_ = 0, bool pre = false, double pmx = 0.0,
+                                              double pmy = 0.0) {
   using Sc = Scheme<S>;
   constexpr int SC = weno_scale<Sc::r>();
   const int ppm = DEF ? 1 : ppm_, linw = DEF ? 0 : linw_, interp = DEF ? 0 : interp_;
@@ -522,7 +529,7 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
     E.recon(Wm, qc, Qs[side]);
   }
 
-  mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, interp, A, mo, msplit);
+  mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, interp, A, mo, msplit, pre, pmx, pmy);
 }
 
 // h+ coefficient n_k of the node flux f+_{p+k} (0 outside the scheme's stencil)
@@ -900,7 +907,7 @@ template <int S, int MODE, typename Real, typename Acc>
 __device__ __forceinline__ void march_row(const Params& P, const Real* __restrict__ Q, const Real* const* qtab,
                                           double lamv, const Acc* __restrict__ Dacc, Acc* __restrict__ Dout,
                                           Real* qout, const Real* Qn, double ca, double cb, double dt, int row,
-                                          int s0, int s1, unsigned char* wsm) {
+                                          int s0, int s1, unsigned char* wsm, const double* __restrict__ mid = nullptr) {
   using Ms = MarchShape<S, Real, Acc>;
   constexpr int NMP = Scheme<S>::nmp;
   constexpr int K = NMP == 1 ? 3 : 2;
@@ -924,6 +931,11 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
   const Real* Qrow = Q + (long long)row * P.ld;
   const double* M0 = P.met + (long long)(row + G) * P.mld + G;   // xi_x^ of node (i, row) at M0[i]
   const double* M1 = M0 + P.mplane;                                // xi_y^
+  // midpoint metrics of the row's interfaces q = -2 .. ni (xi_x^ plane, then xi_y^), when the
+  // batch stored them once per grid (double accumulation only)
+  const bool pre = std::is_same<Acc, double>::value && mid != nullptr;
+  const double* MXr = pre ? mid + (long long)row * (n + 3) + 2 : nullptr;
+  const long long mstr = (long long)P.nj * (n + 3);
 
   // the node stage of one position: interior nodes from the cp.async staging (if staged),
   // else through the boundary rule; positions past n + 3 are never read
@@ -987,15 +999,20 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
     const int q = c - 1;
     if (q >= s0 - NMP && q <= s1 + NMP - 2) {
       auto at = [&](int mm) { return (q + mm) & (RING - 1); };
+      double pmx = 0.0, pmy = 0.0;
+      if (pre) {
+        pmx = MXr[q];
+        pmy = MXr[q + mstr];
+      }
       Mid<Real, Acc> mo;
       if constexpr (CENTRE) {
         Real Qs[2][4];
         ld4(rQp, RING, q & (RING - 1), Qs[0]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) Qs[1][v] = Qm[v];
-        mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, 0, A, mo);
+        mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, 0, A, mo, 0, pre, pmx, pmy);
       } else {
-        interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
+        interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo, 0, 0, pre, pmx, pmy);
       }
       if constexpr (NMP == 1) {
         Acc h[4];
@@ -1097,7 +1114,8 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
                                           const double* __restrict__ lam, const Acc* __restrict__ Dacc,
                                           Acc* __restrict__ Dout, Real* qout, const Real* Qn, double ca, double cb,
                                           double dt, int c0, int s0, int s1, unsigned char* sm,
-                                          double* lxo = nullptr, double* leo = nullptr) {
+                                          double* lxo = nullptr, double* leo = nullptr,
+                                          const double* __restrict__ mid = nullptr) {
   using Ms = MarchEtaShape<S, Real, Acc>;
   constexpr bool STAGE = MODE >= MODE_STAGE, LAM = MODE == MODE_STAGE_L;
   constexpr int NMP = Scheme<S>::nmp;
@@ -1125,6 +1143,10 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
   const Acc A = on ? Acc(P.alpha * lam[col]) : Acc(0);
   const Acc hA = Acc(0.5) * A;
   auto slot = [&](int row) { return (row & (ERING - 1)) * 32 + L; };
+  // midpoint metrics of the column's interfaces q = -2 .. nj (eta_x^ plane, then eta_y^), when
+  // the batch stored them once per grid (double accumulation only)
+  const bool pre = std::is_same<Acc, double>::value && mid != nullptr;
+  const long long mstr = (long long)(P.nj + 3) * P.ni;
 
   auto stage_node = [&](int m, bool staged) {
     if (!on || m > s1 + 3 || m > n + 3) return;
@@ -1200,8 +1222,14 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
     Real qs[4] = {Real(0), Real(0), Real(0), Real(0)};
     if (on && q <= s1 + NMP - 2) {
       auto at = [&](int mm) { return slot(q + mm); };
+      double pmx = 0.0, pmy = 0.0;
+      if (pre) {
+        const long long mo_ = (long long)(q + 2) * P.ni + col;
+        pmx = mid[mo_];
+        pmy = mid[mo_ + mstr];
+      }
       Mid<Real, Acc> mo;
-      interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo);
+      interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo, 0, 0, pre, pmx, pmy);
       if constexpr (NMP == 1) {
         Acc h[4];
         h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h, P);
@@ -1324,6 +1352,7 @@ struct BatchPass {                 // device arrays indexed by block
   const Real* const* qn;           // Q^n of the RK step (mode 2)
   double* const* lxo;              // line maxima of the written state, xi and eta (MODE_STAGE_L)
   double* const* leo;
+  const double* const* mid;        // midpoint metrics of the pass's direction (or null)
 };
 
 template <int S, int DIR, int MODE, typename Real, typename Acc, int V>
@@ -1361,7 +1390,7 @@ march_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
   march_row<S, MODE, Real, Acc>(sp, B.q[b], B.q, B.lam[b][row], MODE == MODE_ACC ? nullptr : B.dacc[b],
                                 MODE == MODE_ACC ? B.dout[b] : nullptr, MODE == MODE_ACC ? nullptr : B.qout[b],
                                 MODE == MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, row, s0, s1,
-                                smem_raw + warp * Ms::warp_bytes());
+                                smem_raw + warp * Ms::warp_bytes(), B.mid ? B.mid[b] : nullptr);
 }
 
 // Marching eta pass of many blocks: CTA b takes the 32 columns from 32 by of block
@@ -1385,7 +1414,8 @@ march_eta_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) 
   march_col<S, MODE, Real, Acc>(sp, B.q[b], B.q, B.lam[b], MODE == MODE_ACC ? nullptr : B.dacc[b],
                                 MODE == MODE_ACC ? B.dout[b] : nullptr, MODE == MODE_ACC ? nullptr : B.qout[b],
                                 MODE >= MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, t.by * 32, s0, s1, smem_raw,
-                                MODE == MODE_STAGE_L ? B.lxo[b] : nullptr, MODE == MODE_STAGE_L ? B.leo[b] : nullptr);
+                                MODE == MODE_STAGE_L ? B.lxo[b] : nullptr, MODE == MODE_STAGE_L ? B.leo[b] : nullptr,
+                                B.mid ? B.mid[b] : nullptr);
 }
 
 // Untyped pass tables (device arrays of per-block pointers) and their typed view.
@@ -1400,6 +1430,7 @@ struct PassTables {
   void* const* qn;
   void* const* lxo;     // MODE_STAGE_L only
   void* const* leo;
+  void* const* mid;     // per block: midpoint metrics of this direction, or null (marching passes)
 };
 
 template <typename Real, typename Acc>
@@ -1415,6 +1446,7 @@ BatchPass<Real, Acc> typed_pass(const PassTables& t) {
   B.qn = reinterpret_cast<const Real* const*>(t.qn);
   B.lxo = reinterpret_cast<double* const*>(t.lxo);
   B.leo = reinterpret_cast<double* const*>(t.leo);
+  B.mid = reinterpret_cast<const double* const*>(t.mid);
   return B;
 }
 

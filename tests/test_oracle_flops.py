@@ -54,3 +54,24 @@ def test_stored_counts_match_the_script():
     assert CF.vortex_counts() == stored["schemes"]
     assert CF.adjoint_counts() == stored["adjoint"]["schemes"]
     assert CF.three_d_counts() == stored["three_d"]["schemes"]
+
+
+def test_midpoint_interpolation_counts():
+    """One midpoint interpolation of a nodal quantity (Section 2.4), as the oracle writes it:
+    the four-point Lagrange interpolant costs three products, three additions and one division
+    (7), the six-point one six, five and one (12), the eight-point one eight, seven and one
+    (16), and the two-point average an addition and a product (2)."""
+    assert [O.count_mid_interp(s) for s in range(6)] == [7, 7, 12, 12, 16, 16]
+    assert all(O.count_mid_interp(s, 1) == 2 for s in range(6))
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
+def test_sweep_count_carries_two_interpolations_per_interface(scheme):
+    """The xi sweep interpolates the two direction metrics at each of its n + 2 nmp - 1
+    interfaces per line: switching the interpolation to the two-point average changes its count
+    by exactly that many interpolations (linear weights: nothing else depends on the data)."""
+    ni, nj = 20, 14
+    nmp = 2 if scheme in (1, 3) else 1
+    a = _parts(scheme, ni, nj, linear_weights=1)[1]
+    b = _parts(scheme, ni, nj, linear_weights=1, interp=1)[1]
+    assert a - b == nj * (ni + 2 * nmp - 1) * 2 * (O.count_mid_interp(scheme) - O.count_mid_interp(scheme, 1))
