@@ -433,10 +433,11 @@ def measure_cylinder(args, prec, C, per_block=False):
     peak, pipe = C.peak(prec)
     t_dev, t_e2e = C.max_over_ranks(t_dev, t_e2e)
     fl = algorithmic_flops(args)
-    # FP64 and mixed batches store the midpoint metrics once per step (mid_batch_kernel) and the
-    # marching passes read them: their interpolation leaves the passes' counts and enters the
-    # step's once instead of three times
+    # FP64 and mixed batches store the midpoint metrics (FP64 also the characteristic direction)
+    # once per step (mid_batch_kernel) and the marching passes read them: that work leaves the
+    # passes' counts and enters the step's once instead of three times
     mid_if = fl["mid_interp_per_interface"] if prec != "fp32" else 0
+    mid_if += fl["char_dir_per_interface"] if prec == "fp64" else 0   # FP64 reads the direction too
     mid_xi = fl["xi_interfaces_per_node"] * mid_if * (tiles["xi"]["variant"] == 3)
     mid_eta = fl["eta_interfaces_per_node"] * mid_if * (tiles["eta"]["variant"] == 3)
     xi_fl = fl["sweep_xi_per_node"] - mid_xi
@@ -458,8 +459,9 @@ def measure_cylinder(args, prec, C, per_block=False):
             "eta": {"kernel_ms": 1e3 * t_e, "flops_per_node": eta_fl, "frac": eta_fl * nodes / t_e / 1e12 / peak},
             "step_frac": step_fl * nodes / (t_dev / args.steps) / 1e12 / peak,
             "midpoint_metrics": ({"flops_per_node_per_step": mid_xi + mid_eta,
-                                  "how": "interpolated once per step by mid_batch_kernel; left out of the "
-                                         "passes' counts"} if mid_if else None)}
+                                  "how": "midpoint metrics" + (" and characteristic direction" if prec == "fp64" else "")
+                                         + " per interface once per step by mid_batch_kernel; left out of the "
+                                           "passes' counts"} if mid_if else None)}
     if prec == "mixed":
         roof = mixed_roofline(args, C, roof, xi_fl, nodes, t_k, clk.get("sm_mhz"), hoisted=mid_xi > 0)
     out = {

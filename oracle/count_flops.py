@@ -33,14 +33,16 @@ def cylinder_counts(scheme):
         tot = [t + p for t, p in zip(tot, parts)]
         nodes += b["x"].size
     lx, sx, le, se, fin = tot
-    # the midpoint metric interpolation inside those sweeps: two components per interface, over
-    # the n + 2 nmp - 1 interfaces of each line (a solver may store them once per grid instead)
+    # the midpoint metric interpolation (two components) and the characteristic direction
+    # inside those sweeps, per interface, over the n + 2 nmp - 1 interfaces of each line (a
+    # solver may store them once per grid instead)
     nmp = 2 if scheme in (1, 3) else 1
     ifx = sum(b["x"].shape[0] * (b["x"].shape[1] + 2 * nmp - 1) for b in blocks)
     ife = sum(b["x"].shape[1] * (b["x"].shape[0] + 2 * nmp - 1) for b in blocks)
     return {"rhs_per_node": sum(tot) / nodes, "lambda_per_node": (lx + le) / nodes,
             "sweep_xi_per_node": sx / nodes, "sweep_eta_per_node": (se + fin) / nodes, "nodes": nodes,
             "mid_interp_per_interface": 2 * O.count_mid_interp(scheme),
+            "char_dir_per_interface": O.count_char_dir(),
             "xi_interfaces_per_node": ifx / nodes, "eta_interfaces_per_node": ife / nodes}
 
 

@@ -346,6 +346,17 @@ static T interp_mid(int scheme, int interp, F phi) {
           - cst<T>(25) * phi(2) + cst<T>(3) * phi(3)) / cst<T>(256);
 }
 
+// The unit characteristic direction of an interface (Section 3.4): the average of its two
+// nodes' direction metrics, normalised.
+template <class T>
+static void char_dir(T mx0, T my0, T mx1, T my1, T& nx, T& ny) {
+  T mbx = cst<T>(0.5L) * (mx0 + mx1);
+  T mby = cst<T>(0.5L) * (my0 + my1);
+  T mb = sqrt(mbx * mbx + mby * mby);
+  nx = mbx / mb;
+  ny = mby / mb;
+}
+
 // ----------------------------------------------------------------------------------
 // Coordinates with ghost nodes.
 // Reading (boundaries are not treated in the paper): a periodic direction wraps and
@@ -856,10 +867,8 @@ static void sweep(const Field<T>& F, int dir, std::vector<T>& R) {
     for (int p = -nmp; p <= n - 2 + nmp; ++p) {
       const int c0 = p + 4;                    // node p
       // characteristic direction from the averaged metrics (Section 3.4)
-      T mbx = cst<T>(0.5L) * (mxs[c0] + mxs[c0 + 1]);
-      T mby = cst<T>(0.5L) * (mys[c0] + mys[c0 + 1]);
-      T mb = sqrt(mbx * mbx + mby * mby);
-      T nx = mbx / mb, ny = mby / mb;
+      T nx, ny;
+      char_dir<T>(mxs[c0], mys[c0], mxs[c0 + 1], mys[c0 + 1], nx, ny);
       T Qs[2][4];
       for (int side = 0; side < 2; ++side) {
         // side 0 ("+"): eigenvectors at Q_p, stencil p-2..p+2;
@@ -1327,9 +1336,17 @@ long long orc_count_flops(const int* ip, const double* dp, int ni, int nj, const
   return g_flops;
 }
 
-// Floating-point operations of one midpoint interpolation I of a nodal quantity (Section 2.4)
+// Floating-point operations of one interface's characteristic direction (Section 3.4), and of
+// one midpoint interpolation I of a nodal quantity (Section 2.4)
 // for a scheme and interpolation option: the work per component that a solver storing the
 // midpoint metrics once per grid no longer repeats in each right-hand side.
+long long orc_count_char_dir() {
+  g_flops = 0;
+  Counted nx, ny;
+  char_dir<Counted>(Counted(1.0), Counted(0.5), Counted(1.25), Counted(0.25), nx, ny);
+  return g_flops;
+}
+
 long long orc_count_mid_interp(int scheme, int interp) {
   if (scheme < 0 || scheme > 5 || interp < 0 || interp > 1) return -1;
   g_flops = 0;

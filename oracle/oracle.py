@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "build", "lib", "metrics", "metrics_jvp", "line_lambda", "rhs", "rhs_jvp", "rk3", "rk3_jvp",
-    "cfl_dt", "count_flops", "count_mid_interp", "count_flops_parts", "fsp_residual", "weno", "ppm", "smoothness", "eig",
+    "cfl_dt", "count_flops", "count_mid_interp", "count_char_dir", "count_flops_parts", "fsp_residual", "weno", "ppm", "smoothness", "eig",
     "scheme_table", "advect1d", "advect1d_dt", "smoothness4", "riemann_exact", "long_double_digits", "G",
     "mb_metrics", "mb_rhs", "mb_rk3", "rhs_vjp", "rk3_vjp", "metrics_vjp", "count_vjp_flops",
     "advect1d_opts", "weno_z", "split_flux",
@@ -78,6 +78,7 @@ def lib():
                 "orc_cfl_dt": (ctypes.c_double, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double]),
                 "orc_count_flops": (ctypes.c_longlong, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D]),
                 "orc_count_mid_interp": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_int]),
+                "orc_count_char_dir": (ctypes.c_longlong, []),
                 "orc_count_flops_parts": (ctypes.c_int, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D,
                                                          ctypes.POINTER(ctypes.c_longlong)]),
                 "orc_fsp_residual": (ctypes.c_double, [_I, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D,
@@ -288,6 +289,11 @@ def count_flops(cfg, M, Q):
     _, nj, ni = Q.shape
     ip, dp, _ = _params(cfg)
     return int(lib().orc_count_flops(ip.ctypes.data_as(_I), _dp(dp), ni, nj, _dp(M), _dp(Q)))
+
+
+def count_char_dir():
+    """Operations of one interface's characteristic direction (Section 3.4)."""
+    return lib().orc_count_char_dir()
 
 
 def count_mid_interp(scheme, interp=0):

@@ -173,53 +173,57 @@ __global__ void __launch_bounds__(256) lambda_batch_kernel(const Params* __restr
   }
 }
 
-// Midpoint metrics of every interface of every block (FP64 and mixed batches): the
-// interpolation I of the metric evaluation (Section 2.4) applied to xi_x^, xi_y^ along each
-// row at the xi interfaces q + 1/2, q = -nmp .. ni + nmp - 2, stored at [c][row][q + 2] of
-// [2][nj][ni + 3], and to eta_x^, eta_y^ along each column at [c][q + 2][col] of
-// [2][nj + 3][ni] -- the same nodal values and the same interpolation as the marching passes
-// would take from their staged nodes, so the results are those of interpolating in the pass.
+// Grid-static data of every interface of every block (FP64 and mixed batches), for the
+// marching passes: the interpolation I of the metric evaluation (Section 2.4) of the two
+// direction metrics at the midpoint, and the unit characteristic direction of Section 3.4
+// (the summed metrics of the interface's two nodes, normalised).  xi interfaces q + 1/2 of
+// each row at [c][row][q + 2] of [4][nj][ni + 3], eta interfaces of each column at
+// [c][q + 2][col] of [4][nj + 3][ni], c = midpoint x, y, direction x, y; q = -2 .. n for the
+// direction (the centre-node layout reads both neighbours of every centre) and wherever the
+// interpolation's stencil lies within the stored ghost layers for the midpoint.  The same
+// stored metrics and the same functions as the passes would apply to their staged nodes.
 // Grid (gx, blocks): the CTAs of row y stride over block y's interfaces.
-template <int R>
+template <int R, bool DIR>
 __global__ void __launch_bounds__(256) mid_batch_kernel(const Params* __restrict__ Ps, double* const* mxt,
-                                                        double* const* met, int nmp) {
+                                                        double* const* met) {
   const Params& P = Ps[blockIdx.y];
   double* MX = mxt[blockIdx.y];
   double* ME = met[blockIdx.y];
   const int ni = P.ni, nj = P.nj;
-  const int wx = ni + 2 * nmp - 1, we = nj + 2 * nmp - 1;
-  const long long nx = (long long)nj * wx, n = nx + (long long)ni * we;
   const long long sx = (long long)nj * (ni + 3), se = (long long)(nj + 3) * ni;
   constexpr int NP = R == 4 ? 8 : 6, OFF = R == 4 ? 3 : 2;
   auto interp = [&](const double* v) {
     if constexpr (R == 4) return mid_interp8(P.interp, v);
     else return mid_interp(P.interp, R == 3, v);
   };
-  for (long long t = blockIdx.x * 256LL + threadIdx.x; t < n; t += (long long)gridDim.x * 256) {
-    double vx[NP], vy[NP];
-    if (t < nx) {
-      const int row = (int)(t / wx), q = (int)(t % wx) - nmp;
+  // store interface q (-2 .. len) of a line whose metric components c = 0, 1 at node k are m(c, k)
+  auto line = [&](double* out, long long stride, int q, int len, auto m) {
+    if (q - OFF >= -G && q - OFF + NP - 1 <= len + G - 1) {
+      double vx[NP], vy[NP];
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
-        vx[k] = met_at(P, 0, q - OFF + k, row);
-        vy[k] = met_at(P, 1, q - OFF + k, row);
+        vx[k] = m(0, q - OFF + k);
+        vy[k] = m(1, q - OFF + k);
       }
-      const long long o = (long long)row * (ni + 3) + q + 2;
-      MX[o] = interp(vx);
-      MX[o + sx] = interp(vy);
-    } else {
-      const long long u = t - nx;
-      const int q = (int)(u / ni) - nmp, col = (int)(u % ni);
-#pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        vx[k] = met_at(P, 2, col, q - OFF + k);
-        vy[k] = met_at(P, 3, col, q - OFF + k);
-      }
-      const long long o = (long long)(q + 2) * ni + col;
-      ME[o] = interp(vx);
-      ME[o + se] = interp(vy);
+      out[0] = interp(vx);
+      out[stride] = interp(vy);
     }
-  }
+    if constexpr (DIR) {
+      // nodes q and q + 1 lie within the ghost layers for q = -2 .. len
+      const double mbx = m(0, q) + m(0, q + 1), mby = m(1, q) + m(1, q + 1);
+      const double rn = rsq(mbx * mbx + mby * mby);
+      out[2 * stride] = mbx * rn;
+      out[3 * stride] = mby * rn;
+    }
+  };
+  // xi: CTA x takes rows x, x + gx, ..., its threads the interfaces of a row; eta: CTA x takes
+  // the interface rows q + 2 = x, x + gx, ..., its threads the columns
+  for (int row = blockIdx.x; row < nj; row += gridDim.x)
+    for (int q = (int)threadIdx.x - 2; q <= ni; q += 256)
+      line(MX + (long long)row * (ni + 3) + q + 2, sx, q, ni, [&](int c, int k) { return met_at(P, c, k, row); });
+  for (int r = blockIdx.x; r < nj + 3; r += gridDim.x)
+    for (int col = threadIdx.x; col < ni; col += 256)
+      line(ME + (long long)r * ni + col, se, r - 2, nj, [&](int c, int k) { return met_at(P, 2 + c, col, k); });
 }
 
 }  // namespace fsp
@@ -420,9 +424,9 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
     acc += al(4 * (size_t)B.nj * B.ld * acc_elem(cfg->precision));
     h->st_off.push_back(st);
     st += al(4 * (size_t)B.nj * B.ld * state_size(cfg->precision));
-    // midpoint metrics (double accumulation only): xi [2][nj][ni + 3], eta [2][nj + 3][ni]
+    // stored interface data (double accumulation only): xi [4][nj][ni + 3], eta [4][nj + 3][ni]
     h->mid_off.push_back(mid);
-    if (cfg->precision != FSP_FP32) mid += al(8 * 2 * ((size_t)B.nj * (B.ni + 3) + (size_t)(B.nj + 3) * B.ni)) / 8;
+    if (cfg->precision != FSP_FP32) mid += al(8 * 4 * ((size_t)B.nj * (B.ni + 3) + (size_t)(B.nj + 3) * B.ni)) / 8;
     const int lr = 8 * (cfg->precision == FSP_FP64 ? lam_rows<double>() : lam_rows<float>());
     for (int by = 0; by < (B.nj + lr - 1) / lr; ++by)
       for (int bx = 0; bx < (B.ni + 31) / 32; ++bx) h->tl.push_back({b, bx, by});
@@ -493,7 +497,7 @@ fsp_status fsp_batch_bind(fsp_batch* h, const double* const* x, const double* co
     if (h->d_mid) {
       const fsp_block& B = h->blk[b];
       tab[T_MX * nb + b] = h->d_mid + h->mid_off[b];
-      tab[T_ME * nb + b] = h->d_mid + h->mid_off[b] + 2 * (size_t)B.nj * (B.ni + 3);
+      tab[T_ME * nb + b] = h->d_mid + h->mid_off[b] + 4 * (size_t)B.nj * (B.ni + 3);
     }
   }
   if (cudaMemcpy(h->d_params, h->params.data(), sizeof(Params) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -529,14 +533,22 @@ namespace {
 fsp_status batch_mids(fsp_batch* h, cudaStream_t st) {
   if (!h->d_mid) return FSP_OK;
   const int nb = h->nb, sc = h->cfg.scheme;
-  const int nmp = (sc == S32 || sc == S52) ? 2 : 1;
   void** T = h->d_tab;
-  const dim3 grid(32, nb);
+  const dim3 grid(64, nb);
   auto mx = reinterpret_cast<double* const*>(T + T_MX * nb);
   auto me = reinterpret_cast<double* const*>(T + T_ME * nb);
-  if (sc == S71) mid_batch_kernel<4><<<grid, 256, 0, st>>>(h->d_params, mx, me, nmp);
-  else if (sc == S51 || sc == S52) mid_batch_kernel<3><<<grid, 256, 0, st>>>(h->d_params, mx, me, nmp);
-  else mid_batch_kernel<2><<<grid, 256, 0, st>>>(h->d_params, mx, me, nmp);
+  // the direction is read by the FP64 passes only (the mixed passes take it in float)
+  const bool dir = h->cfg.precision == FSP_FP64;
+  if (sc == S71) {
+    if (dir) mid_batch_kernel<4, true><<<grid, 256, 0, st>>>(h->d_params, mx, me);
+    else mid_batch_kernel<4, false><<<grid, 256, 0, st>>>(h->d_params, mx, me);
+  } else if (sc == S51 || sc == S52) {
+    if (dir) mid_batch_kernel<3, true><<<grid, 256, 0, st>>>(h->d_params, mx, me);
+    else mid_batch_kernel<3, false><<<grid, 256, 0, st>>>(h->d_params, mx, me);
+  } else {
+    if (dir) mid_batch_kernel<2, true><<<grid, 256, 0, st>>>(h->d_params, mx, me);
+    else mid_batch_kernel<2, false><<<grid, 256, 0, st>>>(h->d_params, mx, me);
+  }
   return cudaGetLastError() == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
 }
 

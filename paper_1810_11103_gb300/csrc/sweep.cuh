@@ -254,6 +254,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // --------------------------------------------------------------------------------------
 // Per-node and per-interface arithmetic, shared by the tile and the marching kernels (the
 // same operations in the same order, so every layout gives the same results)
+// Grid-static data of one interface that a batch stores once per step (FP64 and mixed passes):
+// the midpoint metrics (mid) and, for FP64, the unit characteristic direction (dir).
+struct IfacePre {
+  bool mid = false, dir = false;
+  double mx = 0.0, my = 0.0, nx = 0.0, ny = 0.0;
+};
+
 // --------------------------------------------------------------------------------------
 // A node (Section 2.3).  Same precision throughout (Real = Acc): primitives of the projection
 // and the split fluxes f+- = (E^ +- A^ Q)/2, E^ = mx E + my F, stored in fp and fm.  Mixed
@@ -301,17 +308,17 @@ __device__ __forceinline__ void node_split(const Real q[4], double mx, double my
 // the midpoint fluxes (Section 2.3); at(m) gives the staged index of node p + m.
 // msplit (same precision only): 1 Steger-Warming, 2 Van Leer splitting of the midpoint flux
 // (an option beyond the paper's, Section 7) instead of the Lax-Friedrichs type.
-// pre: the midpoint metrics (pmx, pmy) were interpolated once per grid (the batch's FP64 and
-// mixed passes); otherwise they are interpolated here from the staged nodes.
+// pr.mid: the midpoint metrics were interpolated once per step by the batch (FP64 and mixed
+// passes, IfacePre); otherwise they are interpolated here from the staged nodes.
 template <int S, typename Real, typename Acc, typename At>
 __device__ __forceinline__ void mid_fluxes(const Staged<Real, Acc>& st, const At& at, const Real Qs[2][4], Real gamma,
-                                           int interp, Acc A, Mid<Real, Acc>& mo, int msplit = 0, bool pre = false,
-                                           double pmx = 0.0, double pmy = 0.0) {
+                                           int interp, Acc A, Mid<Real, Acc>& mo, int msplit = 0,
+                                           const IfacePre& pr = IfacePre{}) {
   using Sc = Scheme<S>;
   Acc mmx, mmy;
-  if (pre) {
-    mmx = Acc(pmx);
-    mmy = Acc(pmy);
+  if (pr.mid) {
+    mmx = Acc(pr.mx);
+    mmy = Acc(pr.my);
   } else if constexpr (Sc::r == 4) {
     Acc vx[8], vy[8];
 #pragma unroll
@@ -492,15 +499,19 @@ __device__ __forceinline__ void centre_sides(const Staged<Real, Acc>& st, const 
 template <int S, typename Real, typename Acc, bool DEF = false, typename At>
 __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const At& at, Real gamma, Real eps,
                                               int ppm_, int linw_, int interp_, Acc A, Mid<Real, Acc>& mo,
-                                              int wz_ = 0, int msplit_ = 0, bool pre = false, double pmx = 0.0,
-                                              double pmy = 0.0) {
+                                              int wz_ = 0, int msplit_ = 0, const IfacePre& pr = IfacePre{}) {
   using Sc = Scheme<S>;
   constexpr int SC = weno_scale<Sc::r>();
   const int ppm = DEF ? 1 : ppm_, linw = DEF ? 0 : linw_, interp = DEF ? 0 : interp_;
   const int wz = DEF ? 0 : wz_, msplit = DEF ? 0 : msplit_;
   const int o0 = at(0), o1 = at(1);
   Real nx, ny;
-  char_direction(st, o0, o1, nx, ny);
+  if constexpr (std::is_same<Real, double>::value) {
+    if (pr.dir) { nx = pr.nx; ny = pr.ny; }
+    else char_direction(st, o0, o1, nx, ny);
+  } else {
+    char_direction(st, o0, o1, nx, ny);
+  }
 
   Real Qs[2][4];
 #pragma unroll
@@ -529,7 +540,7 @@ __device__ __forceinline__ void interface_mid(const Staged<Real, Acc>& st, const
     E.recon(Wm, qc, Qs[side]);
   }
 
-  mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, interp, A, mo, msplit, pre, pmx, pmy);
+  mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, interp, A, mo, msplit, pr);
 }
 
 // h+ coefficient n_k of the node flux f+_{p+k} (0 outside the scheme's stencil)
@@ -931,9 +942,10 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
   const Real* Qrow = Q + (long long)row * P.ld;
   const double* M0 = P.met + (long long)(row + G) * P.mld + G;   // xi_x^ of node (i, row) at M0[i]
   const double* M1 = M0 + P.mplane;                                // xi_y^
-  // midpoint metrics of the row's interfaces q = -2 .. ni (xi_x^ plane, then xi_y^), when the
-  // batch stored them once per grid (double accumulation only)
+  // the row's interfaces q = -2 .. ni as the batch stored them once per step (double
+  // accumulation only): planes midpoint xi_x^, xi_y^, then (FP64) the unit direction
   const bool pre = std::is_same<Acc, double>::value && mid != nullptr;
+  const bool pdir = std::is_same<Real, double>::value && pre;
   const double* MXr = pre ? mid + (long long)row * (n + 3) + 2 : nullptr;
   const long long mstr = (long long)P.nj * (n + 3);
 
@@ -987,8 +999,15 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
       if (c <= s1 + NMP - 1) {
         auto at = [&](int mm) { return (c + mm) & (RING - 1); };
         Real npx, npy, nmx, nmy;
-        char_direction(st, at(0), at(1), npx, npy);
-        char_direction(st, at(-1), at(0), nmx, nmy);
+        if (pdir) {
+          npx = Real(MXr[c + 2 * mstr]);
+          npy = Real(MXr[c + 3 * mstr]);
+          nmx = Real(MXr[c - 1 + 2 * mstr]);
+          nmy = Real(MXr[c - 1 + 3 * mstr]);
+        } else {
+          char_direction(st, at(0), at(1), npx, npy);
+          char_direction(st, at(-1), at(0), nmx, nmy);
+        }
         Real Qp[4];
         centre_sides<S, Real, Acc>(st, at, npx, npy, nmx, nmy, eps, Qp, Qm);
         st4(rQp, RING, c & (RING - 1), Qp[0], Qp[1], Qp[2], Qp[3]);
@@ -999,10 +1018,11 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
     const int q = c - 1;
     if (q >= s0 - NMP && q <= s1 + NMP - 2) {
       auto at = [&](int mm) { return (q + mm) & (RING - 1); };
-      double pmx = 0.0, pmy = 0.0;
+      IfacePre pr;
       if (pre) {
-        pmx = MXr[q];
-        pmy = MXr[q + mstr];
+        pr.mid = true;
+        pr.mx = MXr[q];
+        pr.my = MXr[q + mstr];
       }
       Mid<Real, Acc> mo;
       if constexpr (CENTRE) {
@@ -1010,9 +1030,14 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
         ld4(rQp, RING, q & (RING - 1), Qs[0]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) Qs[1][v] = Qm[v];
-        mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, 0, A, mo, 0, pre, pmx, pmy);
+        mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, 0, A, mo, 0, pr);
       } else {
-        interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo, 0, 0, pre, pmx, pmy);
+        if (pdir) {
+          pr.dir = true;
+          pr.nx = MXr[q + 2 * mstr];
+          pr.ny = MXr[q + 3 * mstr];
+        }
+        interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo, 0, 0, pr);
       }
       if constexpr (NMP == 1) {
         Acc h[4];
@@ -1143,9 +1168,10 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
   const Acc A = on ? Acc(P.alpha * lam[col]) : Acc(0);
   const Acc hA = Acc(0.5) * A;
   auto slot = [&](int row) { return (row & (ERING - 1)) * 32 + L; };
-  // midpoint metrics of the column's interfaces q = -2 .. nj (eta_x^ plane, then eta_y^), when
-  // the batch stored them once per grid (double accumulation only)
+  // the column's interfaces q = -2 .. nj as the batch stored them once per step (double
+  // accumulation only): planes midpoint eta_x^, eta_y^, then (FP64) the unit direction
   const bool pre = std::is_same<Acc, double>::value && mid != nullptr;
+  const bool pdir = std::is_same<Real, double>::value && pre;
   const long long mstr = (long long)(P.nj + 3) * P.ni;
 
   auto stage_node = [&](int m, bool staged) {
@@ -1222,14 +1248,20 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
     Real qs[4] = {Real(0), Real(0), Real(0), Real(0)};
     if (on && q <= s1 + NMP - 2) {
       auto at = [&](int mm) { return slot(q + mm); };
-      double pmx = 0.0, pmy = 0.0;
+      IfacePre pr;
       if (pre) {
         const long long mo_ = (long long)(q + 2) * P.ni + col;
-        pmx = mid[mo_];
-        pmy = mid[mo_ + mstr];
+        pr.mid = true;
+        pr.mx = mid[mo_];
+        pr.my = mid[mo_ + mstr];
+        if (pdir) {
+          pr.dir = true;
+          pr.nx = mid[mo_ + 2 * mstr];
+          pr.ny = mid[mo_ + 3 * mstr];
+        }
       }
       Mid<Real, Acc> mo;
-      interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo, 0, 0, pre, pmx, pmy);
+      interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo, 0, 0, pr);
       if constexpr (NMP == 1) {
         Acc h[4];
         h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h, P);

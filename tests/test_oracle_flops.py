@@ -63,6 +63,9 @@ def test_midpoint_interpolation_counts():
     (16), and the two-point average an addition and a product (2)."""
     assert [O.count_mid_interp(s) for s in range(6)] == [7, 7, 12, 12, 16, 16]
     assert all(O.count_mid_interp(s, 1) == 2 for s in range(6))
+    # the interface direction: two averages (2 each), |m| (two products, a sum, a square root),
+    # two divisions
+    assert O.count_char_dir() == 10
 
 
 @pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])

@@ -109,7 +109,7 @@ MUTANTS = [
      [EUL + "test_free_stream_preservation_randomized_grid[0-1]", EUL + "test_mirror_symmetry[1]"]),
     ("line_max_min", "if (s == 0 || sp > best) best = sp;", "if (s == 0 || sp < best) best = sp;",
      [EUL + "test_linear_weights_reduce_to_linear_upwind_operator[0]"]),
-    ("direction_swap", "T nx = mbx / mb, ny = mby / mb;", "T nx = mby / mb, ny = mbx / mb;",
+    ("direction_swap", "  nx = mbx / mb;\n  ny = mby / mb;", "  nx = mby / mb;\n  ny = mbx / mb;",
      [EUL + "test_rotation_equivariance[2]"]),
     ("mirror_stencil", "const int node = side == 0 ? c0 + m : c0 + 1 - m;",
      "const int node = side == 0 ? c0 + m : c0 + 1 + m;",
