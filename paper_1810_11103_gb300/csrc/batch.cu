@@ -254,6 +254,8 @@ struct fsp_batch {
   char* d_acc = nullptr;             // xi differences, one per block
   double* d_mid = nullptr;           // midpoint metrics per block (FP64 and mixed; see mid_batch_kernel)
   std::vector<size_t> mid_off;       // in doubles
+  double* d_nc = nullptr;            // FP64 node characteristic data per block ([NC_COUNT][nj][ld])
+  std::vector<size_t> nc_off;        // in doubles
   char* d_q1 = nullptr;              // RK stage states
   char* d_q2 = nullptr;
   void** d_tab = nullptr;            // pointer tables, nb entries each (see Tab)
@@ -267,7 +269,7 @@ struct fsp_batch {
 namespace {
 
 // pointer tables inside d_tab
-enum Tab { T_Q0 = 0, T_Q1, T_Q2, T_ACC, T_LX, T_LE, T_LX2, T_LE2, T_OUT, T_MX, T_ME, T_COUNT };
+enum Tab { T_Q0 = 0, T_Q1, T_Q2, T_ACC, T_LX, T_LE, T_LX2, T_LE2, T_OUT, T_MX, T_ME, T_NC, T_COUNT };
 
 size_t al(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -387,7 +389,7 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   // host descriptors
   h->params.resize(nblocks);
   h->coords.resize(nblocks);
-  size_t lam = 0, acc = 0, st = 0, mid = 0;
+  size_t lam = 0, acc = 0, st = 0, mid = 0, nc = 0;
   for (int b = 0; b < nblocks; ++b) {
     const fsp_block& B = blocks[b];
     Params& P = h->params[b];
@@ -427,6 +429,9 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
     // stored interface data (double accumulation only): xi [4][nj][ni + 3], eta [4][nj + 3][ni]
     h->mid_off.push_back(mid);
     if (cfg->precision != FSP_FP32) mid += al(8 * 4 * ((size_t)B.nj * (B.ni + 3) + (size_t)(B.nj + 3) * B.ni)) / 8;
+    h->nc_off.push_back(nc);
+    if (cfg->precision == FSP_FP64 && cfg->scheme != S32 && cfg->scheme != S52)
+      nc += al(8 * (size_t)NC_COUNT * B.nj * B.ld) / 8;
     const int lr = 8 * (cfg->precision == FSP_FP64 ? lam_rows<double>() : lam_rows<float>());
     for (int by = 0; by < (B.nj + lr - 1) / lr; ++by)
       for (int bx = 0; bx < (B.ni + 31) / 32; ++bx) h->tl.push_back({b, bx, by});
@@ -444,7 +449,7 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   const size_t bytes = al(sizeof(Params) * nblocks) + al(sizeof(CoordBlock) * nblocks) +
                        al(sizeof(TileRef) * h->tx_cap) + al(sizeof(TileRef) * h->te_cap) +
                        al(sizeof(TileRef) * h->tl.size()) + al(sizeof(double) * 2 * lam) + acc + 2 * st +
-                       al(sizeof(void*) * T_COUNT * nblocks) + sizeof(double) * mid;
+                       al(sizeof(void*) * T_COUNT * nblocks) + sizeof(double) * (mid + nc);
   if (cudaMalloc(&h->dmem, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -463,6 +468,7 @@ fsp_status fsp_batch_create(const fsp_config* cfg, int nblocks, const fsp_block*
   h->d_tab = reinterpret_cast<void**>(cur);
   cur += al(sizeof(void*) * T_COUNT * nblocks);
   h->d_mid = mid ? reinterpret_cast<double*>(cur) : nullptr;
+  h->d_nc = nc ? reinterpret_cast<double*>(cur) + mid : nullptr;
   bool ok = cudaMemcpy(h->d_params, h->params.data(), sizeof(Params) * nblocks, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(h->d_tx, h->tx.data(), sizeof(TileRef) * h->tx.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(h->d_te, h->te.data(), sizeof(TileRef) * h->te.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -499,6 +505,7 @@ fsp_status fsp_batch_bind(fsp_batch* h, const double* const* x, const double* co
       tab[T_MX * nb + b] = h->d_mid + h->mid_off[b];
       tab[T_ME * nb + b] = h->d_mid + h->mid_off[b] + 4 * (size_t)B.nj * (B.ni + 3);
     }
+    if (h->d_nc) tab[T_NC * nb + b] = h->d_nc + h->nc_off[b];
   }
   if (cudaMemcpy(h->d_params, h->params.data(), sizeof(Params) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(h->d_coords, h->coords.data(), sizeof(CoordBlock) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -593,6 +600,11 @@ fsp_status batch_stage(fsp_batch* h, int in, int out, int mode, double ca, doubl
     xi.mid = T + T_MX * nb;
     eta.mid = T + T_ME * nb;
   }
+  // FP64 with both passes marching: the xi pass leaves each node's characteristic data for
+  // the eta pass of the same right-hand side
+  // the one-midpoint schemes only: the two-midpoint eta pass has no shared memory left for it
+  const bool one_mid = h->cfg.scheme != S32 && h->cfg.scheme != S52;
+  if (h->d_nc && one_mid && h->vx == MARCH && h->ve == MARCH) xi.nc = eta.nc = T + T_NC * nb;
   if (lam_out >= 0) {
     eta.lxo = T + (lam_out ? T_LX2 : T_LX) * nb;
     eta.leo = T + (lam_out ? T_LE2 : T_LE) * nb;

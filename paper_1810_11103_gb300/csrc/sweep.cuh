@@ -267,11 +267,37 @@ struct IfacePre {
 // precision (float state, double Acc): only the metric-weighted flux E^ = mx E + my F, with the
 // Cartesian fluxes E, F in float and the two metric products in double, stored in fp; the
 // dissipative part A^ Q of the split is taken at the interfaces from the staged state.
+// The split fluxes from the node's characteristic data w and pressure p, already formed.
+template <typename Real, typename Acc>
+__device__ __forceinline__ void node_split_from(const Real q[4], const NodeChar<Real>& w, Real p, double mx,
+                                                double my, Acc hA, Acc& amx, Acc& amy, Acc fp[4], Acc fm[4]);
+
 template <int SC, typename Real, typename Acc>
 __device__ __forceinline__ void node_split(const Real q[4], double mx, double my, Real gamma, Acc hA,
                                            NodeChar<Real>& w, Acc& amx, Acc& amy, Acc fp[4], Acc fm[4]) {
   Real p;
   w = node_char<Real, SC>(q, gamma, p);
+  node_split_from<Real, Acc>(q, w, p, mx, my, hA, amx, amy, fp, fm);
+}
+
+// The characteristic data of an FP64 node as the xi pass stores it for the eta pass of the same
+// right-hand side (NC_COUNT planes: the twelve NodeChar values, then the pressure).
+constexpr int NC_COUNT = 13;
+__device__ __forceinline__ void nc_put(double* b, long long plane, long long o, const NodeChar<double>& w, double p) {
+  const double v[NC_COUNT] = {w.u, w.v, w.hc, w.a10, w.b1u, w.b1v, w.b1, w.cs, w.us, w.vs, w.Hs, w.h2s, p};
+#pragma unroll
+  for (int k = 0; k < NC_COUNT; ++k) b[k * plane + o] = v[k];
+}
+__device__ __forceinline__ void nc_get(const double* b, long long stride, NodeChar<double>& w, double& p) {
+  w.u = b[0]; w.v = b[stride]; w.hc = b[2 * stride]; w.a10 = b[3 * stride];
+  w.b1u = b[4 * stride]; w.b1v = b[5 * stride]; w.b1 = b[6 * stride]; w.cs = b[7 * stride];
+  w.us = b[8 * stride]; w.vs = b[9 * stride]; w.Hs = b[10 * stride]; w.h2s = b[11 * stride];
+  p = b[12 * stride];
+}
+
+template <typename Real, typename Acc>
+__device__ __forceinline__ void node_split_from(const Real q[4], const NodeChar<Real>& w, Real p, double mx,
+                                                double my, Acc hA, Acc& amx, Acc& amy, Acc fp[4], Acc fm[4]) {
   amx = from_f64<Acc>(mx);
   amy = from_f64<Acc>(my);
   if constexpr (Staged<Real, Acc>::SPLIT) {
@@ -918,7 +944,8 @@ template <int S, int MODE, typename Real, typename Acc>
 __device__ __forceinline__ void march_row(const Params& P, const Real* __restrict__ Q, const Real* const* qtab,
                                           double lamv, const Acc* __restrict__ Dacc, Acc* __restrict__ Dout,
                                           Real* qout, const Real* Qn, double ca, double cb, double dt, int row,
-                                          int s0, int s1, unsigned char* wsm, const double* __restrict__ mid = nullptr) {
+                                          int s0, int s1, unsigned char* wsm, const double* __restrict__ mid = nullptr,
+                                          double* __restrict__ ncout = nullptr) {
   using Ms = MarchShape<S, Real, Acc>;
   constexpr int NMP = Scheme<S>::nmp;
   constexpr int K = NMP == 1 ? 3 : 2;
@@ -965,10 +992,14 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
       mx = met_at(P, 0, m, row);
       my = met_at(P, 1, m, row);
     }
-    NodeChar<Real> w;
     Acc amx, amy, fp[4], fm[4];
-    node_split<weno_scale<Scheme<S>::r>(), Real, Acc>(q, mx, my, gamma, hA, w, amx, amy, fp, fm);
+    Real pr;
+    const NodeChar<Real> w = node_char<Real, weno_scale<Scheme<S>::r>()>(q, gamma, pr);
+    node_split_from<Real, Acc>(q, w, pr, mx, my, hA, amx, amy, fp, fm);
     st.store(m & (RING - 1), q, w, amx, amy, fp, fm, mx, my);
+    // FP64: the row's own nodes' characteristic data for the eta pass of this right-hand side
+    if constexpr (std::is_same<Real, double>::value && MODE == MODE_ACC && NMP == 1)
+      if (ncout && m >= s0 && m < s1) nc_put(ncout, plane, (long long)row * P.ld + m, w, pr);
   };
   // cp.async of node m's state and metrics into this lane's staging slot (interior only)
   auto prefetch = [&](int m) -> bool {
@@ -1126,7 +1157,11 @@ struct MarchEtaShape {
   // per thread: next node's state and two metrics; then two buffers (steps t even and odd)
   // of the epilogue operands: J^-1, the xi metrics (MODE_STAGE_L), the other direction's
   // difference, Q^n (stage modes)
-  static constexpr size_t o_ep() { return o_raw() + (size_t)NT * (4 * sizeof(Real) + 16); }
+  // FP64 one-midpoint schemes: the next node's stored characteristic data (NC_COUNT doubles per
+  // thread); the two-midpoint schemes' midpoint records leave no room for it
+  static constexpr bool NC = sizeof(Real) == 8 && NMP == 1;
+  static constexpr size_t o_nc() { return o_raw() + (size_t)NT * (4 * sizeof(Real) + 16); }
+  static constexpr size_t o_ep() { return o_nc() + (NC ? (size_t)NT * NC_COUNT * 8 : 0); }
   static constexpr size_t ep_bytes(int mode) {
     return mode == 0 ? 0
                      : (size_t)NT * (8 + (mode == 3 ? 16 : 0) + 4 * sizeof(Acc) + (mode >= 2 ? 4 * sizeof(Real) : 0));
@@ -1140,7 +1175,8 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
                                           Acc* __restrict__ Dout, Real* qout, const Real* Qn, double ca, double cb,
                                           double dt, int c0, int s0, int s1, unsigned char* sm,
                                           double* lxo = nullptr, double* leo = nullptr,
-                                          const double* __restrict__ mid = nullptr) {
+                                          const double* __restrict__ mid = nullptr,
+                                          const double* __restrict__ ncin = nullptr) {
   using Ms = MarchEtaShape<S, Real, Acc>;
   constexpr bool STAGE = MODE >= MODE_STAGE, LAM = MODE == MODE_STAGE_L;
   constexpr int NMP = Scheme<S>::nmp;
@@ -1156,6 +1192,8 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
   rF.carve(sm + Ms::o_f(), Ms::NS);
   Real* rawq = reinterpret_cast<Real*>(sm + Ms::o_raw());              // [4][NT]
   double* rawm = reinterpret_cast<double*>(rawq + 4 * Ms::NT);         // [2][NT]
+  double* rawc = reinterpret_cast<double*>(sm + Ms::o_nc());            // [NC_COUNT][NT] (FP64)
+  const bool usenc = Ms::NC && ncin != nullptr;
   // epilogue buffer k: J^-1 [NT], xi metrics [2][NT] (MODE_STAGE_L), difference [4][NT], Q^n [4][NT]
   auto eJ = [&](int k) { return reinterpret_cast<double*>(sm + Ms::o_ep() + k * Ms::ep_bytes(MODE)); };
   auto eX = [&](int k) { return eJ(k) + Ms::NT; };
@@ -1190,7 +1228,18 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
     }
     NodeChar<Real> pw;
     Acc amx, amy, fp[4], fm[4];
-    node_split<weno_scale<Scheme<S>::r>(), Real, Acc>(q, mx, my, gamma, hA, pw, amx, amy, fp, fm);
+    if constexpr (std::is_same<Real, double>::value) {
+      if (staged && usenc) {
+        // the xi pass of this right-hand side formed them from the same state
+        double pr;
+        nc_get(rawc + tid, Ms::NT, pw, pr);
+        node_split_from<Real, Acc>(q, pw, pr, mx, my, hA, amx, amy, fp, fm);
+      } else {
+        node_split<weno_scale<Scheme<S>::r>(), Real, Acc>(q, mx, my, gamma, hA, pw, amx, amy, fp, fm);
+      }
+    } else {
+      node_split<weno_scale<Scheme<S>::r>(), Real, Acc>(q, mx, my, gamma, hA, pw, amx, amy, fp, fm);
+    }
     st.store(slot(m), q, pw, amx, amy, fp, fm, mx, my);
   };
   // cp.async of node (col, m) into this thread's staging slot (interior rows only), and of the
@@ -1205,6 +1254,10 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
       const double* mp = P.met + (long long)(m + G) * P.mld + (col + G);
       cp_async<8>(rawm + tid, mp + 2 * P.mplane);
       cp_async<8>(rawm + Ms::NT + tid, mp + 3 * P.mplane);
+      if (usenc) {
+#pragma unroll
+        for (int k = 0; k < NC_COUNT; ++k) cp_async<8>(rawc + k * Ms::NT + tid, ncin + k * plane + o);
+      }
       ok = true;
     }
     if constexpr (MODE != MODE_ACC) {
@@ -1385,6 +1438,7 @@ struct BatchPass {                 // device arrays indexed by block
   double* const* lxo;              // line maxima of the written state, xi and eta (MODE_STAGE_L)
   double* const* leo;
   const double* const* mid;        // midpoint metrics of the pass's direction (or null)
+  const double* const* nc;         // FP64 node characteristic data: written by xi, read by eta (or null)
 };
 
 template <int S, int DIR, int MODE, typename Real, typename Acc, int V>
@@ -1422,7 +1476,8 @@ march_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) {
   march_row<S, MODE, Real, Acc>(sp, B.q[b], B.q, B.lam[b][row], MODE == MODE_ACC ? nullptr : B.dacc[b],
                                 MODE == MODE_ACC ? B.dout[b] : nullptr, MODE == MODE_ACC ? nullptr : B.qout[b],
                                 MODE == MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, row, s0, s1,
-                                smem_raw + warp * Ms::warp_bytes(), B.mid ? B.mid[b] : nullptr);
+                                smem_raw + warp * Ms::warp_bytes(), B.mid ? B.mid[b] : nullptr,
+                                B.nc ? const_cast<double*>(B.nc[b]) : nullptr);
 }
 
 // Marching eta pass of many blocks: CTA b takes the 32 columns from 32 by of block
@@ -1447,7 +1502,7 @@ march_eta_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) 
                                 MODE == MODE_ACC ? B.dout[b] : nullptr, MODE == MODE_ACC ? nullptr : B.qout[b],
                                 MODE >= MODE_STAGE ? B.qn[b] : nullptr, ca, cb, dt, t.by * 32, s0, s1, smem_raw,
                                 MODE == MODE_STAGE_L ? B.lxo[b] : nullptr, MODE == MODE_STAGE_L ? B.leo[b] : nullptr,
-                                B.mid ? B.mid[b] : nullptr);
+                                B.mid ? B.mid[b] : nullptr, B.nc ? B.nc[b] : nullptr);
 }
 
 // Untyped pass tables (device arrays of per-block pointers) and their typed view.
@@ -1463,6 +1518,7 @@ struct PassTables {
   void* const* lxo;     // MODE_STAGE_L only
   void* const* leo;
   void* const* mid;     // per block: midpoint metrics of this direction, or null (marching passes)
+  void* const* nc;      // per block: FP64 node characteristic data (xi writes, eta reads), or null
 };
 
 template <typename Real, typename Acc>
@@ -1479,6 +1535,7 @@ BatchPass<Real, Acc> typed_pass(const PassTables& t) {
   B.lxo = reinterpret_cast<double* const*>(t.lxo);
   B.leo = reinterpret_cast<double* const*>(t.leo);
   B.mid = reinterpret_cast<const double* const*>(t.mid);
+  B.nc = reinterpret_cast<const double* const*>(t.nc);
   return B;
 }
 
