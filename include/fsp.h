@@ -347,7 +347,9 @@ fsp_status fsp_reciprocal_check(const double* in, double* out, long long n, void
  * layers, corners included.  Line maxima of the splitting are taken per block line.
  * The handle owns its device memory (descriptors, tile tables, per-block line maxima,
  * xi accumulators, RK stage states and, for FSP_FP64 and FSP_FP32_MIXED, the midpoint
- * metrics of every interface) from create to destroy; no other call allocates.  The midpoint
+ * metrics of every interface, for FSP_FP64 also the interfaces' characteristic directions and
+ * the nodes' characteristic data that the xi pass leaves for the eta pass) from create to
+ * destroy; no other call allocates.  The midpoint
  * metrics (the interpolation of Section 2.4) are taken from the bound metrics at the start of
  * each fsp_batch_rhs, fsp_batch_rk3_step and fsp_batch_tune, so the marching passes read them
  * instead of interpolating per right-hand side.
