@@ -137,9 +137,9 @@ def algorithmic_flops(args):
     return d["schemes"][SCHEME_NAMES[args.scheme]]
 
 
-def traffic_of(args, prec, variant):
-    """DRAM bytes of one launch of the xi sweep in tile variant `variant`, from an ncu capture of
-    the current kernel sources (None if there is none)."""
+def traffic_of(args, prec, variant, direction=0):
+    """DRAM bytes of one launch of the xi (direction 0) or eta (1) sweep in tile variant
+    `variant`, from an ncu capture of the current kernel sources (None if there is none)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -148,7 +148,7 @@ def traffic_of(args, prec, variant):
     for tr in entries if isinstance(entries, list) else [entries]:
         if (tr.get("source_hash") == source_hash() and tr.get("workload") == args.workload
                 and tr.get("scheme") == args.scheme and tr.get("precision") == prec
-                and tr.get("variant") == variant):
+                and tr.get("variant") == variant and tr.get("dir", 0) == direction):
             return tr.get("bytes_per_launch")
     return None
 
@@ -443,27 +443,34 @@ def measure_cylinder(args, prec, C, per_block=False):
     xi_fl = fl["sweep_xi_per_node"] - mid_xi
     eta_fl = fl["sweep_eta_per_node"] - 4.0 - mid_eta
     step_fl = 3 * fl["rhs_per_node"] - 2 * (mid_xi + mid_eta)
-    achieved = xi_fl * nodes / t_k / 1e12
     rhs_total = job_rhs(nodes, args.steps, C.world)
-    kname = ("march_batch_kernel xi (marching warps)" if tiles["xi"]["variant"] == 3 else "sweep_batch_kernel xi") \
-        + ", all 64 blocks (fsp_batch_flux_difference dir 0)"
     nom = C.nominal(prec, clk.get("sm_mhz"))
-    roof = {"bound": "alu", "kernel": kname,
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic_of(args, prec, tiles["xi"]["variant"]),
+
+    def pass_roof(d, fl_node, t):
+        var = tiles["xi" if d == 0 else "eta"]["variant"]
+        name = (("march_batch_kernel xi (marching warps)" if var == 3 else "sweep_batch_kernel xi") if d == 0 else
+                ("march_eta_batch_kernel eta (marching CTAs)" if var == 3 else "sweep_batch_kernel eta"))
+        a = fl_node * nodes / t / 1e12
+        return {"kernel": name + f", all 64 blocks (fsp_batch_flux_difference dir {d})", "kernel_ms": 1e3 * t,
+                "flops_per_node": fl_node, "achieved": a, "frac": a / peak, "frac_vs_nominal": a / nom,
+                "traffic": traffic_of(args, prec, var, d)}
+    passes = {"xi": pass_roof(0, xi_fl, t_k), "eta": pass_roof(1, eta_fl, t_e)}
+    # the roofline kernel: the longer of the two passes, each timed alone (one launch over all
+    # blocks); the other beside it
+    dom = "eta" if t_e > t_k else "xi"
+    roof = {"bound": "alu", **passes[dom], "direction": dom, "peak": peak, "unit": "TFLOP/s",
             "peak_source": f"{pipe} FMA probe (fsp_fma_peak) in this run, same clocks",
-            "nominal_peak": nom, "frac_vs_nominal": achieved / nom,
-            "flops_per_node": xi_fl, "units_per_launch": nodes,
-            "kernel_ms": 1e3 * t_k,
-            # the other sweep and the whole step against the same peak
-            "eta": {"kernel_ms": 1e3 * t_e, "flops_per_node": eta_fl, "frac": eta_fl * nodes / t_e / 1e12 / peak},
+            "nominal_peak": nom, "units_per_launch": nodes,
+            "xi": passes["xi"], "eta": passes["eta"],
+            # the whole step against the same peak
             "step_frac": step_fl * nodes / (t_dev / args.steps) / 1e12 / peak,
             "midpoint_metrics": ({"flops_per_node_per_step": mid_xi + mid_eta,
                                   "how": "midpoint metrics" + (" and characteristic direction" if prec == "fp64" else "")
                                          + " per interface once per step by mid_batch_kernel; left out of the "
                                            "passes' counts"} if mid_if else None)}
     if prec == "mixed":
-        roof = mixed_roofline(args, C, roof, xi_fl, nodes, t_k, clk.get("sm_mhz"), hoisted=mid_xi > 0)
+        roof = mixed_roofline(args, C, roof, passes[dom]["flops_per_node"], nodes, t_e if dom == "eta" else t_k,
+                              clk.get("sm_mhz"), hoisted=mid_xi > 0)
     out = {
         "value": rhs_total / t_dev / 1e6, "ms_per_step": 1e3 * t_dev / args.steps, "nodes": nodes,
         "nblocks": len(blocks),
@@ -524,11 +531,13 @@ def mixed_roofline(args, C, roof, flops_node, nodes, t_k, mhz, hoisted=False):
               "frac_vs_nominal": f64 * nodes / t_k / 1e12 / n64}
     head, other = (part64, part32) if t64 >= t32 else (part32, part64)
     out = dict(roof)
-    # the eta sweep and the whole step against the bounding part as well (FP64 operations of the
-    # two sweeps; the float line maxima are left out of the bound)
-    te = roof["eta"]["kernel_ms"] / 1e3
-    out["eta"] = {"kernel_ms": roof["eta"]["kernel_ms"], "flops_per_node": f64,
-                  "frac": f64 * nodes / te / 1e12 / p64, "part": "FP64 part"}
+    # both sweeps against the bounding part as well (the FP64 operations of each; the float line
+    # maxima are left out of the bound)
+    for d in ("xi", "eta"):
+        td = roof[d]["kernel_ms"] / 1e3
+        out[d] = dict(roof[d], flops_per_node=f64, frac=f64 * nodes / td / 1e12 / p64,
+                      achieved=f64 * nodes / td / 1e12, frac_vs_nominal=f64 * nodes / td / 1e12 / n64,
+                      part="FP64 part")
     out["step_frac"] = None
     out.update({"bound": "alu", "achieved": head["achieved"], "peak": head["peak"], "frac": head["frac"],
                 "nominal_peak": head["nominal_peak"], "frac_vs_nominal": head["frac_vs_nominal"],
@@ -847,10 +856,11 @@ def summary(args, head, others, adjoint, seventh, three_d=None):
     for p, r in [(args.precision, head)] + list(others.items()):
         rf = r["roofline"]
         e = {"value": _r(r["value"]), "ms_step": _r(r["ms_per_step"]), "e2e": _r(r["e2e"]["value"]),
-             "frac": _r(rf["frac"], 3), "frac_nominal": _r(rf.get("frac_vs_nominal"), 3),
-             "xi_ms": _r(rf["kernel_ms"])}
-        if rf.get("eta"):
-            e["eta_ms"], e["eta_frac"] = _r(rf["eta"]["kernel_ms"]), _r(rf["eta"]["frac"], 3)
+             "kernel": rf.get("direction", "xi"), "frac": _r(rf["frac"], 3),
+             "frac_nominal": _r(rf.get("frac_vs_nominal"), 3)}
+        for d in ("xi", "eta"):
+            if rf.get(d):
+                e[d + "_ms"], e[d + "_frac"] = _r(rf[d]["kernel_ms"]), _r(rf[d]["frac"], 3)
         if rf.get("step_frac"):
             e["step_frac"] = _r(rf["step_frac"], 3)
         if p == "mixed":
@@ -968,8 +978,8 @@ def main():
         for p in ("fp64", "fp32"):
             r = measure_cylinder(a7, p, C)
             seventh[p] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
-                          "roofline": {k: r["roofline"][k] for k in ("kernel", "achieved", "peak", "unit", "frac",
-                                                                   "flops_per_node", "kernel_ms")},
+                          "roofline": {k: r["roofline"][k] for k in ("kernel", "direction", "achieved", "peak", "unit",
+                                                                   "frac", "flops_per_node", "kernel_ms")},
                           "tiles": r["tiles"]}
     three_d = measure_3d(args, C) if args.three_d and args.workload == "cylinder64" else None
     if rank == 0:
