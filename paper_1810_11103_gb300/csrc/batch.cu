@@ -330,14 +330,19 @@ T* carve(char*& cur, size_t count) {
 // on the cylinder).  The order does not change any result.
 void tiles_for(const fsp_batch* h, int dir, int v, std::vector<TileRef>& out) {
   int T0, NL0;
-  tile_dims(h->cfg.scheme, dir, T0, NL0, v);
+  const bool fp64 = h->cfg.precision == FSP_FP64;
+  tile_dims(h->cfg.scheme, dir, T0, NL0, v, fp64);
   std::vector<std::pair<long long, TileRef>> w;
   for (int b = 0; b < h->nb; ++b) {
     const fsp_block& B = h->blk[b];
     const int n = dir == 0 ? B.ni : B.nj, nl = dir == 0 ? B.nj : B.ni;
     int T = T0, NL = NL0;
     if (dir == 0 && v == MARCH) T = march_seg_len(n);   // rows split into equal segments
-    if (dir == 1 && v == MARCH) { T = march_eta_seg((h->cfg.scheme == S32 || h->cfg.scheme == S52) ? 2 : 1); NL = 32; }
+    if (dir == 1 && v == MARCH) {
+      const int nmp = (h->cfg.scheme == S32 || h->cfg.scheme == S52) ? 2 : 1;
+      T = march_eta_seg(nmp, march_eta_centres(fp64, nmp));
+      NL = 32;
+    }
     for (int by = 0; by < (nl + NL - 1) / NL; ++by)
       for (int bx = 0; bx < (n + T - 1) / T; ++bx) {
         // work: outputs along the line plus the stencil halo, times the lines
@@ -872,7 +877,7 @@ fsp_status fsp_batch_tile_shape(const fsp_batch* h, int dir, int* variant, int* 
   if (!h || (dir != 0 && dir != 1)) return FSP_ERR_INVALID_ARG;
   const int v = dir == 0 ? h->vx : h->ve;
   int T, NL;
-  tile_dims(h->cfg.scheme, dir, T, NL, v);
+  tile_dims(h->cfg.scheme, dir, T, NL, v, h->cfg.precision == FSP_FP64);
   if (variant) *variant = v;
   if (lines) *lines = NL;
   if (outputs) *outputs = T;

@@ -342,7 +342,7 @@ sweep3_kernel(P3 P, const double* __restrict__ Q, const double* __restrict__ lam
               const double* Qn, double ca, double cb, double dt) {
   using Sh = Tile3<S, D>;
   using Sc = Scheme<S>;
-  constexpr int NL = Sh::NL, W = Sh::W, T = Sh::T, NP = Sh::NP, NN = Sh::NN, NW = Sh::NW, NMP = Sh::NMP;
+  constexpr int NL = Sh::NL, T = Sh::T, NN = Sh::NN, NW = Sh::NW, NMP = Sh::NMP;
   constexpr int R = Sc::r, H = R == 4 ? 3 : 2, NA = 2 * H, SC = weno_scale<R>();
   extern __shared__ __align__(16) double sm3[];
   double* sq = sm3;                 // [5][NN]

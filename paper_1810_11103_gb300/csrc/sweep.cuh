@@ -232,12 +232,22 @@ struct MarchShape {
   static constexpr size_t smem_bytes() { return MARCH_WARPS * warp_bytes(); }
 };
 
+constexpr int EW = 8;                               // warps (rows per step) of a marching eta CTA
+// Whether the marching eta pass evaluates the interface sides per centre node (centre_sides,
+// as the FP64 xi pass does): FP64 one-midpoint schemes, whose pass is bound by its FP64
+// instructions.  A step then takes the centres r - 1 + w and the interfaces one row behind
+// them, so a segment of eight steps ends one output earlier (62 rows).
+__host__ __device__ constexpr bool march_eta_centres(bool fp64, int nmp) { return fp64 && nmp == 1; }
+__host__ __device__ constexpr int march_eta_seg(int nmp, bool centre = false) {
+  return 8 * EW - (2 * nmp - 1) - (centre ? 1 : 0);
+}
+
 // Host view of the tile shape: output nodes per line T and lines per CTA NL (for the
 // marching variant: rows per CTA, and the longest segment a warp walks).
-inline void tile_dims(int scheme, int dir, int& T, int& NL, int variant = 0) {
+inline void tile_dims(int scheme, int dir, int& T, int& NL, int variant = 0, bool fp64 = false) {
   const int nmp = (scheme == S32 || scheme == S52) ? 2 : 1;
   if (dir == 0 && variant == MARCH) { NL = MARCH_WARPS; T = MARCH_SEG; return; }
-  if (dir == 1 && variant == MARCH) { NL = 32; T = 8 * 8 - (2 * nmp - 1); return; }   // EW = 8
+  if (dir == 1 && variant == MARCH) { NL = 32; T = march_eta_seg(nmp, march_eta_centres(fp64, nmp)); return; }
   NL = shape_nl(dir, variant);
   T = scheme == S74 ? 256 / NL - 5 : 256 / NL - nmp - 1;
 }
@@ -1136,24 +1146,29 @@ __device__ __forceinline__ void march_row(const Params& P, const Real* __restric
 //   nodes       m = r + K + w (K = 2, 3 for WENOIU7) into the ring (row slot m mod ERING),
 //               state, metrics and the
 //               epilogue operands of the next step staged by cp.async during this step
-//   interfaces  q = r - NMP + w: midpoint fluxes, h (1MP) or the midpoint record (2MP)
+//   centres     (FP64 1MP) c = r - 1 + w: both interface sides centred at node c
+//               (centre_sides), Q+ of c + 1/2 into a ring, Q- of c - 1/2 kept by the thread
+//   interfaces  q = r - NMP + w (FP64 1MP: q = c - 1, Q+ from the warp below): midpoint
+//               fluxes, h (1MP) or the midpoint record (2MP)
 //   h           (2MP) at q - 1 from the records of q - 2 .. q
 //   outputs     node s = the interface just completed
 // with a block barrier after each phase that hands data to other warps.  The ring holds the
 // at most 15 rows a step reads or stages; the start-up stages the rows below r + K.
 // --------------------------------------------------------------------------------------
-constexpr int EW = 8;                               // warps (rows per step) of a marching eta CTA
 constexpr int ERING = 16;                           // row slots of its ring
 constexpr int MARCH_ETA = 3;                        // the marching eta variant
-__host__ __device__ constexpr int march_eta_seg(int nmp) { return 8 * EW - (2 * nmp - 1); }
 template <int S, typename Real, typename Acc>
 struct MarchEtaShape {
   static constexpr int NMP = Scheme<S>::nmp;
   static constexpr int NS = ERING * 32;             // ring entries (row slot x lane)
   static constexpr int NT = EW * 32;                // threads
+  static constexpr bool CENTRE = march_eta_centres(sizeof(Real) == 8, NMP);
+  static constexpr int SEG = march_eta_seg(NMP, CENTRE);
   static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(NS); }
   static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * NS; }
-  static constexpr size_t o_raw() { return o_f() + (NMP == 2 ? MidStore<Real, Acc>::bytes(NS) : 0); }
+  // Q+ of the interface above each centre node (4 Real per ring slot)
+  static constexpr size_t o_qp() { return o_f() + (NMP == 2 ? MidStore<Real, Acc>::bytes(NS) : 0); }
+  static constexpr size_t o_raw() { return o_qp() + (CENTRE ? sizeof(Real) * 4 * NS : 0); }
   // per thread: next node's state and two metrics; then two buffers (steps t even and odd)
   // of the epilogue operands: J^-1, the xi metrics (MODE_STAGE_L), the other direction's
   // difference, Q^n (stage modes)
@@ -1193,6 +1208,8 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
   Real* rawq = reinterpret_cast<Real*>(sm + Ms::o_raw());              // [4][NT]
   double* rawm = reinterpret_cast<double*>(rawq + 4 * Ms::NT);         // [2][NT]
   double* rawc = reinterpret_cast<double*>(sm + Ms::o_nc());            // [NC_COUNT][NT] (FP64)
+  Real* rQp = reinterpret_cast<Real*>(sm + Ms::o_qp());                 // Q+ per centre slot
+  constexpr bool CENTRE = Ms::CENTRE;
   const bool usenc = Ms::NC && ncin != nullptr;
   // epilogue buffer k: J^-1 [NT], xi metrics [2][NT] (MODE_STAGE_L), difference [4][NT], Q^n [4][NT]
   auto eJ = [&](int k) { return reinterpret_cast<double*>(sm + Ms::o_ep() + k * Ms::ep_bytes(MODE)); };
@@ -1280,12 +1297,12 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
     return ok;
   };
   Real colmax = Real(0);                                   // MODE_STAGE_L: this thread's eta maximum
-  const int lag = NMP == 1 ? 1 : 3;                       // output s = r - lag + w
+  const int lag = CENTRE ? 2 : NMP == 1 ? 1 : 3;          // output s = r - lag + w
   // start-up: rows s0 - 2 - NMP .. s0 + K - 1
   if (w < K + NMP + H) stage_node(s0 - NMP - H + w, false);
   bool staged = prefetch(s0 + K + w, s0 - lag + w, 0);
   cp_async_commit();
-  const int steps = (s1 - s0 + 2 * NMP - 1 + EW - 1) / EW;
+  const int steps = (s1 - s0 + 2 * NMP - 1 + (CENTRE ? 1 : 0) + EW - 1) / EW;
   for (int t = 0; t < steps; ++t) {
     const int r = s0 + EW * t;
     const int m = r + K + w;
@@ -1297,9 +1314,33 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
     staged = prefetch(m + EW, s + EW, (t + 1) & 1);
     cp_async_commit();
     __syncthreads();
-    const int q = r - NMP + w;
+    // centre layout: centre c = r - 1 + w takes the "+" side of interface c + 1/2 (to the Q+
+    // ring, read by the warp above or by warp 0 a step later) and the "-" side of c - 1/2
+    Real Qm[4];
+    if constexpr (CENTRE) {
+      const int c = r - 1 + w;
+      if (on && c <= s1) {
+        auto at = [&](int mm) { return slot(c + mm); };
+        Real npx, npy, nmx, nmy;
+        if (pdir) {
+          const long long mo_ = (long long)(c + 2) * P.ni + col;   // interface c; c - 1 one row below
+          npx = mid[mo_ + 2 * mstr];
+          npy = mid[mo_ + 3 * mstr];
+          nmx = mid[mo_ - P.ni + 2 * mstr];
+          nmy = mid[mo_ - P.ni + 3 * mstr];
+        } else {
+          char_direction(st, at(0), at(1), npx, npy);
+          char_direction(st, at(-1), at(0), nmx, nmy);
+        }
+        Real Qp[4];
+        centre_sides<S, Real, Acc>(st, at, npx, npy, nmx, nmy, eps, Qp, Qm);
+        st4(rQp, Ms::NS, slot(c), Qp[0], Qp[1], Qp[2], Qp[3]);
+      }
+      __syncthreads();
+    }
+    const int q = r - NMP - (CENTRE ? 1 : 0) + w;
     Real qs[4] = {Real(0), Real(0), Real(0), Real(0)};
-    if (on && q <= s1 + NMP - 2) {
+    if (on && q >= s0 - NMP && q <= s1 + NMP - 2) {
       auto at = [&](int mm) { return slot(q + mm); };
       IfacePre pr;
       if (pre) {
@@ -1307,14 +1348,23 @@ __device__ __forceinline__ void march_col(const Params& P, const Real* __restric
         pr.mid = true;
         pr.mx = mid[mo_];
         pr.my = mid[mo_ + mstr];
-        if (pdir) {
+        if (pdir && !CENTRE) {
           pr.dir = true;
           pr.nx = mid[mo_ + 2 * mstr];
           pr.ny = mid[mo_ + 3 * mstr];
         }
       }
       Mid<Real, Acc> mo;
-      interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo, 0, 0, pr);
+      if constexpr (CENTRE) {
+        // Q+ from centre q, Q- from this thread's centre q + 1
+        Real Qs[2][4];
+        ld4(rQp, Ms::NS, slot(q), Qs[0]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Qs[1][v] = Qm[v];
+        mid_fluxes<S, Real, Acc>(st, at, Qs, gamma, 0, A, mo, 0, pr);
+      } else {
+        interface_mid<S, Real, Acc, true>(st, at, gamma, eps, P.ppm, P.linw, P.interp, A, mo, 0, 0, pr);
+      }
       if constexpr (NMP == 1) {
         Acc h[4];
         h_combine<S, Real, Acc>(st, at, A, mo, mo, mo, h, P);
@@ -1496,7 +1546,7 @@ march_eta_batch_kernel(BatchPass<Real, Acc> B, double ca, double cb, double dt) 
   if (threadIdx.x == 0) sp = B.params[t.block];
   __syncthreads();
   const int b = t.block;
-  const int seg = march_eta_seg(Scheme<S>::nmp);
+  const int seg = MarchEtaShape<S, Real, Acc>::SEG;
   const int s0 = t.bx * seg, s1 = min(sp.nj, s0 + seg);
   march_col<S, MODE, Real, Acc>(sp, B.q[b], B.q, B.lam[b], MODE == MODE_ACC ? nullptr : B.dacc[b],
                                 MODE == MODE_ACC ? B.dout[b] : nullptr, MODE == MODE_ACC ? nullptr : B.qout[b],
