@@ -1,18 +1,24 @@
 """Host model of the marching eta pass's step schedule (`march_col` in csrc/sweep.cuh).
 
 A CTA of EW warps walks a column segment [s0, s1) EW rows per step; warp w of the step at row r
-stages node r + K + w into a ring of ERING row slots, then (FP64 one-midpoint schemes) takes
-the centre r - 1 + w, the interface r - 2 + w and the output r - 2 + w, or (per-interface
-layout) the interface and output r - 1 + w.  Block barriers split a step into barrier
-intervals: staging | centres | interfaces | outputs, where the outputs of step t share an
-interval with the staging of step t + 1.  The model checks, for columns of 1 to 129, 255, 256
-and 299 rows (every segment length up to a full segment, first, inner and last segments) and
-stencil half-widths 2 (WENOIU3/5) and 3 (WENOIU7):
+stages node r + K + w into a ring of ERING row slots, then takes, in the per-interface layout,
+the interface and output r - 1 + w, or, in the centre layout (FP64 one-midpoint schemes), the
+centre r - 1 + w and the interface and output r - 2 + w.  Each lane is one column, so all data
+moves along a column between warps, through three shared-memory rings: staged nodes, Q+ of
+each centre (centre layout) and h of each interface.
 
-* every row a phase reads from a ring (node ring, Q+ ring, h ring) was written in an earlier
-  interval and no other row overwrites its slot up to and including the reading interval;
-* every interface s0 - 1 .. s1 - 1, every output s0 .. s1 - 1 and (centre layout) every
-  centre s0 - 1 .. s1 is taken exactly once, within the step count the kernel computes.
+The phases of a step are separated by block barriers (__syncthreads).  The model builds the
+happens-before order of one segment from program order and the barriers, where a synchronisation
+point is either a block barrier ("full") or a hand-off from warp to warp ("chain": warp w
+waits until warp w - 1 has arrived, then arrives itself, so that after its wait it follows
+every earlier phase of warps 0 .. w - 1; a weaker point the tests use to show that the block
+barriers cannot be thinned that way everywhere), and checks, for columns of 1 to 129, 255, 256 and 299 rows (every segment length up to a
+full one; first, inner and last segments) and stencil half-widths 2 (WENOIU3/5) and 3
+(WENOIU7):
+* every ring row a phase reads was written before the read, and every other row written to
+  the same slot is ordered before that write or after the read;
+* every centre, interface and output of the segment is taken exactly once, within the step
+  count the kernel computes.
 
 EW and ERING are read from the header so that the model follows the kernel's constants.
 """
@@ -35,88 +41,152 @@ EW = _const("EW")
 ERING = _const("ERING")
 NMP = 1
 
+# phases and the synchronisation after each, per layout
+LAYOUTS = {
+    # per-interface layout (the float paths): two block barriers per step
+    "barriers": [("stage", "full"), ("iface", "full"), ("out", None)],
+    # centre layout (FP64 one-midpoint schemes): three block barriers per step
+    "centre": [("stage", "full"), ("centre", "full"), ("iface", "full"), ("out", None)],
+}
 
-def schedule(s0, s1, n, H, K, centre, centre_barrier=True):
-    """Writes and reads of one segment: (ring, row, interval) triples, and what was taken."""
+
+class Order:
+    """Nodes in construction (topological) order with their ancestor sets as bit masks."""
+
+    def __init__(self):
+        self.anc = []
+
+    def node(self, preds):
+        a = 0
+        for p in preds:
+            if p is not None:
+                a |= self.anc[p] | (1 << p)
+        self.anc.append(a)
+        return len(self.anc) - 1
+
+    def before(self, a, b):
+        return (self.anc[b] >> a) & 1 == 1
+
+
+def schedule(s0, s1, n, H, K, layout):
+    """Accesses of one segment: writes[ring] = [(row, node)], reads = [(ring, row, node)]."""
+    centre = layout.startswith("centre")
+    phases = LAYOUTS[layout]
     lag = 2 if centre else 1
     steps = (s1 - s0 + 2 * NMP - 1 + (1 if centre else 0) + EW - 1) // EW
+    order = Order()
     writes = {"node": [], "qp": [], "h": []}
     reads = []
     taken = {"iface": [], "out": [], "centre": []}
+    last = [None] * EW                                   # each warp's latest node
 
     def staged(m):
         return m <= s1 + 3 and m <= n + 3
 
-    for w in range(EW):                                  # start-up rows below s0 + K
+    for w in range(EW):                                  # start-up: rows below s0 + K
+        last[w] = order.node([])
         if w < K + NMP + H and staged(s0 - NMP - H + w):
-            writes["node"].append((s0 - NMP - H + w, 0))
-    for t in range(steps):
+            writes["node"].append((s0 - NMP - H + w, last[w]))
+
+    def phase(name, t, w, nd):
         r = s0 + EW * t
-        if centre:   # stage | centres | interfaces | outputs: three barriers per step
-            i_stage, i_centre, i_iface, i_out = 3 * t, 3 * t + 1, 3 * t + 2, 3 * t + 3
-            if not centre_barrier:
-                i_iface = i_centre
-        else:        # stage | interfaces | outputs: two barriers per step
-            i_stage, i_iface, i_out = 2 * t, 2 * t + 1, 2 * t + 2
-        for w in range(EW):
+        if name == "stage":
             m = r + K + w
             if staged(m):
-                writes["node"].append((m, i_stage))
-            if centre:
-                c = r - 1 + w
-                if c <= s1:
-                    taken["centre"].append(c)
-                    reads += [("node", x, i_centre) for x in range(c - H, c + H + 1)]
-                    writes["qp"].append((c, i_centre))
+                writes["node"].append((m, nd))
+        elif name == "centre":
+            c = r - 1 + w
+            if c <= s1:
+                taken["centre"].append(c)
+                reads.extend(("node", x, nd) for x in range(c - H, c + H + 1))
+                writes["qp"].append((c, nd))
+        elif name == "iface":
             q = r - NMP - (1 if centre else 0) + w
             if s0 - NMP <= q <= s1 + NMP - 2:
                 taken["iface"].append(q)
+                # both sides' stencils (per-interface layout), the midpoint metrics and the
+                # central part of h (q - 2 .. q + 3; q - 3 .. q + 4 for WENOIU7)
                 lo, hi = (q - 3, q + 4) if H == 3 else (q - 2, q + 3)
-                reads += [("node", x, i_iface) for x in range(lo, hi + 1)]
+                reads.extend(("node", x, nd) for x in range(lo, hi + 1))
                 if centre:
-                    reads.append(("qp", q, i_iface))
-                writes["h"].append((q, i_iface))
+                    reads.append(("qp", q, nd))
+                writes["h"].append((q, nd))
+            s = r - lag + w
+            if s0 <= s < s1:
+                reads.append(("node", s, nd))            # the output's stage state, read here
+        elif name == "out":
             s = r - lag + w
             if s0 <= s < s1:
                 taken["out"].append(s)
-                reads += [("node", s, i_iface), ("h", s, i_out), ("h", s - 1, i_out)]
-    return writes, reads, taken
+                reads.extend([("h", s, nd), ("h", s - 1, nd)])
+
+    for t in range(steps):
+        for name, sync in phases:
+            for w in range(EW):
+                last[w] = order.node([last[w]])
+                phase(name, t, w, last[w])
+            if sync == "full":
+                b = order.node(last)
+                last = [b] * EW
+            elif sync == "chain":
+                arrived = None
+                for w in range(EW):
+                    waited = order.node([last[w], arrived])      # wait for warp w - 1
+                    arrived = order.node([waited])               # then arrive for warp w + 1
+                    last[w] = arrived
+    return order, writes, reads, taken
 
 
-def hazards(writes, reads):
+def hazards(order, writes, reads):
     bad = []
-    for ring, row, iv in reads:
-        hist = [(i, r) for (r, i) in writes[ring] if r % ERING == row % ERING]
-        mine = [i for (i, r) in hist if r == row and i < iv]
-        if not mine:
-            bad.append((ring, "not visible", row, iv))
+    for ring, row, nd in reads:
+        slot = [(r, wn) for (r, wn) in writes[ring] if r % ERING == row % ERING]
+        mine = [wn for (r, wn) in slot if r == row]
+        if len(mine) != 1 or not order.before(mine[0], nd):
+            bad.append((ring, "not visible", row))
             continue
-        # from the interval of the row's write up to the read, no other row in the slot
-        if any(max(mine) <= i <= iv and r != row for (i, r) in hist):
-            bad.append((ring, "overwritten", row, iv))
+        for r, wn in slot:
+            if r != row and not (order.before(wn, mine[0]) or order.before(nd, wn)):
+                bad.append((ring, "overwritten", row, r))
     return bad
 
 
-@pytest.mark.parametrize("centre", [True, False])
-@pytest.mark.parametrize("H,K", [(2, 2), (3, 3)])
-def test_eta_march_schedule(centre, H, K):
-    seg = 8 * EW - 1 - (1 if centre else 0)
+def _segments(seg):
     for n in list(range(1, 130)) + [255, 256, 299]:
         for s0 in range(0, n, seg):
-            s1 = min(n, s0 + seg)
-            writes, reads, taken = schedule(s0, s1, n, H, K, centre)
-            assert hazards(writes, reads) == [], (n, s0, s1)
-            assert sorted(taken["iface"]) == list(range(s0 - 1, s1)), (n, s0)
-            assert sorted(taken["out"]) == list(range(s0, s1)), (n, s0)
-            if centre:
-                assert sorted(taken["centre"]) == list(range(s0 - 1, s1 + 1)), (n, s0)
+            yield n, s0, min(n, s0 + seg)
 
 
-def test_eta_march_schedule_catches_a_missing_barrier():
-    # without the barrier between the centres and the interfaces, Q+ from the warp below is
-    # read in the interval that writes it
-    writes, reads, _ = schedule(0, 62, 200, 2, 2, True, centre_barrier=False)
-    assert any(ring == "qp" for ring, *_ in hazards(writes, reads))
+@pytest.mark.parametrize("layout", list(LAYOUTS))
+@pytest.mark.parametrize("H,K", [(2, 2), (3, 3)])
+def test_eta_march_schedule(layout, H, K):
+    seg = 8 * EW - 1 - (1 if layout.startswith("centre") else 0)
+    for n, s0, s1 in _segments(seg):
+        order, writes, reads, taken = schedule(s0, s1, n, H, K, layout)
+        assert hazards(order, writes, reads) == [], (layout, n, s0, s1)
+        assert sorted(taken["iface"]) == list(range(s0 - 1, s1)), (n, s0)
+        assert sorted(taken["out"]) == list(range(s0, s1)), (n, s0)
+        if layout.startswith("centre"):
+            assert sorted(taken["centre"]) == list(range(s0 - 1, s1 + 1)), (n, s0)
+
+
+@pytest.mark.parametrize("layout,weaker", [
+    ("centre", [("stage", "full"), ("centre", None), ("iface", "full"), ("out", None)]),
+    ("centre", [("stage", "full"), ("centre", "full"), ("iface", None), ("out", None)]),
+    ("centre", [("stage", "chain"), ("centre", "full"), ("iface", "full"), ("out", None)]),
+    ("barriers", [("stage", "full"), ("iface", None), ("out", None)]),
+    ("barriers", [("stage", None), ("iface", "full"), ("out", None)]),
+    ("barriers", [("stage", "chain"), ("iface", "chain"), ("out", None)]),
+])
+def test_eta_march_schedule_catches_a_missing_barrier(layout, weaker):
+    # a barrier dropped, or the staging barrier weakened to a hand-off, must show up as a hazard
+    keep = LAYOUTS[layout]
+    try:
+        LAYOUTS[layout] = weaker
+        order, writes, reads, _ = schedule(0, 62, 200, 2, 2, layout)
+        assert hazards(order, writes, reads)
+    finally:
+        LAYOUTS[layout] = keep
 
 
 def test_eta_march_schedule_catches_a_short_ring():
@@ -125,7 +195,7 @@ def test_eta_march_schedule_catches_a_short_ring():
     keep = ERING
     try:
         ERING = 8
-        writes, reads, _ = schedule(0, 62, 200, 3, 3, True)
-        assert hazards(writes, reads)
+        order, writes, reads, _ = schedule(0, 62, 200, 3, 3, "centre")
+        assert hazards(order, writes, reads)
     finally:
         ERING = keep
