@@ -340,7 +340,7 @@ void tiles_for(const fsp_batch* h, int dir, int v, std::vector<TileRef>& out) {
     if (dir == 0 && v == MARCH) T = march_seg_len(n);   // rows split into equal segments
     if (dir == 1 && v == MARCH) {
       const int nmp = (h->cfg.scheme == S32 || h->cfg.scheme == S52) ? 2 : 1;
-      T = march_eta_seg(nmp, march_eta_centres(fp64, nmp));
+      T = march_eta_seg(fp64, nmp);
       NL = 32;
     }
     for (int by = 0; by < (nl + NL - 1) / NL; ++by)

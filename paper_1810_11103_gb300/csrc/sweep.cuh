@@ -236,10 +236,15 @@ constexpr int EW = 8;                               // warps (rows per step) of 
 // Whether the marching eta pass evaluates the interface sides per centre node (centre_sides,
 // as the FP64 xi pass does): FP64 one-midpoint schemes, whose pass is bound by its FP64
 // instructions.  A step then takes the centres r - 1 + w and the interfaces one row behind
-// them, so a segment of eight steps ends one output earlier (62 rows).
+// them, so a segment of whole steps ends one output earlier (126 rows in sixteen steps).
 __host__ __device__ constexpr bool march_eta_centres(bool fp64, int nmp) { return fp64 && nmp == 1; }
-__host__ __device__ constexpr int march_eta_seg(int nmp, bool centre = false) {
-  return 8 * EW - (2 * nmp - 1) - (centre ? 1 : 0);
+// Steps per segment: sixteen (FP64), 32 (float paths).  Each CTA stages its segment's first
+// rows and waits for its first cp.async round trip before the steps overlap them, a cost that
+// longer segments spread over more rows; on the 64-block cylinder the eta pass took FP64
+// 8.05 -> 7.95 ms (8 -> 16 steps) and FP32 0.250 -> 0.229 -> 0.226 ms (8 -> 16 -> 32 steps).
+__host__ __device__ constexpr int march_eta_steps(bool fp64) { return fp64 ? 16 : 32; }
+__host__ __device__ constexpr int march_eta_seg(bool fp64, int nmp) {
+  return march_eta_steps(fp64) * EW - (2 * nmp - 1) - (march_eta_centres(fp64, nmp) ? 1 : 0);
 }
 
 // Host view of the tile shape: output nodes per line T and lines per CTA NL (for the
@@ -247,7 +252,7 @@ __host__ __device__ constexpr int march_eta_seg(int nmp, bool centre = false) {
 inline void tile_dims(int scheme, int dir, int& T, int& NL, int variant = 0, bool fp64 = false) {
   const int nmp = (scheme == S32 || scheme == S52) ? 2 : 1;
   if (dir == 0 && variant == MARCH) { NL = MARCH_WARPS; T = MARCH_SEG; return; }
-  if (dir == 1 && variant == MARCH) { NL = 32; T = march_eta_seg(nmp, march_eta_centres(fp64, nmp)); return; }
+  if (dir == 1 && variant == MARCH) { NL = 32; T = march_eta_seg(fp64, nmp); return; }
   NL = shape_nl(dir, variant);
   T = scheme == S74 ? 256 / NL - 5 : 256 / NL - nmp - 1;
 }
@@ -1163,7 +1168,7 @@ struct MarchEtaShape {
   static constexpr int NS = ERING * 32;             // ring entries (row slot x lane)
   static constexpr int NT = EW * 32;                // threads
   static constexpr bool CENTRE = march_eta_centres(sizeof(Real) == 8, NMP);
-  static constexpr int SEG = march_eta_seg(NMP, CENTRE);
+  static constexpr int SEG = march_eta_seg(sizeof(Real) == 8, NMP);
   static constexpr size_t o_h() { return Staged<Real, Acc>::bytes(NS); }
   static constexpr size_t o_f() { return o_h() + sizeof(Acc) * 4 * NS; }
   // Q+ of the interface above each centre node (4 Real per ring slot)

@@ -12,9 +12,9 @@ happens-before order of one segment from program order and the barriers, where a
 point is either a block barrier ("full") or a hand-off from warp to warp ("chain": warp w
 waits until warp w - 1 has arrived, then arrives itself, so that after its wait it follows
 every earlier phase of warps 0 .. w - 1; a weaker point the tests use to show that the block
-barriers cannot be thinned that way everywhere), and checks, for columns of 1 to 129, 255, 256 and 299 rows (every segment length up to a
-full one; first, inner and last segments) and stencil half-widths 2 (WENOIU3/5) and 3
-(WENOIU7):
+barriers cannot be thinned that way everywhere), and checks, for the kernel's segment lengths
+and eight-step ones, every column length up to a segment and a few of two and three segments
+(first, inner and last segments), and stencil half-widths 2 (WENOIU3/5) and 3 (WENOIU7):
 * every ring row a phase reads was written before the read, and every other row written to
   the same slot is ordered before that write or after the read;
 * every centre, interface and output of the segment is taken exactly once, within the step
@@ -152,15 +152,17 @@ def hazards(order, writes, reads):
 
 
 def _segments(seg):
-    for n in list(range(1, 130)) + [255, 256, 299]:
+    # every segment length up to a full one, and columns of two to three segments
+    for n in list(range(1, seg + 3)) + [2 * seg - 1, 2 * seg, 2 * seg + 1, 3 * seg - 2]:
         for s0 in range(0, n, seg):
             yield n, s0, min(n, s0 + seg)
 
 
-@pytest.mark.parametrize("layout", list(LAYOUTS))
+# the kernel's segments (sixteen steps in FP64, 32 in the float paths) and eight-step ones
+@pytest.mark.parametrize("layout,steps", [("barriers", 32), ("centre", 16), ("barriers", 8), ("centre", 8)])
 @pytest.mark.parametrize("H,K", [(2, 2), (3, 3)])
-def test_eta_march_schedule(layout, H, K):
-    seg = 8 * EW - 1 - (1 if layout.startswith("centre") else 0)
+def test_eta_march_schedule(layout, H, K, steps):
+    seg = steps * EW - 1 - (1 if layout.startswith("centre") else 0)
     for n, s0, s1 in _segments(seg):
         order, writes, reads, taken = schedule(s0, s1, n, H, K, layout)
         assert hazards(order, writes, reads) == [], (layout, n, s0, s1)

@@ -225,7 +225,7 @@ def test_batch_tile_shapes_agree(F, scheme, prec):
 @pytest.mark.parametrize("shape", [(1100, 6), (6, 1100), (45, 70)])
 def test_batch_marching_segments(F, scheme, shape):
     # lines longer than one marching segment: rows of 1100 nodes (xi: three segments of 384,
-    # 384, 332), columns of 1100 nodes (eta: segments of 62, 63 or 61 rows), partial warps (6 and
+    # 384, 332), columns of 1100 nodes (eta: FP64 segments of 126 or 125 rows), partial warps (6 and
     # 45 columns); periodic in both directions, against the oracle and the tile variants
     ni, nj = shape
     x, y, per = I.periodic_square(ni, 10.0, 0.2, seed=5, nj=nj)
